@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark: gasket cell-updates/s at n = 2^16 on one GB300, lambda map vs BB.
+
+One bench step is one pass of the whole hot path over the level-16 gasket
+(65536 x 65536 embedding, 3^16 cells): 100 B3/S23 automaton steps on the
+uint8 state, 200 FP32 heat-diffusion steps (a = 0.2) with a global-sum reduce
+after every 100, and a final count reduce of the automaton -- all launched
+through the C ABI on device-resident buffers.  value = 3^16 * 300 / step time.
+
+The same step is timed with the bounding-box launch (BB) and per kernel for
+rho in {8, 16, 32}; the map-only single write is timed separately.
+``--impl reference`` times the CPU oracle instead (a bounded sample).
+Run with torchrun for N > 1: the work does not shard across GPUs, so every
+rank runs an independent replica ("replicas only"), and value sums them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gasket cell-updates/s at n=2^16: λ-map vs BB on one GB300; % of HBM peak"
+K = 16
+N = 1 << K
+MEMBERS = 3 ** K
+CA_STEPS = 100
+DIFF_STEPS = 200
+REDUCE_EVERY = 100
+COEF = 0.2
+SEED = 0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (replicas only; host-side barrier and max of times)
+# --------------------------------------------------------------------------
+
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    dist.init_process_group("gloo")
+    return dist, dist.get_rank(), dist.get_world_size()
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for ln in f:
+                    parts = [p.strip() for p in ln.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+# --------------------------------------------------------------------------
+# oracle arm (CPU baseline and --impl reference)
+# --------------------------------------------------------------------------
+
+ORACLE_WINDOW = 4096  # sample: the [0, 4096)^2 corner of the level-16 array (3^12 members)
+
+
+def oracle_sample(ca_steps, diff_steps):
+    """Time the CPU oracle on the corner window of the workload; returns
+    (cell-updates per second, seconds, description)."""
+    import numpy as np
+    import oracle
+    import synth
+    w = ORACLE_WINDOW
+    dom = oracle.Domain.build(N, 0, 0, w, w)
+    s = dom.take(synth.bernoulli_u8(SEED, N, 0, 0, w, w))
+    u = dom.take(synth.uniform_f32(SEED, N, 0, 0, w, w)).astype(np.float64)
+    t0 = time.perf_counter()
+    for _ in range(ca_steps):
+        s = oracle.ca_step(dom, s)
+    for i in range(diff_steps):
+        u = oracle.diffusion_step(dom, u, COEF)
+        if (i + 1) % REDUCE_EVERY == 0:
+            oracle.reduce_sum(u)
+    oracle.reduce_sum(s)
+    dt = time.perf_counter() - t0
+    updates = dom.m * (ca_steps + diff_steps)
+    desc = (f"numpy oracle, single thread, window [0,{w})^2 of the k=16 array "
+            f"({dom.m} members), {ca_steps} CA + {diff_steps} diffusion steps")
+    return updates / dt, dt, desc
+
+
+def run_reference(args, dist, rank, world):
+    if rank != 0:
+        return
+    ca, df = 10, 20
+    for _ in range(args.warmup):
+        oracle_sample(ca, df)
+    times = []
+    rates = []
+    rate = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        rate, dt, desc = oracle_sample(ca, df)
+        times.append(dt)
+        rates.append(rate)
+    total = sum(times)
+    value = rate if not times else statistics.mean([r for r in rates])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u8",
+        "data": "synthetic (SplitMix64-seeded Bernoulli(0.5) uint8 and U[0,1) FP64 states)",
+        "config": {"workload": "CPU oracle on a bounded sample of the level-16 gasket workload", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rho-ca", type=int, default=32)
+    ap.add_argument("--rho-diff", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-detail", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        run_reference(args, None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
+    dist, rank, world = dist_init(args.gpus)
+
+    import torch
+    import paper_2004_13475_gb300 as fr
+    from paper_2004_13475_gb300 import build as fbuild
+    import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        fbuild.build()
+    barrier(dist)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    # device-resident state: uint8 automaton (4 GiB x 2), FP32 field (16 GiB x 2)
+    ca_a = torch.empty(N * N, dtype=torch.uint8, device="cuda")
+    ca_b = torch.empty_like(ca_a)
+    u_a = torch.empty(N * N, dtype=torch.float32, device="cuda")
+    u_b = torch.empty_like(u_a)
+    sums = torch.zeros(8, dtype=torch.float64, device="cuda")
+
+    def fill():
+        synth.device_fill(ca_a.data_ptr(), synth.SYNTH_BERNOULLI_U8, N, SEED + rank, stream=sptr)
+        synth.device_fill(u_a.data_ptr(), synth.SYNTH_UNIFORM_F32, N, SEED + rank, stream=sptr)
+
+    fill()
+    plans = {}
+
+    def plan(rho, mode):
+        key = (rho, mode)
+        if key not in plans:
+            plans[key] = fr.fractal_map(K, rho, mode)
+        return plans[key]
+
+    def step(mode, ev=None):
+        """One bench step; if ev is given, record events around the diffusion segments."""
+        pc, pd = plan(args.rho_ca, mode), plan(args.rho_diff, mode)
+        fr.fractal_step_ca(pc, ca_a, ca_b, CA_STEPS, stream)          # even: result back in ca_a
+        cur, oth = u_a, u_b
+        for seg in range(DIFF_STEPS // REDUCE_EVERY):
+            if ev is not None:
+                ev[0].append(torch.cuda.Event(enable_timing=True))
+                ev[1].append(torch.cuda.Event(enable_timing=True))
+                ev[0][-1].record(stream)
+            cur = fr.fractal_step_diffusion(pd, cur, oth, COEF, REDUCE_EVERY, stream)
+            if ev is not None:
+                ev[1][-1].record(stream)
+            oth = u_b if cur is u_a else u_a
+            fr.fractal_reduce_async(pd, cur, fr.FRACTAL_F32, sums[seg:seg + 1], stream)
+        fr.fractal_reduce_async(pc, ca_a, fr.FRACTAL_U8, sums[4:5], stream)
+        return cur
+
+    launches_per_step = CA_STEPS + DIFF_STEPS + 2 * (DIFF_STEPS // REDUCE_EVERY + 1)
+
+    def timed(mode, steps, warmup, ev=None):
+        for _ in range(warmup):
+            step(mode)
+        torch.cuda.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            step(mode, ev)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3
+
+    hbm, peak_kind = peaks()
+
+    # ---- headline: lambda ----
+    ev = ([], [])
+    with Clocks(local) as clk:
+        t_lam = timed(0, args.steps, args.warmup, ev)
+    clocks = clk.summary()
+    t_lam = max_over_ranks(dist, t_lam)
+    diff_ms = sum(a.elapsed_time(b) for a, b in zip(*ev))
+    diff_launch_s = diff_ms / 1e3 / (args.steps * DIFF_STEPS)
+    value = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * args.steps / t_lam
+
+    # ---- same step with the bounding-box launch ----
+    t_bb = max_over_ranks(dist, timed(1, max(1, args.steps // 2), 3))
+    value_bb = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * max(1, args.steps // 2) / t_bb
+
+    info_d = plan(args.rho_diff, 0).info()
+    info_c = plan(args.rho_ca, 0).info()
+    tile_bytes_d = (args.rho_diff * 4) * args.rho_diff     # FP32 tile
+    alg_bytes_d = 2 * info_d["member_tiles"] * tile_bytes_d  # read + write every member tile once
+    achieved = alg_bytes_d / diff_launch_s / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_lam / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+f32",
+        "data": "synthetic (SplitMix64-seeded Bernoulli(0.5) uint8 and U[0,1) FP32 states, generated on device)",
+        "config": {
+            "workload": (f"gasket k=16 (65536x65536, 3^16 cells): {CA_STEPS} B3/S23 CA steps (uint8, rho={args.rho_ca})"
+                         f" + {DIFF_STEPS} FP32 diffusion steps (a={COEF}, rho={args.rho_diff}) with a global-sum"
+                         f" reduce every {REDUCE_EVERY} + 1 count reduce"),
+            "map": "lambda", "k": K, "rho_ca": args.rho_ca, "rho_diffusion": args.rho_diff,
+            "cta_levels_ca": info_c["cta_levels"][0], "cta_levels_diffusion": info_d["cta_levels"][1],
+            "l2": "inputs larger than L2 (4 GiB uint8 + 16 GiB FP32 per buffer)",
+            "parallelism": "replicas only" if world > 1 else "single GPU",
+        },
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "roofline": {
+            "kernel": f"diffusion_kernel<lambda, rho={args.rho_diff}>", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "alg_bytes_per_launch": alg_bytes_d, "launch_us": diff_launch_s * 1e6,
+        },
+        "bb": {"value": value_bb, "ms_per_step": 1e3 * t_bb / max(1, args.steps // 2),
+               "speedup_lambda_over_bb": value / value_bb},
+    }
+
+    if rank == 0 and not args.no_detail:
+        line["detail"] = kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm)
+
+    # ---- end to end through the C ABI with host buffers ----
+    if not args.no_e2e:
+        line["e2e"] = e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world)
+
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt, desc = oracle_sample(CA_STEPS, DIFF_STEPS)
+        line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm):
+    """Per-kernel times for rho in {8, 16, 32}, lambda and BB (launch-averaged)."""
+    out = {}
+    reps = 10
+
+    def clock(fn):
+        for _ in range(3):
+            fn()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    for rho in (8, 16, 32):
+        for mode, name in ((0, "lambda"), (1, "bb")):
+            p = plan(rho, mode)
+            inf = p.info()
+            tiles = inf["member_tiles"]
+            rec = {}
+            t = clock(lambda: fr.fractal_step_ca(p, ca_a, ca_b, 2, stream)) / 2
+            b = 2 * tiles * rho * rho
+            rec["ca"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
+                         "frac": b / t / 1e9 / hbm, "cta_levels": inf["cta_levels"][0]}
+            t = clock(lambda: fr.fractal_step_diffusion(p, u_a, u_b, COEF, 2, stream)) / 2
+            b = 2 * tiles * rho * rho * 4
+            rec["diffusion"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
+                                "frac": b / t / 1e9 / hbm, "cta_levels": inf["cta_levels"][1]}
+            t = clock(lambda: fr.fractal_map_write(p, u_b, fr.FRACTAL_F32, 1.0, stream))
+            b = tiles * rho * rho * 4
+            rec["sw_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+            t = clock(lambda: fr.fractal_map_write(p, ca_b, fr.FRACTAL_U8, 1.0, stream))
+            b = tiles * rho * rho
+            rec["sw_u8"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+            dev_out = torch.zeros(1, dtype=torch.float64, device="cuda")
+            t = clock(lambda: fr.fractal_reduce_async(p, u_a, fr.FRACTAL_F32, dev_out, stream))
+            b = tiles * rho * rho * 4
+            rec["reduce_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+            out.setdefault(str(rho), {})[name] = rec
+        for kname in ("ca", "diffusion", "sw_f32", "sw_u8", "reduce_f32"):
+            lam = out[str(rho)]["lambda"][kname]["us"]
+            bb = out[str(rho)]["bb"][kname]["us"]
+            out[str(rho)].setdefault("speedup_lambda_over_bb", {})[kname] = bb / lam
+    return out
+
+
+def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):
+    """Same metric with host buffers: per step, copy both states in from pinned
+    host memory, run the step, copy both states and the sums back."""
+    h_ca = torch.empty(ca_a.numel(), dtype=torch.uint8, pin_memory=True)
+    h_u = torch.empty(u_a.numel(), dtype=torch.float32, pin_memory=True)
+    h_sums = torch.empty(sums.numel(), dtype=torch.float64, pin_memory=True)
+    ca_a_host = h_ca
+    u_host = h_u
+    ca_a_host.copy_(ca_a, non_blocking=False)
+    u_host.copy_(u_a, non_blocking=False)
+    steps = max(1, min(args.steps, 2))
+
+    def one():
+        ca_a.copy_(ca_a_host, non_blocking=True)
+        u_a.copy_(u_host, non_blocking=True)
+        res = step(0)
+        ca_a_host.copy_(ca_a, non_blocking=True)
+        u_host.copy_(res, non_blocking=True)
+        h_sums.copy_(sums, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        one()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    t = max_over_ranks(dist, t0.elapsed_time(t1) / 1e3)
+    nbytes = ca_a.numel() + 4 * u_a.numel()
+    return {"value": world * MEMBERS * (CA_STEPS + DIFF_STEPS) * steps / t, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8 * sums.numel(),
+            "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "note": "whole n x n arrays copied each way through pinned host memory"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * fractal.h -- C ABI of the GB300 (sm_103a) block-space-map library for the
+ * embedded Sierpinski gasket.
+ *
+ * Method: "Efficient GPU Thread Mapping on Embedded 2D Fractals" (Navarro,
+ * Quezada, Hitschfeld, Vega, Bustos).  A compact grid of 3^{r_b} blocks
+ * (Lemma 2) is sent onto the member tiles of a gasket of level k embedded in
+ * an n x n array (n = 2^k) by the block-space map lambda(omega) (Theorem 1,
+ * Sec. 6.1); each tile of rho x rho cells is processed with the bounding
+ * sub-box approach (Sec. 5.3).  The bounding-box (BB) launch, which maps
+ * blocks by the identity and discards non-member ones (Sec. 1, Theorem 2), is
+ * built beside it as the plain method.
+ *
+ * Geometry and layout (all entry points):
+ *   - cell (x, y) is a gasket member iff 0 <= x, y < n and (x & y) == 0;
+ *   - every data buffer is a caller-owned DEVICE array of n*n elements,
+ *     row-major (element index y*n + x), 16-byte aligned;
+ *   - kernels read only member cells: the contents of non-member cells of an
+ *     input are ignored;
+ *   - kernels that write a field write every cell of every member tile
+ *     (value at members, 0 at the non-member cells of that tile) and leave
+ *     all cells outside member tiles untouched;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All calls are asynchronous on that stream except
+ *     fractal_reduce, which synchronises it.
+ *
+ * Status: every entry point returns FRACTAL_OK (0) or a negative code; the
+ * caller's buffers are not touched when a call fails validation.  No call
+ * aborts the process.
+ */
+#ifndef FRACTAL_H_
+#define FRACTAL_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FRACTAL_OK 0
+#define FRACTAL_EINVAL (-1)  /* bad argument: level, rho, mode, dtype, pointer, alignment */
+#define FRACTAL_ENOMEM (-2)  /* host or device allocation failed */
+#define FRACTAL_ECUDA (-3)   /* a CUDA runtime call or kernel launch failed */
+
+/* Launch modes. */
+#define FRACTAL_LAMBDA 0     /* compact grid + lambda(omega) (Theorem 1) */
+#define FRACTAL_BB 1         /* bounding-box grid, identity map, discard non-members */
+
+/* Element types. */
+#define FRACTAL_U8 0         /* uint8 automaton states (nonzero = alive) */
+#define FRACTAL_F32 1        /* float32 field */
+
+#define FRACTAL_MAX_LEVEL 16
+
+typedef struct fractal_plan_s* fractal_plan_t;
+
+/* Read-only description of a plan (filled by fractal_plan_get_info). */
+typedef struct fractal_plan_info {
+  int32_t k;             /* gasket level; n = 2^k */
+  int32_t rho;           /* tile side (block size of the map) */
+  int32_t mode;          /* FRACTAL_LAMBDA or FRACTAL_BB */
+  int32_t r_b;           /* block-space level k - log2(rho) (Theorem 1) */
+  int64_t n;             /* embedding side */
+  int64_t n_b;           /* blocks per side, 2^r_b */
+  int32_t grid_w;        /* packed grid of the map at block level: 3^ceil(r_b/2) (Lemma 2) */
+  int32_t grid_h;        /*                                      3^floor(r_b/2) */
+  int64_t member_tiles;  /* 3^r_b */
+  int64_t members;       /* 3^k cells */
+  int32_t cta_levels[2]; /* per dtype: tile levels unrolled inside one CTA (Sec. 5.1) */
+  int64_t ctas[2];       /* per dtype: CTAs one launch of this plan starts */
+  int32_t threads[2];    /* per dtype: threads per CTA */
+  int32_t smem_bytes[2]; /* per dtype: dynamic shared memory per CTA of a step kernel */
+} fractal_plan_info;
+
+/* Human-readable text of a status code (static storage). */
+const char* fractal_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread inside the library ("" if none). */
+const char* fractal_last_cuda_error(void);
+
+/*
+ * fractal_map -- build a plan for level k (0 <= k <= 16), tile side rho
+ * (power of two, 1 <= rho <= min(32, 2^k)) and a launch mode.
+ * Theorem 1: r_b = k - log2(rho); the lambda grid is the Lemma-2 orthotope of
+ * 3^ceil(r_b/2) x 3^floor(r_b/2) blocks, the BB grid is n_b x n_b.
+ * The plan belongs to the CUDA device current at this call, owns a small
+ * device scratch area for fractal_reduce and a pinned host word; it is freed
+ * by fractal_plan_destroy.  One plan may be used from one host thread at a
+ * time.  Errors: FRACTAL_EINVAL (bad k, rho, mode or NULL out),
+ * FRACTAL_ENOMEM, FRACTAL_ECUDA.
+ */
+int fractal_map(int k, int rho, int mode, fractal_plan_t* plan);
+
+/* Free a plan (NULL is accepted).  Waits for nothing: the caller must make
+ * sure no work using the plan is still queued. */
+int fractal_plan_destroy(fractal_plan_t plan);
+
+int fractal_plan_get_info(fractal_plan_t plan, fractal_plan_info* info);
+
+/*
+ * Tile levels unrolled inside one CTA for dtype (Sec. 5.1, "further
+ * unrolling"): a CTA handles the 3^levels member tiles (lambda) or 4^levels
+ * tile slots (BB) of one super-tile of side rho * 2^levels; the grid maps
+ * super-tiles (level r_b - levels).  0 <= levels <= min(r_b, 5), and the
+ * super-tile must fit in shared memory.  Errors: FRACTAL_EINVAL,
+ * FRACTAL_ENOMEM (reduce scratch could not grow).
+ */
+int fractal_plan_set_cta_levels(fractal_plan_t plan, int dtype, int levels);
+
+/*
+ * fractal_map_blocks -- export the block-space map of the plan (Theorem 1,
+ * Sec. 6.1): for omega in row-major order of the grid_w x grid_h packed grid,
+ * dev_xy[2*(wy*grid_w + wx) + {0,1}] = (block_x, block_y) in the
+ * (x & y) == 0 orientation.  dev_xy: device array of 2*3^r_b int32, written
+ * entirely.  Computed by the same warp-level lambda the step kernels use.
+ * Errors: FRACTAL_EINVAL (NULL), FRACTAL_ECUDA.
+ */
+int fractal_map_blocks(fractal_plan_t plan, int32_t* dev_xy, void* stream);
+
+/*
+ * fractal_map_write -- the single-write test of Sec. 6.2 (SW): write `value`
+ * (cast to dtype; uint8 takes (uint8_t)value) at every member cell of the
+ * n x n device array dev_buf, 0 at the non-member cells of member tiles;
+ * nothing is read.  Errors: FRACTAL_EINVAL (NULL, misaligned, dtype),
+ * FRACTAL_ECUDA.
+ */
+int fractal_map_write(fractal_plan_t plan, void* dev_buf, int dtype, double value, void* stream);
+
+/*
+ * fractal_step_ca -- `steps` synchronous steps of the fractal Life-like
+ * automaton of Sec. 6.2 (test CA), rule B3/S23 on the Moore neighbourhood,
+ * counting only member neighbours; non-members are never born.  States are
+ * uint8 (nonzero = alive; outputs are 0/1).  dev_a holds the start state;
+ * the steps alternate dev_a -> dev_b -> dev_a ...: after the call the state
+ * is in dev_a when `steps` is even and in dev_b when it is odd.  Both buffers
+ * are n*n bytes, 16-byte aligned, distinct.  steps == 0 does nothing.
+ * Errors: FRACTAL_EINVAL (NULL, equal or misaligned buffers, steps < 0),
+ * FRACTAL_ECUDA.
+ */
+int fractal_step_ca(fractal_plan_t plan, uint8_t* dev_a, uint8_t* dev_b, int steps, void* stream);
+
+/*
+ * fractal_step_diffusion -- `steps` explicit FDM heat-diffusion steps on the
+ * gasket (the FDM time-step pattern of Sec. 1), FP32:
+ *   u'_c = u_c + a * sum_{nb in N4(c), nb member} (u_nb - u_c),
+ * zero flux towards non-members and the array edge.  a = alpha*dt; the
+ * scheme is stable and positivity-preserving for 0 <= a < 1/3 (members have
+ * at most three 4-neighbours).  Buffers and ping-pong as in fractal_step_ca
+ * (n*n floats each).  Errors: FRACTAL_EINVAL (NULL, equal or misaligned
+ * buffers, steps < 0, a not finite), FRACTAL_ECUDA.
+ */
+int fractal_step_diffusion(fractal_plan_t plan, float* dev_a, float* dev_b, float a, int steps,
+                           void* stream);
+
+/*
+ * fractal_reduce -- the reduction test of Sec. 6.2 (RD): the sum over all
+ * member cells of dev_buf (uint8: number of alive members, exact; float32:
+ * per-thread FP32 partials of at most 16 cells, summed in FP64 in a fixed
+ * order, so the result is deterministic).  Writes the result to *host_out
+ * and synchronises `stream`.  Errors: FRACTAL_EINVAL (NULL, misaligned,
+ * dtype), FRACTAL_ECUDA.
+ */
+int fractal_reduce(fractal_plan_t plan, const void* dev_buf, int dtype, double* host_out,
+                   void* stream);
+
+/*
+ * fractal_reduce_async -- as fractal_reduce, but the result is written to the
+ * device double *dev_out and nothing is synchronised (usable inside a step
+ * loop or a CUDA graph).  Uses the plan's scratch: calls on one plan must be
+ * ordered on one stream.  Errors: as fractal_reduce.
+ */
+int fractal_reduce_async(fractal_plan_t plan, const void* dev_buf, int dtype, double* dev_out,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRACTAL_H_ */

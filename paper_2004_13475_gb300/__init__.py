@@ -1,0 +1,213 @@
+"""Python binding of libfractal.so (C ABI in include/fractal.h).
+
+Argument marshalling only: every step of the map and the workloads runs in
+the library's CUDA kernels.  Tensors are used for device memory and streams;
+any object with ``data_ptr()`` (a CUDA tensor) or a plain integer device
+address is accepted.  There is no CPU path: importing works anywhere, but the
+first call loads the library and raises if it was not built, and the library
+itself needs a CUDA device.
+
+Names follow the C ABI: ``fractal_map`` returns a :class:`Plan`; the step,
+write and reduce calls take the plan first.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+FRACTAL_OK = 0
+FRACTAL_EINVAL = -1
+FRACTAL_ENOMEM = -2
+FRACTAL_ECUDA = -3
+
+FRACTAL_LAMBDA = 0
+FRACTAL_BB = 1
+FRACTAL_U8 = 0
+FRACTAL_F32 = 1
+FRACTAL_MAX_LEVEL = 16
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfractal.so")
+
+# Every entry point declared in include/fractal.h.
+EXPORTS = (
+    "fractal_strerror", "fractal_last_cuda_error", "fractal_map", "fractal_plan_destroy",
+    "fractal_plan_get_info", "fractal_plan_set_cta_levels", "fractal_map_blocks",
+    "fractal_map_write", "fractal_step_ca", "fractal_step_diffusion", "fractal_reduce",
+    "fractal_reduce_async",
+)
+
+
+class FractalError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _load()
+        msg = lib.fractal_strerror(status).decode()
+        cuda = lib.fractal_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f"; {cuda}" if cuda and status == FRACTAL_ECUDA else ""))
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int32), ("rho", ctypes.c_int32), ("mode", ctypes.c_int32), ("r_b", ctypes.c_int32),
+        ("n", ctypes.c_int64), ("n_b", ctypes.c_int64), ("grid_w", ctypes.c_int32), ("grid_h", ctypes.c_int32),
+        ("member_tiles", ctypes.c_int64), ("members", ctypes.c_int64),
+        ("cta_levels", ctypes.c_int32 * 2), ("ctas", ctypes.c_int64 * 2),
+        ("threads", ctypes.c_int32 * 2), ("smem_bytes", ctypes.c_int32 * 2),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+_lib = None
+
+
+def _load() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, F, VP = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.c_void_p
+    sig = {
+        "fractal_strerror": (ctypes.c_char_p, [I]),
+        "fractal_last_cuda_error": (ctypes.c_char_p, []),
+        "fractal_map": (I, [I, I, I, ctypes.POINTER(P)]),
+        "fractal_plan_destroy": (I, [P]),
+        "fractal_plan_get_info": (I, [P, ctypes.POINTER(PlanInfo)]),
+        "fractal_plan_set_cta_levels": (I, [P, I, I]),
+        "fractal_map_blocks": (I, [P, VP, VP]),
+        "fractal_map_write": (I, [P, VP, I, D, VP]),
+        "fractal_step_ca": (I, [P, VP, VP, I, VP]),
+        "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
+        "fractal_reduce": (I, [P, VP, I, ctypes.POINTER(D), VP]),
+        "fractal_reduce_async": (I, [P, VP, I, VP, VP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:  # pragma: no cover - torch absent
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check(status: int, where: str) -> None:
+    if status != FRACTAL_OK:
+        raise FractalError(status, where)
+
+
+class Plan:
+    """Owner of a ``fractal_plan_t`` (freed on close / garbage collection)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("plan is closed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(_load().fractal_plan_get_info(self.handle, ctypes.byref(inf)), "fractal_plan_get_info")
+        return inf.as_dict()
+
+    def close(self) -> None:
+        if self._h:
+            _load().fractal_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fractal_map(k: int, rho: int, mode: int = FRACTAL_LAMBDA) -> Plan:
+    h = ctypes.c_void_p()
+    _check(_load().fractal_map(k, rho, mode, ctypes.byref(h)), "fractal_map")
+    return Plan(h.value)
+
+
+def fractal_plan_set_cta_levels(plan: Plan, dtype: int, levels: int) -> None:
+    _check(_load().fractal_plan_set_cta_levels(plan.handle, dtype, levels), "fractal_plan_set_cta_levels")
+
+
+def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:
+    _check(_load().fractal_map_blocks(plan.handle, _ptr(dev_xy), _stream(stream)), "fractal_map_blocks")
+
+
+def fractal_map_write(plan: Plan, buf, dtype: int, value: float, stream=None) -> None:
+    _check(_load().fractal_map_write(plan.handle, _ptr(buf), dtype, float(value), _stream(stream)),
+           "fractal_map_write")
+
+
+def fractal_step_ca(plan: Plan, a, b, steps: int, stream=None):
+    """Run `steps` CA steps; returns whichever of (a, b) holds the result."""
+    _check(_load().fractal_step_ca(plan.handle, _ptr(a), _ptr(b), int(steps), _stream(stream)),
+           "fractal_step_ca")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_step_diffusion(plan: Plan, a, b, coef: float, steps: int, stream=None):
+    """Run `steps` diffusion steps with a = alpha*dt; returns the buffer holding the result."""
+    _check(_load().fractal_step_diffusion(plan.handle, _ptr(a), _ptr(b), float(coef), int(steps),
+                                          _stream(stream)), "fractal_step_diffusion")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_reduce(plan: Plan, buf, dtype: int, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(_load().fractal_reduce(plan.handle, _ptr(buf), dtype, ctypes.byref(out), _stream(stream)),
+           "fractal_reduce")
+    return out.value
+
+
+def fractal_reduce_async(plan: Plan, buf, dtype: int, dev_out, stream=None) -> None:
+    _check(_load().fractal_reduce_async(plan.handle, _ptr(buf), dtype, _ptr(dev_out), _stream(stream)),
+           "fractal_reduce_async")
+
+
+def fractal_strerror(status: int) -> str:
+    return _load().fractal_strerror(status).decode()
+
+
+def fractal_last_cuda_error() -> str:
+    return _load().fractal_last_cuda_error().decode()

@@ -1,0 +1,303 @@
+// C ABI of the library (declared in include/fractal.h): plans, validation,
+// launch geometry and the step drivers.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/fractal.h"
+#include "launch.h"
+
+namespace fractal {
+namespace {
+
+thread_local char g_last_cuda_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where) {
+  std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", where, cudaGetErrorString(e));
+  return FRACTAL_ECUDA;
+}
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+constexpr int kMaxLevelsPerCta = 5;
+constexpr int kMaxSmem = 200 * 1024;
+
+}  // namespace
+}  // namespace fractal
+
+using namespace fractal;
+
+struct fractal_plan_s {
+  int k = 0, log_rho = 0, rb = 0, mode = 0;
+  int32_t n = 1;
+  int device = 0;
+  int m[2] = {0, 0};            // tile levels per CTA, per dtype
+  Launch step[2];               // CA (u8) / diffusion (f32) kernels
+  Launch aux[2];                // SW / reduce kernels (slot table only in shared memory)
+  void* d_partials = nullptr;   // reduce scratch: one 8-byte partial per CTA
+  size_t partials_cap = 0;      // elements
+  double* d_result = nullptr;
+  double* h_result = nullptr;   // pinned
+};
+
+namespace {
+
+// Geometry for one dtype at `levels` tile levels per CTA; returns false if it
+// does not fit (grid limits, shared memory).
+bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, Launch& aux) {
+  if (levels < 0 || levels > p.rb || levels > kMaxLevelsPerCta) return false;
+  const int R = p.rb - levels;
+  const int rho = 1 << p.log_rho;
+  Geo g;
+  g.n = p.n;
+  g.m = levels;
+  g.R = R;
+  g.T = rho << levels;
+  g.slots = (int)(p.mode == kLambda ? ipow(3, levels) : ipow(4, levels));
+  g.lw = (int)ipow(3, (levels + 1) / 2);
+  dim3 grid;
+  if (p.mode == kLambda) {
+    grid = dim3((unsigned)ipow(3, (R + 1) / 2), (unsigned)ipow(3, R / 2), 1);
+  } else {
+    if (R > 15) return false;  // gridDim.y <= 65535
+    grid = dim3(1u << R, 1u << R, 1);
+  }
+  // chunks (row segments) per tile: uint8 one per row; float32 float4s
+  const int wc = dtype == FRACTAL_U8 ? rho : (rho < 4 ? rho : 4);
+  const int64_t chunks = (int64_t)g.slots * rho * (rho / wc);
+  const int64_t ipt = (chunks + 255) / 256;
+  int threads = (int)(((chunks + ipt - 1) / ipt + 31) / 32 * 32);
+  if (threads < 32) threads = 32;
+  if (threads > 512) threads = 512;
+  const int tab_bytes = tab_words(g.slots) * 4;
+  int smem;
+  if (dtype == FRACTAL_U8) {
+    smem = tab_bytes + (g.T + 2) * ((g.T >> 5) + 3) * 4;
+  } else {
+    smem = tab_bytes + (g.T + 2) * (((g.T + 3) & ~3) + 8) * 4;
+  }
+  if (smem > kMaxSmem) return false;
+  step.grid = grid;
+  step.threads = threads;
+  step.smem = smem;
+  step.geo = g;
+  aux = step;
+  aux.smem = tab_bytes;
+  return true;
+}
+
+int default_levels(const fractal_plan_s& p, int dtype) {
+  // Super-tile of about 128 uint8 cells or 64 float cells per side; BB also
+  // needs 2^R <= 32768.
+  const int target = dtype == FRACTAL_U8 ? 7 : 6;
+  int m = target - p.log_rho;
+  if (m < 0) m = 0;
+  if (m > p.rb) m = p.rb;
+  if (m > kMaxLevelsPerCta) m = kMaxLevelsPerCta;
+  if (p.mode == kBB && p.rb - m > 15) m = p.rb - 15;
+  return m;
+}
+
+int ensure_partials(fractal_plan_s* p) {
+  size_t need = 1;
+  for (int d = 0; d < 2; ++d) {
+    const size_t c = (size_t)p->aux[d].grid.x * p->aux[d].grid.y;
+    if (c > need) need = c;
+  }
+  if (need <= p->partials_cap) return FRACTAL_OK;
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, need * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FRACTAL_ENOMEM;
+  }
+  if (p->d_partials) cudaFree(p->d_partials);
+  p->d_partials = buf;
+  p->partials_cap = need;
+  return FRACTAL_OK;
+}
+
+int check_plan(const fractal_plan_s* p) { return p ? FRACTAL_OK : FRACTAL_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+const char* fractal_strerror(int status) {
+  switch (status) {
+    case FRACTAL_OK: return "ok";
+    case FRACTAL_EINVAL: return "invalid argument";
+    case FRACTAL_ENOMEM: return "out of memory";
+    case FRACTAL_ECUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+const char* fractal_last_cuda_error(void) { return g_last_cuda_error; }
+
+int fractal_map(int k, int rho, int mode, fractal_plan_t* out) {
+  if (out == nullptr) return FRACTAL_EINVAL;
+  *out = nullptr;
+  if (k < 0 || k > FRACTAL_MAX_LEVEL) return FRACTAL_EINVAL;
+  if (rho < 1 || rho > 32 || (rho & (rho - 1)) != 0 || rho > (1 << k)) return FRACTAL_EINVAL;
+  if (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB) return FRACTAL_EINVAL;
+  fractal_plan_s* p = new (std::nothrow) fractal_plan_s();
+  if (!p) return FRACTAL_ENOMEM;
+  p->k = k;
+  p->log_rho = ilog2c(rho);
+  p->rb = k - p->log_rho;
+  p->mode = mode;
+  p->n = 1 << k;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  for (int d = 0; d < 2; ++d) {
+    p->m[d] = default_levels(*p, d);
+    if (!make_launch(*p, d, p->m[d], p->step[d], p->aux[d])) {
+      delete p;
+      return FRACTAL_EINVAL;
+    }
+  }
+  int st = ensure_partials(p);
+  if (st != FRACTAL_OK) {
+    delete p;
+    return st;
+  }
+  if (cudaMalloc(&p->d_result, sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&p->h_result, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    fractal_plan_destroy(p);
+    return FRACTAL_ENOMEM;
+  }
+  *out = p;
+  return FRACTAL_OK;
+}
+
+int fractal_plan_destroy(fractal_plan_t p) {
+  if (!p) return FRACTAL_OK;
+  if (p->d_partials) cudaFree(p->d_partials);
+  if (p->d_result) cudaFree(p->d_result);
+  if (p->h_result) cudaFreeHost(p->h_result);
+  delete p;
+  return FRACTAL_OK;
+}
+
+int fractal_plan_get_info(fractal_plan_t p, fractal_plan_info* info) {
+  if (!p || !info) return FRACTAL_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->k = p->k;
+  info->rho = 1 << p->log_rho;
+  info->mode = p->mode;
+  info->r_b = p->rb;
+  info->n = p->n;
+  info->n_b = (int64_t)1 << p->rb;
+  info->grid_w = (int32_t)ipow(3, (p->rb + 1) / 2);
+  info->grid_h = (int32_t)ipow(3, p->rb / 2);
+  info->member_tiles = ipow(3, p->rb);
+  info->members = ipow(3, p->k);
+  for (int d = 0; d < 2; ++d) {
+    info->cta_levels[d] = p->m[d];
+    info->ctas[d] = (int64_t)p->step[d].grid.x * p->step[d].grid.y;
+    info->threads[d] = p->step[d].threads;
+    info->smem_bytes[d] = p->step[d].smem;
+  }
+  return FRACTAL_OK;
+}
+
+int fractal_plan_set_cta_levels(fractal_plan_t p, int dtype, int levels) {
+  if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32)) return FRACTAL_EINVAL;
+  Launch s, a;
+  if (!make_launch(*p, dtype, levels, s, a)) return FRACTAL_EINVAL;
+  const Launch old_s = p->step[dtype], old_a = p->aux[dtype];
+  const int old_m = p->m[dtype];
+  p->step[dtype] = s;
+  p->aux[dtype] = a;
+  p->m[dtype] = levels;
+  int st = ensure_partials(p);
+  if (st != FRACTAL_OK) {
+    p->step[dtype] = old_s;
+    p->aux[dtype] = old_a;
+    p->m[dtype] = old_m;
+  }
+  return st;
+}
+
+int fractal_map_blocks(fractal_plan_t p, int32_t* dev_xy, void* stream) {
+  if (check_plan(p) || !dev_xy) return FRACTAL_EINVAL;
+  const int w = (int)ipow(3, (p->rb + 1) / 2), h = (int)ipow(3, p->rb / 2);
+  cudaError_t e = launch_map_blocks(dev_xy, w, h, p->rb, (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "map_blocks");
+}
+
+int fractal_map_write(fractal_plan_t p, void* dev_buf, int dtype, double value, void* stream) {
+  if (check_plan(p) || !dev_buf || !aligned16(dev_buf)) return FRACTAL_EINVAL;
+  if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
+  cudaError_t e = launch_sw(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, value, (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "map_write");
+}
+
+int fractal_step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, void* stream) {
+  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0)
+    return FRACTAL_EINVAL;
+  uint8_t* cur = a;
+  uint8_t* nxt = b;
+  for (int s = 0; s < steps; ++s) {
+    cudaError_t e = launch_ca(p->mode, p->log_rho, p->step[FRACTAL_U8], cur, nxt, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    uint8_t* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  return FRACTAL_OK;
+}
+
+int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, void* stream) {
+  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0 ||
+      !std::isfinite(coef))
+    return FRACTAL_EINVAL;
+  float* cur = a;
+  float* nxt = b;
+  for (int s = 0; s < steps; ++s) {
+    cudaError_t e =
+        launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], cur, nxt, coef, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+    float* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  return FRACTAL_OK;
+}
+
+int fractal_reduce_async(fractal_plan_t p, const void* dev_buf, int dtype, double* dev_out, void* stream) {
+  if (check_plan(p) || !dev_buf || !dev_out || !aligned16(dev_buf)) return FRACTAL_EINVAL;
+  if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
+  cudaError_t e = launch_reduce(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, p->d_partials, dev_out,
+                                (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "reduce");
+}
+
+int fractal_reduce(fractal_plan_t p, const void* dev_buf, int dtype, double* host_out, void* stream) {
+  if (check_plan(p) || !host_out) return FRACTAL_EINVAL;
+  int st = fractal_reduce_async(p, dev_buf, dtype, p->d_result, stream);
+  if (st != FRACTAL_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(p->h_result, p->d_result, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "reduce copy");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reduce sync");
+  *host_out = *p->h_result;
+  return FRACTAL_OK;
+}
+
+}  // extern "C"

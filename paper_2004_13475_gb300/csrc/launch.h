@@ -1,0 +1,32 @@
+// Host-side launch descriptors and per-family dispatchers (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gasket.cuh"
+
+namespace fractal {
+
+struct Launch {
+  dim3 grid;
+  int threads;
+  int smem;  // dynamic shared memory bytes
+  Geo geo;
+};
+
+// Each returns the launch error (cudaSuccess when queued).
+cudaError_t launch_ca(int mode, int log_rho, const Launch& L, const uint8_t* in, uint8_t* out,
+                      cudaStream_t s);
+cudaError_t launch_diffusion(int mode, int log_rho, const Launch& L, const float* in, float* out,
+                             float a, cudaStream_t s);
+cudaError_t launch_sw(int mode, int log_rho, int dtype, const Launch& L, void* out, double value,
+                      cudaStream_t s);
+cudaError_t launch_reduce(int mode, int log_rho, int dtype, const Launch& L, const void* in,
+                          void* partials, double* dev_out, cudaStream_t s);
+cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s);
+
+// Dynamic shared memory above the 48 KB default needs an opt-in per kernel.
+cudaError_t allow_smem(const void* func, int bytes);
+
+}  // namespace fractal

@@ -91,6 +91,19 @@ def uniform_f32(seed: int, n: int, x0: int = 0, y0: int = 0,
     return (lo + width * u).astype(np.float32)
 
 
+def values_at(seed: int, n: int, xs: np.ndarray, ys: np.ndarray, dist: str = "uniform",
+              lo: float = 0.0, width: float = 1.0) -> np.ndarray:
+    """Values of the cells (xs[i], ys[i]) only (same numbers as the window functions)."""
+    xs = np.asarray(xs, dtype=np.uint64)
+    ys = np.asarray(ys, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        h = splitmix64(seed, ys * np.uint64(n) + xs)
+    if dist == "bernoulli":
+        return (h >> np.uint64(63)).astype(np.uint8)
+    u = (h >> np.uint64(40)).astype(np.float64) * 2.0 ** -24
+    return (lo + width * u).astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # Device twin (CUDA).  Loaded lazily; only GPU tests and the benchmark use it.
 # --------------------------------------------------------------------------

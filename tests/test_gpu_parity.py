@@ -1,0 +1,308 @@
+"""Element-by-element parity of the CUDA path against the CPU oracle, through
+the C ABI, on sizes the oracle finishes in seconds.  Maps, the single write
+and the automaton are bit-exact; FP32 diffusion is held to the FP64 oracle."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import SENTINEL_F32, SENTINEL_U8, check_field_contract, rel_err, tile_cover
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_2004_13475_gb300 import build as fbuild
+    fbuild.build()
+    import paper_2004_13475_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+@functools.lru_cache(maxsize=None)
+def domain(k):
+    return oracle.Domain.build(1 << k)
+
+
+def cases(ks, rhos=(1, 2, 4, 8, 16, 32)):
+    return [(k, r) for k in ks for r in rhos if r <= (1 << k)]
+
+
+MODES = [0, 1]   # FRACTAL_LAMBDA, FRACTAL_BB
+
+
+def dev_u8(arr):
+    return torch.from_numpy(np.ascontiguousarray(arr).reshape(-1)).cuda()
+
+
+def dev_f32(arr):
+    return torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float32).reshape(-1)).cuda()
+
+
+# ------------------------------------------------------------------ map ----
+
+@pytest.mark.parametrize("k,rho", cases(range(0, 11)))
+def test_map_blocks_bit_exact(fr, k, rho):
+    plan = fr.fractal_map(k, rho)
+    info = plan.info()
+    xy = torch.full((2 * info["member_tiles"],), -1, dtype=torch.int32, device="cuda")
+    fr.fractal_map_blocks(plan, xy)
+    assert np.array_equal(xy.cpu().numpy(), oracle.block_table(k, rho).reshape(-1))
+
+
+def test_map_blocks_level16(fr):
+    # full-size block level r_b = 13 (k = 16, rho = 8): bijection onto member blocks
+    plan = fr.fractal_map(16, 8)
+    info = plan.info()
+    xy = torch.empty((info["member_tiles"], 2), dtype=torch.int32, device="cuda")
+    fr.fractal_map_blocks(plan, xy)
+    bx, by = xy[:, 0].long(), xy[:, 1].long()
+    assert int(((bx & by) != 0).sum()) == 0
+    assert int(bx.max()) < 8192 and int(by.max()) < 8192
+    key = torch.unique(by * 8192 + bx)
+    assert key.numel() == 3 ** 13
+    # spot rows against the oracle's formula
+    W = info["grid_w"]
+    for wx, wy in [(0, 0), (W - 1, 0), (5, 7), (W - 1, info["grid_h"] - 1), (1234, 321)]:
+        assert tuple(xy[wy * W + wx].tolist()) == oracle.lambda_canonical(wx, wy, 13)
+
+
+# ------------------------------------------------------------------- SW ----
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k,rho", cases([0, 1, 2, 3, 5, 8, 10]))
+def test_single_write(fr, k, rho, mode):
+    n = 1 << k
+    plan = fr.fractal_map(k, rho, mode)
+    mask = oracle.member_mask(n)
+    b8 = torch.full((n * n,), SENTINEL_U8, dtype=torch.uint8, device="cuda")
+    fr.fractal_map_write(plan, b8, fr.FRACTAL_U8, 3)
+    check_field_contract(b8.cpu().numpy().reshape(n, n), (oracle.sw_write(n, 3)).astype(np.uint8), n, rho,
+                         SENTINEL_U8, mask)
+    bf = torch.full((n * n,), SENTINEL_F32, dtype=torch.float32, device="cuda")
+    fr.fractal_map_write(plan, bf, fr.FRACTAL_F32, 1.5)
+    check_field_contract(bf.cpu().numpy().reshape(n, n), oracle.sw_write(n, 1.5).astype(np.float32), n, rho,
+                         SENTINEL_F32, mask)
+
+
+# ------------------------------------------------------------------- CA ----
+
+def run_ca(fr, plan, s0, steps, sentinel=SENTINEL_U8):
+    n = s0.shape[0]
+    a = dev_u8(s0)
+    b = torch.full_like(a, sentinel)
+    out = fr.fractal_step_ca(plan, a, b, steps)
+    return out.cpu().numpy().reshape(n, n), a, b
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k,rho", cases([1, 2, 3, 4, 6, 8, 10]))
+def test_ca_bit_exact(fr, k, rho, mode):
+    n = 1 << k
+    plan = fr.fractal_map(k, rho, mode)
+    s0 = synth.bernoulli_u8(k, n)          # non-member cells hold noise and must be ignored
+    want = oracle.ca_run(s0, 6, domain(k))
+    # 6 steps: result in a; b holds step 5.  Cells outside member tiles keep
+    # their starting contents (a: noise, b: sentinel).
+    a = dev_u8(s0)
+    b = torch.full_like(a, SENTINEL_U8)
+    out = fr.fractal_step_ca(plan, a, b, 6)
+    got = out.cpu().numpy().reshape(n, n)
+    mask = domain(k).mask
+    cover = tile_cover(n, rho)
+    assert np.array_equal(got[mask], want[mask])
+    assert np.all(got[cover & ~mask] == 0)
+    assert np.array_equal(got[~cover], s0[~cover])
+    odd = b.cpu().numpy().reshape(n, n)
+    assert np.array_equal(odd[mask], oracle.ca_run(s0, 5, domain(k))[mask])
+    assert np.all(odd[~cover] == SENTINEL_U8)
+
+
+@pytest.mark.parametrize("k,rho", [(9, 8), (9, 16), (9, 32), (10, 32)])
+def test_ca_every_cta_level(fr, k, rho):
+    n = 1 << k
+    s0 = synth.bernoulli_u8(100 + k, n)
+    want = oracle.ca_run(s0, 3, domain(k))
+    mask = domain(k).mask
+    for mode in MODES:
+        plan = fr.fractal_map(k, rho, mode)
+        rb = k - int(np.log2(rho))
+        for m in range(0, min(rb, 5) + 1):
+            try:
+                fr.fractal_plan_set_cta_levels(plan, fr.FRACTAL_U8, m)
+            except fr.FractalError:
+                continue     # super-tile too large for shared memory
+            got, _, _ = run_ca(fr, plan, s0, 3)
+            assert np.array_equal(got[mask], want[mask]), (mode, m)
+
+
+def test_ca_zero_steps_and_states(fr):
+    k, n = 6, 64
+    plan = fr.fractal_map(k, 16)
+    s0 = synth.bernoulli_u8(1, n)
+    a = dev_u8(s0)
+    b = torch.zeros_like(a)
+    assert fr.fractal_step_ca(plan, a, b, 0) is a
+    assert np.array_equal(a.cpu().numpy().reshape(n, n), s0)
+    # any nonzero byte is alive
+    s2 = s0 * np.uint8(77)
+    got, _, _ = run_ca(fr, plan, s2, 4)
+    want = oracle.ca_run(s0, 4, domain(k))
+    assert np.array_equal(got[domain(k).mask], want[domain(k).mask])
+
+
+def test_ca_hand_cases_on_gpu(fr):
+    from conftest import read_golden
+    for line in read_golden("ca_hand_cases.txt"):
+        head, before, after = line.split("|")
+        _, k, steps = head.split()
+        n = 1 << int(k)
+        s = np.zeros((n, n), dtype=np.uint8)
+        for tok in before.split():
+            x, y = map(int, tok.split(","))
+            s[y, x] = 1
+        for rho in (1, 2, 4, 8):
+            got, _, _ = run_ca(fr, fr.fractal_map(int(k), rho), s, int(steps), 0)
+            cells = {(int(x), int(y)) for y, x in zip(*np.nonzero(got))}
+            want = set() if after.strip() == "-" else {tuple(map(int, t.split(","))) for t in after.split()}
+            assert cells == want, (head, rho)
+
+
+# ------------------------------------------------------------ diffusion ----
+
+def run_diffusion(fr, plan, u0, steps, a=0.2, sentinel=SENTINEL_F32):
+    n = u0.shape[0]
+    ua = dev_f32(u0)
+    ub = torch.full_like(ua, sentinel)
+    out = fr.fractal_step_diffusion(plan, ua, ub, a, steps)
+    return out.cpu().numpy().reshape(n, n)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k,rho", cases([1, 2, 3, 4, 6, 8, 10]))
+def test_diffusion_parity(fr, k, rho, mode):
+    n = 1 << k
+    plan = fr.fractal_map(k, rho, mode)
+    u0 = synth.uniform_f32(k, n)
+    want = oracle.diffusion_run(u0.astype(np.float64), 7, 0.2, domain(k))
+    got = run_diffusion(fr, plan, u0, 7)
+    mask = domain(k).mask
+    err, _ = rel_err(got, want, mask)
+    assert err <= 2e-6, err
+    cover = tile_cover(n, rho)
+    assert np.all(got[cover & ~mask] == 0)
+    assert np.array_equal(got[~cover], np.full_like(got[~cover], SENTINEL_F32))
+
+
+@pytest.mark.parametrize("k,rho", [(9, 4), (9, 8), (10, 16), (10, 32)])
+def test_diffusion_every_cta_level(fr, k, rho):
+    n = 1 << k
+    u0 = synth.uniform_f32(50 + k, n)
+    want = oracle.diffusion_run(u0.astype(np.float64), 3, 0.2, domain(k))
+    mask = domain(k).mask
+    for mode in MODES:
+        plan = fr.fractal_map(k, rho, mode)
+        rb = k - int(np.log2(rho))
+        for m in range(0, min(rb, 5) + 1):
+            try:
+                fr.fractal_plan_set_cta_levels(plan, fr.FRACTAL_F32, m)
+            except fr.FractalError:
+                continue
+            got = run_diffusion(fr, plan, u0, 3)
+            assert rel_err(got, want, mask)[0] <= 1e-6, (mode, m)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_diffusion_1000_steps(fr, mode):
+    # the accuracy bound at the step count of the k = 14 workload, on k = 10
+    k, n = 10, 1024
+    u0 = synth.uniform_f32(3, n)
+    want = oracle.diffusion_run(u0.astype(np.float64), 1000, 0.2, domain(k))
+    got = run_diffusion(fr, fr.fractal_map(k, 8, mode), u0, 1000)
+    err, raw = rel_err(got, want, domain(k).mask)
+    assert err <= 1e-4, (err, raw)
+
+
+def test_diffusion_conserves_and_ignores_nonmembers(fr):
+    k, n = 8, 256
+    plan = fr.fractal_map(k, 8)
+    u0 = synth.uniform_f32(2, n)
+    noisy = u0.copy()
+    noisy[~domain(k).mask] = np.float32(np.nan)
+    got = run_diffusion(fr, plan, noisy, 40)
+    clean = run_diffusion(fr, plan, u0, 40)
+    mask = domain(k).mask
+    assert np.array_equal(got[mask], clean[mask])
+    s0 = u0[mask].astype(np.float64).sum()
+    assert abs(got[mask].astype(np.float64).sum() - s0) <= 1e-5 * s0
+
+
+# --------------------------------------------------------------- reduce ----
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k,rho", cases([0, 1, 3, 5, 8, 10]))
+def test_reduce(fr, k, rho, mode):
+    n = 1 << k
+    plan = fr.fractal_map(k, rho, mode)
+    mask = oracle.member_mask(n)
+    s = synth.bernoulli_u8(7, n)
+    assert fr.fractal_reduce(plan, dev_u8(s), fr.FRACTAL_U8) == int(s[mask].sum())
+    u = synth.uniform_f32(7, n)
+    want = oracle.reduce_sum(u[mask])
+    got = fr.fractal_reduce(plan, dev_f32(u), fr.FRACTAL_F32)
+    assert abs(got - want) <= 1e-6 * max(want, 1.0)
+    # deterministic
+    assert fr.fractal_reduce(plan, dev_f32(u), fr.FRACTAL_F32) == got
+    # reduce of the single write is the volume 3^k (Eq. 2)
+    b = torch.zeros(n * n, dtype=torch.float32, device="cuda")
+    fr.fractal_map_write(plan, b, fr.FRACTAL_F32, 1.0)
+    assert fr.fractal_reduce(plan, b, fr.FRACTAL_F32) == 3 ** k
+
+
+def test_reduce_async_device_output(fr):
+    k, n = 9, 512
+    plan = fr.fractal_map(k, 16)
+    s = synth.bernoulli_u8(5, n)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    fr.fractal_reduce_async(plan, dev_u8(s), fr.FRACTAL_U8, out[1:])
+    torch.cuda.synchronize()
+    assert out[1].item() == int(s[oracle.member_mask(n)].sum())
+    assert out[0].item() == 0.0
+
+
+# ------------------------------------------------------------ generator ----
+
+@pytest.mark.parametrize("n", [1, 64, 1000])
+def test_device_generator_matches_host(fr, n):
+    b = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+    synth.device_fill(b.data_ptr(), synth.SYNTH_BERNOULLI_U8, n, 42)
+    f = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    synth.device_fill(f.data_ptr(), synth.SYNTH_UNIFORM_F32, n, 42, lo=0.5, width=1.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(b.cpu().numpy().reshape(n, n), synth.bernoulli_u8(42, n))
+    assert np.array_equal(f.cpu().numpy().reshape(n, n), synth.uniform_f32(42, n, lo=0.5))
+
+
+# -------------------------------------------------------------- errors -----
+
+def test_runtime_validation(fr):
+    plan = fr.fractal_map(6, 8)
+    a = torch.zeros(64 * 64 + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_ca(plan, a, a, 1)                 # same buffer
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_ca(plan, a[1:], a[16:], 1)        # misaligned
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_ca(plan, a[:4096], a[16:], -1)    # negative steps
+    f = torch.zeros(2 * 64 * 64, dtype=torch.float32, device="cuda")
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_diffusion(plan, f[:4096], f[4096:], float("nan"), 1)
+    with pytest.raises(fr.FractalError):
+        fr.fractal_map_write(plan, f, 5, 1.0)
+    with pytest.raises(fr.FractalError):
+        fr.fractal_plan_set_cta_levels(plan, 0, 9)
