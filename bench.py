@@ -209,7 +209,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-detail", action="store_true")
+    ap.add_argument("--profile", choices=["ca", "diffusion", "reduce", "sw"],
+                    help="run only `--launches` launches of one kernel (for ncu captures)")
+    ap.add_argument("--k", type=int, default=15, help="gasket level of a --profile run")
+    ap.add_argument("--rho", type=int, default=8, help="tile side of a --profile run")
+    ap.add_argument("--mode", type=int, default=0, help="0 = lambda, 1 = BB (--profile)")
+    ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--l2-fetch", type=int, default=32, choices=[0, 32, 64, 128],
+                    help="L2 fetch granularity hint for this process (0 = leave the driver's)")
     args = ap.parse_args()
+    if args.profile:
+        profile_run(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
 
@@ -228,6 +239,9 @@ def main():
     if rank == 0:
         fbuild.build()
     barrier(dist)
+    if args.l2_fetch:
+        fr.fractal_set_l2_fetch_granularity(args.l2_fetch)
+    l2_fetch = fr.fractal_get_l2_fetch_granularity()
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
 
@@ -322,6 +336,7 @@ def main():
             "map": "lambda", "k": K, "rho_ca": args.rho_ca, "rho_diffusion": args.rho_diff,
             "cta_levels_ca": info_c["cta_levels"][0], "cta_levels_diffusion": info_d["cta_levels"][1],
             "l2": "inputs larger than L2 (4 GiB uint8 + 16 GiB FP32 per buffer)",
+            "l2_fetch_granularity_bytes": l2_fetch,
             "parallelism": "replicas only" if world > 1 else "single GPU",
         },
         "gpu_launches": launches_per_step * args.steps,
@@ -353,6 +368,41 @@ def main():
         p.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def profile_run(args):
+    """A few launches of one kernel at level args.k (small cases for ncu)."""
+    import torch
+    import paper_2004_13475_gb300 as fr
+    from paper_2004_13475_gb300 import build as fbuild
+    import synth
+    fbuild.build()
+    if args.l2_fetch:
+        fr.fractal_set_l2_fetch_granularity(args.l2_fetch)
+    n = 1 << args.k
+    plan = fr.fractal_map(args.k, args.rho, args.mode)
+    if args.profile == "ca":
+        a = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+        synth.device_fill(a.data_ptr(), synth.SYNTH_BERNOULLI_U8, n, SEED)
+    else:
+        a = torch.empty(n * n, dtype=torch.float32, device="cuda")
+        synth.device_fill(a.data_ptr(), synth.SYNTH_UNIFORM_F32, n, SEED)
+    b = torch.empty_like(a)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(args.launches):
+        if args.profile == "ca":
+            fr.fractal_step_ca(plan, a, b, 1)
+            a, b = b, a
+        elif args.profile == "diffusion":
+            fr.fractal_step_diffusion(plan, a, b, COEF, 1)
+            a, b = b, a
+        elif args.profile == "reduce":
+            fr.fractal_reduce_async(plan, a, fr.FRACTAL_F32, out)
+        else:
+            fr.fractal_map_write(plan, b, fr.FRACTAL_F32, 1.0)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "k": args.k, "rho": args.rho, "mode": args.mode,
+                      "launches": args.launches, "plan": plan.info()}))
 
 
 def kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm):

@@ -172,6 +172,23 @@ int fractal_reduce(fractal_plan_t plan, const void* dev_buf, int dtype, double* 
 int fractal_reduce_async(fractal_plan_t plan, const void* dev_buf, int dtype, double* dev_out,
                          void* stream);
 
+/*
+ * fractal_set_l2_fetch_granularity -- set the L2 fetch granularity hint of
+ * the CURRENT CUDA context (cudaLimitMaxL2FetchGranularity) to 32, 64 or 128
+ * bytes.  Not part of the paper: a GB300 memory-system knob.  The tiles of a
+ * gasket touch scattered 32-byte row segments (one sector: 32 uint8 cells or
+ * 8 float32 cells); with a coarser fetch granularity every DRAM read brings
+ * neighbouring sectors that hold no member tile.  32 makes reads exact.  The
+ * setting is a hint, lasts until the context is destroyed or the limit is set
+ * again, and applies to every kernel of the context (the caller's too), so the
+ * library never changes it on its own.  Errors: FRACTAL_EINVAL (other sizes),
+ * FRACTAL_ECUDA.
+ */
+int fractal_set_l2_fetch_granularity(int bytes);
+
+/* Current value of that hint for the current context, in bytes. */
+int fractal_get_l2_fetch_granularity(int* bytes);
+
 #ifdef __cplusplus
 }
 #endif

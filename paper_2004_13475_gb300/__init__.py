@@ -34,7 +34,7 @@ EXPORTS = (
     "fractal_strerror", "fractal_last_cuda_error", "fractal_map", "fractal_plan_destroy",
     "fractal_plan_get_info", "fractal_plan_set_cta_levels", "fractal_map_blocks",
     "fractal_map_write", "fractal_step_ca", "fractal_step_diffusion", "fractal_reduce",
-    "fractal_reduce_async",
+    "fractal_reduce_async", "fractal_set_l2_fetch_granularity", "fractal_get_l2_fetch_granularity",
 )
 
 
@@ -89,6 +89,8 @@ def _load() -> ctypes.CDLL:
         "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
         "fractal_reduce": (I, [P, VP, I, ctypes.POINTER(D), VP]),
         "fractal_reduce_async": (I, [P, VP, I, VP, VP]),
+        "fractal_set_l2_fetch_granularity": (I, [I]),
+        "fractal_get_l2_fetch_granularity": (I, [ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -203,6 +205,16 @@ def fractal_reduce(plan: Plan, buf, dtype: int, stream=None) -> float:
 def fractal_reduce_async(plan: Plan, buf, dtype: int, dev_out, stream=None) -> None:
     _check(_load().fractal_reduce_async(plan.handle, _ptr(buf), dtype, _ptr(dev_out), _stream(stream)),
            "fractal_reduce_async")
+
+
+def fractal_set_l2_fetch_granularity(nbytes: int) -> None:
+    _check(_load().fractal_set_l2_fetch_granularity(int(nbytes)), "fractal_set_l2_fetch_granularity")
+
+
+def fractal_get_l2_fetch_granularity() -> int:
+    v = ctypes.c_int()
+    _check(_load().fractal_get_l2_fetch_granularity(ctypes.byref(v)), "fractal_get_l2_fetch_granularity")
+    return v.value
 
 
 def fractal_strerror(status: int) -> str:

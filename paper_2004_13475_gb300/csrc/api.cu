@@ -30,6 +30,9 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 constexpr int kMaxLevelsPerCta = 5;
 constexpr int kMaxSmem = 200 * 1024;
+// Loads per thread a launch is sized for (at most kIPT; fewer keeps more warps
+// for the update phase).
+constexpr int kLoadsPerThread = 2;
 
 }  // namespace
 }  // namespace fractal
@@ -71,11 +74,12 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
     if (R > 15) return false;  // gridDim.y <= 65535
     grid = dim3(1u << R, 1u << R, 1);
   }
-  // chunks (row segments) per tile: uint8 one per row; float32 float4s
-  const int wc = dtype == FRACTAL_U8 ? rho : (rho < 4 ? rho : 4);
+  // Vector accesses per tile: uint8 rows in pieces of at most 16 bytes, float
+  // rows in float4s.  A staging pass of kIPT loads per thread covers the
+  // whole super-tile.
+  const int wc = dtype == FRACTAL_U8 ? (rho < 16 ? rho : 16) : (rho < 4 ? rho : 4);
   const int64_t chunks = (int64_t)g.slots * rho * (rho / wc);
-  const int64_t ipt = (chunks + 255) / 256;
-  int threads = (int)(((chunks + ipt - 1) / ipt + 31) / 32 * 32);
+  int threads = (int)(((chunks + kLoadsPerThread - 1) / kLoadsPerThread + 31) / 32 * 32);
   if (threads < 32) threads = 32;
   if (threads > 512) threads = 512;
   const int tab_bytes = tab_words(g.slots) * 4;
@@ -297,6 +301,21 @@ int fractal_reduce(fractal_plan_t p, const void* dev_buf, int dtype, double* hos
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "reduce sync");
   *host_out = *p->h_result;
+  return FRACTAL_OK;
+}
+
+int fractal_set_l2_fetch_granularity(int bytes) {
+  if (bytes != 32 && bytes != 64 && bytes != 128) return FRACTAL_EINVAL;
+  cudaError_t e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "set L2 fetch granularity");
+}
+
+int fractal_get_l2_fetch_granularity(int* bytes) {
+  if (!bytes) return FRACTAL_EINVAL;
+  size_t v = 0;
+  cudaError_t e = cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity);
+  if (e != cudaSuccess) return cuda_fail(e, "get L2 fetch granularity");
+  *bytes = (int)v;
   return FRACTAL_OK;
 }
 

@@ -36,6 +36,10 @@ struct Geo {
 
 constexpr uint32_t kNoTile = 0xffffffffu;
 
+// Loads a thread keeps in flight at once in a staging pass; launches size the
+// CTA so that one pass covers the whole super-tile.
+constexpr int kIPT = 4;
+
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
 __host__ __device__ inline int tab_words(int slots) { return (slots + 3) & ~3; }

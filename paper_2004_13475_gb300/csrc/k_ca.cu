@@ -43,7 +43,9 @@ template <int MODE, int LOG_RHO>
 __global__ void __launch_bounds__(512) ca_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                                  Geo g) {
   constexpr int RHO = 1 << LOG_RHO;
-  constexpr int WC = RHO;  // one chunk = one tile row (rho <= 32 cells)
+  constexpr int WC = RHO;                     // update chunk: one tile row (<= 32 cells)
+  constexpr int WL = RHO < 16 ? RHO : 16;     // load chunk: at most 16 bytes
+  constexpr int LOG_LQ = 2 * LOG_RHO - ilog2c(WL);  // load chunks per tile
   extern __shared__ __align__(16) uint32_t smem[];
 
   int sx, sy;
@@ -60,21 +62,43 @@ __global__ void __launch_bounds__(512) ca_kernel(const uint8_t* __restrict__ in,
   __syncthreads();
 
   const int ox = sx * T, oy = sy * T;
-  const int total = g.slots << LOG_RHO;
 
-  // Stage: alive & member bits of every member tile row.
-  for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    const uint32_t e = tab[it >> LOG_RHO];
-    if (e == kNoTile) continue;
-    const int lx0 = (int)(e & 0xffffu) * RHO;
-    const int ly = (int)(e >> 16) * RHO + (it & (RHO - 1));
-    const int gx0 = ox + lx0, gy = oy + ly;
-    uint32_t bits = load_alive_bits<WC>(in + (size_t)gy * n + gx0) & chunk_members<WC>(gx0, gy, n);
-    uint32_t* w = img + (ly + 1) * wpr + ((lx0 + 32) >> 5);
-    if (WC == 32) {
-      *w = bits;
-    } else if (bits) {
-      atomicOr(w, bits << (lx0 & 31));
+  // Stage alive & member bits of every member tile row.  Consecutive threads
+  // take consecutive 16-byte pieces of a row, so a warp instruction reads
+  // whole 32-byte sectors; each thread issues all its loads first.
+  const int total_l = g.slots << LOG_LQ;
+  for (int base = threadIdx.x; base < total_l; base += blockDim.x * kIPT) {
+    uint32_t bits[kIPT];
+    int word[kIPT];
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u) {
+      const int it = base + u * (int)blockDim.x;
+      word[u] = -1;
+      if (it < total_l) {
+        const uint32_t e = tab[it >> LOG_LQ];
+        if (e != kNoTile) {
+          const int c = it & ((1 << LOG_LQ) - 1);
+          const int lx0 = (int)(e & 0xffffu) * RHO + (c & (RHO / WL - 1)) * WL;
+          const int ly = (int)(e >> 16) * RHO + c / (RHO / WL);
+          const int gx0 = ox + lx0, gy = oy + ly;
+          bits[u] = load_alive_bits<WL>(in + (size_t)gy * n + gx0) & chunk_members<WL>(gx0, gy, n);
+          // half-word index for 16-cell chunks, else word index and bit shift
+          word[u] = WL == 16 ? 2 * ((ly + 1) * wpr + ((lx0 + 32) >> 5)) + ((lx0 >> 4) & 1)
+                             : ((ly + 1) * wpr + ((lx0 + 32) >> 5)) * 32 + (lx0 & 31);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u) {
+      if (word[u] < 0) continue;
+      if (WL == 16 && T >= 32) {
+        // exclusive half-word (ring bits live in other words when T >= 32)
+        reinterpret_cast<uint16_t*>(img)[word[u]] = (uint16_t)bits[u];
+      } else if (WL == 16) {
+        if (bits[u]) atomicOr(img + (word[u] >> 1), bits[u] << (16 * (word[u] & 1)));
+      } else if (bits[u]) {
+        atomicOr(img + (word[u] >> 5), bits[u] << (word[u] & 31));
+      }
     }
   }
   // Stage: ring cells that are members next to a member of the super-tile.
@@ -88,9 +112,12 @@ __global__ void __launch_bounds__(512) ca_kernel(const uint8_t* __restrict__ in,
   }
   __syncthreads();
 
-  // Update and store every member tile row.
+  // Update every member tile row (one row per thread).
+  const int total = g.slots << LOG_RHO;
   for (int it = threadIdx.x; it < total; it += blockDim.x) {
     const uint32_t e = tab[it >> LOG_RHO];
+    // With rho = 32 a warp's 32 consecutive rows are one tile, so this exit and
+    // the shuffles below are warp-uniform.
     if (e == kNoTile) continue;
     const int lx0 = (int)(e & 0xffffu) * RHO;
     const int ly = (int)(e >> 16) * RHO + (it & (RHO - 1));
@@ -100,7 +127,21 @@ __global__ void __launch_bounds__(512) ca_kernel(const uint8_t* __restrict__ in,
     const uint64_t mid = bit_window(row + wpr, lx0);
     const uint64_t dn = bit_window(row + 2 * wpr, lx0);
     const uint32_t next = life_rule(up, mid, dn) & chunk_members<WC>(gx0, gy, n);
-    store_state_bytes<WC>(out + (size_t)gy * n + gx0, next, 1u);
+    if constexpr (RHO == 32) {
+      // Lanes 2r and 2r+1 store the two 16-byte halves of tile row r (then
+      // r + 16), so each store instruction writes whole sectors.
+      const int lane = threadIdx.x & 31;
+      const int h = lane & 1;
+      uint8_t* base = out + (size_t)(gy - (it & 31)) * n + gx0 + 16 * h;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int r = (lane >> 1) + 16 * j;
+        const uint32_t b = __shfl_sync(0xffffffffu, next, r);
+        store_state_bytes<16>(base + (size_t)r * n, b >> (16 * h), 1u);
+      }
+    } else {
+      store_state_bytes<WC>(out + (size_t)gy * n + gx0, next, 1u);
+    }
   }
 }
 

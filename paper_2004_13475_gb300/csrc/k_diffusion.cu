@@ -41,15 +41,31 @@ __global__ void __launch_bounds__(512) diffusion_kernel(const float* __restrict_
   }
   __syncthreads();
 
+  // Stage the member tiles.  Each thread issues all of its (up to kIPT)
+  // loads before it writes any of them to shared memory, so the CTA keeps
+  // every load of its super-tile in flight at once.
   const int total = g.slots << LOG_Q;
-  for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    const uint32_t e = tab[it >> LOG_Q];
-    if (e == kNoTile) continue;
-    const int c = it & ((1 << LOG_Q) - 1);
-    const int lx0 = (int)(e & 0xffffu) * RHO + (c & ((1 << LOG_C) - 1)) * WC;
-    const int ly = (int)(e >> 16) * RHO + (c >> LOG_C);
-    const FVec<WC> v = load_f<WC>(in + (size_t)(oy + ly) * n + ox + lx0, true);
-    store_f<WC>(img + (ly + 1) * P + 4 + lx0, v);
+  for (int base = threadIdx.x; base < total; base += blockDim.x * kIPT) {
+    FVec<WC> v[kIPT];
+    int off[kIPT];
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u) {
+      const int it = base + u * (int)blockDim.x;
+      off[u] = -1;
+      if (it < total) {
+        const uint32_t e = tab[it >> LOG_Q];
+        if (e != kNoTile) {
+          const int c = it & ((1 << LOG_Q) - 1);
+          const int lx0 = (int)(e & 0xffffu) * RHO + (c & ((1 << LOG_C) - 1)) * WC;
+          const int ly = (int)(e >> 16) * RHO + (c >> LOG_C);
+          v[u] = load_f<WC>(in + (size_t)(oy + ly) * n + ox + lx0, true);
+          off[u] = (ly + 1) * P + 4 + lx0;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u)
+      if (off[u] >= 0) store_f<WC>(img + off[u], v[u]);
   }
   __syncthreads();
 

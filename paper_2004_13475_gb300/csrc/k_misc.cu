@@ -31,18 +31,21 @@ __global__ void map_blocks_kernel(int32_t* __restrict__ out, int w, int h, int l
 template <int MODE, int LOG_RHO>
 __global__ void __launch_bounds__(512) sw_u8_kernel(uint8_t* __restrict__ out, uint32_t value, Geo g) {
   constexpr int RHO = 1 << LOG_RHO;
+  constexpr int WL = RHO < 16 ? RHO : 16;           // bytes per store
+  constexpr int LOG_LQ = 2 * LOG_RHO - ilog2c(WL);  // stores per tile
   extern __shared__ __align__(16) uint32_t smem[];
   int sx, sy;
   if (!cta_supertile<MODE>(g, sx, sy)) return;
   build_slot_table<MODE>(smem, g);
   __syncthreads();
-  const int total = g.slots << LOG_RHO;
+  const int total = g.slots << LOG_LQ;
   for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    const uint32_t e = smem[it >> LOG_RHO];
+    const uint32_t e = smem[it >> LOG_LQ];
     if (e == kNoTile) continue;
-    const int gx0 = sx * g.T + (int)(e & 0xffffu) * RHO;
-    const int gy = sy * g.T + (int)(e >> 16) * RHO + (it & (RHO - 1));
-    store_state_bytes<RHO>(out + (size_t)gy * g.n + gx0, chunk_members<RHO>(gx0, gy, g.n), value);
+    const int c = it & ((1 << LOG_LQ) - 1);
+    const int gx0 = sx * g.T + (int)(e & 0xffffu) * RHO + (c & (RHO / WL - 1)) * WL;
+    const int gy = sy * g.T + (int)(e >> 16) * RHO + c / (RHO / WL);
+    store_state_bytes<WL>(out + (size_t)gy * g.n + gx0, chunk_members<WL>(gx0, gy, g.n), value);
   }
 }
 
@@ -110,6 +113,8 @@ template <int MODE, int LOG_RHO>
 __global__ void __launch_bounds__(512) reduce_u8_kernel(const uint8_t* __restrict__ in,
                                                         unsigned long long* __restrict__ partials, Geo g) {
   constexpr int RHO = 1 << LOG_RHO;
+  constexpr int WL = RHO < 16 ? RHO : 16;
+  constexpr int LOG_LQ = 2 * LOG_RHO - ilog2c(WL);
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ unsigned long long red[32];
   int sx, sy;
@@ -119,14 +124,26 @@ __global__ void __launch_bounds__(512) reduce_u8_kernel(const uint8_t* __restric
   }
   build_slot_table<MODE>(smem, g);
   __syncthreads();
-  const int total = g.slots << LOG_RHO;
+  const int total = g.slots << LOG_LQ;
   unsigned count = 0;
-  for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    const uint32_t e = smem[it >> LOG_RHO];
-    if (e == kNoTile) continue;
-    const int gx0 = sx * g.T + (int)(e & 0xffffu) * RHO;
-    const int gy = sy * g.T + (int)(e >> 16) * RHO + (it & (RHO - 1));
-    count += __popc(load_alive_bits<RHO>(in + (size_t)gy * g.n + gx0) & chunk_members<RHO>(gx0, gy, g.n));
+  for (int base = threadIdx.x; base < total; base += blockDim.x * kIPT) {
+    uint32_t bits[kIPT];
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u) {
+      const int it = base + u * (int)blockDim.x;
+      bits[u] = 0u;
+      if (it < total) {
+        const uint32_t e = smem[it >> LOG_LQ];
+        if (e != kNoTile) {
+          const int c = it & ((1 << LOG_LQ) - 1);
+          const int gx0 = sx * g.T + (int)(e & 0xffffu) * RHO + (c & (RHO / WL - 1)) * WL;
+          const int gy = sy * g.T + (int)(e >> 16) * RHO + c / (RHO / WL);
+          bits[u] = load_alive_bits<WL>(in + (size_t)gy * g.n + gx0) & chunk_members<WL>(gx0, gy, g.n);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u) count += __popc(bits[u]);
   }
   const unsigned long long s = block_sum<unsigned long long>(count, red);
   if (threadIdx.x == 0) partials[cta_id()] = s;
@@ -150,26 +167,33 @@ __global__ void __launch_bounds__(512) reduce_f32_kernel(const float* __restrict
   __syncthreads();
   const int total = g.slots << LOG_Q;
   double acc = 0.0;
-  float part = 0.0f;  // FP32 partial over at most 4 chunks (16 cells)
-  int in_part = 0;
-  for (int it = threadIdx.x; it < total; it += blockDim.x) {
-    const uint32_t e = smem[it >> LOG_Q];
-    if (e == kNoTile) continue;
-    const int c = it & ((1 << LOG_Q) - 1);
-    const int gx0 = sx * g.T + (int)(e & 0xffffu) * RHO + (c & ((1 << LOG_C) - 1)) * WC;
-    const int gy = sy * g.T + (int)(e >> 16) * RHO + (c >> LOG_C);
-    const uint32_t mm = chunk_members<WC>(gx0, gy, g.n);
-    if (mm == 0u) continue;
-    const FVec<WC> v = load_f<WC>(in + (size_t)gy * g.n + gx0, true);
+  for (int base = threadIdx.x; base < total; base += blockDim.x * kIPT) {
+    FVec<WC> v[kIPT];
+    uint32_t mm[kIPT];
 #pragma unroll
-    for (int i = 0; i < WC; ++i) part += ((mm >> i) & 1u) ? v.v[i] : 0.0f;
-    if (++in_part == 4) {
-      acc += (double)part;
-      part = 0.0f;
-      in_part = 0;
+    for (int u = 0; u < kIPT; ++u) {
+      const int it = base + u * (int)blockDim.x;
+      mm[u] = 0u;
+      if (it < total) {
+        const uint32_t e = smem[it >> LOG_Q];
+        if (e != kNoTile) {
+          const int c = it & ((1 << LOG_Q) - 1);
+          const int gx0 = sx * g.T + (int)(e & 0xffffu) * RHO + (c & ((1 << LOG_C) - 1)) * WC;
+          const int gy = sy * g.T + (int)(e >> 16) * RHO + (c >> LOG_C);
+          mm[u] = chunk_members<WC>(gx0, gy, g.n);
+          if (mm[u]) v[u] = load_f<WC>(in + (size_t)gy * g.n + gx0, true);
+        }
+      }
     }
+    // FP32 partial over at most kIPT chunks (16 cells), then FP64
+    float part = 0.0f;
+#pragma unroll
+    for (int u = 0; u < kIPT; ++u) {
+#pragma unroll
+      for (int i = 0; i < WC; ++i) part += ((mm[u] >> i) & 1u) ? v[u].v[i] : 0.0f;
+    }
+    acc += (double)part;
   }
-  acc += (double)part;
   const double s = block_sum<double>(acc, red);
   if (threadIdx.x == 0) partials[cta_id()] = s;
 }

@@ -23,7 +23,7 @@ def _declared():
     with open(os.path.join(ROOT, "include", "fractal.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(fractal_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(fractal_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_and_binding_agree():

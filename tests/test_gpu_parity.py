@@ -290,6 +290,16 @@ def test_device_generator_matches_host(fr, n):
 
 # -------------------------------------------------------------- errors -----
 
+def test_l2_fetch_granularity_hint(fr):
+    old = fr.fractal_get_l2_fetch_granularity()
+    for v in (32, 64, 128):
+        fr.fractal_set_l2_fetch_granularity(v)
+        assert fr.fractal_get_l2_fetch_granularity() == v
+    with pytest.raises(fr.FractalError):
+        fr.fractal_set_l2_fetch_granularity(48)
+    fr.fractal_set_l2_fetch_granularity(old if old in (32, 64, 128) else 64)
+
+
 def test_runtime_validation(fr):
     plan = fr.fractal_map(6, 8)
     a = torch.zeros(64 * 64 + 16, dtype=torch.uint8, device="cuda")
