@@ -335,6 +335,8 @@ def main():
                          f" reduce every {REDUCE_EVERY} + 1 count reduce"),
             "map": "lambda", "k": K, "rho_ca": args.rho_ca, "rho_diffusion": args.rho_diff,
             "cta_levels_ca": info_c["cta_levels"][0], "cta_levels_diffusion": info_d["cta_levels"][1],
+            "staging_ca": "tma" if info_c["tma"][0] else "vector loads",
+            "staging_diffusion": "tma" if info_d["tma"][1] else "vector loads",
             "l2": "inputs larger than L2 (4 GiB uint8 + 16 GiB FP32 per buffer)",
             "l2_fetch_granularity_bytes": l2_fetch,
             "parallelism": "replicas only" if world > 1 else "single GPU",
@@ -342,7 +344,8 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "roofline": {
-            "kernel": f"diffusion_kernel<lambda, rho={args.rho_diff}>", "bound": "hbm",
+            "kernel": ("diffusion_tma_kernel" if info_d["tma"][1] else "diffusion_kernel") + f"<lambda, rho={args.rho_diff}>",
+            "bound": "hbm",
             "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None,
             "alg_bytes_per_launch": alg_bytes_d, "launch_us": diff_launch_s * 1e6,
@@ -436,6 +439,16 @@ def kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm):
             b = 2 * tiles * rho * rho * 4
             rec["diffusion"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
                                 "frac": b / t / 1e9 / hbm, "cta_levels": inf["cta_levels"][1]}
+            # the same steps with the vector-load staging instead of TMA
+            fr.fractal_plan_set_schedule(p, fr.FRACTAL_SCHED_STAGED)
+            t = clock(lambda: fr.fractal_step_ca(p, ca_a, ca_b, 2, stream)) / 2
+            b = 2 * tiles * rho * rho
+            rec["ca_staged"] = {"us": t * 1e6, "frac": b / t / 1e9 / hbm}
+            t = clock(lambda: fr.fractal_step_diffusion(p, u_a, u_b, COEF, 2, stream)) / 2
+            b = 2 * tiles * rho * rho * 4
+            rec["diffusion_staged"] = {"us": t * 1e6, "frac": b / t / 1e9 / hbm}
+            fr.fractal_plan_set_schedule(p, fr.FRACTAL_SCHED_AUTO)
+            rec["tma"] = inf["tma"]
             t = clock(lambda: fr.fractal_map_write(p, u_b, fr.FRACTAL_F32, 1.0, stream))
             b = tiles * rho * rho * 4
             rec["sw_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
@@ -447,7 +460,7 @@ def kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm):
             b = tiles * rho * rho * 4
             rec["reduce_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
             out.setdefault(str(rho), {})[name] = rec
-        for kname in ("ca", "diffusion", "sw_f32", "sw_u8", "reduce_f32"):
+        for kname in ("ca", "diffusion", "ca_staged", "diffusion_staged", "sw_f32", "sw_u8", "reduce_f32"):
             lam = out[str(rho)]["lambda"][kname]["us"]
             bb = out[str(rho)]["bb"][kname]["us"]
             out[str(rho)].setdefault("speedup_lambda_over_bb", {})[kname] = bb / lam

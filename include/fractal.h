@@ -46,6 +46,11 @@ extern "C" {
 #define FRACTAL_LAMBDA 0     /* compact grid + lambda(omega) (Theorem 1) */
 #define FRACTAL_BB 1         /* bounding-box grid, identity map, discard non-members */
 
+/* Step-kernel schedules (fractal_plan_set_schedule). */
+#define FRACTAL_SCHED_AUTO 0   /* TMA staging where it applies, else vector-load staging */
+#define FRACTAL_SCHED_STAGED 1 /* vector loads into a shared-memory image of the super-tile */
+#define FRACTAL_SCHED_TMA 2    /* one cp.async.bulk.tensor box per member tile (rows >= 16 B) */
+
 /* Element types. */
 #define FRACTAL_U8 0         /* uint8 automaton states (nonzero = alive) */
 #define FRACTAL_F32 1        /* float32 field */
@@ -70,6 +75,8 @@ typedef struct fractal_plan_info {
   int64_t ctas[2];       /* per dtype: CTAs one launch of this plan starts */
   int32_t threads[2];    /* per dtype: threads per CTA */
   int32_t smem_bytes[2]; /* per dtype: dynamic shared memory per CTA of a step kernel */
+  int32_t tma[2];        /* per dtype: 1 if the step kernel stages tiles with TMA */
+  int32_t sched;         /* FRACTAL_SCHED_* */
 } fractal_plan_info;
 
 /* Human-readable text of a status code (static storage). */
@@ -106,6 +113,23 @@ int fractal_plan_get_info(fractal_plan_t plan, fractal_plan_info* info);
  * FRACTAL_ENOMEM (reduce scratch could not grow).
  */
 int fractal_plan_set_cta_levels(fractal_plan_t plan, int dtype, int levels);
+
+/*
+ * Choose how step kernels stage tiles: FRACTAL_SCHED_AUTO (default),
+ * FRACTAL_SCHED_STAGED or FRACTAL_SCHED_TMA.  Results are identical; only
+ * the data movement differs (TMA needs tile rows of at least 16 bytes: float32
+ * rho >= 4, uint8 rho >= 16; other plans keep the staged kernels).  Errors:
+ * FRACTAL_EINVAL (unknown value, or TMA requested where it never applies).
+ */
+int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
+
+/*
+ * Device status word of the plan's TMA kernels: 0, or the first error a CTA
+ * recorded (1: a tile copy did not complete within the wait limit; 2: the
+ * drain after it also timed out).  The step kernels never trap or spin
+ * forever; they record a code here and return.  Synchronous copy.
+ */
+int fractal_plan_device_status(fractal_plan_t plan, int* code);
 
 /*
  * fractal_map_blocks -- export the block-space map of the plan (Theorem 1,

@@ -35,7 +35,12 @@ EXPORTS = (
     "fractal_plan_get_info", "fractal_plan_set_cta_levels", "fractal_map_blocks",
     "fractal_map_write", "fractal_step_ca", "fractal_step_diffusion", "fractal_reduce",
     "fractal_reduce_async", "fractal_set_l2_fetch_granularity", "fractal_get_l2_fetch_granularity",
+    "fractal_plan_set_schedule", "fractal_plan_device_status",
 )
+
+FRACTAL_SCHED_AUTO = 0
+FRACTAL_SCHED_STAGED = 1
+FRACTAL_SCHED_TMA = 2
 
 
 class FractalError(RuntimeError):
@@ -54,6 +59,7 @@ class PlanInfo(ctypes.Structure):
         ("member_tiles", ctypes.c_int64), ("members", ctypes.c_int64),
         ("cta_levels", ctypes.c_int32 * 2), ("ctas", ctypes.c_int64 * 2),
         ("threads", ctypes.c_int32 * 2), ("smem_bytes", ctypes.c_int32 * 2),
+        ("tma", ctypes.c_int32 * 2), ("sched", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -91,6 +97,8 @@ def _load() -> ctypes.CDLL:
         "fractal_reduce_async": (I, [P, VP, I, VP, VP]),
         "fractal_set_l2_fetch_granularity": (I, [I]),
         "fractal_get_l2_fetch_granularity": (I, [ctypes.POINTER(I)]),
+        "fractal_plan_set_schedule": (I, [P, I]),
+        "fractal_plan_device_status": (I, [P, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +178,16 @@ def fractal_map(k: int, rho: int, mode: int = FRACTAL_LAMBDA) -> Plan:
 
 def fractal_plan_set_cta_levels(plan: Plan, dtype: int, levels: int) -> None:
     _check(_load().fractal_plan_set_cta_levels(plan.handle, dtype, levels), "fractal_plan_set_cta_levels")
+
+
+def fractal_plan_set_schedule(plan: Plan, sched: int) -> None:
+    _check(_load().fractal_plan_set_schedule(plan.handle, int(sched)), "fractal_plan_set_schedule")
+
+
+def fractal_plan_device_status(plan: Plan) -> int:
+    v = ctypes.c_int()
+    _check(_load().fractal_plan_device_status(plan.handle, ctypes.byref(v)), "fractal_plan_device_status")
+    return v.value
 
 
 def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:

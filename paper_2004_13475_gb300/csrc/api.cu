@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/fractal.h"
 #include "launch.h"
 
@@ -43,9 +45,13 @@ struct fractal_plan_s {
   int k = 0, log_rho = 0, rb = 0, mode = 0;
   int32_t n = 1;
   int device = 0;
+  int sched = FRACTAL_SCHED_AUTO;
   int m[2] = {0, 0};            // tile levels per CTA, per dtype
-  Launch step[2];               // CA (u8) / diffusion (f32) kernels
+  Launch step[2];               // staged CA (u8) / diffusion (f32) kernels
+  Launch tma[2];                // TMA-staged CA / diffusion kernels
+  bool tma_ok[2] = {false, false};
   Launch aux[2];                // SW / reduce kernels (slot table only in shared memory)
+  int* d_err = nullptr;         // device error word of the TMA kernels
   void* d_partials = nullptr;   // reduce scratch: one 8-byte partial per CTA
   size_t partials_cap = 0;      // elements
   double* d_result = nullptr;
@@ -55,8 +61,11 @@ struct fractal_plan_s {
 namespace {
 
 // Geometry for one dtype at `levels` tile levels per CTA; returns false if it
-// does not fit (grid limits, shared memory).
-bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, Launch& aux) {
+// does not fit (grid limits, shared memory).  `tma` receives the TMA-staged
+// step kernel's launch and `tma_ok` whether that kernel applies (rows of at
+// least 16 bytes: float32 rho >= 4, uint8 rho >= 16).
+bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
+                 bool& tma_ok) {
   if (levels < 0 || levels > p.rb || levels > kMaxLevelsPerCta) return false;
   const int R = p.rb - levels;
   const int rho = 1 << p.log_rho;
@@ -67,6 +76,7 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   g.T = rho << levels;
   g.slots = (int)(p.mode == kLambda ? ipow(3, levels) : ipow(4, levels));
   g.lw = (int)ipow(3, (levels + 1) / 2);
+  g.tiles = (int)ipow(3, levels);
   dim3 grid;
   if (p.mode == kLambda) {
     grid = dim3((unsigned)ipow(3, (R + 1) / 2), (unsigned)ipow(3, R / 2), 1);
@@ -96,7 +106,46 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   step.geo = g;
   aux = step;
   aux.smem = tab_bytes;
+  // TMA-staged kernel: uint8 one thread per tile row, float32 one per 4x4 cells
+  tma_ok = dtype == FRACTAL_U8 ? rho >= 16 : rho >= 4;
+  tma = step;
+  if (tma_ok) {
+    const int64_t items = dtype == FRACTAL_U8 ? (int64_t)g.tiles * rho : (int64_t)g.tiles * (rho / 4) * (rho / 4);
+    const int cap = dtype == FRACTAL_U8 ? 1024 : 512;
+    int t = (int)((items + 31) / 32 * 32);
+    if (t > cap) t = cap;
+    tma.threads = t;
+    tma.smem = tma_smem_bytes(g, rho * rho * (dtype == FRACTAL_U8 ? 1 : 4));
+    if (tma.smem > kMaxSmem) tma_ok = false;
+  }
   return true;
+}
+
+// Tensor map of an n x n array for rho x rho boxes (driver entry point).
+bool encode_tile_map(CUtensorMap* map, const void* base, int n, int rho, int dtype) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int e = dtype == FRACTAL_U8 ? 1 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)n * e};
+  cuuint32_t box[2] = {(cuuint32_t)rho, (cuuint32_t)rho};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, dtype == FRACTAL_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool use_tma(const fractal_plan_s* p, int dtype) {
+  return p->tma_ok[dtype] && p->sched != FRACTAL_SCHED_STAGED;
 }
 
 int default_levels(const fractal_plan_s& p, int dtype) {
@@ -168,7 +217,7 @@ int fractal_map(int k, int rho, int mode, fractal_plan_t* out) {
   }
   for (int d = 0; d < 2; ++d) {
     p->m[d] = default_levels(*p, d);
-    if (!make_launch(*p, d, p->m[d], p->step[d], p->aux[d])) {
+    if (!make_launch(*p, d, p->m[d], p->step[d], p->aux[d], p->tma[d], p->tma_ok[d])) {
       delete p;
       return FRACTAL_EINVAL;
     }
@@ -179,7 +228,8 @@ int fractal_map(int k, int rho, int mode, fractal_plan_t* out) {
     return st;
   }
   if (cudaMalloc(&p->d_result, sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&p->h_result, sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&p->h_result, sizeof(double)) != cudaSuccess || cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     fractal_plan_destroy(p);
     return FRACTAL_ENOMEM;
@@ -193,6 +243,7 @@ int fractal_plan_destroy(fractal_plan_t p) {
   if (p->d_partials) cudaFree(p->d_partials);
   if (p->d_result) cudaFree(p->d_result);
   if (p->h_result) cudaFreeHost(p->h_result);
+  if (p->d_err) cudaFree(p->d_err);
   delete p;
   return FRACTAL_OK;
 }
@@ -213,28 +264,54 @@ int fractal_plan_get_info(fractal_plan_t p, fractal_plan_info* info) {
   for (int d = 0; d < 2; ++d) {
     info->cta_levels[d] = p->m[d];
     info->ctas[d] = (int64_t)p->step[d].grid.x * p->step[d].grid.y;
-    info->threads[d] = p->step[d].threads;
-    info->smem_bytes[d] = p->step[d].smem;
+    const Launch& L = use_tma(p, d) ? p->tma[d] : p->step[d];
+    info->threads[d] = L.threads;
+    info->smem_bytes[d] = L.smem;
+    info->tma[d] = use_tma(p, d) ? 1 : 0;
   }
+  info->sched = p->sched;
   return FRACTAL_OK;
 }
 
 int fractal_plan_set_cta_levels(fractal_plan_t p, int dtype, int levels) {
   if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32)) return FRACTAL_EINVAL;
-  Launch s, a;
-  if (!make_launch(*p, dtype, levels, s, a)) return FRACTAL_EINVAL;
-  const Launch old_s = p->step[dtype], old_a = p->aux[dtype];
+  Launch s, a, t;
+  bool ok = false;
+  if (!make_launch(*p, dtype, levels, s, a, t, ok)) return FRACTAL_EINVAL;
+  const Launch old_s = p->step[dtype], old_a = p->aux[dtype], old_t = p->tma[dtype];
   const int old_m = p->m[dtype];
+  const bool old_ok = p->tma_ok[dtype];
   p->step[dtype] = s;
   p->aux[dtype] = a;
+  p->tma[dtype] = t;
+  p->tma_ok[dtype] = ok;
   p->m[dtype] = levels;
   int st = ensure_partials(p);
   if (st != FRACTAL_OK) {
     p->step[dtype] = old_s;
     p->aux[dtype] = old_a;
+    p->tma[dtype] = old_t;
+    p->tma_ok[dtype] = old_ok;
     p->m[dtype] = old_m;
   }
   return st;
+}
+
+int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
+  if (!p || (sched != FRACTAL_SCHED_AUTO && sched != FRACTAL_SCHED_STAGED && sched != FRACTAL_SCHED_TMA))
+    return FRACTAL_EINVAL;
+  if (sched == FRACTAL_SCHED_TMA && !(p->tma_ok[0] || p->tma_ok[1])) return FRACTAL_EINVAL;
+  p->sched = sched;
+  return FRACTAL_OK;
+}
+
+int fractal_plan_device_status(fractal_plan_t p, int* code) {
+  if (!p || !code) return FRACTAL_EINVAL;
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "device status");
+  *code = v;
+  return FRACTAL_OK;
 }
 
 int fractal_map_blocks(fractal_plan_t p, int32_t* dev_xy, void* stream) {
@@ -254,14 +331,24 @@ int fractal_map_write(fractal_plan_t p, void* dev_buf, int dtype, double value, 
 int fractal_step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, void* stream) {
   if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0)
     return FRACTAL_EINVAL;
-  uint8_t* cur = a;
-  uint8_t* nxt = b;
+  if (steps == 0) return FRACTAL_OK;
+  const cudaStream_t st = (cudaStream_t)stream;
+  uint8_t* buf[2] = {a, b};
+  if (use_tma(p, FRACTAL_U8)) {
+    CUtensorMap maps[2];
+    const int rho = 1 << p->log_rho;
+    if (!encode_tile_map(&maps[0], a, p->n, rho, FRACTAL_U8) || !encode_tile_map(&maps[1], b, p->n, rho, FRACTAL_U8))
+      return cuda_fail(cudaErrorInvalidValue, "tensor map");
+    for (int s = 0; s < steps; ++s) {
+      cudaError_t e = launch_ca_tma(p->mode, p->log_rho, p->tma[FRACTAL_U8], maps[s & 1], buf[s & 1],
+                                    buf[(s + 1) & 1], p->d_err, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    }
+    return FRACTAL_OK;
+  }
   for (int s = 0; s < steps; ++s) {
-    cudaError_t e = launch_ca(p->mode, p->log_rho, p->step[FRACTAL_U8], cur, nxt, (cudaStream_t)stream);
+    cudaError_t e = launch_ca(p->mode, p->log_rho, p->step[FRACTAL_U8], buf[s & 1], buf[(s + 1) & 1], st);
     if (e != cudaSuccess) return cuda_fail(e, "step_ca");
-    uint8_t* t = cur;
-    cur = nxt;
-    nxt = t;
   }
   return FRACTAL_OK;
 }
@@ -270,15 +357,26 @@ int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int
   if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0 ||
       !std::isfinite(coef))
     return FRACTAL_EINVAL;
-  float* cur = a;
-  float* nxt = b;
+  if (steps == 0) return FRACTAL_OK;
+  const cudaStream_t st = (cudaStream_t)stream;
+  float* buf[2] = {a, b};
+  if (use_tma(p, FRACTAL_F32)) {
+    CUtensorMap maps[2];
+    const int rho = 1 << p->log_rho;
+    if (!encode_tile_map(&maps[0], a, p->n, rho, FRACTAL_F32) ||
+        !encode_tile_map(&maps[1], b, p->n, rho, FRACTAL_F32))
+      return cuda_fail(cudaErrorInvalidValue, "tensor map");
+    for (int s = 0; s < steps; ++s) {
+      cudaError_t e = launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], buf[s & 1],
+                                           buf[(s + 1) & 1], coef, p->d_err, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+    }
+    return FRACTAL_OK;
+  }
   for (int s = 0; s < steps; ++s) {
     cudaError_t e =
-        launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], cur, nxt, coef, (cudaStream_t)stream);
+        launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], buf[s & 1], buf[(s + 1) & 1], coef, st);
     if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-    float* t = cur;
-    cur = nxt;
-    nxt = t;
   }
   return FRACTAL_OK;
 }

@@ -32,6 +32,7 @@ struct Geo {
   int32_t T;      // super-tile side in cells: rho << m
   int32_t slots;  // tile slots per CTA: 3^m (lambda) or 4^m (BB)
   int32_t lw;     // width of the level-m packed grid: 3^ceil(m/2)
+  int32_t tiles;  // member tiles of a member super-tile: 3^m
 };
 
 constexpr uint32_t kNoTile = 0xffffffffu;

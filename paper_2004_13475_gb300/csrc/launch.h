@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "gasket.cuh"
@@ -25,6 +26,13 @@ cudaError_t launch_sw(int mode, int log_rho, int dtype, const Launch& L, void* o
 cudaError_t launch_reduce(int mode, int log_rho, int dtype, const Launch& L, const void* in,
                           void* partials, double* dev_out, cudaStream_t s);
 cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s);
+
+// TMA-staged step kernels (rho * element size >= 16 bytes; see k_tma.cu).
+cudaError_t launch_diffusion_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const float* in,
+                                 float* out, float a, int* err, cudaStream_t s);
+cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const uint8_t* in,
+                          uint8_t* out, int* err, cudaStream_t s);
+int tma_smem_bytes(const Geo& g, int tile_bytes);
 
 // Dynamic shared memory above the 48 KB default needs an opt-in per kernel.
 cudaError_t allow_smem(const void* func, int bytes);

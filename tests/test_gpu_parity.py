@@ -34,6 +34,13 @@ def cases(ks, rhos=(1, 2, 4, 8, 16, 32)):
 
 
 MODES = [0, 1]   # FRACTAL_LAMBDA, FRACTAL_BB
+SCHEDS = [0, 1]  # FRACTAL_SCHED_AUTO (TMA where it applies), FRACTAL_SCHED_STAGED
+
+
+def make_plan(fr, k, rho, mode, sched=0):
+    plan = fr.fractal_map(k, rho, mode)
+    fr.fractal_plan_set_schedule(plan, sched)
+    return plan
 
 
 def dev_u8(arr):
@@ -100,11 +107,12 @@ def run_ca(fr, plan, s0, steps, sentinel=SENTINEL_U8):
     return out.cpu().numpy().reshape(n, n), a, b
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("k,rho", cases([1, 2, 3, 4, 6, 8, 10]))
-def test_ca_bit_exact(fr, k, rho, mode):
+def test_ca_bit_exact(fr, k, rho, mode, sched):
     n = 1 << k
-    plan = fr.fractal_map(k, rho, mode)
+    plan = make_plan(fr, k, rho, mode, sched)
     s0 = synth.bernoulli_u8(k, n)          # non-member cells hold noise and must be ignored
     want = oracle.ca_run(s0, 6, domain(k))
     # 6 steps: result in a; b holds step 5.  Cells outside member tiles keep
@@ -121,16 +129,18 @@ def test_ca_bit_exact(fr, k, rho, mode):
     odd = b.cpu().numpy().reshape(n, n)
     assert np.array_equal(odd[mask], oracle.ca_run(s0, 5, domain(k))[mask])
     assert np.all(odd[~cover] == SENTINEL_U8)
+    assert fr.fractal_plan_device_status(plan) == 0
 
 
 @pytest.mark.parametrize("k,rho", [(9, 8), (9, 16), (9, 32), (10, 32)])
-def test_ca_every_cta_level(fr, k, rho):
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_ca_every_cta_level(fr, k, rho, sched):
     n = 1 << k
     s0 = synth.bernoulli_u8(100 + k, n)
     want = oracle.ca_run(s0, 3, domain(k))
     mask = domain(k).mask
     for mode in MODES:
-        plan = fr.fractal_map(k, rho, mode)
+        plan = make_plan(fr, k, rho, mode, sched)
         rb = k - int(np.log2(rho))
         for m in range(0, min(rb, 5) + 1):
             try:
@@ -183,11 +193,12 @@ def run_diffusion(fr, plan, u0, steps, a=0.2, sentinel=SENTINEL_F32):
     return out.cpu().numpy().reshape(n, n)
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("k,rho", cases([1, 2, 3, 4, 6, 8, 10]))
-def test_diffusion_parity(fr, k, rho, mode):
+def test_diffusion_parity(fr, k, rho, mode, sched):
     n = 1 << k
-    plan = fr.fractal_map(k, rho, mode)
+    plan = make_plan(fr, k, rho, mode, sched)
     u0 = synth.uniform_f32(k, n)
     want = oracle.diffusion_run(u0.astype(np.float64), 7, 0.2, domain(k))
     got = run_diffusion(fr, plan, u0, 7)
@@ -197,16 +208,18 @@ def test_diffusion_parity(fr, k, rho, mode):
     cover = tile_cover(n, rho)
     assert np.all(got[cover & ~mask] == 0)
     assert np.array_equal(got[~cover], np.full_like(got[~cover], SENTINEL_F32))
+    assert fr.fractal_plan_device_status(plan) == 0
 
 
 @pytest.mark.parametrize("k,rho", [(9, 4), (9, 8), (10, 16), (10, 32)])
-def test_diffusion_every_cta_level(fr, k, rho):
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_diffusion_every_cta_level(fr, k, rho, sched):
     n = 1 << k
     u0 = synth.uniform_f32(50 + k, n)
     want = oracle.diffusion_run(u0.astype(np.float64), 3, 0.2, domain(k))
     mask = domain(k).mask
     for mode in MODES:
-        plan = fr.fractal_map(k, rho, mode)
+        plan = make_plan(fr, k, rho, mode, sched)
         rb = k - int(np.log2(rho))
         for m in range(0, min(rb, 5) + 1):
             try:
@@ -217,13 +230,14 @@ def test_diffusion_every_cta_level(fr, k, rho):
             assert rel_err(got, want, mask)[0] <= 1e-6, (mode, m)
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("mode", MODES)
-def test_diffusion_1000_steps(fr, mode):
+def test_diffusion_1000_steps(fr, mode, sched):
     # the accuracy bound at the step count of the k = 14 workload, on k = 10
     k, n = 10, 1024
     u0 = synth.uniform_f32(3, n)
     want = oracle.diffusion_run(u0.astype(np.float64), 1000, 0.2, domain(k))
-    got = run_diffusion(fr, fr.fractal_map(k, 8, mode), u0, 1000)
+    got = run_diffusion(fr, make_plan(fr, k, 8, mode, sched), u0, 1000)
     err, raw = rel_err(got, want, domain(k).mask)
     assert err <= 1e-4, (err, raw)
 
@@ -316,3 +330,18 @@ def test_runtime_validation(fr):
         fr.fractal_map_write(plan, f, 5, 1.0)
     with pytest.raises(fr.FractalError):
         fr.fractal_plan_set_cta_levels(plan, 0, 9)
+    with pytest.raises(fr.FractalError):
+        fr.fractal_plan_set_schedule(plan, 7)
+    tiny = fr.fractal_map(2, 1)        # rows of 1 element: no TMA kernel applies
+    with pytest.raises(fr.FractalError):
+        fr.fractal_plan_set_schedule(tiny, fr.FRACTAL_SCHED_TMA)
+
+
+def test_plan_reports_tma(fr):
+    inf = fr.fractal_map(16, 8).info()
+    assert inf["tma"] == [0, 1]          # uint8 rho = 8 stages by vector loads; float32 by TMA
+    inf = fr.fractal_map(16, 32).info()
+    assert inf["tma"] == [1, 1]
+    p = fr.fractal_map(16, 32)
+    fr.fractal_plan_set_schedule(p, fr.FRACTAL_SCHED_STAGED)
+    assert p.info()["tma"] == [0, 0]
