@@ -110,19 +110,21 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   tma_ok = dtype == FRACTAL_U8 ? rho >= 16 : rho >= 4;
   tma = step;
   if (tma_ok) {
-    const int64_t items = dtype == FRACTAL_U8 ? (int64_t)g.tiles * rho : (int64_t)g.tiles * (rho / 4) * (rho / 4);
-    const int cap = dtype == FRACTAL_U8 ? 1024 : 512;
+    // one thread per tile row (uint8) or per float4 (float32), capped at the
+    // kernels' launch bounds (the update loop strides over the rest)
+    const int64_t items = dtype == FRACTAL_U8 ? (int64_t)g.tiles * rho : (int64_t)g.tiles * rho * (rho / 4);
+    const int cap = dtype == FRACTAL_U8 ? 512 : 256;
     int t = (int)((items + 31) / 32 * 32);
     if (t > cap) t = cap;
     tma.threads = t;
-    tma.smem = tma_smem_bytes(g, rho * rho * (dtype == FRACTAL_U8 ? 1 : 4));
+    tma.smem = tma_smem_bytes(g, rho * rho * (dtype == FRACTAL_U8 ? 1 : 4), dtype);
     if (tma.smem > kMaxSmem) tma_ok = false;
   }
   return true;
 }
 
-// Tensor map of an n x n array for rho x rho boxes (driver entry point).
-bool encode_tile_map(CUtensorMap* map, const void* base, int n, int rho, int dtype) {
+// Tensor map of an n x n array for bw x bh boxes (driver entry point).
+bool encode_box_map(CUtensorMap* map, const void* base, int n, int bw, int bh, int dtype) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -136,7 +138,7 @@ bool encode_tile_map(CUtensorMap* map, const void* base, int n, int rho, int dty
   const int e = dtype == FRACTAL_U8 ? 1 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
   cuuint64_t strides[1] = {(cuuint64_t)n * e};
-  cuuint32_t box[2] = {(cuuint32_t)rho, (cuuint32_t)rho};
+  cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(map, dtype == FRACTAL_U8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                       const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -144,14 +146,23 @@ bool encode_tile_map(CUtensorMap* map, const void* base, int n, int rho, int dty
   return r == CUDA_SUCCESS;
 }
 
+// rho x rho tile boxes and 16-byte ring boxes of one array.
+bool encode_maps(CUtensorMap* tile, CUtensorMap* ring, const void* base, int n, int rho, int dtype) {
+  return encode_box_map(tile, base, n, rho, rho, dtype) &&
+         encode_box_map(ring, base, n, dtype == FRACTAL_U8 ? 16 : 4, 1, dtype);
+}
+
 bool use_tma(const fractal_plan_s* p, int dtype) {
   return p->tma_ok[dtype] && p->sched != FRACTAL_SCHED_STAGED;
 }
 
 int default_levels(const fractal_plan_s& p, int dtype) {
-  // Super-tile of about 128 uint8 cells or 64 float cells per side; BB also
-  // needs 2^R <= 32768.
-  const int target = dtype == FRACTAL_U8 ? 7 : 6;
+  // Super-tile side: the TMA kernels (uint8 rho >= 16, float32 rho >= 4) keep
+  // the whole super-tile in flight, 256 uint8 / 128 float cells per side; the
+  // vector-load kernels stage an image of it, 128 uint8 / 64 float cells.
+  const int rho = 1 << p.log_rho;
+  const bool tma = dtype == FRACTAL_U8 ? rho >= 16 : rho >= 4;
+  const int target = dtype == FRACTAL_U8 ? (tma ? 8 : 7) : (tma ? 7 : 6);
   int m = target - p.log_rho;
   if (m < 0) m = 0;
   if (m > p.rb) m = p.rb;
@@ -335,12 +346,13 @@ int fractal_step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, void* s
   const cudaStream_t st = (cudaStream_t)stream;
   uint8_t* buf[2] = {a, b};
   if (use_tma(p, FRACTAL_U8)) {
-    CUtensorMap maps[2];
+    CUtensorMap maps[2], rings[2];
     const int rho = 1 << p->log_rho;
-    if (!encode_tile_map(&maps[0], a, p->n, rho, FRACTAL_U8) || !encode_tile_map(&maps[1], b, p->n, rho, FRACTAL_U8))
+    if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_U8) ||
+        !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_U8))
       return cuda_fail(cudaErrorInvalidValue, "tensor map");
     for (int s = 0; s < steps; ++s) {
-      cudaError_t e = launch_ca_tma(p->mode, p->log_rho, p->tma[FRACTAL_U8], maps[s & 1], buf[s & 1],
+      cudaError_t e = launch_ca_tma(p->mode, p->log_rho, p->tma[FRACTAL_U8], maps[s & 1], rings[s & 1],
                                     buf[(s + 1) & 1], p->d_err, st);
       if (e != cudaSuccess) return cuda_fail(e, "step_ca");
     }
@@ -361,13 +373,13 @@ int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int
   const cudaStream_t st = (cudaStream_t)stream;
   float* buf[2] = {a, b};
   if (use_tma(p, FRACTAL_F32)) {
-    CUtensorMap maps[2];
+    CUtensorMap maps[2], rings[2];
     const int rho = 1 << p->log_rho;
-    if (!encode_tile_map(&maps[0], a, p->n, rho, FRACTAL_F32) ||
-        !encode_tile_map(&maps[1], b, p->n, rho, FRACTAL_F32))
+    if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_F32) ||
+        !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_F32))
       return cuda_fail(cudaErrorInvalidValue, "tensor map");
     for (int s = 0; s < steps; ++s) {
-      cudaError_t e = launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], buf[s & 1],
+      cudaError_t e = launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], rings[s & 1],
                                            buf[(s + 1) & 1], coef, p->d_err, st);
       if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
     }

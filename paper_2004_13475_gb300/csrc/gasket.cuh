@@ -140,6 +140,27 @@ __device__ __forceinline__ bool cta_supertile(const Geo& g, int& sx, int& sy) {
   return (sx & sy) == 0;
 }
 
+// Inverse of the level-m map: tile (ux, uy) of a member super-tile (ux & uy
+// == 0) -> its index j = omega_y * lw + omega_x in the level-m packed grid.
+// Per level mu the bit pair (x, y) gives the replica index (flipped table H:
+// (0,1) -> 0, (0,0) -> 1, (1,0) -> 2), a base-3 digit of omega_x (odd mu) or
+// omega_y (even mu).
+__device__ __forceinline__ int lambda_inverse(int ux, int uy, int levels, int lw) {
+  int wx = 0, wy = 0, px = 1, py = 1;
+  for (int mu = 1; mu <= levels; ++mu) {
+    const int bx = (ux >> (mu - 1)) & 1, by = (uy >> (mu - 1)) & 1;
+    const int beta = bx ? 2 : (by ? 0 : 1);
+    if (mu & 1) {
+      wx += beta * px;
+      px *= 3;
+    } else {
+      wy += beta * py;
+      py *= 3;
+    }
+  }
+  return wy * lw + wx;
+}
+
 // Step 2: slot table in shared memory, entry = ux | uy << 16 (tile offsets
 // inside the super-tile) or kNoTile for a discarded BB slot.
 template <int MODE>

@@ -1,229 +1,281 @@
 // TMA-staged step kernels (sm_103a): one elected warp issues a 2-D tensor
 // copy (cp.async.bulk.tensor) per member tile of the CTA's super-tile into
-// dense shared-memory tiles, completing on one mbarrier; the CTA then updates
-// the tiles from shared memory and writes them back with vector stores.
+// dense shared-memory tiles, plus one 16-byte box per super-tile ring cell,
+// all completing on one mbarrier; the CTA then updates the tiles from shared
+// memory and writes them back with vector stores.
 //
 // Halo.  With membership (x & y) == 0, a member tile's member cells touch
 // only a handful of cells outside the tile (all of them at in-tile offsets
 // whose low bits are zero, so each is a member iff its tile is):
 //   von Neumann (diffusion): (0,-1), (-1,0), (rho,0), (0,rho);
 //   Moore (automaton):       those four and (rho,-1), (rho,1), (-1,rho), (1,rho).
-// Each comes from a neighbouring tile of the same super-tile (shared memory),
-// or, for the super-tile's own border, from the matching cell of the
-// super-tile's ring, which is prefetched before the wait.
+// The same holds one level up for the super-tile of side T, so its ring holds
+// at most these 4 (resp. 8) cells, loaded as 16-byte TMA boxes (coordinates
+// outside the array read as zero).  Everything else comes from neighbouring
+// tiles in shared memory.
 #include "launch.h"
 #include "tma.cuh"
 
 namespace fractal {
 
-// TMA writes each tile to a 128-byte aligned shared-memory slot.
+// TMA writes each tile and ring box to a 128-byte aligned shared-memory slot.
 __host__ __device__ constexpr int tile_stride(int tile_bytes) { return (tile_bytes + 127) & ~127; }
+
+constexpr int kRingSlot = 128;  // bytes per ring box slot (the box itself is 16 bytes)
 
 // Shared-memory layout of the TMA kernels; host and device compute it alike.
 struct TmaLayout {
-  int bar, tab, inv, ring, tiles, total;
-  __host__ __device__ TmaLayout(const Geo& g, int tile_bytes) {
-    const int nt = g.tiles;          // member tiles per CTA (3^m)
-    const int side = 1 << g.m;       // tile slots per super-tile side
+  int bar, sxy, tab, inv, ring, tiles, total;
+  __host__ __device__ TmaLayout(const Geo& g, int tile_bytes, int rings) {
+    const int side = 1 << g.m;
     bar = 0;
+    sxy = 8;
     tab = 16;
-    inv = tab + ((nt * 4 + 15) & ~15);
-    ring = inv + ((side * side * 2 + 15) & ~15);
-    tiles = (ring + 8 * 4 + 127) & ~127;
-    total = tiles + nt * tile_stride(tile_bytes);
+    inv = tab + ((g.tiles * 4 + 15) & ~15);
+    ring = (inv + side * side * 2 + 127) & ~127;
+    tiles = ring + rings * kRingSlot;
+    total = tiles + g.tiles * tile_stride(tile_bytes);
   }
 };
 
-int tma_smem_bytes(const Geo& g, int tile_bytes) { return TmaLayout(g, tile_bytes).total; }
-
 namespace {
 
-// Member tiles of the super-tile in the launch's order (lambda: further
-// unrolling; BB: row-major scan of all 4^m slots keeping members), and the
-// inverse map (local tile -> index, -1 for a non-member tile).
+// Member tiles of the super-tile in launch order and the inverse map (local
+// tile -> index, -1 for a non-member tile), one pass over the 4^m slots.
+// lambda: the level-m map's order (index = omega_y * lw + omega_x);
+// BB: row-major scan keeping members, as a bounding-box launch discards.
 template <int MODE>
 __device__ __forceinline__ void build_tables(uint32_t* tab, int16_t* inv, const Geo& g) {
   const int side = 1 << g.m;
-  for (int j = threadIdx.x; j < side * side; j += blockDim.x) inv[j] = -1;
-  __syncthreads();
-  if (MODE == kLambda) {
-    for (int j = threadIdx.x; j < g.tiles; j += blockDim.x) {
-      int ux, uy;
-      lambda_scalar((uint32_t)(j % g.lw), (uint32_t)(j / g.lw), g.m, ux, uy);
-      tab[j] = (uint32_t)ux | ((uint32_t)uy << 16);
-      inv[uy * side + ux] = (int16_t)j;
+  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+    const int ux = j & (side - 1), uy = j >> g.m;
+    if (ux & uy) {
+      inv[j] = -1;
+      continue;
     }
-  } else {
-    // slot j = (ux, uy) row-major; its rank among member slots is the number
-    // of member slots before it (discarding the others, as the BB launch does)
-    for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
-      const int ux = j & (side - 1), uy = j >> g.m;
-      if (ux & uy) continue;
-      int rank = 0;
+    int rank;
+    if (MODE == kLambda) {
+      rank = lambda_inverse(ux, uy, g.m, g.lw);
+    } else {
+      rank = 0;
       for (int q = 0; q < j; ++q) rank += ((q & (side - 1)) & (q >> g.m)) == 0;
-      tab[rank] = (uint32_t)ux | ((uint32_t)uy << 16);
-      inv[j] = (int16_t)rank;
     }
+    tab[rank] = (uint32_t)ux | ((uint32_t)uy << 16);
+    inv[j] = (int16_t)rank;
   }
 }
 
-template <int MODE, int LOG_RHO>
-__global__ void __launch_bounds__(512) diffusion_tma_kernel(const __grid_constant__ CUtensorMap tin,
-                                                            const float* __restrict__ in, float* __restrict__ out,
-                                                            float a, Geo g, int* err) {
-  constexpr int RHO = 1 << LOG_RHO;
-  constexpr int MBH = RHO < 4 ? RHO : 4;                  // micro-block: 4 columns x MBH rows
-  constexpr int MBX = RHO / 4;                            // micro-blocks per tile row
-  constexpr int LOG_MBT = ilog2c(MBX * (RHO / MBH));      // micro-blocks per tile (log)
-  constexpr int TILE = RHO * RHO;                         // floats
-  constexpr int TS = tile_stride(TILE * 4) / 4;           // slot stride (floats)
-  extern __shared__ __align__(128) unsigned char sm[];
-
-  int sx, sy;
-  if (!cta_supertile<MODE>(g, sx, sy)) return;
-  const TmaLayout L(g, TILE * 4);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
-  uint32_t* tab = reinterpret_cast<uint32_t*>(sm + L.tab);
-  int16_t* inv = reinterpret_cast<int16_t*>(sm + L.inv);
-  float* ring = reinterpret_cast<float*>(sm + L.ring);
-  float* tiles = reinterpret_cast<float*>(sm + L.tiles);
-  const int n = g.n, T = g.T, side = 1 << g.m;
-  const int ox = sx * T, oy = sy * T;
-
-  if (threadIdx.x == 0) {
-    prefetch_tensormap(&tin);
-    mbar_init(bar, 1);
-    fence_barrier_init();
+// Prologue shared by both kernels: CTA -> super-tile (lambda by warp 0, BB by
+// identity), barrier init, tables.  Returns false for a discarded BB block.
+template <int MODE>
+__device__ __forceinline__ bool tma_prologue(const Geo& g, uint64_t* bar, int* sxy, uint32_t* tab, int16_t* inv,
+                                             const CUtensorMap* t0, const CUtensorMap* t1, int& sx, int& sy) {
+  if (MODE == kBB) {
+    sx = (int)blockIdx.x;
+    sy = (int)blockIdx.y;
+    if (sx & sy) return false;
+  }
+  if (threadIdx.x < 32) {
+    if (MODE == kLambda) {
+      warp_lambda(blockIdx.x, blockIdx.y, g.R, sx, sy);
+      if (threadIdx.x == 0) {
+        sxy[0] = sx;
+        sxy[1] = sy;
+      }
+    }
+    if (threadIdx.x == 0) {
+      prefetch_tensormap(t0);
+      prefetch_tensormap(t1);
+      mbar_init(bar, 1);
+      fence_barrier_init();
+    }
   }
   build_tables<MODE>(tab, inv, g);
   __syncthreads();
-
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)(g.tiles * TILE * 4));
-    __syncwarp();
-    for (int c = threadIdx.x; c < g.tiles; c += 32) {
-      const uint32_t e = tab[c];
-      tma_load_2d(tiles + c * TS, &tin, ox + (int)(e & 0xffffu) * RHO, oy + (int)(e >> 16) * RHO, bar);
-    }
-    // super-tile ring for the von Neumann halo: (0,-1), (-1,0), (T,0), (0,T)
-    if (threadIdx.x < 4) {
-      const int r = threadIdx.x;
-      const int lx = r == 1 ? -1 : (r == 2 ? T : 0);
-      const int ly = r == 0 ? -1 : (r == 3 ? T : 0);
-      const int gx = ox + lx, gy = oy + ly;
-      float v = 0.0f;
-      if (is_member(gx, gy, n)) v = __ldg(in + (size_t)gy * n + gx);
-      ring[r] = v;
-      ring[4 + r] = is_member(gx, gy, n) ? 1.0f : 0.0f;
-    }
+  if (MODE == kLambda) {
+    sx = sxy[0];
+    sy = sxy[1];
   }
-  __syncthreads();
+  return true;
+}
+
+// Halo cell k of a square of side S (tile or super-tile), relative to its
+// corner.  Moore order: (-1,0) (S,0) (S,1) (0,-1) (S,-1) (-1,S) (0,S) (1,S);
+// von Neumann order: (0,-1) (-1,0) (S,0) (0,S).
+__device__ __forceinline__ void moore_halo(int k, int S, int& x, int& y) {
+  x = (k == 0 || k == 5) ? -1 : ((k == 3 || k == 6) ? 0 : (k == 7 ? 1 : S));
+  y = (k == 0 || k == 1) ? 0 : (k == 2 ? 1 : ((k == 3 || k == 4) ? -1 : S));
+}
+
+__device__ __forceinline__ void vn_halo(int k, int S, int& x, int& y) {
+  x = k == 1 ? -1 : (k == 2 ? S : 0);
+  y = k == 0 ? -1 : (k == 3 ? S : 0);
+}
+
+// Global x of a ring box holding cell gx (16-byte aligned, may be negative).
+template <int RB>
+__device__ __forceinline__ int box_x(int gx) {
+  return gx >= 0 ? (gx & ~(RB - 1)) : -RB;
+}
+
+// Warp 0: expect the bytes, then one TMA per member tile and per ring cell
+// (RINGS = 8: Moore halo of the super-tile, 4: von Neumann).
+template <int RHO, int E, int RINGS>
+__device__ __forceinline__ void tma_issue(uint64_t* bar, const uint32_t* tab, unsigned char* tiles,
+                                          unsigned char* rings, const CUtensorMap* tin, const CUtensorMap* tring,
+                                          const Geo& g, int ox, int oy) {
+  constexpr int TS = tile_stride(RHO * RHO * E);
+  constexpr int RB = 16 / E;  // ring box width in elements
+  const int lane = threadIdx.x;
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(g.tiles * RHO * RHO * E + RINGS * 16));
+  __syncwarp();
+  for (int c = lane; c < g.tiles; c += 32) {
+    const uint32_t e = tab[c];
+    tma_load_2d(tiles + c * TS, tin, ox + (int)(e & 0xffffu) * RHO, oy + (int)(e >> 16) * RHO, bar);
+  }
+  if (lane < RINGS) {
+    int lx, ly;
+    if (RINGS == 8) moore_halo(lane, g.T, lx, ly);
+    else vn_halo(lane, g.T, lx, ly);
+    const int gx = ox + lx, gy = oy + ly;
+    tma_load_2d(rings + lane * kRingSlot, tring, box_x<RB>(gx), gy, bar);
+  }
+}
+
+// ------------------------------------------------------------- diffusion ----
+
+template <int MODE, int LOG_RHO>
+__global__ void __launch_bounds__(256, 6) diffusion_tma_kernel(const __grid_constant__ CUtensorMap tin,
+                                                            const __grid_constant__ CUtensorMap tring,
+                                                            float* __restrict__ out, float a, Geo g, int* err) {
+  constexpr int RHO = 1 << LOG_RHO;                       // >= 4
+  constexpr int MBX = RHO / 4;                            // float4s per tile row
+  constexpr int LOG_Q = 2 * LOG_RHO - 2;                  // float4s per tile (log)
+  constexpr int TILE = RHO * RHO;                         // floats
+  constexpr int TS = tile_stride(TILE * 4) / 4;           // slot stride (floats)
+  constexpr int RB = 4;                                   // ring box: 4 floats
+  extern __shared__ __align__(128) unsigned char sm[];
+
+  const TmaLayout L(g, TILE * 4, 4);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
+  int* sxy = reinterpret_cast<int*>(sm + L.sxy);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(sm + L.tab);
+  int16_t* inv = reinterpret_cast<int16_t*>(sm + L.inv);
+  const float* ring = reinterpret_cast<const float*>(sm + L.ring);
+  float* tiles = reinterpret_cast<float*>(sm + L.tiles);
+  int sx, sy;
+  if (!tma_prologue<MODE>(g, bar, sxy, tab, inv, &tin, &tring, sx, sy)) return;
+  const int n = g.n, T = g.T, side = 1 << g.m;
+  const int ox = sx * T, oy = sy * T;
+  // super-tile ring cells of the von Neumann halo: (0,-1), (-1,0), (T,0), (0,T)
+  if (threadIdx.x < 32)
+    tma_issue<RHO, 4, 4>(bar, tab, reinterpret_cast<unsigned char*>(tiles), sm + L.ring, &tin, &tring, g, ox, oy);
   if (!mbar_wait_bounded(bar, 0, err, kErrTmaTimeout)) {
     mbar_wait_bounded(bar, 0, err, kErrDrainTimeout);
     return;
   }
 
-  const int items = g.tiles << LOG_MBT;
+  // One float4 (4 cells of a tile row) per thread; consecutive threads take
+  // consecutive float4s of a tile, so the 8 lanes of a 128-bit shared-memory
+  // phase read 8 different bank groups and every store writes whole sectors.
+  const int items = g.tiles << LOG_Q;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it >> LOG_MBT;
-    const int mb = it & ((1 << LOG_MBT) - 1);
+    const int c = it >> LOG_Q;
+    const int q = it & ((1 << LOG_Q) - 1);
     const uint32_t e = tab[c];
     const int ux = (int)(e & 0xffffu), uy = (int)(e >> 16);
-    const int tx0 = (mb % MBX) * 4, ty0 = (mb / MBX) * MBH;
+    const int ty = q / MBX, tx0 = (q % MBX) * 4;
     const float* tile = tiles + c * TS;
+    const float* row = tile + ty * RHO + tx0;
 
-    // The four cells outside the tile (value, member flag).
-    float ev_up = 0.f, ev_lf = 0.f, ev_rt = 0.f, ev_dn = 0.f;
-    bool ef_up = false, ef_lf = false, ef_rt = false, ef_dn = false;
-    if (ty0 == 0 && tx0 == 0) {
+    const float4 cur = *reinterpret_cast<const float4*>(row);
+    float4 up = make_float4(0.f, 0.f, 0.f, 0.f), dn = up;
+    uint32_t mu = 0u, md = 0u;
+    if (ty > 0) {
+      up = *reinterpret_cast<const float4*>(row - RHO);
+      mu = row_pattern((uint32_t)(ty - 1)) >> tx0;
+    } else if (tx0 == 0) {
+      // (0,-1): bottom-left cell of the tile above, or the super-tile ring
       if (uy > 0) {
-        const int q = inv[(uy - 1) * side + ux];
-        if (q >= 0) { ev_up = tiles[q * TS + (RHO - 1) * RHO]; ef_up = true; }
+        const int qq = inv[(uy - 1) * side + ux];
+        if (qq >= 0) { up.x = tiles[qq * TS + (RHO - 1) * RHO]; mu = 1u; }
       } else if (ux == 0) {
-        ev_up = ring[0]; ef_up = ring[4] != 0.f;
-      }
-      if (ux > 0) {
-        const int q = inv[uy * side + ux - 1];
-        if (q >= 0) { ev_lf = tiles[q * TS + RHO - 1]; ef_lf = true; }
-      } else if (uy == 0) {
-        ev_lf = ring[1]; ef_lf = ring[5] != 0.f;
+        const int gx = ox, gy = oy - 1;
+        up.x = ring[0 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
+        mu = is_member(gx, gy, n) ? 1u : 0u;
       }
     }
-    if (ty0 == 0 && tx0 + 4 == RHO) {
-      if (ux + 1 < side) {
-        const int q = inv[uy * side + ux + 1];
-        if (q >= 0) { ev_rt = tiles[q * TS]; ef_rt = true; }
-      } else if (uy == 0) {
-        ev_rt = ring[2]; ef_rt = ring[6] != 0.f;
-      }
-    }
-    if (tx0 == 0 && ty0 + MBH == RHO) {
+    if (ty < RHO - 1) {
+      dn = *reinterpret_cast<const float4*>(row + RHO);
+      md = row_pattern((uint32_t)(ty + 1)) >> tx0;
+    } else if (tx0 == 0) {
+      // (0,rho): top-left cell of the tile below, or the super-tile ring
       if (uy + 1 < side) {
-        const int q = inv[(uy + 1) * side + ux];
-        if (q >= 0) { ev_dn = tiles[q * TS]; ef_dn = true; }
+        const int qq = inv[(uy + 1) * side + ux];
+        if (qq >= 0) { dn.x = tiles[qq * TS]; md = 1u; }
       } else if (ux == 0) {
-        ev_dn = ring[3]; ef_dn = ring[7] != 0.f;
+        const int gx = ox, gy = oy + T;
+        dn.x = ring[3 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
+        md = is_member(gx, gy, n) ? 1u : 0u;
       }
     }
-
-    float* gout = out + (size_t)(oy + uy * RHO) * n + ox + ux * RHO + tx0;
-#pragma unroll
-    for (int r = 0; r < MBH; ++r) {
-      const int ty = ty0 + r;
-      const float4 cur = *reinterpret_cast<const float4*>(tile + ty * RHO + tx0);
-      float4 up = make_float4(ev_up, 0.f, 0.f, 0.f), dn = make_float4(ev_dn, 0.f, 0.f, 0.f);
-      uint32_t mu = ef_up ? 1u : 0u, md = ef_dn ? 1u : 0u;
-      if (ty > 0) {
-        up = *reinterpret_cast<const float4*>(tile + (ty - 1) * RHO + tx0);
-        mu = row_pattern((uint32_t)(ty - 1)) >> tx0;
+    const uint32_t pm = row_pattern((uint32_t)ty);
+    const uint32_t mm = pm >> tx0;
+    // left of column tx0 and right of column tx0+3
+    float lf = 0.f, rt = 0.f;
+    bool ml = false, mr = false;
+    if (tx0 > 0) {
+      lf = row[-1];
+      ml = (pm >> (tx0 - 1)) & 1u;
+    } else if (ty == 0) {
+      // (-1,0): top-right cell of the tile to the left, or the super-tile ring
+      if (ux > 0) {
+        const int qq = inv[uy * side + ux - 1];
+        if (qq >= 0) { lf = tiles[qq * TS + RHO - 1]; ml = true; }
+      } else if (uy == 0) {
+        const int gx = ox - 1, gy = oy;
+        lf = ring[1 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
+        ml = is_member(gx, gy, n);
       }
-      if (ty < RHO - 1) {
-        dn = *reinterpret_cast<const float4*>(tile + (ty + 1) * RHO + tx0);
-        md = row_pattern((uint32_t)(ty + 1)) >> tx0;
-      }
-      const uint32_t pm = row_pattern((uint32_t)ty);
-      const uint32_t mm = pm >> tx0;
-      // left of column tx0 and right of column tx0+3
-      float lf = ev_lf, rt = ev_rt;
-      bool ml = (ty == 0) && ef_lf, mr = (ty == 0) && ef_rt;
-      if (tx0 > 0) { lf = tile[ty * RHO + tx0 - 1]; ml = (pm >> (tx0 - 1)) & 1u; }
-      if (tx0 + 4 < RHO) { rt = tile[ty * RHO + tx0 + 4]; mr = (pm >> (tx0 + 4)) & 1u; }
-      const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
-      const float uv[4] = {up.x, up.y, up.z, up.w};
-      const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
-      float res[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float u = cv[i];
-        const bool hl = i == 0 ? ml : ((mm >> (i - 1)) & 1u) != 0u;
-        const bool hr = i == 3 ? mr : ((mm >> (i + 1)) & 1u) != 0u;
-        const float vl = i == 0 ? lf : cv[i > 0 ? i - 1 : 0];
-        const float vr = i == 3 ? rt : cv[i < 3 ? i + 1 : 0];
-        // N4 in the order up, left, right, down; absent neighbours carry no flux
-        float s = ((mu >> i) & 1u) ? uv[i] - u : 0.0f;
-        s += hl ? vl - u : 0.0f;
-        s += hr ? vr - u : 0.0f;
-        s += ((md >> i) & 1u) ? dv[i] - u : 0.0f;
-        res[i] = ((mm >> i) & 1u) ? fmaf(a, s, u) : 0.0f;
-      }
-      *reinterpret_cast<float4*>(gout + (size_t)ty * n) = make_float4(res[0], res[1], res[2], res[3]);
     }
+    if (tx0 + 4 < RHO) {
+      rt = row[4];
+      mr = (pm >> (tx0 + 4)) & 1u;
+    } else if (ty == 0) {
+      // (rho,0): top-left cell of the tile to the right, or the super-tile ring
+      if (ux + 1 < side) {
+        const int qq = inv[uy * side + ux + 1];
+        if (qq >= 0) { rt = tiles[qq * TS]; mr = true; }
+      } else if (uy == 0) {
+        const int gx = ox + T, gy = oy;
+        rt = ring[2 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
+        mr = is_member(gx, gy, n);
+      }
+    }
+    const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+    const float uv[4] = {up.x, up.y, up.z, up.w};
+    const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+    float res[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float u = cv[i];
+      const bool hl = i == 0 ? ml : ((mm >> (i - 1)) & 1u) != 0u;
+      const bool hr = i == 3 ? mr : ((mm >> (i + 1)) & 1u) != 0u;
+      const float vl = i == 0 ? lf : cv[i > 0 ? i - 1 : 0];
+      const float vr = i == 3 ? rt : cv[i < 3 ? i + 1 : 0];
+      // N4 in the order up, left, right, down; absent neighbours carry no flux
+      float acc = ((mu >> i) & 1u) ? uv[i] - u : 0.0f;
+      acc += hl ? vl - u : 0.0f;
+      acc += hr ? vr - u : 0.0f;
+      acc += ((md >> i) & 1u) ? dv[i] - u : 0.0f;
+      res[i] = ((mm >> i) & 1u) ? fmaf(a, acc, u) : 0.0f;
+    }
+    *reinterpret_cast<float4*>(out + (size_t)(oy + uy * RHO + ty) * n + ox + ux * RHO + tx0) =
+        make_float4(res[0], res[1], res[2], res[3]);
   }
 }
 
-// Bits of a uint8 tile row (nonzero -> 1).
-template <int RHO>
-__device__ __forceinline__ uint32_t row_bits(const uint8_t* p) {
-  if constexpr (RHO == 32) {
-    const uint4 a = *reinterpret_cast<const uint4*>(p);
-    const uint4 b = *reinterpret_cast<const uint4*>(p + 16);
-    return nz4(a.x) | nz4(a.y) << 4 | nz4(a.z) << 8 | nz4(a.w) << 12 | nz4(b.x) << 16 | nz4(b.y) << 20 |
-           nz4(b.z) << 24 | nz4(b.w) << 28;
-  } else {
-    const uint4 a = *reinterpret_cast<const uint4*>(p);
-    return nz4(a.x) | nz4(a.y) << 4 | nz4(a.z) << 8 | nz4(a.w) << 12;
-  }
-}
+// ------------------------------------------------------------- automaton ----
 
 __device__ __forceinline__ uint32_t life_rule32(uint64_t up, uint64_t mid, uint64_t dn) {
   const uint32_t a = (uint32_t)up, b = (uint32_t)(up >> 1), c = (uint32_t)(up >> 2);
@@ -240,87 +292,45 @@ __device__ __forceinline__ uint32_t life_rule32(uint64_t up, uint64_t mid, uint6
   return bit1 & ~bit2 & (bit0 | self);
 }
 
-// Alive bit of a cell outside tile (ux, uy): a neighbouring tile's cell
-// (tile offsets dx, dy in {-1,0,1}; in-tile cell (cx, cy)), or the matching
-// super-tile ring entry when the neighbour tile lies outside the super-tile.
-template <int RHO>
-__device__ __forceinline__ uint32_t ext_bit(const uint8_t* tiles, const int16_t* inv, const uint8_t* ring, int side,
-                                            int ux, int uy, int dx, int dy, int cx, int cy) {
-  const int vx = ux + dx, vy = uy + dy;
-  if (vx >= 0 && vx < side && vy >= 0 && vy < side) {
-    const int q = inv[vy * side + vx];
-    return q >= 0 ? (tiles[q * RHO * RHO + cy * RHO + cx] != 0 ? 1u : 0u) : 0u;
-  }
-  // local super-tile coordinates of the cell
-  const int T = RHO * side;
-  const int lx = vx * RHO + cx, ly = vy * RHO + cy;
-  int r = -1;
-  if (lx == -1 && ly == 0) r = 0;
-  else if (lx == -1 && ly == T) r = 1;
-  else if (lx == 0 && ly == -1) r = 2;
-  else if (lx == T && ly == -1) r = 3;
-  else if (lx == T && ly == 0) r = 4;
-  else if (lx == T && ly == 1) r = 5;
-  else if (lx == 0 && ly == T) r = 6;
-  else if (lx == 1 && ly == T) r = 7;
-  return r >= 0 ? ring[r] : 0u;  // no other cell outside the super-tile can touch a member
+__device__ __forceinline__ uint32_t nz_half(uint4 v) {
+  return nz4(v.x) | nz4(v.y) << 4 | nz4(v.z) << 8 | nz4(v.w) << 12;
 }
 
 template <int MODE, int LOG_RHO>
-__global__ void __launch_bounds__(1024) ca_tma_kernel(const __grid_constant__ CUtensorMap tin,
-                                                      const uint8_t* __restrict__ in, uint8_t* __restrict__ out, Geo g,
-                                                      int* err) {
+__global__ void __launch_bounds__(512, 4) ca_tma_kernel(const __grid_constant__ CUtensorMap tin,
+                                                      const __grid_constant__ CUtensorMap tring,
+                                                      uint8_t* __restrict__ out, Geo g, int* err) {
   constexpr int RHO = 1 << LOG_RHO;  // 16 or 32: one lane per tile row
   constexpr int TILE = RHO * RHO;    // bytes
   static_assert(tile_stride(TILE) == TILE, "uint8 tiles of 16x16 or 32x32 bytes are 128-byte multiples");
+  constexpr int RB = 16;             // ring box: 16 bytes
   extern __shared__ __align__(128) unsigned char sm[];
 
-  int sx, sy;
-  if (!cta_supertile<MODE>(g, sx, sy)) return;
-  const TmaLayout L(g, TILE);
+  const TmaLayout L(g, TILE, 8);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar);
+  int* sxy = reinterpret_cast<int*>(sm + L.sxy);
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm + L.tab);
   int16_t* inv = reinterpret_cast<int16_t*>(sm + L.inv);
-  uint8_t* ring = reinterpret_cast<uint8_t*>(sm + L.ring);
+  const uint8_t* ring = sm + L.ring;
   uint8_t* tiles = sm + L.tiles;
+  int sx, sy;
+  if (!tma_prologue<MODE>(g, bar, sxy, tab, inv, &tin, &tring, sx, sy)) return;
   const int n = g.n, T = g.T, side = 1 << g.m;
   const int ox = sx * T, oy = sy * T;
-
-  if (threadIdx.x == 0) {
-    prefetch_tensormap(&tin);
-    mbar_init(bar, 1);
-    fence_barrier_init();
-  }
-  build_tables<MODE>(tab, inv, g);
-  __syncthreads();
-
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)(g.tiles * TILE));
-    __syncwarp();
-    for (int c = threadIdx.x; c < g.tiles; c += 32) {
-      const uint32_t e = tab[c];
-      tma_load_2d(tiles + c * TILE, &tin, ox + (int)(e & 0xffffu) * RHO, oy + (int)(e >> 16) * RHO, bar);
-    }
-    // the eight super-tile ring cells a member can touch (Moore halo)
-    if (threadIdx.x < 8) {
-      const int r = threadIdx.x;  // ring order: (-1,0) (-1,T) (0,-1) (T,-1) (T,0) (T,1) (0,T) (1,T)
-      const int lx = r < 2 ? -1 : (r == 2 || r == 6) ? 0 : (r == 7 ? 1 : T);
-      const int ly = r == 0 ? 0 : (r == 2 || r == 3) ? -1 : (r == 4 ? 0 : (r == 5 ? 1 : T));
-      const int gx = ox + lx, gy = oy + ly;
-      ring[r] = (is_member(gx, gy, n) && in[(size_t)gy * n + gx] != 0) ? 1 : 0;
-    }
-  }
-  __syncthreads();
+  // the eight super-tile ring cells a member can touch (Moore halo)
+  if (threadIdx.x < 32) tma_issue<RHO, 1, 8>(bar, tab, tiles, sm + L.ring, &tin, &tring, g, ox, oy);
   if (!mbar_wait_bounded(bar, 0, err, kErrTmaTimeout)) {
     mbar_wait_bounded(bar, 0, err, kErrDrainTimeout);
     return;
   }
 
   // One lane per tile row; groups of RHO lanes are one tile.  The loop runs
-  // whole warps (the shuffles need every lane), padding lanes store nothing.
+  // whole warps (the shuffles and ballots need every lane); padding lanes
+  // compute on tile 0 and store nothing.
   const int rows = g.tiles * RHO;
   const int rows_padded = (rows + 31) & ~31;
   const int lane = threadIdx.x & 31;
+  const int gl = lane & (RHO - 1);  // lane within the tile group
   for (int it = threadIdx.x; it < rows_padded; it += blockDim.x) {
     const bool live = it < rows;
     const int c = live ? it / RHO : 0;
@@ -328,28 +338,59 @@ __global__ void __launch_bounds__(1024) ca_tma_kernel(const __grid_constant__ CU
     const uint32_t e = tab[c];
     const int ux = (int)(e & 0xffffu), uy = (int)(e >> 16);
     const uint8_t* tile = tiles + c * TILE;
+
+    // Halo bits: lane i < 8 of the group fetches halo cell i (relative to the
+    // tile: (-1,0) (R,0) (R,1) (0,-1) (R,-1) (-1,R) (0,R) (1,R), R = rho); a
+    // ballot hands all eight to every lane of the group.
+    uint32_t hb = 0;
+    if (gl < 8) {
+      int hx, hy;
+      moore_halo(gl, RHO, hx, hy);
+      const int dx = hx < 0 ? -1 : (hx >= RHO ? 1 : 0), dy = hy < 0 ? -1 : (hy >= RHO ? 1 : 0);
+      const int vx = ux + dx, vy = uy + dy;
+      if (vx >= 0 && vx < side && vy >= 0 && vy < side) {
+        const int q = inv[vy * side + vx];
+        if (q >= 0) hb = tiles[q * TILE + (hy - dy * RHO) * RHO + (hx - dx * RHO)] != 0;
+      } else {
+        // Outside the super-tile the cell is the super-tile's halo cell of the
+        // same index or no member at all (no other cell outside the
+        // super-tile neighbours one of its members).
+        int sx_, sy_;
+        moore_halo(gl, T, sx_, sy_);
+        const int lx = ux * RHO + hx, ly = uy * RHO + hy;
+        if (lx == sx_ && ly == sy_) {
+          const int gx = ox + lx, gy = oy + ly;
+          hb = is_member(gx, gy, n) && ring[gl * kRingSlot + gx - box_x<RB>(gx)] != 0;
+        }
+      }
+    }
+    const uint32_t halo = (__ballot_sync(0xffffffffu, hb != 0) >> (lane & ~(RHO - 1))) & 0xffu;
+
+    // this row's bits; the two 16-byte halves are read in an order that
+    // spreads a 128-bit shared-memory phase over all bank groups
     const uint32_t pm = row_pattern((uint32_t)r) & low_bits<RHO>();
-    const uint32_t bits = row_bits<RHO>(tile + r * RHO) & pm;
+    uint32_t bits;
+    if constexpr (RHO == 32) {
+      const int h0 = (r >> 2) & 1;
+      const uint4 p = *reinterpret_cast<const uint4*>(tile + r * RHO + 16 * h0);
+      const uint4 q = *reinterpret_cast<const uint4*>(tile + r * RHO + 16 * (1 - h0));
+      const uint32_t bp = nz_half(p), bq = nz_half(q);
+      bits = h0 ? (bq | bp << 16) : (bp | bq << 16);
+    } else {
+      bits = nz_half(*reinterpret_cast<const uint4*>(tile + r * RHO));
+    }
+    bits &= pm;
     // own-row window: bit 0 = cell -1, bits 1..RHO = the row, bit RHO+1 = cell RHO
     uint64_t own = (uint64_t)bits << 1;
-    if (r == 0) {
-      own |= ext_bit<RHO>(tiles, inv, ring, side, ux, uy, -1, 0, RHO - 1, 0);
-      own |= (uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, 1, 0, 0, 0) << (RHO + 1);
-    } else if (r == 1) {
-      own |= (uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, 1, 0, 0, 1) << (RHO + 1);
-    }
+    if (r == 0) own |= (uint64_t)(halo & 1u) | ((uint64_t)((halo >> 1) & 1u) << (RHO + 1));
+    if (r == 1) own |= (uint64_t)((halo >> 2) & 1u) << (RHO + 1);
     uint64_t up = __shfl_up_sync(0xffffffffu, own, 1, RHO);
     uint64_t dn = __shfl_down_sync(0xffffffffu, own, 1, RHO);
-    if (r == 0) {
-      up = ((uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, 0, -1, 0, RHO - 1) << 1) |
-           ((uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, 1, -1, 0, RHO - 1) << (RHO + 1));
-    }
-    if (r == RHO - 1) {
-      dn = (uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, -1, 1, RHO - 1, 0) |
-           ((uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, 0, 1, 0, 0) << 1) |
-           ((uint64_t)ext_bit<RHO>(tiles, inv, ring, side, ux, uy, 0, 1, 1, 0) << 2);
-    }
+    if (r == 0) up = ((uint64_t)((halo >> 3) & 1u) << 1) | ((uint64_t)((halo >> 4) & 1u) << (RHO + 1));
+    if (r == RHO - 1)
+      dn = (uint64_t)((halo >> 5) & 1u) | ((uint64_t)((halo >> 6) & 1u) << 1) | ((uint64_t)((halo >> 7) & 1u) << 2);
     const uint32_t next = life_rule32(up, own, dn) & pm;
+
     uint8_t* gtile = out + (size_t)(oy + uy * RHO) * n + ox + ux * RHO;
     if constexpr (RHO == 32) {
       // lanes 2q, 2q+1 store the halves of rows q and q + 16 (whole sectors)
@@ -367,49 +408,54 @@ __global__ void __launch_bounds__(1024) ca_tma_kernel(const __grid_constant__ CU
 }
 
 template <int MODE, int LOG_RHO>
-cudaError_t go_diff(const Launch& L, const CUtensorMap& map, const float* in, float* out, float a, int* err,
+cudaError_t go_diff(const Launch& L, const CUtensorMap& map, const CUtensorMap& ring, float* out, float a, int* err,
                     cudaStream_t s) {
   auto* k = diffusion_tma_kernel<MODE, LOG_RHO>;
   cudaError_t e = allow_smem((const void*)k, L.smem);
   if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(map, in, out, a, L.geo, err);
+  k<<<L.grid, L.threads, L.smem, s>>>(map, ring, out, a, L.geo, err);
   return cudaGetLastError();
 }
 
 template <int MODE, int LOG_RHO>
-cudaError_t go_ca(const Launch& L, const CUtensorMap& map, const uint8_t* in, uint8_t* out, int* err,
+cudaError_t go_ca(const Launch& L, const CUtensorMap& map, const CUtensorMap& ring, uint8_t* out, int* err,
                   cudaStream_t s) {
   auto* k = ca_tma_kernel<MODE, LOG_RHO>;
   cudaError_t e = allow_smem((const void*)k, L.smem);
   if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(map, in, out, L.geo, err);
+  k<<<L.grid, L.threads, L.smem, s>>>(map, ring, out, L.geo, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_diffusion_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const float* in,
-                                 float* out, float a, int* err, cudaStream_t s) {
+// Ring cells staged per super-tile: 8 (uint8 automaton, Moore) or 4 (float32 diffusion).
+int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype) {
+  return TmaLayout(g, tile_bytes, dtype == 0 ? 8 : 4).total;
+}
+
+cudaError_t launch_diffusion_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map,
+                                 const CUtensorMap& ring, float* out, float a, int* err, cudaStream_t s) {
   switch (mode * 8 + log_rho) {
-    case 0 * 8 + 2: return go_diff<kLambda, 2>(L, map, in, out, a, err, s);
-    case 0 * 8 + 3: return go_diff<kLambda, 3>(L, map, in, out, a, err, s);
-    case 0 * 8 + 4: return go_diff<kLambda, 4>(L, map, in, out, a, err, s);
-    case 0 * 8 + 5: return go_diff<kLambda, 5>(L, map, in, out, a, err, s);
-    case 1 * 8 + 2: return go_diff<kBB, 2>(L, map, in, out, a, err, s);
-    case 1 * 8 + 3: return go_diff<kBB, 3>(L, map, in, out, a, err, s);
-    case 1 * 8 + 4: return go_diff<kBB, 4>(L, map, in, out, a, err, s);
-    case 1 * 8 + 5: return go_diff<kBB, 5>(L, map, in, out, a, err, s);
+    case 0 * 8 + 2: return go_diff<kLambda, 2>(L, map, ring, out, a, err, s);
+    case 0 * 8 + 3: return go_diff<kLambda, 3>(L, map, ring, out, a, err, s);
+    case 0 * 8 + 4: return go_diff<kLambda, 4>(L, map, ring, out, a, err, s);
+    case 0 * 8 + 5: return go_diff<kLambda, 5>(L, map, ring, out, a, err, s);
+    case 1 * 8 + 2: return go_diff<kBB, 2>(L, map, ring, out, a, err, s);
+    case 1 * 8 + 3: return go_diff<kBB, 3>(L, map, ring, out, a, err, s);
+    case 1 * 8 + 4: return go_diff<kBB, 4>(L, map, ring, out, a, err, s);
+    case 1 * 8 + 5: return go_diff<kBB, 5>(L, map, ring, out, a, err, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const uint8_t* in,
+cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const CUtensorMap& ring,
                           uint8_t* out, int* err, cudaStream_t s) {
   switch (mode * 8 + log_rho) {
-    case 0 * 8 + 4: return go_ca<kLambda, 4>(L, map, in, out, err, s);
-    case 0 * 8 + 5: return go_ca<kLambda, 5>(L, map, in, out, err, s);
-    case 1 * 8 + 4: return go_ca<kBB, 4>(L, map, in, out, err, s);
-    case 1 * 8 + 5: return go_ca<kBB, 5>(L, map, in, out, err, s);
+    case 0 * 8 + 4: return go_ca<kLambda, 4>(L, map, ring, out, err, s);
+    case 0 * 8 + 5: return go_ca<kLambda, 5>(L, map, ring, out, err, s);
+    case 1 * 8 + 4: return go_ca<kBB, 4>(L, map, ring, out, err, s);
+    case 1 * 8 + 5: return go_ca<kBB, 5>(L, map, ring, out, err, s);
     default: return cudaErrorInvalidValue;
   }
 }

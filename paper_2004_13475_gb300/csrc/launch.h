@@ -28,11 +28,12 @@ cudaError_t launch_reduce(int mode, int log_rho, int dtype, const Launch& L, con
 cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s);
 
 // TMA-staged step kernels (rho * element size >= 16 bytes; see k_tma.cu).
-cudaError_t launch_diffusion_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const float* in,
-                                 float* out, float a, int* err, cudaStream_t s);
-cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const uint8_t* in,
+// `map` has rho x rho boxes over the input array, `ring` 16-byte boxes of one row.
+cudaError_t launch_diffusion_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map,
+                                 const CUtensorMap& ring, float* out, float a, int* err, cudaStream_t s);
+cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensorMap& map, const CUtensorMap& ring,
                           uint8_t* out, int* err, cudaStream_t s);
-int tma_smem_bytes(const Geo& g, int tile_bytes);
+int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 
 // Dynamic shared memory above the 48 KB default needs an opt-in per kernel.
 cudaError_t allow_smem(const void* func, int bytes);
