@@ -110,9 +110,10 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   tma_ok = dtype == FRACTAL_U8 ? rho >= 16 : rho >= 4;
   tma = step;
   if (tma_ok) {
-    // one thread per tile row (uint8) or per float4 (float32), capped at the
-    // kernels' launch bounds (the update loop strides over the rest)
-    const int64_t items = dtype == FRACTAL_U8 ? (int64_t)g.tiles * rho : (int64_t)g.tiles * rho * (rho / 4);
+    // one thread per tile row (uint8) or per 4-column strip of a tile
+    // (float32), capped at the kernels' launch bounds (the update loop
+    // strides over the rest)
+    const int64_t items = dtype == FRACTAL_U8 ? (int64_t)g.tiles * rho : (int64_t)g.tiles * (rho / 4);
     const int cap = dtype == FRACTAL_U8 ? 512 : 256;
     int t = (int)((items + 31) / 32 * 32);
     if (t > cap) t = cap;

@@ -25,14 +25,15 @@ constexpr int kRingSlot = 128;  // bytes per ring box slot (the box itself is 16
 
 // Shared-memory layout of the TMA kernels; host and device compute it alike.
 struct TmaLayout {
-  int bar, sxy, tab, inv, ring, tiles, total;
+  int bar, sxy, tab, inv, halo, ring, tiles, total;
   __host__ __device__ TmaLayout(const Geo& g, int tile_bytes, int rings) {
     const int side = 1 << g.m;
     bar = 0;
     sxy = 8;
     tab = 16;
     inv = tab + ((g.tiles * 4 + 15) & ~15);
-    ring = (inv + side * side * 2 + 127) & ~127;
+    halo = inv + ((side * side * 2 + 15) & ~15);  // per tile: 4 floats + flag word, or 1 word of bits
+    ring = (halo + g.tiles * 20 + 127) & ~127;
     tiles = ring + rings * kRingSlot;
     total = tiles + g.tiles * tile_stride(tile_bytes);
   }
@@ -145,7 +146,7 @@ __device__ __forceinline__ void tma_issue(uint64_t* bar, const uint32_t* tab, un
 // ------------------------------------------------------------- diffusion ----
 
 template <int MODE, int LOG_RHO>
-__global__ void __launch_bounds__(256, 6) diffusion_tma_kernel(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(256, 4) diffusion_tma_kernel(const __grid_constant__ CUtensorMap tin,
                                                             const __grid_constant__ CUtensorMap tring,
                                                             float* __restrict__ out, float a, Geo g, int* err) {
   constexpr int RHO = 1 << LOG_RHO;                       // >= 4
@@ -175,103 +176,124 @@ __global__ void __launch_bounds__(256, 6) diffusion_tma_kernel(const __grid_cons
     return;
   }
 
-  // One float4 (4 cells of a tile row) per thread; consecutive threads take
-  // consecutive float4s of a tile, so the 8 lanes of a 128-bit shared-memory
-  // phase read 8 different bank groups and every store writes whole sectors.
-  const int items = g.tiles << LOG_Q;
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int c = it >> LOG_Q;
-    const int q = it & ((1 << LOG_Q) - 1);
+  // Halo pre-pass: the four cells outside each tile, (0,-1) (-1,0) (rho,0)
+  // (0,rho), from the neighbouring tile's corner cell or the super-tile ring;
+  // absent cells get value 0 and flag 0.
+  float* hv = reinterpret_cast<float*>(sm + L.halo);                     // [tiles][4]
+  uint32_t* hf = reinterpret_cast<uint32_t*>(sm + L.halo + g.tiles * 16);  // [tiles] flag bits
+  for (int t = threadIdx.x; t < g.tiles * 4; t += blockDim.x) {
+    const int c = t >> 2, k = t & 3;
     const uint32_t e = tab[c];
     const int ux = (int)(e & 0xffffu), uy = (int)(e >> 16);
-    const int ty = q / MBX, tx0 = (q % MBX) * 4;
-    const float* tile = tiles + c * TS;
-    const float* row = tile + ty * RHO + tx0;
+    int hx, hy;
+    vn_halo(k, RHO, hx, hy);
+    const int dx = hx < 0 ? -1 : (hx >= RHO ? 1 : 0), dy = hy < 0 ? -1 : (hy >= RHO ? 1 : 0);
+    const int vx = ux + dx, vy = uy + dy;
+    float v = 0.f;
+    bool f = false;
+    if (vx >= 0 && vx < side && vy >= 0 && vy < side) {
+      const int q = inv[vy * side + vx];
+      if (q >= 0) {
+        v = tiles[q * TS + (hy - dy * RHO) * RHO + (hx - dx * RHO)];
+        f = true;
+      }
+    } else {
+      // outside the super-tile: the super-tile's halo cell of the same index or no member
+      int rx, ry;
+      vn_halo(k, T, rx, ry);
+      const int lx = ux * RHO + hx, ly = uy * RHO + hy;
+      if (lx == rx && ly == ry) {
+        const int gx = ox + lx, gy = oy + ly;
+        f = is_member(gx, gy, n);
+        if (f) v = ring[k * (kRingSlot / 4) + gx - box_x<RB>(gx)];
+      }
+    }
+    hv[t] = v;
+    reinterpret_cast<uint8_t*>(hf)[t] = f ? 1 : 0;
+  }
+  __syncthreads();
 
-    const float4 cur = *reinterpret_cast<const float4*>(row);
-    float4 up = make_float4(0.f, 0.f, 0.f, 0.f), dn = up;
-    uint32_t mu = 0u, md = 0u;
-    if (ty > 0) {
-      up = *reinterpret_cast<const float4*>(row - RHO);
-      mu = row_pattern((uint32_t)(ty - 1)) >> tx0;
-    } else if (tx0 == 0) {
-      // (0,-1): bottom-left cell of the tile above, or the super-tile ring
-      if (uy > 0) {
-        const int qq = inv[(uy - 1) * side + ux];
-        if (qq >= 0) { up.x = tiles[qq * TS + (RHO - 1) * RHO]; mu = 1u; }
-      } else if (ux == 0) {
-        const int gx = ox, gy = oy - 1;
-        up.x = ring[0 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
-        mu = is_member(gx, gy, n) ? 1u : 0u;
+  // One thread per 4-column strip of a tile, walking all RHO rows; the S =
+  // RHO/4 strips of a tile are adjacent lanes (horizontal neighbours by
+  // shuffle).  Tiles start their walk at different rows so that the 8 lanes
+  // of a 128-bit shared-memory phase read 8 different bank groups.  Whole
+  // warps run every iteration (shuffles); padding lanes store nothing.
+  constexpr int S = RHO / 4;
+  constexpr int LOG_S = LOG_RHO - 2;
+  const int lane = threadIdx.x & 31;
+  const int strip = lane & (S - 1);
+  const int tx0 = strip * 4;
+  const int rot = (lane >> LOG_S) & ((8 >> LOG_S) > 1 ? (8 >> LOG_S) - 1 : 0) & (RHO - 1);
+  const int items = g.tiles * S;
+  const int items_padded = (items + 31) & ~31;
+  for (int it = threadIdx.x; it < items_padded; it += blockDim.x) {
+    const bool live = it < items;
+    const int c = live ? (it >> LOG_S) : 0;
+    const uint32_t e = tab[c];
+    const int ux = (int)(e & 0xffffu), uy = (int)(e >> 16);
+    const float* tile = tiles + c * TS;
+    const uint32_t hfl = reinterpret_cast<const uint32_t*>(hf)[c];  // byte k = flag of halo k
+    const float ev_up = hv[c * 4 + 0], ev_lf = hv[c * 4 + 1], ev_rt = hv[c * 4 + 2], ev_dn = hv[c * 4 + 3];
+    const bool ef_up = (hfl & 0xffu) != 0u, ef_lf = (hfl & 0xff00u) != 0u;
+    const bool ef_rt = (hfl & 0xff0000u) != 0u, ef_dn = (hfl & 0xff000000u) != 0u;
+    float* gtile = out + (size_t)(oy + uy * RHO) * n + ox + ux * RHO + tx0;
+#pragma unroll 2
+    for (int st = 0; st < RHO; ++st) {
+      const int ty = (st + rot) & (RHO - 1);
+      const float4 cur = *reinterpret_cast<const float4*>(tile + ty * RHO + tx0);
+      float4 up = *reinterpret_cast<const float4*>(tile + (ty > 0 ? ty - 1 : 0) * RHO + tx0);
+      float4 dn = *reinterpret_cast<const float4*>(tile + (ty < RHO - 1 ? ty + 1 : RHO - 1) * RHO + tx0);
+      const uint32_t pm = row_pattern((uint32_t)ty);
+      uint32_t mu, md;
+      if (ty > 0) {
+        mu = row_pattern((uint32_t)(ty - 1)) >> tx0;
+      } else {
+        up = make_float4(ev_up, 0.f, 0.f, 0.f);
+        mu = (strip == 0 && ef_up) ? 1u : 0u;
       }
-    }
-    if (ty < RHO - 1) {
-      dn = *reinterpret_cast<const float4*>(row + RHO);
-      md = row_pattern((uint32_t)(ty + 1)) >> tx0;
-    } else if (tx0 == 0) {
-      // (0,rho): top-left cell of the tile below, or the super-tile ring
-      if (uy + 1 < side) {
-        const int qq = inv[(uy + 1) * side + ux];
-        if (qq >= 0) { dn.x = tiles[qq * TS]; md = 1u; }
-      } else if (ux == 0) {
-        const int gx = ox, gy = oy + T;
-        dn.x = ring[3 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
-        md = is_member(gx, gy, n) ? 1u : 0u;
+      if (ty < RHO - 1) {
+        md = row_pattern((uint32_t)(ty + 1)) >> tx0;
+      } else {
+        dn = make_float4(ev_dn, 0.f, 0.f, 0.f);
+        md = (strip == 0 && ef_dn) ? 1u : 0u;
       }
-    }
-    const uint32_t pm = row_pattern((uint32_t)ty);
-    const uint32_t mm = pm >> tx0;
-    // left of column tx0 and right of column tx0+3
-    float lf = 0.f, rt = 0.f;
-    bool ml = false, mr = false;
-    if (tx0 > 0) {
-      lf = row[-1];
-      ml = (pm >> (tx0 - 1)) & 1u;
-    } else if (ty == 0) {
-      // (-1,0): top-right cell of the tile to the left, or the super-tile ring
-      if (ux > 0) {
-        const int qq = inv[uy * side + ux - 1];
-        if (qq >= 0) { lf = tiles[qq * TS + RHO - 1]; ml = true; }
-      } else if (uy == 0) {
-        const int gx = ox - 1, gy = oy;
-        lf = ring[1 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
-        ml = is_member(gx, gy, n);
+      const uint32_t mm = pm >> tx0;
+      // horizontal neighbours across strips
+      float lf = __shfl_up_sync(0xffffffffu, cur.w, 1, S);
+      float rt = __shfl_down_sync(0xffffffffu, cur.x, 1, S);
+      bool ml, mr;
+      if (strip > 0) {
+        ml = (pm >> (tx0 - 1)) & 1u;
+      } else {
+        lf = ev_lf;
+        ml = ty == 0 && ef_lf;
       }
-    }
-    if (tx0 + 4 < RHO) {
-      rt = row[4];
-      mr = (pm >> (tx0 + 4)) & 1u;
-    } else if (ty == 0) {
-      // (rho,0): top-left cell of the tile to the right, or the super-tile ring
-      if (ux + 1 < side) {
-        const int qq = inv[uy * side + ux + 1];
-        if (qq >= 0) { rt = tiles[qq * TS]; mr = true; }
-      } else if (uy == 0) {
-        const int gx = ox + T, gy = oy;
-        rt = ring[2 * (kRingSlot / 4) + gx - box_x<RB>(gx)];
-        mr = is_member(gx, gy, n);
+      if (strip < S - 1) {
+        mr = (pm >> (tx0 + 4)) & 1u;
+      } else {
+        rt = ev_rt;
+        mr = ty == 0 && ef_rt;
       }
-    }
-    const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
-    const float uv[4] = {up.x, up.y, up.z, up.w};
-    const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
-    float res[4];
+      const float cv[4] = {cur.x, cur.y, cur.z, cur.w};
+      const float uv[4] = {up.x, up.y, up.z, up.w};
+      const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+      float res[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float u = cv[i];
-      const bool hl = i == 0 ? ml : ((mm >> (i - 1)) & 1u) != 0u;
-      const bool hr = i == 3 ? mr : ((mm >> (i + 1)) & 1u) != 0u;
-      const float vl = i == 0 ? lf : cv[i > 0 ? i - 1 : 0];
-      const float vr = i == 3 ? rt : cv[i < 3 ? i + 1 : 0];
-      // N4 in the order up, left, right, down; absent neighbours carry no flux
-      float acc = ((mu >> i) & 1u) ? uv[i] - u : 0.0f;
-      acc += hl ? vl - u : 0.0f;
-      acc += hr ? vr - u : 0.0f;
-      acc += ((md >> i) & 1u) ? dv[i] - u : 0.0f;
-      res[i] = ((mm >> i) & 1u) ? fmaf(a, acc, u) : 0.0f;
+      for (int i = 0; i < 4; ++i) {
+        const float u = cv[i];
+        const bool hl = i == 0 ? ml : ((mm >> (i - 1)) & 1u) != 0u;
+        const bool hr = i == 3 ? mr : ((mm >> (i + 1)) & 1u) != 0u;
+        const float vl = i == 0 ? lf : cv[i > 0 ? i - 1 : 0];
+        const float vr = i == 3 ? rt : cv[i < 3 ? i + 1 : 0];
+        // N4 in the order up, left, right, down; absent neighbours carry no flux
+        float acc = ((mu >> i) & 1u) ? uv[i] - u : 0.0f;
+        acc += hl ? vl - u : 0.0f;
+        acc += hr ? vr - u : 0.0f;
+        acc += ((md >> i) & 1u) ? dv[i] - u : 0.0f;
+        res[i] = ((mm >> i) & 1u) ? fmaf(a, acc, u) : 0.0f;
+      }
+      if (live) *reinterpret_cast<float4*>(gtile + (size_t)ty * n) = make_float4(res[0], res[1], res[2], res[3]);
     }
-    *reinterpret_cast<float4*>(out + (size_t)(oy + uy * RHO + ty) * n + ox + ux * RHO + tx0) =
-        make_float4(res[0], res[1], res[2], res[3]);
   }
 }
 
@@ -324,13 +346,44 @@ __global__ void __launch_bounds__(512, 4) ca_tma_kernel(const __grid_constant__ 
     return;
   }
 
+  // Halo pre-pass: alive bit of each of the 8 Moore halo cells of every
+  // tile, (-1,0) (R,0) (R,1) (0,-1) (R,-1) (-1,R) (0,R) (1,R) with R = rho,
+  // from the neighbouring tile or the super-tile ring (absent cells: 0).
+  uint8_t* hb = sm + L.halo;  // [tiles][8]
+  for (int t = threadIdx.x; t < g.tiles * 8; t += blockDim.x) {
+    const int c = t >> 3, k = t & 7;
+    const uint32_t e = tab[c];
+    const int ux = (int)(e & 0xffffu), uy = (int)(e >> 16);
+    int hx, hy;
+    moore_halo(k, RHO, hx, hy);
+    const int dx = hx < 0 ? -1 : (hx >= RHO ? 1 : 0), dy = hy < 0 ? -1 : (hy >= RHO ? 1 : 0);
+    const int vx = ux + dx, vy = uy + dy;
+    uint8_t bit = 0;
+    if (vx >= 0 && vx < side && vy >= 0 && vy < side) {
+      const int q = inv[vy * side + vx];
+      if (q >= 0) bit = tiles[q * TILE + (hy - dy * RHO) * RHO + (hx - dx * RHO)] != 0;
+    } else {
+      // Outside the super-tile the cell is the super-tile's halo cell of the
+      // same index or no member at all (no other cell outside the
+      // super-tile neighbours one of its members).
+      int rx, ry;
+      moore_halo(k, T, rx, ry);
+      const int lx = ux * RHO + hx, ly = uy * RHO + hy;
+      if (lx == rx && ly == ry) {
+        const int gx = ox + lx, gy = oy + ly;
+        bit = is_member(gx, gy, n) && ring[k * kRingSlot + gx - box_x<RB>(gx)] != 0;
+      }
+    }
+    hb[t] = bit;
+  }
+  __syncthreads();
+
   // One lane per tile row; groups of RHO lanes are one tile.  The loop runs
-  // whole warps (the shuffles and ballots need every lane); padding lanes
-  // compute on tile 0 and store nothing.
+  // whole warps (the shuffles need every lane); padding lanes compute on tile
+  // 0 and store nothing.
   const int rows = g.tiles * RHO;
   const int rows_padded = (rows + 31) & ~31;
   const int lane = threadIdx.x & 31;
-  const int gl = lane & (RHO - 1);  // lane within the tile group
   for (int it = threadIdx.x; it < rows_padded; it += blockDim.x) {
     const bool live = it < rows;
     const int c = live ? it / RHO : 0;
@@ -338,33 +391,8 @@ __global__ void __launch_bounds__(512, 4) ca_tma_kernel(const __grid_constant__ 
     const uint32_t e = tab[c];
     const int ux = (int)(e & 0xffffu), uy = (int)(e >> 16);
     const uint8_t* tile = tiles + c * TILE;
-
-    // Halo bits: lane i < 8 of the group fetches halo cell i (relative to the
-    // tile: (-1,0) (R,0) (R,1) (0,-1) (R,-1) (-1,R) (0,R) (1,R), R = rho); a
-    // ballot hands all eight to every lane of the group.
-    uint32_t hb = 0;
-    if (gl < 8) {
-      int hx, hy;
-      moore_halo(gl, RHO, hx, hy);
-      const int dx = hx < 0 ? -1 : (hx >= RHO ? 1 : 0), dy = hy < 0 ? -1 : (hy >= RHO ? 1 : 0);
-      const int vx = ux + dx, vy = uy + dy;
-      if (vx >= 0 && vx < side && vy >= 0 && vy < side) {
-        const int q = inv[vy * side + vx];
-        if (q >= 0) hb = tiles[q * TILE + (hy - dy * RHO) * RHO + (hx - dx * RHO)] != 0;
-      } else {
-        // Outside the super-tile the cell is the super-tile's halo cell of the
-        // same index or no member at all (no other cell outside the
-        // super-tile neighbours one of its members).
-        int sx_, sy_;
-        moore_halo(gl, T, sx_, sy_);
-        const int lx = ux * RHO + hx, ly = uy * RHO + hy;
-        if (lx == sx_ && ly == sy_) {
-          const int gx = ox + lx, gy = oy + ly;
-          hb = is_member(gx, gy, n) && ring[gl * kRingSlot + gx - box_x<RB>(gx)] != 0;
-        }
-      }
-    }
-    const uint32_t halo = (__ballot_sync(0xffffffffu, hb != 0) >> (lane & ~(RHO - 1))) & 0xffu;
+    const uint2 hw = *reinterpret_cast<const uint2*>(hb + c * 8);
+    const uint32_t halo = nz4(hw.x) | (nz4(hw.y) << 4);
 
     // this row's bits; the two 16-byte halves are read in an order that
     // spreads a 128-bit shared-memory phase over all bank groups
