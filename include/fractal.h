@@ -41,6 +41,7 @@ extern "C" {
 #define FRACTAL_EINVAL (-1)  /* bad argument: level, rho, mode, dtype, pointer, alignment */
 #define FRACTAL_ENOMEM (-2)  /* host or device allocation failed */
 #define FRACTAL_ECUDA (-3)   /* a CUDA runtime call or kernel launch failed */
+#define FRACTAL_ETOOBIG (-4) /* fractal_reduce_noalloc: the launch needs more partials than its fixed array */
 
 /* Launch modes. */
 #define FRACTAL_LAMBDA 0     /* compact grid + lambda(omega) (Theorem 1) */
@@ -195,6 +196,32 @@ int fractal_reduce(fractal_plan_t plan, const void* dev_buf, int dtype, double* 
  */
 int fractal_reduce_async(fractal_plan_t plan, const void* dev_buf, int dtype, double* dev_out,
                          void* stream);
+
+/*
+ * fractal_reduce_noalloc -- the sum of fractal_reduce_async (lambda launch,
+ * same kernels, same result) for callers that cannot allocate: it takes no
+ * plan and calls no cudaMalloc, cudaFree or other allocating routine.  Such
+ * callers are, for example, code that runs while another allocator (a
+ * framework's caching allocator, a fixed memory pool) owns the device memory,
+ * and latency-bound loops that must not pay for, or synchronise on, an
+ * allocation.  There is no counterpart in the paper.
+ *
+ * Its scratch (one partial sum per CTA) is a fixed device array of
+ * FRACTAL_NOALLOC_MAX_PARTIALS doubles (512 KiB) built into the library;
+ * every GPU that loads the library holds it until the process exits.  Levels
+ * whose launch would need more partials are rejected with FRACTAL_ETOOBIG
+ * (k = 16 with rho = 1 is the only such case).  The array is shared by all
+ * calls: calls whose work overlaps on the GPU (different streams without
+ * ordering, or several host threads) race on it, so order them on one
+ * stream.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  k, rho and dtype as in fractal_map / fractal_reduce;
+ * dev_buf: n*n device array, 16-byte aligned; dev_out: device double that
+ * receives the sum.  Asynchronous on `stream`.  Errors: FRACTAL_EINVAL,
+ * FRACTAL_ETOOBIG, FRACTAL_ECUDA.
+ */
+#define FRACTAL_NOALLOC_MAX_PARTIALS 65536
+int fractal_reduce_noalloc(int k, int rho, const void* dev_buf, int dtype, double* dev_out, void* stream);
 
 /*
  * fractal_set_l2_fetch_granularity -- set the L2 fetch granularity hint of

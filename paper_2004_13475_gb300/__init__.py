@@ -20,6 +20,8 @@ FRACTAL_OK = 0
 FRACTAL_EINVAL = -1
 FRACTAL_ENOMEM = -2
 FRACTAL_ECUDA = -3
+FRACTAL_ETOOBIG = -4
+FRACTAL_NOALLOC_MAX_PARTIALS = 65536
 
 FRACTAL_LAMBDA = 0
 FRACTAL_BB = 1
@@ -35,7 +37,7 @@ EXPORTS = (
     "fractal_plan_get_info", "fractal_plan_set_cta_levels", "fractal_map_blocks",
     "fractal_map_write", "fractal_step_ca", "fractal_step_diffusion", "fractal_reduce",
     "fractal_reduce_async", "fractal_set_l2_fetch_granularity", "fractal_get_l2_fetch_granularity",
-    "fractal_plan_set_schedule", "fractal_plan_device_status",
+    "fractal_plan_set_schedule", "fractal_plan_device_status", "fractal_reduce_noalloc",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -99,6 +101,7 @@ def _load() -> ctypes.CDLL:
         "fractal_get_l2_fetch_granularity": (I, [ctypes.POINTER(I)]),
         "fractal_plan_set_schedule": (I, [P, I]),
         "fractal_plan_device_status": (I, [P, ctypes.POINTER(I)]),
+        "fractal_reduce_noalloc": (I, [I, I, VP, I, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +226,13 @@ def fractal_reduce(plan: Plan, buf, dtype: int, stream=None) -> float:
 def fractal_reduce_async(plan: Plan, buf, dtype: int, dev_out, stream=None) -> None:
     _check(_load().fractal_reduce_async(plan.handle, _ptr(buf), dtype, _ptr(dev_out), _stream(stream)),
            "fractal_reduce_async")
+
+
+def fractal_reduce_noalloc(k: int, rho: int, buf, dtype: int, dev_out, stream=None) -> None:
+    """Sum over the members into the device double `dev_out` without any allocation
+    (fixed scratch inside the library; see include/fractal.h)."""
+    _check(_load().fractal_reduce_noalloc(int(k), int(rho), _ptr(buf), int(dtype), _ptr(dev_out),
+                                          _stream(stream)), "fractal_reduce_noalloc")
 
 
 def fractal_set_l2_fetch_granularity(nbytes: int) -> None:

@@ -66,6 +66,17 @@ namespace {
 // least 16 bytes: float32 rho >= 4, uint8 rho >= 16).
 bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
                  bool& tma_ok) {
+  return plan_geometry(p.k, p.log_rho, p.mode, dtype, levels, step, aux, tma, tma_ok);
+}
+
+}  // namespace
+
+bool fractal::plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
+                   bool& tma_ok) {
+  struct {
+    int k, log_rho, rb, mode;
+    int32_t n;
+  } p{k, log_rho, k - log_rho, mode, 1 << k};
   if (levels < 0 || levels > p.rb || levels > kMaxLevelsPerCta) return false;
   const int R = p.rb - levels;
   const int rho = 1 << p.log_rho;
@@ -124,6 +135,24 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   return true;
 }
 
+int fractal::default_cta_levels(int k, int log_rho, int mode, int dtype) {
+  // Super-tile side: the TMA kernels (uint8 rho >= 16, float32 rho >= 4) keep
+  // the whole super-tile in flight, 256 uint8 / 128 float cells per side; the
+  // vector-load kernels stage an image of it, 128 uint8 / 64 float cells.
+  const int rb = k - log_rho;
+  const int rho = 1 << log_rho;
+  const bool tma = dtype == FRACTAL_U8 ? rho >= 16 : rho >= 4;
+  const int target = dtype == FRACTAL_U8 ? (tma ? 8 : 7) : (tma ? 7 : 6);
+  int m = target - log_rho;
+  if (m < 0) m = 0;
+  if (m > rb) m = rb;
+  if (m > kMaxLevelsPerCta) m = kMaxLevelsPerCta;
+  if (mode == kBB && rb - m > 15) m = rb - 15;
+  return m;
+}
+
+namespace {
+
 // Tensor map of an n x n array for bw x bh boxes (driver entry point).
 bool encode_box_map(CUtensorMap* map, const void* base, int n, int bw, int bh, int dtype) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -157,20 +186,7 @@ bool use_tma(const fractal_plan_s* p, int dtype) {
   return p->tma_ok[dtype] && p->sched != FRACTAL_SCHED_STAGED;
 }
 
-int default_levels(const fractal_plan_s& p, int dtype) {
-  // Super-tile side: the TMA kernels (uint8 rho >= 16, float32 rho >= 4) keep
-  // the whole super-tile in flight, 256 uint8 / 128 float cells per side; the
-  // vector-load kernels stage an image of it, 128 uint8 / 64 float cells.
-  const int rho = 1 << p.log_rho;
-  const bool tma = dtype == FRACTAL_U8 ? rho >= 16 : rho >= 4;
-  const int target = dtype == FRACTAL_U8 ? (tma ? 8 : 7) : (tma ? 7 : 6);
-  int m = target - p.log_rho;
-  if (m < 0) m = 0;
-  if (m > p.rb) m = p.rb;
-  if (m > kMaxLevelsPerCta) m = kMaxLevelsPerCta;
-  if (p.mode == kBB && p.rb - m > 15) m = p.rb - 15;
-  return m;
-}
+int default_levels(const fractal_plan_s& p, int dtype) { return default_cta_levels(p.k, p.log_rho, p.mode, dtype); }
 
 int ensure_partials(fractal_plan_s* p) {
   size_t need = 1;
@@ -203,6 +219,7 @@ const char* fractal_strerror(int status) {
     case FRACTAL_EINVAL: return "invalid argument";
     case FRACTAL_ENOMEM: return "out of memory";
     case FRACTAL_ECUDA: return "CUDA error";
+    case FRACTAL_ETOOBIG: return "launch needs more partial sums than the fixed scratch array holds";
     default: return "unknown status";
   }
 }

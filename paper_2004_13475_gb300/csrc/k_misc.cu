@@ -1,4 +1,8 @@
-// Map export, single write (SW) and reduction (RD) kernels (Sec. 6.2).
+// Map export, single write (SW) and reduction (RD) kernels (Sec. 6.2), and
+// the allocation-free variant of the reduction.
+#include <mutex>
+
+#include "../../include/fractal.h"
 #include "launch.h"
 
 namespace fractal {
@@ -291,4 +295,66 @@ cudaError_t launch_reduce(int mode, int log_rho, int dtype, const Launch& L, con
                          : rd_by_rho<kBB>(log_rho, dtype, L, in, partials, dev_out, s);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free reduce: the per-CTA partial sums live in this fixed device
+// array instead of plan-owned memory.  Every GPU that loads the library holds
+// it (512 KiB) until the process exits; all calls share it.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) double g_noalloc_partials[FRACTAL_NOALLOC_MAX_PARTIALS];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device.  The host-side name of
+// the array is not a device address, so it is resolved once per device, with
+// that device current, and cached.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace fractal
+
+extern "C" int fractal_reduce_noalloc(int k, int rho, const void* dev_buf, int dtype, double* dev_out,
+                                      void* stream) {
+  using namespace fractal;
+  if (k < 0 || k > FRACTAL_MAX_LEVEL || rho < 1 || rho > 32 || (rho & (rho - 1)) != 0 || rho > (1 << k))
+    return FRACTAL_EINVAL;
+  if (!dev_buf || !dev_out || (reinterpret_cast<uintptr_t>(dev_buf) & 15u) != 0) return FRACTAL_EINVAL;
+  if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
+  const int log_rho = ilog2c(rho);
+  // lambda launch; more tile levels per CTA until the partials fit the array
+  Launch step, aux, tma;
+  bool tma_ok = false;
+  int levels = default_cta_levels(k, log_rho, kLambda, dtype);
+  bool fits = false;
+  for (; levels <= 5 && levels <= k - log_rho; ++levels) {
+    if (!plan_geometry(k, log_rho, kLambda, dtype, levels, step, aux, tma, tma_ok)) continue;
+    if ((int64_t)aux.grid.x * aux.grid.y <= FRACTAL_NOALLOC_MAX_PARTIALS) {
+      fits = true;
+      break;
+    }
+  }
+  if (!fits) return FRACTAL_ETOOBIG;
+  void* partials = nullptr;
+  if (noalloc_scratch(&partials) != cudaSuccess) return FRACTAL_ECUDA;
+  cudaError_t e = launch_reduce(kLambda, log_rho, dtype, aux, dev_buf, partials, dev_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : FRACTAL_ECUDA;
+}

@@ -35,6 +35,12 @@ cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensor
                           uint8_t* out, int* err, cudaStream_t s);
 int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 
+// Launch geometry of the kernels for level k, tile side 2^log_rho, mode,
+// dtype and `levels` tile levels per CTA (false if it does not fit).
+bool plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
+                   bool& tma_ok);
+int default_cta_levels(int k, int log_rho, int mode, int dtype);
+
 // Dynamic shared memory above the 48 KB default needs an opt-in per kernel.
 cudaError_t allow_smem(const void* func, int bytes);
 
