@@ -204,11 +204,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--rho-ca", type=int, default=32)
-    ap.add_argument("--rho-diff", type=int, default=8)
+    ap.add_argument("--rho-ca", type=int, default=0, help="fix the automaton's rho (0: tune over 8, 16, 32)")
+    ap.add_argument("--rho-diff", type=int, default=0, help="fix the diffusion's rho (0: tune over 8, 16, 32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-detail", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner: use --rho-ca/--rho-diff (default 32/8) and --levels-ca/--levels-diff")
+    ap.add_argument("--levels-ca", type=int, default=-1, help="CTA tile levels of the automaton (--no-tune)")
+    ap.add_argument("--levels-diff", type=int, default=-1, help="CTA tile levels of the diffusion (--no-tune)")
     ap.add_argument("--profile", choices=["ca", "diffusion", "reduce", "sw"],
                     help="run only `--launches` launches of one kernel (for ncu captures)")
     ap.add_argument("--k", type=int, default=15, help="gasket level of a --profile run")
@@ -223,6 +227,9 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    if args.no_tune:
+        args.rho_ca = args.rho_ca or 32
+        args.rho_diff = args.rho_diff or 8
 
     if args.impl == "reference":
         run_reference(args, None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
@@ -257,17 +264,40 @@ def main():
         synth.device_fill(u_a.data_ptr(), synth.SYNTH_UNIFORM_F32, N, SEED + rank, stream=sptr)
 
     fill()
-    plans = {}
+    hbm, peak_kind = peaks()
 
-    def plan(rho, mode):
-        key = (rho, mode)
-        if key not in plans:
-            plans[key] = fr.fractal_map(K, rho, mode)
-        return plans[key]
+    # ---- autotune: for each workload and launch mode, every rho in {8, 16, 32}
+    # with its fastest staging and CTA shape; the step uses the best rho of
+    # each mode (the paper compares each approach at its best block size) ----
+    tuned = {}   # (workload, mode, rho) -> (plan, us)
+    for wl, dtype, src, scratch in (("ca", fr.FRACTAL_U8, ca_a, ca_b), ("diffusion", fr.FRACTAL_F32, u_a, u_b)):
+        for mode in (0, 1):
+            for rho in (8, 16, 32):
+                if args.rho_ca and wl == "ca" and rho != args.rho_ca:
+                    continue
+                if args.rho_diff and wl == "diffusion" and rho != args.rho_diff:
+                    continue
+                pl = fr.fractal_map(K, rho, mode)
+                if args.no_tune:
+                    lv = args.levels_ca if wl == "ca" else args.levels_diff
+                    if lv >= 0:
+                        fr.fractal_plan_set_cta_levels(pl, dtype, lv)
+                    us = 0.0
+                else:
+                    us = fr.fractal_plan_autotune(pl, dtype, src, scratch, 5, stream)
+                tuned[(wl, mode, rho)] = (pl, us)
+    best = {}
+    for wl in ("ca", "diffusion"):
+        for mode in (0, 1):
+            cands = [(us, rho) for (w, md, rho), (_, us) in tuned.items() if w == wl and md == mode]
+            best[(wl, mode)] = min(cands)[1]
+
+    def plan(wl, mode):
+        return tuned[(wl, mode, best[(wl, mode)])][0]
 
     def step(mode, ev=None):
         """One bench step; if ev is given, record events around the diffusion segments."""
-        pc, pd = plan(args.rho_ca, mode), plan(args.rho_diff, mode)
+        pc, pd = plan("ca", mode), plan("diffusion", mode)
         fr.fractal_step_ca(pc, ca_a, ca_b, CA_STEPS, stream)          # even: result back in ca_a
         cur, oth = u_a, u_b
         for seg in range(DIFF_STEPS // REDUCE_EVERY):
@@ -302,7 +332,7 @@ def main():
         torch.cuda.synchronize()
         return t0.elapsed_time(t1) / 1e3
 
-    hbm, peak_kind = peaks()
+    fill()   # the tuning runs read the start states only; refill anyway
 
     # ---- headline: lambda ----
     ev = ([], [])
@@ -318,10 +348,10 @@ def main():
     t_bb = max_over_ranks(dist, timed(1, max(1, args.steps // 2), 3))
     value_bb = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * max(1, args.steps // 2) / t_bb
 
-    info_d = plan(args.rho_diff, 0).info()
-    info_c = plan(args.rho_ca, 0).info()
-    tile_bytes_d = (args.rho_diff * 4) * args.rho_diff     # FP32 tile
-    alg_bytes_d = 2 * info_d["member_tiles"] * tile_bytes_d  # read + write every member tile once
+    info_d = plan("diffusion", 0).info()
+    info_c = plan("ca", 0).info()
+    rho_d, rho_c = info_d["rho"], info_c["rho"]
+    alg_bytes_d = 2 * info_d["member_tiles"] * rho_d * rho_d * 4  # read + write every member tile once
     achieved = alg_bytes_d / diff_launch_s / 1e9
 
     line = {
@@ -330,13 +360,14 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+f32",
         "data": "synthetic (SplitMix64-seeded Bernoulli(0.5) uint8 and U[0,1) FP32 states, generated on device)",
         "config": {
-            "workload": (f"gasket k=16 (65536x65536, 3^16 cells): {CA_STEPS} B3/S23 CA steps (uint8, rho={args.rho_ca})"
-                         f" + {DIFF_STEPS} FP32 diffusion steps (a={COEF}, rho={args.rho_diff}) with a global-sum"
+            "workload": (f"gasket k=16 (65536x65536, 3^16 cells): {CA_STEPS} B3/S23 CA steps (uint8)"
+                         f" + {DIFF_STEPS} FP32 diffusion steps (a={COEF}) with a global-sum"
                          f" reduce every {REDUCE_EVERY} + 1 count reduce"),
-            "map": "lambda", "k": K, "rho_ca": args.rho_ca, "rho_diffusion": args.rho_diff,
+            "map": "lambda", "k": K, "rho_ca": rho_c, "rho_diffusion": rho_d,
             "cta_levels_ca": info_c["cta_levels"][0], "cta_levels_diffusion": info_d["cta_levels"][1],
             "staging_ca": "tma" if info_c["tma"][0] else "vector loads",
             "staging_diffusion": "tma" if info_d["tma"][1] else "vector loads",
+            "tuning": "rho in {8,16,32}, staging and CTA levels chosen by fractal_plan_autotune",
             "l2": "inputs larger than L2 (4 GiB uint8 + 16 GiB FP32 per buffer)",
             "l2_fetch_granularity_bytes": l2_fetch,
             "parallelism": "replicas only" if world > 1 else "single GPU",
@@ -344,18 +375,21 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "roofline": {
-            "kernel": ("diffusion_tma_kernel" if info_d["tma"][1] else "diffusion_kernel") + f"<lambda, rho={args.rho_diff}>",
-            "bound": "hbm",
-            "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+            "kernel": ("diffusion_tma_kernel" if info_d["tma"][1] else "diffusion_kernel") + f"<lambda, rho={rho_d}>",
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None,
             "alg_bytes_per_launch": alg_bytes_d, "launch_us": diff_launch_s * 1e6,
         },
         "bb": {"value": value_bb, "ms_per_step": 1e3 * t_bb / max(1, args.steps // 2),
-               "speedup_lambda_over_bb": value / value_bb},
+               "speedup_lambda_over_bb": value / value_bb,
+               "rho_ca": best[("ca", 1)], "rho_diffusion": best[("diffusion", 1)]},
+        "tuned_step_us": {f"{wl}/{'lambda' if md == 0 else 'bb'}/rho{rho}": round(us, 2)
+                          for (wl, md, rho), (_, us) in sorted(tuned.items())},
     }
 
     if rank == 0 and not args.no_detail:
-        line["detail"] = kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm)
+        line["detail"] = kernel_detail(fr, torch, stream, lambda rho, mode: tuned[("diffusion", mode, rho)][0],
+                                       lambda rho, mode: tuned[("ca", mode, rho)][0], ca_a, ca_b, u_a, u_b, hbm)
 
     # ---- end to end through the C ABI with host buffers ----
     if not args.no_e2e:
@@ -367,8 +401,8 @@ def main():
                                 "sample": desc, "seconds": dt}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for p in plans.values():
-        p.close()
+    for pl, _ in tuned.values():
+        pl.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -408,8 +442,9 @@ def profile_run(args):
                       "launches": args.launches, "plan": plan.info()}))
 
 
-def kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm):
-    """Per-kernel times for rho in {8, 16, 32}, lambda and BB (launch-averaged)."""
+def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
+    """Per-kernel times for rho in {8, 16, 32}, lambda and BB, each with its
+    tuned staging and CTA shape (launch-averaged, CUDA events)."""
     out = {}
     reps = 10
 
@@ -427,40 +462,30 @@ def kernel_detail(fr, torch, stream, plan, ca_a, ca_b, u_a, u_b, hbm):
 
     for rho in (8, 16, 32):
         for mode, name in ((0, "lambda"), (1, "bb")):
-            p = plan(rho, mode)
-            inf = p.info()
-            tiles = inf["member_tiles"]
+            pc, pd = plan_c(rho, mode), plan_d(rho, mode)
+            ic, idf = pc.info(), pd.info()
+            tiles = ic["member_tiles"]
             rec = {}
-            t = clock(lambda: fr.fractal_step_ca(p, ca_a, ca_b, 2, stream)) / 2
+            t = clock(lambda: fr.fractal_step_ca(pc, ca_a, ca_b, 2, stream)) / 2
             b = 2 * tiles * rho * rho
             rec["ca"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
-                         "frac": b / t / 1e9 / hbm, "cta_levels": inf["cta_levels"][0]}
-            t = clock(lambda: fr.fractal_step_diffusion(p, u_a, u_b, COEF, 2, stream)) / 2
+                         "frac": b / t / 1e9 / hbm, "cta_levels": ic["cta_levels"][0], "tma": ic["tma"][0]}
+            t = clock(lambda: fr.fractal_step_diffusion(pd, u_a, u_b, COEF, 2, stream)) / 2
             b = 2 * tiles * rho * rho * 4
             rec["diffusion"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
-                                "frac": b / t / 1e9 / hbm, "cta_levels": inf["cta_levels"][1]}
-            # the same steps with the vector-load staging instead of TMA
-            fr.fractal_plan_set_schedule(p, fr.FRACTAL_SCHED_STAGED)
-            t = clock(lambda: fr.fractal_step_ca(p, ca_a, ca_b, 2, stream)) / 2
-            b = 2 * tiles * rho * rho
-            rec["ca_staged"] = {"us": t * 1e6, "frac": b / t / 1e9 / hbm}
-            t = clock(lambda: fr.fractal_step_diffusion(p, u_a, u_b, COEF, 2, stream)) / 2
-            b = 2 * tiles * rho * rho * 4
-            rec["diffusion_staged"] = {"us": t * 1e6, "frac": b / t / 1e9 / hbm}
-            fr.fractal_plan_set_schedule(p, fr.FRACTAL_SCHED_AUTO)
-            rec["tma"] = inf["tma"]
-            t = clock(lambda: fr.fractal_map_write(p, u_b, fr.FRACTAL_F32, 1.0, stream))
+                                "frac": b / t / 1e9 / hbm, "cta_levels": idf["cta_levels"][1], "tma": idf["tma"][1]}
+            t = clock(lambda: fr.fractal_map_write(pd, u_b, fr.FRACTAL_F32, 1.0, stream))
             b = tiles * rho * rho * 4
             rec["sw_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
-            t = clock(lambda: fr.fractal_map_write(p, ca_b, fr.FRACTAL_U8, 1.0, stream))
+            t = clock(lambda: fr.fractal_map_write(pc, ca_b, fr.FRACTAL_U8, 1.0, stream))
             b = tiles * rho * rho
             rec["sw_u8"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
             dev_out = torch.zeros(1, dtype=torch.float64, device="cuda")
-            t = clock(lambda: fr.fractal_reduce_async(p, u_a, fr.FRACTAL_F32, dev_out, stream))
+            t = clock(lambda: fr.fractal_reduce_async(pd, u_a, fr.FRACTAL_F32, dev_out, stream))
             b = tiles * rho * rho * 4
             rec["reduce_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
             out.setdefault(str(rho), {})[name] = rec
-        for kname in ("ca", "diffusion", "ca_staged", "diffusion_staged", "sw_f32", "sw_u8", "reduce_f32"):
+        for kname in ("ca", "diffusion", "sw_f32", "sw_u8", "reduce_f32"):
             lam = out[str(rho)]["lambda"][kname]["us"]
             bb = out[str(rho)]["bb"][kname]["us"]
             out[str(rho)].setdefault("speedup_lambda_over_bb", {})[kname] = bb / lam

@@ -125,6 +125,20 @@ int fractal_plan_set_cta_levels(fractal_plan_t plan, int dtype, int levels);
 int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
 
 /*
+ * fractal_plan_autotune -- time the plan's step kernel for dtype under every
+ * staging (TMA where it applies, vector loads) and every valid number of
+ * tile levels per CTA, and keep the fastest.  Each candidate runs `reps`
+ * timed single steps dev_in -> dev_scratch (after two untimed ones) on
+ * `stream`, which is synchronised.  dev_in is only read; dev_scratch is
+ * overwritten.  Both are n*n arrays of dtype, 16-byte aligned.  *best_us
+ * (nullable) receives the best mean step time in microseconds.  The tuned
+ * choice applies to this plan only (results never depend on it).  Errors:
+ * FRACTAL_EINVAL, FRACTAL_ENOMEM, FRACTAL_ECUDA.
+ */
+int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, void* dev_scratch, int reps,
+                          float* best_us, void* stream);
+
+/*
  * Device status word of the plan's TMA kernels: 0, or the first error a CTA
  * recorded (1: a tile copy did not complete within the wait limit; 2: the
  * drain after it also timed out).  The step kernels never trap or spin

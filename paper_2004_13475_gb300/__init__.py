@@ -38,6 +38,7 @@ EXPORTS = (
     "fractal_map_write", "fractal_step_ca", "fractal_step_diffusion", "fractal_reduce",
     "fractal_reduce_async", "fractal_set_l2_fetch_granularity", "fractal_get_l2_fetch_granularity",
     "fractal_plan_set_schedule", "fractal_plan_device_status", "fractal_reduce_noalloc",
+    "fractal_plan_autotune",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -102,6 +103,7 @@ def _load() -> ctypes.CDLL:
         "fractal_plan_set_schedule": (I, [P, I]),
         "fractal_plan_device_status": (I, [P, ctypes.POINTER(I)]),
         "fractal_reduce_noalloc": (I, [I, I, VP, I, VP, VP]),
+        "fractal_plan_autotune": (I, [P, I, VP, VP, I, ctypes.POINTER(F), VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +187,15 @@ def fractal_plan_set_cta_levels(plan: Plan, dtype: int, levels: int) -> None:
 
 def fractal_plan_set_schedule(plan: Plan, sched: int) -> None:
     _check(_load().fractal_plan_set_schedule(plan.handle, int(sched)), "fractal_plan_set_schedule")
+
+
+def fractal_plan_autotune(plan: Plan, dtype: int, dev_in, dev_scratch, reps: int = 5, stream=None) -> float:
+    """Pick the fastest staging and CTA shape for `dtype`; returns its mean step time (us).
+    dev_in is only read, dev_scratch is overwritten."""
+    best = ctypes.c_float(-1.0)
+    _check(_load().fractal_plan_autotune(plan.handle, int(dtype), _ptr(dev_in), _ptr(dev_scratch), int(reps),
+                                         ctypes.byref(best), _stream(stream)), "fractal_plan_autotune")
+    return best.value
 
 
 def fractal_plan_device_status(plan: Plan) -> int:

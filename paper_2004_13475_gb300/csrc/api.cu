@@ -334,6 +334,70 @@ int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
   return FRACTAL_OK;
 }
 
+int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void* dev_scratch, int reps,
+                          float* best_us, void* stream) {
+  if (check_plan(p) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) || !dev_in || !dev_scratch ||
+      dev_in == dev_scratch || !aligned16(dev_in) || !aligned16(dev_scratch) || reps < 1)
+    return FRACTAL_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return FRACTAL_ENOMEM;
+  }
+  const int old_sched = p->sched, old_m = p->m[dtype];
+  float best = -1.0f;
+  int best_sched = old_sched, best_m = old_m;
+  int status = FRACTAL_OK;
+  for (int sched = FRACTAL_SCHED_STAGED; sched <= FRACTAL_SCHED_TMA && status == FRACTAL_OK; ++sched) {
+    for (int m = 0; m <= kMaxLevelsPerCta && m <= p->rb; ++m) {
+      if (fractal_plan_set_cta_levels(p, dtype, m) != FRACTAL_OK) continue;
+      if (sched == FRACTAL_SCHED_TMA && !p->tma_ok[dtype]) continue;
+      p->sched = sched;
+      // one step in -> scratch per launch (two untimed, then `reps` timed)
+      auto run = [&](int times) -> int {
+        for (int i = 0; i < times; ++i) {
+          int r = dtype == FRACTAL_U8
+                      ? fractal_step_ca(p, (uint8_t*)dev_in, (uint8_t*)dev_scratch, 1, stream)
+                      : fractal_step_diffusion(p, (float*)dev_in, (float*)dev_scratch, 0.2f, 1, stream);
+          if (r != FRACTAL_OK) return r;
+        }
+        return FRACTAL_OK;
+      };
+      status = run(2);
+      if (status != FRACTAL_OK) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { status = cuda_fail(cudaGetLastError(), "autotune"); break; }
+      status = run(reps);
+      if (status != FRACTAL_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        status = cuda_fail(cudaGetLastError(), "autotune");
+        break;
+      }
+      const float us = 1000.f * ms / (float)reps;
+      if (best < 0.f || us < best) {
+        best = us;
+        best_sched = sched;
+        best_m = m;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // keep the winner (or restore the previous choice on failure)
+  if (status == FRACTAL_OK && best >= 0.f) {
+    fractal_plan_set_cta_levels(p, dtype, best_m);
+    p->sched = best_sched == FRACTAL_SCHED_TMA ? FRACTAL_SCHED_AUTO : FRACTAL_SCHED_STAGED;
+    if (best_us) *best_us = best;
+  } else {
+    fractal_plan_set_cta_levels(p, dtype, old_m);
+    p->sched = old_sched;
+  }
+  return status;
+}
+
 int fractal_plan_device_status(fractal_plan_t p, int* code) {
   if (!p || !code) return FRACTAL_EINVAL;
   int v = 0;

@@ -337,6 +337,31 @@ def test_runtime_validation(fr):
         fr.fractal_plan_set_schedule(tiny, fr.FRACTAL_SCHED_TMA)
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_autotune_keeps_results_exact(fr, dtype):
+    k, n = 12, 4096
+    plan = fr.fractal_map(k, 16)
+    if dtype == 0:
+        s0 = synth.bernoulli_u8(9, n)
+        src, scratch = dev_u8(s0), torch.zeros(n * n, dtype=torch.uint8, device="cuda")
+    else:
+        s0 = synth.uniform_f32(9, n)
+        src, scratch = dev_f32(s0), torch.zeros(n * n, dtype=torch.float32, device="cuda")
+    keep = src.clone()
+    us = fr.fractal_plan_autotune(plan, dtype, src, scratch, 3)
+    assert us > 0
+    assert torch.equal(src, keep)                      # the input is only read
+    mask = domain(k).mask
+    if dtype == 0:
+        got, _, _ = run_ca(fr, plan, s0, 3)
+        assert np.array_equal(got[mask], oracle.ca_run(s0, 3, domain(k))[mask])
+    else:
+        got = run_diffusion(fr, plan, s0, 3)
+        want = oracle.diffusion_run(s0.astype(np.float64), 3, 0.2, domain(k))
+        assert rel_err(got, want, mask)[0] <= 1e-6
+    assert fr.fractal_plan_device_status(plan) == 0
+
+
 def test_plan_reports_tma(fr):
     inf = fr.fractal_map(16, 8).info()
     assert inf["tma"] == [0, 1]          # uint8 rho = 8 stages by vector loads; float32 by TMA
