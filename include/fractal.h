@@ -78,6 +78,7 @@ typedef struct fractal_plan_info {
   int32_t smem_bytes[2]; /* per dtype: dynamic shared memory per CTA of a step kernel */
   int32_t tma[2];        /* per dtype: 1 if the step kernel stages tiles with TMA */
   int32_t sched;         /* FRACTAL_SCHED_* */
+  int32_t steps_per_launch[2]; /* per dtype: steps one launch advances (temporal fusion) */
 } fractal_plan_info;
 
 /* Human-readable text of a status code (static storage). */
@@ -126,10 +127,10 @@ int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
 
 /*
  * fractal_plan_autotune -- time the plan's step kernel for dtype under every
- * staging (TMA where it applies, vector loads) and every valid number of
- * tile levels per CTA, and keep the fastest.  Each candidate runs `reps`
- * timed single steps dev_in -> dev_scratch (after two untimed ones) on
- * `stream`, which is synchronised.  dev_in is only read; dev_scratch is
+ * staging (TMA where it applies, vector loads), every valid number of tile
+ * levels per CTA and, for float32, 1, 2, 4 or 8 steps per launch, and keep
+ * the fastest per step.  Each candidate runs `reps` timed launches dev_in ->
+ * dev_scratch (after two untimed ones) on `stream`, which is synchronised.  dev_in is only read; dev_scratch is
  * overwritten.  Both are n*n arrays of dtype, 16-byte aligned.  *best_us
  * (nullable) receives the best mean step time in microseconds.  The tuned
  * choice applies to this plan only (results never depend on it).  Errors:
@@ -137,6 +138,19 @@ int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
  */
 int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, void* dev_scratch, int reps,
                           float* best_us, void* stream);
+
+/*
+ * fractal_plan_set_steps_per_launch -- temporal fusion: each launch advances
+ * every member tile by up to `spl` (1..8) steps, staging the tile once and
+ * the few cells around the super-tile's three contacts with the rest of the
+ * gasket (margin boxes of 4 or 8 cells).  Results equal those of single-step
+ * launches up to FP32 rounding order; the buffer holding the result after
+ * `steps` steps is unchanged (dev_a for even, dev_b for odd).  spl = 1 turns
+ * fusion off.  Available for FRACTAL_F32 (diffusion) with rho >= 4 and a
+ * super-tile side of at least 8 (spl <= 4) or 16 cells.  Errors:
+ * FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan).
+ */
+int fractal_plan_set_steps_per_launch(fractal_plan_t plan, int dtype, int spl);
 
 /*
  * Device status word of the plan's TMA kernels: 0, or the first error a CTA

@@ -38,7 +38,7 @@ EXPORTS = (
     "fractal_map_write", "fractal_step_ca", "fractal_step_diffusion", "fractal_reduce",
     "fractal_reduce_async", "fractal_set_l2_fetch_granularity", "fractal_get_l2_fetch_granularity",
     "fractal_plan_set_schedule", "fractal_plan_device_status", "fractal_reduce_noalloc",
-    "fractal_plan_autotune",
+    "fractal_plan_autotune", "fractal_plan_set_steps_per_launch",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -63,6 +63,7 @@ class PlanInfo(ctypes.Structure):
         ("cta_levels", ctypes.c_int32 * 2), ("ctas", ctypes.c_int64 * 2),
         ("threads", ctypes.c_int32 * 2), ("smem_bytes", ctypes.c_int32 * 2),
         ("tma", ctypes.c_int32 * 2), ("sched", ctypes.c_int32),
+        ("steps_per_launch", ctypes.c_int32 * 2),
     ]
 
     def as_dict(self) -> dict:
@@ -104,6 +105,7 @@ def _load() -> ctypes.CDLL:
         "fractal_plan_device_status": (I, [P, ctypes.POINTER(I)]),
         "fractal_reduce_noalloc": (I, [I, I, VP, I, VP, VP]),
         "fractal_plan_autotune": (I, [P, I, VP, VP, I, ctypes.POINTER(F), VP]),
+        "fractal_plan_set_steps_per_launch": (I, [P, I, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +198,11 @@ def fractal_plan_autotune(plan: Plan, dtype: int, dev_in, dev_scratch, reps: int
     _check(_load().fractal_plan_autotune(plan.handle, int(dtype), _ptr(dev_in), _ptr(dev_scratch), int(reps),
                                          ctypes.byref(best), _stream(stream)), "fractal_plan_autotune")
     return best.value
+
+
+def fractal_plan_set_steps_per_launch(plan: Plan, dtype: int, spl: int) -> None:
+    _check(_load().fractal_plan_set_steps_per_launch(plan.handle, int(dtype), int(spl)),
+           "fractal_plan_set_steps_per_launch")
 
 
 def fractal_plan_device_status(plan: Plan) -> int:

@@ -51,6 +51,9 @@ struct fractal_plan_s {
   Launch tma[2];                // TMA-staged CA / diffusion kernels
   bool tma_ok[2] = {false, false};
   Launch aux[2];                // SW / reduce kernels (slot table only in shared memory)
+  int spl[2] = {1, 1};          // steps per launch (temporal fusion), per dtype
+  Launch fused[2];              // fused kernel launch for the plan's steps per launch
+  bool fused_ok[2] = {false, false};
   int* d_err = nullptr;         // device error word of the TMA kernels
   void* d_partials = nullptr;   // reduce scratch: one 8-byte partial per CTA
   size_t partials_cap = 0;      // elements
@@ -67,6 +70,19 @@ namespace {
 bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
                  bool& tma_ok) {
   return plan_geometry(p.k, p.log_rho, p.mode, dtype, levels, step, aux, tma, tma_ok);
+}
+
+// Launch of the temporally fused kernel for `spl` steps per launch (float32
+// diffusion, rho >= 4, super-tile side >= twice the margin); false if none.
+bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step, Launch& fused) {
+  if (dtype != FRACTAL_F32 || spl < 2 || spl > 8) return false;
+  const int rho = 1 << p.log_rho;
+  const int margin = fused_margin(spl);
+  if (rho < 4 || step.geo.T < 2 * margin) return false;
+  fused = step;
+  fused.threads = fused_threads(step.geo, rho, margin);
+  fused.smem = fused_smem_bytes(step.geo, margin);
+  return fused.smem <= kMaxSmem;
 }
 
 }  // namespace
@@ -297,6 +313,7 @@ int fractal_plan_get_info(fractal_plan_t p, fractal_plan_info* info) {
     info->threads[d] = L.threads;
     info->smem_bytes[d] = L.smem;
     info->tma[d] = use_tma(p, d) ? 1 : 0;
+    info->steps_per_launch[d] = p->spl[d] > 1 && p->fused_ok[d] ? p->spl[d] : 1;
   }
   info->sched = p->sched;
   return FRACTAL_OK;
@@ -315,6 +332,7 @@ int fractal_plan_set_cta_levels(fractal_plan_t p, int dtype, int levels) {
   p->tma[dtype] = t;
   p->tma_ok[dtype] = ok;
   p->m[dtype] = levels;
+  p->fused_ok[dtype] = p->spl[dtype] > 1 && make_fused(*p, dtype, p->spl[dtype], s, p->fused[dtype]);
   int st = ensure_partials(p);
   if (st != FRACTAL_OK) {
     p->step[dtype] = old_s;
@@ -324,6 +342,21 @@ int fractal_plan_set_cta_levels(fractal_plan_t p, int dtype, int levels) {
     p->m[dtype] = old_m;
   }
   return st;
+}
+
+int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
+  if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) || spl < 1 || spl > 8) return FRACTAL_EINVAL;
+  if (spl == 1) {
+    p->spl[dtype] = 1;
+    p->fused_ok[dtype] = false;
+    return FRACTAL_OK;
+  }
+  Launch f;
+  if (!make_fused(*p, dtype, spl, p->step[dtype], f)) return FRACTAL_EINVAL;
+  p->spl[dtype] = spl;
+  p->fused[dtype] = f;
+  p->fused_ok[dtype] = true;
+  return FRACTAL_OK;
 }
 
 int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
@@ -346,29 +379,41 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
     cudaGetLastError();
     return FRACTAL_ENOMEM;
   }
-  const int old_sched = p->sched, old_m = p->m[dtype];
+  const int old_sched = p->sched, old_m = p->m[dtype], old_spl = p->spl[dtype];
   float best = -1.0f;
-  int best_sched = old_sched, best_m = old_m;
+  int best_sched = old_sched, best_m = old_m, best_spl = old_spl;
   int status = FRACTAL_OK;
-  for (int sched = FRACTAL_SCHED_STAGED; sched <= FRACTAL_SCHED_TMA && status == FRACTAL_OK; ++sched) {
-    for (int m = 0; m <= kMaxLevelsPerCta && m <= p->rb; ++m) {
-      if (fractal_plan_set_cta_levels(p, dtype, m) != FRACTAL_OK) continue;
+  // One launch dev_in -> dev_scratch: a single step, or `spl` fused steps.
+  auto launch = [&](int spl) -> int {
+    if (spl > 1)
+      return launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[dtype], (const float*)dev_in,
+                                    (float*)dev_scratch, 0.2f, spl, st) == cudaSuccess
+                 ? FRACTAL_OK
+                 : cuda_fail(cudaGetLastError(), "autotune");
+    return dtype == FRACTAL_U8 ? fractal_step_ca(p, (uint8_t*)dev_in, (uint8_t*)dev_scratch, 1, stream)
+                               : fractal_step_diffusion(p, (float*)dev_in, (float*)dev_scratch, 0.2f, 1, stream);
+  };
+  for (int m = 0; m <= kMaxLevelsPerCta && m <= p->rb && status == FRACTAL_OK; ++m) {
+    if (fractal_plan_set_cta_levels(p, dtype, m) != FRACTAL_OK) continue;
+    // candidates: (schedule, steps per launch)
+    const int cands[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 2},
+                             {FRACTAL_SCHED_AUTO, 4}, {FRACTAL_SCHED_AUTO, 8}};
+    for (int ci = 0; ci < 5 && status == FRACTAL_OK; ++ci) {
+      const int sched = cands[ci][0], spl = cands[ci][1];
       if (sched == FRACTAL_SCHED_TMA && !p->tma_ok[dtype]) continue;
+      if (spl > 1) {
+        if (!make_fused(*p, dtype, spl, p->step[dtype], p->fused[dtype])) continue;
+        p->spl[dtype] = spl;
+        p->fused_ok[dtype] = true;
+      } else {
+        p->spl[dtype] = 1;
+        p->fused_ok[dtype] = false;
+      }
       p->sched = sched;
-      // one step in -> scratch per launch (two untimed, then `reps` timed)
-      auto run = [&](int times) -> int {
-        for (int i = 0; i < times; ++i) {
-          int r = dtype == FRACTAL_U8
-                      ? fractal_step_ca(p, (uint8_t*)dev_in, (uint8_t*)dev_scratch, 1, stream)
-                      : fractal_step_diffusion(p, (float*)dev_in, (float*)dev_scratch, 0.2f, 1, stream);
-          if (r != FRACTAL_OK) return r;
-        }
-        return FRACTAL_OK;
-      };
-      status = run(2);
+      for (int i = 0; i < 2 && status == FRACTAL_OK; ++i) status = launch(spl);
       if (status != FRACTAL_OK) break;
       if (cudaEventRecord(e0, st) != cudaSuccess) { status = cuda_fail(cudaGetLastError(), "autotune"); break; }
-      status = run(reps);
+      for (int i = 0; i < reps && status == FRACTAL_OK; ++i) status = launch(spl);
       if (status != FRACTAL_OK) break;
       float ms = 0.f;
       if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -376,25 +421,23 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
         status = cuda_fail(cudaGetLastError(), "autotune");
         break;
       }
-      const float us = 1000.f * ms / (float)reps;
+      const float us = 1000.f * ms / (float)(reps * spl);
       if (best < 0.f || us < best) {
         best = us;
         best_sched = sched;
         best_m = m;
+        best_spl = spl;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // keep the winner (or restore the previous choice on failure)
-  if (status == FRACTAL_OK && best >= 0.f) {
-    fractal_plan_set_cta_levels(p, dtype, best_m);
-    p->sched = best_sched == FRACTAL_SCHED_TMA ? FRACTAL_SCHED_AUTO : FRACTAL_SCHED_STAGED;
-    if (best_us) *best_us = best;
-  } else {
-    fractal_plan_set_cta_levels(p, dtype, old_m);
-    p->sched = old_sched;
-  }
+  const bool ok = status == FRACTAL_OK && best >= 0.f;
+  fractal_plan_set_cta_levels(p, dtype, ok ? best_m : old_m);
+  p->sched = ok ? (best_sched == FRACTAL_SCHED_STAGED ? FRACTAL_SCHED_STAGED : FRACTAL_SCHED_AUTO) : old_sched;
+  fractal_plan_set_steps_per_launch(p, dtype, ok ? best_spl : old_spl);
+  if (ok && best_us) *best_us = best;
   return status;
 }
 
@@ -454,6 +497,21 @@ int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int
   if (steps == 0) return FRACTAL_OK;
   const cudaStream_t st = (cudaStream_t)stream;
   float* buf[2] = {a, b};
+  if (p->spl[FRACTAL_F32] > 1 && p->fused_ok[FRACTAL_F32]) {
+    // L launches of at most spl steps; L has the parity of `steps` so that the
+    // result lands where the single-step ping-pong would leave it
+    const int spl = p->spl[FRACTAL_F32];
+    int L = (steps + spl - 1) / spl;
+    if ((L & 1) != (steps & 1)) ++L;
+    const int base = steps / L, extra = steps % L;
+    for (int i = 0; i < L; ++i) {
+      const int ns = base + (i < extra ? 1 : 0);
+      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[FRACTAL_F32],
+                                             buf[i & 1], buf[(i + 1) & 1], coef, ns, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+    }
+    return FRACTAL_OK;
+  }
   if (use_tma(p, FRACTAL_F32)) {
     CUtensorMap maps[2], rings[2];
     const int rho = 1 << p->log_rho;

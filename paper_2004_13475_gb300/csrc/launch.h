@@ -35,6 +35,13 @@ cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensor
                           uint8_t* out, int* err, cudaStream_t s);
 int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 
+// Temporally fused diffusion: nsteps (<= margin) steps per launch (k_fused.cu).
+cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
+                                   float a, int nsteps, cudaStream_t s);
+int fused_margin(int steps_per_launch);
+int fused_smem_bytes(const Geo& g, int margin);
+int fused_threads(const Geo& g, int rho, int margin);
+
 // Launch geometry of the kernels for level k, tile side 2^log_rho, mode,
 // dtype and `levels` tile levels per CTA (false if it does not fit).
 bool plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,

@@ -73,13 +73,16 @@ def k16_u8(fr):
     return n, a, b
 
 
+@pytest.mark.parametrize("tuned", [False, True])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("rho", [8, 16, 32])
-def test_k16_ca_100_steps(fr, k16_u8, rho, mode):
+def test_k16_ca_100_steps(fr, k16_u8, rho, mode, tuned):
     n, a, b = k16_u8
     steps = 100
     synth.device_fill(a.data_ptr(), synth.SYNTH_BERNOULLI_U8, n, SEED)
     plan = fr.fractal_map(16, rho, mode)
+    if tuned:               # what the benchmark runs: the autotuner's choice
+        fr.fractal_plan_autotune(plan, fr.FRACTAL_U8, a, b, 2)
     out = fr.fractal_step_ca(plan, a, b, steps).view(n, n)
     for (x0, y0, w, h) in windows(n, steps):
         dom = oracle.Domain.build(n, x0, y0, w, h)
@@ -112,13 +115,18 @@ def k16_f32(fr, k16_u8):
     return n, a, b
 
 
+@pytest.mark.parametrize("spl", [1, 8, "tuned"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("rho", [8, 16, 32])
-def test_k16_diffusion_200_steps(fr, k16_f32, rho, mode):
+def test_k16_diffusion_200_steps(fr, k16_f32, rho, mode, spl):
     n, a, b = k16_f32
     steps = 200
     synth.device_fill(a.data_ptr(), synth.SYNTH_UNIFORM_F32, n, SEED)
     plan = fr.fractal_map(16, rho, mode)
+    if spl == "tuned":      # what the benchmark runs: the autotuner's choice
+        fr.fractal_plan_autotune(plan, fr.FRACTAL_F32, a, b, 2)
+    elif spl > 1:
+        fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
     start = fr.fractal_reduce(plan, a, fr.FRACTAL_F32)
     out = fr.fractal_step_diffusion(plan, a, b, 0.2, steps).view(n, n)
     for (x0, y0, w, h) in windows(n, steps, inner=128)[:3]:
@@ -151,6 +159,7 @@ def test_k14_diffusion_1000_steps(fr, mode):
     b = torch.empty_like(a)
     synth.device_fill(a.data_ptr(), synth.SYNTH_UNIFORM_F32, n, SEED)
     plan = fr.fractal_map(14, 16, mode)
+    fr.fractal_plan_autotune(plan, fr.FRACTAL_F32, a, b, 2)
     sums = [fr.fractal_reduce(plan, a, fr.FRACTAL_F32)]
     cur, other = a, b
     for _ in range(10):
