@@ -219,6 +219,8 @@ def main():
     ap.add_argument("--rho", type=int, default=8, help="tile side of a --profile run")
     ap.add_argument("--mode", type=int, default=0, help="0 = lambda, 1 = BB (--profile)")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--spl", type=int, default=1, help="steps per launch of a --profile diffusion run")
+    ap.add_argument("--levels", type=int, default=-1, help="CTA tile levels of a --profile run")
     ap.add_argument("--l2-fetch", type=int, default=32, choices=[0, 32, 64, 128],
                     help="L2 fetch granularity hint for this process (0 = leave the driver's)")
     args = ap.parse_args()
@@ -313,8 +315,6 @@ def main():
         fr.fractal_reduce_async(pc, ca_a, fr.FRACTAL_U8, sums[4:5], stream)
         return cur
 
-    launches_per_step = CA_STEPS + DIFF_STEPS + 2 * (DIFF_STEPS // REDUCE_EVERY + 1)
-
     def timed(mode, steps, warmup, ev=None):
         for _ in range(warmup):
             step(mode)
@@ -341,7 +341,6 @@ def main():
     clocks = clk.summary()
     t_lam = max_over_ranks(dist, t_lam)
     diff_ms = sum(a.elapsed_time(b) for a, b in zip(*ev))
-    diff_launch_s = diff_ms / 1e3 / (args.steps * DIFF_STEPS)
     value = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * args.steps / t_lam
 
     # ---- same step with the bounding-box launch ----
@@ -351,8 +350,19 @@ def main():
     info_d = plan("diffusion", 0).info()
     info_c = plan("ca", 0).info()
     rho_d, rho_c = info_d["rho"], info_c["rho"]
+    spl_d = info_d["steps_per_launch"][1]
+    # launches per 100-step segment: ceil(100 / spl), made to have the parity of 100
+    lpseg = -(-REDUCE_EVERY // spl_d)
+    if lpseg % 2 != REDUCE_EVERY % 2:
+        lpseg += 1
+    diff_launches = lpseg * (DIFF_STEPS // REDUCE_EVERY) * args.steps
+    diff_launch_s = diff_ms / 1e3 / diff_launches
     alg_bytes_d = 2 * info_d["member_tiles"] * rho_d * rho_d * 4  # read + write every member tile once
+    if spl_d > 1:   # plus the contact boxes each fused launch reads (6 M^2/4 chunks of 16 B per super-tile)
+        margin = 4 if spl_d <= 4 else 8
+        alg_bytes_d += info_d["ctas"][1] * (6 * margin * margin // 4) * 16
     achieved = alg_bytes_d / diff_launch_s / 1e9
+    launches_per_step = CA_STEPS + diff_launches // args.steps + 2 * (DIFF_STEPS // REDUCE_EVERY + 1)
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -365,6 +375,7 @@ def main():
                          f" reduce every {REDUCE_EVERY} + 1 count reduce"),
             "map": "lambda", "k": K, "rho_ca": rho_c, "rho_diffusion": rho_d,
             "cta_levels_ca": info_c["cta_levels"][0], "cta_levels_diffusion": info_d["cta_levels"][1],
+            "steps_per_launch_diffusion": spl_d,
             "staging_ca": "tma" if info_c["tma"][0] else "vector loads",
             "staging_diffusion": "tma" if info_d["tma"][1] else "vector loads",
             "tuning": "rho in {8,16,32}, staging and CTA levels chosen by fractal_plan_autotune",
@@ -375,7 +386,9 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "roofline": {
-            "kernel": ("diffusion_tma_kernel" if info_d["tma"][1] else "diffusion_kernel") + f"<lambda, rho={rho_d}>",
+            "kernel": ("diffusion_fused_kernel" if spl_d > 1 else
+                       "diffusion_tma_kernel" if info_d["tma"][1] else "diffusion_kernel")
+                      + f"<lambda, rho={rho_d}>" + (f" x{spl_d} steps/launch" if spl_d > 1 else ""),
             "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None,
             "alg_bytes_per_launch": alg_bytes_d, "launch_us": diff_launch_s * 1e6,
@@ -418,6 +431,11 @@ def profile_run(args):
         fr.fractal_set_l2_fetch_granularity(args.l2_fetch)
     n = 1 << args.k
     plan = fr.fractal_map(args.k, args.rho, args.mode)
+    dt = fr.FRACTAL_U8 if args.profile == "ca" else fr.FRACTAL_F32
+    if args.levels >= 0:
+        fr.fractal_plan_set_cta_levels(plan, dt, args.levels)
+    if args.spl > 1:
+        fr.fractal_plan_set_steps_per_launch(plan, dt, args.spl)
     if args.profile == "ca":
         a = torch.empty(n * n, dtype=torch.uint8, device="cuda")
         synth.device_fill(a.data_ptr(), synth.SYNTH_BERNOULLI_U8, n, SEED)
@@ -431,8 +449,10 @@ def profile_run(args):
             fr.fractal_step_ca(plan, a, b, 1)
             a, b = b, a
         elif args.profile == "diffusion":
-            fr.fractal_step_diffusion(plan, a, b, COEF, 1)
-            a, b = b, a
+            # one launch of `spl` steps (spl even keeps the result in a)
+            fr.fractal_step_diffusion(plan, a, b, COEF, args.spl)
+            if args.spl % 2:
+                a, b = b, a
         elif args.profile == "reduce":
             fr.fractal_reduce_async(plan, a, fr.FRACTAL_F32, out)
         else:
@@ -470,10 +490,13 @@ def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
             b = 2 * tiles * rho * rho
             rec["ca"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
                          "frac": b / t / 1e9 / hbm, "cta_levels": ic["cta_levels"][0], "tma": ic["tma"][0]}
-            t = clock(lambda: fr.fractal_step_diffusion(pd, u_a, u_b, COEF, 2, stream)) / 2
+            t = clock(lambda: fr.fractal_step_diffusion(pd, u_a, u_b, COEF, 16, stream)) / 16
             b = 2 * tiles * rho * rho * 4
-            rec["diffusion"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
-                                "frac": b / t / 1e9 / hbm, "cta_levels": idf["cta_levels"][1], "tma": idf["tma"][1]}
+            spl = idf["steps_per_launch"][1]
+            rec["diffusion"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9,
+                                "steps_per_launch": spl, "alg_gbs_per_launch": b / (t * spl) / 1e9,
+                                "frac": b / (t * spl) / 1e9 / hbm, "cta_levels": idf["cta_levels"][1],
+                                "tma": idf["tma"][1]}
             t = clock(lambda: fr.fractal_map_write(pd, u_b, fr.FRACTAL_F32, 1.0, stream))
             b = tiles * rho * rho * 4
             rec["sw_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}

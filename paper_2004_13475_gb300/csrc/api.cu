@@ -82,7 +82,7 @@ bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step,
   fused = step;
   fused.threads = fused_threads(step.geo, rho, margin);
   fused.smem = fused_smem_bytes(step.geo, margin);
-  return fused.smem <= kMaxSmem;
+  return fused.threads > 0 && fused.smem <= kMaxSmem;
 }
 
 }  // namespace

@@ -64,22 +64,33 @@ __device__ __forceinline__ void fused_chunk(int it, int nt_chunks, const uint32_
 template <int M>
 __host__ __device__ constexpr int fused_box_chunks() { return (M / 4) * (M + M + 2 * M + 2 * M); }
 
+// Image pitch (floats): T + 2M, padded so that consecutive rows start in
+// different 32-byte bank groups (pitch mod 32 floats is 8 or 24); with 4
+// consecutive rows per 8-lane phase of 128-bit accesses, no bank conflicts.
+__host__ __device__ inline int fused_pitch(int T, int M) {
+  int P = T + 2 * M;
+  if ((P & 31) == 0 || (P & 31) == 16) P += 8;
+  return P;
+}
+
+constexpr int kFusedChunksPerThread = 3;
+
 template <int MODE, int LOG_RHO, int M>
-__global__ void __launch_bounds__(256) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
+__global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                               float a, int nsteps, Geo g) {
   constexpr int RHO = 1 << LOG_RHO;  // >= 4
+  constexpr int CT = kFusedChunksPerThread;
   extern __shared__ __align__(16) unsigned char sm[];
   int sx, sy;
   if (!cta_supertile<MODE>(g, sx, sy)) return;
   const int n = g.n, T = g.T;
-  const int P = T + 2 * M;            // image pitch (floats)
-  const int img = (P + 2) * P;        // floats per image: P rows plus a guard row above and below
+  const int P = fused_pitch(T, M);
+  const int img = (T + 2 * M + 2) * P;  // floats per image: rows plus a guard row above and below
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
   float* A = reinterpret_cast<float*>(sm + tab_words(g.tiles) * 4);
   float* B = A + img;
-  int8_t* D = reinterpret_cast<int8_t*>(B + img);  // per cell: member 4-degree, or -1 for a non-member
   // cell (lx, ly) of the image sits at (ly + M + 1) * P + lx + M; the guard
-  // rows keep the neighbour reads of the outermost chunks inside the image
+  // rows and the padding keep every neighbour read inside the image
   const int ox = sx * T, oy = sy * T;
 
   // member tiles of the super-tile (further unrolling, or BB discard)
@@ -102,65 +113,74 @@ __global__ void __launch_bounds__(256) diffusion_fused_kernel(const float* __res
     reinterpret_cast<float4*>(A)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
 
+  // This thread's chunks (4 cells of a row): their image offsets, and per
+  // cell the coefficient c (a for a member, 0 otherwise) and the member
+  // 4-degree d, so that a step is u' = u + c * (neighbour sum - d * u) for
+  // every cell alike (a non-member holds 0 and stays 0).
   const int nt_chunks = g.tiles * RHO * (RHO / 4);
   const int chunks = nt_chunks + fused_box_chunks<M>();
-  // stage: async copies of every in-array chunk; degree table
-  for (int it = threadIdx.x; it < chunks; it += blockDim.x) {
+  int off[CT];
+  uint32_t mk[CT];  // member bits of the chunk's 4 cells
+  float cf[CT][4], dg[CT][4];
+#pragma unroll
+  for (int k = 0; k < CT; ++k) {
+    const int it = threadIdx.x + k * (int)blockDim.x;
+    off[k] = -1;
+    mk[k] = 0u;
+    if (it >= chunks) continue;
     int lx, ly;
     fused_chunk<RHO, M>(it, nt_chunks, tab, T, lx, ly);
     const int gx0 = ox + lx, gy = oy + ly;
-    const int off = (ly + M + 1) * P + lx + M;
+    off[k] = (ly + M + 1) * P + lx + M;
     if ((unsigned)gy < (unsigned)n && (unsigned)gx0 < (unsigned)n)
-      cp_async16(A + off, in + (size_t)gy * n + gx0);
-    uint32_t dw = 0;
+      cp_async16(A + off[k], in + (size_t)gy * n + gx0);
+    // membership of the chunk's row and its neighbours, as bit masks
+    const uint32_t mc = chunk_members<4>(gx0, gy, n);
+    const uint32_t mu = chunk_members<4>(gx0, gy - 1, n);
+    const uint32_t md = chunk_members<4>(gx0, gy + 1, n);
+    const uint32_t ml = is_member(gx0 - 1, gy, n) ? 1u : 0u;
+    const uint32_t mr = is_member(gx0 + 4, gy, n) ? 1u : 0u;
+    const uint32_t row = ml | (mc << 1) | (mr << 5);  // bit j+1 = cell j of the chunk
+    mk[k] = mc;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int gx = gx0 + i;
-      int d = -1;
-      if (is_member(gx, gy, n))
-        d = (int)is_member(gx, gy - 1, n) + (int)is_member(gx - 1, gy, n) + (int)is_member(gx + 1, gy, n) +
-            (int)is_member(gx, gy + 1, n);
-      dw |= (uint32_t)(uint8_t)(int8_t)d << (8 * i);
+      const uint32_t deg = ((mu >> i) & 1u) + ((md >> i) & 1u) + ((row >> i) & 1u) + ((row >> (i + 2)) & 1u);
+      const bool mem = (mc >> i) & 1u;
+      cf[k][i] = mem ? a : 0.0f;
+      dg[k][i] = mem ? (float)deg : 0.0f;
     }
-    *reinterpret_cast<uint32_t*>(D + off - P) = dw;
   }
   cp_async_wait_all();
   __syncthreads();
   // non-member cells of staged chunks -> 0, so that neighbour sums need no masks
-  for (int it = threadIdx.x; it < chunks; it += blockDim.x) {
-    int lx, ly;
-    fused_chunk<RHO, M>(it, nt_chunks, tab, T, lx, ly);
-    const int off = (ly + M + 1) * P + lx + M;
-    const uint32_t dw = *reinterpret_cast<const uint32_t*>(D + off - P);
-    float4 v = *reinterpret_cast<const float4*>(A + off);
-    v.x = (dw & 0x80u) ? 0.f : v.x;
-    v.y = (dw & 0x8000u) ? 0.f : v.y;
-    v.z = (dw & 0x800000u) ? 0.f : v.z;
-    v.w = (dw & 0x80000000u) ? 0.f : v.w;
-    *reinterpret_cast<float4*>(A + off) = v;
+#pragma unroll
+  for (int k = 0; k < CT; ++k) {
+    if (off[k] < 0) continue;
+    float4 v = *reinterpret_cast<const float4*>(A + off[k]);
+    v.x = (mk[k] & 1u) ? v.x : 0.f;
+    v.y = (mk[k] & 2u) ? v.y : 0.f;
+    v.z = (mk[k] & 4u) ? v.z : 0.f;
+    v.w = (mk[k] & 8u) ? v.w : 0.f;
+    *reinterpret_cast<float4*>(A + off[k]) = v;
   }
   __syncthreads();
 
-  // nsteps updates A -> B -> A ...:  u' = u + a * (sum of member neighbours - deg * u)
+  // nsteps updates A -> B -> A ...
   for (int t = 0; t < nsteps; ++t) {
-    for (int it = threadIdx.x; it < chunks; it += blockDim.x) {
-      int lx, ly;
-      fused_chunk<RHO, M>(it, nt_chunks, tab, T, lx, ly);
-      const int off = (ly + M + 1) * P + lx + M;
-      const float4 c = *reinterpret_cast<const float4*>(A + off);
-      const float4 u = *reinterpret_cast<const float4*>(A + off - P);
-      const float4 d = *reinterpret_cast<const float4*>(A + off + P);
-      const float l = A[off - 1], r = A[off + 4];
-      const uint32_t dw = *reinterpret_cast<const uint32_t*>(D + off - P);
-      const float cv[4] = {c.x, c.y, c.z, c.w};
-      const float nb[4] = {u.x + d.x + l + c.y, u.y + d.y + c.x + c.z, u.z + d.z + c.y + c.w, u.w + d.w + c.z + r};
-      float res[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int deg = (int)(int8_t)(dw >> (8 * i));
-        res[i] = deg >= 0 ? fmaf(a, fmaf(-(float)deg, cv[i], nb[i]), cv[i]) : 0.f;
-      }
-      *reinterpret_cast<float4*>(B + off) = make_float4(res[0], res[1], res[2], res[3]);
+    for (int k = 0; k < CT; ++k) {
+      if (off[k] < 0) continue;
+      const float* p = A + off[k];
+      const float4 c = *reinterpret_cast<const float4*>(p);
+      const float4 u = *reinterpret_cast<const float4*>(p - P);
+      const float4 d = *reinterpret_cast<const float4*>(p + P);
+      const float l = p[-1], r = p[4];
+      float4 o;
+      o.x = fmaf(cf[k][0], fmaf(-dg[k][0], c.x, (u.x + d.x) + (l + c.y)), c.x);
+      o.y = fmaf(cf[k][1], fmaf(-dg[k][1], c.y, (u.y + d.y) + (c.x + c.z)), c.y);
+      o.z = fmaf(cf[k][2], fmaf(-dg[k][2], c.z, (u.z + d.z) + (c.y + c.w)), c.z);
+      o.w = fmaf(cf[k][3], fmaf(-dg[k][3], c.w, (u.w + d.w) + (c.z + r)), c.w);
+      *reinterpret_cast<float4*>(B + off[k]) = o;
     }
     __syncthreads();
     float* tmp = A;
@@ -168,12 +188,13 @@ __global__ void __launch_bounds__(256) diffusion_fused_kernel(const float* __res
     B = tmp;
   }
 
-  // write back the member tiles
-  for (int it = threadIdx.x; it < nt_chunks; it += blockDim.x) {
-    int lx, ly;
-    fused_chunk<RHO, M>(it, nt_chunks, tab, T, lx, ly);
-    const int off = (ly + M + 1) * P + lx + M;
-    *reinterpret_cast<float4*>(out + (size_t)(oy + ly) * n + ox + lx) = *reinterpret_cast<const float4*>(A + off);
+  // write back the member tiles (the first nt_chunks chunks)
+#pragma unroll
+  for (int k = 0; k < CT; ++k) {
+    const int it = threadIdx.x + k * (int)blockDim.x;
+    if (off[k] < 0 || it >= nt_chunks) continue;
+    const int lx = off[k] % P - M, ly = off[k] / P - M - 1;
+    *reinterpret_cast<float4*>(out + (size_t)(oy + ly) * n + ox + lx) = *reinterpret_cast<const float4*>(A + off[k]);
   }
 }
 
@@ -202,14 +223,17 @@ cudaError_t by_rho(int log_rho, const Launch& L, const float* in, float* out, fl
 int fused_margin(int steps_per_launch) { return steps_per_launch <= 4 ? 4 : 8; }
 
 int fused_smem_bytes(const Geo& g, int margin) {
-  const int P = g.T + 2 * margin;
-  return tab_words(g.tiles) * 4 + 2 * (P + 2) * P * 4 + P * P;
+  const int P = fused_pitch(g.T, margin);
+  return tab_words(g.tiles) * 4 + 2 * (g.T + 2 * margin + 2) * P * 4;
 }
 
+// Threads of a fused launch: every chunk owned by one thread, at most
+// kFusedChunksPerThread each; 0 if that needs more than 512 threads.
 int fused_threads(const Geo& g, int rho, int margin) {
   const int chunks = g.tiles * rho * (rho / 4) + (margin / 4) * 6 * margin;
-  int t = ((chunks + 1) / 2 + 31) / 32 * 32;
-  return t < 32 ? 32 : (t > 256 ? 256 : t);
+  int t = ((chunks + kFusedChunksPerThread - 1) / kFusedChunksPerThread + 31) / 32 * 32;
+  if (t < 32) t = 32;
+  return t > 512 ? 0 : t;
 }
 
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
