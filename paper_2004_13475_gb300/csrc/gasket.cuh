@@ -71,8 +71,9 @@ __device__ __forceinline__ uint32_t low_bits() {
   return W >= 32 ? 0xffffffffu : ((1u << W) - 1u);
 }
 
-// Membership bits of the W cells (gx0 .. gx0+W-1, gy); gx0 is a multiple of W
-// inside the array, so (gx0 + i) & gy == (gx0 & gy) | (i & gy).
+// Membership bits of the W cells (gx0 .. gx0+W-1, gy); gx0 must be a
+// multiple of W inside the array (callers check), so
+// (gx0 + i) & gy == (gx0 & gy) | (i & gy).
 template <int W>
 __device__ __forceinline__ uint32_t chunk_members(int gx0, int gy, int n) {
   if ((unsigned)gy >= (unsigned)n || (gx0 & gy) != 0) return 0u;

@@ -134,10 +134,12 @@ __global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __res
     off[k] = (ly + M + 1) * P + lx + M;
     if ((unsigned)gy < (unsigned)n && (unsigned)gx0 < (unsigned)n)
       cp_async16(A + off[k], in + (size_t)gy * n + gx0);
-    // membership of the chunk's row and its neighbours, as bit masks
-    const uint32_t mc = chunk_members<4>(gx0, gy, n);
-    const uint32_t mu = chunk_members<4>(gx0, gy - 1, n);
-    const uint32_t md = chunk_members<4>(gx0, gy + 1, n);
+    // membership of the chunk's row and its neighbours, as bit masks (box
+    // chunks may lie left of or beyond the array: no members there)
+    const bool inx = (unsigned)gx0 < (unsigned)n;
+    const uint32_t mc = inx ? chunk_members<4>(gx0, gy, n) : 0u;
+    const uint32_t mu = inx ? chunk_members<4>(gx0, gy - 1, n) : 0u;
+    const uint32_t md = inx ? chunk_members<4>(gx0, gy + 1, n) : 0u;
     const uint32_t ml = is_member(gx0 - 1, gy, n) ? 1u : 0u;
     const uint32_t mr = is_member(gx0 + 4, gy, n) ? 1u : 0u;
     const uint32_t row = ml | (mc << 1) | (mr << 5);  // bit j+1 = cell j of the chunk

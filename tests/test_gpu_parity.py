@@ -245,6 +245,18 @@ def test_diffusion_fused_1000_steps(fr, mode):
     assert err <= 1e-4, (err, raw)
 
 
+@pytest.mark.parametrize("spl", [1, 4, 8])
+def test_diffusion_zero_coefficient_is_identity(fr, spl):
+    k, n = 9, 512
+    plan = fr.fractal_map(k, 8)
+    if spl > 1:
+        fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
+    u0 = synth.uniform_f32(4, n)
+    got = run_diffusion(fr, plan, u0, 10, a=0.0)
+    mask = domain(k).mask
+    assert np.array_equal(got[mask], u0[mask])
+
+
 def test_fused_needs_room(fr):
     with pytest.raises(fr.FractalError):
         fr.fractal_plan_set_steps_per_launch(fr.fractal_map(3, 4), fr.FRACTAL_F32, 8)   # super-tile < 16
