@@ -73,18 +73,30 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
 }
 
 // Launch of the temporally fused kernel for `spl` steps per launch (float32
-// diffusion, rho >= 4, super-tile side >= twice the margin); false if none.
+// diffusion, rho >= 4, super-tile side >= twice the margin); the fused kernel
+// keeps every chunk of its super-tile in registers of one thread, so it may
+// take fewer tile levels per CTA than the plan's `step`.  False if none fits.
 bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step, Launch& fused) {
   if (dtype != FRACTAL_F32 || spl < 2 || spl > 8) return false;
   const int rho = 1 << p.log_rho;
   const int margin = fused_margin(spl);
-  if (rho < 4 || step.geo.T < 2 * margin) return false;
-  fused = step;
-  fused.threads = fused_threads(step.geo, rho, margin);
-  fused.smem = fused_smem_bytes(step.geo, margin);
-  return fused.threads > 0 && fused.smem <= kMaxSmem;
+  if (rho < 4) return false;
+  for (int m = step.geo.m; m >= 0; --m) {
+    Launch st, aux, tma;
+    bool tok = false;
+    if (!plan_geometry(p.k, p.log_rho, p.mode, dtype, m, st, aux, tma, tok)) continue;
+    if (st.geo.T < 2 * margin) break;
+    const int threads = fused_threads(st.geo, rho, margin);
+    const int smem = fused_smem_bytes(st.geo, margin);
+    if (threads > 0 && smem <= kMaxSmem) {
+      fused = st;
+      fused.threads = threads;
+      fused.smem = smem;
+      return true;
+    }
+  }
+  return false;
 }
-
 }  // namespace
 
 bool fractal::plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
@@ -307,13 +319,15 @@ int fractal_plan_get_info(fractal_plan_t p, fractal_plan_info* info) {
   info->member_tiles = ipow(3, p->rb);
   info->members = ipow(3, p->k);
   for (int d = 0; d < 2; ++d) {
-    info->cta_levels[d] = p->m[d];
-    info->ctas[d] = (int64_t)p->step[d].grid.x * p->step[d].grid.y;
-    const Launch& L = use_tma(p, d) ? p->tma[d] : p->step[d];
+    // the kernel a step call launches: fused, TMA-staged or vector-staged
+    const bool fused = p->spl[d] > 1 && p->fused_ok[d];
+    const Launch& L = fused ? p->fused[d] : (use_tma(p, d) ? p->tma[d] : p->step[d]);
+    info->cta_levels[d] = L.geo.m;
+    info->ctas[d] = (int64_t)L.grid.x * L.grid.y;
     info->threads[d] = L.threads;
     info->smem_bytes[d] = L.smem;
-    info->tma[d] = use_tma(p, d) ? 1 : 0;
-    info->steps_per_launch[d] = p->spl[d] > 1 && p->fused_ok[d] ? p->spl[d] : 1;
+    info->tma[d] = !fused && use_tma(p, d) ? 1 : 0;
+    info->steps_per_launch[d] = fused ? p->spl[d] : 1;
   }
   info->sched = p->sched;
   return FRACTAL_OK;

@@ -73,7 +73,7 @@ __host__ __device__ inline int fused_pitch(int T, int M) {
   return P;
 }
 
-constexpr int kFusedChunksPerThread = 3;
+constexpr int kFusedChunksPerThread = 4;
 
 template <int MODE, int LOG_RHO, int M>
 __global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
