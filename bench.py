@@ -213,13 +213,17 @@ def main():
                     help="skip the autotuner: use --rho-ca/--rho-diff (default 32/8) and --levels-ca/--levels-diff")
     ap.add_argument("--levels-ca", type=int, default=-1, help="CTA tile levels of the automaton (--no-tune)")
     ap.add_argument("--levels-diff", type=int, default=-1, help="CTA tile levels of the diffusion (--no-tune)")
+    ap.add_argument("--spl-ca", type=int, default=1, help="automaton steps per launch (--no-tune)")
+    ap.add_argument("--spl-diff", type=int, default=1, help="diffusion steps per launch (--no-tune)")
+    ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box run of the step")
     ap.add_argument("--profile", choices=["ca", "diffusion", "reduce", "sw"],
                     help="run only `--launches` launches of one kernel (for ncu captures)")
     ap.add_argument("--k", type=int, default=15, help="gasket level of a --profile run")
     ap.add_argument("--rho", type=int, default=8, help="tile side of a --profile run")
     ap.add_argument("--mode", type=int, default=0, help="0 = lambda, 1 = BB (--profile)")
     ap.add_argument("--launches", type=int, default=3)
-    ap.add_argument("--spl", type=int, default=1, help="steps per launch of a --profile diffusion run")
+    ap.add_argument("--spl", type=int, default=1,
+                    help="steps per launch of a --profile ca/diffusion run (each repetition is 2 launches)")
     ap.add_argument("--levels", type=int, default=-1, help="CTA tile levels of a --profile run")
     ap.add_argument("--l2-fetch", type=int, default=32, choices=[0, 32, 64, 128],
                     help="L2 fetch granularity hint for this process (0 = leave the driver's)")
@@ -284,6 +288,9 @@ def main():
                     lv = args.levels_ca if wl == "ca" else args.levels_diff
                     if lv >= 0:
                         fr.fractal_plan_set_cta_levels(pl, dtype, lv)
+                    spl = args.spl_ca if wl == "ca" else args.spl_diff
+                    if spl > 1:
+                        fr.fractal_plan_set_steps_per_launch(pl, dtype, spl)
                     us = 0.0
                 else:
                     us = fr.fractal_plan_autotune(pl, dtype, src, scratch, 5, stream)
@@ -297,19 +304,24 @@ def main():
     def plan(wl, mode):
         return tuned[(wl, mode, best[(wl, mode)])][0]
 
+    def mark(ev, key):
+        if ev is not None:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            ev.setdefault(key, []).append(e)
+
     def step(mode, ev=None):
-        """One bench step; if ev is given, record events around the diffusion segments."""
+        """One bench step; if ev (a dict) is given, record events around the
+        automaton run and the diffusion segments."""
         pc, pd = plan("ca", mode), plan("diffusion", mode)
+        mark(ev, "ca0")
         fr.fractal_step_ca(pc, ca_a, ca_b, CA_STEPS, stream)          # even: result back in ca_a
+        mark(ev, "ca1")
         cur, oth = u_a, u_b
         for seg in range(DIFF_STEPS // REDUCE_EVERY):
-            if ev is not None:
-                ev[0].append(torch.cuda.Event(enable_timing=True))
-                ev[1].append(torch.cuda.Event(enable_timing=True))
-                ev[0][-1].record(stream)
+            mark(ev, "d0")
             cur = fr.fractal_step_diffusion(pd, cur, oth, COEF, REDUCE_EVERY, stream)
-            if ev is not None:
-                ev[1][-1].record(stream)
+            mark(ev, "d1")
             oth = u_b if cur is u_a else u_a
             fr.fractal_reduce_async(pd, cur, fr.FRACTAL_F32, sums[seg:seg + 1], stream)
         fr.fractal_reduce_async(pc, ca_a, fr.FRACTAL_U8, sums[4:5], stream)
@@ -335,34 +347,44 @@ def main():
     fill()   # the tuning runs read the start states only; refill anyway
 
     # ---- headline: lambda ----
-    ev = ([], [])
+    ev = {}
     with Clocks(local) as clk:
         t_lam = timed(0, args.steps, args.warmup, ev)
     clocks = clk.summary()
     t_lam = max_over_ranks(dist, t_lam)
-    diff_ms = sum(a.elapsed_time(b) for a, b in zip(*ev))
+    diff_ms = sum(a.elapsed_time(b) for a, b in zip(ev["d0"], ev["d1"]))
+    ca_ms = sum(a.elapsed_time(b) for a, b in zip(ev["ca0"], ev["ca1"]))
     value = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * args.steps / t_lam
 
     # ---- same step with the bounding-box launch ----
-    t_bb = max_over_ranks(dist, timed(1, max(1, args.steps // 2), 3))
-    value_bb = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * max(1, args.steps // 2) / t_bb
+    if args.no_bb:
+        t_bb = value_bb = None
+    else:
+        t_bb = max_over_ranks(dist, timed(1, max(1, args.steps // 2), 3))
+        value_bb = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * max(1, args.steps // 2) / t_bb
 
     info_d = plan("diffusion", 0).info()
     info_c = plan("ca", 0).info()
     rho_d, rho_c = info_d["rho"], info_c["rho"]
     spl_d = info_d["steps_per_launch"][1]
-    # launches per 100-step segment: ceil(100 / spl), made to have the parity of 100
-    lpseg = -(-REDUCE_EVERY // spl_d)
-    if lpseg % 2 != REDUCE_EVERY % 2:
-        lpseg += 1
-    diff_launches = lpseg * (DIFF_STEPS // REDUCE_EVERY) * args.steps
-    diff_launch_s = diff_ms / 1e3 / diff_launches
-    alg_bytes_d = 2 * info_d["member_tiles"] * rho_d * rho_d * 4  # read + write every member tile once
-    if spl_d > 1:   # plus the contact boxes each fused launch reads (6 M^2/4 chunks of 16 B per super-tile)
-        margin = 4 if spl_d <= 4 else 8
-        alg_bytes_d += info_d["ctas"][1] * (6 * margin * margin // 4) * 16
-    achieved = alg_bytes_d / diff_launch_s / 1e9
-    launches_per_step = CA_STEPS + diff_launches // args.steps + 2 * (DIFF_STEPS // REDUCE_EVERY + 1)
+    spl_c = info_c["steps_per_launch"][0]
+    kd = kernel_launches(spl_d, REDUCE_EVERY) * (DIFF_STEPS // REDUCE_EVERY)    # per bench step
+    kc = kernel_launches(spl_c, CA_STEPS)
+    rf_d = launch_roofline("diffusion", info_d, spl_d, diff_ms / 1e3 / (kd * args.steps), hbm, peak_kind)
+    rf_c = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind)
+    roofline = rf_d if diff_ms >= ca_ms else rf_c          # the kernel that takes most of the step
+    launches_per_step = kc + kd + 2 * (DIFF_STEPS // REDUCE_EVERY + 1)
+    # each workload's cell-updates/s against its HBM floor: every member
+    # sector read and written once per step at the measured copy bandwidth
+    # (rho = 32 sectors for uint8, rho = 8 for float32)
+    floors = {}
+    for wl, ms, steps, floor_bytes in (("ca", ca_ms, CA_STEPS, 2 * 3 ** (K - 5) * 32 * 32),
+                                       ("diffusion", diff_ms, DIFF_STEPS, 2 * 3 ** (K - 3) * 64 * 4)):
+        rate = MEMBERS * steps * args.steps / (ms / 1e3)
+        floor_rate = MEMBERS / (floor_bytes / (hbm * 1e9))
+        floors[wl] = {"cell_updates_per_s": rate, "floor_cell_updates_per_s": floor_rate,
+                      "frac_of_floor": rate / floor_rate, "ms_per_bench_step": ms / args.steps,
+                      "floor_bytes_per_step": floor_bytes}
 
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -375,9 +397,8 @@ def main():
                          f" reduce every {REDUCE_EVERY} + 1 count reduce"),
             "map": "lambda", "k": K, "rho_ca": rho_c, "rho_diffusion": rho_d,
             "cta_levels_ca": info_c["cta_levels"][0], "cta_levels_diffusion": info_d["cta_levels"][1],
-            "steps_per_launch_diffusion": spl_d,
-            "staging_ca": "tma" if info_c["tma"][0] else "vector loads",
-            "staging_diffusion": "tma" if info_d["tma"][1] else "vector loads",
+            "steps_per_launch_diffusion": spl_d, "steps_per_launch_ca": spl_c,
+            "staging_ca": staging(info_c, 0), "staging_diffusion": staging(info_d, 1),
             "tuning": "rho in {8,16,32}, staging and CTA levels chosen by fractal_plan_autotune",
             "l2": "inputs larger than L2 (4 GiB uint8 + 16 GiB FP32 per buffer)",
             "l2_fetch_granularity_bytes": l2_fetch,
@@ -385,17 +406,13 @@ def main():
         },
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "roofline": {
-            "kernel": ("diffusion_fused_kernel" if spl_d > 1 else
-                       "diffusion_tma_kernel" if info_d["tma"][1] else "diffusion_kernel")
-                      + f"<lambda, rho={rho_d}>" + (f" x{spl_d} steps/launch" if spl_d > 1 else ""),
-            "bound": "hbm", "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
-            "alg_bytes_per_launch": alg_bytes_d, "launch_us": diff_launch_s * 1e6,
-        },
-        "bb": {"value": value_bb, "ms_per_step": 1e3 * t_bb / max(1, args.steps // 2),
-               "speedup_lambda_over_bb": value / value_bb,
-               "rho_ca": best[("ca", 1)], "rho_diffusion": best[("diffusion", 1)]},
+        "roofline": roofline,
+        "roofline_other": rf_c if roofline is rf_d else rf_d,
+        "vs_hbm_floor": floors,
+        "bb": None if value_bb is None else {
+            "value": value_bb, "ms_per_step": 1e3 * t_bb / max(1, args.steps // 2),
+            "speedup_lambda_over_bb": value / value_bb,
+            "rho_ca": best[("ca", 1)], "rho_diffusion": best[("diffusion", 1)]},
         "tuned_step_us": {f"{wl}/{'lambda' if md == 0 else 'bb'}/rho{rho}": round(us, 2)
                           for (wl, md, rho), (_, us) in sorted(tuned.items())},
     }
@@ -418,6 +435,73 @@ def main():
         pl.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def kernel_launches(spl, steps):
+    """Launches the step driver makes for `steps` steps at `spl` per launch:
+    ceil(steps / spl), raised by one if its parity differs from steps'."""
+    if spl <= 1:
+        return steps
+    L = -(-steps // spl)
+    return L + 1 if L % 2 != steps % 2 else L
+
+
+def staging(info, d):
+    if info["steps_per_launch"][d] > 1:
+        return f"fused, {info['steps_per_launch'][d]} steps/launch"
+    return "tma" if info["tma"][d] else "vector loads"
+
+
+def kernel_name(wl, info, spl):
+    d = 0 if wl == "ca" else 1
+    if spl > 1:
+        base = "ca_fused_kernel<lambda>" if wl == "ca" else f"diffusion_fused_kernel<lambda, rho={info['rho']}>"
+        return base + f" x{spl} steps/launch"
+    kind = "tma_kernel" if info["tma"][d] else "kernel"
+    return f"{'ca' if wl == 'ca' else 'diffusion'}_{kind}<lambda, rho={info['rho']}>"
+
+
+def ca_box_member_words(k, T, M):
+    """Box words (32-cell row segments) holding members, summed over the member
+    super-tiles of side T: what a fused automaton launch loads besides its
+    word tiles.  Row segments of columns -1, 0 and T/32 around each super-tile
+    (left, top, right and bottom boxes)."""
+    import numpy as np
+    n = 1 << k
+    s = n // T
+    sy, sx = np.nonzero((np.arange(s)[None, :] & np.arange(s)[:, None]) == 0)
+    ox, oy = sx * T, sy * T
+    total = 0
+    right = 2 * M + 1
+    for col, y0, rows in ((-1, 0, M), (0, -M, M), (T // 32, -M, right), (-1, T, M), (0, T, M)):
+        for i in range(rows):
+            gx0 = ox + 32 * col
+            gy = oy + y0 + i
+            inside = (gx0 >= 0) & (gx0 < n) & (gy >= 0) & (gy < n)
+            total += int(np.count_nonzero(inside & ((gx0 & gy) == 0)))
+    return total
+
+
+def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind):
+    """HBM roofline of one launch of the workload's step kernel: algorithmic
+    bytes (every member tile read and written once, plus the margin boxes a
+    fused launch reads) over the launch's measured mean duration."""
+    rho = info["rho"]
+    d = 0 if wl == "ca" else 1
+    if wl == "diffusion":
+        alg = 2 * info["member_tiles"] * rho * rho * 4
+        if spl > 1:     # 6 M^2 cells of margin boxes per super-tile, M = 4 or 8
+            margin = 4 if spl <= 4 else 8
+            alg += info["ctas"][d] * 6 * margin * margin * 4
+    elif spl > 1:       # 32-byte row segments of the member 32 x 32 word tiles, plus box words
+        T = rho << info["cta_levels"][d]
+        alg = 2 * 3 ** (info["k"] - 5) * 32 * 32 + 32 * ca_box_member_words(info["k"], T, spl)
+    else:
+        alg = 2 * info["member_tiles"] * rho * rho
+    achieved = alg / launch_s / 1e9
+    return {"kernel": kernel_name(wl, info, spl), "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "alg_bytes_per_launch": alg, "launch_us": launch_s * 1e6, "steps_per_launch": spl}
 
 
 def profile_run(args):
@@ -446,13 +530,10 @@ def profile_run(args):
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     for _ in range(args.launches):
         if args.profile == "ca":
-            fr.fractal_step_ca(plan, a, b, 1)
-            a, b = b, a
+            # two launches of `spl` steps each (the result lands back in a)
+            fr.fractal_step_ca(plan, a, b, 2 * args.spl)
         elif args.profile == "diffusion":
-            # one launch of `spl` steps (spl even keeps the result in a)
-            fr.fractal_step_diffusion(plan, a, b, COEF, args.spl)
-            if args.spl % 2:
-                a, b = b, a
+            fr.fractal_step_diffusion(plan, a, b, COEF, 2 * args.spl)
         elif args.profile == "reduce":
             fr.fractal_reduce_async(plan, a, fr.FRACTAL_F32, out)
         else:
@@ -486,10 +567,14 @@ def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
             ic, idf = pc.info(), pd.info()
             tiles = ic["member_tiles"]
             rec = {}
-            t = clock(lambda: fr.fractal_step_ca(pc, ca_a, ca_b, 2, stream)) / 2
+            spl_c = ic["steps_per_launch"][0]
+            nst = 2 * spl_c if spl_c > 1 else 2          # two launches, result back in ca_a
+            t = clock(lambda: fr.fractal_step_ca(pc, ca_a, ca_b, nst, stream)) / nst
             b = 2 * tiles * rho * rho
-            rec["ca"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "alg_gbs": b / t / 1e9,
-                         "frac": b / t / 1e9 / hbm, "cta_levels": ic["cta_levels"][0], "tma": ic["tma"][0]}
+            rec["ca"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9, "steps_per_launch": spl_c,
+                         "alg_gbs_per_launch": b / (t * max(1, spl_c)) / 1e9,
+                         "frac": b / (t * max(1, spl_c)) / 1e9 / hbm, "cta_levels": ic["cta_levels"][0],
+                         "tma": ic["tma"][0]}
             t = clock(lambda: fr.fractal_step_diffusion(pd, u_a, u_b, COEF, 16, stream)) / 16
             b = 2 * tiles * rho * rho * 4
             spl = idf["steps_per_launch"][1]

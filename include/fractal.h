@@ -128,7 +128,8 @@ int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
 /*
  * fractal_plan_autotune -- time the plan's step kernel for dtype under every
  * staging (TMA where it applies, vector loads), every valid number of tile
- * levels per CTA and, for float32, 1, 2, 4 or 8 steps per launch, and keep
+ * levels per CTA and 1 step per launch or temporal fusion (float32: 2, 4 or
+ * 8 steps per launch; uint8: 8, 16 or 25), and keep
  * the fastest per step.  Each candidate runs `reps` timed launches dev_in ->
  * dev_scratch (after two untimed ones) on `stream`, which is synchronised.  dev_in is only read; dev_scratch is
  * overwritten.  Both are n*n arrays of dtype, 16-byte aligned.  *best_us
@@ -141,14 +142,17 @@ int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, vo
 
 /*
  * fractal_plan_set_steps_per_launch -- temporal fusion: each launch advances
- * every member tile by up to `spl` (1..8) steps, staging the tile once and
- * the few cells around the super-tile's three contacts with the rest of the
- * gasket (margin boxes of 4 or 8 cells).  Results equal those of single-step
- * launches up to FP32 rounding order; the buffer holding the result after
- * `steps` steps is unchanged (dev_a for even, dev_b for odd).  spl = 1 turns
- * fusion off.  Available for FRACTAL_F32 (diffusion) with rho >= 4 and a
- * super-tile side of at least 8 (spl <= 4) or 16 cells.  Errors:
- * FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan).
+ * every member tile by up to `spl` steps, staging the tile once and the few
+ * cells around the super-tile's three contacts with the rest of the gasket
+ * (margin boxes of width >= spl).  Results equal those of single-step
+ * launches (bit for bit for the automaton, up to FP32 rounding order for the
+ * diffusion); the buffer holding the result after `steps` steps is unchanged
+ * (dev_a for even, dev_b for odd).  spl = 1 turns fusion off.
+ * FRACTAL_F32 (diffusion): spl <= 8, rho >= 4, a super-tile side of at least
+ * 8 (spl <= 4) or 16 cells.  FRACTAL_U8 (automaton, on a bit image of 32-cell
+ * words): spl <= 31, a super-tile side of 32 to 512 cells and at least 2*spl
+ * (k >= 6).  The super-tile may be smaller than the plan's step kernels use.
+ * Errors: FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan).
  */
 int fractal_plan_set_steps_per_launch(fractal_plan_t plan, int dtype, int spl);
 
@@ -187,6 +191,9 @@ int fractal_map_write(fractal_plan_t plan, void* dev_buf, int dtype, double valu
  * the steps alternate dev_a -> dev_b -> dev_a ...: after the call the state
  * is in dev_a when `steps` is even and in dev_b when it is odd.  Both buffers
  * are n*n bytes, 16-byte aligned, distinct.  steps == 0 does nothing.
+ * Only member tiles are written (their non-member cells as 0); with temporal
+ * fusion on (fractal_plan_set_steps_per_launch), whole 32-cell row segments
+ * of the member 32 x 32 blocks, non-member cells again as 0.
  * Errors: FRACTAL_EINVAL (NULL, equal or misaligned buffers, steps < 0),
  * FRACTAL_ECUDA.
  */

@@ -72,12 +72,34 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   return plan_geometry(p.k, p.log_rho, p.mode, dtype, levels, step, aux, tma, tma_ok);
 }
 
-// Launch of the temporally fused kernel for `spl` steps per launch (float32
-// diffusion, rho >= 4, super-tile side >= twice the margin); the fused kernel
-// keeps every chunk of its super-tile in registers of one thread, so it may
-// take fewer tile levels per CTA than the plan's `step`.  False if none fits.
+// Largest steps per launch of the fused kernels: float32 margins of 4 or 8
+// cells; uint8 margins of up to 31 cells (one word column of the bit image).
+int max_spl(int dtype) { return dtype == FRACTAL_U8 ? 31 : 8; }
+
+// Launch of the temporally fused kernel for `spl` steps per launch (super-tile
+// side >= twice the margin).  The float32 kernel (rho >= 4) keeps every chunk
+// of its super-tile in registers of one thread, the uint8 kernel at most a few
+// 32-row word columns per warp, so either may take fewer tile levels per CTA
+// than the plan's `step`.  False if none fits.
 bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step, Launch& fused) {
-  if (dtype != FRACTAL_F32 || spl < 2 || spl > 8) return false;
+  if (spl < 2 || spl > max_spl(dtype)) return false;
+  if (dtype == FRACTAL_U8) {
+    for (int m = step.geo.m; m >= 0; --m) {
+      Launch st, aux, tma;
+      bool tok = false;
+      if (!plan_geometry(p.k, p.log_rho, p.mode, dtype, m, st, aux, tma, tok)) continue;
+      const int threads = ca_fused_threads(st.geo, spl);
+      const int smem = ca_fused_smem_bytes(st.geo, spl);
+      if (threads > 0 && smem <= kMaxSmem) {
+        fused = st;
+        fused.threads = threads;
+        fused.smem = smem;
+        return true;
+      }
+      if (st.geo.T < 2 * spl) break;
+    }
+    return false;
+  }
   const int rho = 1 << p.log_rho;
   const int margin = fused_margin(spl);
   if (rho < 4) return false;
@@ -359,7 +381,7 @@ int fractal_plan_set_cta_levels(fractal_plan_t p, int dtype, int levels) {
 }
 
 int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
-  if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) || spl < 1 || spl > 8) return FRACTAL_EINVAL;
+  if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) || spl < 1 || spl > max_spl(dtype)) return FRACTAL_EINVAL;
   if (spl == 1) {
     p->spl[dtype] = 1;
     p->fused_ok[dtype] = false;
@@ -399,19 +421,25 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   int status = FRACTAL_OK;
   // One launch dev_in -> dev_scratch: a single step, or `spl` fused steps.
   auto launch = [&](int spl) -> int {
-    if (spl > 1)
-      return launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[dtype], (const float*)dev_in,
-                                    (float*)dev_scratch, 0.2f, spl, st) == cudaSuccess
-                 ? FRACTAL_OK
-                 : cuda_fail(cudaGetLastError(), "autotune");
+    if (spl > 1) {
+      const cudaError_t e =
+          dtype == FRACTAL_U8
+              ? launch_ca_fused(p->mode, p->fused[dtype], (const uint8_t*)dev_in, (uint8_t*)dev_scratch, spl, spl, st)
+              : launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[dtype],
+                                       (const float*)dev_in, (float*)dev_scratch, 0.2f, spl, st);
+      return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "autotune");
+    }
     return dtype == FRACTAL_U8 ? fractal_step_ca(p, (uint8_t*)dev_in, (uint8_t*)dev_scratch, 1, stream)
                                : fractal_step_diffusion(p, (float*)dev_in, (float*)dev_scratch, 0.2f, 1, stream);
   };
   for (int m = 0; m <= kMaxLevelsPerCta && m <= p->rb && status == FRACTAL_OK; ++m) {
     if (fractal_plan_set_cta_levels(p, dtype, m) != FRACTAL_OK) continue;
     // candidates: (schedule, steps per launch)
-    const int cands[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 2},
-                             {FRACTAL_SCHED_AUTO, 4}, {FRACTAL_SCHED_AUTO, 8}};
+    const int cands_f32[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 2},
+                                 {FRACTAL_SCHED_AUTO, 4}, {FRACTAL_SCHED_AUTO, 8}};
+    const int cands_u8[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
+                                {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 25}};
+    const int(*cands)[2] = dtype == FRACTAL_U8 ? cands_u8 : cands_f32;
     for (int ci = 0; ci < 5 && status == FRACTAL_OK; ++ci) {
       const int sched = cands[ci][0], spl = cands[ci][1];
       if (sched == FRACTAL_SCHED_TMA && !p->tma_ok[dtype]) continue;
@@ -484,6 +512,19 @@ int fractal_step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, void* s
   if (steps == 0) return FRACTAL_OK;
   const cudaStream_t st = (cudaStream_t)stream;
   uint8_t* buf[2] = {a, b};
+  if (p->spl[FRACTAL_U8] > 1 && p->fused_ok[FRACTAL_U8]) {
+    // as for the diffusion: L launches with the parity of `steps`
+    const int spl = p->spl[FRACTAL_U8];
+    int L = (steps + spl - 1) / spl;
+    if ((L & 1) != (steps & 1)) ++L;
+    const int base = steps / L, extra = steps % L;
+    for (int i = 0; i < L; ++i) {
+      const int ns = base + (i < extra ? 1 : 0);
+      cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], buf[i & 1], buf[(i + 1) & 1], ns, spl, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    }
+    return FRACTAL_OK;
+  }
   if (use_tma(p, FRACTAL_U8)) {
     CUtensorMap maps[2], rings[2];
     const int rho = 1 << p->log_rho;

@@ -198,6 +198,27 @@ __device__ __forceinline__ uint32_t spread4(uint32_t b) {
   return ((b & 0xfu) * 0x00204081u) & 0x01010101u;
 }
 
+// B3/S23 on a 32-cell row segment, bit-sliced: up/mid/dn are the rows above,
+// at and below the segment as 34-bit windows (bit 0 = the cell left of the
+// segment, bits 1..32 = its cells, bit 33 = the cell right of it).  The eight
+// neighbour planes are summed with full adders into the count's bits 0..2
+// (a count of 8 wraps to 0, which is neither 2 nor 3); a cell is alive next
+// if the count is 3, or 2 and it is alive now.
+__device__ __forceinline__ uint32_t life_rule32(uint64_t up, uint64_t mid, uint64_t dn) {
+  const uint32_t a = (uint32_t)up, b = (uint32_t)(up >> 1), c = (uint32_t)(up >> 2);
+  const uint32_t d = (uint32_t)mid, e = (uint32_t)(mid >> 2);
+  const uint32_t f = (uint32_t)dn, g = (uint32_t)(dn >> 1), h = (uint32_t)(dn >> 2);
+  const uint32_t self = (uint32_t)(mid >> 1);
+  const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
+  const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
+  const uint32_t s3 = g ^ h, c3 = g & h;
+  const uint32_t bit0 = s1 ^ s2 ^ s3, c4 = (s1 & s2) | (s3 & (s1 ^ s2));
+  const uint32_t t1 = c1 ^ c2 ^ c3, c5 = (c1 & c2) | (c3 & (c1 ^ c2));
+  const uint32_t bit1 = t1 ^ c4, c6 = t1 & c4;
+  const uint32_t bit2 = c5 ^ c6;
+  return bit1 & ~bit2 & (bit0 | self);
+}
+
 template <int W>
 __device__ __forceinline__ uint32_t load_alive_bits(const uint8_t* __restrict__ p) {
   if constexpr (W == 32) {

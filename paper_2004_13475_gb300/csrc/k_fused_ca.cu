@@ -1,0 +1,232 @@
+// Temporally fused automaton: one CTA advances its member super-tile by up to
+// `margin` B3/S23 steps per launch on a bit image in shared memory.
+//
+// Word tiles.  The state is packed one bit per cell, 32 cells of a row per
+// word.  Inside a super-tile of side T (T >= 32, super-tile coordinates) the
+// word of row y covering columns [32c, 32c + 32) holds members iff
+// c & (y >> 5) == 0, whatever the plan's rho: the CTA works on 32 x 32-cell
+// word tiles, the member ones being the level-log2(T/32) gasket of word
+// tiles, enumerated with lambda (Sec. 5.1 further unrolling) or, in BB mode,
+// by discarding the non-member slots of the 2^j x 2^j bounding box.  A word
+// tile covers whole rho x rho tiles for rho <= 32; its 32-byte row segments
+// are the sectors a rho = 32 tile reads and writes.  Cells of the segment in
+// non-member rho-tiles are non-members and are written back as 0.
+//
+// Margin boxes.  Influence travels along member cells only (non-members are
+// dead for ever), at one cell per step in the 8-neighbourhood.  For s <= M <=
+// T/2 every member reached from the super-tile in s steps lies in
+//   left   [-M, 0) x [0, M)        top    [0, M) x [-M, 0)
+//   right  [T, T+M) x [-M, M]      bottom [-M, M] x [T, T+M)
+// (the right and bottom boxes reach one row / column further than the
+// diffusion's 4-neighbour ones: the corner cell (T-1, 0) reaches (T, M) by M
+// diagonal moves).  For M <= 31 these are the words of column -1 (left,
+// bottom), 0 (top, bottom) and T/32 (right).  Box words are evolved with the
+// tiles; cells whose neighbours were not staged go wrong from the box edge
+// inwards, one cell per step, and never reach the super-tile within s steps.
+//
+// Tasks.  A task is one word column of at most 32 consecutive rows (a word
+// tile, or a piece of a box); lane i of the warp that owns it keeps row i.
+// Each step a lane reads the 3 x 3 words around its word (rows above and
+// below, columns left and right), builds the three 34-bit row windows,
+// applies the bit-sliced rule, masks births outside the gasket and writes the
+// word to the other image.  Every staged word is the word of exactly one task
+// lane; every other word of the image is 0 and stays 0.
+#include "launch.h"
+
+namespace fractal {
+namespace {
+
+constexpr int kCaTasksPerWarp = 6;
+
+// Image geometry: rows [-M-1, T+M] (a guard row beyond each box), word columns
+// [-2, T/32+1] (a guard column beyond each box column), padded to an odd
+// pitch so that the 32 rows of a task fall into 32 different banks.
+__host__ __device__ inline int ca_pitch(int T) { return (T >> 5) + 5; }
+__host__ __device__ inline int ca_rows(int T, int M) { return T + 2 * M + 2; }
+__host__ __device__ inline int ca_image_words(int T, int M) { return (ca_pitch(T) * ca_rows(T, M) + 3) & ~3; }
+
+// Tasks of a super-tile: word tiles first, then the six box pieces.
+__host__ __device__ inline int ca_tasks(int wtiles) { return wtiles + 6; }
+
+// Task -> (word column c, first row y0, rows) in super-tile coordinates.
+__device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, int T, int M, int& c, int& y0,
+                                        int& rows) {
+  if (j < wtiles) {
+    const uint32_t e = tab[j];
+    c = (int)(e & 0xffffu);
+    y0 = (int)(e >> 16) * 32;
+    rows = 32;
+    return;
+  }
+  const int right = 2 * M + 1;  // rows of the right box
+  switch (j - wtiles) {
+    case 0: c = -1; y0 = 0; rows = M; return;                                   // left
+    case 1: c = 0; y0 = -M; rows = M; return;                                   // top
+    case 2: c = T >> 5; y0 = -M; rows = right < 32 ? right : 32; return;        // right, first 32 rows
+    case 3: c = T >> 5; y0 = -M + 32; rows = right > 32 ? right - 32 : 0; return;  // right, the rest
+    case 4: c = -1; y0 = T; rows = M; return;                                   // bottom, left word
+    default: c = 0; y0 = T; rows = M; return;                                   // bottom, right word
+  }
+}
+
+// 32 bytes of 0/1 cells -> 32 bits (bit i = cell i).
+__device__ __forceinline__ uint32_t pack32(uint4 a, uint4 b) {
+  return nz4(a.x) | nz4(a.y) << 4 | nz4(a.z) << 8 | nz4(a.w) << 12 | nz4(b.x) << 16 | nz4(b.y) << 20 |
+         nz4(b.z) << 24 | nz4(b.w) << 28;
+}
+
+// 34-bit row window of the word p[0] with its neighbours' edge cells.
+__device__ __forceinline__ uint64_t window(uint32_t l, uint32_t c, uint32_t r) {
+  return (uint64_t)(l >> 31) | ((uint64_t)c << 1) | ((uint64_t)(r & 1u) << 33);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                                       int nsteps, int M, int wlev, Geo g) {
+  constexpr int TPW = kCaTasksPerWarp;
+  extern __shared__ __align__(16) unsigned char sm[];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  const int n = g.n, T = g.T;
+  const int wside = 1 << wlev;                         // word tiles per super-tile side
+  int wtiles = 1, wlw = 1;                             // 3^wlev, 3^ceil(wlev/2)
+  for (int i = 0; i < wlev; ++i) wtiles *= 3;
+  for (int i = 0; i < (wlev + 1) / 2; ++i) wlw *= 3;
+  const int P = ca_pitch(T);
+  const int img = ca_image_words(T, M);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
+  uint32_t* A = tab + tab_words(wtiles);
+  uint32_t* B = A + img;
+  const int ox = sx * T, oy = sy * T;
+
+  // member word tiles of the super-tile
+  if (MODE == kLambda) {
+    for (int j = threadIdx.x; j < wtiles; j += blockDim.x) {
+      int ux, uy;
+      lambda_scalar((uint32_t)(j % wlw), (uint32_t)(j / wlw), wlev, ux, uy);
+      tab[j] = (uint32_t)ux | ((uint32_t)uy << 16);
+    }
+  } else {
+    for (int j = threadIdx.x; j < wside * wside; j += blockDim.x) {
+      const int ux = j & (wside - 1), uy = j >> wlev;
+      if ((ux & uy) == 0) {
+        int rank = 0;
+        for (int q = 0; q < j; ++q) rank += ((q & (wside - 1)) & (q >> wlev)) == 0;
+        tab[rank] = (uint32_t)ux | ((uint32_t)uy << 16);
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < 2 * img / 4; i += blockDim.x)
+    reinterpret_cast<uint4*>(A)[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+
+  // this lane's row of each of its warp's tasks: image offset and member bits
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ntasks = ca_tasks(wtiles);
+  int off[TPW];
+  uint32_t mk[TPW];
+  // staged in two halves, each with all of its loads in flight
+#pragma unroll
+  for (int h = 0; h < TPW; h += TPW / 2) {
+    uint4 ld[TPW / 2][2];
+#pragma unroll
+    for (int k = h; k < h + TPW / 2; ++k) {
+      off[k] = -1;
+      mk[k] = 0u;
+      const int j = warp + k * nw;
+      if (j >= ntasks) continue;
+      int c, y0, rows;
+      ca_task(j, wtiles, tab, T, M, c, y0, rows);
+      if (lane >= rows) continue;
+      const int y = y0 + lane;
+      const int gx0 = ox + 32 * c, gy = oy + y;
+      off[k] = (y + M + 1) * P + c + 2;
+      mk[k] = (unsigned)gx0 < (unsigned)n ? chunk_members<32>(gx0, gy, n) : 0u;
+      if (mk[k]) {
+        const uint4* p = reinterpret_cast<const uint4*>(in + (size_t)gy * n + gx0);
+        ld[k - h][0] = __ldg(p);
+        ld[k - h][1] = __ldg(p + 1);
+      }
+    }
+#pragma unroll
+    for (int k = h; k < h + TPW / 2; ++k)
+      if (off[k] >= 0 && mk[k]) A[off[k]] = pack32(ld[k - h][0], ld[k - h][1]) & mk[k];
+  }
+  __syncthreads();
+
+  for (int t = 0; t < nsteps; ++t) {
+#pragma unroll
+    for (int k = 0; k < TPW; ++k) {
+      if (off[k] < 0) continue;
+      const uint32_t* p = A + off[k];
+      const uint64_t up = window(p[-P - 1], p[-P], p[-P + 1]);
+      const uint64_t mid = window(p[-1], p[0], p[1]);
+      const uint64_t dn = window(p[P - 1], p[P], p[P + 1]);
+      B[off[k]] = life_rule32(up, mid, dn) & mk[k];
+    }
+    __syncthreads();
+    uint32_t* tmp = A;
+    A = B;
+    B = tmp;
+  }
+
+  // write back the word tiles (whole 32-byte row segments)
+#pragma unroll
+  for (int k = 0; k < TPW; ++k) {
+    const int j = warp + k * nw;
+    if (off[k] < 0 || j >= wtiles) continue;
+    const int c = off[k] % P - 2, y = off[k] / P - M - 1;
+    const uint32_t w = A[off[k]];
+    uint4 v0, v1;
+    v0.x = spread4(w);
+    v0.y = spread4(w >> 4);
+    v0.z = spread4(w >> 8);
+    v0.w = spread4(w >> 12);
+    v1.x = spread4(w >> 16);
+    v1.y = spread4(w >> 20);
+    v1.z = spread4(w >> 24);
+    v1.w = spread4(w >> 28);
+    uint4* q = reinterpret_cast<uint4*>(out + (size_t)(oy + y) * n + ox + 32 * c);
+    q[0] = v0;
+    q[1] = v1;
+  }
+}
+
+template <int MODE>
+cudaError_t go(const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin, cudaStream_t s) {
+  auto* k = ca_fused_kernel<MODE>;
+  cudaError_t e = allow_smem((const void*)k, L.smem);
+  if (e != cudaSuccess) return e;
+  k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, ilog2c(L.geo.T) - 5, L.geo);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int ca_fused_smem_bytes(const Geo& g, int margin) {
+  const int wlev = ilog2c(g.T) - 5;
+  int wtiles = 1;
+  for (int i = 0; i < wlev; ++i) wtiles *= 3;
+  return tab_words(wtiles) * 4 + 2 * ca_image_words(g.T, margin) * 4;
+}
+
+// Warps of a fused automaton launch: the fewest that give every warp the
+// least number of tasks; 0 if the super-tile does not fit the kernel.
+int ca_fused_threads(const Geo& g, int margin) {
+  if (g.T < 32 || g.T > 512 || margin < 1 || margin > 31 || 2 * margin > g.T) return 0;
+  int wtiles = 1;
+  for (int i = 0; i < ilog2c(g.T) - 5; ++i) wtiles *= 3;
+  const int tasks = ca_tasks(wtiles);
+  const int per = (tasks + 15) / 16;  // with 16 warps
+  if (per > kCaTasksPerWarp) return 0;
+  const int warps = (tasks + per - 1) / per;
+  return 32 * warps;
+}
+
+cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
+                            cudaStream_t s) {
+  if (nsteps < 1 || nsteps > margin || ca_fused_threads(L.geo, margin) != L.threads) return cudaErrorInvalidValue;
+  return mode == kLambda ? go<kLambda>(L, in, out, nsteps, margin, s) : go<kBB>(L, in, out, nsteps, margin, s);
+}
+
+}  // namespace fractal

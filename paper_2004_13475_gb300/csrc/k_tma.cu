@@ -299,21 +299,6 @@ __global__ void __launch_bounds__(256, 4) diffusion_tma_kernel(const __grid_cons
 
 // ------------------------------------------------------------- automaton ----
 
-__device__ __forceinline__ uint32_t life_rule32(uint64_t up, uint64_t mid, uint64_t dn) {
-  const uint32_t a = (uint32_t)up, b = (uint32_t)(up >> 1), c = (uint32_t)(up >> 2);
-  const uint32_t d = (uint32_t)mid, e = (uint32_t)(mid >> 2);
-  const uint32_t f = (uint32_t)dn, g = (uint32_t)(dn >> 1), h = (uint32_t)(dn >> 2);
-  const uint32_t self = (uint32_t)(mid >> 1);
-  const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
-  const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
-  const uint32_t s3 = g ^ h, c3 = g & h;
-  const uint32_t bit0 = s1 ^ s2 ^ s3, c4 = (s1 & s2) | (s3 & (s1 ^ s2));
-  const uint32_t t1 = c1 ^ c2 ^ c3, c5 = (c1 & c2) | (c3 & (c1 ^ c2));
-  const uint32_t bit1 = t1 ^ c4, c6 = t1 & c4;
-  const uint32_t bit2 = c5 ^ c6;
-  return bit1 & ~bit2 & (bit0 | self);
-}
-
 __device__ __forceinline__ uint32_t nz_half(uint4 v) {
   return nz4(v.x) | nz4(v.y) << 4 | nz4(v.z) << 8 | nz4(v.w) << 12;
 }

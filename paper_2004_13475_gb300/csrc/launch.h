@@ -42,6 +42,13 @@ int fused_margin(int steps_per_launch);
 int fused_smem_bytes(const Geo& g, int margin);
 int fused_threads(const Geo& g, int rho, int margin);
 
+// Temporally fused automaton on a bit image: nsteps (<= margin <= 31) steps
+// per launch over 32 x 32-cell word tiles (k_fused_ca.cu).
+cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
+                            cudaStream_t s);
+int ca_fused_smem_bytes(const Geo& g, int margin);
+int ca_fused_threads(const Geo& g, int margin);
+
 // Launch geometry of the kernels for level k, tile side 2^log_rho, mode,
 // dtype and `levels` tile levels per CTA (false if it does not fit).
 bool plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,

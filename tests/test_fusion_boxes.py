@@ -1,0 +1,102 @@
+"""The geometric fact behind temporal fusion (several steps per launch).
+
+A CTA that advances its member super-tile (side T, T a power of two) by s
+steps needs every gasket cell that can influence it within s steps.  Non-member
+cells never change and hold 0, so influence travels only along chains of
+member cells: s moves of the step's neighbourhood (4 neighbours for the
+diffusion, 8 for the automaton).  Besides its member tiles, a fused kernel
+stages four margin boxes of width M >= s (super-tile coordinates):
+
+  diffusion (4 neighbours)
+    left   [-M, 0) x [0, M)        top    [0, M) x [-M, 0)
+    right  [T, T+M) x [-M, M)      bottom [-M, M) x [T, T+M)
+  automaton (8 neighbours): the same, but the right box spans rows [-M, M]
+    and the bottom box columns [-M, M] (the corner cells (T-1, 0) and (0, T-1)
+    reach one row or column further diagonally)
+
+This file checks, by breadth-first search over member cells from every member
+super-tile of small gaskets, that for M <= T/2 every member reached in M moves
+outside the super-tile lies in one of the boxes, and that each box is needed.
+The kernels fuse s <= M <= T/2 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _boxes(T, M, nb):
+    e = 1 if nb == 8 else 0      # the automaton's boxes reach one row / column further
+    return [(-M, 0, 0, M), (0, M, -M, 0), (T, T + M, -M, M + e), (-M, M + e, T, T + M)]   # x0, x1, y0, y1
+
+
+def _moves(nb):
+    m = [(0, 1), (0, -1), (1, 0), (-1, 0)]
+    return m + [(1, 1), (1, -1), (-1, 1), (-1, -1)] if nb == 8 else m
+
+
+def _check(k, t, M, nb):
+    n = 1 << k
+    T = 1 << t
+    mem = oracle.member_mask(n)
+    g = M + 1                                        # padding: a guard ring beyond the reach
+    pad = np.zeros((n + 2 * g, n + 2 * g), dtype=bool)
+    pad[g:g + n, g:g + n] = mem
+    used = [False] * 4
+    for sy in range(n // T):
+        for sx in range(n // T):
+            if sx & sy:
+                continue
+            ox, oy = sx * T, sy * T
+            win = pad[oy:oy + T + 2 * g, ox:ox + T + 2 * g]
+            reach = np.zeros_like(win)
+            reach[g:g + T, g:g + T] = win[g:g + T, g:g + T]
+            for _ in range(M):                       # M moves along member cells
+                nxt = reach.copy()
+                for dy, dx in _moves(nb):
+                    nxt |= np.roll(np.roll(reach, dy, 0), dx, 1)
+                reach = nxt & win
+            reach[g:g + T, g:g + T] = False
+            ys, xs = np.nonzero(reach)
+            for y, x in zip(ys - g, xs - g):         # super-tile coordinates
+                hit = [b for b, (x0, x1, y0, y1) in enumerate(_boxes(T, M, nb))
+                       if x0 <= x < x1 and y0 <= y < y1]
+                assert hit, (k, T, M, nb, sx, sy, x, y)
+                for b in hit:
+                    used[b] = True
+    return used
+
+
+@pytest.mark.parametrize("nb", [4, 8])
+@pytest.mark.parametrize("k,t", [(6, 2), (6, 3), (7, 3), (7, 4), (8, 4), (8, 5), (9, 5), (8, 6)])
+def test_margin_boxes_hold_every_reachable_member(k, t, nb):
+    T = 1 << t
+    used = [False] * 4
+    for M in sorted({1, 2, 4, T // 4, T // 2} - {0}):
+        if M > T // 2:
+            continue
+        u = _check(k, t, M, nb)
+        used = [a or b for a, b in zip(used, u)]
+    assert all(used)     # each box is needed somewhere
+
+
+@pytest.mark.parametrize("nb", [4, 8])
+def test_margin_bound_is_sharp(nb):
+    # The kernels fuse at most T/2 steps; the boxes actually hold up to M = T
+    # (4 neighbours) or T - 1 (8 neighbours) and no further: one more move
+    # reaches the member (-1, -T) of the super-tile above-left.
+    T = 8
+    for M in range(T // 2, T if nb == 8 else T + 1):
+        _check(8, 3, M, nb)
+    with pytest.raises(AssertionError):
+        _check(8, 3, T if nb == 8 else T + 1, nb)
+
+
+def test_automaton_needs_the_wider_boxes():
+    # The diffusion's boxes are too small for 8 neighbours: the member (T, M)
+    # is M diagonal moves from the corner (T-1, 0).
+    T, M = 8, 2
+    n = 1 << 6
+    assert oracle.is_member(n, T, M) and oracle.is_member(n, T - 1, 0)
+    assert not any(x0 <= T < x1 and y0 <= M < y1 for x0, x1, y0, y1 in _boxes(T, M, 4))
+    assert any(x0 <= T < x1 and y0 <= M < y1 for x0, x1, y0, y1 in _boxes(T, M, 8))

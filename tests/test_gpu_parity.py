@@ -151,6 +151,81 @@ def test_ca_every_cta_level(fr, k, rho, sched):
             assert np.array_equal(got[mask], want[mask]), (mode, m)
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("spl", [2, 3, 8, 16, 25, 31])
+@pytest.mark.parametrize("k,rho", [(6, 8), (7, 16), (8, 32), (9, 4), (10, 8), (10, 32), (11, 16)])
+def test_ca_fused_bit_exact(fr, k, rho, mode, spl):
+    # several automaton steps per launch on the bit image: members equal the
+    # oracle bit for bit; the launch writes whole 32-cell row segments of
+    # member word tiles (non-members there become 0) and nothing else
+    n = 1 << k
+    plan = fr.fractal_map(k, rho, mode)
+    fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_U8, spl)
+    assert plan.info()["steps_per_launch"][0] == spl
+    s0 = synth.bernoulli_u8(40 + k, n)      # noise on non-members too: ignored
+    mask = domain(k).mask
+    cover = tile_cover(n, 32) if n >= 32 else np.ones((n, n), dtype=bool)
+    for steps in (1, 5, spl, 2 * spl + 1, 40):
+        want = oracle.ca_run(s0, steps, domain(k))
+        a = dev_u8(s0)
+        b = torch.full_like(a, SENTINEL_U8)
+        out = fr.fractal_step_ca(plan, a, b, steps)
+        assert out is (a if steps % 2 == 0 else b)
+        got = out.cpu().numpy().reshape(n, n)
+        assert np.array_equal(got[mask], want[mask]), steps
+        assert np.all(got[cover & ~mask] == 0)
+        if steps % 2:
+            assert np.all(got[~cover] == SENTINEL_U8)
+        else:
+            assert np.array_equal(got[~cover], s0[~cover])
+    assert fr.fractal_plan_device_status(plan) == 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k,rho", [(10, 32), (12, 8)])
+def test_ca_fused_every_cta_level(fr, k, rho, mode):
+    n = 1 << k
+    s0 = synth.bernoulli_u8(7 * k, n)
+    want = oracle.ca_run(s0, 30, domain(k))
+    mask = domain(k).mask
+    rb = k - int(np.log2(rho))
+    done = 0
+    for m in range(0, min(rb, 5) + 1):
+        plan = fr.fractal_map(k, rho, mode)
+        try:
+            fr.fractal_plan_set_cta_levels(plan, fr.FRACTAL_U8, m)
+            fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_U8, 12)
+        except fr.FractalError:
+            continue     # super-tile below 32 or 24 cells, or above 512
+        got, _, _ = run_ca(fr, plan, s0, 30)
+        assert np.array_equal(got[mask], want[mask]), m
+        done += 1
+    assert done >= 2
+
+
+def test_ca_fused_100_steps_level_12(fr):
+    k, n = 12, 4096
+    s0 = synth.bernoulli_u8(5, n)
+    want = oracle.ca_run(s0, 100, domain(k))
+    for mode in MODES:
+        plan = fr.fractal_map(k, 32, mode)
+        fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_U8, 25)
+        got, _, _ = run_ca(fr, plan, s0, 100)
+        assert np.array_equal(got[domain(k).mask], want[domain(k).mask]), mode
+
+
+def test_ca_fused_needs_room(fr):
+    with pytest.raises(fr.FractalError):
+        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(4, 4), fr.FRACTAL_U8, 2)    # n = 16 < 32
+    with pytest.raises(fr.FractalError):
+        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(10, 8), fr.FRACTAL_U8, 32)
+    with pytest.raises(fr.FractalError):
+        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(5, 8), fr.FRACTAL_U8, 17)   # T = 32 < 2 * 17
+    p = fr.fractal_map(5, 8)
+    fr.fractal_plan_set_steps_per_launch(p, fr.FRACTAL_U8, 16)
+    assert p.info()["steps_per_launch"] == [16, 1]
+
+
 def test_ca_zero_steps_and_states(fr):
     k, n = 6, 64
     plan = fr.fractal_map(k, 16)
