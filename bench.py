@@ -482,17 +482,42 @@ def ca_box_member_words(k, T, M):
     return total
 
 
+def diffusion_box_member_blocks(k, T, M):
+    """Member 8 x 8 blocks in the margin boxes (width M) of every member
+    super-tile of side T: what a fused diffusion launch reads besides the
+    super-tiles' own member blocks."""
+    import numpy as np
+    nblk = (1 << k) // 8
+    s = (1 << k) // T
+    sy, sx = np.nonzero((np.arange(s)[None, :] & np.arange(s)[:, None]) == 0)
+    OX, OY = sx * (T // 8), sy * (T // 8)
+    W, side = M // 8, T // 8
+    boxes = [(-W, 0, 0, W), (0, W, -W, 0), (side, side + W, -W, W), (-W, W, side, side + W)]
+    total = 0
+    for x0, x1, y0, y1 in boxes:
+        for by in range(y0, y1):
+            for bx in range(x0, x1):
+                gx, gy = OX + bx, OY + by
+                ok = (gx >= 0) & (gx < nblk) & (gy >= 0) & (gy < nblk) & ((gx & gy) == 0)
+                total += int(np.count_nonzero(ok))
+    return total
+
+
 def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind):
     """HBM roofline of one launch of the workload's step kernel: algorithmic
     bytes (every member tile read and written once, plus the margin boxes a
     fused launch reads) over the launch's measured mean duration."""
     rho = info["rho"]
     d = 0 if wl == "ca" else 1
-    if wl == "diffusion":
+    if wl == "diffusion" and spl > 1:
+        # every member 8 x 8 block (8 rows of one 32-byte sector) read and
+        # written once, plus the member blocks of the margin boxes (M = spl
+        # rounded up to a multiple of 8) read once
+        T = rho << info["cta_levels"][d]
+        margin = -(-spl // 8) * 8
+        alg = 2 * 3 ** (info["k"] - 3) * 256 + 256 * diffusion_box_member_blocks(info["k"], T, margin)
+    elif wl == "diffusion":
         alg = 2 * info["member_tiles"] * rho * rho * 4
-        if spl > 1:     # 6 M^2 cells of margin boxes per super-tile, M = 4 or 8
-            margin = 4 if spl <= 4 else 8
-            alg += info["ctas"][d] * 6 * margin * margin * 4
     elif spl > 1:       # 32-byte row segments of the member 32 x 32 word tiles, plus box words
         T = rho << info["cta_levels"][d]
         alg = 2 * 3 ** (info["k"] - 5) * 32 * 32 + 32 * ca_box_member_words(info["k"], T, spl)
@@ -575,25 +600,40 @@ def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
                          "alg_gbs_per_launch": b / (t * max(1, spl_c)) / 1e9,
                          "frac": b / (t * max(1, spl_c)) / 1e9 / hbm, "cta_levels": ic["cta_levels"][0],
                          "tma": ic["tma"][0]}
-            t = clock(lambda: fr.fractal_step_diffusion(pd, u_a, u_b, COEF, 16, stream)) / 16
-            b = 2 * tiles * rho * rho * 4
             spl = idf["steps_per_launch"][1]
+            nsd = 2 * spl if spl > 1 else 16            # two launches of spl steps
+            t = clock(lambda: fr.fractal_step_diffusion(pd, u_a, u_b, COEF, nsd, stream)) / nsd
+            b = 2 * tiles * rho * rho * 4
             rec["diffusion"] = {"us": t * 1e6, "gcups": MEMBERS / t / 1e9,
                                 "steps_per_launch": spl, "alg_gbs_per_launch": b / (t * spl) / 1e9,
                                 "frac": b / (t * spl) / 1e9 / hbm, "cta_levels": idf["cta_levels"][1],
                                 "tma": idf["tma"][1]}
-            t = clock(lambda: fr.fractal_map_write(pd, u_b, fr.FRACTAL_F32, 1.0, stream))
-            b = tiles * rho * rho * 4
-            rec["sw_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
-            t = clock(lambda: fr.fractal_map_write(pc, ca_b, fr.FRACTAL_U8, 1.0, stream))
-            b = tiles * rho * rho
-            rec["sw_u8"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+            # map-only write and reduce on fresh plans: one rho-tile per CTA
+            # (the paper's block-per-tile setting) and the default tile levels
             dev_out = torch.zeros(1, dtype=torch.float64, device="cuda")
-            t = clock(lambda: fr.fractal_reduce_async(pd, u_a, fr.FRACTAL_F32, dev_out, stream))
-            b = tiles * rho * rho * 4
-            rec["reduce_f32"] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm}
+            for lv_name in ("tile_per_cta", "default_levels"):
+                pl = fr.fractal_map(K, rho, mode)
+                if lv_name == "tile_per_cta":
+                    fr.fractal_plan_set_cta_levels(pl, fr.FRACTAL_F32, 0)
+                    fr.fractal_plan_set_cta_levels(pl, fr.FRACTAL_U8, 0)
+                lv = pl.info()["cta_levels"]
+                suffix = "" if lv_name == "default_levels" else "_tile_per_cta"
+                t = clock(lambda: fr.fractal_map_write(pl, u_b, fr.FRACTAL_F32, 1.0, stream))
+                b = tiles * rho * rho * 4
+                rec["sw_f32" + suffix] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm,
+                                          "cta_levels": lv[1]}
+                t = clock(lambda: fr.fractal_map_write(pl, ca_b, fr.FRACTAL_U8, 1.0, stream))
+                b = tiles * rho * rho
+                rec["sw_u8" + suffix] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm,
+                                         "cta_levels": lv[0]}
+                t = clock(lambda: fr.fractal_reduce_async(pl, u_a, fr.FRACTAL_F32, dev_out, stream))
+                b = tiles * rho * rho * 4
+                rec["reduce_f32" + suffix] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm,
+                                              "cta_levels": lv[1]}
+                pl.close()
             out.setdefault(str(rho), {})[name] = rec
-        for kname in ("ca", "diffusion", "sw_f32", "sw_u8", "reduce_f32"):
+        for kname in ("ca", "diffusion", "sw_f32", "sw_u8", "reduce_f32", "sw_f32_tile_per_cta",
+                      "sw_u8_tile_per_cta", "reduce_f32_tile_per_cta"):
             lam = out[str(rho)]["lambda"][kname]["us"]
             bb = out[str(rho)]["bb"][kname]["us"]
             out[str(rho)].setdefault("speedup_lambda_over_bb", {})[kname] = bb / lam

@@ -72,15 +72,16 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   return plan_geometry(p.k, p.log_rho, p.mode, dtype, levels, step, aux, tma, tma_ok);
 }
 
-// Largest steps per launch of the fused kernels: float32 margins of 4 or 8
-// cells; uint8 margins of up to 31 cells (one word column of the bit image).
-int max_spl(int dtype) { return dtype == FRACTAL_U8 ? 31 : 8; }
+// Largest steps per launch of the fused kernels: float32 margins of 8, 16 or
+// 32 cells (whole 8 x 8 blocks); uint8 margins of up to 31 cells (one word
+// column of the bit image).
+int max_spl(int dtype) { return dtype == FRACTAL_U8 ? 31 : 32; }
 
 // Launch of the temporally fused kernel for `spl` steps per launch (super-tile
-// side >= twice the margin).  The float32 kernel (rho >= 4) keeps every chunk
-// of its super-tile in registers of one thread, the uint8 kernel at most a few
-// 32-row word columns per warp, so either may take fewer tile levels per CTA
-// than the plan's `step`.  False if none fits.
+// side >= twice the margin).  The float32 kernel (rho >= 4) keeps one 8 x 8
+// block per thread, the uint8 kernel at most a few 32-row word columns per
+// warp, so either may take fewer tile levels per CTA than the plan's `step`.
+// False if none fits.
 bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step, Launch& fused) {
   if (spl < 2 || spl > max_spl(dtype)) return false;
   if (dtype == FRACTAL_U8) {
@@ -100,13 +101,15 @@ bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step,
     }
     return false;
   }
+  // float32: the largest super-tile the kernel takes (at most 512 threads),
+  // whatever the plan's step kernels use
+  (void)step;
   const int rho = 1 << p.log_rho;
   const int margin = fused_margin(spl);
   if (rho < 4) return false;
-  for (int m = step.geo.m; m >= 0; --m) {
-    Launch st, aux, tma;
-    bool tok = false;
-    if (!plan_geometry(p.k, p.log_rho, p.mode, dtype, m, st, aux, tma, tok)) continue;
+  for (int m = kMaxLevelsPerCta; m >= 0; --m) {
+    Launch st;
+    if (!supertile_grid(p.k, p.log_rho, p.mode, m, st)) continue;
     if (st.geo.T < 2 * margin) break;
     const int threads = fused_threads(st.geo, rho, margin);
     const int smem = fused_smem_bytes(st.geo, margin);
@@ -120,6 +123,30 @@ bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step,
   return false;
 }
 }  // namespace
+
+bool fractal::supertile_grid(int k, int log_rho, int mode, int levels, Launch& L) {
+  const int rb = k - log_rho;
+  if (levels < 0 || levels > rb || levels > kMaxLevelsPerCta) return false;
+  const int R = rb - levels;
+  Geo g;
+  g.n = 1 << k;
+  g.m = levels;
+  g.R = R;
+  g.T = (1 << log_rho) << levels;
+  g.slots = (int)(mode == kLambda ? ipow(3, levels) : ipow(4, levels));
+  g.lw = (int)ipow(3, (levels + 1) / 2);
+  g.tiles = (int)ipow(3, levels);
+  if (mode == kLambda) {
+    L.grid = dim3((unsigned)ipow(3, (R + 1) / 2), (unsigned)ipow(3, R / 2), 1);
+  } else {
+    if (R > 15) return false;  // gridDim.y <= 65535
+    L.grid = dim3(1u << R, 1u << R, 1);
+  }
+  L.geo = g;
+  L.threads = 0;
+  L.smem = 0;
+  return true;
+}
 
 bool fractal::plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,
                    bool& tma_ok) {
@@ -418,6 +445,10 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   const int old_sched = p->sched, old_m = p->m[dtype], old_spl = p->spl[dtype];
   float best = -1.0f;
   int best_sched = old_sched, best_m = old_m, best_spl = old_spl;
+  // best single-step candidate: its tile levels also serve the single-write
+  // and reduce kernels when the float32 fused kernel (own super-tile) wins
+  float best1 = -1.0f;
+  int best1_m = old_m;
   int status = FRACTAL_OK;
   // One launch dev_in -> dev_scratch: a single step, or `spl` fused steps.
   auto launch = [&](int spl) -> int {
@@ -432,17 +463,21 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
     return dtype == FRACTAL_U8 ? fractal_step_ca(p, (uint8_t*)dev_in, (uint8_t*)dev_scratch, 1, stream)
                                : fractal_step_diffusion(p, (float*)dev_in, (float*)dev_scratch, 0.2f, 1, stream);
   };
+  bool f32_fused_timed = false;  // the float32 fused kernel picks its own super-tile: time it once
   for (int m = 0; m <= kMaxLevelsPerCta && m <= p->rb && status == FRACTAL_OK; ++m) {
     if (fractal_plan_set_cta_levels(p, dtype, m) != FRACTAL_OK) continue;
+    const bool skip_f32_fused = dtype == FRACTAL_F32 && f32_fused_timed;
+    f32_fused_timed = true;
     // candidates: (schedule, steps per launch)
-    const int cands_f32[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 2},
-                                 {FRACTAL_SCHED_AUTO, 4}, {FRACTAL_SCHED_AUTO, 8}};
+    const int cands_f32[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
+                                 {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 32}};
     const int cands_u8[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
                                 {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 25}};
     const int(*cands)[2] = dtype == FRACTAL_U8 ? cands_u8 : cands_f32;
     for (int ci = 0; ci < 5 && status == FRACTAL_OK; ++ci) {
       const int sched = cands[ci][0], spl = cands[ci][1];
       if (sched == FRACTAL_SCHED_TMA && !p->tma_ok[dtype]) continue;
+      if (spl > 1 && skip_f32_fused) continue;
       if (spl > 1) {
         if (!make_fused(*p, dtype, spl, p->step[dtype], p->fused[dtype])) continue;
         p->spl[dtype] = spl;
@@ -464,6 +499,10 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
         break;
       }
       const float us = 1000.f * ms / (float)(reps * spl);
+      if (spl == 1 && (best1 < 0.f || us < best1)) {
+        best1 = us;
+        best1_m = m;
+      }
       if (best < 0.f || us < best) {
         best = us;
         best_sched = sched;
@@ -476,7 +515,8 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   cudaEventDestroy(e1);
   // keep the winner (or restore the previous choice on failure)
   const bool ok = status == FRACTAL_OK && best >= 0.f;
-  fractal_plan_set_cta_levels(p, dtype, ok ? best_m : old_m);
+  const bool own_tile = dtype == FRACTAL_F32 && best_spl > 1;
+  fractal_plan_set_cta_levels(p, dtype, ok ? (own_tile ? best1_m : best_m) : old_m);
   p->sched = ok ? (best_sched == FRACTAL_SCHED_STAGED ? FRACTAL_SCHED_STAGED : FRACTAL_SCHED_AUTO) : old_sched;
   fractal_plan_set_steps_per_launch(p, dtype, ok ? best_spl : old_spl);
   if (ok && best_us) *best_us = best;

@@ -1,251 +1,401 @@
-// Temporally fused step kernels: one CTA advances its super-tile by up to
-// MARGIN steps per launch, so each member tile is read and written once per
-// launch instead of once per step.
+// Temporally fused diffusion: one CTA advances its member super-tile by up to
+// M steps per launch, each thread holding one 8 x 8-cell block of the gasket
+// in registers.
 //
-// Why the halo stays tiny.  A member super-tile of side T (cells (x, y) in
-// [0,T)^2 with x & y == 0, T a power of two) meets the rest of the gasket
-// only near three contacts: left of (0,0), above (0,0), right of (T-1,0) and
-// below (0,T-1).  For s <= T/2 every member cell outside the super-tile
-// within distance s of one of its members lies in one of four margin boxes
-// (super-tile coordinates, margin width M >= s):
+// Blocks and ports.  Split the array into 8 x 8 blocks.  A block (BX, BY) with
+// BX & BY == 0 holds the 27 members (i, j), i & j == 0, of a level-3 gasket;
+// every other block holds none.  Its members touch cells of other blocks at
+// four links only, through three corner cells ("ports"):
+//   (0,0) <-> (0,7) of the block above      (0,0) <-> (7,0) of the block left
+//   (7,0) <-> (0,0) of the block right      (0,7) <-> (0,0) of the block below
+// (any other member (i, 0) or (0, j) on the near edges faces a cell (i, 7) or
+// (7, j) of the neighbour with i & 7 or 7 & j nonzero, a non-member; the far
+// edges (7, j) and (i, 7) hold members only at j = 0 and i = 0).  So a step
+// needs, besides the block's own 27 values, four values of its neighbours:
+// each thread publishes its three port values per step in shared memory and
+// reads four.
+//
+// Margin boxes.  The gasket outside a member super-tile of side T touches it
+// only near (0, 0), (T-1, 0) and (0, T-1); for s <= M <= T/2 every member that
+// can reach the super-tile within s steps of the 4-neighbour stencil lies in
 //   left   [-M, 0) x [0, M)        top    [0, M) x [-M, 0)
 //   right  [T, T+M) x [-M, M)      bottom [-M, M) x [T, T+M)
-// (outside the super-tile, a member in row -i or column -i lies within i
-// cells of the contact, and members of the right/bottom neighbours deeper
-// than M rows from the contact are more than s cells from every member
-// here).  The CTA stages its member tiles and these boxes in a shared-memory
-// image with a margin of M cells, evolves every member cell of them for s
-// steps (cells of the boxes whose neighbours were not staged go wrong from
-// the box edge inwards, one cell per step, and never reach the super-tile),
-// and writes back only the member tiles.
+// With M a multiple of 8 these are whole blocks; they are evolved with the
+// super-tile (a box block whose neighbour was not staged goes wrong from the
+// box edge inwards, one cell per step, and never reaches the super-tile) and
+// are not written back.
+//
+// A launch reads the member blocks' member 16-byte chunks once, runs the steps
+// with one barrier each, and writes the member blocks back; for rho >= 8 it
+// also writes the zeros of the non-member cells of member tiles, so that every
+// write covers whole 32-byte sectors.
 #include "launch.h"
 
 namespace fractal {
 namespace {
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
-               "l"(gmem)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+constexpr int kS = 8;  // block side in cells
+
+__host__ __device__ constexpr bool bmem(int i, int j) { return i >= 0 && j >= 0 && i < kS && j < kS && (i & j) == 0; }
+__host__ __device__ constexpr int bdeg(int i, int j) {
+  return (bmem(i - 1, j) ? 1 : 0) + (bmem(i + 1, j) ? 1 : 0) + (bmem(i, j - 1) ? 1 : 0) + (bmem(i, j + 1) ? 1 : 0);
 }
 
-// Chunks (4 consecutive cells of a row) the CTA updates: Q per member tile,
-// then the margin boxes.  Returns super-tile coordinates of the first cell.
-template <int RHO, int M>
-__device__ __forceinline__ void fused_chunk(int it, int nt_chunks, const uint32_t* tab, int T, int& lx, int& ly) {
-  constexpr int CPR = RHO / 4;  // chunks per tile row
-  constexpr int Q = RHO * CPR;  // chunks per tile
-  if (it < nt_chunks) {
-    const int c = it / Q, q = it - c * Q;
-    const uint32_t e = tab[c];
-    lx = (int)(e & 0xffffu) * RHO + (q % CPR) * 4;
-    ly = (int)(e >> 16) * RHO + q / CPR;
+// Rank of the member slot (x, y) among the member slots (x & y == 0) of the
+// 2^L x 2^L box in row-major order (the BB enumeration, compacted).  Rows
+// above contribute sum_{y' < y} 2^(L - popc(y')); the row itself the x' < x
+// with x' & y == 0.  Both by the bits from the top, O(L).
+__device__ __forceinline__ int bb_rank(int x, int y, int L) {
+  int above = 0, pref = 1, p3 = 1;
+  for (int i = 0; i < L; ++i) p3 *= 3;
+  for (int i = L - 1; i >= 0; --i) {
+    p3 /= 3;  // 3^i
+    if ((y >> i) & 1) {
+      above += pref * 2 * p3;
+    } else {
+      pref *= 2;
+    }
+  }
+  int within = 0;
+  for (int i = L - 1; i >= 0; --i) {
+    if ((x >> i) & 1) {
+      within += 1 << (i - __popc(y & ((1 << i) - 1)));
+      if ((y >> i) & 1) break;
+    }
+  }
+  return above + within;
+}
+
+// Per-CTA geometry of a fused launch.
+struct FGeo {
+  int n;        // array side
+  int L;        // block levels of the super-tile: T / 8 = 2^L
+  int lw;       // 3^ceil(L/2): width of the level-L packed grid
+  int nb;       // member blocks of the super-tile: 3^L
+  int W;        // box width in blocks: M / 8
+  int nbox;     // box blocks: 6 W^2
+  int log_rho;  // the plan's tile side (write-back of whole member tiles)
+};
+
+// Block of thread t: member blocks first (lambda order, or BB rank order via
+// tab), then the box blocks.  Block coordinates relative to the super-tile.
+template <int MODE>
+__device__ __forceinline__ void fused_block(int t, const FGeo& f, const int* tab, int& bx, int& by) {
+  if (t < f.nb) {
+    if (MODE == kLambda) {
+      lambda_scalar((uint32_t)(t % f.lw), (uint32_t)(t / f.lw), f.L, bx, by);
+    } else {
+      const int j = tab[t];
+      bx = j & ((1 << f.L) - 1);
+      by = j >> f.L;
+    }
     return;
   }
-  int b = it - nt_chunks;
-  constexpr int W = M / 4;  // chunks per box row of width M
-  // left: M rows x W
-  if (b < M * W) { lx = -M + (b % W) * 4; ly = b / W; return; }
-  b -= M * W;
-  // top: M rows x W
-  if (b < M * W) { lx = (b % W) * 4; ly = -M + b / W; return; }
-  b -= M * W;
-  // right: 2M rows x W
-  if (b < 2 * M * W) { lx = T + (b % W) * 4; ly = -M + b / W; return; }
-  b -= 2 * M * W;
-  // bottom: M rows x 2W
-  lx = -M + (b % (2 * W)) * 4;
-  ly = T + b / (2 * W);
+  int b = t - f.nb;
+  const int W = f.W, W2 = W * W, side = 1 << f.L;
+  if (b < W2) {  // left
+    bx = -W + b % W;
+    by = b / W;
+    return;
+  }
+  b -= W2;
+  if (b < W2) {  // top
+    bx = b % W;
+    by = -W + b / W;
+    return;
+  }
+  b -= W2;
+  if (b < 2 * W2) {  // right
+    bx = side + b % W;
+    by = -W + b / W;
+    return;
+  }
+  b -= 2 * W2;  // bottom
+  bx = -W + b % (2 * W);
+  by = side + b / (2 * W);
 }
 
-template <int M>
-__host__ __device__ constexpr int fused_box_chunks() { return (M / 4) * (M + M + 2 * M + 2 * M); }
-
-// Image pitch (floats): T + 2M, padded so that consecutive rows start in
-// different 32-byte bank groups (pitch mod 32 floats is 8 or 24); with 4
-// consecutive rows per 8-lane phase of 128-bit accesses, no bank conflicts.
-__host__ __device__ inline int fused_pitch(int T, int M) {
-  int P = T + 2 * M;
-  if ((P & 31) == 0 || (P & 31) == 16) P += 8;
-  return P;
+// Thread that owns block (bx, by), or `none` if no staged block is there.
+template <int MODE>
+__device__ __forceinline__ int fused_owner(int bx, int by, const FGeo& f, int none) {
+  const int side = 1 << f.L, W = f.W, W2 = W * W;
+  if (bx >= 0 && by >= 0 && bx < side && by < side) {
+    if (bx & by) return none;
+    return MODE == kLambda ? lambda_inverse(bx, by, f.L, f.lw) : bb_rank(bx, by, f.L);
+  }
+  if (bx >= -W && bx < 0 && by >= 0 && by < W) return f.nb + by * W + (bx + W);
+  if (bx >= 0 && bx < W && by >= -W && by < 0) return f.nb + W2 + (by + W) * W + bx;
+  if (bx >= side && bx < side + W && by >= -W && by < W) return f.nb + 2 * W2 + (by + W) * W + (bx - side);
+  if (bx >= -W && bx < W && by >= side && by < side + W) return f.nb + 4 * W2 + (by - side) * 2 * W + (bx + W);
+  return none;
 }
 
-constexpr int kFusedChunksPerThread = 4;
+__device__ __forceinline__ bool block_member(int gx, int gy, int nblk) {
+  return (unsigned)gx < (unsigned)nblk && (unsigned)gy < (unsigned)nblk && (gx & gy) == 0;
+}
 
-template <int MODE, int LOG_RHO, int M>
-__global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                              float a, int nsteps, Geo g) {
-  constexpr int RHO = 1 << LOG_RHO;  // >= 4
-  constexpr int CT = kFusedChunksPerThread;
-  extern __shared__ __align__(16) unsigned char sm[];
-  int sx, sy;
-  if (!cta_supertile<MODE>(g, sx, sy)) return;
-  const int n = g.n, T = g.T;
-  const int P = fused_pitch(T, M);
-  const int img = (T + 2 * M + 2) * P;  // floats per image: rows plus a guard row above and below
-  uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
-  float* A = reinterpret_cast<float*>(sm + tab_words(g.tiles) * 4);
-  float* B = A + img;
-  // cell (lx, ly) of the image sits at (ly + M + 1) * P + lx + M; the guard
-  // rows and the padding keep every neighbour read inside the image
-  const int ox = sx * T, oy = sy * T;
+// Sum of a cell's neighbour values, in a fixed order, with no leading 0 + x.
+struct NbSum {
+  float s = 0.f;
+  bool any = false;
+  __device__ __forceinline__ void add(float v) {
+    s = any ? s + v : v;
+    any = true;
+  }
+};
 
-  // member tiles of the super-tile (further unrolling, or BB discard)
-  for (int j = threadIdx.x; j < g.slots; j += blockDim.x) {
-    int ux, uy;
-    if (MODE == kLambda) {
-      lambda_scalar((uint32_t)(j % g.lw), (uint32_t)(j / g.lw), g.m, ux, uy);
-      tab[j] = (uint32_t)ux | ((uint32_t)uy << 16);
-    } else {
-      ux = j & ((1 << g.m) - 1);
-      uy = j >> g.m;
-      if ((ux & uy) == 0) {
-        int rank = 0;
-        for (int q = 0; q < j; ++q) rank += ((q & ((1 << g.m) - 1)) & (q >> g.m)) == 0;
-        tab[rank] = (uint32_t)ux | ((uint32_t)uy << 16);
+// One step of the 27 members of a block: u' = u + a * (sum of member
+// neighbours - degree * u).  Non-member neighbours hold no value and are not
+// summed; vu, vl, vr, vd are the neighbour values at the ports (0 where the
+// neighbour is not a staged member) and d0, dr, dd the ports' degrees.
+__device__ __forceinline__ void block_step(float (&u)[kS * kS], float a, float vu, float vl, float vr, float vd,
+                                           float d0, float dr, float dd) {
+  float w[kS * kS];
+#pragma unroll
+  for (int j = 0; j < kS; ++j) {
+#pragma unroll
+    for (int i = 0; i < kS; ++i) {
+      if (!bmem(i, j)) continue;
+      NbSum nb;
+      if (bmem(i, j - 1)) nb.add(u[(j - 1) * kS + i]);
+      if (bmem(i - 1, j)) nb.add(u[j * kS + i - 1]);
+      if (bmem(i + 1, j)) nb.add(u[j * kS + i + 1]);
+      if (bmem(i, j + 1)) nb.add(u[(j + 1) * kS + i]);
+      float d = (float)bdeg(i, j);
+      if (i == 0 && j == 0) {
+        nb.add(vu);
+        nb.add(vl);
+        d = d0;
+      }
+      if (i == kS - 1 && j == 0) {
+        nb.add(vr);
+        d = dr;
+      }
+      if (i == 0 && j == kS - 1) {
+        nb.add(vd);
+        d = dd;
+      }
+      const float c = u[j * kS + i];
+      w[j * kS + i] = fmaf(a, fmaf(-d, c, nb.s), c);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kS * kS; ++q)
+    if (bmem(q % kS, q / kS)) u[q] = w[q];
+}
+
+// A 16-byte chunk of row j starting at column i0 with its non-members zeroed.
+__device__ __forceinline__ float4 mask_chunk(float4 v, int i0, int j) {
+  v.x = bmem(i0 + 0, j) ? v.x : 0.f;
+  v.y = bmem(i0 + 1, j) ? v.y : 0.f;
+  v.z = bmem(i0 + 2, j) ? v.z : 0.f;
+  v.w = bmem(i0 + 3, j) ? v.w : 0.f;
+  return v;
+}
+
+// Port slots: P0 = (0,0), PR = (7,0), PD = (0,7) of every block, double-
+// buffered by step parity, plus a zero slot at index `threads`.
+__host__ __device__ inline int fused_slots(int threads) { return threads + 1; }
+
+// One super-tile whose block origin is (OX, OY) (in blocks).  All threads of
+// the CTA call it; it ends after the write-back.  ports: 6 * slots floats.
+template <int MODE>
+__device__ __forceinline__ void fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
+                                                int nsteps, const FGeo& f, int OX, int OY, const int* tab,
+                                                float* ports) {
+  const int t = threadIdx.x, nthreads = blockDim.x;
+  const int slots = fused_slots(nthreads), zero = nthreads;
+  const int nblk = f.n / kS;
+  float* P0 = ports;  // [2][slots] each
+  float* PR = ports + 2 * slots;
+  float* PD = ports + 4 * slots;
+
+  int bx = 0, by = 0;
+  bool active = false;
+  if (t < f.nb + f.nbox) {
+    fused_block<MODE>(t, f, tab, bx, by);
+    active = block_member(OX + bx, OY + by, nblk);
+  }
+  const int GX = OX + bx, GY = OY + by;
+  // neighbour ports (the zero slot where no staged member block is) and the
+  // ports' degrees: 2, 1, 1 inside the block plus the member neighbour blocks
+  int up = zero, lf = zero, rt = zero, dn = zero;
+  float d0 = 2.f, dr = 1.f, dd = 1.f;
+  if (active) {
+    const bool fu = block_member(GX, GY - 1, nblk), fl = block_member(GX - 1, GY, nblk);
+    const bool fr = block_member(GX + 1, GY, nblk), fd = block_member(GX, GY + 1, nblk);
+    d0 += (fu ? 1.f : 0.f) + (fl ? 1.f : 0.f);
+    dr += fr ? 1.f : 0.f;
+    dd += fd ? 1.f : 0.f;
+    if (fu) up = fused_owner<MODE>(bx, by - 1, f, zero);
+    if (fl) lf = fused_owner<MODE>(bx - 1, by, f, zero);
+    if (fr) rt = fused_owner<MODE>(bx + 1, by, f, zero);
+    if (fd) dn = fused_owner<MODE>(bx, by + 1, f, zero);
+  }
+
+  // stage: the block's 12 member chunks straight into registers
+  float u[kS * kS];
+#pragma unroll
+  for (int q = 0; q < kS * kS; ++q) u[q] = 0.f;
+  const size_t base = (size_t)GY * kS * (size_t)f.n + (size_t)GX * kS;
+  if (active) {
+    float4 c[12];
+#pragma unroll
+    for (int j = 0; j < kS; ++j) c[j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[8 + j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n + 4));
+#pragma unroll
+    for (int j = 0; j < kS; ++j) {
+      const float4 v = mask_chunk(c[j], 0, j);
+      u[j * kS + 0] = v.x;
+      u[j * kS + 1] = v.y;
+      u[j * kS + 2] = v.z;
+      u[j * kS + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = mask_chunk(c[8 + j], 4, j);
+      u[j * kS + 4] = v.x;
+      u[j * kS + 5] = v.y;
+      u[j * kS + 6] = v.z;
+      u[j * kS + 7] = v.w;
+    }
+  }
+  P0[t] = u[0];
+  PR[t] = u[kS - 1];
+  PD[t] = u[(kS - 1) * kS];
+  if (t == 0) {
+    P0[zero] = P0[slots + zero] = 0.f;
+    PR[zero] = PR[slots + zero] = 0.f;
+    PD[zero] = PD[slots + zero] = 0.f;
+  }
+  __syncthreads();
+
+  for (int s = 0; s < nsteps; ++s) {
+    const int cur = (s & 1) * slots, nxt = slots - cur;
+    if (active) {
+      const float vu = PD[cur + up], vl = PR[cur + lf], vr = P0[cur + rt], vd = P0[cur + dn];
+      block_step(u, a, vu, vl, vr, vd, d0, dr, dd);
+    }
+    P0[nxt + t] = u[0];
+    PR[nxt + t] = u[kS - 1];
+    PD[nxt + t] = u[(kS - 1) * kS];
+    __syncthreads();
+  }
+
+  // write back the super-tile's member blocks (not the boxes)
+  if (active && t < f.nb) {
+    float* o = out + base;
+#pragma unroll
+    for (int j = 0; j < kS; ++j)
+      *reinterpret_cast<float4*>(o + (size_t)j * f.n) =
+          make_float4(u[j * kS + 0], u[j * kS + 1], u[j * kS + 2], u[j * kS + 3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) =
+          make_float4(u[j * kS + 4], u[j * kS + 5], u[j * kS + 6], u[j * kS + 7]);
+    if (f.log_rho >= 3) {
+      // non-member cells of member tiles: the block's lower right quarter,
+      // and (rho >= 16) the non-member blocks right of this one in its tile
+      // row, up to the next member block
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 4; j < kS; ++j) *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) = z;
+      const int bpt = 1 << (f.log_rho - 3);  // blocks per tile side
+      const int tx = GX & (bpt - 1), ty = GY & (bpt - 1);
+      for (int q = tx + 1; q < bpt && (q & ty) != 0; ++q) {
+        float* p = o + (size_t)(q - tx) * kS;
+        for (int j = 0; j < kS; ++j) {
+          *reinterpret_cast<float4*>(p + (size_t)j * f.n) = z;
+          *reinterpret_cast<float4*>(p + (size_t)j * f.n + 4) = z;
+        }
       }
     }
   }
-  for (int i = threadIdx.x; i < 2 * img / 4; i += blockDim.x)
-    reinterpret_cast<float4*>(A)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
+}
 
-  // This thread's chunks (4 cells of a row): their image offsets, and per
-  // cell the coefficient c (a for a member, 0 otherwise) and the member
-  // 4-degree d, so that a step is u' = u + c * (neighbour sum - d * u) for
-  // every cell alike (a non-member holds 0 and stays 0).
-  const int nt_chunks = g.tiles * RHO * (RHO / 4);
-  const int chunks = nt_chunks + fused_box_chunks<M>();
-  int off[CT];
-  uint32_t mk[CT];  // member bits of the chunk's 4 cells
-  float cf[CT][4], dg[CT][4];
-#pragma unroll
-  for (int k = 0; k < CT; ++k) {
-    const int it = threadIdx.x + k * (int)blockDim.x;
-    off[k] = -1;
-    mk[k] = 0u;
-    if (it >= chunks) continue;
-    int lx, ly;
-    fused_chunk<RHO, M>(it, nt_chunks, tab, T, lx, ly);
-    const int gx0 = ox + lx, gy = oy + ly;
-    off[k] = (ly + M + 1) * P + lx + M;
-    if ((unsigned)gy < (unsigned)n && (unsigned)gx0 < (unsigned)n)
-      cp_async16(A + off[k], in + (size_t)gy * n + gx0);
-    // membership of the chunk's row and its neighbours, as bit masks (box
-    // chunks may lie left of or beyond the array: no members there)
-    const bool inx = (unsigned)gx0 < (unsigned)n;
-    const uint32_t mc = inx ? chunk_members<4>(gx0, gy, n) : 0u;
-    const uint32_t mu = inx ? chunk_members<4>(gx0, gy - 1, n) : 0u;
-    const uint32_t md = inx ? chunk_members<4>(gx0, gy + 1, n) : 0u;
-    const uint32_t ml = is_member(gx0 - 1, gy, n) ? 1u : 0u;
-    const uint32_t mr = is_member(gx0 + 4, gy, n) ? 1u : 0u;
-    const uint32_t row = ml | (mc << 1) | (mr << 5);  // bit j+1 = cell j of the chunk
-    mk[k] = mc;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t deg = ((mu >> i) & 1u) + ((md >> i) & 1u) + ((row >> i) & 1u) + ((row >> (i + 2)) & 1u);
-      const bool mem = (mc >> i) & 1u;
-      cf[k][i] = mem ? a : 0.0f;
-      dg[k][i] = mem ? (float)deg : 0.0f;
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // non-member cells of staged chunks -> 0, so that neighbour sums need no masks
-#pragma unroll
-  for (int k = 0; k < CT; ++k) {
-    if (off[k] < 0) continue;
-    float4 v = *reinterpret_cast<const float4*>(A + off[k]);
-    v.x = (mk[k] & 1u) ? v.x : 0.f;
-    v.y = (mk[k] & 2u) ? v.y : 0.f;
-    v.z = (mk[k] & 4u) ? v.z : 0.f;
-    v.w = (mk[k] & 8u) ? v.w : 0.f;
-    *reinterpret_cast<float4*>(A + off[k]) = v;
-  }
-  __syncthreads();
+__device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho) {
+  FGeo f;
+  f.n = n;
+  f.L = ilog2c(T) - 3;
+  int lw = 1, nb = 1;
+  for (int i = 0; i < f.L; ++i) nb *= 3;
+  for (int i = 0; i < (f.L + 1) / 2; ++i) lw *= 3;
+  f.lw = lw;
+  f.nb = nb;
+  f.W = M / kS;
+  f.nbox = 6 * f.W * f.W;
+  f.log_rho = log_rho;
+  return f;
+}
 
-  // nsteps updates A -> B -> A ...
-  for (int t = 0; t < nsteps; ++t) {
-#pragma unroll
-    for (int k = 0; k < CT; ++k) {
-      if (off[k] < 0) continue;
-      const float* p = A + off[k];
-      const float4 c = *reinterpret_cast<const float4*>(p);
-      const float4 u = *reinterpret_cast<const float4*>(p - P);
-      const float4 d = *reinterpret_cast<const float4*>(p + P);
-      const float l = p[-1], r = p[4];
-      float4 o;
-      o.x = fmaf(cf[k][0], fmaf(-dg[k][0], c.x, (u.x + d.x) + (l + c.y)), c.x);
-      o.y = fmaf(cf[k][1], fmaf(-dg[k][1], c.y, (u.y + d.y) + (c.x + c.z)), c.y);
-      o.z = fmaf(cf[k][2], fmaf(-dg[k][2], c.z, (u.z + d.z) + (c.y + c.w)), c.z);
-      o.w = fmaf(cf[k][3], fmaf(-dg[k][3], c.w, (u.w + d.w) + (c.z + r)), c.w);
-      *reinterpret_cast<float4*>(B + off[k]) = o;
-    }
-    __syncthreads();
-    float* tmp = A;
-    A = B;
-    B = tmp;
-  }
-
-  // write back the member tiles (the first nt_chunks chunks)
-#pragma unroll
-  for (int k = 0; k < CT; ++k) {
-    const int it = threadIdx.x + k * (int)blockDim.x;
-    if (off[k] < 0 || it >= nt_chunks) continue;
-    const int lx = off[k] % P - M, ly = off[k] / P - M - 1;
-    *reinterpret_cast<float4*>(out + (size_t)(oy + ly) * n + ox + lx) = *reinterpret_cast<const float4*>(A + off[k]);
+// BB: member block slots of the 2^L x 2^L box, in row-major order.
+__device__ __forceinline__ void bb_table(int* tab, const FGeo& f) {
+  const int side = 1 << f.L;
+  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+    const int x = j & (side - 1), y = j >> f.L;
+    if ((x & y) == 0) tab[bb_rank(x, y, f.L)] = j;
   }
 }
 
-template <int MODE, int LOG_RHO, int M>
-cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, cudaStream_t s) {
-  auto* k = diffusion_fused_kernel<MODE, LOG_RHO, M>;
+template <int MODE>
+__global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                              float a, int nsteps, int M, int log_rho, Geo g) {
+  extern __shared__ __align__(16) float fsm[];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  const FGeo f = make_fgeo(g.n, g.T, M, log_rho);
+  float* ports = fsm;
+  int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(blockDim.x));
+  if (MODE == kBB) {
+    bb_table(tab, f);
+    __syncthreads();
+  }
+  fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports);
+}
+
+template <int MODE>
+cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
+               cudaStream_t s) {
+  auto* k = diffusion_fused_kernel<MODE>;
   cudaError_t e = allow_smem((const void*)k, L.smem);
   if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, L.geo);
+  k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo);
   return cudaGetLastError();
 }
 
-template <int MODE, int M>
-cudaError_t by_rho(int log_rho, const Launch& L, const float* in, float* out, float a, int nsteps, cudaStream_t s) {
-  switch (log_rho) {
-    case 2: return go<MODE, 2, M>(L, in, out, a, nsteps, s);
-    case 3: return go<MODE, 3, M>(L, in, out, a, nsteps, s);
-    case 4: return go<MODE, 4, M>(L, in, out, a, nsteps, s);
-    case 5: return go<MODE, 5, M>(L, in, out, a, nsteps, s);
-    default: return cudaErrorInvalidValue;
-  }
+int member_blocks(int T) {
+  int nb = 1;
+  for (int i = 0; i < ilog2c(T) - 3; ++i) nb *= 3;
+  return nb;
 }
 
 }  // namespace
 
-int fused_margin(int steps_per_launch) { return steps_per_launch <= 4 ? 4 : 8; }
+// Margin of a fused launch: the smallest multiple of the block side >= spl.
+int fused_margin(int steps_per_launch) { return (steps_per_launch + kS - 1) / kS * kS; }
 
-int fused_smem_bytes(const Geo& g, int margin) {
-  const int P = fused_pitch(g.T, margin);
-  return tab_words(g.tiles) * 4 + 2 * (g.T + 2 * margin + 2) * P * 4;
+// Threads of a fused launch: one per member block and box block, rounded up
+// to whole warps; 0 if the super-tile does not fit (side < 16 or < 2 M, a
+// margin that is not a multiple of 8, more than 512 threads).
+int fused_threads(const Geo& g, int rho, int margin) {
+  (void)rho;
+  if (g.T < 2 * kS || g.T < 2 * margin || margin < kS || margin % kS != 0) return 0;
+  const int W = margin / kS;
+  const int t = (member_blocks(g.T) + 6 * W * W + 31) / 32 * 32;
+  return t > 512 ? 0 : t;
 }
 
-// Threads of a fused launch: every chunk owned by one thread, at most
-// kFusedChunksPerThread each; 0 if that needs more than 512 threads.
-int fused_threads(const Geo& g, int rho, int margin) {
-  const int chunks = g.tiles * rho * (rho / 4) + (margin / 4) * 6 * margin;
-  int t = ((chunks + kFusedChunksPerThread - 1) / kFusedChunksPerThread + 31) / 32 * 32;
-  if (t < 32) t = 32;
-  return t > 512 ? 0 : t;
+int fused_smem_bytes(const Geo& g, int margin) {
+  return 6 * fused_slots(fused_threads(g, 0, margin)) * 4 + member_blocks(g.T) * 4;
 }
 
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
                                    float a, int nsteps, cudaStream_t s) {
-  const int M = margin;
-  if (nsteps < 1 || nsteps > M) return cudaErrorInvalidValue;
-  if (mode == kLambda)
-    return M == 4 ? by_rho<kLambda, 4>(log_rho, L, in, out, a, nsteps, s)
-                  : by_rho<kLambda, 8>(log_rho, L, in, out, a, nsteps, s);
-  return M == 4 ? by_rho<kBB, 4>(log_rho, L, in, out, a, nsteps, s) : by_rho<kBB, 8>(log_rho, L, in, out, a, nsteps, s);
+  if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads)
+    return cudaErrorInvalidValue;
+  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, s)
+                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, s);
 }
 
 }  // namespace fractal

@@ -49,6 +49,10 @@ cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_
 int ca_fused_smem_bytes(const Geo& g, int margin);
 int ca_fused_threads(const Geo& g, int margin);
 
+// Grid and Geo of super-tiles of `levels` tile levels (threads and shared
+// memory left 0); false if levels or the grid are out of range.
+bool supertile_grid(int k, int log_rho, int mode, int levels, Launch& L);
+
 // Launch geometry of the kernels for level k, tile side 2^log_rho, mode,
 // dtype and `levels` tile levels per CTA (false if it does not fit).
 bool plan_geometry(int k, int log_rho, int mode, int dtype, int levels, Launch& step, Launch& aux, Launch& tma,

@@ -287,19 +287,23 @@ def test_diffusion_parity(fr, k, rho, mode, sched):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("spl", [2, 3, 4, 8])
-@pytest.mark.parametrize("k,rho", [(5, 4), (6, 8), (8, 4), (8, 8), (9, 16), (10, 32), (10, 8)])
+@pytest.mark.parametrize("spl", [2, 3, 4, 8, 16, 32])
+@pytest.mark.parametrize("k,rho", [(5, 4), (6, 8), (8, 4), (8, 8), (9, 16), (10, 32), (10, 8), (11, 16)])
 def test_diffusion_fused_parity(fr, k, rho, mode, spl):
     # several steps per launch: same field as the oracle, same result buffer,
     # cells outside member tiles untouched
     n = 1 << k
     plan = fr.fractal_map(k, rho, mode)
+    if (1 << k) < 2 * (-(-spl // 8) * 8):
+        with pytest.raises(fr.FractalError):       # no super-tile of side >= 2 * margin
+            fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
+        return
     fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
     assert plan.info()["steps_per_launch"][1] == spl
     u0 = synth.uniform_f32(70 + k, n)
     mask = domain(k).mask
     cover = tile_cover(n, rho)
-    for steps in (1, 5, 8, 13):
+    for steps in (1, 5, 8, 13, 2 * spl + 1):
         want = oracle.diffusion_run(u0.astype(np.float64), steps, 0.2, domain(k))
         got = run_diffusion(fr, plan, u0, steps)
         assert rel_err(got, want, mask)[0] <= 2e-6, (steps, rel_err(got, want, mask))
@@ -309,12 +313,13 @@ def test_diffusion_fused_parity(fr, k, rho, mode, spl):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_diffusion_fused_1000_steps(fr, mode):
+@pytest.mark.parametrize("spl", [8, 32])
+def test_diffusion_fused_1000_steps(fr, mode, spl):
     k, n = 10, 1024
     u0 = synth.uniform_f32(3, n)
     want = oracle.diffusion_run(u0.astype(np.float64), 1000, 0.2, domain(k))
     plan = fr.fractal_map(k, 8, mode)
-    fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, 8)
+    fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
     got = run_diffusion(fr, plan, u0, 1000)
     err, raw = rel_err(got, want, domain(k).mask)
     assert err <= 1e-4, (err, raw)
@@ -336,7 +341,7 @@ def test_fused_needs_room(fr):
     with pytest.raises(fr.FractalError):
         fr.fractal_plan_set_steps_per_launch(fr.fractal_map(3, 4), fr.FRACTAL_F32, 8)   # super-tile < 16
     with pytest.raises(fr.FractalError):
-        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(10, 8), fr.FRACTAL_F32, 9)
+        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(10, 8), fr.FRACTAL_F32, 33)
     p = fr.fractal_map(10, 8)
     fr.fractal_plan_set_steps_per_launch(p, fr.FRACTAL_F32, 1)
     assert p.info()["steps_per_launch"] == [1, 1]
