@@ -277,6 +277,114 @@ int fractal_set_l2_fetch_granularity(int bytes);
 /* Current value of that hint for the current context, in bytes. */
 int fractal_get_l2_fetch_granularity(int* bytes);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent gaskets of uneven levels in one launch.
+ *
+ * The diffusion step of fractal_step_diffusion applied to `count` separate
+ * instances, instance i of level k_i in its own n_i x n_i arrays (n_i =
+ * 2^k_i).  One persistent launch covers all of them: its CTAs walk the
+ * instances' member super-tiles in order, an instance's super-tiles forming
+ * the contiguous range [first_i, first_i + 3^R_i) of a per-instance offset
+ * table (prefix sums); a CTA finds its instance by binary search on that
+ * table and its super-tile by lambda(omega) at level R_i = k_i - log2(T)
+ * (Theorem 1).  Each super-tile runs the temporally fused diffusion (several
+ * steps per launch, one 8 x 8 block of the gasket per thread).  Results are
+ * bit for bit those of fractal_step_diffusion on each instance with the same
+ * steps per launch.  Not in the paper: the batching is this library's.
+ * ------------------------------------------------------------------------ */
+typedef struct fractal_batch_s* fractal_batch_t;
+
+typedef struct fractal_batch_info {
+  int32_t count;            /* instances */
+  int32_t k_min, k_max;     /* smallest and largest level */
+  int32_t supertile;        /* super-tile side T in cells (same for all instances) */
+  int32_t steps_per_launch; /* temporal fusion: steps one launch advances */
+  int32_t ctas;             /* persistent grid: CTAs per launch */
+  int32_t threads;          /* threads per CTA */
+  int32_t smem_bytes;       /* dynamic shared memory per CTA */
+  int64_t supertiles;       /* member super-tiles over all instances: sum 3^R_i */
+  int64_t members;          /* member cells over all instances: sum 3^k_i */
+  int32_t bound;            /* 1 after fractal_batch_bind */
+  int32_t graph_steps;      /* steps in the captured graph, 0 if none */
+} fractal_batch_info;
+
+/*
+ * fractal_batch_create -- a batch of `count` (1 .. 65536) instances with the
+ * levels ks[0..count-1] (host array; 4 <= k_i <= 16).  The batch owns a small
+ * device table (the instances' pointers, sizes and super-tile offsets), a
+ * non-blocking stream used only to capture graphs, and any captured graph.
+ * Default: 8 steps per launch, the largest super-tile side <= 256 that every
+ * instance holds.  Belongs to the device current at the call.  Errors:
+ * FRACTAL_EINVAL, FRACTAL_ENOMEM, FRACTAL_ECUDA.
+ */
+int fractal_batch_create(int count, const int32_t* ks, fractal_batch_t* batch);
+
+/* Free a batch and its graph (NULL accepted); waits for nothing. */
+int fractal_batch_destroy(fractal_batch_t batch);
+
+/*
+ * fractal_batch_bind -- the instances' buffers: dev_a[i] and dev_b[i] (host
+ * arrays of `count` device pointers) are distinct n_i*n_i float32 arrays,
+ * 16-byte aligned.  Copies the table to the device (synchronous); may be
+ * called again with other buffers, which a captured graph then uses too.
+ * Errors: FRACTAL_EINVAL (NULL, equal or misaligned pointers), FRACTAL_ECUDA.
+ */
+int fractal_batch_bind(fractal_batch_t batch, float* const* dev_a, float* const* dev_b);
+
+/*
+ * fractal_batch_configure -- super-tile side T (a power of two, 16 <= T <=
+ * 2^k_min, T >= 2 * margin, at most 512 threads per CTA) and steps per launch
+ * spl (1 .. 32; margin = spl rounded up to a multiple of 8).  T = 0 keeps
+ * the current side.  Drops a captured graph.  Synchronous when bound (the
+ * offset table is rewritten).  Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
+ */
+int fractal_batch_configure(fractal_batch_t batch, int supertile, int steps_per_launch);
+
+/*
+ * fractal_batch_step_diffusion -- `steps` diffusion steps (coefficient a, as
+ * fractal_step_diffusion) on every instance, in ceil(steps / spl) persistent
+ * launches (one more if needed for the parity): after the call each
+ * instance's state is in dev_a[i] when `steps` is even and in dev_b[i] when
+ * it is odd.  Asynchronous on `stream`.  Errors: FRACTAL_EINVAL (unbound,
+ * steps < 0, a not finite), FRACTAL_ECUDA.
+ */
+int fractal_batch_step_diffusion(fractal_batch_t batch, float a, int steps, void* stream);
+
+/*
+ * fractal_batch_reduce -- per-instance sums over the member cells of dev_a[i]
+ * (which = 0) or dev_b[i] (which = 1): dev_out[i] (device array of `count`
+ * doubles).  Each super-tile's FP32 values are summed in FP64 in a fixed
+ * order, then each instance's super-tiles in order: deterministic.
+ * Asynchronous.  Errors: FRACTAL_EINVAL, FRACTAL_ENOMEM, FRACTAL_ECUDA.
+ */
+int fractal_batch_reduce(fractal_batch_t batch, int which, double* dev_out, void* stream);
+
+/*
+ * fractal_batch_autotune -- time every valid (super-tile side, steps per
+ * launch in {8, 16, 32}) on the bound buffers (launches dev_a -> dev_b,
+ * `reps` timed after two untimed; dev_a is only read, dev_b overwritten) and
+ * keep the fastest per step.  Synchronises `stream`.  *best_us (nullable):
+ * the best mean step time.  Errors: FRACTAL_EINVAL, FRACTAL_ENOMEM,
+ * FRACTAL_ECUDA.
+ */
+int fractal_batch_autotune(fractal_batch_t batch, float a, int reps, float* best_us, void* stream);
+
+/*
+ * fractal_batch_graph_capture -- capture the launches of
+ * fractal_batch_step_diffusion(batch, a, steps) into a CUDA graph owned by
+ * the batch (replacing any earlier one) and instantiate it.  Captured on the
+ * batch's own stream; nothing runs.  Errors: FRACTAL_EINVAL (unbound, steps
+ * < 1), FRACTAL_ECUDA.
+ */
+int fractal_batch_graph_capture(fractal_batch_t batch, float a, int steps);
+
+/* Launch the captured graph on `stream` (asynchronous).  Errors:
+ * FRACTAL_EINVAL (no graph), FRACTAL_ECUDA. */
+int fractal_batch_graph_launch(fractal_batch_t batch, void* stream);
+
+/* Fill *info.  Errors: FRACTAL_EINVAL (NULL). */
+int fractal_batch_get_info(fractal_batch_t batch, fractal_batch_info* info);
+
 #ifdef __cplusplus
 }
 #endif

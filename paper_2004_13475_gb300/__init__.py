@@ -39,6 +39,9 @@ EXPORTS = (
     "fractal_reduce_async", "fractal_set_l2_fetch_granularity", "fractal_get_l2_fetch_granularity",
     "fractal_plan_set_schedule", "fractal_plan_device_status", "fractal_reduce_noalloc",
     "fractal_plan_autotune", "fractal_plan_set_steps_per_launch",
+    "fractal_batch_create", "fractal_batch_destroy", "fractal_batch_bind", "fractal_batch_configure",
+    "fractal_batch_step_diffusion", "fractal_batch_reduce", "fractal_batch_autotune",
+    "fractal_batch_graph_capture", "fractal_batch_graph_launch", "fractal_batch_get_info",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -74,6 +77,18 @@ class PlanInfo(ctypes.Structure):
         return out
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int32), ("k_min", ctypes.c_int32), ("k_max", ctypes.c_int32),
+        ("supertile", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32), ("ctas", ctypes.c_int32),
+        ("threads", ctypes.c_int32), ("smem_bytes", ctypes.c_int32), ("supertiles", ctypes.c_int64),
+        ("members", ctypes.c_int64), ("bound", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -106,6 +121,16 @@ def _load() -> ctypes.CDLL:
         "fractal_reduce_noalloc": (I, [I, I, VP, I, VP, VP]),
         "fractal_plan_autotune": (I, [P, I, VP, VP, I, ctypes.POINTER(F), VP]),
         "fractal_plan_set_steps_per_launch": (I, [P, I, I]),
+        "fractal_batch_create": (I, [I, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(P)]),
+        "fractal_batch_destroy": (I, [P]),
+        "fractal_batch_bind": (I, [P, ctypes.POINTER(VP), ctypes.POINTER(VP)]),
+        "fractal_batch_configure": (I, [P, I, I]),
+        "fractal_batch_step_diffusion": (I, [P, F, I, VP]),
+        "fractal_batch_reduce": (I, [P, I, VP, VP]),
+        "fractal_batch_autotune": (I, [P, F, I, ctypes.POINTER(F), VP]),
+        "fractal_batch_graph_capture": (I, [P, F, I]),
+        "fractal_batch_graph_launch": (I, [P, VP]),
+        "fractal_batch_get_info": (I, [P, ctypes.POINTER(BatchInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -261,6 +286,87 @@ def fractal_get_l2_fetch_granularity() -> int:
     v = ctypes.c_int()
     _check(_load().fractal_get_l2_fetch_granularity(ctypes.byref(v)), "fractal_get_l2_fetch_granularity")
     return v.value
+
+
+class Batch:
+    """Owner of a ``fractal_batch_t``: many gaskets of uneven levels advanced
+    by one persistent launch (include/fractal.h, "Batches")."""
+
+    def __init__(self, handle: int, ks):
+        self._h = ctypes.c_void_p(handle)
+        self.ks = list(ks)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h:
+            raise ValueError("batch is closed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = BatchInfo()
+        _check(_load().fractal_batch_get_info(self.handle, ctypes.byref(inf)), "fractal_batch_get_info")
+        return inf.as_dict()
+
+    def close(self) -> None:
+        if self._h:
+            _load().fractal_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fractal_batch_create(ks) -> Batch:
+    arr = (ctypes.c_int32 * len(ks))(*[int(k) for k in ks])
+    h = ctypes.c_void_p()
+    _check(_load().fractal_batch_create(len(ks), arr, ctypes.byref(h)), "fractal_batch_create")
+    return Batch(h.value, ks)
+
+
+def fractal_batch_bind(batch: Batch, a_list, b_list) -> None:
+    """a_list, b_list: per-instance device buffers (tensors or addresses)."""
+    n = len(batch.ks)
+    if len(a_list) != n or len(b_list) != n:
+        raise ValueError("one buffer pair per instance")
+    A = (ctypes.c_void_p * n)(*[_ptr(x) for x in a_list])
+    B = (ctypes.c_void_p * n)(*[_ptr(x) for x in b_list])
+    _check(_load().fractal_batch_bind(batch.handle, A, B), "fractal_batch_bind")
+
+
+def fractal_batch_configure(batch: Batch, supertile: int, steps_per_launch: int) -> None:
+    _check(_load().fractal_batch_configure(batch.handle, int(supertile), int(steps_per_launch)),
+           "fractal_batch_configure")
+
+
+def fractal_batch_step_diffusion(batch: Batch, coef: float, steps: int, stream=None) -> int:
+    """Run `steps` steps on every instance; returns 0 if the results are in the
+    a buffers, 1 if in the b buffers."""
+    _check(_load().fractal_batch_step_diffusion(batch.handle, float(coef), int(steps), _stream(stream)),
+           "fractal_batch_step_diffusion")
+    return steps % 2
+
+
+def fractal_batch_reduce(batch: Batch, which: int, dev_out, stream=None) -> None:
+    _check(_load().fractal_batch_reduce(batch.handle, int(which), _ptr(dev_out), _stream(stream)),
+           "fractal_batch_reduce")
+
+
+def fractal_batch_autotune(batch: Batch, coef: float = 0.2, reps: int = 3, stream=None) -> float:
+    best = ctypes.c_float(-1.0)
+    _check(_load().fractal_batch_autotune(batch.handle, float(coef), int(reps), ctypes.byref(best),
+                                          _stream(stream)), "fractal_batch_autotune")
+    return best.value
+
+
+def fractal_batch_graph_capture(batch: Batch, coef: float, steps: int) -> None:
+    _check(_load().fractal_batch_graph_capture(batch.handle, float(coef), int(steps)), "fractal_batch_graph_capture")
+
+
+def fractal_batch_graph_launch(batch: Batch, stream=None) -> None:
+    _check(_load().fractal_batch_graph_launch(batch.handle, _stream(stream)), "fractal_batch_graph_launch")
 
 
 def fractal_strerror(status: int) -> str:

@@ -354,6 +354,89 @@ __global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __res
   fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports);
 }
 
+// ---------------------------------------------------------------- batches ---
+// Persistent launch over the member super-tiles of many instances: CTA c
+// takes items c, c + gridDim.x, ...; item w belongs to the last instance
+// whose first item is <= w (binary search on the prefix table), and is that
+// instance's super-tile lambda(w - first) at level R (Theorem 1).
+__device__ __forceinline__ int batch_instance(const BatchInst* __restrict__ inst, int count, int64_t w) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].first <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(512) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
+                                                              int64_t items, int which, float a, int nsteps, int M,
+                                                              int T) {
+  extern __shared__ __align__(16) float fsm[];
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const BatchInst I = inst[batch_instance(inst, count, w)];
+    const int64_t om = w - I.first;
+    int sx, sy;
+    warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
+    const FGeo f = make_fgeo(I.n, T, M, 3);
+    fused_supertile<kLambda>(which ? I.b : I.a, which ? I.a : I.b, a, nsteps, f, sx << f.L, sy << f.L, nullptr, fsm);
+  }
+}
+
+// Per-super-tile sums of the member cells (FP32 within a 16-byte chunk, FP64
+// above; fixed order), then per instance in item order.
+__global__ void __launch_bounds__(512) batch_partials_kernel(const BatchInst* __restrict__ inst, int count,
+                                                             int64_t items, int which, int T,
+                                                             double* __restrict__ partials) {
+  __shared__ double warp_sum[16];
+  const int L = ilog2c(T) - 3;
+  int nb = 1, lw = 1;
+  for (int i = 0; i < L; ++i) nb *= 3;
+  for (int i = 0; i < (L + 1) / 2; ++i) lw *= 3;
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const BatchInst I = inst[batch_instance(inst, count, w)];
+    const int64_t om = w - I.first;
+    int sx, sy;
+    warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
+    const float* buf = which ? I.b : I.a;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      int bx, by;
+      lambda_scalar((uint32_t)(t % lw), (uint32_t)(t / lw), L, bx, by);
+      const float* p = buf + ((size_t)((sy << L) + by) * kS) * (size_t)I.n + (size_t)((sx << L) + bx) * kS;
+#pragma unroll
+      for (int j = 0; j < kS; ++j) {
+        const float4 v = mask_chunk(__ldg(reinterpret_cast<const float4*>(p + (size_t)j * I.n)), 0, j);
+        acc += (double)((v.x + v.y) + (v.z + v.w));
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = mask_chunk(__ldg(reinterpret_cast<const float4*>(p + (size_t)j * I.n + 4)), 4, j);
+        acc += (double)((v.x + v.y) + (v.z + v.w));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += warp_sum[i];
+      partials[w] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void batch_sums_kernel(const BatchInst* __restrict__ inst, int count, int64_t items,
+                                  const double* __restrict__ partials, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t e = i + 1 < count ? inst[i + 1].first : items;
+  double s = 0.0;
+  for (int64_t w = inst[i].first; w < e; ++w) s += partials[w];
+  out[i] = s;
+}
+
 template <int MODE>
 cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
                cudaStream_t s) {
@@ -388,6 +471,30 @@ int fused_threads(const Geo& g, int rho, int margin) {
 
 int fused_smem_bytes(const Geo& g, int margin) {
   return 6 * fused_slots(fused_threads(g, 0, margin)) * 4 + member_blocks(g.T) * 4;
+}
+
+int fused_batch_smem_bytes(int threads) { return 6 * fused_slots(threads) * 4; }
+
+const void* fused_batch_kernel() { return (const void*)diffusion_batch_kernel; }
+
+cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
+                                   int margin, int T, int ctas, int threads, cudaStream_t s) {
+  if (nsteps < 1 || nsteps > margin || ctas < 1) return cudaErrorInvalidValue;
+  Geo g{};
+  g.T = T;
+  if (fused_threads(g, 0, margin) != threads) return cudaErrorInvalidValue;
+  diffusion_batch_kernel<<<ctas, threads, fused_batch_smem_bytes(threads), s>>>(inst, count, items, which, a, nsteps,
+                                                                               margin, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items, int which, int T, int ctas,
+                                double* partials, double* out, cudaStream_t s) {
+  batch_partials_kernel<<<ctas, 256, 0, s>>>(inst, count, items, which, T, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_sums_kernel<<<(count + 127) / 128, 128, 0, s>>>(inst, count, items, partials, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,

@@ -49,6 +49,27 @@ cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_
 int ca_fused_smem_bytes(const Geo& g, int margin);
 int ca_fused_threads(const Geo& g, int margin);
 
+// One instance of a batch (device table entry).
+struct BatchInst {
+  float* a;       // the instance's two n x n buffers
+  float* b;
+  int64_t first;  // its first item (member super-tile) in the batch
+  int32_t n;      // 2^k
+  int32_t R;      // super-tile levels of its grid: k - log2(T)
+  int32_t lwR;    // 3^ceil(R/2)
+  int32_t pad;
+};
+
+// Persistent fused diffusion over `items` super-tiles of side T of the
+// instances (which = 0: a -> b, 1: b -> a); threads = fused_threads for T
+// and margin.  Per-instance member sums through `partials` (items doubles).
+cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
+                                   int margin, int T, int ctas, int threads, cudaStream_t s);
+cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items, int which, int T, int ctas,
+                                double* partials, double* out, cudaStream_t s);
+int fused_batch_smem_bytes(int threads);
+const void* fused_batch_kernel();
+
 // Grid and Geo of super-tiles of `levels` tile levels (threads and shared
 // memory left 0); false if levels or the grid are out of range.
 bool supertile_grid(int k, int log_rho, int mode, int levels, Launch& L);
