@@ -15,6 +15,8 @@ from .gasket import (  # noqa: F401
     block_table,
     ca_step,
     ca_run,
+    diffusion_loss_gradients,
+    diffusion_matrix,
     diffusion_run,
     diffusion_step,
     embed,

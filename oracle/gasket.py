@@ -308,3 +308,67 @@ def diffusion_run(u0: np.ndarray, steps: int, a: float, dom: Optional[Domain] = 
     for _ in range(steps):
         u = diffusion_step(dom, u, a, kap)
     return dom.put(u, np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Differentiation of the diffusion (not in the paper: the gradient of a
+# loss through the FDM steps named in Sec. 1, by the discrete adjoint)
+# ---------------------------------------------------------------------------
+
+
+def diffusion_matrix(dom: Domain, a: float, kappa: Optional[np.ndarray] = None):
+    """The step as a sparse matrix A over the members: u_{t+1} = A u_t.
+
+    Row c: A_cc = 1 - a * sum_nb g_{c,nb}, A_{c,nb} = a * g_{c,nb} for every
+    member neighbour nb in N4(c), g as in ``diffusion_step`` (1, or
+    (kappa_c + kappa_nb) / 2).  Pinned against ``diffusion_step``.
+    """
+    import scipy.sparse as sp
+    m = dom.m
+    valid = dom.nb4 >= 0
+    rows = np.repeat(np.arange(m), 4)[valid.reshape(-1)]
+    cols = dom.nb4.reshape(-1)[valid.reshape(-1)]
+    if kappa is None:
+        g = np.ones(rows.size)
+    else:
+        kap = np.asarray(kappa, dtype=np.float64)
+        g = 0.5 * (kap[rows] + kap[cols])
+    off = sp.csr_matrix((a * g, (rows, cols)), shape=(m, m))
+    diag = 1.0 - np.asarray(off.sum(axis=1)).reshape(-1)
+    return (off + sp.diags(diag)).tocsr()
+
+
+def diffusion_loss_gradients(dom: Domain, u0: np.ndarray, kappa: np.ndarray, target: np.ndarray,
+                             steps: int, a: float):
+    """Loss J = sum over members of (u_T - target)^2, u_T after ``steps`` steps
+    of ``diffusion_step`` with conductivity ``kappa``, and its gradients, FP64.
+
+    Discrete adjoint, every state kept:
+      u_{t+1} = A u_t                      (A = diffusion_matrix(dom, a, kappa))
+      p_T = dJ/du_T = 2 (u_T - target)
+      p_t = A^T p_{t+1}                    (explicit transpose)
+      dJ/du_0 = p_0
+      dJ/dkappa_c = sum_{t < T} p_{t+1}^T (d A / d kappa_c) u_t
+                  = sum_t sum_{nb in N4(c)} (a / 2) (u_t,nb - u_t,c) (p_{t+1},c - p_{t+1},nb)
+    (A u depends on kappa_c through g_{c,nb} = (kappa_c + kappa_nb) / 2 in row
+    c and in the rows of c's neighbours).  Member vectors in, member vectors
+    out: returns (J, dJ/du_0, dJ/dkappa).  Pinned by finite differences.
+    """
+    A = diffusion_matrix(dom, a, kappa)
+    AT = A.T.tocsr()
+    u = [np.asarray(u0, dtype=np.float64)]
+    for _ in range(steps):
+        u.append(A @ u[-1])
+    r = u[-1] - np.asarray(target, dtype=np.float64)
+    J = float(np.sum(r * r))
+    p = 2.0 * r
+    gk = np.zeros(dom.m)
+    valid = dom.nb4 >= 0
+    for t in range(steps - 1, -1, -1):
+        upad = np.append(u[t], 0.0)
+        ppad = np.append(p, 0.0)
+        du = upad[dom.nb4] - u[t][:, None]
+        dp = p[:, None] - ppad[dom.nb4]
+        gk += 0.5 * a * np.where(valid, du * dp, 0.0).sum(axis=1)
+        p = AT @ p
+    return J, p, gk
