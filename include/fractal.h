@@ -278,6 +278,63 @@ int fractal_set_l2_fetch_granularity(int bytes);
 int fractal_get_l2_fetch_granularity(int* bytes);
 
 /* ------------------------------------------------------------------------
+ * Differentiation: diffusion with a per-cell conductivity and its adjoint.
+ *
+ * Not in the paper (which names the FDM time step, Sec. 1): the step of
+ * fractal_step_diffusion with edge conductances g_{c,nb} = (kappa_c +
+ * kappa_nb) / 2,
+ *   u'_c = u_c + a * sum_{nb in N4(c), nb member} g_{c,nb} (u_nb - u_c),
+ * i.e. u_{t+1} = A u_t with A symmetric (heat is conserved; stable for
+ * a * 3 * max kappa < 1), and the reverse step that carries p_{t+1} =
+ * dJ/du_{t+1} of a loss J back one step:
+ *   p_t = A^T p_{t+1} = A p_{t+1},
+ *   dJ/dkappa_c += (a / 2) sum_{nb} (u_t,nb - u_t,c) (p_{t+1},c - p_{t+1},nb).
+ * Both use the plan's level k (k >= 3) and launch mode; they run one thread
+ * per member 8 x 8 block (lambda map at the block level, Theorem 1), one step
+ * per launch, and write whole member 8 x 8 blocks (0 at non-members).  All
+ * arrays are n*n float32 device arrays, 16-byte aligned.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * fractal_step_diffusion_kappa -- `steps` steps with conductivity dev_kappa
+ * (read only), ping-pong dev_a -> dev_b -> dev_a ... as fractal_step_diffusion
+ * (result in dev_a for even `steps`, dev_b for odd).  Errors: FRACTAL_EINVAL
+ * (NULL, equal or misaligned buffers, k < 3, steps < 0, a not finite),
+ * FRACTAL_ECUDA.
+ */
+int fractal_step_diffusion_kappa(fractal_plan_t plan, float* dev_a, float* dev_b, const float* dev_kappa, float a,
+                                 int steps, void* stream);
+
+/*
+ * fractal_step_diffusion_kappa_f64 -- the same with the state in doubles
+ * (dev_a, dev_b: n*n double arrays; dev_kappa still float).  An FP32
+ * trajectory rounds the state every step; through differences of neighbour
+ * values those roundings alone move the gradients of a 200-step run by a few
+ * 1e-4 of their scale, so gradient work that must stay within 1e-4 of an
+ * FP64 reference keeps the state in doubles.  Errors as above.
+ */
+int fractal_step_diffusion_kappa_f64(fractal_plan_t plan, double* dev_a, double* dev_b, const float* dev_kappa,
+                                     double a, int steps, void* stream);
+
+/*
+ * fractal_adjoint_diffusion_step -- one reverse step: dev_p_out = A dev_p_in
+ * (A from dev_kappa and a) and dev_gkappa += the step's contribution to
+ * dJ/dkappa, with dev_u the forward state u_t that entered the step and
+ * dev_p_in = dJ/du_{t+1}.  dev_gkappa is an n*n array of DOUBLES (the sum
+ * over steps cancels; each contribution, a product of differences of close
+ * FP32 values, is formed exactly in FP64); its non-member cells in member
+ * 8 x 8 blocks are set to 0.  All five arrays distinct.  Errors:
+ * FRACTAL_EINVAL, FRACTAL_ECUDA.
+ */
+int fractal_adjoint_diffusion_step(fractal_plan_t plan, const float* dev_u, const float* dev_p_in, float* dev_p_out,
+                                   const float* dev_kappa, double* dev_gkappa, float a, void* stream);
+
+/* The reverse step with u and p in doubles (see fractal_step_diffusion_kappa_f64). */
+int fractal_adjoint_diffusion_step_f64(fractal_plan_t plan, const double* dev_u, const double* dev_p_in,
+                                       double* dev_p_out, const float* dev_kappa, double* dev_gkappa, double a,
+                                       void* stream);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.
  *
  * The diffusion step of fractal_step_diffusion applied to `count` separate

@@ -42,6 +42,8 @@ EXPORTS = (
     "fractal_batch_create", "fractal_batch_destroy", "fractal_batch_bind", "fractal_batch_configure",
     "fractal_batch_step_diffusion", "fractal_batch_reduce", "fractal_batch_autotune",
     "fractal_batch_graph_capture", "fractal_batch_graph_launch", "fractal_batch_get_info",
+    "fractal_step_diffusion_kappa", "fractal_adjoint_diffusion_step",
+    "fractal_step_diffusion_kappa_f64", "fractal_adjoint_diffusion_step_f64",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -131,6 +133,10 @@ def _load() -> ctypes.CDLL:
         "fractal_batch_graph_capture": (I, [P, F, I]),
         "fractal_batch_graph_launch": (I, [P, VP]),
         "fractal_batch_get_info": (I, [P, ctypes.POINTER(BatchInfo)]),
+        "fractal_step_diffusion_kappa": (I, [P, VP, VP, VP, F, I, VP]),
+        "fractal_adjoint_diffusion_step": (I, [P, VP, VP, VP, VP, VP, F, VP]),
+        "fractal_step_diffusion_kappa_f64": (I, [P, VP, VP, VP, D, I, VP]),
+        "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -286,6 +292,35 @@ def fractal_get_l2_fetch_granularity() -> int:
     v = ctypes.c_int()
     _check(_load().fractal_get_l2_fetch_granularity(ctypes.byref(v)), "fractal_get_l2_fetch_granularity")
     return v.value
+
+
+def fractal_step_diffusion_kappa(plan: Plan, a, b, kappa, coef: float, steps: int, stream=None):
+    """`steps` diffusion steps with per-cell conductivity `kappa` (float32 state);
+    returns the buffer holding the result."""
+    _check(_load().fractal_step_diffusion_kappa(plan.handle, _ptr(a), _ptr(b), _ptr(kappa), float(coef), int(steps),
+                                                _stream(stream)), "fractal_step_diffusion_kappa")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_step_diffusion_kappa_f64(plan: Plan, a, b, kappa, coef: float, steps: int, stream=None):
+    """The same with a float64 state (a, b float64; kappa float32)."""
+    _check(_load().fractal_step_diffusion_kappa_f64(plan.handle, _ptr(a), _ptr(b), _ptr(kappa), float(coef),
+                                                    int(steps), _stream(stream)), "fractal_step_diffusion_kappa_f64")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_adjoint_diffusion_step(plan: Plan, u, p_in, p_out, kappa, gkappa, coef: float, stream=None) -> None:
+    """One reverse step: p_out = A p_in, gkappa (float64) += the step's dJ/dkappa (u = the forward state u_t)."""
+    _check(_load().fractal_adjoint_diffusion_step(plan.handle, _ptr(u), _ptr(p_in), _ptr(p_out), _ptr(kappa),
+                                                  _ptr(gkappa), float(coef), _stream(stream)),
+           "fractal_adjoint_diffusion_step")
+
+
+def fractal_adjoint_diffusion_step_f64(plan: Plan, u, p_in, p_out, kappa, gkappa, coef: float, stream=None) -> None:
+    """The reverse step with float64 u and p."""
+    _check(_load().fractal_adjoint_diffusion_step_f64(plan.handle, _ptr(u), _ptr(p_in), _ptr(p_out), _ptr(kappa),
+                                                      _ptr(gkappa), float(coef), _stream(stream)),
+           "fractal_adjoint_diffusion_step_f64")
 
 
 class Batch:

@@ -288,6 +288,49 @@ int check_plan(const fractal_plan_s* p) { return p ? FRACTAL_OK : FRACTAL_EINVAL
 
 }  // namespace
 
+namespace {
+
+// Steps with per-cell conductivity, state type T (float or double).
+template <typename T>
+int step_kappa(fractal_plan_t p, T* a, T* b, const float* kappa, T coef, int steps, void* stream) {
+  if (check_plan(p) || !a || !b || !kappa || a == b || (const void*)kappa == (const void*)a ||
+      (const void*)kappa == (const void*)b || !aligned16(a) || !aligned16(b) || !aligned16(kappa) || steps < 0 ||
+      !std::isfinite((double)coef))
+    return FRACTAL_EINVAL;
+  Launch L;
+  int levels = 0;
+  if (!kappa_geometry(p->k, p->mode, L, levels)) return FRACTAL_EINVAL;
+  if (steps == 0) return FRACTAL_OK;
+  T* buf[2] = {a, b};
+  for (int s = 0; s < steps; ++s) {
+    cudaError_t e =
+        launch_diffusion_kappa<T>(p->mode, L, levels, buf[s & 1], buf[(s + 1) & 1], kappa, coef, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step_diffusion_kappa");
+  }
+  return FRACTAL_OK;
+}
+
+template <typename T>
+int adjoint_step(fractal_plan_t p, const T* u, const T* p_in, T* p_out, const float* kappa, double* gkappa, T coef,
+                 void* stream) {
+  if (check_plan(p) || !u || !p_in || !p_out || !kappa || !gkappa || !std::isfinite((double)coef))
+    return FRACTAL_EINVAL;
+  const void* all[5] = {u, p_in, p_out, kappa, gkappa};
+  for (int i = 0; i < 5; ++i) {
+    if (!aligned16(all[i])) return FRACTAL_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (all[i] == all[j]) return FRACTAL_EINVAL;
+  }
+  Launch L;
+  int levels = 0;
+  if (!kappa_geometry(p->k, p->mode, L, levels)) return FRACTAL_EINVAL;
+  cudaError_t e = launch_diffusion_adjoint<T>(p->mode, L, levels, u, p_in, p_out, kappa, gkappa, coef,
+                                              (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "adjoint_diffusion_step");
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* fractal_strerror(int status) {
@@ -626,6 +669,26 @@ int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int
     if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
   }
   return FRACTAL_OK;
+}
+
+int fractal_step_diffusion_kappa(fractal_plan_t p, float* a, float* b, const float* kappa, float coef, int steps,
+                                 void* stream) {
+  return step_kappa(p, a, b, kappa, coef, steps, stream);
+}
+
+int fractal_step_diffusion_kappa_f64(fractal_plan_t p, double* a, double* b, const float* kappa, double coef,
+                                     int steps, void* stream) {
+  return step_kappa(p, a, b, kappa, coef, steps, stream);
+}
+
+int fractal_adjoint_diffusion_step(fractal_plan_t p, const float* u, const float* p_in, float* p_out,
+                                   const float* kappa, double* gkappa, float coef, void* stream) {
+  return adjoint_step(p, u, p_in, p_out, kappa, gkappa, coef, stream);
+}
+
+int fractal_adjoint_diffusion_step_f64(fractal_plan_t p, const double* u, const double* p_in, double* p_out,
+                                       const float* kappa, double* gkappa, double coef, void* stream) {
+  return adjoint_step(p, u, p_in, p_out, kappa, gkappa, coef, stream);
 }
 
 int fractal_reduce_async(fractal_plan_t p, const void* dev_buf, int dtype, double* dev_out, void* stream) {

@@ -1,0 +1,281 @@
+// Diffusion with a per-cell conductivity and its adjoint (reverse) step, for
+// gradients of a loss with respect to the initial state and the conductivity.
+//
+// The step: u'_c = u_c + a * sum_{nb in N4(c), nb member} g_{c,nb} (u_nb - u_c),
+// with g_{c,nb} = (kappa_c + kappa_nb) / 2, i.e. u_{t+1} = A u_t with A
+// symmetric.  The reverse step of a loss J with p_{t+1} = dJ/du_{t+1}:
+//   p_t = A^T p_{t+1} = A p_{t+1}
+//   dJ/dkappa_c += (a / 2) sum_{nb} (u_t,nb - u_t,c) (p_{t+1},c - p_{t+1},nb)
+// (g_{c,nb} enters row c and row nb of A u_t).
+//
+// State precision.  The states u and p are float or double (template T);
+// kappa is float; dJ/dkappa is accumulated in double.  An FP32 trajectory
+// rounds u every step, and those roundings reach the gradients through
+// differences of neighbouring values: over 200 steps they alone move the
+// gradients by a few 1e-4 of their scale from the exact ones.  The double
+// state keeps the adjoint within 1e-4 of an FP64 reference.
+//
+// Launch: the lambda map at the level of 8 x 8 blocks.  A CTA takes a member
+// super-tile of 2^L x 2^L blocks (Theorem 1 for the CTA, lambda again for the
+// 3^L member blocks inside, Sec. 5.1), one thread per block.  A member block
+// (BX & BY == 0) holds the 27 members (i, j), i & j == 0, of a level-3
+// gasket and meets the rest of the gasket through four links only: (0,0) to
+// (0,7) of the block above and to (7,0) of the block left, (7,0) to (0,0) of
+// the block right, (0,7) to (0,0) of the block below.  Each thread reads its
+// block's member chunks and those four neighbour cells, and writes whole
+// 32-byte rows of its block (0 at the non-members).
+#include "launch.h"
+
+namespace fractal {
+namespace {
+
+constexpr int kB = 8;
+
+__host__ __device__ constexpr bool amem(int i, int j) { return i >= 0 && j >= 0 && i < kB && j < kB && (i & j) == 0; }
+
+__device__ __forceinline__ bool ablock(int gx, int gy, int nblk) {
+  return (unsigned)gx < (unsigned)nblk && (unsigned)gy < (unsigned)nblk && (gx & gy) == 0;
+}
+
+// Four consecutive values of a row, 16-byte accesses.
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 c = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = c.x;
+  v[1] = c.y;
+  v[2] = c.z;
+  v[3] = c.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 c0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 c1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = c0.x;
+  v[1] = c0.y;
+  v[2] = c1.x;
+  v[3] = c1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// The block's member values (0 at non-members) from a row-major n x n array.
+template <typename T>
+__device__ __forceinline__ void load_block(T (&v)[kB * kB], const T* __restrict__ p, int n) {
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    ld4(p + (size_t)j * n, &v[j * kB]);
+    if (j < 4) {
+      ld4(p + (size_t)j * n + 4, &v[j * kB + 4]);
+    } else {
+#pragma unroll
+      for (int i = 4; i < kB; ++i) v[j * kB + i] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < kB; ++i)
+      if (!amem(i, j)) v[j * kB + i] = T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_block(T* __restrict__ p, int n, const T (&v)[kB * kB]) {
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    st4(p + (size_t)j * n, &v[j * kB]);
+    st4(p + (size_t)j * n + 4, &v[j * kB + 4]);
+  }
+}
+
+// Neighbour cells at the ports: up (0,-1), left (-1,0), right (8,0), down
+// (0,8) relative to the block origin; 0 where that block is not a member
+// (or outside the array).
+template <typename T>
+struct Ports {
+  T up, lf, rt, dn;
+};
+
+template <typename T>
+__device__ __forceinline__ Ports<T> load_ports(const T* __restrict__ base, int n, bool hu, bool hl, bool hr, bool hd) {
+  Ports<T> q;
+  q.up = hu ? __ldg(base - n) : T(0);
+  q.lf = hl ? __ldg(base - 1) : T(0);
+  q.rt = hr ? __ldg(base + kB) : T(0);
+  q.dn = hd ? __ldg(base + (size_t)kB * n) : T(0);
+  return q;
+}
+
+// Visit the member neighbours of member cell (i, j): f(u there, kappa there,
+// x there) for three fields u, kappa, x of the block and its ports.
+template <typename T, typename F>
+__device__ __forceinline__ void for_neighbours(int i, int j, const T (&u)[kB * kB], const float (&k)[kB * kB],
+                                               const T (&x)[kB * kB], const Ports<T>& pu, const Ports<float>& pk,
+                                               const Ports<T>& px, bool hu, bool hl, bool hr, bool hd, F f) {
+  if (amem(i, j - 1)) f(u[(j - 1) * kB + i], k[(j - 1) * kB + i], x[(j - 1) * kB + i]);
+  if (amem(i - 1, j)) f(u[j * kB + i - 1], k[j * kB + i - 1], x[j * kB + i - 1]);
+  if (amem(i + 1, j)) f(u[j * kB + i + 1], k[j * kB + i + 1], x[j * kB + i + 1]);
+  if (amem(i, j + 1)) f(u[(j + 1) * kB + i], k[(j + 1) * kB + i], x[(j + 1) * kB + i]);
+  if (i == 0 && j == 0) {
+    if (hu) f(pu.up, pk.up, px.up);
+    if (hl) f(pu.lf, pk.lf, px.lf);
+  }
+  if (i == kB - 1 && j == 0 && hr) f(pu.rt, pk.rt, px.rt);
+  if (i == 0 && j == kB - 1 && hd) f(pu.dn, pk.dn, px.dn);
+}
+
+// This thread's block and whether it and its four neighbour blocks are members.
+struct BlockPos {
+  bool active;
+  bool hu, hl, hr, hd;
+  size_t base;  // element index of the block origin
+};
+
+template <int MODE>
+__device__ __forceinline__ bool block_pos(const Geo& g, int L, BlockPos& b) {
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return false;  // whole CTA: BB slot off the gasket
+  int nb = 1, lw = 1;
+  for (int i = 0; i < L; ++i) nb *= 3;
+  for (int i = 0; i < (L + 1) / 2; ++i) lw *= 3;
+  b.active = false;
+  const int t = threadIdx.x;
+  if (t >= nb) return true;
+  int bx, by;
+  lambda_scalar((uint32_t)(t % lw), (uint32_t)(t / lw), L, bx, by);
+  const int GX = (sx << L) + bx, GY = (sy << L) + by, nblk = g.n / kB;
+  b.active = true;
+  b.hu = ablock(GX, GY - 1, nblk);
+  b.hl = ablock(GX - 1, GY, nblk);
+  b.hr = ablock(GX + 1, GY, nblk);
+  b.hd = ablock(GX, GY + 1, nblk);
+  b.base = (size_t)GY * kB * (size_t)g.n + (size_t)GX * kB;
+  return true;
+}
+
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(128) diffusion_kappa_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                                              const float* __restrict__ kappa, T a, Geo g, int L) {
+  BlockPos b;
+  if (!block_pos<MODE>(g, L, b) || !b.active) return;
+  const int n = g.n;
+  T u[kB * kB], w[kB * kB];
+  float k[kB * kB];
+  load_block(u, in + b.base, n);
+  load_block(k, kappa + b.base, n);
+  const Ports<T> pu = load_ports(in + b.base, n, b.hu, b.hl, b.hr, b.hd);
+  const Ports<float> pk = load_ports(kappa + b.base, n, b.hu, b.hl, b.hr, b.hd);
+  const T ha = T(0.5) * a;
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const int c = j * kB + i;
+      if (!amem(i, j)) {
+        w[c] = T(0);
+        continue;
+      }
+      T s = T(0);
+      for_neighbours(i, j, u, k, u, pu, pk, pu, b.hu, b.hl, b.hr, b.hd,
+                     [&](T un, float kn, T) { s = fmat(T(k[c]) + T(kn), un - u[c], s); });
+      w[c] = fmat(ha, s, u[c]);
+    }
+  }
+  store_block(out + b.base, n, w);
+}
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(128) diffusion_adjoint_kernel(const T* __restrict__ ut, const T* __restrict__ pin,
+                                                                T* __restrict__ pout, const float* __restrict__ kappa,
+                                                                double* __restrict__ gkappa, T a, Geo g, int L) {
+  BlockPos b;
+  if (!block_pos<MODE>(g, L, b) || !b.active) return;
+  const int n = g.n;
+  T u[kB * kB], p[kB * kB], w[kB * kB];
+  float k[kB * kB];
+  load_block(u, ut + b.base, n);
+  load_block(k, kappa + b.base, n);
+  load_block(p, pin + b.base, n);
+  const Ports<T> pu = load_ports(ut + b.base, n, b.hu, b.hl, b.hr, b.hd);
+  const Ports<float> pk = load_ports(kappa + b.base, n, b.hu, b.hl, b.hr, b.hd);
+  const Ports<T> pp = load_ports(pin + b.base, n, b.hu, b.hl, b.hr, b.hd);
+  const T ha = T(0.5) * a;
+  const double hd = 0.5 * (double)a;
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    double* grow = gkappa + b.base + (size_t)j * n;
+    double gr[kB];
+    ld4(grow, gr);
+    ld4(grow + 4, gr + 4);
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      const int c = j * kB + i;
+      if (!amem(i, j)) {
+        w[c] = T(0);
+        gr[i] = 0.0;
+        continue;
+      }
+      T sp = T(0);
+      double sg = 0.0;
+      for_neighbours(i, j, u, k, p, pu, pk, pp, b.hu, b.hl, b.hr, b.hd, [&](T un, float kn, T pn) {
+        sp = fmat(T(k[c]) + T(kn), pn - p[c], sp);                 // ((A p)_c - p_c) * 2 / a
+        sg = fma((double)(un - u[c]), (double)(p[c] - pn), sg);    // dJ/dkappa_c of this step * 2 / a
+      });
+      w[c] = fmat(ha, sp, p[c]);
+      gr[i] = fma(hd, sg, gr[i]);
+    }
+    st4(grow, gr);
+    st4(grow + 4, gr + 4);
+  }
+  store_block(pout + b.base, n, w);
+}
+
+}  // namespace
+
+// Geometry: super-tiles of 2^L x 2^L blocks (L = 4: 81 member blocks, 96
+// threads; smaller arrays take one super-tile).
+bool kappa_geometry(int k, int mode, Launch& L, int& levels) {
+  if (k < 3) return false;
+  const int rb = k - 3;          // block levels of the array
+  levels = rb < 4 ? rb : 4;
+  if (!supertile_grid(k, 3, mode, levels, L)) return false;
+  int nb = 1;
+  for (int i = 0; i < levels; ++i) nb *= 3;
+  L.threads = (nb + 31) / 32 * 32;
+  L.smem = 0;
+  return true;
+}
+
+template <typename T>
+cudaError_t launch_diffusion_kappa(int mode, const Launch& L, int levels, const T* in, T* out, const float* kappa,
+                                   T a, cudaStream_t s) {
+  if (mode == kLambda)
+    diffusion_kappa_kernel<kLambda, T><<<L.grid, L.threads, 0, s>>>(in, out, kappa, a, L.geo, levels);
+  else
+    diffusion_kappa_kernel<kBB, T><<<L.grid, L.threads, 0, s>>>(in, out, kappa, a, L.geo, levels);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diffusion_adjoint(int mode, const Launch& L, int levels, const T* ut, const T* pin, T* pout,
+                                     const float* kappa, double* gkappa, T a, cudaStream_t s) {
+  if (mode == kLambda)
+    diffusion_adjoint_kernel<kLambda, T><<<L.grid, L.threads, 0, s>>>(ut, pin, pout, kappa, gkappa, a, L.geo, levels);
+  else
+    diffusion_adjoint_kernel<kBB, T><<<L.grid, L.threads, 0, s>>>(ut, pin, pout, kappa, gkappa, a, L.geo, levels);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_diffusion_kappa<float>(int, const Launch&, int, const float*, float*, const float*, float,
+                                                   cudaStream_t);
+template cudaError_t launch_diffusion_kappa<double>(int, const Launch&, int, const double*, double*, const float*,
+                                                    double, cudaStream_t);
+template cudaError_t launch_diffusion_adjoint<float>(int, const Launch&, int, const float*, const float*, float*,
+                                                     const float*, double*, float, cudaStream_t);
+template cudaError_t launch_diffusion_adjoint<double>(int, const Launch&, int, const double*, const double*, double*,
+                                                      const float*, double*, double, cudaStream_t);
+
+}  // namespace fractal

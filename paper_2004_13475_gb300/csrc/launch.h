@@ -49,6 +49,17 @@ cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_
 int ca_fused_smem_bytes(const Geo& g, int margin);
 int ca_fused_threads(const Geo& g, int margin);
 
+// Diffusion with per-cell conductivity and its reverse step (k_adjoint.cu):
+// one thread per member 8 x 8 block, super-tiles of 2^levels blocks a side.
+// T = float or double (the state precision).
+bool kappa_geometry(int k, int mode, Launch& L, int& levels);
+template <typename T>
+cudaError_t launch_diffusion_kappa(int mode, const Launch& L, int levels, const T* in, T* out, const float* kappa,
+                                   T a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_diffusion_adjoint(int mode, const Launch& L, int levels, const T* ut, const T* pin, T* pout,
+                                     const float* kappa, double* gkappa, T a, cudaStream_t s);
+
 // One instance of a batch (device table entry).
 struct BatchInst {
   float* a;       // the instance's two n x n buffers

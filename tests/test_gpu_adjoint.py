@@ -1,0 +1,182 @@
+"""Diffusion with per-cell conductivity and its adjoint on the GPU.
+
+Forward steps against the FP64 oracle step; gradients through the
+checkpointed torch.autograd.Function against the oracle's FP64 adjoint and
+FP64 central finite differences; the full-size case (k = 13, 200 steps,
+checkpoint every 20) on sampled cells whose gradients a window of the array
+gives exactly (no influence travels farther than one cell per step, forward
+and backward).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+A = 0.2
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_2004_13475_gb300 import build as fbuild
+    fbuild.build()
+    import paper_2004_13475_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def fields(k, seed):
+    n = 1 << k
+    u0 = synth.uniform_f32(seed, n)
+    mask = oracle.member_mask(n)
+    kappa = np.where(mask, np.float32(0.5) + synth.uniform_f32(seed + 1, n), np.float32(0))
+    # the loss runs over members: the target is 0 elsewhere (u0 keeps its
+    # non-member noise, which the function must ignore)
+    target = np.where(mask, synth.uniform_f32(seed + 2, n), np.float32(0)).astype(np.float32)
+    return u0, kappa.astype(np.float32), target
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).cuda()
+
+
+def block_cover(n):
+    nb = n // 8
+    by, bx = np.mgrid[0:nb, 0:nb]
+    return np.kron((bx & by) == 0, np.ones((8, 8), dtype=bool))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k", [3, 5, 8, 10])
+def test_kappa_steps_match_oracle(fr, k, mode):
+    n = 1 << k
+    u0, kappa, _ = fields(k, 10 + k)
+    plan = fr.fractal_map(k, 8 if k >= 3 else n, mode)
+    dom = oracle.Domain.build(n)
+    for steps in (1, 7):
+        a = dev(u0)
+        b = torch.full_like(a, -3.0)
+        out = fr.fractal_step_diffusion_kappa(plan, a, b, dev(kappa), A, steps)
+        got = out.cpu().numpy().reshape(n, n)
+        want = oracle.diffusion_run(u0.astype(np.float64), steps, A, dom, kappa.astype(np.float64))
+        assert rel_err(got, want, dom.mask)[0] <= 2e-6, steps
+        cover = block_cover(n)
+        assert np.all(got[cover & ~dom.mask] == 0)
+        if steps % 2:
+            assert np.all(got[~cover] == -3.0)
+        # the float64-state kernel: FP64 arithmetic in another order
+        a64 = dev(u0.astype(np.float64))
+        b64 = torch.zeros_like(a64)
+        got64 = fr.fractal_step_diffusion_kappa_f64(plan, a64, b64, dev(kappa), A, steps).cpu().numpy().reshape(n, n)
+        assert rel_err(got64, want, dom.mask)[0] <= 1e-13
+
+
+def grads_gpu(fr, k, u0, kappa, target, steps, every, mode=0, state="f64"):
+    from paper_2004_13475_gb300.autograd import diffusion_kappa
+    u = dev(u0).requires_grad_(True)
+    kp = dev(kappa).requires_grad_(True)
+    uT = diffusion_kappa(u, kp, k, A, steps, every, mode, state)
+    loss = ((uT - dev(target)) ** 2).sum()
+    loss.backward()
+    n = 1 << k
+    return (float(loss.detach()), u.grad.cpu().numpy().reshape(n, n), kp.grad.cpu().numpy().reshape(n, n),
+            uT.detach().cpu().numpy().reshape(n, n))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k,steps,every", [(4, 9, 1), (6, 25, 7), (8, 45, 20), (9, 60, 20)])
+def test_gradients_match_oracle_adjoint(fr, k, steps, every, mode):
+    n = 1 << k
+    u0, kappa, target = fields(k, 30 + k)
+    dom = oracle.Domain.build(n)
+    J, gu, gk, uT = grads_gpu(fr, k, u0, kappa, target, steps, every, mode)
+    Jw, wu, wk = oracle.diffusion_loss_gradients(dom, dom.take(u0).astype(np.float64),
+                                                 dom.take(kappa).astype(np.float64),
+                                                 dom.take(target).astype(np.float64), steps, A)
+    assert J == pytest.approx(Jw, rel=1e-5)
+    WU, WK = dom.put(wu, np.float64), dom.put(wk, np.float64)
+    assert rel_err(gu, WU, dom.mask)[0] <= 1e-4
+    assert rel_err(gk, WK, dom.mask)[0] <= 1e-4
+    assert not gu[~dom.mask].any() and not gk[~dom.mask].any()
+
+
+@pytest.mark.parametrize("k,steps,every", [(6, 25, 7), (9, 60, 20)])
+def test_float32_state_gradients(fr, k, steps, every):
+    # float32 trajectory: its per-step roundings alone put the gradients a
+    # few 1e-4 (of their scale) from the exact ones; bound 1e-3
+    n = 1 << k
+    u0, kappa, target = fields(k, 50 + k)
+    dom = oracle.Domain.build(n)
+    _, gu, gk, _ = grads_gpu(fr, k, u0, kappa, target, steps, every, state="f32")
+    _, wu, wk = oracle.diffusion_loss_gradients(dom, dom.take(u0).astype(np.float64),
+                                                dom.take(kappa).astype(np.float64),
+                                                dom.take(target).astype(np.float64), steps, A)
+    assert rel_err(gu, dom.put(wu, np.float64), dom.mask)[0] <= 1e-3
+    assert rel_err(gk, dom.put(wk, np.float64), dom.mask)[0] <= 1e-3
+
+
+def test_gradients_match_finite_differences(fr):
+    # FP64 central differences of the oracle's loss on sampled cells (1e-3 bound)
+    k, steps = 6, 30
+    n = 1 << k
+    u0, kappa, target = fields(k, 77)
+    dom = oracle.Domain.build(n)
+    _, gu, gk, _ = grads_gpu(fr, k, u0, kappa, target, steps, 10)
+    U, K, G = (dom.take(x).astype(np.float64) for x in (u0, kappa, target))
+
+    def loss(uu, kk):
+        for _ in range(steps):
+            uu = oracle.diffusion_step(dom, uu, A, kk)
+        return float(np.sum((uu - G) ** 2))
+
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for c in rng.choice(dom.m, size=6, replace=False):
+        e = np.zeros(dom.m)
+        e[c] = h
+        fdu = (loss(U + e, K) - loss(U - e, K)) / (2 * h)
+        fdk = (loss(U, K + e) - loss(U, K - e)) / (2 * h)
+        x, y = dom.cx[c], dom.cy[c]
+        assert gu[y, x] == pytest.approx(fdu, rel=1e-3, abs=1e-6)
+        assert gk[y, x] == pytest.approx(fdk, rel=1e-3, abs=1e-6)
+
+
+def test_level_13_200_steps_sampled_cells(fr):
+    """k = 13 (8192 x 8192), kappa ~ U[0.5, 1.5), 200 steps, checkpoint every 20."""
+    k, steps, every = 13, 200, 20
+    n = 1 << k
+    u0, kappa, target = fields(k, 2024)
+    _, gu, gk, _ = grads_gpu(fr, k, u0, kappa, target, steps, every)
+    r = 2 * steps + 1
+    # sampled member cells: near the corner (window clipped by the array edges) and inside
+    for (x, y) in ((3, 400), (1000, 17), (2048 + 600, 1024)):
+        assert (x & y) == 0
+        x0, y0 = max(0, x - r), max(0, y - r)
+        x1, y1 = min(n, x + r + 1), min(n, y + r + 1)
+        win = oracle.Domain.build(n, x0, y0, x1 - x0, y1 - y0)
+        sl = (slice(y0, y1), slice(x0, x1))
+        _, wu, wk = oracle.diffusion_loss_gradients(win, win.take(u0[sl]).astype(np.float64),
+                                                    win.take(kappa[sl]).astype(np.float64),
+                                                    win.take(target[sl]).astype(np.float64), steps, A)
+        WU, WK = win.put(wu, np.float64), win.put(wk, np.float64)
+        for G, W in ((gu, WU), (gk, WK)):
+            want = W[y - y0, x - x0]
+            scale = max(abs(want), 1e-3 * np.abs(W).max())
+            assert abs(G[y, x] - want) <= 1e-4 * scale, (x, y, G[y, x], want)
+
+
+def test_adjoint_validation(fr):
+    plan = fr.fractal_map(6, 8)
+    x = [torch.zeros(64 * 64, device="cuda") for _ in range(5)]
+    with pytest.raises(fr.FractalError):
+        fr.fractal_adjoint_diffusion_step(plan, x[0], x[1], x[1], x[3], x[4], A)     # p_in == p_out
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_diffusion_kappa(plan, x[0], x[1], x[0], A, 2)              # kappa aliases a
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_diffusion_kappa(fr.fractal_map(2, 4), x[0], x[1], x[2], A, 1)   # k < 3
+    fr.fractal_adjoint_diffusion_step(plan, x[0], x[1], x[2], x[3], x[4], A)
