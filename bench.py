@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--spl-ca", type=int, default=1, help="automaton steps per launch (--no-tune)")
     ap.add_argument("--spl-diff", type=int, default=1, help="diffusion steps per launch (--no-tune)")
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box run of the step")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-gasket measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (adjoint) measurement")
     ap.add_argument("--profile", choices=["ca", "diffusion", "reduce", "sw"],
                     help="run only `--launches` launches of one kernel (for ncu captures)")
     ap.add_argument("--k", type=int, default=15, help="gasket level of a --profile run")
@@ -420,6 +422,11 @@ def main():
     if rank == 0 and not args.no_detail:
         line["detail"] = kernel_detail(fr, torch, stream, lambda rho, mode: tuned[("diffusion", mode, rho)][0],
                                        lambda rho, mode: tuned[("ca", mode, rho)][0], ca_a, ca_b, u_a, u_b, hbm)
+
+    if rank == 0 and not args.no_batch:
+        line["batched"] = batched(fr, torch, stream, SEED + 17)
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = adjoint(fr, torch, stream, SEED + 31)
 
     # ---- end to end through the C ABI with host buffers ----
     if not args.no_e2e:
@@ -637,6 +644,158 @@ def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
             lam = out[str(rho)]["lambda"][kname]["us"]
             bb = out[str(rho)]["bb"][kname]["us"]
             out[str(rho)].setdefault("speedup_lambda_over_bb", {})[kname] = bb / lam
+    return out
+
+
+BATCH_COUNT = 256
+BATCH_STEPS = 100
+BATCH_KS = (8, 13)
+
+
+def batched(fr, torch, stream, seed):
+    """256 independent gaskets, k ~ U{8..13} (seeded), FP32 diffusion, 100
+    steps: one persistent launch per group of steps through a batch, replayed
+    from a CUDA graph, against one launch sequence per instance (plans with the
+    same steps per launch).  Both leave bit-identical states."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    ks = [int(k) for k in rng.integers(BATCH_KS[0], BATCH_KS[1] + 1, size=BATCH_COUNT)]
+    sizes = [(1 << k) * (1 << k) for k in ks]
+    total = sum(sizes)
+    arena_a = torch.empty(total, dtype=torch.float32, device="cuda")
+    arena_b = torch.empty(total, dtype=torch.float32, device="cuda")
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    A = [arena_a[o:o + s] for o, s in zip(offs, sizes)]
+    B = [arena_b[o:o + s] for o, s in zip(offs, sizes)]
+    sptr = stream.cuda_stream
+
+    def fill():
+        for i, k in enumerate(ks):
+            synth.device_fill(A[i].data_ptr(), synth.SYNTH_UNIFORM_F32, 1 << k, seed + 1 + i, stream=sptr)
+
+    fill()
+    batch = fr.fractal_batch_create(ks)
+    fr.fractal_batch_bind(batch, A, B)
+    tune_us = fr.fractal_batch_autotune(batch, COEF, 3, stream)
+    inf = batch.info()
+    fr.fractal_batch_graph_capture(batch, COEF, BATCH_STEPS)
+    members = inf["members"]
+
+    def clock(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    t_graph = clock(lambda: fr.fractal_batch_graph_launch(batch, stream), 5)
+    t_batch = clock(lambda: fr.fractal_batch_step_diffusion(batch, COEF, BATCH_STEPS, stream), 5)
+    # per-instance launches: one plan per instance, the same steps per launch
+    plans = []
+    for k in ks:
+        p = fr.fractal_map(k, 8)
+        fr.fractal_plan_set_steps_per_launch(p, fr.FRACTAL_F32, inf["steps_per_launch"])
+        plans.append(p)
+
+    def per_instance():
+        for p, x, y in zip(plans, A, B):
+            fr.fractal_step_diffusion(p, x, y, COEF, BATCH_STEPS, stream)
+
+    t_each = clock(per_instance, 3)
+    # same result: batch vs per-instance on a few instances (100 steps, result in A)
+    fill()
+    fr.fractal_batch_graph_launch(batch, stream)
+    torch.cuda.synchronize()
+    check = [i for i in range(BATCH_COUNT) if ks[i] <= 10][:8]
+    got = [A[i].clone() for i in check]
+    fill()
+    per_instance()
+    torch.cuda.synchronize()
+    identical = all(torch.equal(g, A[i]) for g, i in zip(got, check))
+    launches = kernel_launches(inf["steps_per_launch"], BATCH_STEPS)
+    out = {
+        "workload": (f"{BATCH_COUNT} gaskets, k ~ U{{{BATCH_KS[0]}..{BATCH_KS[1]}}} (seeded), FP32 diffusion "
+                     f"a={COEF}, {BATCH_STEPS} steps, {members} member cells in all"),
+        "cell_updates_per_s_graph": members * BATCH_STEPS / t_graph,
+        "cell_updates_per_s_batch_stream": members * BATCH_STEPS / t_batch,
+        "cell_updates_per_s_per_instance": members * BATCH_STEPS / t_each,
+        "ms_graph": t_graph * 1e3, "ms_batch_stream": t_batch * 1e3, "ms_per_instance": t_each * 1e3,
+        "speedup_graph_over_per_instance": t_each / t_graph,
+        "launches_graph": launches, "launches_per_instance": launches * BATCH_COUNT,
+        "supertile": inf["supertile"], "steps_per_launch": inf["steps_per_launch"], "ctas": inf["ctas"],
+        "tuned_step_us": tune_us,
+        "bit_identical_to_per_instance": identical, "checked_instances": len(check),
+        "memory_gib": 2 * 4 * total / 2 ** 30,
+    }
+    for p in plans:
+        p.close()
+    batch.close()
+    del arena_a, arena_b
+    torch.cuda.empty_cache()
+    return out
+
+
+ADJ_K = 13
+ADJ_STEPS = 200
+ADJ_EVERY = 20
+
+
+def adjoint(fr, torch, stream, seed):
+    """k = 13, kappa ~ U[0.5, 1.5), 200 steps, loss sum((u_T - target)^2),
+    gradients w.r.t. u0 and kappa through the checkpointed autograd function
+    (a state every 20 steps), float64 and float32 state.  A timed pass is one
+    forward and one backward (the backward recomputes each segment)."""
+    import synth
+    from paper_2004_13475_gb300.autograd import diffusion_kappa
+    n = 1 << ADJ_K
+    sptr = stream.cuda_stream
+    u0 = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    kap = torch.empty_like(u0)
+    tg = torch.empty_like(u0)
+    synth.device_fill(u0.data_ptr(), synth.SYNTH_UNIFORM_F32, n, seed, stream=sptr)
+    synth.device_fill(kap.data_ptr(), synth.SYNTH_UNIFORM_F32, n, seed + 1, stream=sptr)
+    synth.device_fill(tg.data_ptr(), synth.SYNTH_UNIFORM_F32, n, seed + 2, stream=sptr)
+    plan = fr.fractal_map(ADJ_K, 8)
+    mask = torch.zeros_like(u0)
+    fr.fractal_map_write(plan, mask, fr.FRACTAL_F32, 1.0, stream)
+    kap = (kap + 0.5) * mask
+    tg = tg * mask
+    out = {"workload": (f"gasket k={ADJ_K} ({n}x{n}), kappa ~ U[0.5,1.5), {ADJ_STEPS} steps a={COEF}, "
+                        f"loss sum((u_T - target)^2), gradients w.r.t. u0 and kappa, checkpoint every {ADJ_EVERY}")}
+    members = 3 ** ADJ_K
+    for state in ("f64", "f32"):
+        def one():
+            u = u0.clone().requires_grad_(True)
+            k = kap.clone().requires_grad_(True)
+            loss = ((diffusion_kappa(u, k, ADJ_K, COEF, ADJ_STEPS, ADJ_EVERY, 0, state) - tg) ** 2).sum()
+            loss.backward()
+            return loss
+        one()
+        torch.cuda.synchronize()
+        reps = 2
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            one()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        t = t0.elapsed_time(t1) / 1e3 / reps
+        elem = 8 if state == "f64" else 4
+        out[state] = {
+            "ms_forward_backward": t * 1e3,
+            # forward, recomputation and reverse: three passes over the steps
+            "cell_steps_per_s": 3 * members * ADJ_STEPS / t,
+            "state_memory_gib": ((ADJ_STEPS // ADJ_EVERY) + ADJ_EVERY) * n * n * elem / 2 ** 30,
+            "state_memory_gib_without_checkpoints": (ADJ_STEPS + 1) * n * n * elem / 2 ** 30,
+        }
+    plan.close()
     return out
 
 
