@@ -316,17 +316,17 @@ def main():
         """One bench step; if ev (a dict) is given, record events around the
         automaton run and the diffusion segments."""
         pc, pd = plan("ca", mode), plan("diffusion", mode)
+        # each call leaves the global measure of its result in `sums` (taken by
+        # the last fused launch from the values it writes, or a reduce after)
         mark(ev, "ca0")
-        fr.fractal_step_ca(pc, ca_a, ca_b, CA_STEPS, stream)          # even: result back in ca_a
+        fr.fractal_step_ca_count(pc, ca_a, ca_b, CA_STEPS, sums[4:5], stream)   # even: result back in ca_a
         mark(ev, "ca1")
         cur, oth = u_a, u_b
         for seg in range(DIFF_STEPS // REDUCE_EVERY):
             mark(ev, "d0")
-            cur = fr.fractal_step_diffusion(pd, cur, oth, COEF, REDUCE_EVERY, stream)
+            cur = fr.fractal_step_diffusion_sum(pd, cur, oth, COEF, REDUCE_EVERY, sums[seg:seg + 1], stream)
             mark(ev, "d1")
             oth = u_b if cur is u_a else u_a
-            fr.fractal_reduce_async(pd, cur, fr.FRACTAL_F32, sums[seg:seg + 1], stream)
-        fr.fractal_reduce_async(pc, ca_a, fr.FRACTAL_U8, sums[4:5], stream)
         return cur
 
     def timed(mode, steps, warmup, ev=None):
@@ -375,7 +375,9 @@ def main():
     rf_d = launch_roofline("diffusion", info_d, spl_d, diff_ms / 1e3 / (kd * args.steps), hbm, peak_kind)
     rf_c = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind)
     roofline = rf_d if diff_ms >= ca_ms else rf_c          # the kernel that takes most of the step
-    launches_per_step = kc + kd + 2 * (DIFF_STEPS // REDUCE_EVERY + 1)
+    # plus, per global measure, a final-sum launch (fused) or a reduce and a final sum
+    launches_per_step = (kc + kd + (1 if spl_c > 1 else 2)
+                         + (DIFF_STEPS // REDUCE_EVERY) * (1 if spl_d > 1 else 2))
     # each workload's cell-updates/s against its HBM floor: every member
     # sector read and written once per step at the measured copy bandwidth
     # (rho = 32 sectors for uint8, rho = 8 for float32)

@@ -202,6 +202,17 @@ int fractal_map_write(fractal_plan_t plan, void* dev_buf, int dtype, double valu
 int fractal_step_ca(fractal_plan_t plan, uint8_t* dev_a, uint8_t* dev_b, int steps, void* stream);
 
 /*
+ * fractal_step_ca_count -- fractal_step_ca followed by the global measure of
+ * Sec. 6.2 (RD) on the result: *dev_count (a device double) receives the
+ * number of alive members after the steps.  With temporal fusion the count is
+ * taken by the last launch from the words it writes (no second pass over the
+ * array); otherwise a reduce follows.  steps == 0 counts dev_a.  Asynchronous.
+ * Errors: as fractal_step_ca, FRACTAL_EINVAL for a NULL dev_count.
+ */
+int fractal_step_ca_count(fractal_plan_t plan, uint8_t* dev_a, uint8_t* dev_b, int steps, double* dev_count,
+                          void* stream);
+
+/*
  * fractal_step_diffusion -- `steps` explicit FDM heat-diffusion steps on the
  * gasket (the FDM time-step pattern of Sec. 1), FP32:
  *   u'_c = u_c + a * sum_{nb in N4(c), nb member} (u_nb - u_c),
@@ -213,6 +224,18 @@ int fractal_step_ca(fractal_plan_t plan, uint8_t* dev_a, uint8_t* dev_b, int ste
  */
 int fractal_step_diffusion(fractal_plan_t plan, float* dev_a, float* dev_b, float a, int steps,
                            void* stream);
+
+/*
+ * fractal_step_diffusion_sum -- fractal_step_diffusion followed by the global
+ * sum of Sec. 6.2 (RD) on the result: *dev_sum (a device double) receives the
+ * sum over the members after the steps (FP32 within an 8-cell row of a block,
+ * FP64 above, fixed order).  With temporal fusion the sum is taken by the
+ * last launch from the values it writes; otherwise a reduce follows.  steps
+ * == 0 sums dev_a.  Asynchronous.  Errors: as fractal_step_diffusion,
+ * FRACTAL_EINVAL for a NULL dev_sum.
+ */
+int fractal_step_diffusion_sum(fractal_plan_t plan, float* dev_a, float* dev_b, float a, int steps, double* dev_sum,
+                               void* stream);
 
 /*
  * fractal_reduce -- the reduction test of Sec. 6.2 (RD): the sum over all

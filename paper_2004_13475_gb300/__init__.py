@@ -44,6 +44,7 @@ EXPORTS = (
     "fractal_batch_graph_capture", "fractal_batch_graph_launch", "fractal_batch_get_info",
     "fractal_step_diffusion_kappa", "fractal_adjoint_diffusion_step",
     "fractal_step_diffusion_kappa_f64", "fractal_adjoint_diffusion_step_f64",
+    "fractal_step_ca_count", "fractal_step_diffusion_sum",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -136,6 +137,8 @@ def _load() -> ctypes.CDLL:
         "fractal_step_diffusion_kappa": (I, [P, VP, VP, VP, F, I, VP]),
         "fractal_adjoint_diffusion_step": (I, [P, VP, VP, VP, VP, VP, F, VP]),
         "fractal_step_diffusion_kappa_f64": (I, [P, VP, VP, VP, D, I, VP]),
+        "fractal_step_ca_count": (I, [P, VP, VP, I, VP, VP]),
+        "fractal_step_diffusion_sum": (I, [P, VP, VP, F, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
     }
     for name, (res, args) in sig.items():
@@ -262,6 +265,22 @@ def fractal_step_diffusion(plan: Plan, a, b, coef: float, steps: int, stream=Non
     """Run `steps` diffusion steps with a = alpha*dt; returns the buffer holding the result."""
     _check(_load().fractal_step_diffusion(plan.handle, _ptr(a), _ptr(b), float(coef), int(steps),
                                           _stream(stream)), "fractal_step_diffusion")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_step_ca_count(plan: Plan, a, b, steps: int, dev_count, stream=None):
+    """CA steps, then the alive count of the result into the device double `dev_count`;
+    returns the buffer holding the result."""
+    _check(_load().fractal_step_ca_count(plan.handle, _ptr(a), _ptr(b), int(steps), _ptr(dev_count),
+                                         _stream(stream)), "fractal_step_ca_count")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_step_diffusion_sum(plan: Plan, a, b, coef: float, steps: int, dev_sum, stream=None):
+    """Diffusion steps, then the member sum of the result into the device double `dev_sum`;
+    returns the buffer holding the result."""
+    _check(_load().fractal_step_diffusion_sum(plan.handle, _ptr(a), _ptr(b), float(coef), int(steps),
+                                              _ptr(dev_sum), _stream(stream)), "fractal_step_diffusion_sum")
     return a if steps % 2 == 0 else b
 
 

@@ -270,6 +270,8 @@ int ensure_partials(fractal_plan_s* p) {
   for (int d = 0; d < 2; ++d) {
     const size_t c = (size_t)p->aux[d].grid.x * p->aux[d].grid.y;
     if (c > need) need = c;
+    const size_t f = p->fused_ok[d] ? (size_t)p->fused[d].grid.x * p->fused[d].grid.y : 0;
+    if (f > need) need = f;
   }
   if (need <= p->partials_cap) return FRACTAL_OK;
   void* buf = nullptr;
@@ -289,6 +291,115 @@ int check_plan(const fractal_plan_s* p) { return p ? FRACTAL_OK : FRACTAL_EINVAL
 }  // namespace
 
 namespace {
+
+// L launches of at most spl steps with the parity of `steps` (so that the
+// result lands where the single-step ping-pong would leave it): steps per
+// launch i.
+struct FusedSplit {
+  int L, base, extra;
+  FusedSplit(int steps, int spl) {
+    L = (steps + spl - 1) / spl;
+    if ((L & 1) != (steps & 1)) ++L;
+    base = steps / L;
+    extra = steps % L;
+  }
+  int of(int i) const { return base + (i < extra ? 1 : 0); }
+};
+
+// `steps` automaton steps; with dev_count, also the alive count of the result
+// (fused into the last launch of the fused kernel, else a reduce after).
+int step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, double* dev_count, void* stream) {
+  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0)
+    return FRACTAL_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  uint8_t* buf[2] = {a, b};
+  if (steps > 0 && p->spl[FRACTAL_U8] > 1 && p->fused_ok[FRACTAL_U8]) {
+    const int spl = p->spl[FRACTAL_U8];
+    const FusedSplit sp(steps, spl);
+    for (int i = 0; i < sp.L; ++i) {
+      const bool last = i == sp.L - 1;
+      auto* part = last && dev_count ? static_cast<unsigned long long*>(p->d_partials) : nullptr;
+      cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], buf[i & 1], buf[(i + 1) & 1], sp.of(i), spl,
+                                      st, part);
+      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    }
+    if (dev_count) {
+      const Launch& F = p->fused[FRACTAL_U8];
+      cudaError_t e = launch_final_sum(0, p->d_partials, (int64_t)F.grid.x * F.grid.y, dev_count, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_ca count");
+    }
+    return FRACTAL_OK;
+  }
+  if (steps > 0 && use_tma(p, FRACTAL_U8)) {
+    CUtensorMap maps[2], rings[2];
+    const int rho = 1 << p->log_rho;
+    if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_U8) ||
+        !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_U8))
+      return cuda_fail(cudaErrorInvalidValue, "tensor map");
+    for (int s = 0; s < steps; ++s) {
+      cudaError_t e = launch_ca_tma(p->mode, p->log_rho, p->tma[FRACTAL_U8], maps[s & 1], rings[s & 1],
+                                    buf[(s + 1) & 1], p->d_err, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    }
+  } else {
+    for (int s = 0; s < steps; ++s) {
+      cudaError_t e = launch_ca(p->mode, p->log_rho, p->step[FRACTAL_U8], buf[s & 1], buf[(s + 1) & 1], st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    }
+  }
+  if (!dev_count) return FRACTAL_OK;
+  cudaError_t e = launch_reduce(p->mode, p->log_rho, FRACTAL_U8, p->aux[FRACTAL_U8], buf[steps & 1], p->d_partials,
+                                dev_count, st);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "step_ca count");
+}
+
+// `steps` diffusion steps; with dev_sum, also the member sum of the result.
+int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, double* dev_sum, void* stream) {
+  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0 ||
+      !std::isfinite(coef))
+    return FRACTAL_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  float* buf[2] = {a, b};
+  if (steps > 0 && p->spl[FRACTAL_F32] > 1 && p->fused_ok[FRACTAL_F32]) {
+    const int spl = p->spl[FRACTAL_F32];
+    const FusedSplit sp(steps, spl);
+    for (int i = 0; i < sp.L; ++i) {
+      const bool last = i == sp.L - 1;
+      double* part = last && dev_sum ? static_cast<double*>(p->d_partials) : nullptr;
+      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[FRACTAL_F32],
+                                             buf[i & 1], buf[(i + 1) & 1], coef, sp.of(i), st, part);
+      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+    }
+    if (dev_sum) {
+      const Launch& F = p->fused[FRACTAL_F32];
+      cudaError_t e = launch_final_sum(1, p->d_partials, (int64_t)F.grid.x * F.grid.y, dev_sum, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion sum");
+    }
+    return FRACTAL_OK;
+  }
+  if (steps > 0 && use_tma(p, FRACTAL_F32)) {
+    CUtensorMap maps[2], rings[2];
+    const int rho = 1 << p->log_rho;
+    if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_F32) ||
+        !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_F32))
+      return cuda_fail(cudaErrorInvalidValue, "tensor map");
+    for (int s = 0; s < steps; ++s) {
+      cudaError_t e = launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], rings[s & 1],
+                                           buf[(s + 1) & 1], coef, p->d_err, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+    }
+  } else {
+    for (int s = 0; s < steps; ++s) {
+      cudaError_t e =
+          launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], buf[s & 1], buf[(s + 1) & 1], coef, st);
+      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+    }
+  }
+  if (!dev_sum) return FRACTAL_OK;
+  cudaError_t e = launch_reduce(p->mode, p->log_rho, FRACTAL_F32, p->aux[FRACTAL_F32], buf[steps & 1], p->d_partials,
+                                dev_sum, st);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "step_diffusion sum");
+}
 
 // Steps with per-cell conductivity, state type T (float or double).
 template <typename T>
@@ -462,7 +573,7 @@ int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
   p->spl[dtype] = spl;
   p->fused[dtype] = f;
   p->fused_ok[dtype] = true;
-  return FRACTAL_OK;
+  return ensure_partials(p);  // the fused kernels' per-CTA sums
 }
 
 int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
@@ -590,85 +701,22 @@ int fractal_map_write(fractal_plan_t p, void* dev_buf, int dtype, double value, 
 }
 
 int fractal_step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, void* stream) {
-  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0)
-    return FRACTAL_EINVAL;
-  if (steps == 0) return FRACTAL_OK;
-  const cudaStream_t st = (cudaStream_t)stream;
-  uint8_t* buf[2] = {a, b};
-  if (p->spl[FRACTAL_U8] > 1 && p->fused_ok[FRACTAL_U8]) {
-    // as for the diffusion: L launches with the parity of `steps`
-    const int spl = p->spl[FRACTAL_U8];
-    int L = (steps + spl - 1) / spl;
-    if ((L & 1) != (steps & 1)) ++L;
-    const int base = steps / L, extra = steps % L;
-    for (int i = 0; i < L; ++i) {
-      const int ns = base + (i < extra ? 1 : 0);
-      cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], buf[i & 1], buf[(i + 1) & 1], ns, spl, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
-    }
-    return FRACTAL_OK;
-  }
-  if (use_tma(p, FRACTAL_U8)) {
-    CUtensorMap maps[2], rings[2];
-    const int rho = 1 << p->log_rho;
-    if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_U8) ||
-        !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_U8))
-      return cuda_fail(cudaErrorInvalidValue, "tensor map");
-    for (int s = 0; s < steps; ++s) {
-      cudaError_t e = launch_ca_tma(p->mode, p->log_rho, p->tma[FRACTAL_U8], maps[s & 1], rings[s & 1],
-                                    buf[(s + 1) & 1], p->d_err, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
-    }
-    return FRACTAL_OK;
-  }
-  for (int s = 0; s < steps; ++s) {
-    cudaError_t e = launch_ca(p->mode, p->log_rho, p->step[FRACTAL_U8], buf[s & 1], buf[(s + 1) & 1], st);
-    if (e != cudaSuccess) return cuda_fail(e, "step_ca");
-  }
-  return FRACTAL_OK;
+  return step_ca(p, a, b, steps, nullptr, stream);
+}
+
+int fractal_step_ca_count(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, double* dev_count, void* stream) {
+  if (!dev_count) return FRACTAL_EINVAL;
+  return step_ca(p, a, b, steps, dev_count, stream);
 }
 
 int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, void* stream) {
-  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0 ||
-      !std::isfinite(coef))
-    return FRACTAL_EINVAL;
-  if (steps == 0) return FRACTAL_OK;
-  const cudaStream_t st = (cudaStream_t)stream;
-  float* buf[2] = {a, b};
-  if (p->spl[FRACTAL_F32] > 1 && p->fused_ok[FRACTAL_F32]) {
-    // L launches of at most spl steps; L has the parity of `steps` so that the
-    // result lands where the single-step ping-pong would leave it
-    const int spl = p->spl[FRACTAL_F32];
-    int L = (steps + spl - 1) / spl;
-    if ((L & 1) != (steps & 1)) ++L;
-    const int base = steps / L, extra = steps % L;
-    for (int i = 0; i < L; ++i) {
-      const int ns = base + (i < extra ? 1 : 0);
-      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[FRACTAL_F32],
-                                             buf[i & 1], buf[(i + 1) & 1], coef, ns, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-    }
-    return FRACTAL_OK;
-  }
-  if (use_tma(p, FRACTAL_F32)) {
-    CUtensorMap maps[2], rings[2];
-    const int rho = 1 << p->log_rho;
-    if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_F32) ||
-        !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_F32))
-      return cuda_fail(cudaErrorInvalidValue, "tensor map");
-    for (int s = 0; s < steps; ++s) {
-      cudaError_t e = launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], rings[s & 1],
-                                           buf[(s + 1) & 1], coef, p->d_err, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-    }
-    return FRACTAL_OK;
-  }
-  for (int s = 0; s < steps; ++s) {
-    cudaError_t e =
-        launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], buf[s & 1], buf[(s + 1) & 1], coef, st);
-    if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-  }
-  return FRACTAL_OK;
+  return step_diffusion(p, a, b, coef, steps, nullptr, stream);
+}
+
+int fractal_step_diffusion_sum(fractal_plan_t p, float* a, float* b, float coef, int steps, double* dev_sum,
+                               void* stream) {
+  if (!dev_sum) return FRACTAL_EINVAL;
+  return step_diffusion(p, a, b, coef, steps, dev_sum, stream);
 }
 
 int fractal_step_diffusion_kappa(fractal_plan_t p, float* a, float* b, const float* kappa, float coef, int steps,

@@ -180,6 +180,40 @@ __device__ __forceinline__ void build_slot_table(uint32_t* tab, const Geo& g) {
 }
 
 // ---------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order (warp trees, then warp 0 over the warps).
+template <typename V>
+__device__ __forceinline__ V block_sum(V v, V* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    V t = lane < nw ? red[lane] : V(0);
+    t = warp_sum(t);
+    return t;
+  }
+  return V(0);
+}
+
+__device__ __forceinline__ int64_t cta_id() { return (int64_t)blockIdx.y * gridDim.x + blockIdx.x; }
+
+// ---------------------------------------------------------------------------
 // uint8 rows <-> bit rows
 // ---------------------------------------------------------------------------
 

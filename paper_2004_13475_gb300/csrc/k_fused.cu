@@ -77,21 +77,31 @@ struct FGeo {
   int log_rho;  // the plan's tile side (write-back of whole member tiles)
 };
 
-// Block of thread t: member blocks first (lambda order, or BB rank order via
-// tab), then the box blocks.  Block coordinates relative to the super-tile.
+// Member blocks the margin boxes can hold: a gasket fragment of side M at
+// each of the three contacts, 3 * 3^log2(W) (tests/test_fusion_boxes.py
+// checks every super-tile position); a launch gives threads to those only.
+__host__ __device__ inline int box_cap(int W) {
+  int c = 3;
+  for (int w = W; w > 1; w >>= 1) c *= 3;
+  return c < 6 * W * W ? c : 6 * W * W;
+}
+constexpr int kMaxBox = 96;  // 6 W^2 for W <= 4
+
+// Member block t of the super-tile (lambda order, or BB rank order via tab).
 template <int MODE>
-__device__ __forceinline__ void fused_block(int t, const FGeo& f, const int* tab, int& bx, int& by) {
-  if (t < f.nb) {
-    if (MODE == kLambda) {
-      lambda_scalar((uint32_t)(t % f.lw), (uint32_t)(t / f.lw), f.L, bx, by);
-    } else {
-      const int j = tab[t];
-      bx = j & ((1 << f.L) - 1);
-      by = j >> f.L;
-    }
-    return;
+__device__ __forceinline__ void member_block(int t, const FGeo& f, const int* tab, int& bx, int& by) {
+  if (MODE == kLambda) {
+    lambda_scalar((uint32_t)(t % f.lw), (uint32_t)(t / f.lw), f.L, bx, by);
+  } else {
+    const int j = tab[t];
+    bx = j & ((1 << f.L) - 1);
+    by = j >> f.L;
   }
-  int b = t - f.nb;
+}
+
+// Box block b (0 <= b < 6 W^2): left, top, right, bottom boxes in row order.
+// Block coordinates relative to the super-tile.
+__device__ __forceinline__ void box_block(int b, const FGeo& f, int& bx, int& by) {
   const int W = f.W, W2 = W * W, side = 1 << f.L;
   if (b < W2) {  // left
     bx = -W + b % W;
@@ -115,19 +125,22 @@ __device__ __forceinline__ void fused_block(int t, const FGeo& f, const int* tab
   by = side + b / (2 * W);
 }
 
-// Thread that owns block (bx, by), or `none` if no staged block is there.
+// Thread that owns block (bx, by), or `none` if no staged member block is
+// there; boxrank: compacted rank of each box block, -1 for non-members.
 template <int MODE>
-__device__ __forceinline__ int fused_owner(int bx, int by, const FGeo& f, int none) {
+__device__ __forceinline__ int fused_owner(int bx, int by, const FGeo& f, const int* boxrank, int none) {
   const int side = 1 << f.L, W = f.W, W2 = W * W;
   if (bx >= 0 && by >= 0 && bx < side && by < side) {
     if (bx & by) return none;
     return MODE == kLambda ? lambda_inverse(bx, by, f.L, f.lw) : bb_rank(bx, by, f.L);
   }
-  if (bx >= -W && bx < 0 && by >= 0 && by < W) return f.nb + by * W + (bx + W);
-  if (bx >= 0 && bx < W && by >= -W && by < 0) return f.nb + W2 + (by + W) * W + bx;
-  if (bx >= side && bx < side + W && by >= -W && by < W) return f.nb + 2 * W2 + (by + W) * W + (bx - side);
-  if (bx >= -W && bx < W && by >= side && by < side + W) return f.nb + 4 * W2 + (by - side) * 2 * W + (bx + W);
-  return none;
+  int b = -1;
+  if (bx >= -W && bx < 0 && by >= 0 && by < W) b = by * W + (bx + W);
+  else if (bx >= 0 && bx < W && by >= -W && by < 0) b = W2 + (by + W) * W + bx;
+  else if (bx >= side && bx < side + W && by >= -W && by < W) b = 2 * W2 + (by + W) * W + (bx - side);
+  else if (bx >= -W && bx < W && by >= side && by < side + W) b = 4 * W2 + (by - side) * 2 * W + (bx + W);
+  if (b < 0 || boxrank[b] < 0) return none;
+  return f.nb + boxrank[b];
 }
 
 __device__ __forceinline__ bool block_member(int gx, int gy, int nblk) {
@@ -199,10 +212,12 @@ __host__ __device__ inline int fused_slots(int threads) { return threads + 1; }
 
 // One super-tile whose block origin is (OX, OY) (in blocks).  All threads of
 // the CTA call it; it ends after the write-back.  ports: 6 * slots floats.
+// Returns this thread's share of the sum of the written members (its block's
+// rows in FP32, the rows in FP64; 0 for box blocks and idle threads).
 template <int MODE>
-__device__ __forceinline__ void fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
-                                                int nsteps, const FGeo& f, int OX, int OY, const int* tab,
-                                                float* ports) {
+__device__ __forceinline__ double fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
+                                                  int nsteps, const FGeo& f, int OX, int OY, const int* tab,
+                                                  float* ports) {
   const int t = threadIdx.x, nthreads = blockDim.x;
   const int slots = fused_slots(nthreads), zero = nthreads;
   const int nblk = f.n / kS;
@@ -210,11 +225,43 @@ __device__ __forceinline__ void fused_supertile(const float* __restrict__ in, fl
   float* PR = ports + 2 * slots;
   float* PD = ports + 4 * slots;
 
+  // the margin boxes' member blocks, compacted in box order: boxrank[b] is
+  // the rank of box block b among them (-1 if not a member), boxlist the list
+  __shared__ int boxrank[kMaxBox], boxlist[kMaxBox], wcnt[16];
+  int nbox_member = 0;
+  for (int b0 = 0; b0 < f.nbox; b0 += nthreads) {
+    const int b = b0 + t;
+    bool m = false;
+    if (b < f.nbox) {
+      int qx, qy;
+      box_block(b, f, qx, qy);
+      m = block_member(OX + qx, OY + qy, nblk);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if ((t & 31) == 0) wcnt[t >> 5] = __popc(bal);
+    __syncthreads();
+    int rank = nbox_member, total = 0;
+    for (int w = 0; w < (nthreads >> 5); ++w) {
+      rank += w < (t >> 5) ? wcnt[w] : 0;
+      total += wcnt[w];
+    }
+    rank += __popc(bal & ((1u << (t & 31)) - 1u));
+    if (b < f.nbox) {
+      boxrank[b] = m ? rank : -1;
+      if (m) boxlist[rank] = b;
+    }
+    nbox_member += total;
+    __syncthreads();
+  }
+
   int bx = 0, by = 0;
   bool active = false;
-  if (t < f.nb + f.nbox) {
-    fused_block<MODE>(t, f, tab, bx, by);
-    active = block_member(OX + bx, OY + by, nblk);
+  if (t < f.nb) {
+    member_block<MODE>(t, f, tab, bx, by);
+    active = true;
+  } else if (t - f.nb < nbox_member && t - f.nb < box_cap(f.W)) {
+    box_block(boxlist[t - f.nb], f, bx, by);
+    active = true;
   }
   const int GX = OX + bx, GY = OY + by;
   // neighbour ports (the zero slot where no staged member block is) and the
@@ -227,10 +274,10 @@ __device__ __forceinline__ void fused_supertile(const float* __restrict__ in, fl
     d0 += (fu ? 1.f : 0.f) + (fl ? 1.f : 0.f);
     dr += fr ? 1.f : 0.f;
     dd += fd ? 1.f : 0.f;
-    if (fu) up = fused_owner<MODE>(bx, by - 1, f, zero);
-    if (fl) lf = fused_owner<MODE>(bx - 1, by, f, zero);
-    if (fr) rt = fused_owner<MODE>(bx + 1, by, f, zero);
-    if (fd) dn = fused_owner<MODE>(bx, by + 1, f, zero);
+    if (fu) up = fused_owner<MODE>(bx, by - 1, f, boxrank, zero);
+    if (fl) lf = fused_owner<MODE>(bx - 1, by, f, boxrank, zero);
+    if (fr) rt = fused_owner<MODE>(bx + 1, by, f, boxrank, zero);
+    if (fd) dn = fused_owner<MODE>(bx, by + 1, f, boxrank, zero);
   }
 
   // stage: the block's 12 member chunks straight into registers
@@ -284,7 +331,20 @@ __device__ __forceinline__ void fused_supertile(const float* __restrict__ in, fl
   }
 
   // write back the super-tile's member blocks (not the boxes)
+  double sum = 0.0;
   if (active && t < f.nb) {
+#pragma unroll
+    for (int j = 0; j < kS; ++j) {
+      float r = 0.f;
+      bool first = true;
+#pragma unroll
+      for (int i = 0; i < kS; ++i) {
+        if (!bmem(i, j)) continue;
+        r = first ? u[j * kS + i] : r + u[j * kS + i];
+        first = false;
+      }
+      sum += (double)r;
+    }
     float* o = out + base;
 #pragma unroll
     for (int j = 0; j < kS; ++j)
@@ -312,6 +372,7 @@ __device__ __forceinline__ void fused_supertile(const float* __restrict__ in, fl
       }
     }
   }
+  return sum;
 }
 
 __device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho) {
@@ -340,10 +401,15 @@ __device__ __forceinline__ void bb_table(int* tab, const FGeo& f) {
 
 template <int MODE>
 __global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                              float a, int nsteps, int M, int log_rho, Geo g) {
+                                                              float a, int nsteps, int M, int log_rho, Geo g,
+                                                              double* __restrict__ partials) {
   extern __shared__ __align__(16) float fsm[];
+  __shared__ double red[32];
   int sx, sy;
-  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  if (!cta_supertile<MODE>(g, sx, sy)) {
+    if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
+    return;
+  }
   const FGeo f = make_fgeo(g.n, g.T, M, log_rho);
   float* ports = fsm;
   int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(blockDim.x));
@@ -351,7 +417,11 @@ __global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __res
     bb_table(tab, f);
     __syncthreads();
   }
-  fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports);
+  const double mine = fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports);
+  if (partials) {  // the sum of the result's members, per CTA (uniform branch)
+    const double s = block_sum<double>(mine, red);
+    if (threadIdx.x == 0) partials[cta_id()] = s;
+  }
 }
 
 // ---------------------------------------------------------------- batches ---
@@ -439,11 +509,11 @@ __global__ void batch_sums_kernel(const BatchInst* __restrict__ inst, int count,
 
 template <int MODE>
 cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
-               cudaStream_t s) {
+               double* partials, cudaStream_t s) {
   auto* k = diffusion_fused_kernel<MODE>;
   cudaError_t e = allow_smem((const void*)k, L.smem);
   if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo);
+  k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials);
   return cudaGetLastError();
 }
 
@@ -458,14 +528,15 @@ int member_blocks(int T) {
 // Margin of a fused launch: the smallest multiple of the block side >= spl.
 int fused_margin(int steps_per_launch) { return (steps_per_launch + kS - 1) / kS * kS; }
 
-// Threads of a fused launch: one per member block and box block, rounded up
-// to whole warps; 0 if the super-tile does not fit (side < 16 or < 2 M, a
-// margin that is not a multiple of 8, more than 512 threads).
+// Threads of a fused launch: one per member block of the super-tile and per
+// member block the margin boxes can hold, rounded up to whole warps; 0 if the
+// super-tile does not fit (side < 16 or < 2 M, a margin that is not a
+// multiple of 8 or above 32, more than 512 threads).
 int fused_threads(const Geo& g, int rho, int margin) {
   (void)rho;
-  if (g.T < 2 * kS || g.T < 2 * margin || margin < kS || margin % kS != 0) return 0;
+  if (g.T < 2 * kS || g.T < 2 * margin || margin < kS || margin % kS != 0 || margin > 4 * kS) return 0;
   const int W = margin / kS;
-  const int t = (member_blocks(g.T) + 6 * W * W + 31) / 32 * 32;
+  const int t = (member_blocks(g.T) + box_cap(W) + 31) / 32 * 32;
   return t > 512 ? 0 : t;
 }
 
@@ -498,11 +569,11 @@ cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items,
 }
 
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
-                                   float a, int nsteps, cudaStream_t s) {
+                                   float a, int nsteps, cudaStream_t s, double* partials) {
   if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads)
     return cudaErrorInvalidValue;
-  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, s)
-                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, s);
+  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, s)
+                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, s);
 }
 
 }  // namespace fractal

@@ -82,11 +82,16 @@ __device__ __forceinline__ uint64_t window(uint32_t l, uint32_t c, uint32_t r) {
 
 template <int MODE>
 __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                                                       int nsteps, int M, int wlev, Geo g) {
+                                                       int nsteps, int M, int wlev, Geo g,
+                                                       unsigned long long* __restrict__ partials) {
   constexpr int TPW = kCaTasksPerWarp;
   extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ unsigned long long red[32];
   int sx, sy;
-  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  if (!cta_supertile<MODE>(g, sx, sy)) {
+    if (partials && threadIdx.x == 0) partials[cta_id()] = 0ull;
+    return;
+  }
   const int n = g.n, T = g.T;
   const int wside = 1 << wlev;                         // word tiles per super-tile side
   int wtiles = 1, wlw = 1;                             // 3^wlev, 3^ceil(wlev/2)
@@ -170,13 +175,15 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     B = tmp;
   }
 
-  // write back the word tiles (whole 32-byte row segments)
+  // write back the word tiles (whole 32-byte row segments); count the alive
+  unsigned alive = 0;
 #pragma unroll
   for (int k = 0; k < TPW; ++k) {
     const int j = warp + k * nw;
     if (off[k] < 0 || j >= wtiles) continue;
     const int c = off[k] % P - 2, y = off[k] / P - M - 1;
     const uint32_t w = A[off[k]];
+    alive += __popc(w);
     uint4 v0, v1;
     v0.x = spread4(w);
     v0.y = spread4(w >> 4);
@@ -190,14 +197,19 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     q[0] = v0;
     q[1] = v1;
   }
+  if (partials) {  // alive members of the result, per CTA (uniform branch)
+    const unsigned long long s = block_sum<unsigned long long>(alive, red);
+    if (threadIdx.x == 0) partials[cta_id()] = s;
+  }
 }
 
 template <int MODE>
-cudaError_t go(const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin, cudaStream_t s) {
+cudaError_t go(const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
+               unsigned long long* partials, cudaStream_t s) {
   auto* k = ca_fused_kernel<MODE>;
   cudaError_t e = allow_smem((const void*)k, L.smem);
   if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, ilog2c(L.geo.T) - 5, L.geo);
+  k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, ilog2c(L.geo.T) - 5, L.geo, partials);
   return cudaGetLastError();
 }
 
@@ -224,9 +236,10 @@ int ca_fused_threads(const Geo& g, int margin) {
 }
 
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
-                            cudaStream_t s) {
+                            cudaStream_t s, unsigned long long* partials) {
   if (nsteps < 1 || nsteps > margin || ca_fused_threads(L.geo, margin) != L.threads) return cudaErrorInvalidValue;
-  return mode == kLambda ? go<kLambda>(L, in, out, nsteps, margin, s) : go<kBB>(L, in, out, nsteps, margin, s);
+  return mode == kLambda ? go<kLambda>(L, in, out, nsteps, margin, partials, s)
+                         : go<kBB>(L, in, out, nsteps, margin, partials, s);
 }
 
 }  // namespace fractal

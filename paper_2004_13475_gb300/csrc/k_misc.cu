@@ -83,36 +83,6 @@ __global__ void __launch_bounds__(512) sw_f32_kernel(float* __restrict__ out, fl
 // Sec. 6.2 RD: sum over all members.  Each CTA writes one partial (0 for a
 // discarded BB block); a single-CTA pass adds the partials in a fixed order.
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-wide sum in a fixed order (warp trees, then warp 0 over the warps).
-template <typename V>
-__device__ __forceinline__ V block_sum(V v, V* red) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    V t = lane < nw ? red[lane] : V(0);
-    t = warp_sum(t);
-    return t;
-  }
-  return V(0);
-}
-
-__device__ __forceinline__ int64_t cta_id() { return (int64_t)blockIdx.y * gridDim.x + blockIdx.x; }
-
 template <int MODE, int LOG_RHO>
 __global__ void __launch_bounds__(512) reduce_u8_kernel(const uint8_t* __restrict__ in,
                                                         unsigned long long* __restrict__ partials, Geo g) {
@@ -244,6 +214,21 @@ cudaError_t go_reduce(int dtype, const Launch& L, const void* in, void* partials
   }
   return cudaGetLastError();
 }
+
+}  // namespace
+
+// Sum of `count` per-CTA partials (uint64 counts for dtype 0, doubles for 1)
+// into *dev_out, one CTA, fixed order.
+cudaError_t launch_final_sum(int dtype, const void* partials, int64_t count, double* dev_out, cudaStream_t s) {
+  if (dtype == 0)
+    final_sum_kernel<unsigned long long>
+        <<<1, 1024, 0, s>>>(static_cast<const unsigned long long*>(partials), count, dev_out);
+  else
+    final_sum_kernel<double><<<1, 1024, 0, s>>>(static_cast<const double*>(partials), count, dev_out);
+  return cudaGetLastError();
+}
+
+namespace {
 
 template <int MODE>
 cudaError_t sw_by_rho(int log_rho, int dtype, const Launch& L, void* out, double value, cudaStream_t s) {

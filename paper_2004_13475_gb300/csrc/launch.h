@@ -36,8 +36,10 @@ cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensor
 int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 
 // Temporally fused diffusion: nsteps (<= margin) steps per launch (k_fused.cu).
+// partials (nullable): one double per CTA of L, the sum of the result's
+// members over the CTA's super-tile (finish with launch_final_sum).
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
-                                   float a, int nsteps, cudaStream_t s);
+                                   float a, int nsteps, cudaStream_t s, double* partials = nullptr);
 int fused_margin(int steps_per_launch);
 int fused_smem_bytes(const Geo& g, int margin);
 int fused_threads(const Geo& g, int rho, int margin);
@@ -45,7 +47,10 @@ int fused_threads(const Geo& g, int rho, int margin);
 // Temporally fused automaton on a bit image: nsteps (<= margin <= 31) steps
 // per launch over 32 x 32-cell word tiles (k_fused_ca.cu).
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned long long* partials = nullptr);
+
+// Sum of per-CTA partials (dtype 0: uint64 counts, 1: doubles) into *dev_out.
+cudaError_t launch_final_sum(int dtype, const void* partials, int64_t count, double* dev_out, cudaStream_t s);
 int ca_fused_smem_bytes(const Geo& g, int margin);
 int ca_fused_threads(const Geo& g, int margin);
 

@@ -100,3 +100,37 @@ def test_automaton_needs_the_wider_boxes():
     assert oracle.is_member(n, T, M) and oracle.is_member(n, T - 1, 0)
     assert not any(x0 <= T < x1 and y0 <= M < y1 for x0, x1, y0, y1 in _boxes(T, M, 4))
     assert any(x0 <= T < x1 and y0 <= M < y1 for x0, x1, y0, y1 in _boxes(T, M, 8))
+
+
+def _active_box_blocks(k, T, M):
+    """Member 8 x 8 blocks in the 4-neighbour margin boxes of every member super-tile."""
+    nblk = (1 << k) // 8
+    s = (1 << k) // T
+    sy, sx = np.nonzero((np.arange(s)[None, :] & np.arange(s)[:, None]) == 0)
+    OX, OY = sx * (T // 8), sy * (T // 8)
+    W, side = M // 8, T // 8
+    boxes = [(-W, 0, 0, W), (0, W, -W, 0), (side, side + W, -W, W), (-W, W, side, side + W)]
+    cnt = np.zeros(sx.size, dtype=np.int64)
+    for x0, x1, y0, y1 in boxes:
+        for by in range(y0, y1):
+            for bx in range(x0, x1):
+                gx, gy = OX + bx, OY + by
+                cnt += (gx >= 0) & (gx < nblk) & (gy >= 0) & (gy < nblk) & ((gx & gy) == 0)
+    return cnt
+
+
+@pytest.mark.parametrize("M", [8, 16, 32])
+def test_member_blocks_of_the_boxes_are_few(M):
+    # The fused diffusion gives a thread only to the member blocks of the
+    # margin boxes: at most 3 * 3^log2(M/8) of the 6 (M/8)^2 (a gasket
+    # fragment of side M at each of the three contacts).  Every member
+    # super-tile position of the largest array is checked.
+    W = M // 8
+    cap = 3 * 3 ** int(np.log2(W))
+    for t in range(4, 10):
+        T = 1 << t
+        if T < 2 * M:
+            continue
+        cnt = _active_box_blocks(16, T, M)
+        assert cnt.max() <= cap, (T, M, cnt.max())
+        assert cnt.max() == cap           # and the bound is reached

@@ -226,6 +226,25 @@ def test_ca_fused_needs_room(fr):
     assert p.info()["steps_per_launch"] == [16, 1]
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("spl", [1, 25])
+def test_ca_count_fused_into_the_steps(fr, mode, spl):
+    k, n = 10, 1024
+    plan = fr.fractal_map(k, 32, mode)
+    if spl > 1:
+        fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_U8, spl)
+    s0 = synth.bernoulli_u8(61, n)
+    mask = domain(k).mask
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    for steps in (0, 1, 7, 40):
+        a = dev_u8(s0)
+        b = torch.zeros_like(a)
+        res = fr.fractal_step_ca_count(plan, a, b, steps, out[1:])
+        want = oracle.ca_run(s0, steps, domain(k))
+        assert out[1].item() == int(want[mask].sum()) == fr.fractal_reduce(plan, res, fr.FRACTAL_U8)
+        assert out[0].item() == -1.0
+
+
 def test_ca_zero_steps_and_states(fr):
     k, n = 6, 64
     plan = fr.fractal_map(k, 16)
@@ -335,6 +354,27 @@ def test_diffusion_zero_coefficient_is_identity(fr, spl):
     got = run_diffusion(fr, plan, u0, 10, a=0.0)
     mask = domain(k).mask
     assert np.array_equal(got[mask], u0[mask])
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("spl", [1, 8, 32])
+def test_diffusion_sum_fused_into_the_steps(fr, mode, spl):
+    k, n = 10, 1024
+    plan = fr.fractal_map(k, 8, mode)
+    if spl > 1:
+        fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
+    u0 = synth.uniform_f32(62, n)
+    dom = domain(k)
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    for steps in (0, 1, 7, 40):
+        a = dev_f32(u0)
+        b = torch.zeros_like(a)
+        res = fr.fractal_step_diffusion_sum(plan, a, b, 0.2, steps, out[1:])
+        got = out[1].item()
+        assert got == pytest.approx(fr.fractal_reduce(plan, res, fr.FRACTAL_F32), rel=1e-6)
+        host = res.cpu().numpy().reshape(n, n)
+        assert got == pytest.approx(oracle.reduce_sum(dom.take(host).astype(np.float64)), rel=1e-6)
+        assert out[0].item() == -1.0
 
 
 def test_fused_needs_room(fr):
