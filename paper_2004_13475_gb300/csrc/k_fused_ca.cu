@@ -27,9 +27,9 @@
 // Tasks.  A task is one word column of at most 32 consecutive rows (a word
 // tile, or a piece of a box); lane i of the warp that owns it keeps row i.
 // Each step a lane reads the 3 x 3 words around its word (rows above and
-// below, columns left and right), builds the three 34-bit row windows,
-// applies the bit-sliced rule, masks births outside the gasket and writes the
-// word to the other image.  Every staged word is the word of exactly one task
+// below, columns left and right), forms the eight neighbour planes by funnel
+// shifts, applies the bit-sliced rule, masks births outside the gasket and
+// writes the word to the other image.  Every staged word is the word of exactly one task
 // lane; every other word of the image is 0 and stays 0.
 #include "launch.h"
 
@@ -75,9 +75,26 @@ __device__ __forceinline__ uint32_t pack32(uint4 a, uint4 b) {
          nz4(b.z) << 24 | nz4(b.w) << 28;
 }
 
-// 34-bit row window of the word p[0] with its neighbours' edge cells.
-__device__ __forceinline__ uint64_t window(uint32_t l, uint32_t c, uint32_t r) {
-  return (uint64_t)(l >> 31) | ((uint64_t)c << 1) | ((uint64_t)(r & 1u) << 33);
+// The eight neighbour planes of a 32-cell word from the 3 x 3 words around
+// it: for each of the rows above, at and below, the word shifted so that bit
+// i holds cell i-1 (funnel shift with the left word's top cell) and cell i+1
+// (with the right word's bottom cell); the row itself contributes only its
+// two shifts.  Summed with full adders into the count's bits 0..2 (a count
+// of 8 wraps to 0, neither 2 nor 3); B3/S23: alive next iff count is 3, or 2
+// and alive now.
+__device__ __forceinline__ uint32_t life_rule_words(uint32_t ul, uint32_t uc, uint32_t ur, uint32_t ml, uint32_t mc,
+                                                    uint32_t mr, uint32_t dl, uint32_t dc, uint32_t dr) {
+  const uint32_t a = __funnelshift_l(ul, uc, 1), b = uc, c = __funnelshift_r(uc, ur, 1);
+  const uint32_t d = __funnelshift_l(ml, mc, 1), e = __funnelshift_r(mc, mr, 1);
+  const uint32_t f = __funnelshift_l(dl, dc, 1), g = dc, h = __funnelshift_r(dc, dr, 1);
+  const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
+  const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
+  const uint32_t s3 = g ^ h, c3 = g & h;
+  const uint32_t bit0 = s1 ^ s2 ^ s3, c4 = (s1 & s2) | (s3 & (s1 ^ s2));
+  const uint32_t t1 = c1 ^ c2 ^ c3, c5 = (c1 & c2) | (c3 & (c1 ^ c2));
+  const uint32_t bit1 = t1 ^ c4, c6 = t1 & c4;
+  const uint32_t bit2 = c5 ^ c6;
+  return bit1 & ~bit2 & (bit0 | mc);
 }
 
 template <int MODE>
@@ -164,10 +181,7 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     for (int k = 0; k < TPW; ++k) {
       if (off[k] < 0) continue;
       const uint32_t* p = A + off[k];
-      const uint64_t up = window(p[-P - 1], p[-P], p[-P + 1]);
-      const uint64_t mid = window(p[-1], p[0], p[1]);
-      const uint64_t dn = window(p[P - 1], p[P], p[P + 1]);
-      B[off[k]] = life_rule32(up, mid, dn) & mk[k];
+      B[off[k]] = life_rule_words(p[-P - 1], p[-P], p[-P + 1], p[-1], p[0], p[1], p[P - 1], p[P], p[P + 1]) & mk[k];
     }
     __syncthreads();
     uint32_t* tmp = A;
