@@ -512,6 +512,42 @@ def diffusion_box_member_blocks(k, T, M):
     return total
 
 
+# Sources each fused kernel is built from: `traffic` is taken from a committed
+# ncu summary only while their hash is the one recorded with it.
+KERNEL_SOURCES = {
+    "diffusion_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_gb300/csrc/gasket.cuh"),
+    "ca_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused_ca.cu", "paper_2004_13475_gb300/csrc/gasket.cuh"),
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def sources_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, k):
+    """DRAM bytes per launch (read + write) of `kernel` at level k from the
+    committed ncu summary (profiles/traffic.txt: kernel, level, bytes, source
+    hash), scaled by the units of a launch (3^(k - level)); None if absent or
+    the kernel's sources changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            for ln in f:
+                parts = ln.split()
+                if len(parts) >= 4 and parts[0] == kernel and not ln.startswith("#"):
+                    if parts[3] != sources_hash(kernel):
+                        return None
+                    return float(parts[2]) * 3.0 ** (k - int(parts[1]))
+    except OSError:
+        return None
+    return None
+
+
 def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind):
     """HBM roofline of one launch of the workload's step kernel: algorithmic
     bytes (every member tile read and written once, plus the margin boxes a
@@ -533,8 +569,10 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind):
     else:
         alg = 2 * info["member_tiles"] * rho * rho
     achieved = alg / launch_s / 1e9
-    return {"kernel": kernel_name(wl, info, spl), "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+    name = kernel_name(wl, info, spl)
+    traffic = measured_traffic(name.split("<")[0], info["k"]) if spl > 1 else None
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "alg_bytes_per_launch": alg, "launch_us": launch_s * 1e6, "steps_per_launch": spl}
 
 
