@@ -425,6 +425,8 @@ def main():
         line["detail"] = kernel_detail(fr, torch, stream, lambda rho, mode: tuned[("diffusion", mode, rho)][0],
                                        lambda rho, mode: tuned[("ca", mode, rho)][0], ca_a, ca_b, u_a, u_b, hbm)
 
+    if rank == 0 and not args.no_detail:
+        line["lambda_forms"] = lambda_forms(fr, torch, stream)
     if rank == 0 and not args.no_batch:
         line["batched"] = batched(fr, torch, stream, SEED + 17)
     if rank == 0 and not args.no_adjoint:
@@ -613,6 +615,30 @@ def profile_run(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "k": args.k, "rho": args.rho, "mode": args.mode,
                       "launches": args.launches, "plan": plan.info()}))
+
+
+def lambda_forms(fr, torch, stream):
+    """The block table of level r_b = 16 (k = 16, rho = 1: 3^16 omegas) by the
+    three forms of lambda: warp ballot, per thread, tensor-core MMA (Sec. 6.3)."""
+    plan = fr.fractal_map(K, 1)
+    m = plan.info()["member_tiles"]
+    xy = torch.empty(2 * m, dtype=torch.int32, device="cuda")
+    out = {"omegas": m}
+    for name, method in (("ballot", 0), ("per_thread", 1), ("mma", 2)):
+        for _ in range(2):
+            fr.fractal_map_blocks_method(plan, xy, method, stream)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(5):
+            fr.fractal_map_blocks_method(plan, xy, method, stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        t = t0.elapsed_time(t1) / 1e3 / 5
+        out[name] = {"us": t * 1e6, "omegas_per_s": m / t}
+    out["mma_kept"] = out["mma"]["us"] < min(out["ballot"]["us"], out["per_thread"]["us"])
+    plan.close()
+    return out
 
 
 def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):

@@ -177,6 +177,22 @@ int fractal_plan_device_status(fractal_plan_t plan, int* code);
 int fractal_map_blocks(fractal_plan_t plan, int32_t* dev_xy, void* stream);
 
 /*
+ * fractal_map_blocks_method -- the same table by one of three forms of
+ * lambda: FRACTAL_MAP_BALLOT (one warp per omega, lane mu-1 computes level
+ * mu, a ballot sums the Delta terms; what the step kernels use),
+ * FRACTAL_MAP_SCALAR (one thread per omega), FRACTAL_MAP_MMA (the tensor-core
+ * encoding of Sec. 6.3: 16 omegas per warp, their level bits as a 16 x 16
+ * bf16 matrix times the powers of two, FP32 accumulate; exact, since the
+ * entries are 0, 1 and powers of two and the sums stay below 2^24).  All
+ * three write the same table; the method only changes the speed.  dev_xy
+ * 8-byte aligned.  Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
+ */
+#define FRACTAL_MAP_BALLOT 0
+#define FRACTAL_MAP_SCALAR 1
+#define FRACTAL_MAP_MMA 2
+int fractal_map_blocks_method(fractal_plan_t plan, int32_t* dev_xy, int method, void* stream);
+
+/*
  * fractal_map_write -- the single-write test of Sec. 6.2 (SW): write `value`
  * (cast to dtype; uint8 takes (uint8_t)value) at every member cell of the
  * n x n device array dev_buf, 0 at the non-member cells of member tiles;

@@ -44,7 +44,7 @@ EXPORTS = (
     "fractal_batch_graph_capture", "fractal_batch_graph_launch", "fractal_batch_get_info",
     "fractal_step_diffusion_kappa", "fractal_adjoint_diffusion_step",
     "fractal_step_diffusion_kappa_f64", "fractal_adjoint_diffusion_step_f64",
-    "fractal_step_ca_count", "fractal_step_diffusion_sum",
+    "fractal_step_ca_count", "fractal_step_diffusion_sum", "fractal_map_blocks_method",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -138,6 +138,7 @@ def _load() -> ctypes.CDLL:
         "fractal_adjoint_diffusion_step": (I, [P, VP, VP, VP, VP, VP, F, VP]),
         "fractal_step_diffusion_kappa_f64": (I, [P, VP, VP, VP, D, I, VP]),
         "fractal_step_ca_count": (I, [P, VP, VP, I, VP, VP]),
+        "fractal_map_blocks_method": (I, [P, VP, I, VP]),
         "fractal_step_diffusion_sum": (I, [P, VP, VP, F, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
     }
@@ -247,6 +248,16 @@ def fractal_plan_device_status(plan: Plan) -> int:
 
 def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:
     _check(_load().fractal_map_blocks(plan.handle, _ptr(dev_xy), _stream(stream)), "fractal_map_blocks")
+
+
+FRACTAL_MAP_BALLOT = 0
+FRACTAL_MAP_SCALAR = 1
+FRACTAL_MAP_MMA = 2
+
+
+def fractal_map_blocks_method(plan: Plan, dev_xy, method: int, stream=None) -> None:
+    _check(_load().fractal_map_blocks_method(plan.handle, _ptr(dev_xy), int(method), _stream(stream)),
+           "fractal_map_blocks_method")
 
 
 def fractal_map_write(plan: Plan, buf, dtype: int, value: float, stream=None) -> None:

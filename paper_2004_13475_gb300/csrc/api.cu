@@ -687,9 +687,15 @@ int fractal_plan_device_status(fractal_plan_t p, int* code) {
 }
 
 int fractal_map_blocks(fractal_plan_t p, int32_t* dev_xy, void* stream) {
-  if (check_plan(p) || !dev_xy) return FRACTAL_EINVAL;
+  return fractal_map_blocks_method(p, dev_xy, FRACTAL_MAP_BALLOT, stream);
+}
+
+int fractal_map_blocks_method(fractal_plan_t p, int32_t* dev_xy, int method, void* stream) {
+  if (check_plan(p) || !dev_xy || (reinterpret_cast<uintptr_t>(dev_xy) & 7u) != 0) return FRACTAL_EINVAL;
+  if (method != FRACTAL_MAP_BALLOT && method != FRACTAL_MAP_SCALAR && method != FRACTAL_MAP_MMA)
+    return FRACTAL_EINVAL;
   const int w = (int)ipow(3, (p->rb + 1) / 2), h = (int)ipow(3, p->rb / 2);
-  cudaError_t e = launch_map_blocks(dev_xy, w, h, p->rb, (cudaStream_t)stream);
+  cudaError_t e = launch_map_blocks(dev_xy, w, h, p->rb, (cudaStream_t)stream, method);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "map_blocks");
 }
 

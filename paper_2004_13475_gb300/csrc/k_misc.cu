@@ -29,6 +29,91 @@ __global__ void map_blocks_kernel(int32_t* __restrict__ out, int w, int h, int l
   }
 }
 
+// One thread per omega: the per-thread form of the map.
+__global__ void map_blocks_scalar_kernel(int32_t* __restrict__ out, int w, int h, int levels) {
+  const int64_t total = (int64_t)w * h;
+  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+    int bx, by;
+    lambda_scalar((uint32_t)(id % w), (uint32_t)(id / w), levels, bx, by);
+    reinterpret_cast<int2*>(out)[id] = make_int2(bx, by);
+  }
+}
+
+// Tensor-core form of the digit-to-offset sum (Sec. 6.3, many blocks per
+// MMA): for 16 omegas per warp, A (16 x 16, bf16 0/1) holds in column c < 8
+// the x bit tau_x of level mu = c + 1 + 8h and in column c >= 8 the flipped y
+// bit of level mu = c - 7 + 8h; B (16 x 8) holds 2^c in column 0 for c < 8
+// and 2^(c-8) in column 1 for c >= 8.  D = A B has lambda_x and lambda_y of
+// those 8 levels in its columns 0 and 1 (bf16 holds 0, 1 and 2^c exactly;
+// FP32 sums < 2^24 are exact).  Half h = 1 (levels 9..16) is a second MMA,
+// weighted by 2^8.  Fragment layouts of mma.m16n8k16 (PTX ISA): lane =
+// 4 * group + tig; A registers {r0,r1} of rows group / group+8 at columns
+// 2 tig + {0,1}, {r2,r3} at columns 2 tig + 8 + {0,1}; B registers at rows
+// 2 tig + {0,1} and 2 tig + 8 + {0,1} of column group; D {d0,d1} row group,
+// {d2,d3} row group + 8, columns 2 tig + {0,1}.
+__device__ __forceinline__ uint32_t bf16_bits(bool one_lo, bool one_hi) {
+  return (one_lo ? 0x3F80u : 0u) | (one_hi ? 0x3F800000u : 0u);
+}
+
+// bit of level mu (1-based) of omega (wx, wy): x bit [beta == 2] or flipped
+// y bit [beta == 0], beta = digit ceil(mu/2)-1 of wx (odd mu) or wy (even mu)
+__device__ __forceinline__ bool level_bit(uint32_t wx, uint32_t wy, int mu, int levels, bool ybit) {
+  if (mu > levels) return false;
+  uint32_t v = (mu & 1) ? wx : wy;
+  for (int j = 0; j < (mu + 1) / 2 - 1; ++j) v /= 3u;
+  const uint32_t beta = v % 3u;
+  return ybit ? beta == 0u : beta == 2u;
+}
+
+__global__ void map_blocks_mma_kernel(int32_t* __restrict__ out, int w, int h, int levels) {
+  const int64_t total = (int64_t)w * h;
+  const int lane = threadIdx.x & 31, group = lane >> 2, tig = lane & 3;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // B fragment (the same for both halves): rows k = 2 tig + {0,1} and
+  // 2 tig + 8 + {0,1}, column n = group
+  auto bval = [&](int k) -> uint32_t {
+    if (group == 0 && k < 8) return 0x3F80u + ((uint32_t)k << 7);         // 2^k
+    if (group == 1 && k >= 8) return 0x3F80u + ((uint32_t)(k - 8) << 7);  // 2^(k-8)
+    return 0u;
+  };
+  const uint32_t b0 = bval(2 * tig) | (bval(2 * tig + 1) << 16);
+  const uint32_t b1 = bval(2 * tig + 8) | (bval(2 * tig + 9) << 16);
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16; base < total;
+       base += warps * 16) {
+    const int64_t id0 = base + group, id1 = base + group + 8;
+    const uint32_t x0 = (uint32_t)(id0 % w), y0 = (uint32_t)(id0 / w);
+    const uint32_t x1 = (uint32_t)(id1 % w), y1 = (uint32_t)(id1 / w);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int half = 0; half < 2 && 8 * half < levels; ++half) {
+      // A entry for (omega, column c) of this half
+      auto abit = [&](uint32_t wx, uint32_t wy, int c) -> bool {
+        return c < 8 ? level_bit(wx, wy, c + 1 + 8 * half, levels, false)
+                     : level_bit(wx, wy, c - 7 + 8 * half, levels, true);
+      };
+      const int c0 = 2 * tig, c1 = 2 * tig + 8;
+      const uint32_t a0 = bf16_bits(abit(x0, y0, c0), abit(x0, y0, c0 + 1));
+      const uint32_t a1 = bf16_bits(abit(x1, y1, c0), abit(x1, y1, c0 + 1));
+      const uint32_t a2 = bf16_bits(abit(x0, y0, c1), abit(x0, y0, c1 + 1));
+      const uint32_t a3 = bf16_bits(abit(x1, y1, c1), abit(x1, y1, c1 + 1));
+      float d0, d1, d2, d3;
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+          "{%10,%11,%12,%13};"
+          : "=f"(d0), "=f"(d1), "=f"(d2), "=f"(d3)
+          : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f), "f"(0.f), "f"(0.f), "f"(0.f));
+      const float scale = half ? 256.f : 1.f;
+      acc[0] += scale * d0;
+      acc[1] += scale * d1;
+      acc[2] += scale * d2;
+      acc[3] += scale * d3;
+    }
+    if (tig == 0) {
+      if (id0 < total) reinterpret_cast<int2*>(out)[id0] = make_int2((int)acc[0], (int)acc[1]);
+      if (id1 < total) reinterpret_cast<int2*>(out)[id1] = make_int2((int)acc[2], (int)acc[3]);
+    }
+  }
+}
+
 // ----------------------------------------------------------------- SW -------
 // Sec. 6.2 SW: `value` at every member of every member tile, 0 at the tile's
 // other cells; no loads.
@@ -259,12 +344,19 @@ cudaError_t rd_by_rho(int log_rho, int dtype, const Launch& L, const void* in, v
 
 }  // namespace
 
-cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s) {
+cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s, int method) {
   const int64_t total = (int64_t)w * h;
-  int64_t blocks = (total + 7) / 8;  // 8 warps per block, one omega per warp per pass
+  // per pass: one omega per warp (ballot), per thread (scalar), 16 per warp (MMA)
+  const int64_t per_cta = method == 1 ? 256 : method == 2 ? 8 * 16 : 8;
+  int64_t blocks = (total + per_cta - 1) / per_cta;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  map_blocks_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, w, h, levels);
+  if (method == 1)
+    map_blocks_scalar_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, w, h, levels);
+  else if (method == 2)
+    map_blocks_mma_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, w, h, levels);
+  else
+    map_blocks_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, w, h, levels);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ cudaError_t launch_sw(int mode, int log_rho, int dtype, const Launch& L, void* o
                       cudaStream_t s);
 cudaError_t launch_reduce(int mode, int log_rho, int dtype, const Launch& L, const void* in,
                           void* partials, double* dev_out, cudaStream_t s);
-cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s);
+// method: 0 warp ballot (one omega per warp), 1 per thread, 2 tensor-core MMA
+cudaError_t launch_map_blocks(int32_t* out, int w, int h, int levels, cudaStream_t s, int method = 0);
 
 // TMA-staged step kernels (rho * element size >= 16 bytes; see k_tma.cu).
 // `map` has rho x rho boxes over the input array, `ring` 16-byte boxes of one row.

@@ -62,6 +62,33 @@ def test_map_blocks_bit_exact(fr, k, rho):
     assert np.array_equal(xy.cpu().numpy(), oracle.block_table(k, rho).reshape(-1))
 
 
+@pytest.mark.parametrize("method", [1, 2])     # per thread, tensor-core MMA
+@pytest.mark.parametrize("k,rho", cases(range(0, 12)))
+def test_map_blocks_methods_bit_exact(fr, k, rho, method):
+    plan = fr.fractal_map(k, rho)
+    info = plan.info()
+    xy = torch.full((2 * info["member_tiles"] + 2,), -7, dtype=torch.int32, device="cuda")
+    fr.fractal_map_blocks_method(plan, xy, method)
+    got = xy.cpu().numpy()
+    assert np.array_equal(got[:-2], oracle.block_table(k, rho).reshape(-1))
+    assert got[-2] == -7 and got[-1] == -7           # nothing past the table
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+def test_map_blocks_methods_level16(fr, method):
+    # 16 levels (k = 16, rho = 1): both MMA halves; the three forms agree everywhere
+    plan = fr.fractal_map(16, 1)
+    m = plan.info()["member_tiles"]
+    ref = torch.empty(2 * m, dtype=torch.int32, device="cuda")
+    fr.fractal_map_blocks(plan, ref)
+    xy = torch.full((2 * m,), -1, dtype=torch.int32, device="cuda")
+    fr.fractal_map_blocks_method(plan, xy, method)
+    assert torch.equal(xy, ref)
+    W = plan.info()["grid_w"]
+    for wx, wy in [(0, 0), (W - 1, 0), (5, 7), (W - 1, plan.info()["grid_h"] - 1), (1234, 321)]:
+        assert tuple(xy[2 * (wy * W + wx):2 * (wy * W + wx) + 2].tolist()) == oracle.lambda_canonical(wx, wy, 16)
+
+
 def test_map_blocks_level16(fr):
     # full-size block level r_b = 13 (k = 16, rho = 8): bijection onto member blocks
     plan = fr.fractal_map(16, 8)
