@@ -35,6 +35,9 @@ namespace fractal {
 namespace {
 
 constexpr int kS = 8;  // block side in cells
+// Largest CTA of a fused launch (super-tile side 256 with 32-cell margins:
+// 243 + 27 blocks); four such CTAs share an SM (56 registers a thread).
+constexpr int kFusedMaxThreads = 288;
 
 __host__ __device__ constexpr bool bmem(int i, int j) { return i >= 0 && j >= 0 && i < kS && j < kS && (i & j) == 0; }
 __host__ __device__ constexpr int bdeg(int i, int j) {
@@ -400,7 +403,7 @@ __device__ __forceinline__ void bb_table(int* tab, const FGeo& f) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(512) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
+__global__ void __launch_bounds__(kFusedMaxThreads, 4) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                               float a, int nsteps, int M, int log_rho, Geo g,
                                                               double* __restrict__ partials) {
   extern __shared__ __align__(16) float fsm[];
@@ -438,7 +441,7 @@ __device__ __forceinline__ int batch_instance(const BatchInst* __restrict__ inst
   return lo;
 }
 
-__global__ void __launch_bounds__(512) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
+__global__ void __launch_bounds__(kFusedMaxThreads, 4) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
                                                               int64_t items, int which, float a, int nsteps, int M,
                                                               int T) {
   extern __shared__ __align__(16) float fsm[];
@@ -531,13 +534,13 @@ int fused_margin(int steps_per_launch) { return (steps_per_launch + kS - 1) / kS
 // Threads of a fused launch: one per member block of the super-tile and per
 // member block the margin boxes can hold, rounded up to whole warps; 0 if the
 // super-tile does not fit (side < 16 or < 2 M, a margin that is not a
-// multiple of 8 or above 32, more than 512 threads).
+// multiple of 8 or above 32, more than kFusedMaxThreads threads).
 int fused_threads(const Geo& g, int rho, int margin) {
   (void)rho;
   if (g.T < 2 * kS || g.T < 2 * margin || margin < kS || margin % kS != 0 || margin > 4 * kS) return 0;
   const int W = margin / kS;
   const int t = (member_blocks(g.T) + box_cap(W) + 31) / 32 * 32;
-  return t > 512 ? 0 : t;
+  return t > kFusedMaxThreads ? 0 : t;
 }
 
 int fused_smem_bytes(const Geo& g, int margin) {
