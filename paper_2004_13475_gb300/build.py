@@ -22,6 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfractal.so")
 SYNTH_SRC = os.path.join(ROOT, "synth", "synth.cu")
 SYNTH_LIB = os.path.join(ROOT, "synth", "libsynth.so")
+EXPORTS_MAP = os.path.join(CSRC, "exports.map")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -87,8 +88,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             futs.append(ex.submit(_run, *synth_job))
         for f in futs:
             f.result()
-    if force or jobs or _stale(LIB, objs):
-        _run([nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"])
+    if force or jobs or _stale(LIB, objs + [EXPORTS_MAP]):
+        # export the C ABI only (the library's internal C++ symbols stay local)
+        _run([nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart", "-Xlinker",
+                                                              "--version-script=" + EXPORTS_MAP])
     if verbose:
         print(f"built {LIB}")
     return LIB

@@ -52,6 +52,7 @@ struct fractal_plan_s {
   bool tma_ok[2] = {false, false};
   Launch aux[2];                // SW / reduce kernels (slot table only in shared memory)
   int spl[2] = {1, 1};          // steps per launch (temporal fusion), per dtype
+  bool user_levels[2] = {false, false};  // tile levels fixed by the caller
   Launch fused[2];              // fused kernel launch for the plan's steps per launch
   bool fused_ok[2] = {false, false};
   int* d_err = nullptr;         // device error word of the TMA kernels
@@ -265,8 +266,22 @@ bool use_tma(const fractal_plan_s* p, int dtype) {
 
 int default_levels(const fractal_plan_s& p, int dtype) { return default_cta_levels(p.k, p.log_rho, p.mode, dtype); }
 
+// Float32 single write and reduce run one 8 x 8 block per thread (their own
+// super-tiles) unless the caller fixed the tile levels of the plan, which
+// then hold for these kernels too (rho-tiles per CTA, the paper's setting at
+// levels 0).
+bool use_blocks(const fractal_plan_s* p, int dtype, Launch& B, int& levels) {
+  return dtype == FRACTAL_F32 && !p->user_levels[FRACTAL_F32] && p->log_rho >= 2 &&
+         blocks_geometry(p->k, p->mode, B, levels);
+}
+
 int ensure_partials(fractal_plan_s* p) {
   size_t need = 1;
+  {
+    Launch B;
+    int levels = 0;
+    if (use_blocks(p, FRACTAL_F32, B, levels)) need = (size_t)B.grid.x * B.grid.y;
+  }
   for (int d = 0; d < 2; ++d) {
     const size_t c = (size_t)p->aux[d].grid.x * p->aux[d].grid.y;
     if (c > need) need = c;
@@ -536,7 +551,15 @@ int fractal_plan_get_info(fractal_plan_t p, fractal_plan_info* info) {
   return FRACTAL_OK;
 }
 
+static int set_levels(fractal_plan_t p, int dtype, int levels);
+
 int fractal_plan_set_cta_levels(fractal_plan_t p, int dtype, int levels) {
+  const int st = set_levels(p, dtype, levels);
+  if (st == FRACTAL_OK) p->user_levels[dtype] = true;
+  return st;
+}
+
+static int set_levels(fractal_plan_t p, int dtype, int levels) {
   if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32)) return FRACTAL_EINVAL;
   Launch s, a, t;
   bool ok = false;
@@ -619,7 +642,7 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   };
   bool f32_fused_timed = false;  // the float32 fused kernel picks its own super-tile: time it once
   for (int m = 0; m <= kMaxLevelsPerCta && m <= p->rb && status == FRACTAL_OK; ++m) {
-    if (fractal_plan_set_cta_levels(p, dtype, m) != FRACTAL_OK) continue;
+    if (set_levels(p, dtype, m) != FRACTAL_OK) continue;
     const bool skip_f32_fused = dtype == FRACTAL_F32 && f32_fused_timed;
     f32_fused_timed = true;
     // candidates: (schedule, steps per launch)
@@ -670,7 +693,7 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   // keep the winner (or restore the previous choice on failure)
   const bool ok = status == FRACTAL_OK && best >= 0.f;
   const bool own_tile = dtype == FRACTAL_F32 && best_spl > 1;
-  fractal_plan_set_cta_levels(p, dtype, ok ? (own_tile ? best1_m : best_m) : old_m);
+  set_levels(p, dtype, ok ? (own_tile ? best1_m : best_m) : old_m);
   p->sched = ok ? (best_sched == FRACTAL_SCHED_STAGED ? FRACTAL_SCHED_STAGED : FRACTAL_SCHED_AUTO) : old_sched;
   fractal_plan_set_steps_per_launch(p, dtype, ok ? best_spl : old_spl);
   if (ok && best_us) *best_us = best;
@@ -702,7 +725,14 @@ int fractal_map_blocks_method(fractal_plan_t p, int32_t* dev_xy, int method, voi
 int fractal_map_write(fractal_plan_t p, void* dev_buf, int dtype, double value, void* stream) {
   if (check_plan(p) || !dev_buf || !aligned16(dev_buf)) return FRACTAL_EINVAL;
   if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
-  cudaError_t e = launch_sw(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, value, (cudaStream_t)stream);
+  Launch B;
+  int levels = 0;
+  cudaError_t e;
+  if (use_blocks(p, dtype, B, levels))
+    e = launch_sw_blocks(p->mode, p->log_rho, B, levels, static_cast<float*>(dev_buf), (float)value,
+                         (cudaStream_t)stream);
+  else
+    e = launch_sw(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, value, (cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "map_write");
 }
 
@@ -748,8 +778,15 @@ int fractal_adjoint_diffusion_step_f64(fractal_plan_t p, const double* u, const 
 int fractal_reduce_async(fractal_plan_t p, const void* dev_buf, int dtype, double* dev_out, void* stream) {
   if (check_plan(p) || !dev_buf || !dev_out || !aligned16(dev_buf)) return FRACTAL_EINVAL;
   if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
-  cudaError_t e = launch_reduce(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, p->d_partials, dev_out,
-                                (cudaStream_t)stream);
+  Launch B;
+  int levels = 0;
+  cudaError_t e;
+  if (use_blocks(p, dtype, B, levels))
+    e = launch_reduce_blocks(p->mode, B, levels, static_cast<const float*>(dev_buf),
+                             static_cast<double*>(p->d_partials), dev_out, (cudaStream_t)stream);
+  else
+    e = launch_reduce(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, p->d_partials, dev_out,
+                      (cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "reduce");
 }
 

@@ -1,0 +1,140 @@
+// 8 x 8-cell blocks of the gasket (internal): a block (BX, BY) with BX & BY
+// == 0 holds the 27 members (i, j), i & j == 0, of a level-3 gasket and meets
+// the rest of the gasket through four links only: (0,0) to (0,7) of the block
+// above and to (7,0) of the block left, (7,0) to (0,0) of the block right,
+// (0,7) to (0,0) of the block below.  Its member cells lie in 12 of its 16
+// 16-byte row chunks (columns 0-3 of every row, 4-7 of rows 0-3); a row of 8
+// floats is one 32-byte sector.
+#pragma once
+
+#include "gasket.cuh"
+
+namespace fractal {
+namespace {
+
+constexpr int kB = 8;
+
+__host__ __device__ constexpr bool amem(int i, int j) { return i >= 0 && j >= 0 && i < kB && j < kB && (i & j) == 0; }
+
+__device__ __forceinline__ bool ablock(int gx, int gy, int nblk) {
+  return (unsigned)gx < (unsigned)nblk && (unsigned)gy < (unsigned)nblk && (gx & gy) == 0;
+}
+
+// Four consecutive values of a row, 16-byte accesses.
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 c = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = c.x;
+  v[1] = c.y;
+  v[2] = c.z;
+  v[3] = c.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 c0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 c1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = c0.x;
+  v[1] = c0.y;
+  v[2] = c1.x;
+  v[3] = c1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// The block's member values (0 at non-members) from a row-major n x n array.
+template <typename T>
+__device__ __forceinline__ void load_block(T (&v)[kB * kB], const T* __restrict__ p, int n) {
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    ld4(p + (size_t)j * n, &v[j * kB]);
+    if (j < 4) {
+      ld4(p + (size_t)j * n + 4, &v[j * kB + 4]);
+    } else {
+#pragma unroll
+      for (int i = 4; i < kB; ++i) v[j * kB + i] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < kB; ++i)
+      if (!amem(i, j)) v[j * kB + i] = T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_block(T* __restrict__ p, int n, const T (&v)[kB * kB]) {
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    st4(p + (size_t)j * n, &v[j * kB]);
+    st4(p + (size_t)j * n + 4, &v[j * kB + 4]);
+  }
+}
+
+// Neighbour cells at the ports: up (0,-1), left (-1,0), right (8,0), down
+// (0,8) relative to the block origin; 0 where that block is not a member
+// (or outside the array).
+template <typename T>
+struct Ports {
+  T up, lf, rt, dn;
+};
+
+template <typename T>
+__device__ __forceinline__ Ports<T> load_ports(const T* __restrict__ base, int n, bool hu, bool hl, bool hr, bool hd) {
+  Ports<T> q;
+  q.up = hu ? __ldg(base - n) : T(0);
+  q.lf = hl ? __ldg(base - 1) : T(0);
+  q.rt = hr ? __ldg(base + kB) : T(0);
+  q.dn = hd ? __ldg(base + (size_t)kB * n) : T(0);
+  return q;
+}
+
+// Visit the member neighbours of member cell (i, j): f(u there, kappa there,
+// x there) for three fields u, kappa, x of the block and its ports.
+template <typename T, typename F>
+__device__ __forceinline__ void for_neighbours(int i, int j, const T (&u)[kB * kB], const float (&k)[kB * kB],
+                                               const T (&x)[kB * kB], const Ports<T>& pu, const Ports<float>& pk,
+                                               const Ports<T>& px, bool hu, bool hl, bool hr, bool hd, F f) {
+  if (amem(i, j - 1)) f(u[(j - 1) * kB + i], k[(j - 1) * kB + i], x[(j - 1) * kB + i]);
+  if (amem(i - 1, j)) f(u[j * kB + i - 1], k[j * kB + i - 1], x[j * kB + i - 1]);
+  if (amem(i + 1, j)) f(u[j * kB + i + 1], k[j * kB + i + 1], x[j * kB + i + 1]);
+  if (amem(i, j + 1)) f(u[(j + 1) * kB + i], k[(j + 1) * kB + i], x[(j + 1) * kB + i]);
+  if (i == 0 && j == 0) {
+    if (hu) f(pu.up, pk.up, px.up);
+    if (hl) f(pu.lf, pk.lf, px.lf);
+  }
+  if (i == kB - 1 && j == 0 && hr) f(pu.rt, pk.rt, px.rt);
+  if (i == 0 && j == kB - 1 && hd) f(pu.dn, pk.dn, px.dn);
+}
+
+// This thread's block and whether it and its four neighbour blocks are members.
+struct BlockPos {
+  bool active;
+  bool hu, hl, hr, hd;
+  size_t base;  // element index of the block origin
+};
+
+template <int MODE>
+__device__ __forceinline__ bool block_pos(const Geo& g, int L, BlockPos& b) {
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return false;  // whole CTA: BB slot off the gasket
+  int nb = 1, lw = 1;
+  for (int i = 0; i < L; ++i) nb *= 3;
+  for (int i = 0; i < (L + 1) / 2; ++i) lw *= 3;
+  b.active = false;
+  const int t = threadIdx.x;
+  if (t >= nb) return true;
+  int bx, by;
+  lambda_scalar((uint32_t)(t % lw), (uint32_t)(t / lw), L, bx, by);
+  const int GX = (sx << L) + bx, GY = (sy << L) + by, nblk = g.n / kB;
+  b.active = true;
+  b.hu = ablock(GX, GY - 1, nblk);
+  b.hl = ablock(GX - 1, GY, nblk);
+  b.hr = ablock(GX + 1, GY, nblk);
+  b.hd = ablock(GX, GY + 1, nblk);
+  b.base = (size_t)GY * kB * (size_t)g.n + (size_t)GX * kB;
+  return true;
+}
+
+}  // namespace
+}  // namespace fractal
