@@ -700,7 +700,8 @@ def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
                 rec["sw_u8" + suffix] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm,
                                          "cta_levels": lv[0]}
                 t = clock(lambda: fr.fractal_reduce_async(pl, u_a, fr.FRACTAL_F32, dev_out, stream))
-                b = tiles * rho * rho * 4
+                # the default reduce reads member 8 x 8 blocks (8 sectors each) whatever rho is
+                b = tiles * rho * rho * 4 if lv_name == "tile_per_cta" else 3 ** (K - 3) * 256
                 rec["reduce_f32" + suffix] = {"us": t * 1e6, "alg_gbs": b / t / 1e9, "frac": b / t / 1e9 / hbm,
                                               "cta_levels": lv[1]}
                 pl.close()

@@ -111,11 +111,11 @@ int fractal_plan_get_info(fractal_plan_t plan, fractal_plan_info* info);
  * unrolling"): a CTA handles the 3^levels member tiles (lambda) or 4^levels
  * tile slots (BB) of one super-tile of side rho * 2^levels; the grid maps
  * super-tiles (level r_b - levels).  0 <= levels <= min(r_b, 5), and the
- * super-tile must fit in shared memory.  By default the float32 single write
- * and reduce run their own kernels (one 8 x 8 block of the gasket per
- * thread, rho >= 4, k >= 3); once this is called for FRACTAL_F32 they run
- * the rho-tile kernels at these levels too (levels 0: one tile per CTA, the
- * paper's block-per-tile setting).  Errors: FRACTAL_EINVAL, FRACTAL_ENOMEM
+ * super-tile must fit in shared memory.  The single write runs rho-tile
+ * kernels at these levels.  By default the float32 reduce runs its own kernel
+ * (one 8 x 8 block of the gasket per thread, rho >= 4, k >= 3); once this is
+ * called for FRACTAL_F32 it runs the rho-tile kernel at these levels too
+ * (levels 0: one tile per CTA, the paper's block-per-tile setting).  Errors: FRACTAL_EINVAL, FRACTAL_ENOMEM
  * (reduce scratch could not grow).
  */
 int fractal_plan_set_cta_levels(fractal_plan_t plan, int dtype, int levels);

@@ -266,10 +266,9 @@ bool use_tma(const fractal_plan_s* p, int dtype) {
 
 int default_levels(const fractal_plan_s& p, int dtype) { return default_cta_levels(p.k, p.log_rho, p.mode, dtype); }
 
-// Float32 single write and reduce run one 8 x 8 block per thread (their own
-// super-tiles) unless the caller fixed the tile levels of the plan, which
-// then hold for these kernels too (rho-tiles per CTA, the paper's setting at
-// levels 0).
+// The float32 reduce runs one 8 x 8 block per thread (its own super-tiles)
+// unless the caller fixed the tile levels of the plan, which then hold for
+// it too (rho-tiles per CTA, the paper's setting at levels 0).
 bool use_blocks(const fractal_plan_s* p, int dtype, Launch& B, int& levels) {
   return dtype == FRACTAL_F32 && !p->user_levels[FRACTAL_F32] && p->log_rho >= 2 &&
          blocks_geometry(p->k, p->mode, B, levels);
@@ -725,14 +724,7 @@ int fractal_map_blocks_method(fractal_plan_t p, int32_t* dev_xy, int method, voi
 int fractal_map_write(fractal_plan_t p, void* dev_buf, int dtype, double value, void* stream) {
   if (check_plan(p) || !dev_buf || !aligned16(dev_buf)) return FRACTAL_EINVAL;
   if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
-  Launch B;
-  int levels = 0;
-  cudaError_t e;
-  if (use_blocks(p, dtype, B, levels))
-    e = launch_sw_blocks(p->mode, p->log_rho, B, levels, static_cast<float*>(dev_buf), (float)value,
-                         (cudaStream_t)stream);
-  else
-    e = launch_sw(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, value, (cudaStream_t)stream);
+  cudaError_t e = launch_sw(p->mode, p->log_rho, dtype, p->aux[dtype], dev_buf, value, (cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "map_write");
 }
 

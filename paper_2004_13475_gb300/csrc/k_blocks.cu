@@ -1,15 +1,14 @@
-// Single write (SW) and global reduce (RD) of Sec. 6.2 for float32 fields,
-// one 8 x 8 block of the gasket per thread.
+// Global reduce (RD) of Sec. 6.2 for float32 fields, one 8 x 8 block of the
+// gasket per thread.
 //
 // Launch: a CTA takes a member super-tile of 2^L x 2^L blocks.  lambda mode:
 // the CTA's super-tile by lambda(omega) (Theorem 1) and its 3^L member blocks
 // by lambda again (Sec. 5.1), L = 5 (243 blocks, 256 threads).  BB mode: the
 // bounding-box grid of super-tiles, non-member ones exiting at once, and
 // inside, the 4^L block slots by the identity, non-member ones idle (the
-// plain method at both levels), L = 4 (256 slots).  Each thread moves whole
-// 32-byte rows: 12 16-byte chunks hold its block's members; SW also writes the
-// zeros of the non-member cells of member tiles (rho >= 8), so its writes
-// cover whole sectors.
+// plain method at both levels), L = 4 (256 slots).  Each thread reads the 12
+// 16-byte chunks that hold its block's members (whole 32-byte rows where a
+// row has members in both halves): 192 bytes in flight per thread.
 #include "blocks.cuh"
 #include "launch.h"
 
@@ -39,38 +38,6 @@ __device__ __forceinline__ bool blk_of_thread(int sx, int sy, int L, int& GX, in
   GX = (sx << L) + bx;
   GY = (sy << L) + by;
   return true;
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(kBlkThreads) sw_blocks_kernel(float* __restrict__ out, float value, Geo g, int L,
-                                                                int log_rho) {
-  int sx, sy, GX, GY;
-  if (!cta_supertile<MODE>(g, sx, sy) || !blk_of_thread<MODE>(sx, sy, L, GX, GY)) return;
-  const int n = g.n;
-  float* o = out + (size_t)GY * kB * n + (size_t)GX * kB;
-  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int j = 0; j < kB; ++j) {
-    *reinterpret_cast<float4*>(o + (size_t)j * n) =
-        make_float4(value, amem(1, j) ? value : 0.f, amem(2, j) ? value : 0.f, amem(3, j) ? value : 0.f);
-    if (j < 4)
-      *reinterpret_cast<float4*>(o + (size_t)j * n + 4) =
-          make_float4(value, amem(5, j) ? value : 0.f, amem(6, j) ? value : 0.f, amem(7, j) ? value : 0.f);
-    else if (log_rho >= 3)
-      *reinterpret_cast<float4*>(o + (size_t)j * n + 4) = z;  // lower right quarter: non-members of the tile
-  }
-  if (log_rho >= 4) {
-    // non-member blocks right of this one in its rho-tile row, up to the next member block
-    const int bpt = 1 << (log_rho - 3);
-    const int tx = GX & (bpt - 1), ty = GY & (bpt - 1);
-    for (int q = tx + 1; q < bpt && (q & ty) != 0; ++q) {
-      float* p = o + (size_t)(q - tx) * kB;
-      for (int j = 0; j < kB; ++j) {
-        *reinterpret_cast<float4*>(p + (size_t)j * n) = z;
-        *reinterpret_cast<float4*>(p + (size_t)j * n + 4) = z;
-      }
-    }
-  }
 }
 
 template <int MODE>
@@ -113,15 +80,6 @@ bool blocks_geometry(int k, int mode, Launch& L, int& levels) {
   L.threads = kBlkThreads;
   L.smem = 0;
   return true;
-}
-
-cudaError_t launch_sw_blocks(int mode, int log_rho, const Launch& L, int levels, float* out, float value,
-                             cudaStream_t s) {
-  if (mode == kLambda)
-    sw_blocks_kernel<kLambda><<<L.grid, L.threads, 0, s>>>(out, value, L.geo, levels, log_rho);
-  else
-    sw_blocks_kernel<kBB><<<L.grid, L.threads, 0, s>>>(out, value, L.geo, levels, log_rho);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_blocks(int mode, const Launch& L, int levels, const float* in, double* partials,

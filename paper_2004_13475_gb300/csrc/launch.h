@@ -57,11 +57,9 @@ int ca_fused_threads(const Geo& g, int margin);
 
 // Diffusion with per-cell conductivity and its reverse step (k_adjoint.cu):
 // one thread per member 8 x 8 block, super-tiles of 2^levels blocks a side.
-// Float32 single write and reduce with one 8 x 8 block per thread
-// (k_blocks.cu); k >= 3, rho >= 4.
+// Float32 reduce with one 8 x 8 block per thread (k_blocks.cu); k >= 3,
+// rho >= 4.
 bool blocks_geometry(int k, int mode, Launch& L, int& levels);
-cudaError_t launch_sw_blocks(int mode, int log_rho, const Launch& L, int levels, float* out, float value,
-                             cudaStream_t s);
 cudaError_t launch_reduce_blocks(int mode, const Launch& L, int levels, const float* in, double* partials,
                                  double* dev_out, cudaStream_t s);
 
