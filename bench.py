@@ -517,7 +517,8 @@ def diffusion_box_member_blocks(k, T, M):
 # Sources each fused kernel is built from: `traffic` is taken from a committed
 # ncu summary only while their hash is the one recorded with it.
 KERNEL_SOURCES = {
-    "diffusion_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_gb300/csrc/gasket.cuh"),
+    "diffusion_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
+                               "paper_2004_13475_gb300/csrc/gasket.cuh"),
     "ca_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused_ca.cu", "paper_2004_13475_gb300/csrc/gasket.cuh"),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")

@@ -136,5 +136,95 @@ __device__ __forceinline__ bool block_pos(const Geo& g, int L, BlockPos& b) {
   return true;
 }
 
+// Member 4-degree of cell (i, j) inside the block (its links to other blocks
+// are added at the ports).
+__host__ __device__ constexpr int bdeg(int i, int j) {
+  return (amem(i - 1, j) ? 1 : 0) + (amem(i + 1, j) ? 1 : 0) + (amem(i, j - 1) ? 1 : 0) + (amem(i, j + 1) ? 1 : 0);
+}
+
+// Sum of a cell's neighbour values, in a fixed order, with no leading 0 + x.
+struct NbSum {
+  float s = 0.f;
+  bool any = false;
+  __device__ __forceinline__ void add(float v) {
+    s = any ? s + v : v;
+    any = true;
+  }
+};
+
+// One step of the 27 members of a block: u' = u + a * (sum of member
+// neighbours - degree * u).  Non-member neighbours hold no value and are not
+// summed; vu, vl, vr, vd are the neighbour values at the ports (0 where the
+// neighbour is not a staged member) and d0, dr, dd the ports' degrees.
+__device__ __forceinline__ void block_step(float (&u)[kB * kB], float a, float vu, float vl, float vr, float vd,
+                                           float d0, float dr, float dd) {
+  float w[kB * kB];
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+#pragma unroll
+    for (int i = 0; i < kB; ++i) {
+      if (!amem(i, j)) continue;
+      NbSum nb;
+      if (amem(i, j - 1)) nb.add(u[(j - 1) * kB + i]);
+      if (amem(i - 1, j)) nb.add(u[j * kB + i - 1]);
+      if (amem(i + 1, j)) nb.add(u[j * kB + i + 1]);
+      if (amem(i, j + 1)) nb.add(u[(j + 1) * kB + i]);
+      float d = (float)bdeg(i, j);
+      if (i == 0 && j == 0) {
+        nb.add(vu);
+        nb.add(vl);
+        d = d0;
+      }
+      if (i == kB - 1 && j == 0) {
+        nb.add(vr);
+        d = dr;
+      }
+      if (i == 0 && j == kB - 1) {
+        nb.add(vd);
+        d = dd;
+      }
+      const float c = u[j * kB + i];
+      w[j * kB + i] = fmaf(a, fmaf(-d, c, nb.s), c);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kB * kB; ++q)
+    if (amem(q % kB, q / kB)) u[q] = w[q];
+}
+
+// A 16-byte chunk of row j starting at column i0 with its non-members zeroed.
+__device__ __forceinline__ float4 mask_chunk(float4 v, int i0, int j) {
+  v.x = amem(i0 + 0, j) ? v.x : 0.f;
+  v.y = amem(i0 + 1, j) ? v.y : 0.f;
+  v.z = amem(i0 + 2, j) ? v.z : 0.f;
+  v.w = amem(i0 + 3, j) ? v.w : 0.f;
+  return v;
+}
+
+// Rank of the member slot (x, y) among the member slots (x & y == 0) of the
+// 2^L x 2^L box in row-major order (the BB enumeration, compacted).  Rows
+// above contribute sum_{y' < y} 2^(L - popc(y')); the row itself the x' < x
+// with x' & y == 0.  Both by the bits from the top, O(L).
+__device__ __forceinline__ int bb_rank(int x, int y, int L) {
+  int above = 0, pref = 1, p3 = 1;
+  for (int i = 0; i < L; ++i) p3 *= 3;
+  for (int i = L - 1; i >= 0; --i) {
+    p3 /= 3;  // 3^i
+    if ((y >> i) & 1) {
+      above += pref * 2 * p3;
+    } else {
+      pref *= 2;
+    }
+  }
+  int within = 0;
+  for (int i = L - 1; i >= 0; --i) {
+    if ((x >> i) & 1) {
+      within += 1 << (i - __popc(y & ((1 << i) - 1)));
+      if ((y >> i) & 1) break;
+    }
+  }
+  return above + within;
+}
+
 }  // namespace
 }  // namespace fractal

@@ -29,45 +29,15 @@
 // with one barrier each, and writes the member blocks back; for rho >= 8 it
 // also writes the zeros of the non-member cells of member tiles, so that every
 // write covers whole 32-byte sectors.
+#include "blocks.cuh"
 #include "launch.h"
 
 namespace fractal {
 namespace {
 
-constexpr int kS = 8;  // block side in cells
 // Largest CTA of a fused launch (super-tile side 256 with 32-cell margins:
 // 243 + 27 blocks); four such CTAs share an SM (56 registers a thread).
 constexpr int kFusedMaxThreads = 288;
-
-__host__ __device__ constexpr bool bmem(int i, int j) { return i >= 0 && j >= 0 && i < kS && j < kS && (i & j) == 0; }
-__host__ __device__ constexpr int bdeg(int i, int j) {
-  return (bmem(i - 1, j) ? 1 : 0) + (bmem(i + 1, j) ? 1 : 0) + (bmem(i, j - 1) ? 1 : 0) + (bmem(i, j + 1) ? 1 : 0);
-}
-
-// Rank of the member slot (x, y) among the member slots (x & y == 0) of the
-// 2^L x 2^L box in row-major order (the BB enumeration, compacted).  Rows
-// above contribute sum_{y' < y} 2^(L - popc(y')); the row itself the x' < x
-// with x' & y == 0.  Both by the bits from the top, O(L).
-__device__ __forceinline__ int bb_rank(int x, int y, int L) {
-  int above = 0, pref = 1, p3 = 1;
-  for (int i = 0; i < L; ++i) p3 *= 3;
-  for (int i = L - 1; i >= 0; --i) {
-    p3 /= 3;  // 3^i
-    if ((y >> i) & 1) {
-      above += pref * 2 * p3;
-    } else {
-      pref *= 2;
-    }
-  }
-  int within = 0;
-  for (int i = L - 1; i >= 0; --i) {
-    if ((x >> i) & 1) {
-      within += 1 << (i - __popc(y & ((1 << i) - 1)));
-      if ((y >> i) & 1) break;
-    }
-  }
-  return above + within;
-}
 
 // Per-CTA geometry of a fused launch.
 struct FGeo {
@@ -150,65 +120,6 @@ __device__ __forceinline__ bool block_member(int gx, int gy, int nblk) {
   return (unsigned)gx < (unsigned)nblk && (unsigned)gy < (unsigned)nblk && (gx & gy) == 0;
 }
 
-// Sum of a cell's neighbour values, in a fixed order, with no leading 0 + x.
-struct NbSum {
-  float s = 0.f;
-  bool any = false;
-  __device__ __forceinline__ void add(float v) {
-    s = any ? s + v : v;
-    any = true;
-  }
-};
-
-// One step of the 27 members of a block: u' = u + a * (sum of member
-// neighbours - degree * u).  Non-member neighbours hold no value and are not
-// summed; vu, vl, vr, vd are the neighbour values at the ports (0 where the
-// neighbour is not a staged member) and d0, dr, dd the ports' degrees.
-__device__ __forceinline__ void block_step(float (&u)[kS * kS], float a, float vu, float vl, float vr, float vd,
-                                           float d0, float dr, float dd) {
-  float w[kS * kS];
-#pragma unroll
-  for (int j = 0; j < kS; ++j) {
-#pragma unroll
-    for (int i = 0; i < kS; ++i) {
-      if (!bmem(i, j)) continue;
-      NbSum nb;
-      if (bmem(i, j - 1)) nb.add(u[(j - 1) * kS + i]);
-      if (bmem(i - 1, j)) nb.add(u[j * kS + i - 1]);
-      if (bmem(i + 1, j)) nb.add(u[j * kS + i + 1]);
-      if (bmem(i, j + 1)) nb.add(u[(j + 1) * kS + i]);
-      float d = (float)bdeg(i, j);
-      if (i == 0 && j == 0) {
-        nb.add(vu);
-        nb.add(vl);
-        d = d0;
-      }
-      if (i == kS - 1 && j == 0) {
-        nb.add(vr);
-        d = dr;
-      }
-      if (i == 0 && j == kS - 1) {
-        nb.add(vd);
-        d = dd;
-      }
-      const float c = u[j * kS + i];
-      w[j * kS + i] = fmaf(a, fmaf(-d, c, nb.s), c);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < kS * kS; ++q)
-    if (bmem(q % kS, q / kS)) u[q] = w[q];
-}
-
-// A 16-byte chunk of row j starting at column i0 with its non-members zeroed.
-__device__ __forceinline__ float4 mask_chunk(float4 v, int i0, int j) {
-  v.x = bmem(i0 + 0, j) ? v.x : 0.f;
-  v.y = bmem(i0 + 1, j) ? v.y : 0.f;
-  v.z = bmem(i0 + 2, j) ? v.z : 0.f;
-  v.w = bmem(i0 + 3, j) ? v.w : 0.f;
-  return v;
-}
-
 // Port slots: P0 = (0,0), PR = (7,0), PD = (0,7) of every block, double-
 // buffered by step parity, plus a zero slot at index `threads`.
 __host__ __device__ inline int fused_slots(int threads) { return threads + 1; }
@@ -223,7 +134,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
                                                   float* ports) {
   const int t = threadIdx.x, nthreads = blockDim.x;
   const int slots = fused_slots(nthreads), zero = nthreads;
-  const int nblk = f.n / kS;
+  const int nblk = f.n / kB;
   float* P0 = ports;  // [2][slots] each
   float* PR = ports + 2 * slots;
   float* PD = ports + 4 * slots;
@@ -284,36 +195,36 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   }
 
   // stage: the block's 12 member chunks straight into registers
-  float u[kS * kS];
+  float u[kB * kB];
 #pragma unroll
-  for (int q = 0; q < kS * kS; ++q) u[q] = 0.f;
-  const size_t base = (size_t)GY * kS * (size_t)f.n + (size_t)GX * kS;
+  for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
+  const size_t base = (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
   if (active) {
     float4 c[12];
 #pragma unroll
-    for (int j = 0; j < kS; ++j) c[j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n));
+    for (int j = 0; j < kB; ++j) c[j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n));
 #pragma unroll
     for (int j = 0; j < 4; ++j) c[8 + j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n + 4));
 #pragma unroll
-    for (int j = 0; j < kS; ++j) {
+    for (int j = 0; j < kB; ++j) {
       const float4 v = mask_chunk(c[j], 0, j);
-      u[j * kS + 0] = v.x;
-      u[j * kS + 1] = v.y;
-      u[j * kS + 2] = v.z;
-      u[j * kS + 3] = v.w;
+      u[j * kB + 0] = v.x;
+      u[j * kB + 1] = v.y;
+      u[j * kB + 2] = v.z;
+      u[j * kB + 3] = v.w;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float4 v = mask_chunk(c[8 + j], 4, j);
-      u[j * kS + 4] = v.x;
-      u[j * kS + 5] = v.y;
-      u[j * kS + 6] = v.z;
-      u[j * kS + 7] = v.w;
+      u[j * kB + 4] = v.x;
+      u[j * kB + 5] = v.y;
+      u[j * kB + 6] = v.z;
+      u[j * kB + 7] = v.w;
     }
   }
   P0[t] = u[0];
-  PR[t] = u[kS - 1];
-  PD[t] = u[(kS - 1) * kS];
+  PR[t] = u[kB - 1];
+  PD[t] = u[(kB - 1) * kB];
   if (t == 0) {
     P0[zero] = P0[slots + zero] = 0.f;
     PR[zero] = PR[slots + zero] = 0.f;
@@ -328,8 +239,8 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
       block_step(u, a, vu, vl, vr, vd, d0, dr, dd);
     }
     P0[nxt + t] = u[0];
-    PR[nxt + t] = u[kS - 1];
-    PD[nxt + t] = u[(kS - 1) * kS];
+    PR[nxt + t] = u[kB - 1];
+    PD[nxt + t] = u[(kB - 1) * kB];
     __syncthreads();
   }
 
@@ -337,38 +248,38 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   double sum = 0.0;
   if (active && t < f.nb) {
 #pragma unroll
-    for (int j = 0; j < kS; ++j) {
+    for (int j = 0; j < kB; ++j) {
       float r = 0.f;
       bool first = true;
 #pragma unroll
-      for (int i = 0; i < kS; ++i) {
-        if (!bmem(i, j)) continue;
-        r = first ? u[j * kS + i] : r + u[j * kS + i];
+      for (int i = 0; i < kB; ++i) {
+        if (!amem(i, j)) continue;
+        r = first ? u[j * kB + i] : r + u[j * kB + i];
         first = false;
       }
       sum += (double)r;
     }
     float* o = out + base;
 #pragma unroll
-    for (int j = 0; j < kS; ++j)
+    for (int j = 0; j < kB; ++j)
       *reinterpret_cast<float4*>(o + (size_t)j * f.n) =
-          make_float4(u[j * kS + 0], u[j * kS + 1], u[j * kS + 2], u[j * kS + 3]);
+          make_float4(u[j * kB + 0], u[j * kB + 1], u[j * kB + 2], u[j * kB + 3]);
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) =
-          make_float4(u[j * kS + 4], u[j * kS + 5], u[j * kS + 6], u[j * kS + 7]);
+          make_float4(u[j * kB + 4], u[j * kB + 5], u[j * kB + 6], u[j * kB + 7]);
     if (f.log_rho >= 3) {
       // non-member cells of member tiles: the block's lower right quarter,
       // and (rho >= 16) the non-member blocks right of this one in its tile
       // row, up to the next member block
       const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int j = 4; j < kS; ++j) *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) = z;
+      for (int j = 4; j < kB; ++j) *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) = z;
       const int bpt = 1 << (f.log_rho - 3);  // blocks per tile side
       const int tx = GX & (bpt - 1), ty = GY & (bpt - 1);
       for (int q = tx + 1; q < bpt && (q & ty) != 0; ++q) {
-        float* p = o + (size_t)(q - tx) * kS;
-        for (int j = 0; j < kS; ++j) {
+        float* p = o + (size_t)(q - tx) * kB;
+        for (int j = 0; j < kB; ++j) {
           *reinterpret_cast<float4*>(p + (size_t)j * f.n) = z;
           *reinterpret_cast<float4*>(p + (size_t)j * f.n + 4) = z;
         }
@@ -387,7 +298,7 @@ __device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho) {
   for (int i = 0; i < (f.L + 1) / 2; ++i) lw *= 3;
   f.lw = lw;
   f.nb = nb;
-  f.W = M / kS;
+  f.W = M / kB;
   f.nbox = 6 * f.W * f.W;
   f.log_rho = log_rho;
   return f;
@@ -475,9 +386,9 @@ __global__ void __launch_bounds__(512) batch_partials_kernel(const BatchInst* __
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
       int bx, by;
       lambda_scalar((uint32_t)(t % lw), (uint32_t)(t / lw), L, bx, by);
-      const float* p = buf + ((size_t)((sy << L) + by) * kS) * (size_t)I.n + (size_t)((sx << L) + bx) * kS;
+      const float* p = buf + ((size_t)((sy << L) + by) * kB) * (size_t)I.n + (size_t)((sx << L) + bx) * kB;
 #pragma unroll
-      for (int j = 0; j < kS; ++j) {
+      for (int j = 0; j < kB; ++j) {
         const float4 v = mask_chunk(__ldg(reinterpret_cast<const float4*>(p + (size_t)j * I.n)), 0, j);
         acc += (double)((v.x + v.y) + (v.z + v.w));
       }
@@ -529,7 +440,7 @@ int member_blocks(int T) {
 }  // namespace
 
 // Margin of a fused launch: the smallest multiple of the block side >= spl.
-int fused_margin(int steps_per_launch) { return (steps_per_launch + kS - 1) / kS * kS; }
+int fused_margin(int steps_per_launch) { return (steps_per_launch + kB - 1) / kB * kB; }
 
 // Threads of a fused launch: one per member block of the super-tile and per
 // member block the margin boxes can hold, rounded up to whole warps; 0 if the
@@ -537,8 +448,8 @@ int fused_margin(int steps_per_launch) { return (steps_per_launch + kS - 1) / kS
 // multiple of 8 or above 32, more than kFusedMaxThreads threads).
 int fused_threads(const Geo& g, int rho, int margin) {
   (void)rho;
-  if (g.T < 2 * kS || g.T < 2 * margin || margin < kS || margin % kS != 0 || margin > 4 * kS) return 0;
-  const int W = margin / kS;
+  if (g.T < 2 * kB || g.T < 2 * margin || margin < kB || margin % kB != 0 || margin > 4 * kB) return 0;
+  const int W = margin / kB;
   const int t = (member_blocks(g.T) + box_cap(W) + 31) / 32 * 32;
   return t > kFusedMaxThreads ? 0 : t;
 }
