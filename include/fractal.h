@@ -132,8 +132,8 @@ int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
 /*
  * fractal_plan_autotune -- time the plan's step kernel for dtype under every
  * staging (TMA where it applies, vector loads), every valid number of tile
- * levels per CTA and 1 step per launch or temporal fusion (float32: 8, 16 or
- * 32 steps per launch; uint8: 8, 16 or 25), and keep
+ * levels per CTA and 1 step per launch or temporal fusion (float32: 25, 50 or
+ * 100 steps per launch; uint8: 8, 16 or 25), and keep
  * the fastest per step.  Each candidate runs `reps` timed launches dev_in ->
  * dev_scratch (after two untimed ones) on `stream`, which is synchronised.  dev_in is only read; dev_scratch is
  * overwritten.  Both are n*n arrays of dtype, 16-byte aligned.  *best_us
@@ -153,9 +153,11 @@ int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, vo
  * diffusion); the buffer holding the result after `steps` steps is unchanged
  * (dev_a for even, dev_b for odd).  spl = 1 turns fusion off.
  * FRACTAL_F32 (diffusion, one 8 x 8 block of the gasket per thread): spl <=
- * 32, rho >= 4, a super-tile side of at least 16 cells and twice the margin
- * (spl rounded up to a multiple of 8); the kernel takes the largest such
- * super-tile it can hold, whatever fractal_plan_set_cta_levels chose.  FRACTAL_U8 (automaton, on a bit image of 32-cell
+ * 128, rho >= 4, a super-tile side of at least 16 cells and twice the margin
+ * (the smallest power of two >= max(spl, 8)); the kernel takes the largest
+ * such super-tile it can hold, whatever fractal_plan_set_cta_levels chose.
+ * Each launch reads and writes every member tile once, so the per-launch
+ * cost is mostly memory traffic: fewer, longer launches pay.  FRACTAL_U8 (automaton, on a bit image of 32-cell
  * words): spl <= 31, a super-tile side of 32 to 512 cells and at least 2*spl
  * (k >= 6).  The super-tile may be smaller than the plan's step kernels use.
  * Errors: FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan).

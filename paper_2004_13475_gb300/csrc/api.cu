@@ -73,10 +73,10 @@ bool make_launch(const fractal_plan_s& p, int dtype, int levels, Launch& step, L
   return plan_geometry(p.k, p.log_rho, p.mode, dtype, levels, step, aux, tma, tma_ok);
 }
 
-// Largest steps per launch of the fused kernels: float32 margins of 8, 16 or
-// 32 cells (whole 8 x 8 blocks); uint8 margins of up to 31 cells (one word
-// column of the bit image).
-int max_spl(int dtype) { return dtype == FRACTAL_U8 ? 31 : 32; }
+// Largest steps per launch of the fused kernels: float32 margins of 8 to 128
+// cells (whole 8 x 8 blocks, a power of two of them); uint8 margins of up to
+// 31 cells (one word column of the bit image).
+int max_spl(int dtype) { return dtype == FRACTAL_U8 ? 31 : 128; }
 
 // Launch of the temporally fused kernel for `spl` steps per launch (super-tile
 // side >= twice the margin).  The float32 kernel (rho >= 4) keeps one 8 x 8
@@ -645,8 +645,8 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
     const bool skip_f32_fused = dtype == FRACTAL_F32 && f32_fused_timed;
     f32_fused_timed = true;
     // candidates: (schedule, steps per launch)
-    const int cands_f32[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
-                                 {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 32}};
+    const int cands_f32[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 25},
+                                 {FRACTAL_SCHED_AUTO, 50}, {FRACTAL_SCHED_AUTO, 100}};
     const int cands_u8[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
                                 {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 25}};
     const int(*cands)[2] = dtype == FRACTAL_U8 ? cands_u8 : cands_f32;

@@ -35,9 +35,11 @@
 namespace fractal {
 namespace {
 
-// Largest CTA of a fused launch (super-tile side 256 with 32-cell margins:
-// 243 + 27 blocks); four such CTAs share an SM (56 registers a thread).
-constexpr int kFusedMaxThreads = 288;
+// CTA sizes of a fused launch, each compiled with its own register budget:
+// up to 288 threads (super-tile side 256 with 32-cell margins: 243 + 27
+// blocks), four CTAs per SM; up to 352 (64-cell margins: 243 + 81), three;
+// up to 512 (128-cell margins: 243 + 243), two.
+constexpr int kFusedMaxThreads = 512;
 
 // Per-CTA geometry of a fused launch.
 struct FGeo {
@@ -58,7 +60,9 @@ __host__ __device__ inline int box_cap(int W) {
   for (int w = W; w > 1; w >>= 1) c *= 3;
   return c < 6 * W * W ? c : 6 * W * W;
 }
-constexpr int kMaxBox = 96;  // 6 W^2 for W <= 4
+constexpr int kMaxW = 16;                    // margins up to 128 cells
+constexpr int kMaxBox = 6 * kMaxW * kMaxW;   // box blocks: 6 W^2
+constexpr int kMaxBoxMembers = 243;          // box_cap(16)
 
 // Member block t of the super-tile (lambda order, or BB rank order via tab).
 template <int MODE>
@@ -141,7 +145,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
 
   // the margin boxes' member blocks, compacted in box order: boxrank[b] is
   // the rank of box block b among them (-1 if not a member), boxlist the list
-  __shared__ int boxrank[kMaxBox], boxlist[kMaxBox], wcnt[16];
+  __shared__ int boxrank[kMaxBox], boxlist[kMaxBoxMembers], wcnt[16];
   int nbox_member = 0;
   for (int b0 = 0; b0 < f.nbox; b0 += nthreads) {
     const int b = b0 + t;
@@ -313,8 +317,8 @@ __device__ __forceinline__ void bb_table(int* tab, const FGeo& f) {
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kFusedMaxThreads, 4) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
+template <int MODE, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                               float a, int nsteps, int M, int log_rho, Geo g,
                                                               double* __restrict__ partials) {
   extern __shared__ __align__(16) float fsm[];
@@ -352,7 +356,7 @@ __device__ __forceinline__ int batch_instance(const BatchInst* __restrict__ inst
   return lo;
 }
 
-__global__ void __launch_bounds__(kFusedMaxThreads, 4) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
+__global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
                                                               int64_t items, int which, float a, int nsteps, int M,
                                                               int T) {
   extern __shared__ __align__(16) float fsm[];
@@ -424,12 +428,18 @@ __global__ void batch_sums_kernel(const BatchInst* __restrict__ inst, int count,
 template <int MODE>
 cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
                double* partials, cudaStream_t s) {
-  auto* k = diffusion_fused_kernel<MODE>;
-  cudaError_t e = allow_smem((const void*)k, L.smem);
-  if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials);
-  return cudaGetLastError();
+  // the smallest CTA class that holds the launch: more CTAs per SM
+  auto run = [&](auto* k) -> cudaError_t {
+    cudaError_t e = allow_smem((const void*)k, L.smem);
+    if (e != cudaSuccess) return e;
+    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials);
+    return cudaGetLastError();
+  };
+  if (L.threads <= 288) return run(diffusion_fused_kernel<MODE, 288, 4>);
+  if (L.threads <= 352) return run(diffusion_fused_kernel<MODE, 352, 3>);
+  return run(diffusion_fused_kernel<MODE, 512, 2>);
 }
+
 
 int member_blocks(int T) {
   int nb = 1;
@@ -439,17 +449,23 @@ int member_blocks(int T) {
 
 }  // namespace
 
-// Margin of a fused launch: the smallest multiple of the block side >= spl.
-int fused_margin(int steps_per_launch) { return (steps_per_launch + kB - 1) / kB * kB; }
+// Margin of a fused launch: the smallest power of two >= spl, at least the
+// block side (8, 16, 32, 64 or 128 cells: whole blocks, W a power of two).
+int fused_margin(int steps_per_launch) {
+  int m = kB;
+  while (m < steps_per_launch) m *= 2;
+  return m;
+}
 
 // Threads of a fused launch: one per member block of the super-tile and per
 // member block the margin boxes can hold, rounded up to whole warps; 0 if the
-// super-tile does not fit (side < 16 or < 2 M, a margin that is not a
-// multiple of 8 or above 32, more than kFusedMaxThreads threads).
+// super-tile does not fit (side < 16 or < 2 M, a margin that is not 8 times
+// a power of two up to 128, more than kFusedMaxThreads threads).
 int fused_threads(const Geo& g, int rho, int margin) {
   (void)rho;
-  if (g.T < 2 * kB || g.T < 2 * margin || margin < kB || margin % kB != 0 || margin > 4 * kB) return 0;
   const int W = margin / kB;
+  if (g.T < 2 * kB || g.T < 2 * margin || margin < kB || margin % kB != 0 || W > kMaxW || (W & (W - 1)) != 0)
+    return 0;
   const int t = (member_blocks(g.T) + box_cap(W) + 31) / 32 * 32;
   return t > kFusedMaxThreads ? 0 : t;
 }

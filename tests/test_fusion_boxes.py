@@ -119,7 +119,7 @@ def _active_box_blocks(k, T, M):
     return cnt
 
 
-@pytest.mark.parametrize("M", [8, 16, 32])
+@pytest.mark.parametrize("M", [8, 16, 32, 64, 128])
 def test_member_blocks_of_the_boxes_are_few(M):
     # The fused diffusion gives a thread only to the member blocks of the
     # margin boxes: at most 3 * 3^log2(M/8) of the 6 (M/8)^2 (a gasket

@@ -117,7 +117,7 @@ def k16_f32(fr, k16_u8):
     return n, a, b
 
 
-@pytest.mark.parametrize("spl", [1, 8, 32, "tuned"])
+@pytest.mark.parametrize("spl", [1, 8, 32, 50, "tuned"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("rho", [8, 16, 32])
 def test_k16_diffusion_200_steps(fr, k16_f32, rho, mode, spl):

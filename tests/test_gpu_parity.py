@@ -333,14 +333,17 @@ def test_diffusion_parity(fr, k, rho, mode, sched):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("spl", [2, 3, 4, 8, 16, 32])
+@pytest.mark.parametrize("spl", [2, 3, 4, 8, 16, 32, 50, 100])
 @pytest.mark.parametrize("k,rho", [(5, 4), (6, 8), (8, 4), (8, 8), (9, 16), (10, 32), (10, 8), (11, 16)])
 def test_diffusion_fused_parity(fr, k, rho, mode, spl):
     # several steps per launch: same field as the oracle, same result buffer,
     # cells outside member tiles untouched
     n = 1 << k
     plan = fr.fractal_map(k, rho, mode)
-    if (1 << k) < 2 * (-(-spl // 8) * 8):
+    margin = 8
+    while margin < spl:
+        margin *= 2
+    if min(1 << k, rho << 5) < 2 * margin:     # super-tile side: at most rho * 2^5 and n
         with pytest.raises(fr.FractalError):       # no super-tile of side >= 2 * margin
             fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
         return
@@ -352,14 +355,16 @@ def test_diffusion_fused_parity(fr, k, rho, mode, spl):
     for steps in (1, 5, 8, 13, 2 * spl + 1):
         want = oracle.diffusion_run(u0.astype(np.float64), steps, 0.2, domain(k))
         got = run_diffusion(fr, plan, u0, steps)
-        assert rel_err(got, want, mask)[0] <= 2e-6, (steps, rel_err(got, want, mask))
+        # FP32 rounding grows with the steps (1e-4 after 1000, the bound of the workload)
+        bound = 2e-6 + 1e-7 * steps
+        assert rel_err(got, want, mask)[0] <= bound, (steps, rel_err(got, want, mask))
         assert np.all(got[cover & ~mask] == 0)
         if steps % 2:
             assert np.all(got[~cover] == SENTINEL_F32)
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("spl", [8, 32])
+@pytest.mark.parametrize("spl", [8, 32, 100])
 def test_diffusion_fused_1000_steps(fr, mode, spl):
     k, n = 10, 1024
     u0 = synth.uniform_f32(3, n)
@@ -408,7 +413,7 @@ def test_fused_needs_room(fr):
     with pytest.raises(fr.FractalError):
         fr.fractal_plan_set_steps_per_launch(fr.fractal_map(3, 4), fr.FRACTAL_F32, 8)   # super-tile < 16
     with pytest.raises(fr.FractalError):
-        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(10, 8), fr.FRACTAL_F32, 33)
+        fr.fractal_plan_set_steps_per_launch(fr.fractal_map(10, 8), fr.FRACTAL_F32, 129)
     p = fr.fractal_map(10, 8)
     fr.fractal_plan_set_steps_per_launch(p, fr.FRACTAL_F32, 1)
     assert p.info()["steps_per_launch"] == [1, 1]
