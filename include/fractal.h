@@ -306,6 +306,22 @@ int fractal_reduce_async(fractal_plan_t plan, const void* dev_buf, int dtype, do
 int fractal_reduce_noalloc(int k, int rho, const void* dev_buf, int dtype, double* dev_out, void* stream);
 
 /*
+ * fractal_pack / fractal_unpack -- compact storage through the block-space
+ * map (the compact lambda / lambda^-1 storage the paper leaves for later
+ * work): the member tiles of the n x n array dev_embedded, one after another
+ * in lambda order -- packed tile j is the tile lambda(omega_j), omega_j =
+ * (j mod grid_w, j div grid_w) (Theorem 1), rows of rho elements in order --
+ * into dev_packed (member_tiles * rho^2 elements of dtype), and back.  Pack
+ * reads only member tiles; unpack writes whole member tiles and nothing else.
+ * The order is lambda's whatever the plan's launch mode.  Both buffers
+ * device, 16-byte aligned, distinct.  Asynchronous.  Not in the paper's
+ * measurements: the form in which a field crosses between host and device.
+ * Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
+ */
+int fractal_pack(fractal_plan_t plan, const void* dev_embedded, int dtype, void* dev_packed, void* stream);
+int fractal_unpack(fractal_plan_t plan, const void* dev_packed, int dtype, void* dev_embedded, void* stream);
+
+/*
  * fractal_set_l2_fetch_granularity -- set the L2 fetch granularity hint of
  * the CURRENT CUDA context (cudaLimitMaxL2FetchGranularity) to 32, 64 or 128
  * bytes.  Not part of the paper: a GB300 memory-system knob.  The tiles of a

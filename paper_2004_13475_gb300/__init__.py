@@ -45,6 +45,7 @@ EXPORTS = (
     "fractal_step_diffusion_kappa", "fractal_adjoint_diffusion_step",
     "fractal_step_diffusion_kappa_f64", "fractal_adjoint_diffusion_step_f64",
     "fractal_step_ca_count", "fractal_step_diffusion_sum", "fractal_map_blocks_method",
+    "fractal_pack", "fractal_unpack",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -139,6 +140,8 @@ def _load() -> ctypes.CDLL:
         "fractal_step_diffusion_kappa_f64": (I, [P, VP, VP, VP, D, I, VP]),
         "fractal_step_ca_count": (I, [P, VP, VP, I, VP, VP]),
         "fractal_map_blocks_method": (I, [P, VP, I, VP]),
+        "fractal_pack": (I, [P, VP, I, VP, VP]),
+        "fractal_unpack": (I, [P, VP, I, VP, VP]),
         "fractal_step_diffusion_sum": (I, [P, VP, VP, F, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
     }
@@ -312,6 +315,18 @@ def fractal_reduce_noalloc(k: int, rho: int, buf, dtype: int, dev_out, stream=No
     (fixed scratch inside the library; see include/fractal.h)."""
     _check(_load().fractal_reduce_noalloc(int(k), int(rho), _ptr(buf), int(dtype), _ptr(dev_out),
                                           _stream(stream)), "fractal_reduce_noalloc")
+
+
+def fractal_pack(plan: Plan, embedded, dtype: int, packed, stream=None) -> None:
+    """Member tiles of `embedded` in lambda order into `packed` (member_tiles * rho^2 elements)."""
+    _check(_load().fractal_pack(plan.handle, _ptr(embedded), int(dtype), _ptr(packed), _stream(stream)),
+           "fractal_pack")
+
+
+def fractal_unpack(plan: Plan, packed, dtype: int, embedded, stream=None) -> None:
+    """Inverse of fractal_pack: writes the member tiles of `embedded`."""
+    _check(_load().fractal_unpack(plan.handle, _ptr(packed), int(dtype), _ptr(embedded), _stream(stream)),
+           "fractal_unpack")
 
 
 def fractal_set_l2_fetch_granularity(nbytes: int) -> None:

@@ -795,6 +795,24 @@ int fractal_reduce(fractal_plan_t p, const void* dev_buf, int dtype, double* hos
   return FRACTAL_OK;
 }
 
+int fractal_pack(fractal_plan_t p, const void* dev_embedded, int dtype, void* dev_packed, void* stream) {
+  if (check_plan(p) || !dev_embedded || !dev_packed || dev_embedded == dev_packed || !aligned16(dev_embedded) ||
+      !aligned16(dev_packed) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32))
+    return FRACTAL_EINVAL;
+  cudaError_t e = launch_pack(dev_embedded, dev_packed, p->n, p->rb, 1 << p->log_rho, dtype == FRACTAL_U8 ? 1 : 4,
+                              (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "pack");
+}
+
+int fractal_unpack(fractal_plan_t p, const void* dev_packed, int dtype, void* dev_embedded, void* stream) {
+  if (check_plan(p) || !dev_embedded || !dev_packed || dev_embedded == dev_packed || !aligned16(dev_embedded) ||
+      !aligned16(dev_packed) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32))
+    return FRACTAL_EINVAL;
+  cudaError_t e = launch_unpack(dev_packed, dev_embedded, p->n, p->rb, 1 << p->log_rho,
+                                dtype == FRACTAL_U8 ? 1 : 4, (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "unpack");
+}
+
 int fractal_set_l2_fetch_granularity(int bytes) {
   if (bytes != 32 && bytes != 64 && bytes != 128) return FRACTAL_EINVAL;
   cudaError_t e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
