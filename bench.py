@@ -314,15 +314,18 @@ def main():
             e.record(stream)
             ev.setdefault(key, []).append(e)
 
-    def step(mode, ev=None):
-        """One bench step; if ev (a dict) is given, record events around the
-        automaton run and the diffusion segments."""
+    def step(mode, ev=None, parts=("ca", "diffusion")):
+        """One bench step (or one of its two parts); if ev (a dict) is given,
+        record events around the automaton run and the diffusion segments."""
         pc, pd = plan("ca", mode), plan("diffusion", mode)
         # each call leaves the global measure of its result in `sums` (taken by
         # the last fused launch from the values it writes, or a reduce after)
-        mark(ev, "ca0")
-        fr.fractal_step_ca_count(pc, ca_a, ca_b, CA_STEPS, sums[4:5], stream)   # even: result back in ca_a
-        mark(ev, "ca1")
+        if "ca" in parts:
+            mark(ev, "ca0")
+            fr.fractal_step_ca_count(pc, ca_a, ca_b, CA_STEPS, sums[4:5], stream)   # even: result back in ca_a
+            mark(ev, "ca1")
+        if "diffusion" not in parts:
+            return None
         cur, oth = u_a, u_b
         for seg in range(DIFF_STEPS // REDUCE_EVERY):
             mark(ev, "d0")
@@ -357,6 +360,8 @@ def main():
     clocks = clk.summary()
     t_lam = max_over_ranks(dist, t_lam)
     diff_ms = sum(a.elapsed_time(b) for a, b in zip(ev["d0"], ev["d1"]))
+    seg = DIFF_STEPS // REDUCE_EVERY
+    per_step = sorted(ev["ca0"][i].elapsed_time(ev["d1"][seg * i + seg - 1]) for i in range(args.steps))
     ca_ms = sum(a.elapsed_time(b) for a, b in zip(ev["ca0"], ev["ca1"]))
     value = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * args.steps / t_lam
 
@@ -411,6 +416,8 @@ def main():
             "parallelism": "replicas only" if world > 1 else "single GPU",
         },
         "gpu_launches": launches_per_step * args.steps,
+        "step_ms": {"median": statistics.median(per_step), "min": per_step[0], "max": per_step[-1],
+                    "n": len(per_step)},
         "clocks": clocks,
         "roofline": roofline,
         "roofline_other": rf_c if roofline is rf_d else rf_d,
@@ -896,18 +903,31 @@ def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):
         h_ca.copy_(ca_a)
         h_u.copy_(u_a)
     steps = max(1, min(args.steps, 2))
+    side = torch.cuda.Stream()
 
     def one():
         if pk is not None:
+            # the diffusion state comes in on a side stream while the
+            # automaton runs; the automaton's result goes out while the
+            # diffusion runs; the step ends when both streams are done
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                d_u.copy_(h_u, non_blocking=True)
+                fr.fractal_unpack(pk, d_u, fr.FRACTAL_F32, u_a, side)
             d_ca.copy_(h_ca, non_blocking=True)
-            d_u.copy_(h_u, non_blocking=True)
             fr.fractal_unpack(pk, d_ca, fr.FRACTAL_U8, ca_a, stream)
-            fr.fractal_unpack(pk, d_u, fr.FRACTAL_F32, u_a, stream)
-            res = step(0)
+            step(0, parts=("ca",))
             fr.fractal_pack(pk, ca_a, fr.FRACTAL_U8, d_ca, stream)
+            ca_done = torch.cuda.Event()
+            ca_done.record(stream)
+            stream.wait_stream(side)
+            res = step(0, parts=("diffusion",))
+            side.wait_event(ca_done)
+            with torch.cuda.stream(side):
+                h_ca.copy_(d_ca, non_blocking=True)
             fr.fractal_pack(pk, res, fr.FRACTAL_F32, d_u, stream)
-            h_ca.copy_(d_ca, non_blocking=True)
             h_u.copy_(d_u, non_blocking=True)
+            stream.wait_stream(side)
         else:
             ca_a.copy_(h_ca, non_blocking=True)
             u_a.copy_(h_u, non_blocking=True)
@@ -931,7 +951,8 @@ def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):
     nbytes = 5 * cells
     note = ("whole n x n arrays copied each way through pinned host memory" if pk is None else
             f"member tiles of side {rho} in lambda order copied each way through pinned host memory, "
-            "unpacked onto / packed from the device arrays inside the timed region")
+            "unpacked onto / packed from the device arrays inside the timed region; the diffusion state's "
+            "copy in and the automaton result's copy out overlap the other workload's kernels")
     if pk is not None:
         pk.close()
     return {"value": world * MEMBERS * (CA_STEPS + DIFF_STEPS) * steps / t, "unit": "cell-updates/s",
