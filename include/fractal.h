@@ -314,8 +314,14 @@ int fractal_reduce_noalloc(int k, int rho, const void* dev_buf, int dtype, doubl
  * into dev_packed (member_tiles * rho^2 elements of dtype), and back.  Pack
  * reads only member tiles; unpack writes whole member tiles and nothing else.
  * The order is lambda's whatever the plan's launch mode.  Both buffers
- * device, 16-byte aligned, distinct.  Asynchronous.  Not in the paper's
- * measurements: the form in which a field crosses between host and device.
+ * 16-byte aligned and distinct; each is device memory of the plan's device
+ * or pinned host memory mapped into its address space at the same address
+ * (cudaHostAlloc / cudaHostRegister under unified addressing): with a host
+ * packed buffer the kernel itself moves the packed field over the host link,
+ * in place of a separate copy.  Pageable host memory is rejected (checked on
+ * the host with cudaPointerGetAttributes, before any launch).  Asynchronous.
+ * Not in the paper's measurements: the form in which a field crosses between
+ * host and device.
  * Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
  */
 int fractal_pack(fractal_plan_t plan, const void* dev_embedded, int dtype, void* dev_packed, void* stream);

@@ -318,7 +318,10 @@ def fractal_reduce_noalloc(k: int, rho: int, buf, dtype: int, dev_out, stream=No
 
 
 def fractal_pack(plan: Plan, embedded, dtype: int, packed, stream=None) -> None:
-    """Member tiles of `embedded` in lambda order into `packed` (member_tiles * rho^2 elements)."""
+    """Member tiles of `embedded` in lambda order into `packed` (member_tiles * rho^2 elements).
+
+    Either buffer may be a pinned CPU tensor (mapped into the device's address
+    space): the kernel then reads or writes host memory directly."""
     _check(_load().fractal_pack(plan.handle, _ptr(embedded), int(dtype), _ptr(packed), _stream(stream)),
            "fractal_pack")
 

@@ -30,6 +30,28 @@ int64_t ipow(int64_t b, int e) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// p can be dereferenced by kernels on `device` at the same address: device
+// or managed memory, or pinned host memory mapped into the device's address
+// space (unified addressing).  Pageable host memory and unknown pointers are
+// not.  Host-side query only: nothing touches the memory.
+bool device_addressable(const void* p, int device) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error
+    return false;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+      return at.device == device;
+    case cudaMemoryTypeManaged:
+      return true;
+    case cudaMemoryTypeHost:
+      return at.devicePointer == p;
+    default:
+      return false;
+  }
+}
+
 constexpr int kMaxLevelsPerCta = 5;
 constexpr int kMaxSmem = 200 * 1024;
 // Loads per thread a launch is sized for (at most kIPT; fewer keeps more warps
@@ -797,7 +819,8 @@ int fractal_reduce(fractal_plan_t p, const void* dev_buf, int dtype, double* hos
 
 int fractal_pack(fractal_plan_t p, const void* dev_embedded, int dtype, void* dev_packed, void* stream) {
   if (check_plan(p) || !dev_embedded || !dev_packed || dev_embedded == dev_packed || !aligned16(dev_embedded) ||
-      !aligned16(dev_packed) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32))
+      !aligned16(dev_packed) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) ||
+      !device_addressable(dev_embedded, p->device) || !device_addressable(dev_packed, p->device))
     return FRACTAL_EINVAL;
   cudaError_t e = launch_pack(dev_embedded, dev_packed, p->n, p->rb, 1 << p->log_rho, dtype == FRACTAL_U8 ? 1 : 4,
                               (cudaStream_t)stream);
@@ -806,7 +829,8 @@ int fractal_pack(fractal_plan_t p, const void* dev_embedded, int dtype, void* de
 
 int fractal_unpack(fractal_plan_t p, const void* dev_packed, int dtype, void* dev_embedded, void* stream) {
   if (check_plan(p) || !dev_embedded || !dev_packed || dev_embedded == dev_packed || !aligned16(dev_embedded) ||
-      !aligned16(dev_packed) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32))
+      !aligned16(dev_packed) || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) ||
+      !device_addressable(dev_embedded, p->device) || !device_addressable(dev_packed, p->device))
     return FRACTAL_EINVAL;
   cudaError_t e = launch_unpack(dev_packed, dev_embedded, p->n, p->rb, 1 << p->log_rho,
                                 dtype == FRACTAL_U8 ? 1 : 4, (cudaStream_t)stream);

@@ -5,8 +5,12 @@
 // of n^2, the member tiles' sectors only; moving a field between host and
 // device in this form moves no cell outside the member tiles.
 //
-// One thread per tile row: it maps its tile by lambda (per-thread form) and
-// copies the row's rho elements with 16-byte (or narrower) accesses.
+// Rows of 16 bytes or more: one thread per tile row; it maps its tile by
+// lambda (per-thread form) and copies the row with 16-byte (or narrower)
+// accesses.  Narrower rows (rho * elem < 16): one thread per 16 bytes of the
+// packed side, i.e. 16 / (rho * elem) consecutive rows, so that the packed
+// side -- possibly pinned host memory across the host link -- sees whole
+// 16-byte accesses, and the embedded side one access per row.
 #include "launch.h"
 
 namespace fractal {
@@ -39,6 +43,48 @@ __global__ void __launch_bounds__(256) pack_kernel(const unsigned char* __restri
   }
 }
 
+// Byte offset of tile row r (packed order) in the embedded array.
+__device__ __forceinline__ size_t embedded_offset(int64_t r, int n, int rb, int w, int rho, int elem) {
+  const int64_t j = r / rho;  // tile, in lambda order
+  const int ty = (int)(r - j * rho);
+  int bx, by;
+  lambda_scalar((uint32_t)(j % w), (uint32_t)(j / w), rb, bx, by);
+  return ((size_t)by * rho + ty) * (size_t)n * elem + (size_t)bx * rho * elem;
+}
+
+template <int RB, bool PACK>  // RB = row bytes < 16
+__global__ void __launch_bounds__(256) pack_narrow_kernel(const unsigned char* __restrict__ src,
+                                                          unsigned char* __restrict__ dst, int n, int rb, int w,
+                                                          int rho, int elem, int64_t rows) {
+  using T = typename Vec<RB>::T;
+  constexpr int G = 16 / RB;
+  const int64_t groups = (rows + G - 1) / G;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < groups;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = q * G;
+    if (r0 + G <= rows) {
+      alignas(16) T e[G];
+      if (PACK) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) e[g] = *reinterpret_cast<const T*>(src + embedded_offset(r0 + g, n, rb, w, rho, elem));
+        *reinterpret_cast<uint4*>(dst + r0 * RB) = *reinterpret_cast<const uint4*>(e);
+      } else {
+        *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(src + r0 * RB);
+#pragma unroll
+        for (int g = 0; g < G; ++g) *reinterpret_cast<T*>(dst + embedded_offset(r0 + g, n, rb, w, rho, elem)) = e[g];
+      }
+    } else {  // the last, partial group
+      for (int64_t r = r0; r < rows; ++r) {
+        const size_t emb = embedded_offset(r, n, rb, w, rho, elem);
+        if (PACK)
+          *reinterpret_cast<T*>(dst + r * RB) = *reinterpret_cast<const T*>(src + emb);
+        else
+          *reinterpret_cast<T*>(dst + emb) = *reinterpret_cast<const T*>(src + r * RB);
+      }
+    }
+  }
+}
+
 template <bool PACK>
 cudaError_t run(const void* src, void* dst, int n, int rb, int rho, int elem, cudaStream_t s) {
   const int w = [rb] {
@@ -53,17 +99,23 @@ cudaError_t run(const void* src, void* dst, int n, int rb, int rho, int elem, cu
   if (blocks > 152 * 64) blocks = 152 * 64;
   const auto* a = static_cast<const unsigned char*>(src);
   auto* b = static_cast<unsigned char*>(dst);
-  const int rb_bytes = rho * elem;
-  if (rb_bytes % 16 == 0)
+  const int rb_bytes = rho * elem;  // a power of two: rho is, elem is 1 or 4
+  if (rb_bytes >= 16) {
     pack_kernel<16, PACK><<<(unsigned)blocks, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
-  else if (rb_bytes % 8 == 0)
-    pack_kernel<8, PACK><<<(unsigned)blocks, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
-  else if (rb_bytes % 4 == 0)
-    pack_kernel<4, PACK><<<(unsigned)blocks, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
-  else if (rb_bytes % 2 == 0)
-    pack_kernel<2, PACK><<<(unsigned)blocks, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
+    return cudaGetLastError();
+  }
+  int64_t groups = (rows * rb_bytes + 15) / 16;
+  int64_t gblocks = (groups + 255) / 256;
+  if (gblocks > 152 * 64) gblocks = 152 * 64;
+  const unsigned g = (unsigned)gblocks;
+  if (rb_bytes == 8)
+    pack_narrow_kernel<8, PACK><<<g, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
+  else if (rb_bytes == 4)
+    pack_narrow_kernel<4, PACK><<<g, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
+  else if (rb_bytes == 2)
+    pack_narrow_kernel<2, PACK><<<g, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
   else
-    pack_kernel<1, PACK><<<(unsigned)blocks, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
+    pack_narrow_kernel<1, PACK><<<g, 256, 0, s>>>(a, b, n, rb, w, rho, elem, rows);
   return cudaGetLastError();
 }
 

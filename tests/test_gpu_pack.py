@@ -97,6 +97,43 @@ def test_pack_level_16_sampled(fr):
         assert bool(torch.equal(win, torch.where(sub, ref, torch.zeros_like(ref))))
 
 
+@pytest.mark.parametrize("dt", ["u8", "f32"])
+def test_pack_through_pinned_host_memory(fr, dt):
+    """The packed side may be pinned host memory: the same bytes as through
+    a device buffer, both ways."""
+    k, rho = 9, 2
+    n = 1 << k
+    npdt, code = (np.uint8, fr.FRACTAL_U8) if dt == "u8" else (np.float32, fr.FRACTAL_F32)
+    plan = fr.fractal_map(k, rho)
+    cells = plan.info()["member_tiles"] * rho * rho
+    arr = field(k, npdt, 77)
+    src = torch.from_numpy(arr.reshape(-1)).cuda()
+    dev = torch.zeros(cells, dtype=src.dtype, device="cuda")
+    host = torch.zeros(cells, dtype=src.dtype).pin_memory()
+    fr.fractal_pack(plan, src, code, dev)
+    fr.fractal_pack(plan, src, code, host)
+    torch.cuda.synchronize()
+    assert torch.equal(dev.cpu(), host)
+    out = torch.zeros(n * n, dtype=src.dtype, device="cuda")
+    fr.fractal_unpack(plan, host, code, out)
+    cover = tile_cover(n, rho)
+    back = out.cpu().numpy().reshape(n, n)
+    assert np.array_equal(back[cover].view(np.uint8), arr[cover].view(np.uint8))
+    assert np.all(back[~cover] == 0)
+
+
+def test_pack_rejects_pageable_host_memory(fr):
+    """Pageable memory is refused by the host-side pointer check, before any launch."""
+    plan = fr.fractal_map(6, 8)
+    a = torch.zeros(64 * 64, dtype=torch.float32, device="cuda")
+    pageable = torch.zeros(27 * 64, dtype=torch.float32)
+    assert not pageable.is_pinned()
+    with pytest.raises(Exception):
+        fr.fractal_pack(plan, a, fr.FRACTAL_F32, pageable)
+    with pytest.raises(Exception):
+        fr.fractal_unpack(plan, pageable, fr.FRACTAL_F32, a)
+
+
 def test_pack_rejects_bad_arguments(fr):
     plan = fr.fractal_map(6, 8)
     a = torch.zeros(64 * 64 + 4, dtype=torch.float32, device="cuda")
