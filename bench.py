@@ -226,6 +226,8 @@ def main():
     ap.add_argument("--rho", type=int, default=8, help="tile side of a --profile run")
     ap.add_argument("--mode", type=int, default=0, help="0 = lambda, 1 = BB (--profile)")
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="steps per call of a --profile run (0: 2 x --spl, i.e. two fused launches)")
     ap.add_argument("--spl", type=int, default=1,
                     help="steps per launch of a --profile ca/diffusion run (each repetition is 2 launches)")
     ap.add_argument("--levels", type=int, default=-1, help="CTA tile levels of a --profile run")
@@ -612,12 +614,13 @@ def profile_run(args):
         synth.device_fill(a.data_ptr(), synth.SYNTH_UNIFORM_F32, n, SEED)
     b = torch.empty_like(a)
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    steps = args.profile_steps or 2 * args.spl
     for _ in range(args.launches):
         if args.profile == "ca":
-            # two launches of `spl` steps each (the result lands back in a)
-            fr.fractal_step_ca(plan, a, b, 2 * args.spl)
+            # by default two launches of `spl` steps each (the result lands back in a)
+            fr.fractal_step_ca(plan, a, b, steps)
         elif args.profile == "diffusion":
-            fr.fractal_step_diffusion(plan, a, b, COEF, 2 * args.spl)
+            fr.fractal_step_diffusion(plan, a, b, COEF, steps)
         elif args.profile == "reduce":
             fr.fractal_reduce_async(plan, a, fr.FRACTAL_F32, out)
         else:

@@ -77,6 +77,10 @@ struct fractal_plan_s {
   bool user_levels[2] = {false, false};  // tile levels fixed by the caller
   Launch fused[2];              // fused kernel launch for the plan's steps per launch
   bool fused_ok[2] = {false, false};
+  float* d_pack[2] = {nullptr, nullptr};  // float32 fused: compact records between launches
+  size_t pack_cap = 0;          // bytes per record buffer
+  uint32_t* d_bits[2] = {nullptr, nullptr};  // uint8 fused: bit records between launches
+  size_t bits_cap = 0;          // bytes per bit-record buffer
   int* d_err = nullptr;         // device error word of the TMA kernels
   void* d_partials = nullptr;   // reduce scratch: one 8-byte partial per CTA
   size_t partials_cap = 0;      // elements
@@ -296,6 +300,39 @@ bool use_blocks(const fractal_plan_s* p, int dtype, Launch& B, int& levels) {
          blocks_geometry(p->k, p->mode, B, levels);
 }
 
+// A pair of device buffers of `need` bytes each, allocated once (kept while
+// large enough).
+template <typename T>
+int ensure_pair(T* (&buf)[2], size_t& cap, size_t need) {
+  if (need == 0 || need <= cap) return FRACTAL_OK;
+  for (int i = 0; i < 2; ++i) {
+    if (buf[i]) cudaFree(buf[i]);
+    buf[i] = nullptr;
+  }
+  cap = 0;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&buf[i], need) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < 2; ++j) {
+        if (buf[j]) cudaFree(buf[j]);
+        buf[j] = nullptr;
+      }
+      return FRACTAL_ENOMEM;
+    }
+  }
+  cap = need;
+  return FRACTAL_OK;
+}
+
+// The two record buffers of the fused launches of `dtype`: float32 3^(k-3)
+// block records of 112 bytes (179 MB at k = 16), uint8 3^(k-5) word-tile
+// records of 128 bytes (22.7 MB at k = 16).
+int ensure_records(fractal_plan_s* p, int dtype) {
+  if (dtype == FRACTAL_F32)
+    return ensure_pair(p->d_pack, p->pack_cap, (size_t)fused_records(p->k) * (size_t)fused_record_bytes());
+  return ensure_pair(p->d_bits, p->bits_cap, (size_t)ca_records(p->k) * 128);
+}
+
 int ensure_partials(fractal_plan_s* p) {
   size_t need = 1;
   {
@@ -352,11 +389,16 @@ int step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, double* dev_cou
   if (steps > 0 && p->spl[FRACTAL_U8] > 1 && p->fused_ok[FRACTAL_U8]) {
     const int spl = p->spl[FRACTAL_U8];
     const FusedSplit sp(steps, spl);
+    // between launches the state stays in the bit records (the first launch
+    // reads the embedded array, the last one writes it)
+    const bool rec = sp.L >= 2 && p->d_bits[0] && p->d_bits[1];
     for (int i = 0; i < sp.L; ++i) {
       const bool last = i == sp.L - 1;
       auto* part = last && dev_count ? static_cast<unsigned long long*>(p->d_partials) : nullptr;
-      cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], buf[i & 1], buf[(i + 1) & 1], sp.of(i), spl,
-                                      st, part);
+      const uint32_t* pin = rec && i > 0 ? p->d_bits[(i - 1) & 1] : nullptr;
+      uint32_t* pout = rec && !last ? p->d_bits[i & 1] : nullptr;
+      cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], pin ? nullptr : buf[i & 1],
+                                      pout ? nullptr : buf[(i + 1) & 1], sp.of(i), spl, st, part, pin, pout);
       if (e != cudaSuccess) return cuda_fail(e, "step_ca");
     }
     if (dev_count) {
@@ -399,11 +441,17 @@ int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, 
   if (steps > 0 && p->spl[FRACTAL_F32] > 1 && p->fused_ok[FRACTAL_F32]) {
     const int spl = p->spl[FRACTAL_F32];
     const FusedSplit sp(steps, spl);
+    // between launches the state stays in the compact records (the first
+    // launch reads the embedded array, the last one writes it)
+    const bool rec = sp.L >= 2 && p->d_pack[0] && p->d_pack[1];
     for (int i = 0; i < sp.L; ++i) {
       const bool last = i == sp.L - 1;
       double* part = last && dev_sum ? static_cast<double*>(p->d_partials) : nullptr;
+      const float* pin = rec && i > 0 ? p->d_pack[(i - 1) & 1] : nullptr;
+      float* pout = rec && !last ? p->d_pack[i & 1] : nullptr;
       cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[FRACTAL_F32],
-                                             buf[i & 1], buf[(i + 1) & 1], coef, sp.of(i), st, part);
+                                             pin ? nullptr : buf[i & 1], pout ? nullptr : buf[(i + 1) & 1], coef,
+                                             sp.of(i), st, part, pin, pout);
       if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
     }
     if (dev_sum) {
@@ -537,6 +585,10 @@ int fractal_map(int k, int rho, int mode, fractal_plan_t* out) {
 int fractal_plan_destroy(fractal_plan_t p) {
   if (!p) return FRACTAL_OK;
   if (p->d_partials) cudaFree(p->d_partials);
+  for (int i = 0; i < 2; ++i) {
+    if (p->d_pack[i]) cudaFree(p->d_pack[i]);
+    if (p->d_bits[i]) cudaFree(p->d_bits[i]);
+  }
   if (p->d_result) cudaFree(p->d_result);
   if (p->h_result) cudaFreeHost(p->h_result);
   if (p->d_err) cudaFree(p->d_err);
@@ -617,7 +669,9 @@ int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
   p->spl[dtype] = spl;
   p->fused[dtype] = f;
   p->fused_ok[dtype] = true;
-  return ensure_partials(p);  // the fused kernels' per-CTA sums
+  const int st = ensure_partials(p);  // the fused kernels' per-CTA sums
+  if (st != FRACTAL_OK) return st;
+  return ensure_records(p, dtype);
 }
 
 int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
@@ -648,8 +702,33 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   float best1 = -1.0f;
   int best1_m = old_m;
   int status = FRACTAL_OK;
-  // One launch dev_in -> dev_scratch: a single step, or `spl` fused steps.
-  auto launch = [&](int spl) -> int {
+  // One timed unit dev_in -> dev_scratch: a single step; `spl` fused steps;
+  // float32 fused: two launches of `spl` steps through the compact records,
+  // as a call of 2 spl steps runs them.  Returns the steps in `done`.
+  const bool records = ensure_records(p, dtype) == FRACTAL_OK;
+  auto launch = [&](int spl, int& done) -> int {
+    done = spl;
+    if (spl > 1 && dtype == FRACTAL_U8 && records) {  // as for float32 below
+      const Launch& F = p->fused[dtype];
+      cudaError_t e = launch_ca_fused(p->mode, F, (const uint8_t*)dev_in, nullptr, spl, spl, st, nullptr, nullptr,
+                                      p->d_bits[0]);
+      if (e == cudaSuccess)
+        e = launch_ca_fused(p->mode, F, nullptr, (uint8_t*)dev_scratch, spl, spl, st, nullptr, p->d_bits[0],
+                            nullptr);
+      done = 2 * spl;
+      return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "autotune");
+    }
+    if (spl > 1 && dtype == FRACTAL_F32 && records) {
+      const Launch& F = p->fused[dtype];
+      const int M = fused_margin(spl);
+      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, M, F, (const float*)dev_in, nullptr, 0.2f, spl, st,
+                                             nullptr, nullptr, p->d_pack[0]);
+      if (e == cudaSuccess)
+        e = launch_diffusion_fused(p->mode, p->log_rho, M, F, nullptr, (float*)dev_scratch, 0.2f, spl, st, nullptr,
+                                   p->d_pack[0], nullptr);
+      done = 2 * spl;
+      return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "autotune");
+    }
     if (spl > 1) {
       const cudaError_t e =
           dtype == FRACTAL_U8
@@ -685,10 +764,11 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
         p->fused_ok[dtype] = false;
       }
       p->sched = sched;
-      for (int i = 0; i < 2 && status == FRACTAL_OK; ++i) status = launch(spl);
+      int done = spl;
+      for (int i = 0; i < 2 && status == FRACTAL_OK; ++i) status = launch(spl, done);
       if (status != FRACTAL_OK) break;
       if (cudaEventRecord(e0, st) != cudaSuccess) { status = cuda_fail(cudaGetLastError(), "autotune"); break; }
-      for (int i = 0; i < reps && status == FRACTAL_OK; ++i) status = launch(spl);
+      for (int i = 0; i < reps && status == FRACTAL_OK; ++i) status = launch(spl, done);
       if (status != FRACTAL_OK) break;
       float ms = 0.f;
       if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -696,7 +776,7 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
         status = cuda_fail(cudaGetLastError(), "autotune");
         break;
       }
-      const float us = 1000.f * ms / (float)(reps * spl);
+      const float us = 1000.f * ms / (float)(reps * done);
       if (spl == 1 && (best1 < 0.f || us < best1)) {
         best1 = us;
         best1_m = m;

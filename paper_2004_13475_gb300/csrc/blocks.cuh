@@ -156,20 +156,31 @@ struct NbSum {
 // neighbours - degree * u).  Non-member neighbours hold no value and are not
 // summed; vu, vl, vr, vd are the neighbour values at the ports (0 where the
 // neighbour is not a staged member) and d0, dr, dd the ports' degrees.
+//
+// The 27 members and 26 links of a block form a tree; bparent names each
+// member's parent in it (the left neighbour if that is a member, else the
+// one above), and these parent links are all 26 links.  The update runs in
+// place, children before parents (anti-diagonals from the far corner): a
+// cell's old value joins its parent's neighbour sum before the cell is
+// overwritten, and the parent is still old when the cell is updated, so no
+// second copy of the block is needed.
+__host__ __device__ constexpr int bparent(int i, int j) {
+  return (i > 0 && amem(i - 1, j)) ? j * kB + i - 1 : (j - 1) * kB + i;
+}
+
 __device__ __forceinline__ void block_step(float (&u)[kB * kB], float a, float vu, float vl, float vr, float vd,
                                            float d0, float dr, float dd) {
-  float w[kB * kB];
+  NbSum acc[kB * kB];  // children's old values, per cell
 #pragma unroll
-  for (int j = 0; j < kB; ++j) {
+  for (int s = 2 * (kB - 1); s >= 0; --s) {
 #pragma unroll
-    for (int i = 0; i < kB; ++i) {
-      if (!amem(i, j)) continue;
-      NbSum nb;
-      if (amem(i, j - 1)) nb.add(u[(j - 1) * kB + i]);
-      if (amem(i - 1, j)) nb.add(u[j * kB + i - 1]);
-      if (amem(i + 1, j)) nb.add(u[j * kB + i + 1]);
-      if (amem(i, j + 1)) nb.add(u[(j + 1) * kB + i]);
+    for (int j = 0; j < kB; ++j) {
+      const int i = s - j;
+      if (i < 0 || i >= kB || !amem(i, j)) continue;
+      const int q = j * kB + i;
+      NbSum nb = acc[q];
       float d = (float)bdeg(i, j);
+      if (q != 0) nb.add(u[bparent(i, j)]);
       if (i == 0 && j == 0) {
         nb.add(vu);
         nb.add(vl);
@@ -183,13 +194,11 @@ __device__ __forceinline__ void block_step(float (&u)[kB * kB], float a, float v
         nb.add(vd);
         d = dd;
       }
-      const float c = u[j * kB + i];
-      w[j * kB + i] = fmaf(a, fmaf(-d, c, nb.s), c);
+      const float c = u[q];
+      if (q != 0) acc[bparent(i, j)].add(c);
+      u[q] = fmaf(a, fmaf(-d, c, nb.s), c);
     }
   }
-#pragma unroll
-  for (int q = 0; q < kB * kB; ++q)
-    if (amem(q % kB, q / kB)) u[q] = w[q];
 }
 
 // A 16-byte chunk of row j starting at column i0 with its non-members zeroed.

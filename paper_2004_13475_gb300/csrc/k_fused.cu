@@ -48,9 +48,40 @@ struct FGeo {
   int lw;       // 3^ceil(L/2): width of the level-L packed grid
   int nb;       // member blocks of the super-tile: 3^L
   int W;        // box width in blocks: M / 8
+  int lW;       // log2 W
   int nbox;     // box blocks: 6 W^2
   int log_rho;  // the plan's tile side (write-back of whole member tiles)
+  int R;        // super-tile levels of the array: (k - 3) - L
+  int lwR;      // 3^ceil(R/2): width of the level-R packed grid of super-tiles
 };
+
+// Compact records between the launches of one call: the 27 members of a
+// member 8 x 8 block (row-major order of the member cells) and one pad, 7
+// float4s, at record s * 3^L + t for member block t (lambda or BB rank order)
+// of member super-tile s (its index in the level-R packed grid, or its BB
+// rank).  3^(k-3) records hold the whole gasket; a launch reads and writes
+// them contiguously instead of eight scattered 32-byte rows per block.
+constexpr int kRecF4 = 7;
+
+// Record of the member block (GX, GY) (block coordinates in the array).
+template <int MODE>
+__device__ __forceinline__ int64_t block_record(int GX, int GY, const FGeo& f) {
+  const int mask = (1 << f.L) - 1;
+  const int ssx = GX >> f.L, ssy = GY >> f.L, lx = GX & mask, ly = GY & mask;
+  const int64_t s = MODE == kLambda ? lambda_inverse(ssx, ssy, f.R, f.lwR) : bb_rank(ssx, ssy, f.R);
+  const int t = MODE == kLambda ? lambda_inverse(lx, ly, f.L, f.lw) : bb_rank(lx, ly, f.L);
+  return s * f.nb + t;
+}
+
+// Member m of a record -> float m%4 of float4 m/4 (compile-time m).
+__device__ __forceinline__ float rec_get(const float4 (&r)[kRecF4], int m) {
+  const float4 v = r[m >> 2];
+  return (m & 3) == 0 ? v.x : (m & 3) == 1 ? v.y : (m & 3) == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void rec_set(float4 (&r)[kRecF4], int m, float x) {
+  float4& v = r[m >> 2];
+  if ((m & 3) == 0) v.x = x; else if ((m & 3) == 1) v.y = x; else if ((m & 3) == 2) v.z = x; else v.w = x;
+}
 
 // Member blocks the margin boxes can hold: a gasket fragment of side M at
 // each of the three contacts, 3 * 3^log2(W) (tests/test_fusion_boxes.py
@@ -63,6 +94,7 @@ __host__ __device__ inline int box_cap(int W) {
 constexpr int kMaxW = 16;                    // margins up to 128 cells
 constexpr int kMaxBox = 6 * kMaxW * kMaxW;   // box blocks: 6 W^2
 constexpr int kMaxBoxMembers = 243;          // box_cap(16)
+constexpr int kMaxSide = 32;                 // blocks per super-tile side (T <= 256)
 
 // Member block t of the super-tile (lambda order, or BB rank order via tab).
 template <int MODE>
@@ -79,37 +111,39 @@ __device__ __forceinline__ void member_block(int t, const FGeo& f, const int* ta
 // Box block b (0 <= b < 6 W^2): left, top, right, bottom boxes in row order.
 // Block coordinates relative to the super-tile.
 __device__ __forceinline__ void box_block(int b, const FGeo& f, int& bx, int& by) {
-  const int W = f.W, W2 = W * W, side = 1 << f.L;
+  const int W = f.W, lW = f.lW, W2 = W * W, side = 1 << f.L;
   if (b < W2) {  // left
-    bx = -W + b % W;
-    by = b / W;
+    bx = -W + (b & (W - 1));
+    by = b >> lW;
     return;
   }
   b -= W2;
   if (b < W2) {  // top
-    bx = b % W;
-    by = -W + b / W;
+    bx = b & (W - 1);
+    by = -W + (b >> lW);
     return;
   }
   b -= W2;
   if (b < 2 * W2) {  // right
-    bx = side + b % W;
-    by = -W + b / W;
+    bx = side + (b & (W - 1));
+    by = -W + (b >> lW);
     return;
   }
   b -= 2 * W2;  // bottom
-  bx = -W + b % (2 * W);
-  by = side + b / (2 * W);
+  bx = -W + (b & (2 * W - 1));
+  by = side + (b >> (lW + 1));
 }
 
 // Thread that owns block (bx, by), or `none` if no staged member block is
-// there; boxrank: compacted rank of each box block, -1 for non-members.
-template <int MODE>
-__device__ __forceinline__ int fused_owner(int bx, int by, const FGeo& f, const int* boxrank, int none) {
+// there; own: the thread of each member block of the super-tile (slot
+// by * side + bx); boxrank: compacted rank of each box block, -1 for
+// non-members.
+__device__ __forceinline__ int fused_owner(int bx, int by, const FGeo& f, const short* own, const int* boxrank,
+                                           int none) {
   const int side = 1 << f.L, W = f.W, W2 = W * W;
   if (bx >= 0 && by >= 0 && bx < side && by < side) {
     if (bx & by) return none;
-    return MODE == kLambda ? lambda_inverse(bx, by, f.L, f.lw) : bb_rank(bx, by, f.L);
+    return own[(by << f.L) + bx];
   }
   int b = -1;
   if (bx >= -W && bx < 0 && by >= 0 && by < W) b = by * W + (bx + W);
@@ -130,12 +164,17 @@ __host__ __device__ inline int fused_slots(int threads) { return threads + 1; }
 
 // One super-tile whose block origin is (OX, OY) (in blocks).  All threads of
 // the CTA call it; it ends after the write-back.  ports: 6 * slots floats.
+// The state comes from the embedded array `in`, or from the records `pin`
+// when that is not null; it goes to the embedded array `out`, or to the
+// records `pout` when that is not null (srec: the super-tile's first record).
 // Returns this thread's share of the sum of the written members (its block's
-// rows in FP32, the rows in FP64; 0 for box blocks and idle threads).
+// rows in FP32, the rows in FP64; 0 for box blocks and idle threads, and 0
+// unless want_sum).
 template <int MODE>
 __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
                                                   int nsteps, const FGeo& f, int OX, int OY, const int* tab,
-                                                  float* ports) {
+                                                  float* ports, bool want_sum, const float* __restrict__ pin,
+                                                  float* __restrict__ pout, int64_t srec) {
   const int t = threadIdx.x, nthreads = blockDim.x;
   const int slots = fused_slots(nthreads), zero = nthreads;
   const int nblk = f.n / kB;
@@ -146,6 +185,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   // the margin boxes' member blocks, compacted in box order: boxrank[b] is
   // the rank of box block b among them (-1 if not a member), boxlist the list
   __shared__ int boxrank[kMaxBox], boxlist[kMaxBoxMembers], wcnt[16];
+  __shared__ short own[kMaxSide * kMaxSide];
   int nbox_member = 0;
   for (int b0 = 0; b0 < f.nbox; b0 += nthreads) {
     const int b = b0 + t;
@@ -158,12 +198,12 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
     const unsigned bal = __ballot_sync(0xffffffffu, m);
     if ((t & 31) == 0) wcnt[t >> 5] = __popc(bal);
     __syncthreads();
-    int rank = nbox_member, total = 0;
-    for (int w = 0; w < (nthreads >> 5); ++w) {
-      rank += w < (t >> 5) ? wcnt[w] : 0;
-      total += wcnt[w];
-    }
-    rank += __popc(bal & ((1u << (t & 31)) - 1u));
+    // lane l holds warp l's count: the warps before this one, and all
+    const int lane = t & 31, nw = nthreads >> 5;
+    const unsigned c = lane < nw ? (unsigned)wcnt[lane] : 0u;
+    int rank = nbox_member + (int)__reduce_add_sync(0xffffffffu, lane < (t >> 5) ? c : 0u);
+    const int total = (int)__reduce_add_sync(0xffffffffu, c);
+    rank += __popc(bal & ((1u << lane) - 1u));
     if (b < f.nbox) {
       boxrank[b] = m ? rank : -1;
       if (m) boxlist[rank] = b;
@@ -176,6 +216,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   bool active = false;
   if (t < f.nb) {
     member_block<MODE>(t, f, tab, bx, by);
+    own[(by << f.L) + bx] = (short)t;  // every member slot is some thread's
     active = true;
   } else if (t - f.nb < nbox_member && t - f.nb < box_cap(f.W)) {
     box_block(boxlist[t - f.nb], f, bx, by);
@@ -186,16 +227,17 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   // ports' degrees: 2, 1, 1 inside the block plus the member neighbour blocks
   int up = zero, lf = zero, rt = zero, dn = zero;
   float d0 = 2.f, dr = 1.f, dd = 1.f;
+  __syncthreads();  // own[] complete
   if (active) {
     const bool fu = block_member(GX, GY - 1, nblk), fl = block_member(GX - 1, GY, nblk);
     const bool fr = block_member(GX + 1, GY, nblk), fd = block_member(GX, GY + 1, nblk);
     d0 += (fu ? 1.f : 0.f) + (fl ? 1.f : 0.f);
     dr += fr ? 1.f : 0.f;
     dd += fd ? 1.f : 0.f;
-    if (fu) up = fused_owner<MODE>(bx, by - 1, f, boxrank, zero);
-    if (fl) lf = fused_owner<MODE>(bx - 1, by, f, boxrank, zero);
-    if (fr) rt = fused_owner<MODE>(bx + 1, by, f, boxrank, zero);
-    if (fd) dn = fused_owner<MODE>(bx, by + 1, f, boxrank, zero);
+    if (fu) up = fused_owner(bx, by - 1, f, own, boxrank, zero);
+    if (fl) lf = fused_owner(bx - 1, by, f, own, boxrank, zero);
+    if (fr) rt = fused_owner(bx + 1, by, f, own, boxrank, zero);
+    if (fd) dn = fused_owner(bx, by + 1, f, own, boxrank, zero);
   }
 
   // stage: the block's 12 member chunks straight into registers
@@ -203,7 +245,17 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
 #pragma unroll
   for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
   const size_t base = (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
-  if (active) {
+  if (active && pin) {
+    const int64_t rec = t < f.nb ? srec + t : block_record<MODE>(GX, GY, f);
+    const float4* p = reinterpret_cast<const float4*>(pin) + rec * kRecF4;
+    float4 r[kRecF4];
+#pragma unroll
+    for (int i = 0; i < kRecF4; ++i) r[i] = __ldg(p + i);
+    int m = 0;
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q)
+      if (amem(q % kB, q / kB)) u[q] = rec_get(r, m++);
+  } else if (active) {
     float4 c[12];
 #pragma unroll
     for (int j = 0; j < kB; ++j) c[j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n));
@@ -236,6 +288,8 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   }
   __syncthreads();
 
+  // two steps per iteration: the port offsets of both parities are fixed
+#pragma unroll 2
   for (int s = 0; s < nsteps; ++s) {
     const int cur = (s & 1) * slots, nxt = slots - cur;
     if (active) {
@@ -250,7 +304,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
 
   // write back the super-tile's member blocks (not the boxes)
   double sum = 0.0;
-  if (active && t < f.nb) {
+  if (want_sum && active && t < f.nb) {
 #pragma unroll
     for (int j = 0; j < kB; ++j) {
       float r = 0.f;
@@ -263,6 +317,18 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
       }
       sum += (double)r;
     }
+  }
+  if (active && t < f.nb && pout) {
+    float4 r[kRecF4];
+    r[kRecF4 - 1].w = 0.f;  // the pad
+    int m = 0;
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q)
+      if (amem(q % kB, q / kB)) rec_set(r, m++, u[q]);
+    float4* p = reinterpret_cast<float4*>(pout) + (srec + t) * kRecF4;
+#pragma unroll
+    for (int i = 0; i < kRecF4; ++i) p[i] = r[i];
+  } else if (active && t < f.nb) {
     float* o = out + base;
 #pragma unroll
     for (int j = 0; j < kB; ++j)
@@ -293,7 +359,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   return sum;
 }
 
-__device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho) {
+__device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho, int R) {
   FGeo f;
   f.n = n;
   f.L = ilog2c(T) - 3;
@@ -303,8 +369,13 @@ __device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho) {
   f.lw = lw;
   f.nb = nb;
   f.W = M / kB;
+  f.lW = ilog2c(f.W);
   f.nbox = 6 * f.W * f.W;
   f.log_rho = log_rho;
+  f.R = R;
+  int lwR = 1;
+  for (int i = 0; i < (R + 1) / 2; ++i) lwR *= 3;
+  f.lwR = lwR;
   return f;
 }
 
@@ -320,7 +391,9 @@ __device__ __forceinline__ void bb_table(int* tab, const FGeo& f) {
 template <int MODE, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                               float a, int nsteps, int M, int log_rho, Geo g,
-                                                              double* __restrict__ partials) {
+                                                              double* __restrict__ partials,
+                                                              const float* __restrict__ pin,
+                                                              float* __restrict__ pout) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ double red[32];
   int sx, sy;
@@ -328,14 +401,18 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
     if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
     return;
   }
-  const FGeo f = make_fgeo(g.n, g.T, M, log_rho);
+  const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
   float* ports = fsm;
   int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(blockDim.x));
   if (MODE == kBB) {
     bb_table(tab, f);
     __syncthreads();
   }
-  const double mine = fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports);
+  int64_t srec = 0;
+  if (pin || pout)
+    srec = (int64_t)(MODE == kLambda ? lambda_inverse(sx, sy, f.R, f.lwR) : bb_rank(sx, sy, f.R)) * f.nb;
+  const double mine = fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports,
+                                            partials != nullptr, pin, pout, srec);
   if (partials) {  // the sum of the result's members, per CTA (uniform branch)
     const double s = block_sum<double>(mine, red);
     if (threadIdx.x == 0) partials[cta_id()] = s;
@@ -365,8 +442,9 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
     const int64_t om = w - I.first;
     int sx, sy;
     warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
-    const FGeo f = make_fgeo(I.n, T, M, 3);
-    fused_supertile<kLambda>(which ? I.b : I.a, which ? I.a : I.b, a, nsteps, f, sx << f.L, sy << f.L, nullptr, fsm);
+    const FGeo f = make_fgeo(I.n, T, M, 3, I.R);
+    fused_supertile<kLambda>(which ? I.b : I.a, which ? I.a : I.b, a, nsteps, f, sx << f.L, sy << f.L, nullptr, fsm, false,
+                              nullptr, nullptr, 0);
   }
 }
 
@@ -427,12 +505,12 @@ __global__ void batch_sums_kernel(const BatchInst* __restrict__ inst, int count,
 
 template <int MODE>
 cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
-               double* partials, cudaStream_t s) {
+               double* partials, const float* pin, float* pout, cudaStream_t s) {
   // the smallest CTA class that holds the launch: more CTAs per SM
   auto run = [&](auto* k) -> cudaError_t {
     cudaError_t e = allow_smem((const void*)k, L.smem);
     if (e != cudaSuccess) return e;
-    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials);
+    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials, pin, pout);
     return cudaGetLastError();
   };
   if (L.threads <= 288) return run(diffusion_fused_kernel<MODE, 288, 4>);
@@ -499,11 +577,21 @@ cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items,
 }
 
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
-                                   float a, int nsteps, cudaStream_t s, double* partials) {
-  if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads)
+                                   float a, int nsteps, cudaStream_t s, double* partials, const float* pin,
+                                   float* pout) {
+  if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads ||
+      (!in && !pin) || (!out && !pout))
     return cudaErrorInvalidValue;
-  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, s)
-                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, s);
+  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, s)
+                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, s);
 }
+
+int64_t fused_records(int k) {
+  int64_t r = 1;
+  for (int i = 3; i < k; ++i) r *= 3;
+  return k >= 3 ? r : 0;
+}
+
+int fused_record_bytes() { return kRecF4 * 16; }
 
 }  // namespace fractal

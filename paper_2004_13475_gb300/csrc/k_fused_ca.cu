@@ -31,6 +31,14 @@
 // shifts, applies the bit-sliced rule, masks births outside the gasket and
 // writes the word to the other image.  Every staged word is the word of exactly one task
 // lane; every other word of the image is 0 and stays 0.
+//
+// Records.  Between the launches of one call the state stays in compact
+// records, one per member word tile: its 32 words (row order), 128 bytes
+// instead of 32 rows of 32 bytes.  Record s * 3^wlev + j holds word tile j
+// (lambda or BB rank order) of member super-tile s (its index in the level-R
+// packed grid, or its BB rank); the first launch of a call reads the embedded
+// array and the last one writes it.
+#include "blocks.cuh"
 #include "launch.h"
 
 namespace fractal {
@@ -100,7 +108,8 @@ __device__ __forceinline__ uint32_t life_rule_words(uint32_t ul, uint32_t uc, ui
 template <int MODE>
 __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                                        int nsteps, int M, int wlev, Geo g,
-                                                       unsigned long long* __restrict__ partials) {
+                                                       unsigned long long* __restrict__ partials,
+                                                       const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout) {
   constexpr int TPW = kCaTasksPerWarp;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ unsigned long long red[32];
@@ -120,6 +129,18 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
   uint32_t* A = tab + tab_words(wtiles);
   uint32_t* B = A + img;
   const int ox = sx * T, oy = sy * T;
+  int lwR = 1;  // 3^ceil(R/2)
+  for (int i = 0; i < (g.R + 1) / 2; ++i) lwR *= 3;
+  // first record of this super-tile, and the record of word tile (tx, ty)
+  auto st_index = [&](int x, int y) -> int64_t {
+    return MODE == kLambda ? lambda_inverse(x, y, g.R, lwR) : bb_rank(x, y, g.R);
+  };
+  const int64_t srec = (pin || pout) ? st_index(sx, sy) * wtiles : 0;
+  auto tile_record = [&](int tx, int ty) -> int64_t {
+    const int lx = tx & (wside - 1), ly = ty & (wside - 1);
+    const int local = MODE == kLambda ? lambda_inverse(lx, ly, wlev, wlw) : bb_rank(lx, ly, wlev);
+    return st_index(tx >> wlev, ty >> wlev) * wtiles + local;
+  };
 
   // member word tiles of the super-tile
   if (MODE == kLambda) {
@@ -151,6 +172,7 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
 #pragma unroll
   for (int h = 0; h < TPW; h += TPW / 2) {
     uint4 ld[TPW / 2][2];
+    uint32_t wd[TPW / 2];
 #pragma unroll
     for (int k = h; k < h + TPW / 2; ++k) {
       off[k] = -1;
@@ -164,7 +186,10 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
       const int gx0 = ox + 32 * c, gy = oy + y;
       off[k] = (y + M + 1) * P + c + 2;
       mk[k] = (unsigned)gx0 < (unsigned)n ? chunk_members<32>(gx0, gy, n) : 0u;
-      if (mk[k]) {
+      if (mk[k] && pin) {  // a member word: its word tile is a member
+        const int64_t rec = j < wtiles ? srec + j : tile_record(gx0 >> 5, gy >> 5);
+        wd[k - h] = __ldg(pin + rec * 32 + (gy & 31));
+      } else if (mk[k]) {
         const uint4* p = reinterpret_cast<const uint4*>(in + (size_t)gy * n + gx0);
         ld[k - h][0] = __ldg(p);
         ld[k - h][1] = __ldg(p + 1);
@@ -172,10 +197,12 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     }
 #pragma unroll
     for (int k = h; k < h + TPW / 2; ++k)
-      if (off[k] >= 0 && mk[k]) A[off[k]] = pack32(ld[k - h][0], ld[k - h][1]) & mk[k];
+      if (off[k] >= 0 && mk[k]) A[off[k]] = (pin ? wd[k - h] : pack32(ld[k - h][0], ld[k - h][1])) & mk[k];
   }
   __syncthreads();
 
+  // unrolled: the image pointers of both parities are fixed
+#pragma unroll 4
   for (int t = 0; t < nsteps; ++t) {
 #pragma unroll
     for (int k = 0; k < TPW; ++k) {
@@ -198,6 +225,10 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     const int c = off[k] % P - 2, y = off[k] / P - M - 1;
     const uint32_t w = A[off[k]];
     alive += __popc(w);
+    if (pout) {  // record of word tile j, row y mod 32
+      pout[(srec + j) * 32 + (y & 31)] = w;
+      continue;
+    }
     uint4 v0, v1;
     v0.x = spread4(w);
     v0.y = spread4(w >> 4);
@@ -219,11 +250,11 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
 
 template <int MODE>
 cudaError_t go(const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
-               unsigned long long* partials, cudaStream_t s) {
+               unsigned long long* partials, const uint32_t* pin, uint32_t* pout, cudaStream_t s) {
   auto* k = ca_fused_kernel<MODE>;
   cudaError_t e = allow_smem((const void*)k, L.smem);
   if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, ilog2c(L.geo.T) - 5, L.geo, partials);
+  k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, ilog2c(L.geo.T) - 5, L.geo, partials, pin, pout);
   return cudaGetLastError();
 }
 
@@ -250,10 +281,18 @@ int ca_fused_threads(const Geo& g, int margin) {
 }
 
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
-                            cudaStream_t s, unsigned long long* partials) {
-  if (nsteps < 1 || nsteps > margin || ca_fused_threads(L.geo, margin) != L.threads) return cudaErrorInvalidValue;
-  return mode == kLambda ? go<kLambda>(L, in, out, nsteps, margin, partials, s)
-                         : go<kBB>(L, in, out, nsteps, margin, partials, s);
+                            cudaStream_t s, unsigned long long* partials, const uint32_t* pin, uint32_t* pout) {
+  if (nsteps < 1 || nsteps > margin || ca_fused_threads(L.geo, margin) != L.threads || (!in && !pin) ||
+      (!out && !pout))
+    return cudaErrorInvalidValue;
+  return mode == kLambda ? go<kLambda>(L, in, out, nsteps, margin, partials, pin, pout, s)
+                         : go<kBB>(L, in, out, nsteps, margin, partials, pin, pout, s);
+}
+
+int64_t ca_records(int k) {
+  int64_t r = 1;
+  for (int i = 5; i < k; ++i) r *= 3;
+  return k >= 5 ? r : 0;
 }
 
 }  // namespace fractal

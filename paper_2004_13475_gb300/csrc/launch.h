@@ -39,16 +39,30 @@ int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 // Temporally fused diffusion: nsteps (<= margin) steps per launch (k_fused.cu).
 // partials (nullable): one double per CTA of L, the sum of the result's
 // members over the CTA's super-tile (finish with launch_final_sum).
+// in / out: embedded arrays; pin / pout (when not null): compact records in
+// place of in / out (the state between the launches of one call).
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
-                                   float a, int nsteps, cudaStream_t s, double* partials = nullptr);
+                                   float a, int nsteps, cudaStream_t s, double* partials = nullptr,
+                                   const float* pin = nullptr, float* pout = nullptr);
+// Compact records of a level-k gasket (3^(k-3), one per member 8 x 8 block)
+// and the bytes of one.
+int64_t fused_records(int k);
+int fused_record_bytes();
 int fused_margin(int steps_per_launch);
 int fused_smem_bytes(const Geo& g, int margin);
 int fused_threads(const Geo& g, int rho, int margin);
 
 // Temporally fused automaton on a bit image: nsteps (<= margin <= 31) steps
 // per launch over 32 x 32-cell word tiles (k_fused_ca.cu).
+// in / out: embedded arrays; pin / pout (when not null): bit records of the
+// member word tiles in place of in / out (the state between the launches of
+// one call).
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
-                            cudaStream_t s, unsigned long long* partials = nullptr);
+                            cudaStream_t s, unsigned long long* partials = nullptr, const uint32_t* pin = nullptr,
+                            uint32_t* pout = nullptr);
+// Bit records of a level-k gasket: 3^(k-5) member 32 x 32 word tiles, 128
+// bytes each.
+int64_t ca_records(int k);
 
 // Sum of per-CTA partials (dtype 0: uint64 counts, 1: doubles) into *dev_out.
 cudaError_t launch_final_sum(int dtype, const void* partials, int64_t count, double* dev_out, cudaStream_t s);
