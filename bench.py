@@ -381,9 +381,15 @@ def main():
     spl_c = info_c["steps_per_launch"][0]
     kd = kernel_launches(spl_d, REDUCE_EVERY) * (DIFF_STEPS // REDUCE_EVERY)    # per bench step
     kc = kernel_launches(spl_c, CA_STEPS)
-    rf_d = launch_roofline("diffusion", info_d, spl_d, diff_ms / 1e3 / (kd * args.steps), hbm, peak_kind)
-    rf_c = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind)
-    roofline = rf_d if diff_ms >= ca_ms else rf_c          # the kernel that takes most of the step
+    rf_d, alu_d = launch_roofline("diffusion", info_d, spl_d, diff_ms / 1e3 / (kd * args.steps), hbm, peak_kind,
+                                  REDUCE_EVERY)
+    rf_c, _ = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind, CA_STEPS)
+    # the kernel that takes most of the step, against the roof that bounds it:
+    # the fused diffusion against the FP32 pipes (its HBM view beside it)
+    if diff_ms >= ca_ms:
+        roofline, roofline_hbm, roofline_other = (alu_d or rf_d), (rf_d if alu_d else None), rf_c
+    else:
+        roofline, roofline_hbm, roofline_other = rf_c, None, (alu_d or rf_d)
     # plus, per global measure, a final-sum launch (fused) or a reduce and a final sum
     launches_per_step = (kc + kd + (1 if spl_c > 1 else 2)
                          + (DIFF_STEPS // REDUCE_EVERY) * (1 if spl_d > 1 else 2))
@@ -422,7 +428,8 @@ def main():
                     "n": len(per_step)},
         "clocks": clocks,
         "roofline": roofline,
-        "roofline_other": rf_c if roofline is rf_d else rf_d,
+        "roofline_hbm": roofline_hbm,
+        "roofline_other": roofline_other,
         "vs_hbm_floor": floors,
         "bb": None if value_bb is None else {
             "value": value_bb, "ms_per_step": 1e3 * t_bb / max(1, args.steps // 2),
@@ -530,7 +537,8 @@ def diffusion_box_member_blocks(k, T, M):
 KERNEL_SOURCES = {
     "diffusion_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
                                "paper_2004_13475_gb300/csrc/gasket.cuh"),
-    "ca_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused_ca.cu", "paper_2004_13475_gb300/csrc/gasket.cuh"),
+    "ca_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused_ca.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
+                        "paper_2004_13475_gb300/csrc/gasket.cuh"),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
@@ -562,32 +570,81 @@ def measured_traffic(kernel, k):
     return None
 
 
-def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind):
-    """HBM roofline of one launch of the workload's step kernel: algorithmic
-    bytes (every member tile read and written once, plus the margin boxes a
-    fused launch reads) over the launch's measured mean duration."""
+# FP32 peak of the plain (non-tensor) pipes: 152 SMs x 128 FP32 lanes x 2
+# flops (FMA) x 2.07 GHz (the part's maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def diffusion_flops_per_step(k):
+    """Algorithmic FP32 flops of one diffusion step of the level-k gasket:
+    u_c + a * sum_nb (u_nb - u_c) costs 2 deg_c + 1 (deg subtractions, deg - 1
+    additions, one multiply, one add); the member 4-neighbour links of the
+    gasket number E_k = 3 E_{k-1} + 2 = 3^k - 1, so the sum over members is
+    4 (3^k - 1) + 3^k."""
+    return 5 * 3 ** k - 4
+
+
+def fused_launch_kinds(call_steps, spl):
+    """Source and target of each launch of a fused call: E = the embedded
+    array, R = the compact records kept between the launches of one call."""
+    n = kernel_launches(spl, call_steps)
+    return ["EE"] if n <= 1 else ["ER"] + ["RR"] * (n - 2) + ["RE"]
+
+
+def fused_launch_bytes(wl, kind, k, box):
+    """Algorithmic DRAM bytes of one fused launch of `kind`: every member unit
+    read from its source and written to its target once, plus the margin-box
+    members read.  Diffusion units: member 8 x 8 blocks, 8 rows of 32 bytes
+    embedded, 112-byte records; automaton units: member 32 x 32 word tiles,
+    32 rows of 32 bytes embedded, 128-byte bit records; `box`: box blocks, or
+    box words (32-byte row segments embedded, 4-byte words in records)."""
+    if wl == "diffusion":
+        units, emb, rec, box_emb, box_rec = 3 ** (k - 3), 256, 112, 256, 112
+    else:
+        units, emb, rec, box_emb, box_rec = 3 ** (k - 5), 1024, 128, 32, 4
+    read = units * (emb if kind[0] == "E" else rec) + box * (box_emb if kind[0] == "E" else box_rec)
+    return read + units * (emb if kind[1] == "E" else rec)
+
+
+def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps):
+    """HBM roofline of the mean launch of the workload's step kernel in a call
+    of `call_steps` steps: algorithmic bytes over the launch's measured mean
+    duration.  For the fused diffusion also its FP32 roofline (returned
+    second, else None): algorithmic flops over the same duration."""
     rho = info["rho"]
     d = 0 if wl == "ca" else 1
-    if wl == "diffusion" and spl > 1:
-        # every member 8 x 8 block (8 rows of one 32-byte sector) read and
-        # written once, plus the member blocks of the margin boxes (M = spl
-        # rounded up to a multiple of 8) read once
+    alu = None
+    kinds = fused_launch_kinds(call_steps, spl) if spl > 1 else []
+    if spl > 1:
         T = rho << info["cta_levels"][d]
-        margin = -(-spl // 8) * 8
-        alg = 2 * 3 ** (info["k"] - 3) * 256 + 256 * diffusion_box_member_blocks(info["k"], T, margin)
+        if wl == "diffusion":
+            margin = 8
+            while margin < spl:         # the kernel's margin: a power of two >= max(8, spl)
+                margin *= 2
+            box = diffusion_box_member_blocks(info["k"], T, margin)
+        else:
+            box = ca_box_member_words(info["k"], T, spl)
+        alg = sum(fused_launch_bytes(wl, kd, info["k"], box) for kd in kinds) / len(kinds)
     elif wl == "diffusion":
         alg = 2 * info["member_tiles"] * rho * rho * 4
-    elif spl > 1:       # 32-byte row segments of the member 32 x 32 word tiles, plus box words
-        T = rho << info["cta_levels"][d]
-        alg = 2 * 3 ** (info["k"] - 5) * 32 * 32 + 32 * ca_box_member_words(info["k"], T, spl)
     else:
         alg = 2 * info["member_tiles"] * rho * rho
     achieved = alg / launch_s / 1e9
     name = kernel_name(wl, info, spl)
     traffic = measured_traffic(name.split("<")[0], info["k"]) if spl > 1 else None
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "alg_bytes_per_launch": alg, "launch_us": launch_s * 1e6, "steps_per_launch": spl}
+    hbm_rf = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
+              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+              "alg_bytes_per_launch": alg, "launch_us": launch_s * 1e6, "steps_per_launch": spl,
+              "launch_kinds": ",".join(kinds) if kinds else "EE"}
+    if wl == "diffusion" and spl > 1:
+        flops = diffusion_flops_per_step(info["k"]) * call_steps / len(kinds)
+        tf = flops / launch_s / 1e12
+        alu = {"kernel": name, "bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS,
+               "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz", "unit": "TFLOP/s",
+               "frac": tf / FP32_PEAK_TFLOPS, "traffic": traffic, "alg_flops_per_launch": flops,
+               "launch_us": launch_s * 1e6, "steps_per_launch": call_steps / len(kinds),
+               "launch_kinds": ",".join(kinds)}
+    return hbm_rf, alu
 
 
 def profile_run(args):

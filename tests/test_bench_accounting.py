@@ -1,0 +1,37 @@
+"""The benchmark's roofline accounting on CPU: the algorithmic flops and bytes
+it divides by, pinned to the oracle's member graph and to hand counts."""
+import oracle
+
+import bench
+
+
+def test_diffusion_flops_count_the_member_links():
+    # 2 deg + 1 flops per member update; the links of the level-k gasket are
+    # 3^k - 1 (three copies joined by two links per level)
+    for k in range(1, 8):
+        dom = oracle.Domain.build(1 << k)
+        deg = (dom.nb4 >= 0).sum(axis=1)
+        assert int(deg.sum()) // 2 == 3 ** k - 1
+        assert bench.diffusion_flops_per_step(k) == int((2 * deg + 1).sum())
+
+
+def test_launch_kinds_follow_the_step_driver():
+    # ceil(steps / spl) launches, one more when the parity differs; records
+    # between the launches of one call
+    assert bench.fused_launch_kinds(100, 50) == ["ER", "RE"]
+    assert bench.fused_launch_kinds(100, 25) == ["ER", "RR", "RR", "RE"]
+    assert bench.fused_launch_kinds(100, 100) == ["ER", "RE"]
+    assert bench.fused_launch_kinds(25, 25) == ["EE"]
+    assert bench.fused_launch_kinds(26, 26) == ["ER", "RE"]
+    assert bench.fused_launch_kinds(3, 3) == ["EE"]
+    assert bench.kernel_launches(50, 100) == 2 and bench.kernel_launches(25, 100) == 4
+
+
+def test_launch_bytes_by_hand():
+    # k = 5: 9 member 8 x 8 blocks (256 B embedded, 112 B records), 1 word tile
+    assert bench.fused_launch_bytes("diffusion", "EE", 5, 0) == 9 * 512
+    assert bench.fused_launch_bytes("diffusion", "ER", 5, 2) == 11 * 256 + 9 * 112
+    assert bench.fused_launch_bytes("diffusion", "RR", 5, 2) == 11 * 112 + 9 * 112
+    assert bench.fused_launch_bytes("diffusion", "RE", 5, 2) == 11 * 112 + 9 * 256
+    assert bench.fused_launch_bytes("ca", "ER", 5, 3) == 1024 + 3 * 32 + 128
+    assert bench.fused_launch_bytes("ca", "RE", 5, 3) == 128 + 3 * 4 + 1024
