@@ -156,11 +156,17 @@ int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, vo
  * 128, rho >= 4, a super-tile side of at least 16 cells and twice the margin
  * (the smallest power of two >= max(spl, 8)); the kernel takes the largest
  * such super-tile it can hold, whatever fractal_plan_set_cta_levels chose.
- * Each launch reads and writes every member tile once, so the per-launch
- * cost is mostly memory traffic: fewer, longer launches pay.  FRACTAL_U8 (automaton, on a bit image of 32-cell
- * words): spl <= 31, a super-tile side of 32 to 512 cells and at least 2*spl
- * (k >= 6).  The super-tile may be smaller than the plan's step kernels use.
- * Errors: FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan).
+ * FRACTAL_U8 (automaton, on a bit image of 32-cell words): spl <= 31, a
+ * super-tile side of 32 to 512 cells and at least 2*spl (k >= 6).  The
+ * super-tile may be smaller than the plan's step kernels use.
+ * A call of more than one launch keeps the state between its launches in
+ * compact records the plan allocates here, two buffers of 3^(k-3) records of
+ * 112 bytes (float32: the 27 members of a member 8 x 8 block) or of 3^(k-5)
+ * records of 128 bytes (uint8: the 32 words of a member 32 x 32 word tile),
+ * freed with the plan: only the first launch reads dev_a and only the last
+ * writes the result buffer; the other caller buffer is then not written.
+ * Errors: FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan),
+ * FRACTAL_ENOMEM.
  */
 int fractal_plan_set_steps_per_launch(fractal_plan_t plan, int dtype, int spl);
 
@@ -451,7 +457,11 @@ int fractal_batch_destroy(fractal_batch_t batch);
  * arrays of `count` device pointers) are distinct n_i*n_i float32 arrays,
  * 16-byte aligned.  Copies the table to the device (synchronous); may be
  * called again with other buffers, which a captured graph then uses too.
- * Errors: FRACTAL_EINVAL (NULL, equal or misaligned pointers), FRACTAL_ECUDA.
+ * The first call also allocates the batch's block records (two buffers of
+ * sum_i 3^(k_i-3) records of 112 bytes), where the state stays between the
+ * launches of one step call.
+ * Errors: FRACTAL_EINVAL (NULL, equal or misaligned pointers), FRACTAL_ENOMEM,
+ * FRACTAL_ECUDA.
  */
 int fractal_batch_bind(fractal_batch_t batch, float* const* dev_a, float* const* dev_b);
 

@@ -32,6 +32,7 @@ struct fractal_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_steps = 0;
+  float* d_rec[2] = {nullptr, nullptr};  // block records between the launches of one call
 };
 
 namespace {
@@ -98,14 +99,19 @@ int rebuild(fractal_batch_s* b) {
 }
 
 int launch_steps(fractal_batch_s* b, float a, int steps, cudaStream_t s) {
-  // L launches with the parity of `steps`, as fractal_step_diffusion
+  // L launches with the parity of `steps`, as fractal_step_diffusion; between
+  // them the state stays in the block records (first launch from the
+  // instances' buffers, last one back into them)
   int L = (steps + b->spl - 1) / b->spl;
   if ((L & 1) != (steps & 1)) ++L;
   const int base = steps / L, extra = steps % L;
+  const bool rec = L >= 2 && b->d_rec[0] && b->d_rec[1];
   for (int i = 0; i < L; ++i) {
     const int ns = base + (i < extra ? 1 : 0);
+    const float* pin = rec && i > 0 ? b->d_rec[(i - 1) & 1] : nullptr;
+    float* pout = rec && i < L - 1 ? b->d_rec[i & 1] : nullptr;
     const cudaError_t e = launch_diffusion_batch(b->d_inst, b->count, b->items, i & 1, a, ns, b->margin, b->T,
-                                                 b->ctas, b->threads, s);
+                                                 b->ctas, b->threads, s, pin, pout);
     if (e != cudaSuccess) return FRACTAL_ECUDA;
   }
   return FRACTAL_OK;
@@ -166,6 +172,8 @@ int fractal_batch_destroy(fractal_batch_t b) {
   if (b->capture) cudaStreamDestroy(b->capture);
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_partials) cudaFree(b->d_partials);
+  for (int i = 0; i < 2; ++i)
+    if (b->d_rec[i]) cudaFree(b->d_rec[i]);
   delete b;
   return FRACTAL_OK;
 }
@@ -178,6 +186,23 @@ int fractal_batch_bind(fractal_batch_t b, float* const* dev_a, float* const* dev
   for (int i = 0; i < b->count; ++i) {
     b->h[i].a = dev_a[i];
     b->h[i].b = dev_b[i];
+  }
+  // block records of all instances, 3^(k_i - 3) of 112 bytes each, whatever
+  // the super-tile side (allocated once, before any launch or capture)
+  if (!b->d_rec[0]) {
+    int64_t recs = 0;
+    for (int k : b->ks) recs += pow3(k - 3);
+    const size_t bytes = (size_t)recs * (size_t)fused_record_bytes();
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&b->d_rec[i], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        for (int j = 0; j < 2; ++j) {
+          if (b->d_rec[j]) cudaFree(b->d_rec[j]);
+          b->d_rec[j] = nullptr;
+        }
+        return FRACTAL_ENOMEM;
+      }
+    }
   }
   b->bound = true;
   return rebuild(b);

@@ -53,6 +53,7 @@ struct FGeo {
   int log_rho;  // the plan's tile side (write-back of whole member tiles)
   int R;        // super-tile levels of the array: (k - 3) - L
   int lwR;      // 3^ceil(R/2): width of the level-R packed grid of super-tiles
+  int64_t rec0; // records before this array's (batches: earlier instances')
 };
 
 // Compact records between the launches of one call: the 27 members of a
@@ -70,7 +71,7 @@ __device__ __forceinline__ int64_t block_record(int GX, int GY, const FGeo& f) {
   const int ssx = GX >> f.L, ssy = GY >> f.L, lx = GX & mask, ly = GY & mask;
   const int64_t s = MODE == kLambda ? lambda_inverse(ssx, ssy, f.R, f.lwR) : bb_rank(ssx, ssy, f.R);
   const int t = MODE == kLambda ? lambda_inverse(lx, ly, f.L, f.lw) : bb_rank(lx, ly, f.L);
-  return s * f.nb + t;
+  return f.rec0 + s * f.nb + t;
 }
 
 // Member m of a record -> float m%4 of float4 m/4 (compile-time m).
@@ -373,6 +374,7 @@ __device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho, int 
   f.nbox = 6 * f.W * f.W;
   f.log_rho = log_rho;
   f.R = R;
+  f.rec0 = 0;
   int lwR = 1;
   for (int i = 0; i < (R + 1) / 2; ++i) lwR *= 3;
   f.lwR = lwR;
@@ -435,16 +437,18 @@ __device__ __forceinline__ int batch_instance(const BatchInst* __restrict__ inst
 
 __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
                                                               int64_t items, int which, float a, int nsteps, int M,
-                                                              int T) {
+                                                              int T, const float* __restrict__ pin,
+                                                              float* __restrict__ pout) {
   extern __shared__ __align__(16) float fsm[];
   for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
     const BatchInst I = inst[batch_instance(inst, count, w)];
     const int64_t om = w - I.first;
     int sx, sy;
     warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
-    const FGeo f = make_fgeo(I.n, T, M, 3, I.R);
-    fused_supertile<kLambda>(which ? I.b : I.a, which ? I.a : I.b, a, nsteps, f, sx << f.L, sy << f.L, nullptr, fsm, false,
-                              nullptr, nullptr, 0);
+    FGeo f = make_fgeo(I.n, T, M, 3, I.R);
+    f.rec0 = I.first * f.nb;  // item w's records start at w * nb
+    fused_supertile<kLambda>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps,
+                              f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb);
   }
 }
 
@@ -557,13 +561,14 @@ int fused_batch_smem_bytes(int threads) { return 6 * fused_slots(threads) * 4; }
 const void* fused_batch_kernel() { return (const void*)diffusion_batch_kernel; }
 
 cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
-                                   int margin, int T, int ctas, int threads, cudaStream_t s) {
+                                   int margin, int T, int ctas, int threads, cudaStream_t s, const float* pin,
+                                   float* pout) {
   if (nsteps < 1 || nsteps > margin || ctas < 1) return cudaErrorInvalidValue;
   Geo g{};
   g.T = T;
   if (fused_threads(g, 0, margin) != threads) return cudaErrorInvalidValue;
   diffusion_batch_kernel<<<ctas, threads, fused_batch_smem_bytes(threads), s>>>(inst, count, items, which, a, nsteps,
-                                                                               margin, T);
+                                                                               margin, T, pin, pout);
   return cudaGetLastError();
 }
 

@@ -105,8 +105,11 @@ struct BatchInst {
 // Persistent fused diffusion over `items` super-tiles of side T of the
 // instances (which = 0: a -> b, 1: b -> a); threads = fused_threads for T
 // and margin.  Per-instance member sums through `partials` (items doubles).
+// pin / pout (when not null): the block records of all instances (item w's
+// at w * 3^log2(T/8)) in place of the instances' buffers.
 cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
-                                   int margin, int T, int ctas, int threads, cudaStream_t s);
+                                   int margin, int T, int ctas, int threads, cudaStream_t s,
+                                   const float* pin = nullptr, float* pout = nullptr);
 cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items, int which, int T, int ctas,
                                 double* partials, double* out, cudaStream_t s);
 int fused_batch_smem_bytes(int threads);
