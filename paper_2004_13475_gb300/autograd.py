@@ -80,15 +80,18 @@ class GasketDiffusion(torch.autograd.Function):
         p = (grad_out.detach().to(dt) * mask).contiguous()
         q = torch.zeros_like(p)
         gk = torch.zeros(kappa.shape, dtype=torch.float64, device=kappa.device)
+        # the recomputed states of a segment, one pool for all segments: a
+        # step writes every member tile of its output and the kernels read
+        # member cells only, so the pool is neither cleared nor reallocated
+        pool = [torch.empty_like(p) for _ in range(min(every, steps) - 1)]
         for seg in range(len(ckpts) - 1, -1, -1):
             t0 = seg * every
             ns = min(every, steps - t0)
             states = [ckpts[seg]]
-            for _ in range(ns - 1):
+            for i in range(ns - 1):
                 # one step reads the first buffer and writes the second
-                nxt = torch.zeros_like(p)
-                step(plan, states[-1], nxt, kappa, a, 1)
-                states.append(nxt)
+                step(plan, states[-1], pool[i], kappa, a, 1)
+                states.append(pool[i])
             for i in range(ns - 1, -1, -1):
                 reverse(plan, states[i], p, q, kappa, gk, a)
                 p, q = q, p
