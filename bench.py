@@ -886,8 +886,9 @@ ADJ_EVERY = 20
 def adjoint(fr, torch, stream, seed):
     """k = 13, kappa ~ U[0.5, 1.5), 200 steps, loss sum((u_T - target)^2),
     gradients w.r.t. u0 and kappa through the checkpointed autograd function
-    (a state every 20 steps), float64 and float32 state.  A timed pass is one
-    forward and one backward (the backward recomputes each segment)."""
+    (a state every 20 steps), with the state in double-float (the default),
+    float64 and float32.  A timed pass is one forward and one backward (the
+    backward recomputes each segment)."""
     import synth
     from paper_2004_13475_gb300.autograd import diffusion_kappa
     n = 1 << ADJ_K
@@ -906,7 +907,7 @@ def adjoint(fr, torch, stream, seed):
     out = {"workload": (f"gasket k={ADJ_K} ({n}x{n}), kappa ~ U[0.5,1.5), {ADJ_STEPS} steps a={COEF}, "
                         f"loss sum((u_T - target)^2), gradients w.r.t. u0 and kappa, checkpoint every {ADJ_EVERY}")}
     members = 3 ** ADJ_K
-    for state in ("f64", "f32"):
+    for state in ("df", "f64", "f32"):
         def one():
             u = u0.clone().requires_grad_(True)
             k = kap.clone().requires_grad_(True)
@@ -924,7 +925,7 @@ def adjoint(fr, torch, stream, seed):
         t1.record(stream)
         torch.cuda.synchronize()
         t = t0.elapsed_time(t1) / 1e3 / reps
-        elem = 8 if state == "f64" else 4
+        elem = 4 if state == "f32" else 8
         out[state] = {
             "ms_forward_backward": t * 1e3,
             # forward, recomputation and reverse: three passes over the steps

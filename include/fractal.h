@@ -407,6 +407,24 @@ int fractal_adjoint_diffusion_step_f64(fractal_plan_t plan, const double* dev_u,
                                        double* dev_p_out, const float* dev_kappa, double* dev_gkappa, double a,
                                        void* stream);
 
+/*
+ * fractal_step_diffusion_kappa_df / fractal_adjoint_diffusion_step_df -- the
+ * same two operations with the state, p and dJ/dkappa in double-float: every
+ * value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2, about
+ * 48 significant bits), stored as consecutive (hi, lo) pairs, so each of
+ * dev_a, dev_b, dev_u, dev_p_in, dev_p_out and dev_gkappa is an array of 2*n*n
+ * floats (dev_kappa stays n*n floats).  Double-float arithmetic (Knuth's
+ * TwoSum, Dekker's product with a fused multiply-add) runs on the FP32 pipes,
+ * where this GPU has many times its FP64 rate; it keeps the gradients of a
+ * 200-step run within 1e-4 of an FP64 reference like the double state does.
+ * a is rounded to the nearest double-float.  Errors as above.
+ */
+int fractal_step_diffusion_kappa_df(fractal_plan_t plan, float* dev_a, float* dev_b, const float* dev_kappa,
+                                    double a, int steps, void* stream);
+int fractal_adjoint_diffusion_step_df(fractal_plan_t plan, const float* dev_u, const float* dev_p_in,
+                                      float* dev_p_out, const float* dev_kappa, float* dev_gkappa, double a,
+                                      void* stream);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.
  *

@@ -46,6 +46,7 @@ EXPORTS = (
     "fractal_step_diffusion_kappa_f64", "fractal_adjoint_diffusion_step_f64",
     "fractal_step_ca_count", "fractal_step_diffusion_sum", "fractal_map_blocks_method",
     "fractal_pack", "fractal_unpack",
+    "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -141,6 +142,8 @@ def _load() -> ctypes.CDLL:
         "fractal_step_ca_count": (I, [P, VP, VP, I, VP, VP]),
         "fractal_map_blocks_method": (I, [P, VP, I, VP]),
         "fractal_pack": (I, [P, VP, I, VP, VP]),
+        "fractal_step_diffusion_kappa_df": (I, [P, VP, VP, VP, D, I, VP]),
+        "fractal_adjoint_diffusion_step_df": (I, [P, VP, VP, VP, VP, VP, D, VP]),
         "fractal_unpack": (I, [P, VP, I, VP, VP]),
         "fractal_step_diffusion_sum": (I, [P, VP, VP, F, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
@@ -369,6 +372,21 @@ def fractal_adjoint_diffusion_step_f64(plan: Plan, u, p_in, p_out, kappa, gkappa
     _check(_load().fractal_adjoint_diffusion_step_f64(plan.handle, _ptr(u), _ptr(p_in), _ptr(p_out), _ptr(kappa),
                                                       _ptr(gkappa), float(coef), _stream(stream)),
            "fractal_adjoint_diffusion_step_f64")
+
+
+def fractal_step_diffusion_kappa_df(plan: Plan, a, b, kappa, coef: float, steps: int, stream=None):
+    """The same with a double-float state: a, b float32 tensors of 2 n^2
+    elements, (hi, lo) per cell (value hi + lo); kappa float32."""
+    _check(_load().fractal_step_diffusion_kappa_df(plan.handle, _ptr(a), _ptr(b), _ptr(kappa), float(coef),
+                                                   int(steps), _stream(stream)), "fractal_step_diffusion_kappa_df")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_adjoint_diffusion_step_df(plan: Plan, u, p_in, p_out, kappa, gkappa, coef: float, stream=None) -> None:
+    """The reverse step with double-float u, p and gkappa ((hi, lo) pairs)."""
+    _check(_load().fractal_adjoint_diffusion_step_df(plan.handle, _ptr(u), _ptr(p_in), _ptr(p_out), _ptr(kappa),
+                                                     _ptr(gkappa), float(coef), _stream(stream)),
+           "fractal_adjoint_diffusion_step_df")
 
 
 class Batch:

@@ -8,19 +8,49 @@ accumulates dJ/dkappa (in float64).  Memory: ceil(steps / every) + every
 states instead of steps + 1.  Every step runs in the library's kernels; this
 module only orders the calls and owns buffers.
 
-``state="f64"`` (default) keeps the trajectory and the adjoint state in
-float64 on the device: an FP32 trajectory rounds the state every step, and
-over 200 steps those roundings alone move the gradients by a few 1e-4 of
-their scale, beyond the 1e-4 agreement with an FP64 adjoint.  ``state="f32"``
-runs the float32 kernels (half the memory traffic).  Inputs and outputs keep
-the callers' dtypes.
+An FP32 trajectory rounds the state every step, and over 200 steps those
+roundings alone move the gradients by a few 1e-4 of their scale, beyond the
+1e-4 agreement with an FP64 adjoint, so the default state is wider:
+``state="df"`` (default) keeps the trajectory, the adjoint state and dJ/dkappa
+in double-float, (hi, lo) float pairs with about 48 significant bits,
+computed on the FP32 pipes; ``state="f64"`` keeps them in float64 (the same
+agreement, on this GPU's much slower FP64 units); ``state="f32"`` runs the
+float32 kernels.  Inputs and outputs keep the callers' dtypes.
 """
 from __future__ import annotations
 
 import torch
 
-from . import (FRACTAL_F32, FRACTAL_LAMBDA, fractal_adjoint_diffusion_step, fractal_adjoint_diffusion_step_f64,
-               fractal_map, fractal_map_write, fractal_step_diffusion_kappa, fractal_step_diffusion_kappa_f64)
+from . import (FRACTAL_F32, FRACTAL_LAMBDA, fractal_adjoint_diffusion_step, fractal_adjoint_diffusion_step_df,
+               fractal_adjoint_diffusion_step_f64, fractal_map, fractal_map_write, fractal_step_diffusion_kappa,
+               fractal_step_diffusion_kappa_df, fractal_step_diffusion_kappa_f64)
+
+# per state: (step, reverse step, storage dtype, elements per cell)
+_STATES = {
+    "df": (fractal_step_diffusion_kappa_df, fractal_adjoint_diffusion_step_df, torch.float32, 2),
+    "f64": (fractal_step_diffusion_kappa_f64, fractal_adjoint_diffusion_step_f64, torch.float64, 1),
+    "f32": (fractal_step_diffusion_kappa, fractal_adjoint_diffusion_step, torch.float32, 1),
+}
+
+
+def _to_state(x, state):
+    """A float field in the state's storage; double-float as (hi, lo) pairs
+    (lo = 0 for float32 input, the float64 remainder otherwise)."""
+    x = x.detach()
+    if state == "df":
+        hi = x.to(torch.float32)
+        lo = ((x.double() - hi.double()).to(torch.float32) if x.dtype == torch.float64
+              else torch.zeros_like(hi))
+        return torch.stack([hi, lo], dim=1).reshape(-1).contiguous()
+    return x.to(_STATES[state][2]).contiguous()
+
+
+def _from_state(y, state, dtype):
+    """The state's values as `dtype` (double-float: hi + lo in float64 first)."""
+    if state == "df":
+        hl = y.view(-1, 2)
+        return (hl[:, 0].double() + hl[:, 1].double()).to(dtype)
+    return y.to(dtype)
 
 
 def _member_mask(plan, like):
@@ -41,18 +71,17 @@ class GasketDiffusion(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, u0, kappa, k: int, a: float, steps: int, every: int = 20, mode: int = FRACTAL_LAMBDA,
-                state: str = "f64"):
+                state: str = "df"):
         if every < 1:
             raise ValueError("every >= 1")
-        if state not in ("f32", "f64"):
-            raise ValueError("state is 'f32' or 'f64'")
-        dt = torch.float64 if state == "f64" else torch.float32
-        step = fractal_step_diffusion_kappa_f64 if state == "f64" else fractal_step_diffusion_kappa
+        if state not in _STATES:
+            raise ValueError("state is 'df', 'f64' or 'f32'")
+        step = _STATES[state][0]
         plan = fractal_map(k, 8 if k >= 3 else 1 << k, mode)
         mask = _member_mask(plan, u0)
         kappa = kappa.detach().to(torch.float32).contiguous()
         # every buffer holds 0 at all non-member cells, so u_T does too
-        u = (u0.detach().to(dt) * mask).contiguous()
+        u = _to_state(u0.detach() * mask.to(u0.dtype), state)
         v = torch.zeros_like(u)
         ckpts = []
         t = 0
@@ -66,20 +95,19 @@ class GasketDiffusion(torch.autograd.Function):
         ctx.save_for_backward(kappa, mask, *ckpts)
         ctx.plan, ctx.a, ctx.steps, ctx.every, ctx.state = plan, a, steps, every, state
         ctx.dtypes = (u0.dtype, kappa.dtype)
-        return u.to(u0.dtype)
+        return _from_state(u, state, u0.dtype)
 
     @staticmethod
     def backward(ctx, grad_out):
         kappa, mask, *ckpts = ctx.saved_tensors
         plan, a, steps, every, state = ctx.plan, ctx.a, ctx.steps, ctx.every, ctx.state
-        f64 = state == "f64"
-        step = fractal_step_diffusion_kappa_f64 if f64 else fractal_step_diffusion_kappa
-        reverse = fractal_adjoint_diffusion_step_f64 if f64 else fractal_adjoint_diffusion_step
-        dt = torch.float64 if f64 else torch.float32
+        step, reverse = _STATES[state][0], _STATES[state][1]
         # u_T is 0 at non-members whatever u0 is: only member cells carry gradient
-        p = (grad_out.detach().to(dt) * mask).contiguous()
+        p = _to_state(grad_out.detach() * mask.to(grad_out.dtype), state)
         q = torch.zeros_like(p)
-        gk = torch.zeros(kappa.shape, dtype=torch.float64, device=kappa.device)
+        # dJ/dkappa: double-float pairs for the "df" state, else float64
+        gk = (torch.zeros(2 * kappa.numel(), dtype=torch.float32, device=kappa.device) if state == "df"
+              else torch.zeros(kappa.shape, dtype=torch.float64, device=kappa.device))
         # the recomputed states of a segment, one pool for all segments: a
         # step writes every member tile of its output and the kernels read
         # member cells only, so the pool is neither cleared nor reallocated
@@ -96,10 +124,11 @@ class GasketDiffusion(torch.autograd.Function):
                 reverse(plan, states[i], p, q, kappa, gk, a)
                 p, q = q, p
         du, dk = ctx.dtypes
-        return p.to(du), gk.to(dk), None, None, None, None, None, None
+        gk = _from_state(gk, "df", dk) if state == "df" else gk.to(dk)
+        return _from_state(p, state, du), gk, None, None, None, None, None, None
 
 
 def diffusion_kappa(u0, kappa, k: int, a: float, steps: int, every: int = 20, mode: int = FRACTAL_LAMBDA,
-                    state: str = "f64"):
+                    state: str = "df"):
     """Functional form of :class:`GasketDiffusion`."""
     return GasketDiffusion.apply(u0, kappa, k, a, steps, every, mode, state)

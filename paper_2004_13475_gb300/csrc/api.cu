@@ -489,8 +489,7 @@ int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, 
 template <typename T>
 int step_kappa(fractal_plan_t p, T* a, T* b, const float* kappa, T coef, int steps, void* stream) {
   if (check_plan(p) || !a || !b || !kappa || a == b || (const void*)kappa == (const void*)a ||
-      (const void*)kappa == (const void*)b || !aligned16(a) || !aligned16(b) || !aligned16(kappa) || steps < 0 ||
-      !std::isfinite((double)coef))
+      (const void*)kappa == (const void*)b || !aligned16(a) || !aligned16(b) || !aligned16(kappa) || steps < 0)
     return FRACTAL_EINVAL;
   Launch L;
   int levels = 0;
@@ -505,11 +504,10 @@ int step_kappa(fractal_plan_t p, T* a, T* b, const float* kappa, T coef, int ste
   return FRACTAL_OK;
 }
 
-template <typename T>
-int adjoint_step(fractal_plan_t p, const T* u, const T* p_in, T* p_out, const float* kappa, double* gkappa, T coef,
+template <typename T, typename G>
+int adjoint_step(fractal_plan_t p, const T* u, const T* p_in, T* p_out, const float* kappa, G* gkappa, T coef,
                  void* stream) {
-  if (check_plan(p) || !u || !p_in || !p_out || !kappa || !gkappa || !std::isfinite((double)coef))
-    return FRACTAL_EINVAL;
+  if (check_plan(p) || !u || !p_in || !p_out || !kappa || !gkappa) return FRACTAL_EINVAL;
   const void* all[5] = {u, p_in, p_out, kappa, gkappa};
   for (int i = 0; i < 5; ++i) {
     if (!aligned16(all[i])) return FRACTAL_EINVAL;
@@ -851,22 +849,41 @@ int fractal_step_diffusion_sum(fractal_plan_t p, float* a, float* b, float coef,
 
 int fractal_step_diffusion_kappa(fractal_plan_t p, float* a, float* b, const float* kappa, float coef, int steps,
                                  void* stream) {
+  if (!std::isfinite(coef)) return FRACTAL_EINVAL;
   return step_kappa(p, a, b, kappa, coef, steps, stream);
 }
 
 int fractal_step_diffusion_kappa_f64(fractal_plan_t p, double* a, double* b, const float* kappa, double coef,
                                      int steps, void* stream) {
+  if (!std::isfinite(coef)) return FRACTAL_EINVAL;
   return step_kappa(p, a, b, kappa, coef, steps, stream);
+}
+
+int fractal_step_diffusion_kappa_df(fractal_plan_t p, float* a, float* b, const float* kappa, double coef,
+                                    int steps, void* stream) {
+  if (!std::isfinite(coef)) return FRACTAL_EINVAL;
+  return step_kappa(p, reinterpret_cast<dfloat*>(a), reinterpret_cast<dfloat*>(b), kappa, dfloat_from_double(coef),
+                    steps, stream);
 }
 
 int fractal_adjoint_diffusion_step(fractal_plan_t p, const float* u, const float* p_in, float* p_out,
                                    const float* kappa, double* gkappa, float coef, void* stream) {
+  if (!std::isfinite(coef)) return FRACTAL_EINVAL;
   return adjoint_step(p, u, p_in, p_out, kappa, gkappa, coef, stream);
 }
 
 int fractal_adjoint_diffusion_step_f64(fractal_plan_t p, const double* u, const double* p_in, double* p_out,
                                        const float* kappa, double* gkappa, double coef, void* stream) {
+  if (!std::isfinite(coef)) return FRACTAL_EINVAL;
   return adjoint_step(p, u, p_in, p_out, kappa, gkappa, coef, stream);
+}
+
+int fractal_adjoint_diffusion_step_df(fractal_plan_t p, const float* u, const float* p_in, float* p_out,
+                                      const float* kappa, float* gkappa, double coef, void* stream) {
+  if (!std::isfinite(coef)) return FRACTAL_EINVAL;
+  return adjoint_step(p, reinterpret_cast<const dfloat*>(u), reinterpret_cast<const dfloat*>(p_in),
+                      reinterpret_cast<dfloat*>(p_out), kappa, reinterpret_cast<dfloat*>(gkappa),
+                      dfloat_from_double(coef), stream);
 }
 
 int fractal_reduce_async(fractal_plan_t p, const void* dev_buf, int dtype, double* dev_out, void* stream) {

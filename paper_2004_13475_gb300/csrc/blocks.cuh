@@ -7,6 +7,7 @@
 // floats is one 32-byte sector.
 #pragma once
 
+#include "dfloat.cuh"
 #include "gasket.cuh"
 
 namespace fractal {
@@ -43,6 +44,9 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
   reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
+
+__device__ __forceinline__ float ldg1(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldg1(const double* p) { return __ldg(p); }
 
 // The block's member values (0 at non-members) from a row-major n x n array.
 template <typename T>
@@ -82,10 +86,10 @@ struct Ports {
 template <typename T>
 __device__ __forceinline__ Ports<T> load_ports(const T* __restrict__ base, int n, bool hu, bool hl, bool hr, bool hd) {
   Ports<T> q;
-  q.up = hu ? __ldg(base - n) : T(0);
-  q.lf = hl ? __ldg(base - 1) : T(0);
-  q.rt = hr ? __ldg(base + kB) : T(0);
-  q.dn = hd ? __ldg(base + (size_t)kB * n) : T(0);
+  q.up = hu ? ldg1(base - n) : T(0);
+  q.lf = hl ? ldg1(base - 1) : T(0);
+  q.rt = hr ? ldg1(base + kB) : T(0);
+  q.dn = hd ? ldg1(base + (size_t)kB * n) : T(0);
   return q;
 }
 

@@ -8,12 +8,15 @@
 //   dJ/dkappa_c += (a / 2) sum_{nb} (u_t,nb - u_t,c) (p_{t+1},c - p_{t+1},nb)
 // (g_{c,nb} enters row c and row nb of A u_t).
 //
-// State precision.  The states u and p are float or double (template T);
-// kappa is float; dJ/dkappa is accumulated in double.  An FP32 trajectory
+// State precision.  The states u and p are float, double or double-float
+// (template T); kappa is float; dJ/dkappa is accumulated in double (float and
+// double states) or double-float (double-float state).  An FP32 trajectory
 // rounds u every step, and those roundings reach the gradients through
 // differences of neighbouring values: over 200 steps they alone move the
-// gradients by a few 1e-4 of their scale from the exact ones.  The double
-// state keeps the adjoint within 1e-4 of an FP64 reference.
+// gradients by a few 1e-4 of their scale from the exact ones.  A double or a
+// double-float state keeps the adjoint within 1e-4 of an FP64 reference; the
+// double-float one runs on the FP32 pipes (FP64 issues at a small fraction of
+// the FP32 rate on this GPU) and converts nothing per step.
 //
 // Launch: the lambda map at the level of 8 x 8 blocks.  A CTA takes a member
 // super-tile of 2^L x 2^L blocks (Theorem 1 for the CTA, lambda again for the
@@ -64,10 +67,20 @@ __global__ void __launch_bounds__(128) diffusion_kappa_kernel(const T* __restric
   store_block(out + b.base, n, w);
 }
 
-template <int MODE, typename T>
+// Accumulator of dJ/dkappa for state type T.
+template <typename T>
+struct GradOf {
+  using type = double;
+};
+template <>
+struct GradOf<dfloat> {
+  using type = dfloat;
+};
+
+template <int MODE, typename T, typename G = typename GradOf<T>::type>
 __global__ void __launch_bounds__(128) diffusion_adjoint_kernel(const T* __restrict__ ut, const T* __restrict__ pin,
                                                                 T* __restrict__ pout, const float* __restrict__ kappa,
-                                                                double* __restrict__ gkappa, T a, Geo g, int L) {
+                                                                G* __restrict__ gkappa, T a, Geo g, int L) {
   BlockPos b;
   if (!block_pos<MODE>(g, L, b) || !b.active) return;
   const int n = g.n;
@@ -80,11 +93,11 @@ __global__ void __launch_bounds__(128) diffusion_adjoint_kernel(const T* __restr
   const Ports<float> pk = load_ports(kappa + b.base, n, b.hu, b.hl, b.hr, b.hd);
   const Ports<T> pp = load_ports(pin + b.base, n, b.hu, b.hl, b.hr, b.hd);
   const T ha = T(0.5) * a;
-  const double hd = 0.5 * (double)a;
+  const G hd = G(0.5) * G(a);
 #pragma unroll
   for (int j = 0; j < kB; ++j) {
-    double* grow = gkappa + b.base + (size_t)j * n;
-    double gr[kB];
+    G* grow = gkappa + b.base + (size_t)j * n;
+    G gr[kB];
     ld4(grow, gr);
     ld4(grow + 4, gr + 4);
 #pragma unroll
@@ -92,17 +105,17 @@ __global__ void __launch_bounds__(128) diffusion_adjoint_kernel(const T* __restr
       const int c = j * kB + i;
       if (!amem(i, j)) {
         w[c] = T(0);
-        gr[i] = 0.0;
+        gr[i] = G(0);
         continue;
       }
       T sp = T(0);
-      double sg = 0.0;
+      G sg = G(0);
       for_neighbours(i, j, u, k, p, pu, pk, pp, b.hu, b.hl, b.hr, b.hd, [&](T un, float kn, T pn) {
-        sp = fmat(T(k[c]) + T(kn), pn - p[c], sp);                 // ((A p)_c - p_c) * 2 / a
-        sg = fma((double)(un - u[c]), (double)(p[c] - pn), sg);    // dJ/dkappa_c of this step * 2 / a
+        sp = fmat(T(k[c]) + T(kn), pn - p[c], sp);          // ((A p)_c - p_c) * 2 / a
+        sg = fmat(G(un - u[c]), G(p[c] - pn), sg);          // dJ/dkappa_c of this step * 2 / a
       });
       w[c] = fmat(ha, sp, p[c]);
-      gr[i] = fma(hd, sg, gr[i]);
+      gr[i] = fmat(hd, sg, gr[i]);
     }
     st4(grow, gr);
     st4(grow + 4, gr + 4);
@@ -136,9 +149,9 @@ cudaError_t launch_diffusion_kappa(int mode, const Launch& L, int levels, const 
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename G>
 cudaError_t launch_diffusion_adjoint(int mode, const Launch& L, int levels, const T* ut, const T* pin, T* pout,
-                                     const float* kappa, double* gkappa, T a, cudaStream_t s) {
+                                     const float* kappa, G* gkappa, T a, cudaStream_t s) {
   if (mode == kLambda)
     diffusion_adjoint_kernel<kLambda, T><<<L.grid, L.threads, 0, s>>>(ut, pin, pout, kappa, gkappa, a, L.geo, levels);
   else
@@ -150,9 +163,13 @@ template cudaError_t launch_diffusion_kappa<float>(int, const Launch&, int, cons
                                                    cudaStream_t);
 template cudaError_t launch_diffusion_kappa<double>(int, const Launch&, int, const double*, double*, const float*,
                                                     double, cudaStream_t);
-template cudaError_t launch_diffusion_adjoint<float>(int, const Launch&, int, const float*, const float*, float*,
-                                                     const float*, double*, float, cudaStream_t);
-template cudaError_t launch_diffusion_adjoint<double>(int, const Launch&, int, const double*, const double*, double*,
-                                                      const float*, double*, double, cudaStream_t);
+template cudaError_t launch_diffusion_kappa<dfloat>(int, const Launch&, int, const dfloat*, dfloat*, const float*,
+                                                    dfloat, cudaStream_t);
+template cudaError_t launch_diffusion_adjoint<float, double>(int, const Launch&, int, const float*, const float*,
+                                                             float*, const float*, double*, float, cudaStream_t);
+template cudaError_t launch_diffusion_adjoint<double, double>(int, const Launch&, int, const double*, const double*,
+                                                              double*, const float*, double*, double, cudaStream_t);
+template cudaError_t launch_diffusion_adjoint<dfloat, dfloat>(int, const Launch&, int, const dfloat*, const dfloat*,
+                                                              dfloat*, const float*, dfloat*, dfloat, cudaStream_t);
 
 }  // namespace fractal

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
 #include "gasket.cuh"
 
 namespace fractal {
@@ -82,14 +83,15 @@ bool blocks_geometry(int k, int mode, Launch& L, int& levels);
 cudaError_t launch_reduce_blocks(int mode, const Launch& L, int levels, const float* in, double* partials,
                                  double* dev_out, cudaStream_t s);
 
-// T = float or double (the state precision).
+// T = float, double or dfloat (the state precision); G = the dJ/dkappa
+// accumulator: double for float and double states, dfloat for dfloat.
 bool kappa_geometry(int k, int mode, Launch& L, int& levels);
 template <typename T>
 cudaError_t launch_diffusion_kappa(int mode, const Launch& L, int levels, const T* in, T* out, const float* kappa,
                                    T a, cudaStream_t s);
-template <typename T>
+template <typename T, typename G>
 cudaError_t launch_diffusion_adjoint(int mode, const Launch& L, int levels, const T* ut, const T* pin, T* pout,
-                                     const float* kappa, double* gkappa, T a, cudaStream_t s);
+                                     const float* kappa, G* gkappa, T a, cudaStream_t s);
 
 // One instance of a batch (device table entry).
 struct BatchInst {

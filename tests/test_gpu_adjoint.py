@@ -74,9 +74,16 @@ def test_kappa_steps_match_oracle(fr, k, mode):
         b64 = torch.zeros_like(a64)
         got64 = fr.fractal_step_diffusion_kappa_f64(plan, a64, b64, dev(kappa), A, steps).cpu().numpy().reshape(n, n)
         assert rel_err(got64, want, dom.mask)[0] <= 1e-13
+        # the double-float kernel: (hi, lo) pairs, about 48 significant bits
+        adf = torch.stack([dev(u0), torch.zeros(n * n, device="cuda")], dim=1).reshape(-1).contiguous()
+        bdf = torch.zeros_like(adf)
+        hl = fr.fractal_step_diffusion_kappa_df(plan, adf, bdf, dev(kappa), A, steps).view(-1, 2).cpu().numpy()
+        gotdf = (hl[:, 0].astype(np.float64) + hl[:, 1]).reshape(n, n)
+        assert rel_err(gotdf, want, dom.mask)[0] <= 1e-12
+        assert np.all(np.abs(hl[:, 1]) <= np.abs(hl[:, 0]) * 2.0 ** -23 + 1e-45)   # normalised pairs
 
 
-def grads_gpu(fr, k, u0, kappa, target, steps, every, mode=0, state="f64"):
+def grads_gpu(fr, k, u0, kappa, target, steps, every, mode=0, state="df"):
     from paper_2004_13475_gb300.autograd import diffusion_kappa
     u = dev(u0).requires_grad_(True)
     kp = dev(kappa).requires_grad_(True)
@@ -88,13 +95,14 @@ def grads_gpu(fr, k, u0, kappa, target, steps, every, mode=0, state="f64"):
             uT.detach().cpu().numpy().reshape(n, n))
 
 
+@pytest.mark.parametrize("state", ["df", "f64"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("k,steps,every", [(4, 9, 1), (6, 25, 7), (8, 45, 20), (9, 60, 20)])
-def test_gradients_match_oracle_adjoint(fr, k, steps, every, mode):
+def test_gradients_match_oracle_adjoint(fr, k, steps, every, mode, state):
     n = 1 << k
     u0, kappa, target = fields(k, 30 + k)
     dom = oracle.Domain.build(n)
-    J, gu, gk, uT = grads_gpu(fr, k, u0, kappa, target, steps, every, mode)
+    J, gu, gk, uT = grads_gpu(fr, k, u0, kappa, target, steps, every, mode, state)
     Jw, wu, wk = oracle.diffusion_loss_gradients(dom, dom.take(u0).astype(np.float64),
                                                  dom.take(kappa).astype(np.float64),
                                                  dom.take(target).astype(np.float64), steps, A)
@@ -180,3 +188,9 @@ def test_adjoint_validation(fr):
     with pytest.raises(fr.FractalError):
         fr.fractal_step_diffusion_kappa(fr.fractal_map(2, 4), x[0], x[1], x[2], A, 1)   # k < 3
     fr.fractal_adjoint_diffusion_step(plan, x[0], x[1], x[2], x[3], x[4], A)
+    y = [torch.zeros(2 * 64 * 64, device="cuda") for _ in range(5)]
+    with pytest.raises(fr.FractalError):
+        fr.fractal_adjoint_diffusion_step_df(plan, y[0], y[1], y[1], x[3], y[4], A)   # p_in == p_out
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_diffusion_kappa_df(plan, y[0], y[0], x[3], A, 1)              # a == b
+    fr.fractal_adjoint_diffusion_step_df(plan, y[0], y[1], y[2], x[3], y[4], A)
