@@ -165,8 +165,13 @@ int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, vo
  * records of 128 bytes (uint8: the 32 words of a member 32 x 32 word tile),
  * freed with the plan: only the first launch reads dev_a and only the last
  * writes the result buffer; the other caller buffer is then not written.
+ * For float32 the call also writes, once, the setup of every thread of the
+ * fused launch (its block, port owners and neighbours: 16 bytes a thread,
+ * 37 MB at k = 16, rho = 8), which every fused launch then reads instead of
+ * computing it; it waits for the device first (no call of this plan may be
+ * in flight) and for that launch after.
  * Errors: FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan),
- * FRACTAL_ENOMEM.
+ * FRACTAL_ENOMEM, FRACTAL_ECUDA.
  */
 int fractal_plan_set_steps_per_launch(fractal_plan_t plan, int dtype, int spl);
 

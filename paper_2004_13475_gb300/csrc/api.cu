@@ -81,6 +81,9 @@ struct fractal_plan_s {
   size_t pack_cap = 0;          // bytes per record buffer
   uint32_t* d_bits[2] = {nullptr, nullptr};  // uint8 fused: bit records between launches
   size_t bits_cap = 0;          // bytes per bit-record buffer
+  int4* d_desc = nullptr;       // float32 fused: per-thread setup of the current fused launch
+  size_t desc_cap = 0;          // bytes
+  bool desc_ok = false;         // d_desc matches fused[FRACTAL_F32] and its margin
   int* d_err = nullptr;         // device error word of the TMA kernels
   void* d_partials = nullptr;   // reduce scratch: one 8-byte partial per CTA
   size_t partials_cap = 0;      // elements
@@ -333,6 +336,34 @@ int ensure_records(fractal_plan_s* p, int dtype) {
   return ensure_pair(p->d_bits, p->bits_cap, (size_t)ca_records(p->k) * 128);
 }
 
+// Descriptors of the float32 fused launch (fused[FRACTAL_F32], margin of
+// spl[FRACTAL_F32]): written by one launch of the describe kernel on `s`
+// (then waited for when `sync`); every later fused launch reads its threads'
+// setup from them.  16 bytes per thread (37 MB at k = 16, rho = 8).
+int build_descriptors(fractal_plan_s* p, cudaStream_t s, bool sync) {
+  p->desc_ok = false;
+  // no launch of this plan may still read the descriptors being replaced
+  if (sync && cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError(), "describe");
+  const Launch& F = p->fused[FRACTAL_F32];
+  const size_t need = (size_t)fused_descriptors(F) * sizeof(int4);
+  if (need > p->desc_cap) {
+    if (p->d_desc) cudaFree(p->d_desc);
+    p->d_desc = nullptr;
+    p->desc_cap = 0;
+    if (cudaMalloc(&p->d_desc, need) != cudaSuccess) {
+      cudaGetLastError();
+      p->d_desc = nullptr;
+      return FRACTAL_ENOMEM;
+    }
+    p->desc_cap = need;
+  }
+  cudaError_t e = launch_fused_describe(p->mode, p->log_rho, fused_margin(p->spl[FRACTAL_F32]), F, p->d_desc, s);
+  if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "describe");
+  p->desc_ok = true;
+  return FRACTAL_OK;
+}
+
 int ensure_partials(fractal_plan_s* p) {
   size_t need = 1;
   {
@@ -451,7 +482,7 @@ int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, 
       float* pout = rec && !last ? p->d_pack[i & 1] : nullptr;
       cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[FRACTAL_F32],
                                              pin ? nullptr : buf[i & 1], pout ? nullptr : buf[(i + 1) & 1], coef,
-                                             sp.of(i), st, part, pin, pout);
+                                             sp.of(i), st, part, pin, pout, p->desc_ok ? p->d_desc : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
     }
     if (dev_sum) {
@@ -587,6 +618,7 @@ int fractal_plan_destroy(fractal_plan_t p) {
     if (p->d_pack[i]) cudaFree(p->d_pack[i]);
     if (p->d_bits[i]) cudaFree(p->d_bits[i]);
   }
+  if (p->d_desc) cudaFree(p->d_desc);
   if (p->d_result) cudaFree(p->d_result);
   if (p->h_result) cudaFreeHost(p->h_result);
   if (p->d_err) cudaFree(p->d_err);
@@ -657,6 +689,7 @@ static int set_levels(fractal_plan_t p, int dtype, int levels) {
 
 int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
   if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) || spl < 1 || spl > max_spl(dtype)) return FRACTAL_EINVAL;
+  if (dtype == FRACTAL_F32) p->desc_ok = false;
   if (spl == 1) {
     p->spl[dtype] = 1;
     p->fused_ok[dtype] = false;
@@ -667,9 +700,11 @@ int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
   p->spl[dtype] = spl;
   p->fused[dtype] = f;
   p->fused_ok[dtype] = true;
-  const int st = ensure_partials(p);  // the fused kernels' per-CTA sums
+  int st = ensure_partials(p);  // the fused kernels' per-CTA sums
   if (st != FRACTAL_OK) return st;
-  return ensure_records(p, dtype);
+  st = ensure_records(p, dtype);
+  if (st != FRACTAL_OK || dtype != FRACTAL_F32) return st;
+  return build_descriptors(p, nullptr, true);
 }
 
 int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
@@ -701,30 +736,33 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   int best1_m = old_m;
   int status = FRACTAL_OK;
   // One timed unit dev_in -> dev_scratch: a single step; `spl` fused steps;
-  // float32 fused: two launches of `spl` steps through the compact records,
-  // as a call of 2 spl steps runs them.  Returns the steps in `done`.
+  // with records, the launches of a call of 100 steps (2 spl when longer)
+  // as the step driver runs them -- the first from dev_in, the last into
+  // dev_scratch, records between -- so that the middle launches count too.
+  // Returns the steps in `done`.
   const bool records = ensure_records(p, dtype) == FRACTAL_OK;
   auto launch = [&](int spl, int& done) -> int {
     done = spl;
-    if (spl > 1 && dtype == FRACTAL_U8 && records) {  // as for float32 below
+    if (spl > 1 && records) {
+      const int S = spl <= 50 ? 100 : 2 * spl;
+      const FusedSplit sp(S, spl);
       const Launch& F = p->fused[dtype];
-      cudaError_t e = launch_ca_fused(p->mode, F, (const uint8_t*)dev_in, nullptr, spl, spl, st, nullptr, nullptr,
-                                      p->d_bits[0]);
-      if (e == cudaSuccess)
-        e = launch_ca_fused(p->mode, F, nullptr, (uint8_t*)dev_scratch, spl, spl, st, nullptr, p->d_bits[0],
-                            nullptr);
-      done = 2 * spl;
-      return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "autotune");
-    }
-    if (spl > 1 && dtype == FRACTAL_F32 && records) {
-      const Launch& F = p->fused[dtype];
-      const int M = fused_margin(spl);
-      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, M, F, (const float*)dev_in, nullptr, 0.2f, spl, st,
-                                             nullptr, nullptr, p->d_pack[0]);
-      if (e == cudaSuccess)
-        e = launch_diffusion_fused(p->mode, p->log_rho, M, F, nullptr, (float*)dev_scratch, 0.2f, spl, st, nullptr,
-                                   p->d_pack[0], nullptr);
-      done = 2 * spl;
+      const int4* desc = p->desc_ok ? p->d_desc : nullptr;
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < sp.L && e == cudaSuccess; ++i) {
+        const bool first = i == 0, last = i == sp.L - 1;
+        if (dtype == FRACTAL_U8) {
+          e = launch_ca_fused(p->mode, F, first ? (const uint8_t*)dev_in : nullptr,
+                              last ? (uint8_t*)dev_scratch : nullptr, sp.of(i), spl, st, nullptr,
+                              first ? nullptr : p->d_bits[(i - 1) & 1], last ? nullptr : p->d_bits[i & 1]);
+        } else {
+          e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), F,
+                                     first ? (const float*)dev_in : nullptr, last ? (float*)dev_scratch : nullptr,
+                                     0.2f, sp.of(i), st, nullptr, first ? nullptr : p->d_pack[(i - 1) & 1],
+                                     last ? nullptr : p->d_pack[i & 1], desc);
+        }
+      }
+      done = S;
       return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "autotune");
     }
     if (spl > 1) {
@@ -757,6 +795,7 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
         if (!make_fused(*p, dtype, spl, p->step[dtype], p->fused[dtype])) continue;
         p->spl[dtype] = spl;
         p->fused_ok[dtype] = true;
+        if (dtype == FRACTAL_F32) build_descriptors(p, st, false);  // on failure: the kernels' own setup
       } else {
         p->spl[dtype] = 1;
         p->fused_ok[dtype] = false;

@@ -171,24 +171,40 @@ __host__ __device__ inline int fused_slots(int threads) { return threads + 1; }
 // Returns this thread's share of the sum of the written members (its block's
 // rows in FP32, the rows in FP64; 0 for box blocks and idle threads, and 0
 // unless want_sum).
-template <int MODE>
-__device__ __forceinline__ double fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
-                                                  int nsteps, const FGeo& f, int OX, int OY, const int* tab,
-                                                  float* ports, bool want_sum, const float* __restrict__ pin,
-                                                  float* __restrict__ pout, int64_t srec) {
-  const int t = threadIdx.x, nthreads = blockDim.x;
-  const int slots = fused_slots(nthreads), zero = nthreads;
-  const int nblk = f.n / kB;
-  float* P0 = ports;  // [2][slots] each
-  float* PR = ports + 2 * slots;
-  float* PD = ports + 4 * slots;
+// Per-thread setup of a fused launch, the same for every launch of one fused
+// configuration (array, super-tile, margin, CTA size): the thread's block
+// (bx, by, relative to the super-tile origin; a member block of the
+// super-tile, a member block of a margin box, or none), the threads that own
+// its four ports' neighbours (`zero`: the zero slot), which of those
+// neighbours are members, and for a box block its record.
+struct FSetup {
+  int bx, by;
+  bool active;
+  int up, lf, rt, dn;
+  bool fu, fl, fr, fd;
+  int rec;  // a box block's record (records launches), -1 otherwise
+};
 
+template <int MODE>
+__device__ __forceinline__ FSetup fused_setup(const FGeo& f, int OX, int OY, const int* tab) {
+  const int t = threadIdx.x, nthreads = blockDim.x;
+  const int zero = nthreads;
+  const int nblk = f.n / kB;
   // the margin boxes' member blocks, compacted in box order: boxrank[b] is
   // the rank of box block b among them (-1 if not a member), boxlist the list
   __shared__ int boxrank[kMaxBox], boxlist[kMaxBoxMembers], wcnt[16];
   __shared__ short own[kMaxSide * kMaxSide];
+  FSetup s;
+  s.bx = s.by = 0;
+  s.active = false;
+  s.rec = -1;
+  if (t < f.nb) {
+    member_block<MODE>(t, f, tab, s.bx, s.by);
+    own[(s.by << f.L) + s.bx] = (short)t;  // every member slot is some thread's
+    s.active = true;
+  }
   int nbox_member = 0;
-  for (int b0 = 0; b0 < f.nbox; b0 += nthreads) {
+  for (int b0 = 0; b0 < f.nbox; b0 += nthreads) {  // its barriers also publish own[]
     const int b = b0 + t;
     bool m = false;
     if (b < f.nbox) {
@@ -212,34 +228,72 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
     nbox_member += total;
     __syncthreads();
   }
+  if (t >= f.nb && t - f.nb < nbox_member && t - f.nb < box_cap(f.W)) {
+    box_block(boxlist[t - f.nb], f, s.bx, s.by);
+    s.active = true;
+    s.rec = (int)block_record<MODE>(OX + s.bx, OY + s.by, f);
+  }
+  const int GX = OX + s.bx, GY = OY + s.by;
+  s.up = s.lf = s.rt = s.dn = zero;
+  s.fu = s.fl = s.fr = s.fd = false;
+  if (s.active) {
+    s.fu = block_member(GX, GY - 1, nblk);
+    s.fl = block_member(GX - 1, GY, nblk);
+    s.fr = block_member(GX + 1, GY, nblk);
+    s.fd = block_member(GX, GY + 1, nblk);
+    if (s.fu) s.up = fused_owner(s.bx, s.by - 1, f, own, boxrank, zero);
+    if (s.fl) s.lf = fused_owner(s.bx - 1, s.by, f, own, boxrank, zero);
+    if (s.fr) s.rt = fused_owner(s.bx + 1, s.by, f, own, boxrank, zero);
+    if (s.fd) s.dn = fused_owner(s.bx, s.by + 1, f, own, boxrank, zero);
+  }
+  return s;
+}
 
-  int bx = 0, by = 0;
-  bool active = false;
-  if (t < f.nb) {
-    member_block<MODE>(t, f, tab, bx, by);
-    own[(by << f.L) + bx] = (short)t;  // every member slot is some thread's
-    active = true;
-  } else if (t - f.nb < nbox_member && t - f.nb < box_cap(f.W)) {
-    box_block(boxlist[t - f.nb], f, bx, by);
-    active = true;
-  }
+// A setup in 16 bytes: x = flags (active, fu, fl, fr, fd) | bx << 8 | by << 16
+// (bytes, two's complement), y = up | lf << 16, z = rt | dn << 16, w = rec.
+__device__ __forceinline__ int4 pack_setup(const FSetup& s) {
+  const int flags = (s.active ? 1 : 0) | (s.fu ? 2 : 0) | (s.fl ? 4 : 0) | (s.fr ? 8 : 0) | (s.fd ? 16 : 0);
+  return make_int4(flags | ((s.bx & 0xff) << 8) | ((s.by & 0xff) << 16), s.up | (s.lf << 16), s.rt | (s.dn << 16),
+                   s.rec);
+}
+__device__ __forceinline__ FSetup unpack_setup(int4 q) {
+  FSetup s;
+  s.active = q.x & 1;
+  s.fu = q.x & 2;
+  s.fl = q.x & 4;
+  s.fr = q.x & 8;
+  s.fd = q.x & 16;
+  s.bx = (int)(signed char)((q.x >> 8) & 0xff);
+  s.by = (int)(signed char)((q.x >> 16) & 0xff);
+  s.up = q.y & 0xffff;
+  s.lf = (q.y >> 16) & 0xffff;
+  s.rt = q.z & 0xffff;
+  s.dn = (q.z >> 16) & 0xffff;
+  s.rec = q.w;
+  return s;
+}
+
+template <int MODE>
+__device__ __forceinline__ double fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
+                                                  int nsteps, const FGeo& f, int OX, int OY, const int* tab,
+                                                  float* ports, bool want_sum, const float* __restrict__ pin,
+                                                  float* __restrict__ pout, int64_t srec,
+                                                  const int4* __restrict__ desc) {
+  const int t = threadIdx.x, nthreads = blockDim.x;
+  const int slots = fused_slots(nthreads), zero = nthreads;
+  float* P0 = ports;  // [2][slots] each
+  float* PR = ports + 2 * slots;
+  float* PD = ports + 4 * slots;
+
+  // this thread's setup: from the launch's descriptors, else computed here
+  const FSetup su = desc ? unpack_setup(__ldg(desc + t)) : fused_setup<MODE>(f, OX, OY, tab);
+  const int bx = su.bx, by = su.by;
+  const bool active = su.active;
   const int GX = OX + bx, GY = OY + by;
-  // neighbour ports (the zero slot where no staged member block is) and the
-  // ports' degrees: 2, 1, 1 inside the block plus the member neighbour blocks
-  int up = zero, lf = zero, rt = zero, dn = zero;
-  float d0 = 2.f, dr = 1.f, dd = 1.f;
-  __syncthreads();  // own[] complete
-  if (active) {
-    const bool fu = block_member(GX, GY - 1, nblk), fl = block_member(GX - 1, GY, nblk);
-    const bool fr = block_member(GX + 1, GY, nblk), fd = block_member(GX, GY + 1, nblk);
-    d0 += (fu ? 1.f : 0.f) + (fl ? 1.f : 0.f);
-    dr += fr ? 1.f : 0.f;
-    dd += fd ? 1.f : 0.f;
-    if (fu) up = fused_owner(bx, by - 1, f, own, boxrank, zero);
-    if (fl) lf = fused_owner(bx - 1, by, f, own, boxrank, zero);
-    if (fr) rt = fused_owner(bx + 1, by, f, own, boxrank, zero);
-    if (fd) dn = fused_owner(bx, by + 1, f, own, boxrank, zero);
-  }
+  const int up = su.up, lf = su.lf, rt = su.rt, dn = su.dn;
+  // the ports' degrees: 2, 1, 1 inside the block plus the member neighbour blocks
+  const float d0 = 2.f + (su.fu ? 1.f : 0.f) + (su.fl ? 1.f : 0.f), dr = 1.f + (su.fr ? 1.f : 0.f),
+              dd = 1.f + (su.fd ? 1.f : 0.f);
 
   // stage: the block's 12 member chunks straight into registers
   float u[kB * kB];
@@ -247,7 +301,7 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
   const size_t base = (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
   if (active && pin) {
-    const int64_t rec = t < f.nb ? srec + t : block_record<MODE>(GX, GY, f);
+    const int64_t rec = t < f.nb ? srec + t : (int64_t)su.rec;
     const float4* p = reinterpret_cast<const float4*>(pin) + rec * kRecF4;
     float4 r[kRecF4];
 #pragma unroll
@@ -395,7 +449,8 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
                                                               float a, int nsteps, int M, int log_rho, Geo g,
                                                               double* __restrict__ partials,
                                                               const float* __restrict__ pin,
-                                                              float* __restrict__ pout) {
+                                                              float* __restrict__ pout,
+                                                              const int4* __restrict__ desc) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ double red[32];
   int sx, sy;
@@ -406,15 +461,16 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
   const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
   float* ports = fsm;
   int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(blockDim.x));
-  if (MODE == kBB) {
+  if (MODE == kBB && !desc) {
     bb_table(tab, f);
     __syncthreads();
   }
-  int64_t srec = 0;
-  if (pin || pout)
-    srec = (int64_t)(MODE == kLambda ? lambda_inverse(sx, sy, f.R, f.lwR) : bb_rank(sx, sy, f.R)) * f.nb;
+  // the super-tile's index among the member super-tiles (lambda: the CTA's
+  // packed index; BB: its rank): its records and its threads' descriptors
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
   const double mine = fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports,
-                                            partials != nullptr, pin, pout, srec);
+                                            partials != nullptr, pin, pout, st * f.nb,
+                                            desc ? desc + st * blockDim.x : nullptr);
   if (partials) {  // the sum of the result's members, per CTA (uniform branch)
     const double s = block_sum<double>(mine, red);
     if (threadIdx.x == 0) partials[cta_id()] = s;
@@ -448,7 +504,7 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
     FGeo f = make_fgeo(I.n, T, M, 3, I.R);
     f.rec0 = I.first * f.nb;  // item w's records start at w * nb
     fused_supertile<kLambda>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps,
-                              f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb);
+                              f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb, nullptr);
   }
 }
 
@@ -507,14 +563,33 @@ __global__ void batch_sums_kernel(const BatchInst* __restrict__ inst, int count,
   out[i] = s;
 }
 
+// One descriptor per thread of a fused launch (the launch's geometry, one
+// CTA per member super-tile): the setup every launch of the configuration
+// would compute, written once.
+template <int MODE>
+__global__ void __launch_bounds__(512) fused_describe_kernel(Geo g, int M, int log_rho, int4* __restrict__ desc) {
+  extern __shared__ __align__(16) float fsm[];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
+  int* tab = reinterpret_cast<int*>(fsm);
+  if (MODE == kBB) {
+    bb_table(tab, f);
+    __syncthreads();
+  }
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
+  const FSetup s = fused_setup<MODE>(f, sx << f.L, sy << f.L, tab);
+  desc[st * blockDim.x + threadIdx.x] = pack_setup(s);
+}
+
 template <int MODE>
 cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
-               double* partials, const float* pin, float* pout, cudaStream_t s) {
+               double* partials, const float* pin, float* pout, const int4* desc, cudaStream_t s) {
   // the smallest CTA class that holds the launch: more CTAs per SM
   auto run = [&](auto* k) -> cudaError_t {
     cudaError_t e = allow_smem((const void*)k, L.smem);
     if (e != cudaSuccess) return e;
-    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials, pin, pout);
+    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials, pin, pout, desc);
     return cudaGetLastError();
   };
   if (L.threads <= 288) return run(diffusion_fused_kernel<MODE, 288, 4>);
@@ -583,12 +658,28 @@ cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items,
 
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
                                    float a, int nsteps, cudaStream_t s, double* partials, const float* pin,
-                                   float* pout) {
+                                   float* pout, const int4* desc) {
   if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads ||
       (!in && !pin) || (!out && !pout))
     return cudaErrorInvalidValue;
-  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, s)
-                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, s);
+  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s)
+                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s);
+}
+
+int64_t fused_descriptors(const Launch& L) {
+  int64_t st = 1;  // member super-tiles: 3^R
+  for (int i = 0; i < L.geo.R; ++i) st *= 3;
+  return st * L.threads;
+}
+
+cudaError_t launch_fused_describe(int mode, int log_rho, int margin, const Launch& L, int4* desc, cudaStream_t s) {
+  if (fused_threads(L.geo, 0, margin) != L.threads) return cudaErrorInvalidValue;
+  const int smem = member_blocks(L.geo.T) * 4;  // BB slot table
+  if (mode == kLambda)
+    fused_describe_kernel<kLambda><<<L.grid, L.threads, smem, s>>>(L.geo, margin, log_rho, desc);
+  else
+    fused_describe_kernel<kBB><<<L.grid, L.threads, smem, s>>>(L.geo, margin, log_rho, desc);
+  return cudaGetLastError();
 }
 
 int64_t fused_records(int k) {

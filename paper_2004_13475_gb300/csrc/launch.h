@@ -42,9 +42,15 @@ int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 // members over the CTA's super-tile (finish with launch_final_sum).
 // in / out: embedded arrays; pin / pout (when not null): compact records in
 // place of in / out (the state between the launches of one call).
+// desc (when not null): the launch's per-thread descriptors from
+// launch_fused_describe for the same geometry and margin.
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
                                    float a, int nsteps, cudaStream_t s, double* partials = nullptr,
-                                   const float* pin = nullptr, float* pout = nullptr);
+                                   const float* pin = nullptr, float* pout = nullptr, const int4* desc = nullptr);
+// Descriptors of a fused launch (one per thread of each member super-tile's
+// CTA, 16 bytes) and the kernel that writes them.
+int64_t fused_descriptors(const Launch& L);
+cudaError_t launch_fused_describe(int mode, int log_rho, int margin, const Launch& L, int4* desc, cudaStream_t s);
 // Compact records of a level-k gasket (3^(k-3), one per member 8 x 8 block)
 // and the bytes of one.
 int64_t fused_records(int k);
