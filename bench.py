@@ -328,12 +328,12 @@ def main():
             mark(ev, "ca1")
         if "diffusion" not in parts:
             return None
-        cur, oth = u_a, u_b
-        for seg in range(DIFF_STEPS // REDUCE_EVERY):
-            mark(ev, "d0")
-            cur = fr.fractal_step_diffusion_sum(pd, cur, oth, COEF, REDUCE_EVERY, sums[seg:seg + 1], stream)
-            mark(ev, "d1")
-            oth = u_b if cur is u_a else u_a
+        # one call: the global sum after every REDUCE_EVERY steps (the state
+        # stays in the plan's records across the sums)
+        mark(ev, "d0")
+        cur = fr.fractal_step_diffusion_sums(pd, u_a, u_b, COEF, DIFF_STEPS, REDUCE_EVERY,
+                                             sums[0:DIFF_STEPS // REDUCE_EVERY], stream)
+        mark(ev, "d1")
         return cur
 
     def timed(mode, steps, warmup, ev=None):
@@ -362,8 +362,7 @@ def main():
     clocks = clk.summary()
     t_lam = max_over_ranks(dist, t_lam)
     diff_ms = sum(a.elapsed_time(b) for a, b in zip(ev["d0"], ev["d1"]))
-    seg = DIFF_STEPS // REDUCE_EVERY
-    per_step = sorted(ev["ca0"][i].elapsed_time(ev["d1"][seg * i + seg - 1]) for i in range(args.steps))
+    per_step = sorted(ev["ca0"][i].elapsed_time(ev["d1"][i]) for i in range(args.steps))
     ca_ms = sum(a.elapsed_time(b) for a, b in zip(ev["ca0"], ev["ca1"]))
     value = world * MEMBERS * (CA_STEPS + DIFF_STEPS) * args.steps / t_lam
 
@@ -379,10 +378,10 @@ def main():
     rho_d, rho_c = info_d["rho"], info_c["rho"]
     spl_d = info_d["steps_per_launch"][1]
     spl_c = info_c["steps_per_launch"][0]
-    kd = kernel_launches(spl_d, REDUCE_EVERY) * (DIFF_STEPS // REDUCE_EVERY)    # per bench step
+    kd = kernel_launches(spl_d, DIFF_STEPS, REDUCE_EVERY)    # per bench step
     kc = kernel_launches(spl_c, CA_STEPS)
     rf_d, alu_d = launch_roofline("diffusion", info_d, spl_d, diff_ms / 1e3 / (kd * args.steps), hbm, peak_kind,
-                                  REDUCE_EVERY)
+                                  DIFF_STEPS, REDUCE_EVERY)
     rf_c, _ = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind, CA_STEPS)
     # the kernel that takes most of the step, against the roof that bounds it:
     # the fused diffusion against the FP32 pipes (its HBM view beside it)
@@ -466,13 +465,18 @@ def main():
         dist.destroy_process_group()
 
 
-def kernel_launches(spl, steps):
-    """Launches the step driver makes for `steps` steps at `spl` per launch:
-    ceil(steps / spl), raised by one if its parity differs from steps'."""
+def kernel_launches(spl, steps, every=None):
+    """Launches the step driver makes for a call of `steps` steps at `spl`
+    per launch (with a sum every `every` steps): ceil(every / spl) per
+    segment, and two rather than one for a one-segment call of an even
+    number of steps (a launch cannot end where it started)."""
     if spl <= 1:
         return steps
-    L = -(-steps // spl)
-    return L + 1 if L % 2 != steps % 2 else L
+    every = every or steps
+    per = -(-every // spl)
+    if steps == every and per == 1 and steps % 2 == 0:
+        per = 2
+    return (steps // every) * per
 
 
 def staging(info, d):
@@ -584,10 +588,10 @@ def diffusion_flops_per_step(k):
     return 5 * 3 ** k - 4
 
 
-def fused_launch_kinds(call_steps, spl):
+def fused_launch_kinds(call_steps, spl, every=None):
     """Source and target of each launch of a fused call: E = the embedded
     array, R = the compact records kept between the launches of one call."""
-    n = kernel_launches(spl, call_steps)
+    n = kernel_launches(spl, call_steps, every)
     return ["EE"] if n <= 1 else ["ER"] + ["RR"] * (n - 2) + ["RE"]
 
 
@@ -606,7 +610,7 @@ def fused_launch_bytes(wl, kind, k, box):
     return read + units * (emb if kind[1] == "E" else rec)
 
 
-def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps):
+def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps, every=None):
     """HBM roofline of the mean launch of the workload's step kernel in a call
     of `call_steps` steps: algorithmic bytes over the launch's measured mean
     duration.  For the fused diffusion also its FP32 roofline (returned
@@ -614,7 +618,7 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps):
     rho = info["rho"]
     d = 0 if wl == "ca" else 1
     alu = None
-    kinds = fused_launch_kinds(call_steps, spl) if spl > 1 else []
+    kinds = fused_launch_kinds(call_steps, spl, every) if spl > 1 else []
     if spl > 1:
         T = rho << info["cta_levels"][d]
         if wl == "diffusion":

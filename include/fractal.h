@@ -271,6 +271,23 @@ int fractal_step_diffusion_sum(fractal_plan_t plan, float* dev_a, float* dev_b, 
                                void* stream);
 
 /*
+ * fractal_step_diffusion_sums -- `steps` steps as fractal_step_diffusion (the
+ * result in dev_a for even steps, dev_b for odd) with the global sum of the
+ * state after every `every` steps: dev_sums[j] (device doubles, steps / every
+ * of them) receives the member sum after (j + 1) * every steps, as
+ * fractal_step_diffusion_sum computes it.  steps must be a multiple of every.
+ * With temporal fusion the whole call is one sequence of fused launches: the
+ * state stays in the plan's records across the sums (the launch that ends a
+ * segment takes its sum), and only the last launch writes the result buffer;
+ * the intermediate states are not written to dev_a / dev_b.  steps == 0
+ * writes nothing.  Asynchronous.  Errors: as fractal_step_diffusion,
+ * FRACTAL_EINVAL for a NULL dev_sums, every < 1 or steps not a multiple of
+ * every.
+ */
+int fractal_step_diffusion_sums(fractal_plan_t plan, float* dev_a, float* dev_b, float a, int steps, int every,
+                                double* dev_sums, void* stream);
+
+/*
  * fractal_reduce -- the reduction test of Sec. 6.2 (RD): the sum over all
  * member cells of dev_buf (uint8: number of alive members, exact; float32:
  * per-thread FP32 partials of at most 16 cells, summed in FP64 in a fixed

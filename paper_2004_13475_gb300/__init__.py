@@ -46,7 +46,7 @@ EXPORTS = (
     "fractal_step_diffusion_kappa_f64", "fractal_adjoint_diffusion_step_f64",
     "fractal_step_ca_count", "fractal_step_diffusion_sum", "fractal_map_blocks_method",
     "fractal_pack", "fractal_unpack",
-    "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df",
+    "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -146,6 +146,7 @@ def _load() -> ctypes.CDLL:
         "fractal_adjoint_diffusion_step_df": (I, [P, VP, VP, VP, VP, VP, D, VP]),
         "fractal_unpack": (I, [P, VP, I, VP, VP]),
         "fractal_step_diffusion_sum": (I, [P, VP, VP, F, I, VP, VP]),
+        "fractal_step_diffusion_sums": (I, [P, VP, VP, F, I, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
     }
     for name, (res, args) in sig.items():
@@ -298,6 +299,15 @@ def fractal_step_diffusion_sum(plan: Plan, a, b, coef: float, steps: int, dev_su
     returns the buffer holding the result."""
     _check(_load().fractal_step_diffusion_sum(plan.handle, _ptr(a), _ptr(b), float(coef), int(steps),
                                               _ptr(dev_sum), _stream(stream)), "fractal_step_diffusion_sum")
+    return a if steps % 2 == 0 else b
+
+
+def fractal_step_diffusion_sums(plan: Plan, a, b, coef: float, steps: int, every: int, dev_sums, stream=None):
+    """Diffusion steps with the member sum after every `every` steps into the
+    device doubles `dev_sums` (steps / every of them); returns the buffer
+    holding the result."""
+    _check(_load().fractal_step_diffusion_sums(plan.handle, _ptr(a), _ptr(b), float(coef), int(steps), int(every),
+                                               _ptr(dev_sums), _stream(stream)), "fractal_step_diffusion_sums")
     return a if steps % 2 == 0 else b
 
 

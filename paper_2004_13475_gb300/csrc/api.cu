@@ -410,6 +410,14 @@ struct FusedSplit {
   int of(int i) const { return base + (i < extra ? 1 : 0); }
 };
 
+// Launches of a fused call of `steps` steps at `spl` per launch when the
+// state stays in records between them: ceil(steps / spl), but two when one
+// launch would have to end where it started (an even number of steps).
+int fused_launches(int steps, int spl) {
+  const int L = (steps + spl - 1) / spl;
+  return L == 1 && (steps & 1) == 0 ? 2 : L;
+}
+
 // `steps` automaton steps; with dev_count, also the alive count of the result
 // (fused into the last launch of the fused kernel, else a reduce after).
 int step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, double* dev_count, void* stream) {
@@ -419,18 +427,26 @@ int step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, double* dev_cou
   uint8_t* buf[2] = {a, b};
   if (steps > 0 && p->spl[FRACTAL_U8] > 1 && p->fused_ok[FRACTAL_U8]) {
     const int spl = p->spl[FRACTAL_U8];
-    const FusedSplit sp(steps, spl);
-    // between launches the state stays in the bit records (the first launch
-    // reads the embedded array, the last one writes it)
-    const bool rec = sp.L >= 2 && p->d_bits[0] && p->d_bits[1];
-    for (int i = 0; i < sp.L; ++i) {
-      const bool last = i == sp.L - 1;
-      auto* part = last && dev_count ? static_cast<unsigned long long*>(p->d_partials) : nullptr;
-      const uint32_t* pin = rec && i > 0 ? p->d_bits[(i - 1) & 1] : nullptr;
-      uint32_t* pout = rec && !last ? p->d_bits[i & 1] : nullptr;
-      cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], pin ? nullptr : buf[i & 1],
-                                      pout ? nullptr : buf[(i + 1) & 1], sp.of(i), spl, st, part, pin, pout);
-      if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+    if (p->d_bits[0] && p->d_bits[1]) {
+      // between launches the state stays in the bit records (the first
+      // launch reads a, the last one writes the result buffer)
+      const int L = fused_launches(steps, spl), base = steps / L, extra = steps % L;
+      for (int i = 0; i < L; ++i) {
+        const bool first = i == 0, last = i == L - 1;
+        auto* part = last && dev_count ? static_cast<unsigned long long*>(p->d_partials) : nullptr;
+        cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], first ? a : nullptr,
+                                        last ? buf[steps & 1] : nullptr, base + (i < extra ? 1 : 0), spl, st, part,
+                                        first ? nullptr : p->d_bits[(i - 1) & 1], last ? nullptr : p->d_bits[i & 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+      }
+    } else {  // no records: ping-pong of a and b, the launches' parity that of steps
+      const FusedSplit sp(steps, spl);
+      for (int i = 0; i < sp.L; ++i) {
+        auto* part = i == sp.L - 1 && dev_count ? static_cast<unsigned long long*>(p->d_partials) : nullptr;
+        cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], buf[i & 1], buf[(i + 1) & 1], sp.of(i), spl,
+                                        st, part);
+        if (e != cudaSuccess) return cuda_fail(e, "step_ca");
+      }
     }
     if (dev_count) {
       const Launch& F = p->fused[FRACTAL_U8];
@@ -462,58 +478,64 @@ int step_ca(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, double* dev_cou
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "step_ca count");
 }
 
-// `steps` diffusion steps; with dev_sum, also the member sum of the result.
-int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, double* dev_sum, void* stream) {
-  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0 ||
-      !std::isfinite(coef))
+// `steps` diffusion steps from a (the result in a for even steps, in b for
+// odd); with dev_sums, the global sum of the state after every `every` steps
+// (steps / every values; steps must be a multiple of every).
+int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, int every, double* dev_sums,
+                   void* stream) {
+  if (check_plan(p) || !a || !b || a == b || !aligned16(a) || !aligned16(b) || steps < 0 || every < 1 ||
+      steps % every != 0 || !std::isfinite(coef))
     return FRACTAL_EINVAL;
   const cudaStream_t st = (cudaStream_t)stream;
   float* buf[2] = {a, b};
-  if (steps > 0 && p->spl[FRACTAL_F32] > 1 && p->fused_ok[FRACTAL_F32]) {
+  const int nseg = steps / every;
+  if (steps > 0 && p->spl[FRACTAL_F32] > 1 && p->fused_ok[FRACTAL_F32] && p->d_pack[0] && p->d_pack[1]) {
+    // fused launches; between them the state stays in the compact records
+    // (the first launch reads a, the last writes the result buffer), also
+    // across the segments: the launch that ends a segment takes its sum
     const int spl = p->spl[FRACTAL_F32];
-    const FusedSplit sp(steps, spl);
-    // between launches the state stays in the compact records (the first
-    // launch reads the embedded array, the last one writes it)
-    const bool rec = sp.L >= 2 && p->d_pack[0] && p->d_pack[1];
-    for (int i = 0; i < sp.L; ++i) {
-      const bool last = i == sp.L - 1;
-      double* part = last && dev_sum ? static_cast<double*>(p->d_partials) : nullptr;
-      const float* pin = rec && i > 0 ? p->d_pack[(i - 1) & 1] : nullptr;
-      float* pout = rec && !last ? p->d_pack[i & 1] : nullptr;
-      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[FRACTAL_F32],
-                                             pin ? nullptr : buf[i & 1], pout ? nullptr : buf[(i + 1) & 1], coef,
-                                             sp.of(i), st, part, pin, pout, p->desc_ok ? p->d_desc : nullptr);
+    const int per = nseg == 1 ? fused_launches(every, spl) : (every + spl - 1) / spl;
+    const int total = nseg * per, base = every / per, extra = every % per;
+    const Launch& F = p->fused[FRACTAL_F32];
+    const int4* desc = p->desc_ok ? p->d_desc : nullptr;
+    for (int i = 0; i < total; ++i) {
+      const int seg = i / per, l = i % per;
+      const bool first = i == 0, last = i == total - 1;
+      double* part = l == per - 1 && dev_sums ? static_cast<double*>(p->d_partials) : nullptr;
+      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), F, first ? a : nullptr,
+                                             last ? buf[steps & 1] : nullptr, coef, base + (l < extra ? 1 : 0), st,
+                                             part, first ? nullptr : p->d_pack[(i - 1) & 1],
+                                             last ? nullptr : p->d_pack[i & 1], desc);
+      if (e == cudaSuccess && part)
+        e = launch_final_sum(1, p->d_partials, (int64_t)F.grid.x * F.grid.y, dev_sums + seg, st);
       if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-    }
-    if (dev_sum) {
-      const Launch& F = p->fused[FRACTAL_F32];
-      cudaError_t e = launch_final_sum(1, p->d_partials, (int64_t)F.grid.x * F.grid.y, dev_sum, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion sum");
     }
     return FRACTAL_OK;
   }
-  if (steps > 0 && use_tma(p, FRACTAL_F32)) {
-    CUtensorMap maps[2], rings[2];
+  // one launch per step; after each segment a reduce of its result
+  CUtensorMap maps[2], rings[2];
+  const bool tma = steps > 0 && use_tma(p, FRACTAL_F32);
+  if (tma) {
     const int rho = 1 << p->log_rho;
     if (!encode_maps(&maps[0], &rings[0], a, p->n, rho, FRACTAL_F32) ||
         !encode_maps(&maps[1], &rings[1], b, p->n, rho, FRACTAL_F32))
       return cuda_fail(cudaErrorInvalidValue, "tensor map");
-    for (int s = 0; s < steps; ++s) {
-      cudaError_t e = launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], rings[s & 1],
-                                           buf[(s + 1) & 1], coef, p->d_err, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-    }
-  } else {
-    for (int s = 0; s < steps; ++s) {
-      cudaError_t e =
-          launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], buf[s & 1], buf[(s + 1) & 1], coef, st);
-      if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
-    }
   }
-  if (!dev_sum) return FRACTAL_OK;
-  cudaError_t e = launch_reduce(p->mode, p->log_rho, FRACTAL_F32, p->aux[FRACTAL_F32], buf[steps & 1], p->d_partials,
-                                dev_sum, st);
-  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "step_diffusion sum");
+  for (int s = 0; s < steps; ++s) {
+    cudaError_t e = tma ? launch_diffusion_tma(p->mode, p->log_rho, p->tma[FRACTAL_F32], maps[s & 1], rings[s & 1],
+                                               buf[(s + 1) & 1], coef, p->d_err, st)
+                        : launch_diffusion(p->mode, p->log_rho, p->step[FRACTAL_F32], buf[s & 1], buf[(s + 1) & 1],
+                                           coef, st);
+    if (e == cudaSuccess && dev_sums && (s + 1) % every == 0)
+      e = launch_reduce(p->mode, p->log_rho, FRACTAL_F32, p->aux[FRACTAL_F32], buf[(s + 1) & 1], p->d_partials,
+                        dev_sums + (s + 1) / every - 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step_diffusion");
+  }
+  if (steps == 0 && dev_sums) {  // a zero-step call with a sum: the sum of a
+    cudaError_t e = launch_reduce(p->mode, p->log_rho, FRACTAL_F32, p->aux[FRACTAL_F32], a, p->d_partials, dev_sums, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step_diffusion sum");
+  }
+  return FRACTAL_OK;
 }
 
 // Steps with per-cell conductivity, state type T (float or double).
@@ -877,13 +899,20 @@ int fractal_step_ca_count(fractal_plan_t p, uint8_t* a, uint8_t* b, int steps, d
 }
 
 int fractal_step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, void* stream) {
-  return step_diffusion(p, a, b, coef, steps, nullptr, stream);
+  return step_diffusion(p, a, b, coef, steps, steps > 0 ? steps : 1, nullptr, stream);
 }
 
 int fractal_step_diffusion_sum(fractal_plan_t p, float* a, float* b, float coef, int steps, double* dev_sum,
                                void* stream) {
   if (!dev_sum) return FRACTAL_EINVAL;
-  return step_diffusion(p, a, b, coef, steps, dev_sum, stream);
+  return step_diffusion(p, a, b, coef, steps, steps > 0 ? steps : 1, dev_sum, stream);
+}
+
+int fractal_step_diffusion_sums(fractal_plan_t p, float* a, float* b, float coef, int steps, int every,
+                                double* dev_sums, void* stream) {
+  if (!dev_sums || every < 1 || steps < 0 || steps % every != 0) return FRACTAL_EINVAL;
+  if (steps == 0) return step_diffusion(p, a, b, coef, 0, 1, nullptr, stream);  // validation only
+  return step_diffusion(p, a, b, coef, steps, every, dev_sums, stream);
 }
 
 int fractal_step_diffusion_kappa(fractal_plan_t p, float* a, float* b, const float* kappa, float coef, int steps,

@@ -99,18 +99,22 @@ int rebuild(fractal_batch_s* b) {
 }
 
 int launch_steps(fractal_batch_s* b, float a, int steps, cudaStream_t s) {
-  // L launches with the parity of `steps`, as fractal_step_diffusion; between
-  // them the state stays in the block records (first launch from the
-  // instances' buffers, last one back into them)
+  // As fractal_step_diffusion: with records, ceil(steps / spl) launches (two
+  // for one even-step launch), the first from the instances' a buffers, the
+  // last into a (even steps) or b (odd), the state in the block records
+  // between them; without, ping-pong launches with the parity of `steps`.
+  const bool rec = b->d_rec[0] && b->d_rec[1];
   int L = (steps + b->spl - 1) / b->spl;
-  if ((L & 1) != (steps & 1)) ++L;
+  if (rec ? (L == 1 && (steps & 1) == 0) : ((L & 1) != (steps & 1))) ++L;
   const int base = steps / L, extra = steps % L;
-  const bool rec = L >= 2 && b->d_rec[0] && b->d_rec[1];
   for (int i = 0; i < L; ++i) {
     const int ns = base + (i < extra ? 1 : 0);
-    const float* pin = rec && i > 0 ? b->d_rec[(i - 1) & 1] : nullptr;
-    float* pout = rec && i < L - 1 ? b->d_rec[i & 1] : nullptr;
-    const cudaError_t e = launch_diffusion_batch(b->d_inst, b->count, b->items, i & 1, a, ns, b->margin, b->T,
+    const bool first = i == 0, last = i == L - 1;
+    const float* pin = rec && !first ? b->d_rec[(i - 1) & 1] : nullptr;
+    float* pout = rec && !last ? b->d_rec[i & 1] : nullptr;
+    // which = 0: a -> b, 1: b -> a (in / out where they are the buffers)
+    const int which = !rec ? (i & 1) : (first ? 0 : ((steps & 1) == 0 ? 1 : 0));
+    const cudaError_t e = launch_diffusion_batch(b->d_inst, b->count, b->items, which, a, ns, b->margin, b->T,
                                                  b->ctas, b->threads, s, pin, pout);
     if (e != cudaSuccess) return FRACTAL_ECUDA;
   }

@@ -16,8 +16,8 @@ def test_diffusion_flops_count_the_member_links():
 
 
 def test_launch_kinds_follow_the_step_driver():
-    # ceil(steps / spl) launches, one more when the parity differs; records
-    # between the launches of one call
+    # ceil(steps / spl) launches per segment (two for a one-launch call of an
+    # even number of steps); records between the launches of one call
     assert bench.fused_launch_kinds(100, 50) == ["ER", "RE"]
     assert bench.fused_launch_kinds(100, 25) == ["ER", "RR", "RR", "RE"]
     assert bench.fused_launch_kinds(100, 100) == ["ER", "RE"]
@@ -25,6 +25,9 @@ def test_launch_kinds_follow_the_step_driver():
     assert bench.fused_launch_kinds(26, 26) == ["ER", "RE"]
     assert bench.fused_launch_kinds(3, 3) == ["EE"]
     assert bench.kernel_launches(50, 100) == 2 and bench.kernel_launches(25, 100) == 4
+    assert bench.kernel_launches(50, 75) == 2                      # no parity launch: records decouple
+    assert bench.fused_launch_kinds(200, 25, 100) == ["ER"] + ["RR"] * 6 + ["RE"]
+    assert bench.kernel_launches(50, 200, 100) == 4 and bench.kernel_launches(100, 200, 100) == 2
 
 
 def test_launch_bytes_by_hand():

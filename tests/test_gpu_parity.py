@@ -409,6 +409,52 @@ def test_diffusion_sum_fused_into_the_steps(fr, mode, spl):
         assert out[0].item() == -1.0
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("spl", [1, 8, 25, 50])
+def test_diffusion_sums_every(fr, mode, spl):
+    """A sum every `every` steps in one call (the state kept in records across
+    the sums): each sum and the result against the oracle run segment by
+    segment, the same sums as separate calls."""
+    k, n = 10, 1024
+    plan = fr.fractal_map(k, 8, mode)
+    if spl > 1:
+        fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
+    u0 = synth.uniform_f32(63, n)
+    dom = domain(k)
+    for steps, every in ((60, 20), (50, 25), (9, 3), (7, 7)):
+        a = dev_f32(u0)
+        b = torch.full_like(a, SENTINEL_F32)
+        sums = torch.full((steps // every + 1,), -1.0, dtype=torch.float64, device="cuda")
+        res = fr.fractal_step_diffusion_sums(plan, a, b, 0.2, steps, every, sums)
+        assert sums[-1].item() == -1.0                      # nothing beyond steps / every sums
+        v = dom.take(u0).astype(np.float64)
+        for j in range(steps // every):
+            for _ in range(every):
+                v = oracle.diffusion_step(dom, v, 0.2)
+            assert sums[j].item() == pytest.approx(oracle.reduce_sum(v), rel=1e-5), (steps, every, j)
+        got = res.cpu().numpy().reshape(n, n)
+        want = dom.put(v, np.float64)
+        assert rel_err(got, want, dom.mask)[0] <= 2e-6 + 1e-7 * steps
+        # the same sums as one call per segment
+        a2 = dev_f32(u0)
+        b2 = torch.zeros_like(a2)
+        one = torch.zeros(1, dtype=torch.float64, device="cuda")
+        cur, oth = a2, b2
+        for j in range(steps // every):
+            cur = fr.fractal_step_diffusion_sum(plan, cur, oth, 0.2, every, one)
+            oth = b2 if cur is a2 else a2
+            assert one.item() == pytest.approx(sums[j].item(), rel=1e-6)
+    a = dev_f32(u0)
+    b = torch.zeros_like(a)
+    sums = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_diffusion_sums(plan, a, b, 0.2, 10, 3, sums)        # not a multiple
+    with pytest.raises(fr.FractalError):
+        fr.fractal_step_diffusion_sums(plan, a, b, 0.2, 10, 0, sums)        # every < 1
+    fr.fractal_step_diffusion_sums(plan, a, b, 0.2, 0, 5, sums)             # no steps: nothing written
+    assert sums[0].item() == -1.0
+
+
 def test_fused_needs_room(fr):
     with pytest.raises(fr.FractalError):
         fr.fractal_plan_set_steps_per_launch(fr.fractal_map(3, 4), fr.FRACTAL_F32, 8)   # super-tile < 16
