@@ -132,11 +132,13 @@ int fractal_plan_set_schedule(fractal_plan_t plan, int sched);
 /*
  * fractal_plan_autotune -- time the plan's step kernel for dtype under every
  * staging (TMA where it applies, vector loads), every valid number of tile
- * levels per CTA and 1 step per launch or temporal fusion (float32: 25, 50 or
- * 100 steps per launch; uint8: 8, 16 or 25), and keep
- * the fastest per step.  Each candidate runs `reps` timed launches dev_in ->
- * dev_scratch (after two untimed ones) on `stream`, which is synchronised.  dev_in is only read; dev_scratch is
- * overwritten.  Both are n*n arrays of dtype, 16-byte aligned.  *best_us
+ * levels per CTA and 1 step per launch or temporal fusion (float32: 16, 25,
+ * 50 or 100 steps per launch; uint8: 8, 16, 25 or 31), and keep the fastest
+ * per step.  Each candidate runs `reps` timed units dev_in -> dev_scratch
+ * (after two untimed ones) on `stream`, which is synchronised: one step, or
+ * with fusion the launches of a 100-step call (200 for 100 per launch) as
+ * the step driver runs them, records between.  dev_in is only read;
+ * dev_scratch is overwritten.  Both are n*n arrays of dtype, 16-byte aligned.  *best_us
  * (nullable) receives the best mean step time in microseconds.  The tuned
  * choice applies to this plan only (results never depend on it).  Errors:
  * FRACTAL_EINVAL, FRACTAL_ENOMEM, FRACTAL_ECUDA.

@@ -804,12 +804,12 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
     const bool skip_f32_fused = dtype == FRACTAL_F32 && f32_fused_timed;
     f32_fused_timed = true;
     // candidates: (schedule, steps per launch)
-    const int cands_f32[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 25},
-                                 {FRACTAL_SCHED_AUTO, 50}, {FRACTAL_SCHED_AUTO, 100}};
-    const int cands_u8[5][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
-                                {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 25}};
+    const int cands_f32[6][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 16},
+                                 {FRACTAL_SCHED_AUTO, 25}, {FRACTAL_SCHED_AUTO, 50}, {FRACTAL_SCHED_AUTO, 100}};
+    const int cands_u8[6][2] = {{FRACTAL_SCHED_STAGED, 1}, {FRACTAL_SCHED_TMA, 1}, {FRACTAL_SCHED_AUTO, 8},
+                                {FRACTAL_SCHED_AUTO, 16}, {FRACTAL_SCHED_AUTO, 25}, {FRACTAL_SCHED_AUTO, 31}};
     const int(*cands)[2] = dtype == FRACTAL_U8 ? cands_u8 : cands_f32;
-    for (int ci = 0; ci < 5 && status == FRACTAL_OK; ++ci) {
+    for (int ci = 0; ci < 6 && status == FRACTAL_OK; ++ci) {
       const int sched = cands[ci][0], spl = cands[ci][1];
       if (sched == FRACTAL_SCHED_TMA && !p->tma_ok[dtype]) continue;
       if (spl > 1 && skip_f32_fused) continue;
