@@ -205,6 +205,53 @@ __device__ __forceinline__ void block_step(float (&u)[kB * kB], float a, float v
   }
 }
 
+// The same step for two blocks at once, one in .x and one in .y of every
+// value: each operation is a paired FP32 instruction (two IEEE
+// round-to-nearest operations, the same results as the scalar form).
+// nd0, ndr, ndd: the ports' degrees, negated.
+struct NbSum2 {
+  float2 s = make_float2(0.f, 0.f);
+  bool any = false;
+  __device__ __forceinline__ void add(float2 v) {
+    s = any ? __fadd2_rn(s, v) : v;
+    any = true;
+  }
+};
+
+__device__ __forceinline__ void block_step2(float2 (&u)[kB * kB], float2 a, float2 vu, float2 vl, float2 vr, float2 vd,
+                                            float2 nd0, float2 ndr, float2 ndd) {
+  NbSum2 acc[kB * kB];  // children's old values, per cell
+#pragma unroll
+  for (int s = 2 * (kB - 1); s >= 0; --s) {
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const int i = s - j;
+      if (i < 0 || i >= kB || !amem(i, j)) continue;
+      const int q = j * kB + i;
+      NbSum2 nb = acc[q];
+      const float dn = -(float)bdeg(i, j);
+      float2 nd = make_float2(dn, dn);
+      if (q != 0) nb.add(u[bparent(i, j)]);
+      if (i == 0 && j == 0) {
+        nb.add(vu);
+        nb.add(vl);
+        nd = nd0;
+      }
+      if (i == kB - 1 && j == 0) {
+        nb.add(vr);
+        nd = ndr;
+      }
+      if (i == 0 && j == kB - 1) {
+        nb.add(vd);
+        nd = ndd;
+      }
+      const float2 c = u[q];
+      if (q != 0) acc[bparent(i, j)].add(c);
+      u[q] = __ffma2_rn(a, __ffma2_rn(nd, c, nb.s), c);
+    }
+  }
+}
+
 // A 16-byte chunk of row j starting at column i0 with its non-members zeroed.
 __device__ __forceinline__ float4 mask_chunk(float4 v, int i0, int j) {
   v.x = amem(i0 + 0, j) ? v.x : 0.f;

@@ -163,6 +163,117 @@ __device__ __forceinline__ bool block_member(int gx, int gy, int nblk) {
 // buffered by step parity, plus a zero slot at index `threads`.
 __host__ __device__ inline int fused_slots(int threads) { return threads + 1; }
 
+// CTA size classes of the fused kernel (launch bounds and, as the port
+// arrays' stride, slots = class + 1, a compile-time constant so that the two
+// parities' offsets are immediates): 288 threads, four CTAs per SM; 352,
+// three; 512, two.
+__host__ __device__ inline int fused_class(int threads) { return threads <= 288 ? 288 : threads <= 352 ? 352 : 512; }
+
+// Write back one member block of the super-tile from its values u (members;
+// other entries unused): to the embedded array out (whole 32-byte rows, 0 at
+// non-members, and the non-member cells of its tile row for rho >= 16), or to
+// record `rec` of pout when that is not null.  Returns the block's member sum
+// (FP32 within a row, FP64 over the rows) when want_sum, else 0.
+__device__ __forceinline__ double write_block(const float (&u)[kB * kB], const FGeo& f, int GX, int GY,
+                                              bool want_sum, float* __restrict__ out, float* __restrict__ pout,
+                                              int64_t rec) {
+  double sum = 0.0;
+  if (want_sum) {
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      float r = 0.f;
+      bool first = true;
+#pragma unroll
+      for (int i = 0; i < kB; ++i) {
+        if (!amem(i, j)) continue;
+        r = first ? u[j * kB + i] : r + u[j * kB + i];
+        first = false;
+      }
+      sum += (double)r;
+    }
+  }
+  if (pout) {
+    float4 r[kRecF4];
+    r[kRecF4 - 1].w = 0.f;  // the pad
+    int m = 0;
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q)
+      if (amem(q % kB, q / kB)) rec_set(r, m++, u[q]);
+    float4* p = reinterpret_cast<float4*>(pout) + rec * kRecF4;
+#pragma unroll
+    for (int i = 0; i < kRecF4; ++i) p[i] = r[i];
+    return sum;
+  }
+  float* o = out + (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
+#pragma unroll
+  for (int j = 0; j < kB; ++j)
+    *reinterpret_cast<float4*>(o + (size_t)j * f.n) =
+        make_float4(u[j * kB + 0], u[j * kB + 1], u[j * kB + 2], u[j * kB + 3]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) =
+        make_float4(u[j * kB + 4], u[j * kB + 5], u[j * kB + 6], u[j * kB + 7]);
+  if (f.log_rho >= 3) {
+    // non-member cells of member tiles: the block's lower right quarter,
+    // and (rho >= 16) the non-member blocks right of this one in its tile
+    // row, up to the next member block
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 4; j < kB; ++j) *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) = z;
+    const int bpt = 1 << (f.log_rho - 3);  // blocks per tile side
+    const int tx = GX & (bpt - 1), ty = GY & (bpt - 1);
+    for (int q = tx + 1; q < bpt && (q & ty) != 0; ++q) {
+      float* p = o + (size_t)(q - tx) * kB;
+      for (int j = 0; j < kB; ++j) {
+        *reinterpret_cast<float4*>(p + (size_t)j * f.n) = z;
+        *reinterpret_cast<float4*>(p + (size_t)j * f.n + 4) = z;
+      }
+    }
+  }
+  return sum;
+}
+
+// The block of one staged slot into u (members; other entries 0): record
+// `rec` of pin when that is not null, else the block (GX, GY) of in.
+__device__ __forceinline__ void stage_block(float (&u)[kB * kB], const FGeo& f, int GX, int GY,
+                                            const float* __restrict__ in, const float* __restrict__ pin, int64_t rec) {
+#pragma unroll
+  for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
+  if (pin) {
+    const float4* p = reinterpret_cast<const float4*>(pin) + rec * kRecF4;
+    float4 r[kRecF4];
+#pragma unroll
+    for (int i = 0; i < kRecF4; ++i) r[i] = __ldg(p + i);
+    int m = 0;
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q)
+      if (amem(q % kB, q / kB)) u[q] = rec_get(r, m++);
+    return;
+  }
+  const float* b = in + (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
+  float4 c[12];
+#pragma unroll
+  for (int j = 0; j < kB; ++j) c[j] = __ldg(reinterpret_cast<const float4*>(b + (size_t)j * f.n));
+#pragma unroll
+  for (int j = 0; j < 4; ++j) c[8 + j] = __ldg(reinterpret_cast<const float4*>(b + (size_t)j * f.n + 4));
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    const float4 v = mask_chunk(c[j], 0, j);
+    u[j * kB + 0] = v.x;
+    u[j * kB + 1] = v.y;
+    u[j * kB + 2] = v.z;
+    u[j * kB + 3] = v.w;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 v = mask_chunk(c[8 + j], 4, j);
+    u[j * kB + 4] = v.x;
+    u[j * kB + 5] = v.y;
+    u[j * kB + 6] = v.z;
+    u[j * kB + 7] = v.w;
+  }
+}
+
 // One super-tile whose block origin is (OX, OY) (in blocks).  All threads of
 // the CTA call it; it ends after the write-back.  ports: 6 * slots floats.
 // The state comes from the embedded array `in`, or from the records `pin`
@@ -273,14 +384,15 @@ __device__ __forceinline__ FSetup unpack_setup(int4 q) {
   return s;
 }
 
-template <int MODE>
+template <int MODE, int SLOTS>
 __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, float* __restrict__ out, float a,
                                                   int nsteps, const FGeo& f, int OX, int OY, const int* tab,
                                                   float* ports, bool want_sum, const float* __restrict__ pin,
                                                   float* __restrict__ pout, int64_t srec,
                                                   const int4* __restrict__ desc) {
   const int t = threadIdx.x, nthreads = blockDim.x;
-  const int slots = fused_slots(nthreads), zero = nthreads;
+  constexpr int slots = SLOTS;  // >= nthreads + 1
+  const int zero = nthreads;
   float* P0 = ports;  // [2][slots] each
   float* PR = ports + 2 * slots;
   float* PD = ports + 4 * slots;
@@ -295,43 +407,13 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   const float d0 = 2.f + (su.fu ? 1.f : 0.f) + (su.fl ? 1.f : 0.f), dr = 1.f + (su.fr ? 1.f : 0.f),
               dd = 1.f + (su.fd ? 1.f : 0.f);
 
-  // stage: the block's 12 member chunks straight into registers
+  // stage: the block's members straight into registers
   float u[kB * kB];
+  if (active) {
+    stage_block(u, f, GX, GY, in, pin, t < f.nb ? srec + t : (int64_t)su.rec);
+  } else {
 #pragma unroll
-  for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
-  const size_t base = (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
-  if (active && pin) {
-    const int64_t rec = t < f.nb ? srec + t : (int64_t)su.rec;
-    const float4* p = reinterpret_cast<const float4*>(pin) + rec * kRecF4;
-    float4 r[kRecF4];
-#pragma unroll
-    for (int i = 0; i < kRecF4; ++i) r[i] = __ldg(p + i);
-    int m = 0;
-#pragma unroll
-    for (int q = 0; q < kB * kB; ++q)
-      if (amem(q % kB, q / kB)) u[q] = rec_get(r, m++);
-  } else if (active) {
-    float4 c[12];
-#pragma unroll
-    for (int j = 0; j < kB; ++j) c[j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) c[8 + j] = __ldg(reinterpret_cast<const float4*>(in + base + (size_t)j * f.n + 4));
-#pragma unroll
-    for (int j = 0; j < kB; ++j) {
-      const float4 v = mask_chunk(c[j], 0, j);
-      u[j * kB + 0] = v.x;
-      u[j * kB + 1] = v.y;
-      u[j * kB + 2] = v.z;
-      u[j * kB + 3] = v.w;
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 v = mask_chunk(c[8 + j], 4, j);
-      u[j * kB + 4] = v.x;
-      u[j * kB + 5] = v.y;
-      u[j * kB + 6] = v.z;
-      u[j * kB + 7] = v.w;
-    }
+    for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
   }
   P0[t] = u[0];
   PR[t] = u[kB - 1];
@@ -358,58 +440,92 @@ __device__ __forceinline__ double fused_supertile(const float* __restrict__ in, 
   }
 
   // write back the super-tile's member blocks (not the boxes)
-  double sum = 0.0;
-  if (want_sum && active && t < f.nb) {
+  if (!(active && t < f.nb)) return 0.0;
+  return write_block(u, f, GX, GY, want_sum, out, pout, srec + t);
+}
+
+// Two blocks per thread: slots 2t and 2t + 1 of the launch's descriptors
+// (written for 2 * blockDim.x slots per CTA), every operation of the step
+// paired across the two (block_step2); otherwise as fused_supertile.  The
+// port arrays hold one value per slot, `slots` (even: the paired port stores
+// are 8-byte aligned) per parity.
+template <int MODE, int SLOTS>
+__device__ __forceinline__ double fused_supertile2(const float* __restrict__ in, float* __restrict__ out, float a,
+                                                   int nsteps, const FGeo& f, int OX, int OY, float* ports,
+                                                   bool want_sum, const float* __restrict__ pin,
+                                                   float* __restrict__ pout, int64_t srec,
+                                                   const int4* __restrict__ desc) {
+  const int t = threadIdx.x, zero = 2 * blockDim.x;
+  constexpr int slots = SLOTS;  // >= zero + 1, even
+  float* P0 = ports;
+  float* PR = ports + 2 * slots;
+  float* PD = ports + 4 * slots;
+  const FSetup s0 = unpack_setup(__ldg(desc + 2 * t)), s1 = unpack_setup(__ldg(desc + 2 * t + 1));
+  float2 u[kB * kB];
+  {
+    float w0[kB * kB], w1[kB * kB];
+    if (s0.active) {
+      stage_block(w0, f, OX + s0.bx, OY + s0.by, in, pin, 2 * t < f.nb ? srec + 2 * t : (int64_t)s0.rec);
+    } else {
 #pragma unroll
-    for (int j = 0; j < kB; ++j) {
-      float r = 0.f;
-      bool first = true;
-#pragma unroll
-      for (int i = 0; i < kB; ++i) {
-        if (!amem(i, j)) continue;
-        r = first ? u[j * kB + i] : r + u[j * kB + i];
-        first = false;
-      }
-      sum += (double)r;
+      for (int q = 0; q < kB * kB; ++q) w0[q] = 0.f;
     }
+    if (s1.active) {
+      stage_block(w1, f, OX + s1.bx, OY + s1.by, in, pin, 2 * t + 1 < f.nb ? srec + 2 * t + 1 : (int64_t)s1.rec);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kB * kB; ++q) w1[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) u[q] = make_float2(w0[q], w1[q]);
   }
-  if (active && t < f.nb && pout) {
-    float4 r[kRecF4];
-    r[kRecF4 - 1].w = 0.f;  // the pad
-    int m = 0;
-#pragma unroll
-    for (int q = 0; q < kB * kB; ++q)
-      if (amem(q % kB, q / kB)) rec_set(r, m++, u[q]);
-    float4* p = reinterpret_cast<float4*>(pout) + (srec + t) * kRecF4;
-#pragma unroll
-    for (int i = 0; i < kRecF4; ++i) p[i] = r[i];
-  } else if (active && t < f.nb) {
-    float* o = out + base;
-#pragma unroll
-    for (int j = 0; j < kB; ++j)
-      *reinterpret_cast<float4*>(o + (size_t)j * f.n) =
-          make_float4(u[j * kB + 0], u[j * kB + 1], u[j * kB + 2], u[j * kB + 3]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) =
-          make_float4(u[j * kB + 4], u[j * kB + 5], u[j * kB + 6], u[j * kB + 7]);
-    if (f.log_rho >= 3) {
-      // non-member cells of member tiles: the block's lower right quarter,
-      // and (rho >= 16) the non-member blocks right of this one in its tile
-      // row, up to the next member block
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int j = 4; j < kB; ++j) *reinterpret_cast<float4*>(o + (size_t)j * f.n + 4) = z;
-      const int bpt = 1 << (f.log_rho - 3);  // blocks per tile side
-      const int tx = GX & (bpt - 1), ty = GY & (bpt - 1);
-      for (int q = tx + 1; q < bpt && (q & ty) != 0; ++q) {
-        float* p = o + (size_t)(q - tx) * kB;
-        for (int j = 0; j < kB; ++j) {
-          *reinterpret_cast<float4*>(p + (size_t)j * f.n) = z;
-          *reinterpret_cast<float4*>(p + (size_t)j * f.n + 4) = z;
-        }
-      }
+  // the ports' degrees, negated: 2, 1, 1 inside the block plus the member neighbour blocks
+  const float2 nd0 = make_float2(-(2.f + (s0.fu ? 1.f : 0.f) + (s0.fl ? 1.f : 0.f)),
+                                 -(2.f + (s1.fu ? 1.f : 0.f) + (s1.fl ? 1.f : 0.f)));
+  const float2 ndr = make_float2(-(1.f + (s0.fr ? 1.f : 0.f)), -(1.f + (s1.fr ? 1.f : 0.f)));
+  const float2 ndd = make_float2(-(1.f + (s0.fd ? 1.f : 0.f)), -(1.f + (s1.fd ? 1.f : 0.f)));
+  const bool active = s0.active || s1.active;
+  const float2 a2 = make_float2(a, a);
+  *reinterpret_cast<float2*>(P0 + 2 * t) = u[0];
+  *reinterpret_cast<float2*>(PR + 2 * t) = u[kB - 1];
+  *reinterpret_cast<float2*>(PD + 2 * t) = u[(kB - 1) * kB];
+  if (t == 0) {
+    P0[zero] = P0[slots + zero] = 0.f;
+    PR[zero] = PR[slots + zero] = 0.f;
+    PD[zero] = PD[slots + zero] = 0.f;
+  }
+  __syncthreads();
+
+  // two steps per iteration: the port offsets of both parities are fixed
+#pragma unroll 2
+  for (int s = 0; s < nsteps; ++s) {
+    const int cur = (s & 1) * slots, nxt = slots - cur;
+    if (active) {
+      const float2 vu = make_float2(PD[cur + s0.up], PD[cur + s1.up]);
+      const float2 vl = make_float2(PR[cur + s0.lf], PR[cur + s1.lf]);
+      const float2 vr = make_float2(P0[cur + s0.rt], P0[cur + s1.rt]);
+      const float2 vd = make_float2(P0[cur + s0.dn], P0[cur + s1.dn]);
+      block_step2(u, a2, vu, vl, vr, vd, nd0, ndr, ndd);
     }
+    *reinterpret_cast<float2*>(P0 + nxt + 2 * t) = u[0];
+    *reinterpret_cast<float2*>(PR + nxt + 2 * t) = u[kB - 1];
+    *reinterpret_cast<float2*>(PD + nxt + 2 * t) = u[(kB - 1) * kB];
+    __syncthreads();
+  }
+
+  // write back the super-tile's member blocks (not the boxes)
+  double sum = 0.0;
+  if (s0.active && 2 * t < f.nb) {
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].x;
+    sum += write_block(w, f, OX + s0.bx, OY + s0.by, want_sum, out, pout, srec + 2 * t);
+  }
+  if (s1.active && 2 * t + 1 < f.nb) {
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].y;
+    sum += write_block(w, f, OX + s1.bx, OY + s1.by, want_sum, out, pout, srec + 2 * t + 1);
   }
   return sum;
 }
@@ -460,7 +576,7 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
   }
   const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
   float* ports = fsm;
-  int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(blockDim.x));
+  int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(MAXT));
   if (MODE == kBB && !desc) {
     bb_table(tab, f);
     __syncthreads();
@@ -468,10 +584,37 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
   // the super-tile's index among the member super-tiles (lambda: the CTA's
   // packed index; BB: its rank): its records and its threads' descriptors
   const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
-  const double mine = fused_supertile<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports,
+  const double mine = fused_supertile<MODE, MAXT + 1>(in, out, a, nsteps, f, sx << f.L, sy << f.L, tab, ports,
                                             partials != nullptr, pin, pout, st * f.nb,
                                             desc ? desc + st * blockDim.x : nullptr);
   if (partials) {  // the sum of the result's members, per CTA (uniform branch)
+    const double s = block_sum<double>(mine, red);
+    if (threadIdx.x == 0) partials[cta_id()] = s;
+  }
+}
+
+// The same launch with two blocks per thread (fused_supertile2): PMAX
+// threads at most, 2 * blockDim.x descriptor slots per CTA.
+template <int MODE, int PMAX, int MINB>
+__global__ void __launch_bounds__(PMAX, MINB) diffusion_fused2_kernel(const float* __restrict__ in,
+                                                                   float* __restrict__ out, float a, int nsteps, int M,
+                                                                   int log_rho, Geo g, double* __restrict__ partials,
+                                                                   const float* __restrict__ pin,
+                                                                   float* __restrict__ pout,
+                                                                   const int4* __restrict__ desc) {
+  extern __shared__ __align__(16) float fsm[];
+  __shared__ double red[32];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) {
+    if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
+    return;
+  }
+  const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
+  const double mine = fused_supertile2<MODE, 2 * PMAX + 2>(in, out, a, nsteps, f, sx << f.L, sy << f.L, fsm,
+                                                           partials != nullptr, pin, pout, st * f.nb,
+                                                           desc + st * 2 * blockDim.x);
+  if (partials) {
     const double s = block_sum<double>(mine, red);
     if (threadIdx.x == 0) partials[cta_id()] = s;
   }
@@ -503,7 +646,7 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
     warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
     FGeo f = make_fgeo(I.n, T, M, 3, I.R);
     f.rec0 = I.first * f.nb;  // item w's records start at w * nb
-    fused_supertile<kLambda>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps,
+    fused_supertile<kLambda, 289>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps,
                               f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb, nullptr);
   }
 }
@@ -597,6 +740,23 @@ cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps
   return run(diffusion_fused_kernel<MODE, 512, 2>);
 }
 
+// Two blocks per thread (with descriptors): L.threads / 2 threads, in the
+// class holding them; ports of 2 * class + 2 slots per parity.
+template <int MODE>
+cudaError_t go2(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
+                double* partials, const float* pin, float* pout, const int4* desc, cudaStream_t s) {
+  const int threads = L.threads / 2;
+  auto run = [&](auto* k, int pmax) -> cudaError_t {
+    const int smem = 6 * (2 * pmax + 2) * 4;
+    cudaError_t e = allow_smem((const void*)k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<L.grid, threads, smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials, pin, pout, desc);
+    return cudaGetLastError();
+  };
+  if (threads <= 176) return run(diffusion_fused2_kernel<MODE, 176, 3>, 176);
+  return run(diffusion_fused2_kernel<MODE, 256, 2>, 256);
+}
+
 
 int member_blocks(int T) {
   int nb = 1;
@@ -628,10 +788,13 @@ int fused_threads(const Geo& g, int rho, int margin) {
 }
 
 int fused_smem_bytes(const Geo& g, int margin) {
-  return 6 * fused_slots(fused_threads(g, 0, margin)) * 4 + member_blocks(g.T) * 4;
+  return 6 * fused_slots(fused_class(fused_threads(g, 0, margin))) * 4 + member_blocks(g.T) * 4;
 }
 
-int fused_batch_smem_bytes(int threads) { return 6 * fused_slots(threads) * 4; }
+int fused_batch_smem_bytes(int threads) {
+  (void)threads;  // the batch kernel's class: 288 threads
+  return 6 * fused_slots(288) * 4;
+}
 
 const void* fused_batch_kernel() { return (const void*)diffusion_batch_kernel; }
 
@@ -662,6 +825,13 @@ cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Laun
   if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads ||
       (!in && !pin) || (!out && !pout))
     return cudaErrorInvalidValue;
+  // two blocks per thread (the descriptors give each thread its two slots)
+  // for the larger CTA classes (margins of 64 cells and more: launches of
+  // many steps, bound by their arithmetic); short launches are bound by their
+  // loads and stores, which one block per thread keeps more of in flight
+  if (desc && L.threads > 288)
+    return mode == kLambda ? go2<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s)
+                           : go2<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s);
   return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s)
                          : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s);
 }
