@@ -488,7 +488,10 @@ def staging(info, d):
 def kernel_name(wl, info, spl):
     d = 0 if wl == "ca" else 1
     if spl > 1:
-        base = "ca_fused_kernel<lambda>" if wl == "ca" else f"diffusion_fused_kernel<lambda, rho={info['rho']}>"
+        # float32: two 8 x 8 blocks per thread in the CTA classes above 288 threads
+        two = wl != "ca" and info["threads"][1] > 288
+        base = ("ca_fused_kernel<lambda>" if wl == "ca" else
+                f"diffusion_fused{'2' if two else ''}_kernel<lambda, rho={info['rho']}>")
         return base + f" x{spl} steps/launch"
     kind = "tma_kernel" if info["tma"][d] else "kernel"
     return f"{'ca' if wl == 'ca' else 'diffusion'}_{kind}<lambda, rho={info['rho']}>"
@@ -538,11 +541,13 @@ def diffusion_box_member_blocks(k, T, M):
 
 # Sources each fused kernel is built from: `traffic` is taken from a committed
 # ncu summary only while their hash is the one recorded with it.
+_FUSED_DIFFUSION = ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
+                    "paper_2004_13475_gb300/csrc/dfloat.cuh", "paper_2004_13475_gb300/csrc/gasket.cuh")
 KERNEL_SOURCES = {
-    "diffusion_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
-                               "paper_2004_13475_gb300/csrc/gasket.cuh"),
+    "diffusion_fused_kernel": _FUSED_DIFFUSION,
+    "diffusion_fused2_kernel": _FUSED_DIFFUSION,
     "ca_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused_ca.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
-                        "paper_2004_13475_gb300/csrc/gasket.cuh"),
+                        "paper_2004_13475_gb300/csrc/dfloat.cuh", "paper_2004_13475_gb300/csrc/gasket.cuh"),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
