@@ -977,27 +977,28 @@ def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):
 
     def one():
         if pk is not None:
-            # the diffusion state comes in (copy engine) on a side stream
-            # while the automaton runs, and the automaton's result goes out
-            # while the diffusion runs; on the critical path, the automaton's
-            # state is unpacked straight from pinned host memory and the
-            # diffusion result packed straight into it (the kernels move the
-            # bytes over the host link); the step ends when both streams do
+            # the diffusion (the larger state) first: its state is unpacked
+            # straight from pinned host memory (the kernel moves the bytes
+            # over the host link) while the automaton's state comes in on a
+            # side stream; the diffusion result goes out on the side stream
+            # while the automaton runs; the automaton result is packed
+            # straight into pinned host memory; the step ends when both
+            # streams do
             side.wait_stream(stream)
             with torch.cuda.stream(side):
-                d_u.copy_(h_u, non_blocking=True)
-                fr.fractal_unpack(pk, d_u, fr.FRACTAL_F32, u_a, side)
-            fr.fractal_unpack(pk, h_ca, fr.FRACTAL_U8, ca_a, stream)
-            step(0, parts=("ca",))
-            fr.fractal_pack(pk, ca_a, fr.FRACTAL_U8, d_ca, stream)
-            ca_done = torch.cuda.Event()
-            ca_done.record(stream)
-            stream.wait_stream(side)
+                d_ca.copy_(h_ca, non_blocking=True)
+                fr.fractal_unpack(pk, d_ca, fr.FRACTAL_U8, ca_a, side)
+            fr.fractal_unpack(pk, h_u, fr.FRACTAL_F32, u_a, stream)
             res = step(0, parts=("diffusion",))
-            side.wait_event(ca_done)
+            fr.fractal_pack(pk, res, fr.FRACTAL_F32, d_u, stream)
+            diff_done = torch.cuda.Event()
+            diff_done.record(stream)
+            stream.wait_stream(side)
+            step(0, parts=("ca",))
+            side.wait_event(diff_done)
             with torch.cuda.stream(side):
-                h_ca.copy_(d_ca, non_blocking=True)
-            fr.fractal_pack(pk, res, fr.FRACTAL_F32, h_u, stream)
+                h_u.copy_(d_u, non_blocking=True)
+            fr.fractal_pack(pk, ca_a, fr.FRACTAL_U8, h_ca, stream)
             stream.wait_stream(side)
         else:
             ca_a.copy_(h_ca, non_blocking=True)
@@ -1022,9 +1023,9 @@ def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):
     nbytes = 5 * cells
     note = ("whole n x n arrays copied each way through pinned host memory" if pk is None else
             f"member tiles of side {rho} in lambda order copied each way through pinned host memory, "
-            "unpacked onto / packed from the device arrays inside the timed region; the diffusion state's "
-            "copy in and the automaton result's copy out overlap the other workload's kernels; the automaton "
-            "state's unpack reads, and the diffusion result's pack writes, pinned host memory directly")
+            "unpacked onto / packed from the device arrays inside the timed region; the automaton state's "
+            "copy in and the diffusion result's copy out overlap the other workload's kernels; the diffusion "
+            "state's unpack reads, and the automaton result's pack writes, pinned host memory directly")
     if pk is not None:
         pk.close()
     return {"value": world * MEMBERS * (CA_STEPS + DIFF_STEPS) * steps / t, "unit": "cell-updates/s",
