@@ -519,9 +519,11 @@ int fractal_batch_configure(fractal_batch_t batch, int supertile, int steps_per_
 /*
  * fractal_batch_step_diffusion -- `steps` diffusion steps (coefficient a, as
  * fractal_step_diffusion) on every instance, in ceil(steps / spl) persistent
- * launches (one more if needed for the parity): after the call each
- * instance's state is in dev_a[i] when `steps` is even and in dev_b[i] when
- * it is odd.  Asynchronous on `stream`.  Errors: FRACTAL_EINVAL (unbound,
+ * launches (two for a single even-step launch), the state in the batch's
+ * block records between them: after the call each instance's state is in
+ * dev_a[i] when `steps` is even and in dev_b[i] when it is odd (the other
+ * buffer is not written by a call of several launches).  Asynchronous on
+ * `stream`.  Errors: FRACTAL_EINVAL (unbound,
  * steps < 0, a not finite), FRACTAL_ECUDA.
  */
 int fractal_batch_step_diffusion(fractal_batch_t batch, float a, int steps, void* stream);

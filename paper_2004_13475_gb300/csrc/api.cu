@@ -396,9 +396,9 @@ int check_plan(const fractal_plan_s* p) { return p ? FRACTAL_OK : FRACTAL_EINVAL
 
 namespace {
 
-// L launches of at most spl steps with the parity of `steps` (so that the
-// result lands where the single-step ping-pong would leave it): steps per
-// launch i.
+// L launches of at most spl steps with the parity of `steps`, for fused
+// calls that ping-pong a and b without records (the result lands where the
+// single-step ping-pong would leave it): steps per launch i.
 struct FusedSplit {
   int L, base, extra;
   FusedSplit(int steps, int spl) {
@@ -767,20 +767,21 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
     done = spl;
     if (spl > 1 && records) {
       const int S = spl <= 50 ? 100 : 2 * spl;
-      const FusedSplit sp(S, spl);
+      const int L = fused_launches(S, spl), base = S / L, extra = S % L;
       const Launch& F = p->fused[dtype];
       const int4* desc = p->desc_ok ? p->d_desc : nullptr;
       cudaError_t e = cudaSuccess;
-      for (int i = 0; i < sp.L && e == cudaSuccess; ++i) {
-        const bool first = i == 0, last = i == sp.L - 1;
+      for (int i = 0; i < L && e == cudaSuccess; ++i) {
+        const bool first = i == 0, last = i == L - 1;
+        const int ns = base + (i < extra ? 1 : 0);
         if (dtype == FRACTAL_U8) {
           e = launch_ca_fused(p->mode, F, first ? (const uint8_t*)dev_in : nullptr,
-                              last ? (uint8_t*)dev_scratch : nullptr, sp.of(i), spl, st, nullptr,
+                              last ? (uint8_t*)dev_scratch : nullptr, ns, spl, st, nullptr,
                               first ? nullptr : p->d_bits[(i - 1) & 1], last ? nullptr : p->d_bits[i & 1]);
         } else {
           e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), F,
                                      first ? (const float*)dev_in : nullptr, last ? (float*)dev_scratch : nullptr,
-                                     0.2f, sp.of(i), st, nullptr, first ? nullptr : p->d_pack[(i - 1) & 1],
+                                     0.2f, ns, st, nullptr, first ? nullptr : p->d_pack[(i - 1) & 1],
                                      last ? nullptr : p->d_pack[i & 1], desc);
         }
       }
