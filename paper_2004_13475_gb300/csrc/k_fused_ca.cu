@@ -105,9 +105,11 @@ __device__ __forceinline__ uint32_t life_rule_words(uint32_t ul, uint32_t uc, ui
   return bit1 & ~bit2 & (bit0 | mc);
 }
 
-template <int MODE>
+// TT: the super-tile side, a compile-time constant so that the image pitch
+// and the nine neighbour offsets of a word are immediates.
+template <int MODE, int TT>
 __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                                                       int nsteps, int M, int wlev, Geo g,
+                                                       int nsteps, int M, Geo g,
                                                        unsigned long long* __restrict__ partials,
                                                        const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout) {
   constexpr int TPW = kCaTasksPerWarp;
@@ -118,12 +120,14 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     if (partials && threadIdx.x == 0) partials[cta_id()] = 0ull;
     return;
   }
-  const int n = g.n, T = g.T;
-  const int wside = 1 << wlev;                         // word tiles per super-tile side
+  const int n = g.n;
+  constexpr int T = TT;
+  constexpr int wlev = ilog2c(TT) - 5;                 // word-tile levels of the super-tile
+  constexpr int wside = 1 << wlev;                     // word tiles per super-tile side
   int wtiles = 1, wlw = 1;                             // 3^wlev, 3^ceil(wlev/2)
   for (int i = 0; i < wlev; ++i) wtiles *= 3;
   for (int i = 0; i < (wlev + 1) / 2; ++i) wlw *= 3;
-  const int P = ca_pitch(T);
+  constexpr int P = (TT >> 5) + 5;                     // ca_pitch(TT)
   const int img = ca_image_words(T, M);
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
   uint32_t* A = tab + tab_words(wtiles);
@@ -251,11 +255,20 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
 template <int MODE>
 cudaError_t go(const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
                unsigned long long* partials, const uint32_t* pin, uint32_t* pout, cudaStream_t s) {
-  auto* k = ca_fused_kernel<MODE>;
-  cudaError_t e = allow_smem((const void*)k, L.smem);
-  if (e != cudaSuccess) return e;
-  k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, ilog2c(L.geo.T) - 5, L.geo, partials, pin, pout);
-  return cudaGetLastError();
+  auto run = [&](auto* k) -> cudaError_t {
+    cudaError_t e = allow_smem((const void*)k, L.smem);
+    if (e != cudaSuccess) return e;
+    k<<<L.grid, L.threads, L.smem, s>>>(in, out, nsteps, margin, L.geo, partials, pin, pout);
+    return cudaGetLastError();
+  };
+  switch (L.geo.T) {
+    case 32: return run(ca_fused_kernel<MODE, 32>);
+    case 64: return run(ca_fused_kernel<MODE, 64>);
+    case 128: return run(ca_fused_kernel<MODE, 128>);
+    case 256: return run(ca_fused_kernel<MODE, 256>);
+    case 512: return run(ca_fused_kernel<MODE, 512>);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
