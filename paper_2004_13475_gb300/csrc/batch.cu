@@ -33,6 +33,9 @@ struct fractal_batch_s {
   cudaGraphExec_t exec = nullptr;
   int graph_steps = 0;
   float* d_rec[2] = {nullptr, nullptr};  // block records between the launches of one call
+  int4* d_desc = nullptr;                // per-thread setups of the current configuration
+  size_t desc_cap = 0;                   // bytes
+  bool desc_ok = false;
 };
 
 namespace {
@@ -95,6 +98,32 @@ int rebuild(fractal_batch_s* b) {
     cudaGetLastError();
     return FRACTAL_ECUDA;
   }
+  // the launches' per-thread setups, once per configuration (the kernels
+  // compute them themselves when there is no room for them)
+  b->desc_ok = false;
+  if (b->bound) {
+    const size_t need = (size_t)b->items * (size_t)b->threads * sizeof(int4);
+    if (need > b->desc_cap) {
+      if (b->d_desc) cudaFree(b->d_desc);
+      b->d_desc = nullptr;
+      b->desc_cap = 0;
+      if (cudaMalloc(&b->d_desc, need) == cudaSuccess) {
+        b->desc_cap = need;
+      } else {
+        cudaGetLastError();
+        b->d_desc = nullptr;
+      }
+    }
+    if (b->d_desc) {
+      if (launch_batch_describe(b->d_inst, b->count, b->items, b->margin, b->T, b->ctas, b->threads, b->d_desc,
+                                nullptr) != cudaSuccess ||
+          cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return FRACTAL_ECUDA;
+      }
+      b->desc_ok = true;
+    }
+  }
   return FRACTAL_OK;
 }
 
@@ -115,7 +144,8 @@ int launch_steps(fractal_batch_s* b, float a, int steps, cudaStream_t s) {
     // which = 0: a -> b, 1: b -> a (in / out where they are the buffers)
     const int which = !rec ? (i & 1) : (first ? 0 : ((steps & 1) == 0 ? 1 : 0));
     const cudaError_t e = launch_diffusion_batch(b->d_inst, b->count, b->items, which, a, ns, b->margin, b->T,
-                                                 b->ctas, b->threads, s, pin, pout);
+                                                 b->ctas, b->threads, s, pin, pout,
+                                                 b->desc_ok ? b->d_desc : nullptr);
     if (e != cudaSuccess) return FRACTAL_ECUDA;
   }
   return FRACTAL_OK;
@@ -178,6 +208,7 @@ int fractal_batch_destroy(fractal_batch_t b) {
   if (b->d_partials) cudaFree(b->d_partials);
   for (int i = 0; i < 2; ++i)
     if (b->d_rec[i]) cudaFree(b->d_rec[i]);
+  if (b->d_desc) cudaFree(b->d_desc);
   delete b;
   return FRACTAL_OK;
 }
@@ -273,7 +304,8 @@ int fractal_batch_autotune(fractal_batch_t b, float a, int reps, float* best_us,
       // launches of spl steps, dev_a -> dev_b only (which = 0)
       auto one = [&]() -> int {
         return launch_diffusion_batch(b->d_inst, b->count, b->items, 0, a, b->spl, b->margin, b->T, b->ctas,
-                                      b->threads, st) == cudaSuccess
+                                      b->threads, st, nullptr, nullptr, b->desc_ok ? b->d_desc : nullptr) ==
+                       cudaSuccess
                    ? FRACTAL_OK
                    : FRACTAL_ECUDA;
       };

@@ -637,7 +637,8 @@ __device__ __forceinline__ int batch_instance(const BatchInst* __restrict__ inst
 __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
                                                               int64_t items, int which, float a, int nsteps, int M,
                                                               int T, const float* __restrict__ pin,
-                                                              float* __restrict__ pout) {
+                                                              float* __restrict__ pout,
+                                                              const int4* __restrict__ desc) {
   extern __shared__ __align__(16) float fsm[];
   for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
     const BatchInst I = inst[batch_instance(inst, count, w)];
@@ -647,7 +648,24 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
     FGeo f = make_fgeo(I.n, T, M, 3, I.R);
     f.rec0 = I.first * f.nb;  // item w's records start at w * nb
     fused_supertile<kLambda, 289>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps,
-                              f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb, nullptr);
+                              f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb,
+                              desc ? desc + w * blockDim.x : nullptr);
+  }
+}
+
+// The batch launch's per-thread setups, item by item (w * blockDim.x + t).
+__global__ void __launch_bounds__(288) batch_describe_kernel(const BatchInst* __restrict__ inst, int count,
+                                                             int64_t items, int M, int T, int4* __restrict__ desc) {
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const BatchInst I = inst[batch_instance(inst, count, w)];
+    const int64_t om = w - I.first;
+    int sx, sy;
+    warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
+    FGeo f = make_fgeo(I.n, T, M, 3, I.R);
+    f.rec0 = I.first * f.nb;
+    const FSetup s = fused_setup<kLambda>(f, sx << f.L, sy << f.L, nullptr);
+    desc[w * blockDim.x + threadIdx.x] = pack_setup(s);
+    __syncthreads();  // the setup's shared tables are rewritten for the next item
   }
 }
 
@@ -798,15 +816,24 @@ int fused_batch_smem_bytes(int threads) {
 
 const void* fused_batch_kernel() { return (const void*)diffusion_batch_kernel; }
 
+cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t items, int margin, int T, int ctas,
+                                  int threads, int4* desc, cudaStream_t s) {
+  Geo g{};
+  g.T = T;
+  if (fused_threads(g, 0, margin) != threads || threads > 288 || ctas < 1) return cudaErrorInvalidValue;
+  batch_describe_kernel<<<ctas, threads, 0, s>>>(inst, count, items, margin, T, desc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
                                    int margin, int T, int ctas, int threads, cudaStream_t s, const float* pin,
-                                   float* pout) {
+                                   float* pout, const int4* desc) {
   if (nsteps < 1 || nsteps > margin || ctas < 1) return cudaErrorInvalidValue;
   Geo g{};
   g.T = T;
   if (fused_threads(g, 0, margin) != threads) return cudaErrorInvalidValue;
   diffusion_batch_kernel<<<ctas, threads, fused_batch_smem_bytes(threads), s>>>(inst, count, items, which, a, nsteps,
-                                                                               margin, T, pin, pout);
+                                                                               margin, T, pin, pout, desc);
   return cudaGetLastError();
 }
 

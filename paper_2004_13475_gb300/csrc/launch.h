@@ -115,9 +115,13 @@ struct BatchInst {
 // and margin.  Per-instance member sums through `partials` (items doubles).
 // pin / pout (when not null): the block records of all instances (item w's
 // at w * 3^log2(T/8)) in place of the instances' buffers.
+// desc (when not null): the batch's per-thread setups from
+// launch_batch_describe for the same table, super-tile side and margin.
 cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
                                    int margin, int T, int ctas, int threads, cudaStream_t s,
-                                   const float* pin = nullptr, float* pout = nullptr);
+                                   const float* pin = nullptr, float* pout = nullptr, const int4* desc = nullptr);
+cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t items, int margin, int T, int ctas,
+                                  int threads, int4* desc, cudaStream_t s);
 cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items, int which, int T, int ctas,
                                 double* partials, double* out, cudaStream_t s);
 int fused_batch_smem_bytes(int threads);
