@@ -20,17 +20,34 @@
 // (the right and bottom boxes reach one row / column further than the
 // diffusion's 4-neighbour ones: the corner cell (T-1, 0) reaches (T, M) by M
 // diagonal moves).  For M <= 31 these are the words of column -1 (left,
-// bottom), 0 (top, bottom) and T/32 (right).  Box words are evolved with the
-// tiles; cells whose neighbours were not staged go wrong from the box edge
-// inwards, one cell per step, and never reach the super-tile within s steps.
+// bottom), 0 (top, bottom) and T/32 (right).  The kernel stages them with
+// the margin rounded up to even, ME, and the right box to rows [-ME, ME+1],
+// so that every box piece starts on an even row and has an even number of
+// rows (the words added belong to no other task: staging more of the state
+// is always correct).  Box words are evolved with the tiles; cells whose
+// neighbours were not staged go wrong from the box edge inwards, one cell
+// per step, and never reach the super-tile within s steps.
 //
 // Tasks.  A task is one word column of at most 32 consecutive rows (a word
-// tile, or a piece of a box); lane i of the warp that owns it keeps row i.
-// Each step a lane reads the 3 x 3 words around its word (rows above and
-// below, columns left and right), forms the eight neighbour planes by funnel
-// shifts, applies the bit-sliced rule, masks births outside the gasket and
-// writes the word to the other image.  Every staged word is the word of exactly one task
-// lane; every other word of the image is 0 and stays 0.
+// tile, or a piece of a box), taken by a half warp: lane i of the half keeps
+// rows 2i and 2i + 1.  The bit image is stored by columns (a column's rows
+// are consecutive words), so a lane's two words are one 8-byte access.  Each
+// step a lane reads rows 2i-1 .. 2i+2 of its column and of the columns left
+// and right, forms each row's three-cell horizontal sum (funnel shifts with
+// the left word's top cell and the right word's bottom cell, a full adder),
+// adds three of them for each of its two rows, applies the rule and masks
+// births outside the gasket.  Every staged word is the word of exactly one
+// task lane; every other word of the image is 0 and stays 0.
+//
+// The rule modulo 4.  No member cell of the gasket has more than 5 member
+// neighbours (the neighbourhood of a cell inside one of the three copies of
+// the level-(j-1) gasket is that copy's, and the copies meet at two corners
+// and one diagonal contact whose cells have at most 5; a brute-force count
+// over levels 2 to 13 agrees), and non-members are always dead.  So the
+// nine-cell sum S = neighbours + self is at most 6, and with m = S mod 4:
+// alive next iff m == 3 (three neighbours, or two and alive) or m == 0 and
+// alive now (S == 4: three neighbours and alive; S == 0 leaves a dead cell
+// dead).  Two bits of the sum suffice.
 //
 // Records.  Between the launches of one call the state stays in compact
 // records, one per member word tile: its 32 words (row order), 128 bytes
@@ -44,20 +61,23 @@
 namespace fractal {
 namespace {
 
-constexpr int kCaTasksPerWarp = 6;
+constexpr int kCaSlots = 3;  // tasks per half warp, at most
+constexpr int kCaRow0 = 34;  // image row of super-tile row 0
 
-// Image geometry: rows [-M-1, T+M] (a guard row beyond each box), word columns
-// [-2, T/32+1] (a guard column beyond each box column), padded to an odd
-// pitch so that the 32 rows of a task fall into 32 different banks.
-__host__ __device__ inline int ca_pitch(int T) { return (T >> 5) + 5; }
-__host__ __device__ inline int ca_rows(int T, int M) { return T + 2 * M + 2; }
-__host__ __device__ inline int ca_image_words(int T, int M) { return (ca_pitch(T) * ca_rows(T, M) + 3) & ~3; }
+// Image geometry: word columns [-2, T/32 + 1] of rows [-34, T + 34) whatever
+// the margin (the box pieces reach rows -ME .. T + ME - 1 and a lane reads one
+// row beyond its pair on each side), so that a column's stride is a
+// compile-time constant.  Word (c, y) is at (c + 2) * ca_col(T) + y + 34.
+__host__ __device__ constexpr int ca_cols(int T) { return (T >> 5) + 4; }
+__host__ __device__ constexpr int ca_col(int T) { return T + 2 * kCaRow0; }
+__host__ __device__ constexpr int ca_image_words(int T) { return ca_cols(T) * ca_col(T); }
 
-// Tasks of a super-tile: word tiles first, then the six box pieces.
-__host__ __device__ inline int ca_tasks(int wtiles) { return wtiles + 6; }
+// Tasks of a super-tile: word tiles first, then the seven box pieces.
+__host__ __device__ inline int ca_tasks(int wtiles) { return wtiles + 7; }
 
-// Task -> (word column c, first row y0, rows) in super-tile coordinates.
-__device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, int T, int M, int& c, int& y0,
+// Task -> (word column c, first row y0, rows) in super-tile coordinates; ME:
+// the margin rounded up to even.  y0 and rows are even.
+__device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, int T, int ME, int& c, int& y0,
                                         int& rows) {
   if (j < wtiles) {
     const uint32_t e = tab[j];
@@ -66,14 +86,15 @@ __device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, 
     rows = 32;
     return;
   }
-  const int right = 2 * M + 1;  // rows of the right box
+  const int right = 2 * ME + 2;  // rows of the right box, [-ME, ME + 1]
   switch (j - wtiles) {
-    case 0: c = -1; y0 = 0; rows = M; return;                                   // left
-    case 1: c = 0; y0 = -M; rows = M; return;                                   // top
-    case 2: c = T >> 5; y0 = -M; rows = right < 32 ? right : 32; return;        // right, first 32 rows
-    case 3: c = T >> 5; y0 = -M + 32; rows = right > 32 ? right - 32 : 0; return;  // right, the rest
-    case 4: c = -1; y0 = T; rows = M; return;                                   // bottom, left word
-    default: c = 0; y0 = T; rows = M; return;                                   // bottom, right word
+    case 0: c = -1; y0 = 0; rows = ME; return;                                   // left
+    case 1: c = 0; y0 = -ME; rows = ME; return;                                  // top
+    case 2: c = T >> 5; y0 = -ME; rows = min(right, 32); return;                 // right, in pieces of 32 rows
+    case 3: c = T >> 5; y0 = -ME + 32; rows = min(max(right - 32, 0), 32); return;
+    case 4: c = T >> 5; y0 = -ME + 64; rows = max(right - 64, 0); return;
+    case 5: c = -1; y0 = T; rows = ME; return;                                   // bottom, left word
+    default: c = 0; y0 = T; rows = ME; return;                                   // bottom, right word
   }
 }
 
@@ -83,36 +104,34 @@ __device__ __forceinline__ uint32_t pack32(uint4 a, uint4 b) {
          nz4(b.z) << 24 | nz4(b.w) << 28;
 }
 
-// The eight neighbour planes of a 32-cell word from the 3 x 3 words around
-// it: for each of the rows above, at and below, the word shifted so that bit
-// i holds cell i-1 (funnel shift with the left word's top cell) and cell i+1
-// (with the right word's bottom cell); the row itself contributes only its
-// two shifts.  Summed with full adders into the count's bits 0..2 (a count
-// of 8 wraps to 0, neither 2 nor 3); B3/S23: alive next iff count is 3, or 2
-// and alive now.
-__device__ __forceinline__ uint32_t life_rule_words(uint32_t ul, uint32_t uc, uint32_t ur, uint32_t ml, uint32_t mc,
-                                                    uint32_t mr, uint32_t dl, uint32_t dc, uint32_t dr) {
-  const uint32_t a = __funnelshift_l(ul, uc, 1), b = uc, c = __funnelshift_r(uc, ur, 1);
-  const uint32_t d = __funnelshift_l(ml, mc, 1), e = __funnelshift_r(mc, mr, 1);
-  const uint32_t f = __funnelshift_l(dl, dc, 1), g = dc, h = __funnelshift_r(dc, dr, 1);
-  const uint32_t s1 = a ^ b ^ c, c1 = (a & b) | (c & (a ^ b));
-  const uint32_t s2 = d ^ e ^ f, c2 = (d & e) | (f & (d ^ e));
-  const uint32_t s3 = g ^ h, c3 = g & h;
-  const uint32_t bit0 = s1 ^ s2 ^ s3, c4 = (s1 & s2) | (s3 & (s1 ^ s2));
-  const uint32_t t1 = c1 ^ c2 ^ c3, c5 = (c1 & c2) | (c3 & (c1 ^ c2));
-  const uint32_t bit1 = t1 ^ c4, c6 = t1 & c4;
-  const uint32_t bit2 = c5 ^ c6;
-  return bit1 & ~bit2 & (bit0 | mc);
+// Three-cell horizontal sum of a row word w with its left and right words,
+// as two bit planes: bit i of (s, k) = cells i-1, i, i+1 summed (s the low
+// bit, k the carry).
+__device__ __forceinline__ void row_sum3(uint32_t l, uint32_t w, uint32_t r, uint32_t& s, uint32_t& k) {
+  const uint32_t a = __funnelshift_l(l, w, 1), c = __funnelshift_r(w, r, 1);
+  s = a ^ w ^ c;
+  k = (a & w) | (c & (a ^ w));
 }
 
-// TT: the super-tile side, a compile-time constant so that the image pitch
-// and the nine neighbour offsets of a word are immediates.
+// Next state of a word from the horizontal sums of the rows above (u), at
+// (m) and below (d), the word itself and its member mask: the nine-cell sum
+// modulo 4 (bit0, bit1), births masked to members (self is already a subset
+// of the members).
+__device__ __forceinline__ uint32_t life_rule_mod4(uint32_t us, uint32_t uk, uint32_t ms, uint32_t mk_, uint32_t ds,
+                                                   uint32_t dk, uint32_t self, uint32_t mask) {
+  const uint32_t bit0 = us ^ ms ^ ds;
+  const uint32_t k0 = (us & ms) | (ds & (us ^ ms));
+  const uint32_t bit1 = (uk ^ mk_ ^ dk ^ k0) & mask;
+  return (bit0 & bit1) | (~bit0 & ~bit1 & self);
+}
+
+// TT: the super-tile side, a compile-time constant so that the column stride
+// and the neighbour offsets of a word are immediates.
 template <int MODE, int TT>
 __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                                        int nsteps, int M, Geo g,
                                                        unsigned long long* __restrict__ partials,
                                                        const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout) {
-  constexpr int TPW = kCaTasksPerWarp;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ unsigned long long red[32];
   int sx, sy;
@@ -127,8 +146,9 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
   int wtiles = 1, wlw = 1;                             // 3^wlev, 3^ceil(wlev/2)
   for (int i = 0; i < wlev; ++i) wtiles *= 3;
   for (int i = 0; i < (wlev + 1) / 2; ++i) wlw *= 3;
-  constexpr int P = (TT >> 5) + 5;                     // ca_pitch(TT)
-  const int img = ca_image_words(T, M);
+  constexpr int CW = ca_col(TT);                       // words per image column
+  constexpr int img = ca_image_words(TT);
+  const int ME = M + (M & 1);
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
   uint32_t* A = tab + tab_words(wtiles);
   uint32_t* B = A + img;
@@ -167,41 +187,49 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     reinterpret_cast<uint4*>(A)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 
-  // this lane's row of each of its warp's tasks: image offset and member bits
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // this lane's row pair of each of its half warp's tasks: image offset of
+  // the first row and the two rows' member bits
+  const int sub = threadIdx.x & 15, hw = threadIdx.x >> 4, nh = blockDim.x >> 4;
   const int ntasks = ca_tasks(wtiles);
-  int off[TPW];
-  uint32_t mk[TPW];
-  // staged in two halves, each with all of its loads in flight
+  int off[kCaSlots];
+  uint32_t mk0[kCaSlots], mk1[kCaSlots];
 #pragma unroll
-  for (int h = 0; h < TPW; h += TPW / 2) {
-    uint4 ld[TPW / 2][2];
-    uint32_t wd[TPW / 2];
-#pragma unroll
-    for (int k = h; k < h + TPW / 2; ++k) {
-      off[k] = -1;
-      mk[k] = 0u;
-      const int j = warp + k * nw;
-      if (j >= ntasks) continue;
-      int c, y0, rows;
-      ca_task(j, wtiles, tab, T, M, c, y0, rows);
-      if (lane >= rows) continue;
-      const int y = y0 + lane;
-      const int gx0 = ox + 32 * c, gy = oy + y;
-      off[k] = (y + M + 1) * P + c + 2;
-      mk[k] = (unsigned)gx0 < (unsigned)n ? chunk_members<32>(gx0, gy, n) : 0u;
-      if (mk[k] && pin) {  // a member word: its word tile is a member
-        const int64_t rec = j < wtiles ? srec + j : tile_record(gx0 >> 5, gy >> 5);
-        wd[k - h] = __ldg(pin + rec * 32 + (gy & 31));
-      } else if (mk[k]) {
-        const uint4* p = reinterpret_cast<const uint4*>(in + (size_t)gy * n + gx0);
-        ld[k - h][0] = __ldg(p);
-        ld[k - h][1] = __ldg(p + 1);
-      }
+  for (int k = 0; k < kCaSlots; ++k) {
+    off[k] = -1;
+    mk0[k] = mk1[k] = 0u;
+    const int j = hw + k * nh;
+    if (j >= ntasks) continue;
+    int c, y0, rows;
+    ca_task(j, wtiles, tab, T, ME, c, y0, rows);
+    if (2 * sub >= rows) continue;
+    const int y = y0 + 2 * sub;
+    const int gx0 = ox + 32 * c, gy = oy + y;
+    off[k] = (c + 2) * CW + y + kCaRow0;
+    if ((unsigned)gx0 < (unsigned)n) {
+      mk0[k] = chunk_members<32>(gx0, gy, n);
+      mk1[k] = chunk_members<32>(gx0, gy + 1, n);
     }
-#pragma unroll
-    for (int k = h; k < h + TPW / 2; ++k)
-      if (off[k] >= 0 && mk[k]) A[off[k]] = (pin ? wd[k - h] : pack32(ld[k - h][0], ld[k - h][1])) & mk[k];
+    uint32_t w0 = 0u, w1 = 0u;
+    if (pin) {  // a member word: its word tile is a member
+      if (mk0[k]) w0 = __ldg(pin + (j < wtiles ? srec + j : tile_record(gx0 >> 5, gy >> 5)) * 32 + (gy & 31));
+      if (mk1[k])
+        w1 = __ldg(pin + (j < wtiles ? srec + j : tile_record(gx0 >> 5, (gy + 1) >> 5)) * 32 + ((gy + 1) & 31));
+    } else {
+      uint4 r0[2], r1[2];
+      if (mk0[k]) {
+        const uint4* q = reinterpret_cast<const uint4*>(in + (size_t)gy * n + gx0);
+        r0[0] = __ldg(q);
+        r0[1] = __ldg(q + 1);
+      }
+      if (mk1[k]) {
+        const uint4* q = reinterpret_cast<const uint4*>(in + (size_t)(gy + 1) * n + gx0);
+        r1[0] = __ldg(q);
+        r1[1] = __ldg(q + 1);
+      }
+      if (mk0[k]) w0 = pack32(r0[0], r0[1]);
+      if (mk1[k]) w1 = pack32(r1[0], r1[1]);
+    }
+    *reinterpret_cast<uint2*>(A + off[k]) = make_uint2(w0 & mk0[k], w1 & mk1[k]);
   }
   __syncthreads();
 
@@ -209,10 +237,20 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
 #pragma unroll 4
   for (int t = 0; t < nsteps; ++t) {
 #pragma unroll
-    for (int k = 0; k < TPW; ++k) {
+    for (int k = 0; k < kCaSlots; ++k) {
       if (off[k] < 0) continue;
       const uint32_t* p = A + off[k];
-      B[off[k]] = life_rule_words(p[-P - 1], p[-P], p[-P + 1], p[-1], p[0], p[1], p[P - 1], p[P], p[P + 1]) & mk[k];
+      uint32_t s[4], q[4];  // horizontal sums of rows y-1 .. y+2
+      const uint2 cm = *reinterpret_cast<const uint2*>(p);
+      const uint2 lm = *reinterpret_cast<const uint2*>(p - CW);
+      const uint2 rm = *reinterpret_cast<const uint2*>(p + CW);
+      row_sum3(p[-CW - 1], p[-1], p[CW - 1], s[0], q[0]);
+      row_sum3(lm.x, cm.x, rm.x, s[1], q[1]);
+      row_sum3(lm.y, cm.y, rm.y, s[2], q[2]);
+      row_sum3(p[-CW + 2], p[2], p[CW + 2], s[3], q[3]);
+      const uint32_t o0 = life_rule_mod4(s[0], q[0], s[1], q[1], s[2], q[2], cm.x, mk0[k]);
+      const uint32_t o1 = life_rule_mod4(s[1], q[1], s[2], q[2], s[3], q[3], cm.y, mk1[k]);
+      *reinterpret_cast<uint2*>(B + off[k]) = make_uint2(o0, o1);
     }
     __syncthreads();
     uint32_t* tmp = A;
@@ -223,28 +261,32 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
   // write back the word tiles (whole 32-byte row segments); count the alive
   unsigned alive = 0;
 #pragma unroll
-  for (int k = 0; k < TPW; ++k) {
-    const int j = warp + k * nw;
+  for (int k = 0; k < kCaSlots; ++k) {
+    const int j = hw + k * nh;
     if (off[k] < 0 || j >= wtiles) continue;
-    const int c = off[k] % P - 2, y = off[k] / P - M - 1;
-    const uint32_t w = A[off[k]];
-    alive += __popc(w);
-    if (pout) {  // record of word tile j, row y mod 32
-      pout[(srec + j) * 32 + (y & 31)] = w;
+    const int c = off[k] / CW - 2, y = off[k] % CW - kCaRow0;
+    const uint2 w = *reinterpret_cast<const uint2*>(A + off[k]);
+    alive += __popc(w.x) + __popc(w.y);
+    if (pout) {  // record of word tile j, rows y, y + 1 mod 32
+      *reinterpret_cast<uint2*>(pout + (srec + j) * 32 + (y & 31)) = w;
       continue;
     }
-    uint4 v0, v1;
-    v0.x = spread4(w);
-    v0.y = spread4(w >> 4);
-    v0.z = spread4(w >> 8);
-    v0.w = spread4(w >> 12);
-    v1.x = spread4(w >> 16);
-    v1.y = spread4(w >> 20);
-    v1.z = spread4(w >> 24);
-    v1.w = spread4(w >> 28);
-    uint4* q = reinterpret_cast<uint4*>(out + (size_t)(oy + y) * n + ox + 32 * c);
-    q[0] = v0;
-    q[1] = v1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t v = h ? w.y : w.x;
+      uint4 v0, v1;
+      v0.x = spread4(v);
+      v0.y = spread4(v >> 4);
+      v0.z = spread4(v >> 8);
+      v0.w = spread4(v >> 12);
+      v1.x = spread4(v >> 16);
+      v1.y = spread4(v >> 20);
+      v1.z = spread4(v >> 24);
+      v1.w = spread4(v >> 28);
+      uint4* q = reinterpret_cast<uint4*>(out + (size_t)(oy + y + h) * n + ox + 32 * c);
+      q[0] = v0;
+      q[1] = v1;
+    }
   }
   if (partials) {  // alive members of the result, per CTA (uniform branch)
     const unsigned long long s = block_sum<unsigned long long>(alive, red);
@@ -274,23 +316,25 @@ cudaError_t go(const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int
 }  // namespace
 
 int ca_fused_smem_bytes(const Geo& g, int margin) {
+  (void)margin;  // the image covers the largest margin
   const int wlev = ilog2c(g.T) - 5;
   int wtiles = 1;
   for (int i = 0; i < wlev; ++i) wtiles *= 3;
-  return tab_words(wtiles) * 4 + 2 * ca_image_words(g.T, margin) * 4;
+  return tab_words(wtiles) * 4 + 2 * ca_image_words(g.T) * 4;
 }
 
-// Warps of a fused automaton launch: the fewest that give every warp the
-// least number of tasks; 0 if the super-tile does not fit the kernel.
+// Warps of a fused automaton launch: the fewest half warps that give every
+// half warp the least number of tasks; 0 if the super-tile does not fit the
+// kernel.
 int ca_fused_threads(const Geo& g, int margin) {
   if (g.T < 32 || g.T > 512 || margin < 1 || margin > 31 || 2 * margin > g.T) return 0;
   int wtiles = 1;
   for (int i = 0; i < ilog2c(g.T) - 5; ++i) wtiles *= 3;
   const int tasks = ca_tasks(wtiles);
-  const int per = (tasks + 15) / 16;  // with 16 warps
-  if (per > kCaTasksPerWarp) return 0;
-  const int warps = (tasks + per - 1) / per;
-  return 32 * warps;
+  const int per = (tasks + 31) / 32;  // with 16 warps
+  if (per > kCaSlots) return 0;
+  const int halves = (tasks + per - 1) / per;
+  return 32 * ((halves + 1) / 2);
 }
 
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,

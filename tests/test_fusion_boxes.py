@@ -134,3 +134,29 @@ def test_member_blocks_of_the_boxes_are_few(M):
         cnt = _active_box_blocks(16, T, M)
         assert cnt.max() <= cap, (T, M, cnt.max())
         assert cnt.max() == cap           # and the bound is reached
+
+
+@pytest.mark.parametrize("k", range(2, 13))
+def test_member_cells_have_at_most_five_member_neighbours(k):
+    """The fused automaton sums the nine-cell neighbourhood modulo 4.  That
+    decides B3/S23 on the gasket because no member cell has more than five
+    member neighbours (non-members hold 0 for ever), so the nine-cell sum is at
+    most 6 and its residue mod 4 separates 3 (alive next) and 4 (alive next if
+    alive now) from every other value.  Brute-force count of member neighbours
+    of every member cell of the level-k gasket; five occurs (from level 3 on),
+    six never."""
+    n = 1 << k
+    m = oracle.member_mask(n).astype(np.int32)
+    p = np.pad(m, 1)
+    count = sum(p[1 + dy:1 + dy + n, 1 + dx:1 + dx + n]
+                for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0))
+    assert count[m == 1].max() == (4 if k == 2 else 5)
+
+
+def test_mod4_rule_matches_b3s23_for_sums_up_to_six():
+    """The residue form of the rule, for every neighbour count 0..5 and state:
+    alive next iff m == 3, or m == 0 and alive now, m = (count + self) mod 4."""
+    for count in range(6):
+        for self_ in (0, 1):
+            m = (count + self_) % 4
+            assert (m == 3 or (m == 0 and self_ == 1)) == (count == 3 or (count == 2 and self_ == 1))
