@@ -193,10 +193,12 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
   const int ntasks = ca_tasks(wtiles);
   int off[kCaSlots];
   uint32_t mk0[kCaSlots], mk1[kCaSlots];
+  uint2 own[kCaSlots];  // the pair's words (the lane is their only writer)
 #pragma unroll
   for (int k = 0; k < kCaSlots; ++k) {
     off[k] = -1;
     mk0[k] = mk1[k] = 0u;
+    own[k] = make_uint2(0u, 0u);
     const int j = hw + k * nh;
     if (j >= ntasks) continue;
     int c, y0, rows;
@@ -229,7 +231,8 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
       if (mk0[k]) w0 = pack32(r0[0], r0[1]);
       if (mk1[k]) w1 = pack32(r1[0], r1[1]);
     }
-    *reinterpret_cast<uint2*>(A + off[k]) = make_uint2(w0 & mk0[k], w1 & mk1[k]);
+    own[k] = make_uint2(w0 & mk0[k], w1 & mk1[k]);
+    *reinterpret_cast<uint2*>(A + off[k]) = own[k];
   }
   __syncthreads();
 
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
       if (off[k] < 0) continue;
       const uint32_t* p = A + off[k];
       uint32_t s[4], q[4];  // horizontal sums of rows y-1 .. y+2
-      const uint2 cm = *reinterpret_cast<const uint2*>(p);
+      const uint2 cm = own[k];
       const uint2 lm = *reinterpret_cast<const uint2*>(p - CW);
       const uint2 rm = *reinterpret_cast<const uint2*>(p + CW);
       row_sum3(p[-CW - 1], p[-1], p[CW - 1], s[0], q[0]);
@@ -250,7 +253,8 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
       row_sum3(p[-CW + 2], p[2], p[CW + 2], s[3], q[3]);
       const uint32_t o0 = life_rule_mod4(s[0], q[0], s[1], q[1], s[2], q[2], cm.x, mk0[k]);
       const uint32_t o1 = life_rule_mod4(s[1], q[1], s[2], q[2], s[3], q[3], cm.y, mk1[k]);
-      *reinterpret_cast<uint2*>(B + off[k]) = make_uint2(o0, o1);
+      own[k] = make_uint2(o0, o1);
+      *reinterpret_cast<uint2*>(B + off[k]) = own[k];
     }
     __syncthreads();
     uint32_t* tmp = A;
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     const int j = hw + k * nh;
     if (off[k] < 0 || j >= wtiles) continue;
     const int c = off[k] / CW - 2, y = off[k] % CW - kCaRow0;
-    const uint2 w = *reinterpret_cast<const uint2*>(A + off[k]);
+    const uint2 w = own[k];
     alive += __popc(w.x) + __popc(w.y);
     if (pout) {  // record of word tile j, rows y, y + 1 mod 32
       *reinterpret_cast<uint2*>(pout + (srec + j) * 32 + (y & 31)) = w;
