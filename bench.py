@@ -518,21 +518,30 @@ def ca_box_member_words(k, T, M):
     return total
 
 
-def diffusion_box_member_blocks(k, T, M):
+def diffusion_box_member_blocks(k, T, M, reach=None):
     """Member 8 x 8 blocks in the margin boxes (width M) of every member
-    super-tile of side T: what a fused diffusion launch reads besides the
-    super-tiles' own member blocks."""
+    super-tile of side T whose nearest cell is within `reach` cells
+    (Manhattan) of the super-tile (default M): what a fused diffusion launch
+    serving up to `reach` steps reads besides the super-tiles' own member
+    blocks."""
     import numpy as np
+    reach = M if reach is None else reach
     nblk = (1 << k) // 8
     s = (1 << k) // T
     sy, sx = np.nonzero((np.arange(s)[None, :] & np.arange(s)[:, None]) == 0)
     OX, OY = sx * (T // 8), sy * (T // 8)
     W, side = M // 8, T // 8
     boxes = [(-W, 0, 0, W), (0, W, -W, 0), (side, side + W, -W, W), (-W, W, side, side + W)]
+
+    def gap(b):  # cells from the block's nearest cell to the super-tile, along one axis
+        return -8 * b - 7 if b < 0 else 8 * (b - side) + 1 if b >= side else 0
+
     total = 0
     for x0, x1, y0, y1 in boxes:
         for by in range(y0, y1):
             for bx in range(x0, x1):
+                if gap(bx) + gap(by) > reach:
+                    continue
                 gx, gy = OX + bx, OY + by
                 ok = (gx >= 0) & (gx < nblk) & (gy >= 0) & (gy < nblk) & ((gx & gy) == 0)
                 total += int(np.count_nonzero(ok))
@@ -630,7 +639,7 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps, every=N
             margin = 8
             while margin < spl:         # the kernel's margin: a power of two >= max(8, spl)
                 margin *= 2
-            box = diffusion_box_member_blocks(info["k"], T, margin)
+            box = diffusion_box_member_blocks(info["k"], T, margin, spl)
         else:
             box = ca_box_member_words(info["k"], T, spl)
         alg = sum(fused_launch_bytes(wl, kd, info["k"], box) for kd in kinds) / len(kinds)

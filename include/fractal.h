@@ -167,15 +167,32 @@ int fractal_plan_autotune(fractal_plan_t plan, int dtype, const void* dev_in, vo
  * records of 128 bytes (uint8: the 32 words of a member 32 x 32 word tile),
  * freed with the plan: only the first launch reads dev_a and only the last
  * writes the result buffer; the other caller buffer is then not written.
+ * Margin-box blocks farther than spl cells from the super-tile are not staged
+ * (fractal_fused_box_blocks).
  * For float32 the call also writes, once, the setup of every thread of the
  * fused launch (its block, port owners and neighbours: 16 bytes a thread,
- * 37 MB at k = 16, rho = 8), which every fused launch then reads instead of
+ * 34 MB at k = 16, rho = 8, spl = 50), which every fused launch then reads instead of
  * computing it; it waits for the device first (no call of this plan may be
  * in flight) and for that launch after.
  * Errors: FRACTAL_EINVAL (dtype, spl, or no fused kernel for this plan),
  * FRACTAL_ENOMEM, FRACTAL_ECUDA.
  */
 int fractal_plan_set_steps_per_launch(fractal_plan_t plan, int dtype, int spl);
+
+/*
+ * fractal_fused_box_blocks -- margin-box blocks a float32 fused launch stages
+ * per super-tile (host only; no device is touched).  A launch serving up to
+ * `reach` steps (reach = spl) stages, besides the member 8 x 8 blocks of its
+ * super-tile of side `supertile` cells, the member blocks of its margin boxes
+ * (width `margin` = the smallest power of two >= max(spl, 8)) whose nearest
+ * cell lies within `reach` cells (Manhattan distance, the reach of `reach`
+ * 4-neighbour steps) of the super-tile: farther blocks cannot influence the
+ * super-tile within the launch.  Returns the most such blocks any member
+ * super-tile has (the launch gives each a thread slot), or FRACTAL_EINVAL
+ * (supertile not a power of two in [16, 256], margin not 8 times a power of
+ * two up to 128 or above supertile / 2, reach outside [1, margin]).
+ */
+int fractal_fused_box_blocks(int supertile, int margin, int reach);
 
 /*
  * Device status word of the plan's TMA kernels: 0, or the first error a CTA

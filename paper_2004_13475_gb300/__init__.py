@@ -47,6 +47,7 @@ EXPORTS = (
     "fractal_step_ca_count", "fractal_step_diffusion_sum", "fractal_map_blocks_method",
     "fractal_pack", "fractal_unpack",
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
+    "fractal_fused_box_blocks",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -120,6 +121,7 @@ def _load() -> ctypes.CDLL:
         "fractal_reduce": (I, [P, VP, I, ctypes.POINTER(D), VP]),
         "fractal_reduce_async": (I, [P, VP, I, VP, VP]),
         "fractal_set_l2_fetch_granularity": (I, [I]),
+        "fractal_fused_box_blocks": (I, [I, I, I]),
         "fractal_get_l2_fetch_granularity": (I, [ctypes.POINTER(I)]),
         "fractal_plan_set_schedule": (I, [P, I]),
         "fractal_plan_device_status": (I, [P, ctypes.POINTER(I)]),
@@ -343,6 +345,14 @@ def fractal_unpack(plan: Plan, packed, dtype: int, embedded, stream=None) -> Non
     """Inverse of fractal_pack: writes the member tiles of `embedded`."""
     _check(_load().fractal_unpack(plan.handle, _ptr(packed), int(dtype), _ptr(embedded), _stream(stream)),
            "fractal_unpack")
+
+
+def fractal_fused_box_blocks(supertile: int, margin: int, reach: int) -> int:
+    """Margin-box blocks a float32 fused launch stages per super-tile (host only)."""
+    r = _load().fractal_fused_box_blocks(int(supertile), int(margin), int(reach))
+    if r < 0:
+        _check(r, "fractal_fused_box_blocks")
+    return r
 
 
 def fractal_set_l2_fetch_granularity(nbytes: int) -> None:

@@ -141,8 +141,8 @@ bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step,
     Launch st;
     if (!supertile_grid(p.k, p.log_rho, p.mode, m, st)) continue;
     if (st.geo.T < 2 * margin) break;
-    const int threads = fused_threads(st.geo, rho, margin);
-    const int smem = fused_smem_bytes(st.geo, margin);
+    const int threads = fused_threads(st.geo, rho, margin, spl);
+    const int smem = fused_smem_bytes(st.geo, margin, spl);
     if (threads > 0 && smem <= kMaxSmem) {
       fused = st;
       fused.threads = threads;
@@ -357,7 +357,8 @@ int build_descriptors(fractal_plan_s* p, cudaStream_t s, bool sync) {
     }
     p->desc_cap = need;
   }
-  cudaError_t e = launch_fused_describe(p->mode, p->log_rho, fused_margin(p->spl[FRACTAL_F32]), F, p->d_desc, s);
+  cudaError_t e = launch_fused_describe(p->mode, p->log_rho, fused_margin(p->spl[FRACTAL_F32]), p->spl[FRACTAL_F32], F,
+                                        p->d_desc, s);
   if (e == cudaSuccess && sync) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "describe");
   p->desc_ok = true;
@@ -502,7 +503,7 @@ int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, 
       const int seg = i / per, l = i % per;
       const bool first = i == 0, last = i == total - 1;
       double* part = l == per - 1 && dev_sums ? static_cast<double*>(p->d_partials) : nullptr;
-      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), F, first ? a : nullptr,
+      cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), spl, F, first ? a : nullptr,
                                              last ? buf[steps & 1] : nullptr, coef, base + (l < extra ? 1 : 0), st,
                                              part, first ? nullptr : p->d_pack[(i - 1) & 1],
                                              last ? nullptr : p->d_pack[i & 1], desc);
@@ -709,6 +710,13 @@ static int set_levels(fractal_plan_t p, int dtype, int levels) {
   return st;
 }
 
+int fractal_fused_box_blocks(int supertile, int margin, int reach) {
+  if (supertile < 16 || supertile > 256 || (supertile & (supertile - 1)) != 0 || margin < 8 || margin > 128 ||
+      (margin & (margin - 1)) != 0 || 2 * margin > supertile || reach < 1 || reach > margin)
+    return FRACTAL_EINVAL;
+  return box_cap_reach(ilog2c(supertile) - 3, margin / 8, reach);
+}
+
 int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
   if (!p || (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) || spl < 1 || spl > max_spl(dtype)) return FRACTAL_EINVAL;
   if (dtype == FRACTAL_F32) p->desc_ok = false;
@@ -779,7 +787,7 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
                               last ? (uint8_t*)dev_scratch : nullptr, ns, spl, st, nullptr,
                               first ? nullptr : p->d_bits[(i - 1) & 1], last ? nullptr : p->d_bits[i & 1]);
         } else {
-          e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), F,
+          e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), spl, F,
                                      first ? (const float*)dev_in : nullptr, last ? (float*)dev_scratch : nullptr,
                                      0.2f, ns, st, nullptr, first ? nullptr : p->d_pack[(i - 1) & 1],
                                      last ? nullptr : p->d_pack[i & 1], desc);
@@ -792,7 +800,7 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
       const cudaError_t e =
           dtype == FRACTAL_U8
               ? launch_ca_fused(p->mode, p->fused[dtype], (const uint8_t*)dev_in, (uint8_t*)dev_scratch, spl, spl, st)
-              : launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), p->fused[dtype],
+              : launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), spl, p->fused[dtype],
                                        (const float*)dev_in, (float*)dev_scratch, 0.2f, spl, st);
       return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "autotune");
     }

@@ -62,12 +62,12 @@ void drop_graph(fractal_batch_s* b) {
   b->graph_steps = 0;
 }
 
-// Threads for side T and margin M (0 if invalid for this batch).
-int batch_threads(const fractal_batch_s* b, int T, int margin) {
+// Threads for side T, margin M and reach (0 if invalid for this batch).
+int batch_threads(const fractal_batch_s* b, int T, int margin, int reach) {
   if (T < 16 || (T & (T - 1)) != 0 || T > (1 << b->kmin)) return 0;
   Geo g{};
   g.T = T;
-  return fused_threads(g, 0, margin);
+  return fused_threads(g, 0, margin, reach);
 }
 
 // Offsets, R and the persistent grid for the current T; table upload if bound.
@@ -115,7 +115,7 @@ int rebuild(fractal_batch_s* b) {
       }
     }
     if (b->d_desc) {
-      if (launch_batch_describe(b->d_inst, b->count, b->items, b->margin, b->T, b->ctas, b->threads, b->d_desc,
+      if (launch_batch_describe(b->d_inst, b->count, b->items, b->margin, b->spl, b->T, b->ctas, b->threads, b->d_desc,
                                 nullptr) != cudaSuccess ||
           cudaStreamSynchronize(nullptr) != cudaSuccess) {
         cudaGetLastError();
@@ -143,7 +143,7 @@ int launch_steps(fractal_batch_s* b, float a, int steps, cudaStream_t s) {
     float* pout = rec && !last ? b->d_rec[i & 1] : nullptr;
     // which = 0: a -> b, 1: b -> a (in / out where they are the buffers)
     const int which = !rec ? (i & 1) : (first ? 0 : ((steps & 1) == 0 ? 1 : 0));
-    const cudaError_t e = launch_diffusion_batch(b->d_inst, b->count, b->items, which, a, ns, b->margin, b->T,
+    const cudaError_t e = launch_diffusion_batch(b->d_inst, b->count, b->items, which, a, ns, b->margin, b->spl, b->T,
                                                  b->ctas, b->threads, s, pin, pout,
                                                  b->desc_ok ? b->d_desc : nullptr);
     if (e != cudaSuccess) return FRACTAL_ECUDA;
@@ -180,7 +180,7 @@ int fractal_batch_create(int count, const int32_t* ks, fractal_batch_t* out) {
   b->spl = 8;
   b->margin = fused_margin(8);
   b->T = 1 << (b->kmin < 8 ? b->kmin : 8);
-  b->threads = batch_threads(b, b->T, b->margin);
+  b->threads = batch_threads(b, b->T, b->margin, b->spl);
   if (b->threads == 0) {
     delete b;
     return FRACTAL_EINVAL;
@@ -247,7 +247,7 @@ int fractal_batch_configure(fractal_batch_t b, int supertile, int spl) {
   if (!b || spl < 1 || spl > 32 || supertile < 0) return FRACTAL_EINVAL;
   const int T = supertile ? supertile : b->T;
   const int margin = fused_margin(spl);
-  const int threads = batch_threads(b, T, margin);
+  const int threads = batch_threads(b, T, margin, spl);
   if (threads == 0) return FRACTAL_EINVAL;
   drop_graph(b);
   b->T = T;
@@ -303,7 +303,7 @@ int fractal_batch_autotune(fractal_batch_t b, float a, int reps, float* best_us,
       if (fractal_batch_configure(b, T, spls[si]) != FRACTAL_OK) continue;
       // launches of spl steps, dev_a -> dev_b only (which = 0)
       auto one = [&]() -> int {
-        return launch_diffusion_batch(b->d_inst, b->count, b->items, 0, a, b->spl, b->margin, b->T, b->ctas,
+        return launch_diffusion_batch(b->d_inst, b->count, b->items, 0, a, b->spl, b->margin, b->spl, b->T, b->ctas,
                                       b->threads, st, nullptr, nullptr, b->desc_ok ? b->d_desc : nullptr) ==
                        cudaSuccess
                    ? FRACTAL_OK

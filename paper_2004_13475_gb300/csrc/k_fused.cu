@@ -29,6 +29,8 @@
 // with one barrier each, and writes the member blocks back; for rho >= 8 it
 // also writes the zeros of the non-member cells of member tiles, so that every
 // write covers whole 32-byte sectors.
+#include <atomic>
+
 #include "blocks.cuh"
 #include "launch.h"
 
@@ -50,6 +52,7 @@ struct FGeo {
   int W;        // box width in blocks: M / 8
   int lW;       // log2 W
   int nbox;     // box blocks: 6 W^2
+  int reach;    // steps per launch served: box blocks further than this are not staged
   int log_rho;  // the plan's tile side (write-back of whole member tiles)
   int R;        // super-tile levels of the array: (k - 3) - L
   int lwR;      // 3^ceil(R/2): width of the level-R packed grid of super-tiles
@@ -157,6 +160,18 @@ __device__ __forceinline__ int fused_owner(int bx, int by, const FGeo& f, const 
 
 __device__ __forceinline__ bool block_member(int gx, int gy, int nblk) {
   return (unsigned)gx < (unsigned)nblk && (unsigned)gy < (unsigned)nblk && (gx & gy) == 0;
+}
+
+// Manhattan distance from the nearest cell of block (qx, qy) (block
+// coordinates relative to the super-tile) to the super-tile [0, 8 side)^2.
+// Influence moves one cell per step along 4-neighbour links, so a launch of
+// s steps needs no box block further than s: a block it leaves out is read
+// as 0 by its neighbours, and the error that starts there (at distance >= s)
+// reaches the super-tile only after more than s steps.
+__host__ __device__ inline int box_distance(int qx, int qy, int side) {
+  const int dx = qx < 0 ? -kB * qx - kB + 1 : qx >= side ? kB * (qx - side) + 1 : 0;
+  const int dy = qy < 0 ? -kB * qy - kB + 1 : qy >= side ? kB * (qy - side) + 1 : 0;
+  return dx + dy;
 }
 
 // Port slots: P0 = (0,0), PR = (7,0), PD = (0,7) of every block, double-
@@ -321,7 +336,7 @@ __device__ __forceinline__ FSetup fused_setup(const FGeo& f, int OX, int OY, con
     if (b < f.nbox) {
       int qx, qy;
       box_block(b, f, qx, qy);
-      m = block_member(OX + qx, OY + qy, nblk);
+      m = block_member(OX + qx, OY + qy, nblk) && box_distance(qx, qy, 1 << f.L) <= f.reach;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, m);
     if ((t & 31) == 0) wcnt[t >> 5] = __popc(bal);
@@ -339,7 +354,7 @@ __device__ __forceinline__ FSetup fused_setup(const FGeo& f, int OX, int OY, con
     nbox_member += total;
     __syncthreads();
   }
-  if (t >= f.nb && t - f.nb < nbox_member && t - f.nb < box_cap(f.W)) {
+  if (t >= f.nb && t - f.nb < nbox_member) {
     box_block(boxlist[t - f.nb], f, s.bx, s.by);
     s.active = true;
     s.rec = (int)block_record<MODE>(OX + s.bx, OY + s.by, f);
@@ -530,7 +545,7 @@ __device__ __forceinline__ double fused_supertile2(const float* __restrict__ in,
   return sum;
 }
 
-__device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho, int R) {
+__device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int reach, int log_rho, int R) {
   FGeo f;
   f.n = n;
   f.L = ilog2c(T) - 3;
@@ -542,6 +557,7 @@ __device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int log_rho, int 
   f.W = M / kB;
   f.lW = ilog2c(f.W);
   f.nbox = 6 * f.W * f.W;
+  f.reach = reach;
   f.log_rho = log_rho;
   f.R = R;
   f.rec0 = 0;
@@ -562,7 +578,8 @@ __device__ __forceinline__ void bb_table(int* tab, const FGeo& f) {
 
 template <int MODE, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                              float a, int nsteps, int M, int log_rho, Geo g,
+                                                              float a, int nsteps, int M, int reach, int log_rho,
+                                                              Geo g,
                                                               double* __restrict__ partials,
                                                               const float* __restrict__ pin,
                                                               float* __restrict__ pout,
@@ -574,7 +591,7 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
     if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
     return;
   }
-  const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
+  const FGeo f = make_fgeo(g.n, g.T, M, reach, log_rho, g.R);
   float* ports = fsm;
   int* tab = reinterpret_cast<int*>(fsm + 6 * fused_slots(MAXT));
   if (MODE == kBB && !desc) {
@@ -598,7 +615,7 @@ __global__ void __launch_bounds__(MAXT, MINB) diffusion_fused_kernel(const float
 template <int MODE, int PMAX, int MINB>
 __global__ void __launch_bounds__(PMAX, MINB) diffusion_fused2_kernel(const float* __restrict__ in,
                                                                    float* __restrict__ out, float a, int nsteps, int M,
-                                                                   int log_rho, Geo g, double* __restrict__ partials,
+                                                                   int reach, int log_rho, Geo g, double* __restrict__ partials,
                                                                    const float* __restrict__ pin,
                                                                    float* __restrict__ pout,
                                                                    const int4* __restrict__ desc) {
@@ -609,7 +626,7 @@ __global__ void __launch_bounds__(PMAX, MINB) diffusion_fused2_kernel(const floa
     if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
     return;
   }
-  const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
+  const FGeo f = make_fgeo(g.n, g.T, M, reach, log_rho, g.R);
   const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
   const double mine = fused_supertile2<MODE, 2 * PMAX + 2>(in, out, a, nsteps, f, sx << f.L, sy << f.L, fsm,
                                                            partials != nullptr, pin, pout, st * f.nb,
@@ -636,7 +653,7 @@ __device__ __forceinline__ int batch_instance(const BatchInst* __restrict__ inst
 
 __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst* __restrict__ inst, int count,
                                                               int64_t items, int which, float a, int nsteps, int M,
-                                                              int T, const float* __restrict__ pin,
+                                                              int reach, int T, const float* __restrict__ pin,
                                                               float* __restrict__ pout,
                                                               const int4* __restrict__ desc) {
   extern __shared__ __align__(16) float fsm[];
@@ -645,7 +662,7 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
     const int64_t om = w - I.first;
     int sx, sy;
     warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
-    FGeo f = make_fgeo(I.n, T, M, 3, I.R);
+    FGeo f = make_fgeo(I.n, T, M, reach, 3, I.R);
     f.rec0 = I.first * f.nb;  // item w's records start at w * nb
     fused_supertile<kLambda, 289>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps,
                               f, sx << f.L, sy << f.L, nullptr, fsm, false, pin, pout, w * f.nb,
@@ -655,13 +672,14 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
 
 // The batch launch's per-thread setups, item by item (w * blockDim.x + t).
 __global__ void __launch_bounds__(288) batch_describe_kernel(const BatchInst* __restrict__ inst, int count,
-                                                             int64_t items, int M, int T, int4* __restrict__ desc) {
+                                                             int64_t items, int M, int reach, int T,
+                                                             int4* __restrict__ desc) {
   for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
     const BatchInst I = inst[batch_instance(inst, count, w)];
     const int64_t om = w - I.first;
     int sx, sy;
     warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
-    FGeo f = make_fgeo(I.n, T, M, 3, I.R);
+    FGeo f = make_fgeo(I.n, T, M, reach, 3, I.R);
     f.rec0 = I.first * f.nb;
     const FSetup s = fused_setup<kLambda>(f, sx << f.L, sy << f.L, nullptr);
     desc[w * blockDim.x + threadIdx.x] = pack_setup(s);
@@ -728,11 +746,12 @@ __global__ void batch_sums_kernel(const BatchInst* __restrict__ inst, int count,
 // CTA per member super-tile): the setup every launch of the configuration
 // would compute, written once.
 template <int MODE>
-__global__ void __launch_bounds__(512) fused_describe_kernel(Geo g, int M, int log_rho, int4* __restrict__ desc) {
+__global__ void __launch_bounds__(512) fused_describe_kernel(Geo g, int M, int reach, int log_rho,
+                                                             int4* __restrict__ desc) {
   extern __shared__ __align__(16) float fsm[];
   int sx, sy;
   if (!cta_supertile<MODE>(g, sx, sy)) return;
-  const FGeo f = make_fgeo(g.n, g.T, M, log_rho, g.R);
+  const FGeo f = make_fgeo(g.n, g.T, M, reach, log_rho, g.R);
   int* tab = reinterpret_cast<int*>(fsm);
   if (MODE == kBB) {
     bb_table(tab, f);
@@ -744,13 +763,13 @@ __global__ void __launch_bounds__(512) fused_describe_kernel(Geo g, int M, int l
 }
 
 template <int MODE>
-cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
+cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int reach, int log_rho,
                double* partials, const float* pin, float* pout, const int4* desc, cudaStream_t s) {
   // the smallest CTA class that holds the launch: more CTAs per SM
   auto run = [&](auto* k) -> cudaError_t {
     cudaError_t e = allow_smem((const void*)k, L.smem);
     if (e != cudaSuccess) return e;
-    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials, pin, pout, desc);
+    k<<<L.grid, L.threads, L.smem, s>>>(in, out, a, nsteps, margin, reach, log_rho, L.geo, partials, pin, pout, desc);
     return cudaGetLastError();
   };
   if (L.threads <= 288) return run(diffusion_fused_kernel<MODE, 288, 4>);
@@ -761,16 +780,17 @@ cudaError_t go(const Launch& L, const float* in, float* out, float a, int nsteps
 // Two blocks per thread (with descriptors): L.threads / 2 threads, in the
 // class holding them; ports of 2 * class + 2 slots per parity.
 template <int MODE>
-cudaError_t go2(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int log_rho,
+cudaError_t go2(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int reach, int log_rho,
                 double* partials, const float* pin, float* pout, const int4* desc, cudaStream_t s) {
   const int threads = L.threads / 2;
   auto run = [&](auto* k, int pmax) -> cudaError_t {
     const int smem = 6 * (2 * pmax + 2) * 4;
     cudaError_t e = allow_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
-    k<<<L.grid, threads, smem, s>>>(in, out, a, nsteps, margin, log_rho, L.geo, partials, pin, pout, desc);
+    k<<<L.grid, threads, smem, s>>>(in, out, a, nsteps, margin, reach, log_rho, L.geo, partials, pin, pout, desc);
     return cudaGetLastError();
   };
+  if (threads <= 160) return run(diffusion_fused2_kernel<MODE, 160, 4>, 160);
   if (threads <= 176) return run(diffusion_fused2_kernel<MODE, 176, 3>, 176);
   return run(diffusion_fused2_kernel<MODE, 256, 2>, 256);
 }
@@ -792,21 +812,60 @@ int fused_margin(int steps_per_launch) {
   return m;
 }
 
+// Member blocks of the margin boxes within `reach` of the super-tile
+// (box_distance), the most any member super-tile has: counted over every
+// member super-tile of a 64 x 64 grid of super-tiles.  Which box blocks are
+// members depends only on which of the super-tile's eight neighbours are
+// members (and on the array's edge, which only removes blocks), and every
+// such neighbourhood of the gasket occurs in that grid.  Cached.
+int box_cap_reach(int L, int W, int reach) {
+  static std::atomic<int> cache[6][kMaxW + 1][129];
+  if (L < 1 || L > 5 || W < 1 || W > kMaxW) return 0;
+  reach = reach < 0 ? 0 : reach > 128 ? 128 : reach;
+  const int hit = cache[L][W][reach].load(std::memory_order_relaxed);
+  if (hit > 0) return hit - 1;
+  const int side = 1 << L, W2 = W * W;
+  constexpr int kGrid = 64;
+  const int nblk = kGrid * side;
+  int best = 0;
+  for (int sy = 0; sy < kGrid; ++sy)
+    for (int sx = 0; sx < kGrid; ++sx) {
+      if (sx & sy) continue;
+      int c = 0;
+      for (int b = 0; b < 6 * W2; ++b) {
+        int qx, qy, r = b;
+        if (r < W2) { qx = -W + r % W; qy = r / W; }
+        else if ((r -= W2) < W2) { qx = r % W; qy = -W + r / W; }
+        else if ((r -= W2) < 2 * W2) { qx = side + r % W; qy = -W + r / W; }
+        else { r -= 2 * W2; qx = -W + r % (2 * W); qy = side + r / (2 * W); }
+        const int gx = sx * side + qx, gy = sy * side + qy;
+        if (gx < 0 || gy < 0 || gx >= nblk || gy >= nblk || (gx & gy) != 0) continue;
+        if (box_distance(qx, qy, side) <= reach) ++c;
+      }
+      best = c > best ? c : best;
+    }
+  cache[L][W][reach].store(best + 1, std::memory_order_relaxed);
+  return best;
+}
+
 // Threads of a fused launch: one per member block of the super-tile and per
-// member block the margin boxes can hold, rounded up to whole warps; 0 if the
-// super-tile does not fit (side < 16 or < 2 M, a margin that is not 8 times
-// a power of two up to 128, more than kFusedMaxThreads threads).
-int fused_threads(const Geo& g, int rho, int margin) {
+// member block of the margin boxes within `reach` (the steps per launch the
+// configuration serves, at most the margin), rounded up to whole warps; 0 if
+// the super-tile does not fit (side < 16 or < 2 M, a margin that is not 8
+// times a power of two up to 128, a reach outside [1, M], more than
+// kFusedMaxThreads threads).
+int fused_threads(const Geo& g, int rho, int margin, int reach) {
   (void)rho;
   const int W = margin / kB;
-  if (g.T < 2 * kB || g.T < 2 * margin || margin < kB || margin % kB != 0 || W > kMaxW || (W & (W - 1)) != 0)
+  if (g.T < 2 * kB || g.T < 2 * margin || margin < kB || margin % kB != 0 || W > kMaxW || (W & (W - 1)) != 0 ||
+      reach < 1 || reach > margin)
     return 0;
-  const int t = (member_blocks(g.T) + box_cap(W) + 31) / 32 * 32;
+  const int t = (member_blocks(g.T) + box_cap_reach(ilog2c(g.T) - 3, W, reach) + 31) / 32 * 32;
   return t > kFusedMaxThreads ? 0 : t;
 }
 
-int fused_smem_bytes(const Geo& g, int margin) {
-  return 6 * fused_slots(fused_class(fused_threads(g, 0, margin))) * 4 + member_blocks(g.T) * 4;
+int fused_smem_bytes(const Geo& g, int margin, int reach) {
+  return 6 * fused_slots(fused_class(fused_threads(g, 0, margin, reach))) * 4 + member_blocks(g.T) * 4;
 }
 
 int fused_batch_smem_bytes(int threads) {
@@ -816,24 +875,24 @@ int fused_batch_smem_bytes(int threads) {
 
 const void* fused_batch_kernel() { return (const void*)diffusion_batch_kernel; }
 
-cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t items, int margin, int T, int ctas,
-                                  int threads, int4* desc, cudaStream_t s) {
+cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t items, int margin, int reach, int T,
+                                  int ctas, int threads, int4* desc, cudaStream_t s) {
   Geo g{};
   g.T = T;
-  if (fused_threads(g, 0, margin) != threads || threads > 288 || ctas < 1) return cudaErrorInvalidValue;
-  batch_describe_kernel<<<ctas, threads, 0, s>>>(inst, count, items, margin, T, desc);
+  if (fused_threads(g, 0, margin, reach) != threads || threads > 288 || ctas < 1) return cudaErrorInvalidValue;
+  batch_describe_kernel<<<ctas, threads, 0, s>>>(inst, count, items, margin, reach, T, desc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
-                                   int margin, int T, int ctas, int threads, cudaStream_t s, const float* pin,
-                                   float* pout, const int4* desc) {
-  if (nsteps < 1 || nsteps > margin || ctas < 1) return cudaErrorInvalidValue;
+                                   int margin, int reach, int T, int ctas, int threads, cudaStream_t s,
+                                   const float* pin, float* pout, const int4* desc) {
+  if (nsteps < 1 || nsteps > reach || ctas < 1) return cudaErrorInvalidValue;
   Geo g{};
   g.T = T;
-  if (fused_threads(g, 0, margin) != threads) return cudaErrorInvalidValue;
+  if (fused_threads(g, 0, margin, reach) != threads) return cudaErrorInvalidValue;
   diffusion_batch_kernel<<<ctas, threads, fused_batch_smem_bytes(threads), s>>>(inst, count, items, which, a, nsteps,
-                                                                               margin, T, pin, pout, desc);
+                                                                               margin, reach, T, pin, pout, desc);
   return cudaGetLastError();
 }
 
@@ -846,10 +905,10 @@ cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items,
   return cudaGetLastError();
 }
 
-cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
-                                   float a, int nsteps, cudaStream_t s, double* partials, const float* pin,
+cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, int reach, const Launch& L, const float* in,
+                                   float* out, float a, int nsteps, cudaStream_t s, double* partials, const float* pin,
                                    float* pout, const int4* desc) {
-  if (nsteps < 1 || nsteps > margin || log_rho < 2 || fused_threads(L.geo, 0, margin) != L.threads ||
+  if (nsteps < 1 || nsteps > reach || log_rho < 2 || fused_threads(L.geo, 0, margin, reach) != L.threads ||
       (!in && !pin) || (!out && !pout))
     return cudaErrorInvalidValue;
   // two blocks per thread (the descriptors give each thread its two slots)
@@ -857,10 +916,10 @@ cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Laun
   // many steps, bound by their arithmetic); short launches are bound by their
   // loads and stores, which one block per thread keeps more of in flight
   if (desc && L.threads > 288)
-    return mode == kLambda ? go2<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s)
-                           : go2<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s);
-  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s)
-                         : go<kBB>(L, in, out, a, nsteps, margin, log_rho, partials, pin, pout, desc, s);
+    return mode == kLambda ? go2<kLambda>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s)
+                           : go2<kBB>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s);
+  return mode == kLambda ? go<kLambda>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s)
+                         : go<kBB>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s);
 }
 
 int64_t fused_descriptors(const Launch& L) {
@@ -869,13 +928,14 @@ int64_t fused_descriptors(const Launch& L) {
   return st * L.threads;
 }
 
-cudaError_t launch_fused_describe(int mode, int log_rho, int margin, const Launch& L, int4* desc, cudaStream_t s) {
-  if (fused_threads(L.geo, 0, margin) != L.threads) return cudaErrorInvalidValue;
+cudaError_t launch_fused_describe(int mode, int log_rho, int margin, int reach, const Launch& L, int4* desc,
+                                  cudaStream_t s) {
+  if (fused_threads(L.geo, 0, margin, reach) != L.threads) return cudaErrorInvalidValue;
   const int smem = member_blocks(L.geo.T) * 4;  // BB slot table
   if (mode == kLambda)
-    fused_describe_kernel<kLambda><<<L.grid, L.threads, smem, s>>>(L.geo, margin, log_rho, desc);
+    fused_describe_kernel<kLambda><<<L.grid, L.threads, smem, s>>>(L.geo, margin, reach, log_rho, desc);
   else
-    fused_describe_kernel<kBB><<<L.grid, L.threads, smem, s>>>(L.geo, margin, log_rho, desc);
+    fused_describe_kernel<kBB><<<L.grid, L.threads, smem, s>>>(L.geo, margin, reach, log_rho, desc);
   return cudaGetLastError();
 }
 

@@ -43,21 +43,28 @@ int tma_smem_bytes(const Geo& g, int tile_bytes, int dtype);
 // in / out: embedded arrays; pin / pout (when not null): compact records in
 // place of in / out (the state between the launches of one call).
 // desc (when not null): the launch's per-thread descriptors from
-// launch_fused_describe for the same geometry and margin.
-cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, const Launch& L, const float* in, float* out,
-                                   float a, int nsteps, cudaStream_t s, double* partials = nullptr,
+// launch_fused_describe for the same geometry, margin and reach.
+// reach (<= margin): the most steps a launch of the configuration takes
+// (nsteps <= reach); margin-box blocks further than that from the
+// super-tile are not staged.
+cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, int reach, const Launch& L, const float* in,
+                                   float* out, float a, int nsteps, cudaStream_t s, double* partials = nullptr,
                                    const float* pin = nullptr, float* pout = nullptr, const int4* desc = nullptr);
 // Descriptors of a fused launch (one per thread of each member super-tile's
 // CTA, 16 bytes) and the kernel that writes them.
 int64_t fused_descriptors(const Launch& L);
-cudaError_t launch_fused_describe(int mode, int log_rho, int margin, const Launch& L, int4* desc, cudaStream_t s);
+cudaError_t launch_fused_describe(int mode, int log_rho, int margin, int reach, const Launch& L, int4* desc,
+                                  cudaStream_t s);
 // Compact records of a level-k gasket (3^(k-3), one per member 8 x 8 block)
 // and the bytes of one.
 int64_t fused_records(int k);
 int fused_record_bytes();
 int fused_margin(int steps_per_launch);
-int fused_smem_bytes(const Geo& g, int margin);
-int fused_threads(const Geo& g, int rho, int margin);
+int fused_smem_bytes(const Geo& g, int margin, int reach);
+int fused_threads(const Geo& g, int rho, int margin, int reach);
+// Most member blocks of the margin boxes (W blocks wide) of a level-L
+// super-tile within `reach` cells of it.
+int box_cap_reach(int L, int W, int reach);
 
 // Temporally fused automaton on a bit image: nsteps (<= margin <= 31) steps
 // per launch over 32 x 32-cell word tiles (k_fused_ca.cu).
@@ -111,17 +118,17 @@ struct BatchInst {
 };
 
 // Persistent fused diffusion over `items` super-tiles of side T of the
-// instances (which = 0: a -> b, 1: b -> a); threads = fused_threads for T
-// and margin.  Per-instance member sums through `partials` (items doubles).
+// instances (which = 0: a -> b, 1: b -> a); threads = fused_threads for T,
+// margin and reach.  Per-instance member sums through `partials` (items doubles).
 // pin / pout (when not null): the block records of all instances (item w's
 // at w * 3^log2(T/8)) in place of the instances' buffers.
 // desc (when not null): the batch's per-thread setups from
 // launch_batch_describe for the same table, super-tile side and margin.
 cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t items, int which, float a, int nsteps,
-                                   int margin, int T, int ctas, int threads, cudaStream_t s,
+                                   int margin, int reach, int T, int ctas, int threads, cudaStream_t s,
                                    const float* pin = nullptr, float* pout = nullptr, const int4* desc = nullptr);
-cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t items, int margin, int T, int ctas,
-                                  int threads, int4* desc, cudaStream_t s);
+cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t items, int margin, int reach, int T,
+                                  int ctas, int threads, int4* desc, cudaStream_t s);
 cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items, int which, int T, int ctas,
                                 double* partials, double* out, cudaStream_t s);
 int fused_batch_smem_bytes(int threads);

@@ -79,3 +79,53 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(fr, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         fr.fractal_map(4, 4)
+
+
+def _box_blocks_brute(T, M, R):
+    """Most member blocks of the margin boxes within each reach 1..M of a
+    super-tile of side T, over every member super-tile of a level-R grid of
+    super-tiles, by direct enumeration (numpy)."""
+    import numpy as np
+    B, side, W = 8, T // 8, M // 8
+    q = []
+    for by in range(-W, side + W):
+        for bx in range(-W, side + W):
+            inside = 0 <= bx < side and 0 <= by < side
+            left = -W <= bx < 0 and 0 <= by < W
+            top = 0 <= bx < W and -W <= by < 0
+            right = side <= bx < side + W and -W <= by < W
+            bottom = -W <= bx < W and side <= by < side + W
+            if inside or not (left or top or right or bottom):
+                continue
+            xs, ys = np.arange(bx * B, bx * B + B), np.arange(by * B, by * B + B)
+            dx = np.maximum(0, np.maximum(-xs, xs - (T - 1))).min()
+            dy = np.maximum(0, np.maximum(-ys, ys - (T - 1))).min()
+            q.append((bx, by, dx + dy))
+    q = np.array(q)
+    g = 1 << R
+    nblk = g * side
+    sx, sy = np.meshgrid(np.arange(g), np.arange(g))
+    keep = (sx & sy) == 0
+    sx, sy = sx[keep], sy[keep]
+    gx = sx[:, None] * side + q[None, :, 0]
+    gy = sy[:, None] * side + q[None, :, 1]
+    member = (gx >= 0) & (gy >= 0) & (gx < nblk) & (gy < nblk) & ((gx & gy) == 0)
+    return {r: int((member & (q[None, :, 2] <= r)).sum(axis=1).max()) for r in range(1, M + 1)}
+
+
+@pytest.mark.parametrize("T,M", [(16, 8), (64, 32), (128, 64), (256, 64), (256, 32), (256, 128)])
+def test_fused_box_blocks_match_brute_force(lib, T, M):
+    """The staged margin-box blocks per super-tile: the library's count (taken
+    over a 64 x 64 grid of super-tiles) equals a brute-force maximum over every
+    member super-tile of a 128 x 128 grid, for every reach; at reach = margin
+    it is the whole boxes' member count, three gasket fragments of side M."""
+    want = _box_blocks_brute(T, M, 7)
+    for r in range(1, M + 1):
+        assert fr.fractal_fused_box_blocks(T, M, r) == want[r], (T, M, r)
+    assert want[M] == 3 ** (1 + (M // 8).bit_length() - 1)
+
+
+@pytest.mark.parametrize("args", [(8, 8, 8), (24, 8, 8), (512, 64, 64), (256, 12, 8), (64, 64, 8), (256, 64, 0),
+                                  (256, 64, 65)])
+def test_fused_box_blocks_rejects_bad_arguments(lib, args):
+    assert lib.fractal_fused_box_blocks(*args) == -1  # FRACTAL_EINVAL
