@@ -52,6 +52,16 @@ bool device_addressable(const void* p, int device) {
   }
 }
 
+// p is device memory (not host memory mapped into the device).
+bool on_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice;
+}
+
 constexpr int kMaxLevelsPerCta = 5;
 constexpr int kMaxSmem = 200 * 1024;
 // Loads per thread a launch is sized for (at most kIPT; fewer keeps more warps
@@ -997,7 +1007,7 @@ int fractal_pack(fractal_plan_t p, const void* dev_embedded, int dtype, void* de
       !device_addressable(dev_embedded, p->device) || !device_addressable(dev_packed, p->device))
     return FRACTAL_EINVAL;
   cudaError_t e = launch_pack(dev_embedded, dev_packed, p->n, p->rb, 1 << p->log_rho, dtype == FRACTAL_U8 ? 1 : 4,
-                              (cudaStream_t)stream);
+                              on_device(dev_packed), (cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "pack");
 }
 
@@ -1007,7 +1017,7 @@ int fractal_unpack(fractal_plan_t p, const void* dev_packed, int dtype, void* de
       !device_addressable(dev_embedded, p->device) || !device_addressable(dev_packed, p->device))
     return FRACTAL_EINVAL;
   cudaError_t e = launch_unpack(dev_packed, dev_embedded, p->n, p->rb, 1 << p->log_rho,
-                                dtype == FRACTAL_U8 ? 1 : 4, (cudaStream_t)stream);
+                                dtype == FRACTAL_U8 ? 1 : 4, on_device(dev_packed), (cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "unpack");
 }
 

@@ -87,8 +87,12 @@ int ca_fused_threads(const Geo& g, int margin);
 // one thread per member 8 x 8 block, super-tiles of 2^levels blocks a side.
 // Member tiles in lambda order <-> the embedded array (k_pack.cu); elem =
 // bytes per element.
-cudaError_t launch_pack(const void* embedded, void* packed, int n, int rb, int rho, int elem, cudaStream_t s);
-cudaError_t launch_unpack(const void* packed, void* embedded, int n, int rb, int rho, int elem, cudaStream_t s);
+// packed_on_device: the packed side is device memory (else pinned host
+// memory mapped into the device).
+cudaError_t launch_pack(const void* embedded, void* packed, int n, int rb, int rho, int elem, bool packed_on_device,
+                        cudaStream_t s);
+cudaError_t launch_unpack(const void* packed, void* embedded, int n, int rb, int rho, int elem,
+                          bool packed_on_device, cudaStream_t s);
 
 // Float32 reduce with one 8 x 8 block per thread (k_blocks.cu); k >= 3,
 // rho >= 4.
