@@ -89,3 +89,24 @@ def test_theorem2_parallel_space_ratio(r):
     # unbounded as n grows.
     W, H = oracle.grid_dims(r)
     assert math.isclose((1 << r) ** 2 / (W * H), (4 / 3) ** r, rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("r", [6, 7, 8, 9])
+def test_packed_rectangles_are_level6_subgaskets(r):
+    """The device pack kernel for narrow tiles relies on this: a 27 x 27
+    rectangle of the packed grid aligned to multiples of 27 varies the low
+    three base-3 digits of omega_x and omega_y, which are the digits of
+    mu = 1..6, so (Theorem 1) its blocks are the level-6 gasket in one 64 x 64
+    square whose corner is lambda of the high digits at level r - 6, shifted
+    by six bits, and the block at (u mod 27, u div 27) of the rectangle is
+    that corner plus lambda of (u mod 27, u div 27) at level 6."""
+    W, H = oracle.grid_dims(r)
+    local = [oracle.lambda_canonical(u % 27, u // 27, 6) for u in range(729)]
+    assert sorted(local) == sorted((x, y) for y in range(64) for x in range(64) if (x & y) == 0)
+    for gy in range(H // 27):
+        for gx in range(W // 27):
+            cx, cy = oracle.lambda_canonical(gx, gy, r - 6)
+            for u in range(729):
+                wx, wy = gx * 27 + u % 27, gy * 27 + u // 27
+                lx, ly = local[u]
+                assert oracle.lambda_canonical(wx, wy, r) == ((cx << 6) + lx, (cy << 6) + ly), (r, gx, gy, u)
