@@ -968,7 +968,7 @@ def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):
     The timed region starts before the first copy in and ends after the last
     copy out.  With 0, the whole n x n arrays cross, one step after the other."""
     rho = args.e2e_rho
-    steps = max(10, args.steps)
+    steps = max(20, args.steps)
     nsums = sums.numel()
     if rho <= 0:
         cells = ca_a.numel()
