@@ -160,3 +160,101 @@ def test_mod4_rule_matches_b3s23_for_sums_up_to_six():
         for self_ in (0, 1):
             m = (count + self_) % 4
             assert (m == 3 or (m == 0 and self_ == 1)) == (count == 3 or (count == 2 and self_ == 1))
+
+
+def _automaton_tasks(T, M):
+    """The fused automaton's staging layout (word column c, first row y0,
+    rows) in super-tile coordinates: every member 32 x 32 word tile of the
+    super-tile, then the seven box pieces, with the margin rounded up to even
+    (ME) and the right box reaching rows [-ME, ME + 1]."""
+    ws = T // 32
+    tasks = [(tx, 32 * ty, 32) for ty in range(ws) for tx in range(ws) if (tx & ty) == 0]
+    ME = M + (M & 1)
+    right = 2 * ME + 2
+    tasks += [(-1, 0, ME), (0, -ME, ME), (ws, -ME, min(right, 32)), (ws, -ME + 32, min(max(right - 32, 0), 32)),
+              (ws, -ME + 64, max(right - 64, 0)), (-1, T, ME), (0, T, ME)]
+    return tasks
+
+
+@pytest.mark.parametrize("T", [32, 64, 128, 256, 512])
+def test_automaton_staging_layout(T):
+    """For every margin the fused automaton takes (1 <= M <= 31, 2 M <= T):
+    each task starts on an even row and has an even number of rows (a lane
+    keeps two adjacent rows as one 8-byte word pair); no word of the bit image
+    is staged twice (each has one writer); the staged words hold the
+    automaton's margin boxes; and the rows a lane reads (one beyond its pair
+    on each side, in its column and the two beside it) stay inside the image's
+    word columns [-2, T/32 + 1] and rows [-34, T + 34)."""
+    ws = T // 32
+    for M in range(1, 32):
+        if 2 * M > T:
+            break
+        staged = set()
+        for c, y0, rows in _automaton_tasks(T, M):
+            assert y0 % 2 == 0 and rows % 2 == 0 and 0 <= rows <= 32
+            for y in range(y0, y0 + rows):
+                assert (c, y) not in staged, (T, M, c, y)
+                staged.add((c, y))
+            if rows:
+                assert -2 <= c - 1 and c + 1 <= ws + 1
+                assert -34 <= y0 - 1 and y0 + rows < T + 34
+        for x0, x1, y0, y1 in _boxes(T, M, 8):
+            for y in range(y0, y1):
+                for x in (x0, x1 - 1):
+                    assert (x // 32, y) in staged, (T, M, x, y)
+
+
+@pytest.mark.parametrize("M", [1, 8, 25, 31])
+def test_automaton_nine_cell_rule_on_the_staged_image(M):
+    """The fused automaton's arithmetic on the bit image, emulated word by
+    word on the host (row sums of three cells by funnel shifts and a full
+    adder, the nine-cell sum modulo 4, births masked to members) over the
+    staging layout above, for one launch of M steps at level 7 with
+    super-tiles of side 64: equal to the oracle's automaton."""
+    k, T = 7, 64
+    n = 1 << k
+    rng = np.random.default_rng(10 + M)
+    mem = oracle.member_mask(n)
+    state = ((rng.random((n, n)) < 0.5) & mem).astype(np.uint8)
+    want = oracle.ca_run(state, M)
+    mask32 = (1 << 32) - 1
+
+    def word(a, x0, y):
+        return sum(int(a[y, x0 + i]) << i for i in range(32)) if 0 <= y < n and 0 <= x0 < n else 0
+
+    def members(x0, y):
+        return word(mem, x0, y)
+
+    def row_sum(l, w, r):
+        a = ((w << 1) | (l >> 31)) & mask32
+        c = ((w >> 1) | (r << 31)) & mask32
+        return a ^ w ^ c, (a & w) | (c & (a ^ w))
+
+    got = np.zeros_like(state)
+    for sy in range(n // T):
+        for sx in range(n // T):
+            if sx & sy:
+                continue
+            ox, oy = sx * T, sy * T
+            img, msk = {}, {}
+            for c, y0, rows in _automaton_tasks(T, M):
+                for y in range(y0, y0 + rows):
+                    img[(c, y)] = word(state, ox + 32 * c, oy + y)
+                    msk[(c, y)] = members(ox + 32 * c, oy + y)
+            for _ in range(M):
+                def at(c, y):
+                    return img.get((c, y), 0)
+                nxt = {}
+                for (c, y), v in img.items():
+                    us, uk = row_sum(at(c - 1, y - 1), at(c, y - 1), at(c + 1, y - 1))
+                    ms, mk = row_sum(at(c - 1, y), v, at(c + 1, y))
+                    ds, dk = row_sum(at(c - 1, y + 1), at(c, y + 1), at(c + 1, y + 1))
+                    bit0 = us ^ ms ^ ds
+                    k0 = (us & ms) | (ds & (us ^ ms))
+                    bit1 = (uk ^ mk ^ dk ^ k0) & msk[(c, y)]
+                    nxt[(c, y)] = ((bit0 & bit1) | (~bit0 & ~bit1 & v)) & mask32
+                img = nxt
+            for (c, y), v in img.items():
+                if 0 <= c < T // 32 and 0 <= y < T:
+                    got[oy + y, ox + 32 * c:ox + 32 * c + 32] = [(v >> i) & 1 for i in range(32)]
+    assert np.array_equal(got, want)
