@@ -258,3 +258,57 @@ def test_automaton_nine_cell_rule_on_the_staged_image(M):
                 if 0 <= c < T // 32 and 0 <= y < T:
                     got[oy + y, ox + 32 * c:ox + 32 * c + 32] = [(v >> i) & 1 for i in range(32)]
     assert np.array_equal(got, want)
+
+
+def _box_block_distance(qx, qy, side):
+    """Manhattan distance from the nearest cell of 8 x 8 block (qx, qy) to the
+    super-tile [0, 8 side)^2 (block coordinates relative to the super-tile)."""
+    def gap(q):
+        return -8 * q - 7 if q < 0 else 8 * (q - side) + 1 if q >= side else 0
+    return gap(qx) + gap(qy)
+
+
+@pytest.mark.parametrize("T,M,reach", [(64, 32, 8), (64, 32, 9), (64, 32, 17), (64, 32, 20), (64, 32, 32), (128, 64, 50),
+                                         (64, 16, 13)])
+def test_diffusion_box_blocks_within_reach_suffice(T, M, reach):
+    """The fused diffusion stages, besides its super-tile, only the member
+    blocks of its margin boxes (width M) whose nearest cell lies within
+    `reach` cells of the super-tile, and runs up to `reach` steps.  Emulated
+    in float64 on the host: staged member cells take the step with their true
+    member degree and read every member neighbour that is not staged as 0 (the
+    kernel's zero port slot); after `reach` steps every cell of the super-tile
+    equals the oracle's diffusion of the whole gasket."""
+    k, a = 9, 0.2
+    n = 1 << k
+    rng = np.random.default_rng(T + M + reach)
+    mem = oracle.member_mask(n)
+    u0 = np.where(mem, rng.random((n, n)), 0.0)
+    want = oracle.diffusion_run(u0, reach, a)
+    side, W = T // 8, M // 8
+    pad = 8 * (W + 1)
+    big = n + 2 * pad
+    memp = np.zeros((big, big), dtype=bool)
+    memp[pad:pad + n, pad:pad + n] = mem
+    deg = sum(np.roll(np.roll(memp, dy, 0), dx, 1) for dy, dx in ((1, 0), (-1, 0), (0, 1), (0, -1))) * memp
+    for sy in range(n // T):
+        for sx in range(n // T):
+            if sx & sy:
+                continue
+            staged = np.zeros((big, big), dtype=bool)
+            oy, ox = pad + sy * T, pad + sx * T
+            staged[oy:oy + T, ox:ox + T] = True
+            for x0, x1, y0, y1 in _boxes(T, M, 4):
+                for qy in range(y0 // 8, y1 // 8):
+                    for qx in range(x0 // 8, x1 // 8):
+                        if _box_block_distance(qx, qy, side) <= reach:
+                            staged[oy + 8 * qy:oy + 8 * qy + 8, ox + 8 * qx:ox + 8 * qx + 8] = True
+            staged &= memp
+            u = np.zeros((big, big))
+            u[pad:pad + n, pad:pad + n] = u0
+            u = np.where(staged, u, 0.0)
+            for _ in range(reach):
+                nb = sum(np.roll(np.roll(u, dy, 0), dx, 1) for dy, dx in ((1, 0), (-1, 0), (0, 1), (0, -1)))
+                u = np.where(staged, u + a * (nb - deg * u), 0.0)
+            got = u[oy:oy + T, ox:ox + T]
+            ref = want[sy * T:(sy + 1) * T, sx * T:(sx + 1) * T]
+            assert np.allclose(got, ref, rtol=0, atol=1e-12), (T, M, reach, sx, sy)
