@@ -38,3 +38,24 @@ def test_launch_bytes_by_hand():
     assert bench.fused_launch_bytes("diffusion", "RE", 5, 2) == 11 * 112 + 9 * 256
     assert bench.fused_launch_bytes("ca", "ER", 5, 3) == 1024 + 3 * 32 + 128
     assert bench.fused_launch_bytes("ca", "RE", 5, 3) == 128 + 3 * 4 + 1024
+
+
+def test_box_blocks_within_reach_agree_with_the_library():
+    """The algorithmic bytes count the margin-box blocks a launch stages: at
+    reach = margin all member blocks of the boxes, fewer for a shorter reach,
+    and never more per super-tile than the library gives thread slots to
+    (fractal_fused_box_blocks, the most any super-tile has)."""
+    from paper_2004_13475_gb300 import build as fbuild
+    import paper_2004_13475_gb300 as fr
+    fbuild.build()
+    k, T, M = 12, 256, 64
+    supertiles = 3 ** (k - 8)
+    full = bench.diffusion_box_member_blocks(k, T, M)
+    assert bench.diffusion_box_member_blocks(k, T, M, M) == full
+    prev = full
+    for reach in (50, 40, 25, 9, 1):
+        c = bench.diffusion_box_member_blocks(k, T, M, reach)
+        assert c <= prev
+        assert c <= supertiles * fr.fractal_fused_box_blocks(T, M, reach)
+        prev = c
+    assert bench.diffusion_box_member_blocks(k, T, M, 50) < full
