@@ -70,6 +70,70 @@ def test_batch_equals_single_instances_and_oracle(fr, ks_range, T, spl):
             assert rel_err(got, want, dom.mask)[0] <= 2e-5, (k, steps)
 
 
+def _windows(n, steps, inner=128):
+    """Oracle windows for a large instance: the corners of the bounding
+    triangle and inner squares centred on contacts between 256-cell
+    super-tiles and between the level-(k-1) replicas."""
+    h = inner // 2
+    origins = [(0, 0), (n - inner, 0), (0, n - inner), (3 * 256 - h, -h), (-h, 5 * 256 - h),
+               (n // 2 + 256 - h, 256 - h), (n // 2 - h, -h), (-h, n // 2 - h)]
+    out = []
+    for X, Y in origins:
+        x0, y0 = max(0, X - steps), max(0, Y - steps)
+        x1, y1 = min(n, X + inner + steps), min(n, Y + inner + steps)
+        out.append((x0, y0, x1 - x0, y1 - y0))
+    return out
+
+
+def _valid(n, x0, y0, w, h, steps):
+    lo_x = 0 if x0 <= 0 else steps
+    lo_y = 0 if y0 <= 0 else steps
+    hi_x = w if x0 + w >= n else w - steps
+    hi_y = h if y0 + h >= n else h - steps
+    return slice(lo_y, hi_y), slice(lo_x, hi_x)
+
+
+def test_batch_as_benchmarked_against_oracle(fr):
+    """The configuration the benchmark times: super-tile side 256, 32 steps
+    per launch, levels drawn from 8..13, 100 steps through the captured graph.
+    One instance of every level is compared with the FP64 oracle (whole array
+    up to k = 11, windows across super-tile and replica seams above)."""
+    rng = np.random.default_rng(13)
+    ks = [8, 9, 10, 11, 12, 13] + [int(k) for k in rng.integers(8, 14, size=10)]
+    seed0, steps = 900, 100
+    a = [torch.empty((1 << k) ** 2, dtype=torch.float32, device="cuda") for k in ks]
+    b = [torch.empty_like(x) for x in a]
+    for i, k in enumerate(ks):
+        synth.device_fill(a[i].data_ptr(), synth.SYNTH_UNIFORM_F32, 1 << k, seed0 + i)
+    batch = fr.fractal_batch_create(ks)
+    fr.fractal_batch_bind(batch, a, b)
+    fr.fractal_batch_configure(batch, 256, 32)
+    inf = batch.info()
+    assert inf["supertile"] == 256 and inf["steps_per_launch"] == 32
+    fr.fractal_batch_graph_capture(batch, 0.2, steps)
+    fr.fractal_batch_graph_launch(batch)              # 100 steps: result in a (records between launches)
+    torch.cuda.synchronize()
+    for i, k in enumerate(ks[:6]):
+        n = 1 << k
+        out = a[i].view(n, n)
+        if k <= 11:
+            u0 = synth.uniform_f32(seed0 + i, n).astype(np.float64)
+            dom = oracle.Domain.build(n)
+            want = oracle.diffusion_run(u0, steps, 0.2, dom)
+            err, raw = rel_err(out.cpu().numpy(), want, dom.mask)
+            assert err <= 1e-4, (k, err, raw)
+            continue
+        for (x0, y0, w, h) in _windows(n, steps):
+            dom = oracle.Domain.build(n, x0, y0, w, h)
+            u0 = synth.uniform_f32(seed0 + i, n, x0, y0, w, h).astype(np.float64)
+            want = oracle.diffusion_run(u0, steps, 0.2, dom)
+            rs, cs = _valid(n, x0, y0, w, h, steps)
+            got = out[y0:y0 + h, x0:x0 + w].cpu().numpy()
+            err, raw = rel_err(got[rs, cs], want[rs, cs], dom.mask[rs, cs])
+            assert err <= 1e-4, (k, x0, y0, err, raw)
+    batch.close()
+
+
 def test_batch_graph_replays_the_steps(fr):
     ks = [6, 9, 7, 8, 6, 10, 8]
     batch, states, a, b = make_batch(fr, ks, 600)

@@ -46,12 +46,45 @@ def windows(n, steps, inner=192):
     right and upper level-1 replicas.  Windows are clipped to the array."""
     corners = [(0, 0), (n - inner, 0), (0, n - inner),
                (n // 2 + n // 8, n // 16), (n // 64, n // 2 + n // 4)]
+    return windows_at(n, steps, corners, inner)
+
+
+def seam_windows(n, steps, inner=128):
+    """Windows whose inner squares are centred on contacts between super-tiles
+    of every side up to 256 (the fused kernels' CTA tiles): seams along the
+    bottom row and the left column, an interior contact, the two seams of the
+    level-15 replicas (the highest lambda digit) and their diagonal contact."""
+    h = inner // 2
+    centres = [(3 * 256, 0), (0, 5 * 256), (n // 2 + 256, 256),
+               (n // 2, 0), (0, n // 2), (n // 2, n // 2)]
+    return windows_at(n, steps, [(cx - h, cy - h) for cx, cy in centres], inner)
+
+
+def windows_at(n, steps, origins, inner):
     out = []
-    for X, Y in corners:
+    for X, Y in origins:
         x0, y0 = max(0, X - steps), max(0, Y - steps)
         x1, y1 = min(n, X + inner + steps), min(n, Y + inner + steps)
         out.append((x0, y0, x1 - x0, y1 - y0))
     return out
+
+
+_ORACLE = {}
+
+
+def oracle_window(kind, n, x0, y0, w, h, steps):
+    """The oracle's state of a window after ``steps`` steps (cached: the same
+    window serves every rho, mode and fusion setting of a test)."""
+    key = (kind, n, x0, y0, w, h, steps)
+    if key not in _ORACLE:
+        dom = oracle.Domain.build(n, x0, y0, w, h)
+        if kind == "ca":
+            want = oracle.ca_run(synth.bernoulli_u8(SEED, n, x0, y0, w, h), steps, dom)
+        else:
+            u0 = synth.uniform_f32(SEED, n, x0, y0, w, h).astype(np.float64)
+            want = oracle.diffusion_run(u0, steps, 0.2, dom)
+        _ORACLE[key] = (dom, want)
+    return _ORACLE[key]
 
 
 def _member_sum(n, dist, seed):
@@ -86,9 +119,8 @@ def test_k16_ca_100_steps(fr, k16_u8, rho, mode, tuned):
     elif tuned:             # temporal fusion, 25 steps per launch
         fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_U8, tuned)
     out = fr.fractal_step_ca(plan, a, b, steps).view(n, n)
-    for (x0, y0, w, h) in windows(n, steps):
-        dom = oracle.Domain.build(n, x0, y0, w, h)
-        want = oracle.ca_run(synth.bernoulli_u8(SEED, n, x0, y0, w, h), steps, dom)
+    for (x0, y0, w, h) in windows(n, steps) + seam_windows(n, steps):
+        dom, want = oracle_window("ca", n, x0, y0, w, h, steps)
         got = out[y0:y0 + h, x0:x0 + w].cpu().numpy()
         rs, cs = valid_region(n, x0, y0, w, h, steps)
         m = dom.mask[rs, cs]
@@ -131,10 +163,8 @@ def test_k16_diffusion_200_steps(fr, k16_f32, rho, mode, spl):
         fr.fractal_plan_set_steps_per_launch(plan, fr.FRACTAL_F32, spl)
     start = fr.fractal_reduce(plan, a, fr.FRACTAL_F32)
     out = fr.fractal_step_diffusion(plan, a, b, 0.2, steps).view(n, n)
-    for (x0, y0, w, h) in windows(n, steps, inner=128)[:3]:
-        dom = oracle.Domain.build(n, x0, y0, w, h)
-        u0 = synth.uniform_f32(SEED, n, x0, y0, w, h).astype(np.float64)
-        want = oracle.diffusion_run(u0, steps, 0.2, dom)
+    for (x0, y0, w, h) in windows(n, steps, inner=128) + seam_windows(n, steps):
+        dom, want = oracle_window("diffusion", n, x0, y0, w, h, steps)
         got = out[y0:y0 + h, x0:x0 + w].cpu().numpy()
         rs, cs = valid_region(n, x0, y0, w, h, steps)
         err, _ = rel_err(got[rs, cs], want[rs, cs], dom.mask[rs, cs])
