@@ -327,9 +327,14 @@ int fractal_reduce_async(fractal_plan_t plan, const void* dev_buf, int dtype, do
                          void* stream);
 
 /*
- * fractal_reduce_noalloc -- the sum of fractal_reduce_async (lambda launch,
- * same kernels, same result) for callers that cannot allocate: it takes no
- * plan and calls no cudaMalloc, cudaFree or other allocating routine.  Such
+ * fractal_reduce_noalloc -- the sum over the members (as fractal_reduce_async)
+ * for callers that cannot allocate: it takes no plan and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  It runs the kernels of a default
+ * lambda plan, fractal_map(k, rho, FRACTAL_LAMBDA): float32 at rho >= 4 the
+ * reduce over 8 x 8 blocks, otherwise the rho-tile reduce at the plan's
+ * default tile levels per CTA (more levels only where those partials would
+ * not fit the array), so its sum equals that plan's; uint8 counts are exact
+ * in every case.  Such
  * callers are, for example, code that runs while another allocator (a
  * framework's caching allocator, a fixed memory pool) owns the device memory,
  * and latency-bound loops that must not pay for, or synchronise on, an
@@ -343,10 +348,14 @@ int fractal_reduce_async(fractal_plan_t plan, const void* dev_buf, int dtype, do
  * calls: calls whose work overlaps on the GPU (different streams without
  * ordering, or several host threads) race on it, so order them on one
  * stream.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  k, rho and dtype as in fractal_map / fractal_reduce;
- * dev_buf: n*n device array, 16-byte aligned; dev_out: device double that
- * receives the sum.  Asynchronous on `stream`.  Errors: FRACTAL_EINVAL,
+ * (once per device, with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture.  A device
+ * reset (cudaDeviceReset) releases the array with the context: do not call
+ * this entry point on that device again in the same process.  k, rho and
+ * dtype as in fractal_map / fractal_reduce; dev_buf: n*n array, 16-byte
+ * aligned, and dev_out: a double receiving the sum, both addressable by the
+ * current device (device memory of that device, managed, or mapped pinned
+ * host memory).  Asynchronous on `stream`.  Errors: FRACTAL_EINVAL,
  * FRACTAL_ETOOBIG, FRACTAL_ECUDA.
  */
 #define FRACTAL_NOALLOC_MAX_PARTIALS 65536

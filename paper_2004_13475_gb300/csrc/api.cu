@@ -30,6 +30,8 @@ int64_t ipow(int64_t b, int e) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+}  // namespace
+
 // p can be dereferenced by kernels on `device` at the same address: device
 // or managed memory, or pinned host memory mapped into the device's address
 // space (unified addressing).  Pageable host memory and unknown pointers are
@@ -51,6 +53,8 @@ bool device_addressable(const void* p, int device) {
       return false;
   }
 }
+
+namespace {
 
 // p is device memory (not host memory mapped into the device).
 bool on_device(const void* p) {

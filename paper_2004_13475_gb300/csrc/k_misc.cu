@@ -387,18 +387,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device.  The host-side name of
-// the array is not a device address, so it is resolved once per device, with
-// that device current, and cached.
-cudaError_t noalloc_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of the array on the current device `dev`.  The host-side
+// name of the array is not a device address, so it is resolved once per
+// device, with that device current, and cached for the life of the process.
+cudaError_t noalloc_scratch(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (g_noalloc_addr[dev] == nullptr) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_noalloc_addr[dev] = p;
   }
@@ -417,8 +414,27 @@ extern "C" int fractal_reduce_noalloc(int k, int rho, const void* dev_buf, int d
     return FRACTAL_EINVAL;
   if (!dev_buf || !dev_out || (reinterpret_cast<uintptr_t>(dev_buf) & 15u) != 0) return FRACTAL_EINVAL;
   if (dtype != FRACTAL_U8 && dtype != FRACTAL_F32) return FRACTAL_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FRACTAL_ECUDA;
+  }
+  if (!device_addressable(dev_buf, dev) || !device_addressable(dev_out, dev)) return FRACTAL_EINVAL;
   const int log_rho = ilog2c(rho);
-  // lambda launch; more tile levels per CTA until the partials fit the array
+  void* partials = nullptr;
+  // float32 at rho >= 4: the 8 x 8-block reduce of a default lambda plan
+  // (6561 partials at k = 16), so the sum is that plan's bit for bit
+  Launch B;
+  int blevels = 0;
+  if (dtype == FRACTAL_F32 && log_rho >= 2 && blocks_geometry(k, kLambda, B, blevels) &&
+      (int64_t)B.grid.x * B.grid.y <= FRACTAL_NOALLOC_MAX_PARTIALS) {
+    if (noalloc_scratch(dev, &partials) != cudaSuccess) return FRACTAL_ECUDA;
+    cudaError_t e = launch_reduce_blocks(kLambda, B, blevels, static_cast<const float*>(dev_buf),
+                                         static_cast<double*>(partials), dev_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? FRACTAL_OK : FRACTAL_ECUDA;
+  }
+  // otherwise the rho-tile reduce of a default lambda plan; more tile levels
+  // per CTA only where its partials would not fit the array
   Launch step, aux, tma;
   bool tma_ok = false;
   int levels = default_cta_levels(k, log_rho, kLambda, dtype);
@@ -431,8 +447,7 @@ extern "C" int fractal_reduce_noalloc(int k, int rho, const void* dev_buf, int d
     }
   }
   if (!fits) return FRACTAL_ETOOBIG;
-  void* partials = nullptr;
-  if (noalloc_scratch(&partials) != cudaSuccess) return FRACTAL_ECUDA;
+  if (noalloc_scratch(dev, &partials) != cudaSuccess) return FRACTAL_ECUDA;
   cudaError_t e = launch_reduce(kLambda, log_rho, dtype, aux, dev_buf, partials, dev_out, (cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : FRACTAL_ECUDA;
 }

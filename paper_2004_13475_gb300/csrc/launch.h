@@ -17,6 +17,10 @@ struct Launch {
   Geo geo;
 };
 
+// Kernels on `device` can dereference p (device, managed, or mapped pinned
+// host memory); a host-side query that touches nothing.
+bool device_addressable(const void* p, int device);
+
 // Each returns the launch error (cudaSuccess when queued).
 cudaError_t launch_ca(int mode, int log_rho, const Launch& L, const uint8_t* in, uint8_t* out,
                       cudaStream_t s);
