@@ -203,6 +203,27 @@ int fractal_fused_box_blocks(int supertile, int margin, int reach);
 int fractal_plan_device_status(fractal_plan_t plan, int* code);
 
 /*
+ * Failure-path hooks for tests.  The paper has no counterpart: they exist so
+ * that the library's error handling can be exercised without faulting a GPU.
+ *
+ * fractal_plan_selftest_wait -- launches one CTA that arms an mbarrier which
+ * nothing completes (no copy is issued) and waits on it with the bounded wait
+ * of the TMA step kernels, at most `spins` polls (1 .. 2^22); the wait runs
+ * out, code 1 is recorded in the plan's device status word (first error
+ * wins) and the kernel returns, leaving the context usable.  Synchronises
+ * `stream`.  Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
+ *
+ * fractal_debug_fail_allocs -- process-wide: after `after` more successful
+ * device allocations by the library, the next one fails as if the device
+ * were out of memory (the call making it returns FRACTAL_ENOMEM, leaving the
+ * caller's buffers untouched and an existing plan in its previous
+ * configuration); then injection is off again.  after < 0: off.  Never
+ * fails.
+ */
+int fractal_plan_selftest_wait(fractal_plan_t plan, unsigned spins, void* stream);
+int fractal_debug_fail_allocs(int after);
+
+/*
  * fractal_map_blocks -- export the block-space map of the plan (Theorem 1,
  * Sec. 6.1): for omega in row-major order of the grid_w x grid_h packed grid,
  * dev_xy[2*(wy*grid_w + wx) + {0,1}] = (block_x, block_y) in the

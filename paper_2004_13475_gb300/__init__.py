@@ -47,7 +47,7 @@ EXPORTS = (
     "fractal_step_ca_count", "fractal_step_diffusion_sum", "fractal_map_blocks_method",
     "fractal_pack", "fractal_unpack",
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
-    "fractal_fused_box_blocks",
+    "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -150,6 +150,8 @@ def _load() -> ctypes.CDLL:
         "fractal_step_diffusion_sum": (I, [P, VP, VP, F, I, VP, VP]),
         "fractal_step_diffusion_sums": (I, [P, VP, VP, F, I, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
+        "fractal_plan_selftest_wait": (I, [P, ctypes.c_uint, VP]),
+        "fractal_debug_fail_allocs": (I, [I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +255,16 @@ def fractal_plan_device_status(plan: Plan) -> int:
     v = ctypes.c_int()
     _check(_load().fractal_plan_device_status(plan.handle, ctypes.byref(v)), "fractal_plan_device_status")
     return v.value
+
+
+def fractal_plan_selftest_wait(plan: Plan, spins: int = 1 << 16, stream=None) -> None:
+    """Make the bounded device wait run out once (the plan's status becomes 1)."""
+    _check(_load().fractal_plan_selftest_wait(plan.handle, int(spins), _stream(stream)), "fractal_plan_selftest_wait")
+
+
+def fractal_debug_fail_allocs(after: int) -> None:
+    """Fail the library's device allocation after `after` more successes (< 0: off)."""
+    _check(_load().fractal_debug_fail_allocs(int(after)), "fractal_debug_fail_allocs")
 
 
 def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:

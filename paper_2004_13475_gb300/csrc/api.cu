@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include <cudaTypedefs.h>
@@ -30,7 +31,24 @@ int64_t ipow(int64_t b, int e) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Allocations left before an injected failure (-1: none pending).
+std::atomic<int> g_fail_after{-1};
+
 }  // namespace
+
+cudaError_t lib_malloc(void** p, size_t bytes) {
+  int left = g_fail_after.load();
+  while (left >= 0) {
+    if (g_fail_after.compare_exchange_weak(left, left - 1)) {
+      if (left == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
 
 // p can be dereferenced by kernels on `device` at the same address: device
 // or managed memory, or pinned host memory mapped into the device's address
@@ -328,7 +346,7 @@ int ensure_pair(T* (&buf)[2], size_t& cap, size_t need) {
   }
   cap = 0;
   for (int i = 0; i < 2; ++i) {
-    if (cudaMalloc(&buf[i], need) != cudaSuccess) {
+    if (lib_malloc(&buf[i], need) != cudaSuccess) {
       cudaGetLastError();
       for (int j = 0; j < 2; ++j) {
         if (buf[j]) cudaFree(buf[j]);
@@ -364,7 +382,7 @@ int build_descriptors(fractal_plan_s* p, cudaStream_t s, bool sync) {
     if (p->d_desc) cudaFree(p->d_desc);
     p->d_desc = nullptr;
     p->desc_cap = 0;
-    if (cudaMalloc(&p->d_desc, need) != cudaSuccess) {
+    if (lib_malloc(&p->d_desc, need) != cudaSuccess) {
       cudaGetLastError();
       p->d_desc = nullptr;
       return FRACTAL_ENOMEM;
@@ -394,7 +412,7 @@ int ensure_partials(fractal_plan_s* p) {
   }
   if (need <= p->partials_cap) return FRACTAL_OK;
   void* buf = nullptr;
-  cudaError_t e = cudaMalloc(&buf, need * 8);
+  cudaError_t e = lib_malloc(&buf, need * 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FRACTAL_ENOMEM;
@@ -637,8 +655,8 @@ int fractal_map(int k, int rho, int mode, fractal_plan_t* out) {
     delete p;
     return st;
   }
-  if (cudaMalloc(&p->d_result, sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&p->h_result, sizeof(double)) != cudaSuccess || cudaMalloc(&p->d_err, sizeof(int)) != cudaSuccess ||
+  if (lib_malloc(&p->d_result, sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&p->h_result, sizeof(double)) != cudaSuccess || lib_malloc(&p->d_err, sizeof(int)) != cudaSuccess ||
       cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     fractal_plan_destroy(p);
@@ -704,9 +722,9 @@ static int set_levels(fractal_plan_t p, int dtype, int levels) {
   Launch s, a, t;
   bool ok = false;
   if (!make_launch(*p, dtype, levels, s, a, t, ok)) return FRACTAL_EINVAL;
-  const Launch old_s = p->step[dtype], old_a = p->aux[dtype], old_t = p->tma[dtype];
+  const Launch old_s = p->step[dtype], old_a = p->aux[dtype], old_t = p->tma[dtype], old_f = p->fused[dtype];
   const int old_m = p->m[dtype];
-  const bool old_ok = p->tma_ok[dtype];
+  const bool old_ok = p->tma_ok[dtype], old_fok = p->fused_ok[dtype];
   p->step[dtype] = s;
   p->aux[dtype] = a;
   p->tma[dtype] = t;
@@ -720,6 +738,8 @@ static int set_levels(fractal_plan_t p, int dtype, int levels) {
     p->tma[dtype] = old_t;
     p->tma_ok[dtype] = old_ok;
     p->m[dtype] = old_m;
+    p->fused[dtype] = old_f;
+    p->fused_ok[dtype] = old_fok;
   }
   return st;
 }
@@ -741,14 +761,24 @@ int fractal_plan_set_steps_per_launch(fractal_plan_t p, int dtype, int spl) {
   }
   Launch f;
   if (!make_fused(*p, dtype, spl, p->step[dtype], f)) return FRACTAL_EINVAL;
+  const int old_spl = p->spl[dtype];
+  const bool old_ok = p->fused_ok[dtype];
+  const Launch old_f = p->fused[dtype];
   p->spl[dtype] = spl;
   p->fused[dtype] = f;
   p->fused_ok[dtype] = true;
   int st = ensure_partials(p);  // the fused kernels' per-CTA sums
-  if (st != FRACTAL_OK) return st;
-  st = ensure_records(p, dtype);
-  if (st != FRACTAL_OK || dtype != FRACTAL_F32) return st;
-  return build_descriptors(p, nullptr, true);
+  if (st == FRACTAL_OK) st = ensure_records(p, dtype);
+  if (st == FRACTAL_OK && dtype == FRACTAL_F32) st = build_descriptors(p, nullptr, true);
+  if (st != FRACTAL_OK) {
+    // the previous configuration stays in force (its partials still fit;
+    // without records or descriptors its launches ping-pong the caller's
+    // buffers and compute their threads' setup themselves)
+    p->spl[dtype] = old_spl;
+    p->fused_ok[dtype] = old_ok;
+    p->fused[dtype] = old_f;
+  }
+  return st;
 }
 
 int fractal_plan_set_schedule(fractal_plan_t p, int sched) {
@@ -881,6 +911,18 @@ int fractal_plan_autotune(fractal_plan_t p, int dtype, const void* dev_in, void*
   fractal_plan_set_steps_per_launch(p, dtype, ok ? best_spl : old_spl);
   if (ok && best_us) *best_us = best;
   return status;
+}
+
+int fractal_debug_fail_allocs(int after) {
+  g_fail_after.store(after < 0 ? -1 : after);
+  return FRACTAL_OK;
+}
+
+int fractal_plan_selftest_wait(fractal_plan_t p, unsigned spins, void* stream) {
+  if (check_plan(p) || spins == 0 || spins > (1u << 22)) return FRACTAL_EINVAL;
+  cudaError_t e = launch_wait_selftest(p->d_err, spins, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "wait self-test");
 }
 
 int fractal_plan_device_status(fractal_plan_t p, int* code) {

@@ -107,7 +107,7 @@ int rebuild(fractal_batch_s* b) {
       if (b->d_desc) cudaFree(b->d_desc);
       b->d_desc = nullptr;
       b->desc_cap = 0;
-      if (cudaMalloc(&b->d_desc, need) == cudaSuccess) {
+      if (lib_malloc(&b->d_desc, need) == cudaSuccess) {
         b->desc_cap = need;
       } else {
         cudaGetLastError();
@@ -185,7 +185,7 @@ int fractal_batch_create(int count, const int32_t* ks, fractal_batch_t* out) {
     delete b;
     return FRACTAL_EINVAL;
   }
-  if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * count) != cudaSuccess ||
+  if (lib_malloc(&b->d_inst, sizeof(BatchInst) * count) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     fractal_batch_destroy(b);
@@ -218,18 +218,15 @@ int fractal_batch_bind(fractal_batch_t b, float* const* dev_a, float* const* dev
   for (int i = 0; i < b->count; ++i)
     if (!dev_a[i] || !dev_b[i] || dev_a[i] == dev_b[i] || !aligned16(dev_a[i]) || !aligned16(dev_b[i]))
       return FRACTAL_EINVAL;
-  for (int i = 0; i < b->count; ++i) {
-    b->h[i].a = dev_a[i];
-    b->h[i].b = dev_b[i];
-  }
   // block records of all instances, 3^(k_i - 3) of 112 bytes each, whatever
-  // the super-tile side (allocated once, before any launch or capture)
+  // the super-tile side (allocated once, before any launch or capture; a
+  // failure leaves the batch as it was)
   if (!b->d_rec[0]) {
     int64_t recs = 0;
     for (int k : b->ks) recs += pow3(k - 3);
     const size_t bytes = (size_t)recs * (size_t)fused_record_bytes();
     for (int i = 0; i < 2; ++i) {
-      if (cudaMalloc(&b->d_rec[i], bytes) != cudaSuccess) {
+      if (lib_malloc(&b->d_rec[i], bytes) != cudaSuccess) {
         cudaGetLastError();
         for (int j = 0; j < 2; ++j) {
           if (b->d_rec[j]) cudaFree(b->d_rec[j]);
@@ -238,6 +235,10 @@ int fractal_batch_bind(fractal_batch_t b, float* const* dev_a, float* const* dev
         return FRACTAL_ENOMEM;
       }
     }
+  }
+  for (int i = 0; i < b->count; ++i) {
+    b->h[i].a = dev_a[i];
+    b->h[i].b = dev_b[i];
   }
   b->bound = true;
   return rebuild(b);
@@ -267,7 +268,7 @@ int fractal_batch_reduce(fractal_batch_t b, int which, double* dev_out, void* st
   if (!b || !b->bound || !dev_out || (which != 0 && which != 1)) return FRACTAL_EINVAL;
   if (b->partials_cap < b->items) {
     double* p = nullptr;
-    if (cudaMalloc(&p, sizeof(double) * b->items) != cudaSuccess) {
+    if (lib_malloc(&p, sizeof(double) * b->items) != cudaSuccess) {
       cudaGetLastError();
       return FRACTAL_ENOMEM;
     }

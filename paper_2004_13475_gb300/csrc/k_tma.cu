@@ -473,4 +473,23 @@ cudaError_t launch_ca_tma(int mode, int log_rho, const Launch& L, const CUtensor
   }
 }
 
+// Bounded-wait self-test: an mbarrier armed for one arrival that never
+// comes (no copy is issued), waited for by every thread with the step
+// kernels' bounded wait; on timeout the first thread records the code in
+// *err and all return.  Nothing is in flight when the wait gives up.
+__global__ void __launch_bounds__(32) wait_selftest_kernel(int* __restrict__ err, uint32_t spins) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  mbar_wait_bounded(&bar, 0, threadIdx.x == 0 ? err : nullptr, kErrTmaTimeout, spins);
+}
+
+cudaError_t launch_wait_selftest(int* err, uint32_t spins, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err, spins);
+  return cudaGetLastError();
+}
+
 }  // namespace fractal

@@ -17,6 +17,19 @@ struct Launch {
   Geo geo;
 };
 
+// Every device allocation of the library goes through here, so that a test
+// can make the n-th one fail (fractal_debug_fail_allocs).
+cudaError_t lib_malloc(void** p, size_t bytes);
+template <typename T>
+cudaError_t lib_malloc(T** p, size_t bytes) {
+  return lib_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
+// One CTA arms an mbarrier that nothing completes and waits on it with the
+// step kernels' bounded wait, `spins` polls at most: the timeout path (code
+// 1 in *err, then return).
+cudaError_t launch_wait_selftest(int* err, uint32_t spins, cudaStream_t s);
+
 // Kernels on `device` can dereference p (device, managed, or mapped pinned
 // host memory); a host-side query that touches nothing.
 bool device_addressable(const void* p, int device);
