@@ -166,29 +166,79 @@ def oracle_sample(ca_steps, diff_steps):
     return updates / dt, dt, desc
 
 
+def _oracle_worker(index, barrier, out_q, ca_steps, diff_steps, rounds):
+    """One process of the all-cores oracle run: the level-12 sub-gasket at
+    (4096 * index, 0) of the level-16 array (3^12 members, the same structure
+    as the corner window), built untimed; then `rounds` timed runs of the
+    steps, each started together with the other processes at a barrier."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import numpy as np
+    import oracle
+    import synth
+    w = ORACLE_WINDOW
+    x0 = w * index
+    dom = oracle.Domain.build(N, x0, 0, w, w)
+    s0 = dom.take(synth.bernoulli_u8(SEED, N, x0, 0, w, w))
+    u0 = dom.take(synth.uniform_f32(SEED, N, x0, 0, w, w)).astype(np.float64)
+    for r in range(rounds):
+        s, u = s0, u0
+        barrier.wait()
+        t0 = time.time()
+        for _ in range(ca_steps):
+            s = oracle.ca_step(dom, s)
+        for i in range(diff_steps):
+            u = oracle.diffusion_step(dom, u, COEF)
+            if (i + 1) % REDUCE_EVERY == 0:
+                oracle.reduce_sum(u)
+        oracle.reduce_sum(s)
+        t1 = time.time()
+        out_q.put((r, dom.m * (ca_steps + diff_steps), t0, t1))
+
+
+def oracle_all_cores(ca_steps, diff_steps, rounds=1, procs=None):
+    """The CPU oracle, as it stands, in one process per host core, each on its
+    own level-12 sub-gasket of the workload (spawned processes: the parent may
+    already hold a CUDA context).  Returns (per-round cell-updates/s over the
+    wall time from the first start to the last end, processes, description)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    procs = min(procs, N // ORACLE_WINDOW)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    out_q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(i, barrier, out_q, ca_steps, diff_steps, rounds), daemon=True)
+          for i in range(procs)]
+    for p in ps:
+        p.start()
+    got = [out_q.get(timeout=600) for _ in range(procs * rounds)]
+    for p in ps:
+        p.join(timeout=60)
+    rates = []
+    for r in range(rounds):
+        rows = [g for g in got if g[0] == r]
+        rates.append(sum(g[1] for g in rows) / (max(g[3] for g in rows) - min(g[2] for g in rows)))
+    desc = (f"numpy oracle in {procs} processes (one per host core, nproc = {os.cpu_count()}), each on a "
+            f"[{ORACLE_WINDOW}]^2 level-12 sub-gasket of the k=16 array (531441 members), "
+            f"{ca_steps} CA + {diff_steps} diffusion steps")
+    return rates, procs, desc
+
+
 def run_reference(args, dist, rank, world):
     if rank != 0:
         return
     ca, df = 10, 20
-    for _ in range(args.warmup):
-        oracle_sample(ca, df)
-    times = []
-    rates = []
-    rate = 0.0
-    desc = ""
-    for _ in range(args.steps):
-        rate, dt, desc = oracle_sample(ca, df)
-        times.append(dt)
-        rates.append(rate)
-    total = sum(times)
-    value = rate if not times else statistics.mean([r for r in rates])
+    rates, procs, desc = oracle_all_cores(ca, df, rounds=args.warmup + args.steps)
+    rates = rates[args.warmup:]
+    value = statistics.mean(rates)
+    per_step_s = 3 ** 12 * procs * (ca + df) / value
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, len(times)),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u8",
         "data": "synthetic (SplitMix64-seeded Bernoulli(0.5) uint8 and U[0,1) FP64 states)",
         "config": {"workload": "CPU oracle on a bounded sample of the level-16 gasket workload", "sample": desc},
-        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": procs, "nproc": os.cpu_count(),
+                         "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -438,6 +488,16 @@ def main():
                           for (wl, md, rho), (_, us) in sorted(tuned.items())},
     }
 
+    useful = {}
+    for wl in ("ca", "diffusion"):
+        for mode in (0, 1):
+            inf = plan(wl, mode).info()
+            d = 0 if wl == "ca" else 1
+            if inf["steps_per_launch"][d] > 1:
+                useful.setdefault(wl, {})["lambda" if mode == 0 else "bb"] = useful_threads(
+                    wl, inf, inf["steps_per_launch"][d], mode)
+    line["useful_threads"] = useful
+
     if rank == 0 and not args.no_detail:
         line["detail"] = kernel_detail(fr, torch, stream, lambda rho, mode: tuned[("diffusion", mode, rho)][0],
                                        lambda rho, mode: tuned[("ca", mode, rho)][0], ca_a, ca_b, u_a, u_b, hbm)
@@ -455,8 +515,10 @@ def main():
 
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, desc = oracle_sample(CA_STEPS, DIFF_STEPS)
-        line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                                "sample": desc, "seconds": dt}
+        rates, procs, desc_all = oracle_all_cores(CA_STEPS, DIFF_STEPS)
+        line["cpu_baseline"] = {"value": rates[0], "unit": "cell-updates/s", "cores": procs, "nproc": os.cpu_count(),
+                                "kind": "oracle", "sample": desc_all,
+                                "single_thread": {"value": rate, "cores": 1, "sample": desc, "seconds": dt}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     for pl, _ in tuned.values():
@@ -477,6 +539,39 @@ def kernel_launches(spl, steps, every=None):
     if steps == every and per == 1 and steps % 2 == 0:
         per = 2
     return (steps // every) * per
+
+
+def useful_threads(wl, info, spl, mode):
+    """Share of the launched work slots that advance a member cell of the
+    launch's own super-tiles (Theorem 2's parallel-space argument, counted
+    per thread slot): useful cell-updates / (slots launched x cells a slot
+    covers), per step.  Fused diffusion: a slot is one 8 x 8 block (27
+    member cells); slots = CTAs (super-tiles; BB: the whole 2^R x 2^R box)
+    x block slots per CTA, so the idle slots, the margin-box blocks (redundant:
+    evolved again by their own super-tile) and BB's discarded CTAs all count
+    as launched.  Fused automaton: a slot is one lane's two 32-cell words of
+    a task (three task slots per half warp), 64 cells."""
+    k = info["k"]
+    ctas, per_cta = info["ctas"][0 if wl == "ca" else 1], info["threads"][0 if wl == "ca" else 1]
+    out = {"ctas": ctas, "mode": "lambda" if mode == 0 else "bb"}
+    if wl == "diffusion":
+        own = 3 ** (k - 3)
+        slots = ctas * per_cta
+        out.update({"unit": "8x8 block (27 member cells)", "slots_per_cta": per_cta,
+                    "useful_fraction": own / slots})
+        if spl > 1:
+            T = info["rho"] << info["cta_levels"][1]
+            margin = 8
+            while margin < spl:
+                margin *= 2
+            box = diffusion_box_member_blocks(k, T, margin, spl)
+            out["box_blocks_per_own_block"] = box / own
+    else:
+        lanes = ctas * per_cta
+        slots = lanes * 3
+        out.update({"unit": "lane task slot (two 32-cell words)", "threads_per_cta": per_cta,
+                    "useful_fraction": 3 ** k / (slots * 64)})
+    return out
 
 
 def staging(info, d):
