@@ -432,13 +432,16 @@ def main():
     kc = kernel_launches(spl_c, CA_STEPS)
     rf_d, alu_d = launch_roofline("diffusion", info_d, spl_d, diff_ms / 1e3 / (kd * args.steps), hbm, peak_kind,
                                   DIFF_STEPS, REDUCE_EVERY)
-    rf_c, _ = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind, CA_STEPS)
+    rf_c, alu_c = launch_roofline("ca", info_c, spl_c, ca_ms / 1e3 / (kc * args.steps), hbm, peak_kind, CA_STEPS)
     # the kernel that takes most of the step, against the roof that bounds it:
-    # the fused diffusion against the FP32 pipes (its HBM view beside it)
+    # the fused kernels against their pipes (FP32 for the diffusion, the
+    # integer ALU for the automaton), each with its HBM view beside it
     if diff_ms >= ca_ms:
-        roofline, roofline_hbm, roofline_other = (alu_d or rf_d), (rf_d if alu_d else None), rf_c
+        roofline, roofline_hbm = (alu_d or rf_d), (rf_d if alu_d else None)
+        roofline_other, roofline_other_hbm = (alu_c or rf_c), (rf_c if alu_c else None)
     else:
-        roofline, roofline_hbm, roofline_other = rf_c, None, (alu_d or rf_d)
+        roofline, roofline_hbm = (alu_c or rf_c), (rf_c if alu_c else None)
+        roofline_other, roofline_other_hbm = (alu_d or rf_d), (rf_d if alu_d else None)
     # plus, per global measure, a final-sum launch (fused) or a reduce and a final sum
     launches_per_step = (kc + kd + (1 if spl_c > 1 else 2)
                          + (DIFF_STEPS // REDUCE_EVERY) * (1 if spl_d > 1 else 2))
@@ -479,6 +482,7 @@ def main():
         "roofline": roofline,
         "roofline_hbm": roofline_hbm,
         "roofline_other": roofline_other,
+        "roofline_other_hbm": roofline_other_hbm,
         "vs_hbm_floor": floors,
         "bb": None if value_bb is None else {
             "value": value_bb, "ms_per_step": 1e3 * t_bb / max(1, args.steps // 2),
@@ -504,6 +508,8 @@ def main():
 
     if rank == 0 and not args.no_detail:
         line["lambda_forms"] = lambda_forms(fr, torch, stream)
+    if rank == 0 and not args.no_detail:
+        line["smaller_configs"] = small_configs(fr, torch, stream)
     if rank == 0 and not args.no_batch:
         line["batched"] = batched(fr, torch, stream, SEED + 17)
     if rank == 0 and not args.no_adjoint:
@@ -583,10 +589,13 @@ def staging(info, d):
 def kernel_name(wl, info, spl):
     d = 0 if wl == "ca" else 1
     if spl > 1:
-        # float32: two 8 x 8 blocks per thread in the CTA classes above 288 threads
-        two = wl != "ca" and info["threads"][1] > 288
-        base = ("ca_fused_kernel<lambda>" if wl == "ca" else
-                f"diffusion_fused{'2' if two else ''}_kernel<lambda, rho={info['rho']}>")
+        # float32 by block slots per super-tile: 96 (side 128, one warp), 320
+        # (four warps, two or three blocks per thread), other classes above 288
+        # two blocks per thread, else one
+        slots = info["threads"][1]
+        kern = ("diffusion_fused_warp_kernel" if slots == 96 else "diffusion_fused3_kernel" if slots == 320 else
+                "diffusion_fused2_kernel" if slots > 288 else "diffusion_fused_kernel")
+        base = "ca_fused_kernel<lambda>" if wl == "ca" else f"{kern}<lambda, rho={info['rho']}>"
         return base + f" x{spl} steps/launch"
     kind = "tma_kernel" if info["tma"][d] else "kernel"
     return f"{'ca' if wl == 'ca' else 'diffusion'}_{kind}<lambda, rho={info['rho']}>"
@@ -650,6 +659,8 @@ _FUSED_DIFFUSION = ("paper_2004_13475_gb300/csrc/k_fused.cu", "paper_2004_13475_
 KERNEL_SOURCES = {
     "diffusion_fused_kernel": _FUSED_DIFFUSION,
     "diffusion_fused2_kernel": _FUSED_DIFFUSION,
+    "diffusion_fused3_kernel": _FUSED_DIFFUSION,
+    "diffusion_fused_warp_kernel": _FUSED_DIFFUSION,
     "ca_fused_kernel": ("paper_2004_13475_gb300/csrc/k_fused_ca.cu", "paper_2004_13475_gb300/csrc/blocks.cuh",
                         "paper_2004_13475_gb300/csrc/dfloat.cuh", "paper_2004_13475_gb300/csrc/gasket.cuh"),
 }
@@ -686,6 +697,24 @@ def measured_traffic(kernel, k):
 # FP32 peak of the plain (non-tensor) pipes: 152 SMs x 128 FP32 lanes x 2
 # flops (FMA) x 2.07 GHz (the part's maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# 32-bit logic and funnel-shift peak (the integer ALU pipe): 152 SMs x 64
+# lanes x 2.07 GHz; a probe of independent LOP3 / SHF chains measures 63.8
+# per clock per SM.
+ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
+# Integer operations of one automaton step on one 32-cell word, bit-sliced:
+# the row's three-cell sum (two funnel shifts for the left and right
+# neighbours, a three-input XOR for the sum bit and a majority for the carry:
+# 4) plus the rule on the nine-cell sum modulo 4 from the three rows' sums
+# (XOR and majority of the sum bits, XOR of the carries with that majority
+# masked to the members, and the select of alive / born: 5).  Each row sum
+# is counted once, for its own word.
+CA_OPS_PER_WORD_STEP = 9
+
+
+def ca_words_per_step(k):
+    """32-cell words holding members of the level-k gasket: every row of every
+    member 32 x 32 word tile (row y of a tile holds the member x = 0)."""
+    return 32 * 3 ** (k - 5)
 
 
 def diffusion_flops_per_step(k):
@@ -749,6 +778,14 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps, every=N
               "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
               "alg_bytes_per_launch": alg, "launch_us": launch_s * 1e6, "steps_per_launch": spl,
               "launch_kinds": ",".join(kinds) if kinds else "EE"}
+    if wl == "ca" and spl > 1:
+        ops = ca_words_per_step(info["k"]) * CA_OPS_PER_WORD_STEP * call_steps / len(kinds)
+        to = ops / launch_s / 1e12
+        alu = {"kernel": name, "bound": "alu", "achieved": to, "peak": ALU_PEAK_TOPS,
+               "peak_kind": "derived: 152 SMs x 64 integer ALU lanes x 2.07 GHz (probe: 63.8 ops/clk/SM)",
+               "unit": "Tops/s", "frac": to / ALU_PEAK_TOPS, "traffic": traffic, "alg_ops_per_launch": ops,
+               "ops_per_word_step": CA_OPS_PER_WORD_STEP, "launch_us": launch_s * 1e6,
+               "steps_per_launch": call_steps / len(kinds), "launch_kinds": ",".join(kinds)}
     if wl == "diffusion" and spl > 1:
         flops = diffusion_flops_per_step(info["k"]) * call_steps / len(kinds)
         tf = flops / launch_s / 1e12
@@ -894,6 +931,66 @@ def kernel_detail(fr, torch, stream, plan_d, plan_c, ca_a, ca_b, u_a, u_b, hbm):
             lam = out[str(rho)]["lambda"][kname]["us"]
             bb = out[str(rho)]["bb"][kname]["us"]
             out[str(rho)].setdefault("speedup_lambda_over_bb", {})[kname] = bb / lam
+    return out
+
+
+def small_configs(fr, torch, stream):
+    """The two smaller workloads of the benchmark's configuration list, each
+    with the lambda and the BB launch (plans tuned by fractal_plan_autotune):
+    k = 10, uint8 B3/S23, 10 steps, rho = 16 (1 MiB arrays: L2-resident);
+    k = 14, FP32 diffusion a = 0.2, 1000 steps with a global sum every 100
+    (1 GiB arrays; the compact records between launches, 20 MB, stay in L2).
+    Times are per call (CUDA events, mean of repeated calls)."""
+    import synth
+    out = {}
+
+    def clock(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    sptr = stream.cuda_stream
+    n = 1 << 10
+    a = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    synth.device_fill(a.data_ptr(), synth.SYNTH_BERNOULLI_U8, n, SEED, stream=sptr)
+    rec = {"workload": "gasket k=10 (1024x1024 uint8), B3/S23, 10 steps, rho=16", "l2": "L2-resident (1 MiB)"}
+    for mode, name in ((0, "lambda"), (1, "bb")):
+        p = fr.fractal_map(10, 16, mode)
+        fr.fractal_plan_autotune(p, fr.FRACTAL_U8, a, b, 3, stream)
+        t = clock(lambda: fr.fractal_step_ca(p, a, b, 10, stream), 50)
+        rec[name] = {"us_per_call": t * 1e6, "cell_updates_per_s": 3 ** 10 * 10 / t,
+                     "steps_per_launch": p.info()["steps_per_launch"][0]}
+        p.close()
+    rec["speedup_lambda_over_bb"] = rec["bb"]["us_per_call"] / rec["lambda"]["us_per_call"]
+    out["k10_ca"] = rec
+    del a, b
+    n = 1 << 14
+    a = torch.empty(n * n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    sums = torch.zeros(10, dtype=torch.float64, device="cuda")
+    synth.device_fill(a.data_ptr(), synth.SYNTH_UNIFORM_F32, n, SEED, stream=sptr)
+    rec = {"workload": "gasket k=14 (16384x16384 FP32), diffusion a=0.2, 1000 steps, global sum every 100",
+           "l2": "arrays 1 GiB each (not L2-resident); records between launches 20 MB (L2-resident)"}
+    for mode, name in ((0, "lambda"), (1, "bb")):
+        p = fr.fractal_map(14, 16, mode)
+        fr.fractal_plan_autotune(p, fr.FRACTAL_F32, a, b, 3, stream)
+        t = clock(lambda: fr.fractal_step_diffusion_sums(p, a, b, COEF, 1000, 100, sums, stream), 3)
+        rec[name] = {"ms_per_call": t * 1e3, "cell_updates_per_s": 3 ** 14 * 1000 / t,
+                     "steps_per_launch": p.info()["steps_per_launch"][1]}
+        p.close()
+    rec["speedup_lambda_over_bb"] = rec["bb"]["ms_per_call"] / rec["lambda"]["ms_per_call"]
+    out["k14_diffusion"] = rec
+    del a, b
+    torch.cuda.empty_cache()
     return out
 
 

@@ -169,6 +169,18 @@ bool make_fused(const fractal_plan_s& p, int dtype, int spl, const Launch& step,
   const int rho = 1 << p.log_rho;
   const int margin = fused_margin(spl);
   if (rho < 4) return false;
+  // margins up to 16 cells: super-tiles of side 128, one warp per CTA
+  if (margin <= 16 && rho <= 128 && (128 >> p.log_rho) >= 1) {
+    Launch st;
+    const int m = 7 - p.log_rho;
+    if (m <= kMaxLevelsPerCta && supertile_grid(p.k, p.log_rho, p.mode, m, st) &&
+        fused_threads(st.geo, rho, margin, spl) == fused_warp_slots()) {
+      fused = st;
+      fused.threads = fused_warp_slots();
+      fused.smem = 0;
+      return true;
+    }
+  }
   for (int m = kMaxLevelsPerCta; m >= 0; --m) {
     Launch st;
     if (!supertile_grid(p.k, p.log_rho, p.mode, m, st)) continue;

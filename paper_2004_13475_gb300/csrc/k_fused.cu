@@ -61,11 +61,20 @@ struct FGeo {
 
 // Compact records between the launches of one call: the 27 members of a
 // member 8 x 8 block (row-major order of the member cells) and one pad, 7
-// float4s, at record s * 3^L + t for member block t (lambda or BB rank order)
+// float4s; record s * 3^L + t for member block t (lambda or BB rank order)
 // of member super-tile s (its index in the level-R packed grid, or its BB
-// rank).  3^(k-3) records hold the whole gasket; a launch reads and writes
-// them contiguously instead of eight scattered 32-byte rows per block.
+// rank).  The records of one super-tile form a group stored float4 by
+// float4: float4 i of its block t at (group start) + i * 3^L + t, so that
+// the threads of a warp, taking consecutive blocks, read and write 16
+// consecutive bytes each.  3^(k-3) records hold the whole gasket; a launch
+// reads and writes them instead of eight scattered 32-byte rows per block.
 constexpr int kRecF4 = 7;
+
+// Float4 index of float4 0 of record `rec` (a record's float4s are nb apart).
+__device__ __forceinline__ int64_t rec_base(int64_t rec, int nb) {
+  const int64_t t = rec % nb;
+  return (rec - t) * kRecF4 + t;
+}
 
 // Record of the member block (GX, GY) (block coordinates in the array).
 template <int MODE>
@@ -214,9 +223,9 @@ __device__ __forceinline__ double write_block(const float (&u)[kB * kB], const F
 #pragma unroll
     for (int q = 0; q < kB * kB; ++q)
       if (amem(q % kB, q / kB)) rec_set(r, m++, u[q]);
-    float4* p = reinterpret_cast<float4*>(pout) + rec * kRecF4;
+    float4* p = reinterpret_cast<float4*>(pout) + rec_base(rec, f.nb);
 #pragma unroll
-    for (int i = 0; i < kRecF4; ++i) p[i] = r[i];
+    for (int i = 0; i < kRecF4; ++i) p[(int64_t)i * f.nb] = r[i];
     return sum;
   }
   float* o = out + (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
@@ -255,10 +264,10 @@ __device__ __forceinline__ void stage_block(float (&u)[kB * kB], const FGeo& f, 
 #pragma unroll
   for (int q = 0; q < kB * kB; ++q) u[q] = 0.f;
   if (pin) {
-    const float4* p = reinterpret_cast<const float4*>(pin) + rec * kRecF4;
+    const float4* p = reinterpret_cast<const float4*>(pin) + rec_base(rec, f.nb);
     float4 r[kRecF4];
 #pragma unroll
-    for (int i = 0; i < kRecF4; ++i) r[i] = __ldg(p + i);
+    for (int i = 0; i < kRecF4; ++i) r[i] = __ldg(p + (int64_t)i * f.nb);
     int m = 0;
 #pragma unroll
     for (int q = 0; q < kB * kB; ++q)
@@ -545,6 +554,252 @@ __device__ __forceinline__ double fused_supertile2(const float* __restrict__ in,
   return sum;
 }
 
+// One warp per CTA: super-tiles of side 128 (81 member blocks) with margins
+// of at most 16 cells (at most 9 box blocks within reach), 96 block slots,
+// three per lane (slots t, t + 32 and t + 64 of lane t: the first two paired
+// in float2 as in fused_supertile2, the third on its own).  With a single
+// warp the per-step port exchange needs only __syncwarp: no CTA waits on a
+// slower warp of its own, and the CTAs, one warp each, spread evenly over the
+// SM's four sub-partitions whatever their number.  The port arrays hold
+// 96 + 2 slots per parity (the zero slot at 96).  Descriptors as for the
+// other fused launches (96 per super-tile).
+constexpr int kWarpSlots = 96;
+constexpr int kWarpSide = 128;
+
+template <int MODE>
+__device__ __forceinline__ double fused_supertile_w(const float* __restrict__ in, float* __restrict__ out, float a,
+                                                    int nsteps, const FGeo& f, int OX, int OY, float* ports,
+                                                    bool want_sum, const float* __restrict__ pin,
+                                                    float* __restrict__ pout, int64_t srec,
+                                                    const int4* __restrict__ desc) {
+  constexpr int kSl = kWarpSlots + 2;
+  constexpr int zero = kWarpSlots;
+  const int t = threadIdx.x;
+  float* P0 = ports;
+  float* PR = ports + 2 * kSl;
+  float* PD = ports + 4 * kSl;
+  const FSetup s0 = unpack_setup(__ldg(desc + t)), s1 = unpack_setup(__ldg(desc + t + 32)),
+               s2 = unpack_setup(__ldg(desc + t + 64));
+  float2 u[kB * kB];
+  float v[kB * kB];
+  {
+    float w0[kB * kB], w1[kB * kB];
+    if (s0.active) {
+      stage_block(w0, f, OX + s0.bx, OY + s0.by, in, pin, t < f.nb ? srec + t : (int64_t)s0.rec);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kB * kB; ++q) w0[q] = 0.f;
+    }
+    if (s1.active) {
+      stage_block(w1, f, OX + s1.bx, OY + s1.by, in, pin, t + 32 < f.nb ? srec + t + 32 : (int64_t)s1.rec);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kB * kB; ++q) w1[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) u[q] = make_float2(w0[q], w1[q]);
+  }
+  if (s2.active) {
+    stage_block(v, f, OX + s2.bx, OY + s2.by, in, pin, t + 64 < f.nb ? srec + t + 64 : (int64_t)s2.rec);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) v[q] = 0.f;
+  }
+  // the ports' degrees: 2, 1, 1 inside the block plus the member neighbour
+  // blocks (negated for the paired step)
+  const float2 nd0 = make_float2(-(2.f + (s0.fu ? 1.f : 0.f) + (s0.fl ? 1.f : 0.f)),
+                                 -(2.f + (s1.fu ? 1.f : 0.f) + (s1.fl ? 1.f : 0.f)));
+  const float2 ndr = make_float2(-(1.f + (s0.fr ? 1.f : 0.f)), -(1.f + (s1.fr ? 1.f : 0.f)));
+  const float2 ndd = make_float2(-(1.f + (s0.fd ? 1.f : 0.f)), -(1.f + (s1.fd ? 1.f : 0.f)));
+  const float d0 = 2.f + (s2.fu ? 1.f : 0.f) + (s2.fl ? 1.f : 0.f), dr = 1.f + (s2.fr ? 1.f : 0.f),
+              dd = 1.f + (s2.fd ? 1.f : 0.f);
+  const float2 a2 = make_float2(a, a);
+  const bool act01 = s0.active || s1.active;
+  P0[t] = u[0].x;
+  P0[t + 32] = u[0].y;
+  P0[t + 64] = v[0];
+  PR[t] = u[kB - 1].x;
+  PR[t + 32] = u[kB - 1].y;
+  PR[t + 64] = v[kB - 1];
+  PD[t] = u[(kB - 1) * kB].x;
+  PD[t + 32] = u[(kB - 1) * kB].y;
+  PD[t + 64] = v[(kB - 1) * kB];
+  if (t == 0) {
+    P0[zero] = P0[kSl + zero] = 0.f;
+    PR[zero] = PR[kSl + zero] = 0.f;
+    PD[zero] = PD[kSl + zero] = 0.f;
+  }
+  __syncwarp();
+
+  // two steps per iteration: the port offsets of both parities are fixed
+#pragma unroll 2
+  for (int s = 0; s < nsteps; ++s) {
+    const int cur = (s & 1) * kSl, nxt = kSl - cur;
+    if (act01) {
+      const float2 vu = make_float2(PD[cur + s0.up], PD[cur + s1.up]);
+      const float2 vl = make_float2(PR[cur + s0.lf], PR[cur + s1.lf]);
+      const float2 vr = make_float2(P0[cur + s0.rt], P0[cur + s1.rt]);
+      const float2 vd = make_float2(P0[cur + s0.dn], P0[cur + s1.dn]);
+      block_step2(u, a2, vu, vl, vr, vd, nd0, ndr, ndd);
+    }
+    if (s2.active)
+      block_step(v, a, PD[cur + s2.up], PR[cur + s2.lf], P0[cur + s2.rt], P0[cur + s2.dn], d0, dr, dd);
+    P0[nxt + t] = u[0].x;
+    P0[nxt + t + 32] = u[0].y;
+    P0[nxt + t + 64] = v[0];
+    PR[nxt + t] = u[kB - 1].x;
+    PR[nxt + t + 32] = u[kB - 1].y;
+    PR[nxt + t + 64] = v[kB - 1];
+    PD[nxt + t] = u[(kB - 1) * kB].x;
+    PD[nxt + t + 32] = u[(kB - 1) * kB].y;
+    PD[nxt + t + 64] = v[(kB - 1) * kB];
+    __syncwarp();
+  }
+
+  // write back the super-tile's member blocks (not the boxes)
+  double sum = 0.0;
+  if (s0.active && t < f.nb) {
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].x;
+    sum += write_block(w, f, OX + s0.bx, OY + s0.by, want_sum, out, pout, srec + t);
+  }
+  if (s1.active && t + 32 < f.nb) {
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].y;
+    sum += write_block(w, f, OX + s1.bx, OY + s1.by, want_sum, out, pout, srec + t + 32);
+  }
+  if (s2.active && t + 64 < f.nb) sum += write_block(v, f, OX + s2.bx, OY + s2.by, want_sum, out, pout, srec + t + 64);
+  return sum;
+}
+
+// Four warps, 320 slots (super-tile side 256 with margins of 33 to 64 cells,
+// at most 71 box blocks within a reach of 56): every thread takes slots t
+// and t + 128 (paired as in fused_supertile2), and the lanes of two of the
+// four warps a third slot 256 + 32 k + lane (k = 0, 1), stepped on its own.
+// A CTA of five warps (two slots each) would put two of its warps on one SM
+// sub-partition, which then sets the pace of every per-step barrier; with
+// four warps each sub-partition holds one warp of the CTA.  The warps with a
+// third slot are 0 and 2 or 1 and 3 by the parity of the CTA, so that the
+// CTAs resident on one SM spread the heavier warps over all four
+// sub-partitions.
+constexpr int kQ3Threads = 128;
+constexpr int kQ3Slots = 320;
+
+template <int MODE>
+__device__ __forceinline__ double fused_supertile3(const float* __restrict__ in, float* __restrict__ out, float a,
+                                                   int nsteps, const FGeo& f, int OX, int OY, float* ports,
+                                                   bool want_sum, const float* __restrict__ pin,
+                                                   float* __restrict__ pout, int64_t srec,
+                                                   const int4* __restrict__ desc, int heavy) {
+  constexpr int kSl = kQ3Slots + 2;
+  constexpr int zero = kQ3Slots;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int k3 = warp == heavy ? 0 : warp == (heavy ^ 2) ? 1 : -1;  // warp-uniform
+  const int q0 = t, q1 = t + kQ3Threads, q2 = 2 * kQ3Threads + 32 * (k3 < 0 ? 0 : k3) + lane;
+  float* P0 = ports;
+  float* PR = ports + 2 * kSl;
+  float* PD = ports + 4 * kSl;
+  const FSetup s0 = unpack_setup(__ldg(desc + q0)), s1 = unpack_setup(__ldg(desc + q1));
+  FSetup s2 = s0;
+  s2.active = false;
+  if (k3 >= 0) s2 = unpack_setup(__ldg(desc + q2));
+  float2 u[kB * kB];
+  float v[kB * kB];
+  {
+    float w0[kB * kB], w1[kB * kB];
+    if (s0.active) {
+      stage_block(w0, f, OX + s0.bx, OY + s0.by, in, pin, q0 < f.nb ? srec + q0 : (int64_t)s0.rec);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kB * kB; ++q) w0[q] = 0.f;
+    }
+    if (s1.active) {
+      stage_block(w1, f, OX + s1.bx, OY + s1.by, in, pin, q1 < f.nb ? srec + q1 : (int64_t)s1.rec);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kB * kB; ++q) w1[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) u[q] = make_float2(w0[q], w1[q]);
+  }
+  if (s2.active) {
+    stage_block(v, f, OX + s2.bx, OY + s2.by, in, pin, q2 < f.nb ? srec + q2 : (int64_t)s2.rec);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) v[q] = 0.f;
+  }
+  const float2 nd0 = make_float2(-(2.f + (s0.fu ? 1.f : 0.f) + (s0.fl ? 1.f : 0.f)),
+                                 -(2.f + (s1.fu ? 1.f : 0.f) + (s1.fl ? 1.f : 0.f)));
+  const float2 ndr = make_float2(-(1.f + (s0.fr ? 1.f : 0.f)), -(1.f + (s1.fr ? 1.f : 0.f)));
+  const float2 ndd = make_float2(-(1.f + (s0.fd ? 1.f : 0.f)), -(1.f + (s1.fd ? 1.f : 0.f)));
+  const float d0 = 2.f + (s2.fu ? 1.f : 0.f) + (s2.fl ? 1.f : 0.f), dr = 1.f + (s2.fr ? 1.f : 0.f),
+              dd = 1.f + (s2.fd ? 1.f : 0.f);
+  const float2 a2 = make_float2(a, a);
+  const bool act01 = s0.active || s1.active;
+  P0[q0] = u[0].x;
+  P0[q1] = u[0].y;
+  PR[q0] = u[kB - 1].x;
+  PR[q1] = u[kB - 1].y;
+  PD[q0] = u[(kB - 1) * kB].x;
+  PD[q1] = u[(kB - 1) * kB].y;
+  if (k3 >= 0) {
+    P0[q2] = v[0];
+    PR[q2] = v[kB - 1];
+    PD[q2] = v[(kB - 1) * kB];
+  }
+  if (t == 0) {
+    P0[zero] = P0[kSl + zero] = 0.f;
+    PR[zero] = PR[kSl + zero] = 0.f;
+    PD[zero] = PD[kSl + zero] = 0.f;
+  }
+  __syncthreads();
+
+  // two steps per iteration: the port offsets of both parities are fixed
+#pragma unroll 2
+  for (int s = 0; s < nsteps; ++s) {
+    const int cur = (s & 1) * kSl, nxt = kSl - cur;
+    if (act01) {
+      const float2 vu = make_float2(PD[cur + s0.up], PD[cur + s1.up]);
+      const float2 vl = make_float2(PR[cur + s0.lf], PR[cur + s1.lf]);
+      const float2 vr = make_float2(P0[cur + s0.rt], P0[cur + s1.rt]);
+      const float2 vd = make_float2(P0[cur + s0.dn], P0[cur + s1.dn]);
+      block_step2(u, a2, vu, vl, vr, vd, nd0, ndr, ndd);
+    }
+    if (k3 >= 0) {
+      if (s2.active)
+        block_step(v, a, PD[cur + s2.up], PR[cur + s2.lf], P0[cur + s2.rt], P0[cur + s2.dn], d0, dr, dd);
+      P0[nxt + q2] = v[0];
+      PR[nxt + q2] = v[kB - 1];
+      PD[nxt + q2] = v[(kB - 1) * kB];
+    }
+    P0[nxt + q0] = u[0].x;
+    P0[nxt + q1] = u[0].y;
+    PR[nxt + q0] = u[kB - 1].x;
+    PR[nxt + q1] = u[kB - 1].y;
+    PD[nxt + q0] = u[(kB - 1) * kB].x;
+    PD[nxt + q1] = u[(kB - 1) * kB].y;
+    __syncthreads();
+  }
+
+  // write back the super-tile's member blocks (slots 256 and up are box blocks)
+  double sum = 0.0;
+  if (s0.active && q0 < f.nb) {
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].x;
+    sum += write_block(w, f, OX + s0.bx, OY + s0.by, want_sum, out, pout, srec + q0);
+  }
+  if (s1.active && q1 < f.nb) {
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].y;
+    sum += write_block(w, f, OX + s1.bx, OY + s1.by, want_sum, out, pout, srec + q1);
+  }
+  return sum;
+}
+
 __device__ __forceinline__ FGeo make_fgeo(int n, int T, int M, int reach, int log_rho, int R) {
   FGeo f;
   f.n = n;
@@ -633,6 +888,57 @@ __global__ void __launch_bounds__(PMAX, MINB) diffusion_fused2_kernel(const floa
                                                            desc + st * 2 * blockDim.x);
   if (partials) {
     const double s = block_sum<double>(mine, red);
+    if (threadIdx.x == 0) partials[cta_id()] = s;
+  }
+}
+
+// One super-tile per CTA of four warps and 320 slots (fused_supertile3).
+template <int MODE>
+__global__ void __launch_bounds__(kQ3Threads, 4) diffusion_fused3_kernel(const float* __restrict__ in,
+                                                                         float* __restrict__ out, float a, int nsteps,
+                                                                         int M, int reach, int log_rho, Geo g,
+                                                                         double* __restrict__ partials,
+                                                                         const float* __restrict__ pin,
+                                                                         float* __restrict__ pout,
+                                                                         const int4* __restrict__ desc) {
+  __shared__ __align__(16) float ports[6 * (kQ3Slots + 2)];
+  __shared__ double red[32];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) {
+    if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
+    return;
+  }
+  const FGeo f = make_fgeo(g.n, g.T, M, reach, log_rho, g.R);
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
+  const double mine = fused_supertile3<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, ports, partials != nullptr,
+                                             pin, pout, st * f.nb, desc + st * kQ3Slots, (int)(cta_id() & 1));
+  if (partials) {
+    const double s = block_sum<double>(mine, red);
+    if (threadIdx.x == 0) partials[cta_id()] = s;
+  }
+}
+
+// One super-tile of side 128 per CTA of one warp (fused_supertile_w).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(32, MINB) diffusion_fused_warp_kernel(const float* __restrict__ in,
+                                                                         float* __restrict__ out, float a, int nsteps,
+                                                                         int M, int reach, int log_rho, Geo g,
+                                                                         double* __restrict__ partials,
+                                                                         const float* __restrict__ pin,
+                                                                         float* __restrict__ pout,
+                                                                         const int4* __restrict__ desc) {
+  __shared__ __align__(16) float ports[6 * (kWarpSlots + 2)];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) {
+    if (partials && threadIdx.x == 0) partials[cta_id()] = 0.0;
+    return;
+  }
+  const FGeo f = make_fgeo(g.n, g.T, M, reach, log_rho, g.R);
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
+  const double mine = fused_supertile_w<MODE>(in, out, a, nsteps, f, sx << f.L, sy << f.L, ports, partials != nullptr,
+                                              pin, pout, st * f.nb, desc + st * kWarpSlots);
+  if (partials) {
+    const double s = warp_sum(mine);
     if (threadIdx.x == 0) partials[cta_id()] = s;
   }
 }
@@ -796,6 +1102,15 @@ cudaError_t go2(const Launch& L, const float* in, float* out, float a, int nstep
 }
 
 
+// One warp per CTA (super-tile side 128, 96 slots, with descriptors).
+template <int MODE>
+cudaError_t gow(const Launch& L, const float* in, float* out, float a, int nsteps, int margin, int reach, int log_rho,
+                double* partials, const float* pin, float* pout, const int4* desc, cudaStream_t s) {
+  diffusion_fused_warp_kernel<MODE, 16><<<L.grid, 32, 0, s>>>(in, out, a, nsteps, margin, reach, log_rho, L.geo,
+                                                                partials, pin, pout, desc);
+  return cudaGetLastError();
+}
+
 int member_blocks(int T) {
   int nb = 1;
   for (int i = 0; i < ilog2c(T) - 3; ++i) nb *= 3;
@@ -915,6 +1230,18 @@ cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, int reach,
   // for the larger CTA classes (margins of 64 cells and more: launches of
   // many steps, bound by their arithmetic); short launches are bound by their
   // loads and stores, which one block per thread keeps more of in flight
+  if (desc && L.geo.T == kWarpSide && L.threads == kWarpSlots)
+    return mode == kLambda ? gow<kLambda>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s)
+                           : gow<kBB>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s);
+  if (desc && L.threads == kQ3Slots) {
+    if (mode == kLambda)
+      diffusion_fused3_kernel<kLambda><<<L.grid, kQ3Threads, 0, s>>>(in, out, a, nsteps, margin, reach, log_rho, L.geo,
+                                                                     partials, pin, pout, desc);
+    else
+      diffusion_fused3_kernel<kBB><<<L.grid, kQ3Threads, 0, s>>>(in, out, a, nsteps, margin, reach, log_rho, L.geo,
+                                                                 partials, pin, pout, desc);
+    return cudaGetLastError();
+  }
   if (desc && L.threads > 288)
     return mode == kLambda ? go2<kLambda>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s)
                            : go2<kBB>(L, in, out, a, nsteps, margin, reach, log_rho, partials, pin, pout, desc, s);
@@ -938,6 +1265,8 @@ cudaError_t launch_fused_describe(int mode, int log_rho, int margin, int reach, 
     fused_describe_kernel<kBB><<<L.grid, L.threads, smem, s>>>(L.geo, margin, reach, log_rho, desc);
   return cudaGetLastError();
 }
+
+int fused_warp_slots() { return kWarpSlots; }
 
 int64_t fused_records(int k) {
   int64_t r = 1;

@@ -79,6 +79,9 @@ int fused_record_bytes();
 int fused_margin(int steps_per_launch);
 int fused_smem_bytes(const Geo& g, int margin, int reach);
 int fused_threads(const Geo& g, int rho, int margin, int reach);
+// Block slots of the one-warp fused launch (super-tiles of side 128, margins
+// up to 16 cells).
+int fused_warp_slots();
 // Most member blocks of the margin boxes (W blocks wide) of a level-L
 // super-tile within `reach` cells of it.
 int box_cap_reach(int L, int W, int reach);

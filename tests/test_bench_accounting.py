@@ -59,3 +59,23 @@ def test_box_blocks_within_reach_agree_with_the_library():
         assert c <= supertiles * fr.fractal_fused_box_blocks(T, M, reach)
         prev = c
     assert bench.diffusion_box_member_blocks(k, T, M, 50) < full
+
+
+def test_automaton_words_are_the_member_holding_row_segments():
+    """The automaton's ALU accounting counts one 32-cell word per row of every
+    member 32 x 32 word tile: exactly the 32-aligned row segments of the
+    array that hold at least one gasket member (brute force over the
+    oracle's membership)."""
+    import numpy as np
+    for k in range(5, 11):
+        n = 1 << k
+        mask = oracle.member_mask(n)
+        holding = mask.reshape(n, n // 32, 32).any(axis=2)
+        assert int(np.count_nonzero(holding)) == bench.ca_words_per_step(k)
+
+
+def test_automaton_ops_per_word_by_hand():
+    # per word and step: the row's three-cell sum (2 funnel shifts, sum bit,
+    # carry bit) and the rule modulo 4 (5 three-input logic operations)
+    assert bench.CA_OPS_PER_WORD_STEP == 4 + 5
+    assert abs(bench.ALU_PEAK_TOPS - 152 * 64 * 2.07e-3) < 1e-9
