@@ -21,23 +21,31 @@
 // diffusion's 4-neighbour ones: the corner cell (T-1, 0) reaches (T, M) by M
 // diagonal moves).  For M <= 31 these are the words of column -1 (left,
 // bottom), 0 (top, bottom) and T/32 (right).  The kernel stages them with
-// the margin rounded up to even, ME, and the right box to rows [-ME, ME+1],
-// so that every box piece starts on an even row and has an even number of
-// rows (the words added belong to no other task: staging more of the state
-// is always correct).  Box words are evolved with the tiles; cells whose
+// the margin rounded up to a multiple of 8, ME8, and the right box to rows
+// [-ME8, ME8 + 8), so that every box piece starts on a row that is a
+// multiple of 8 and has a multiple of 8 rows (the words added belong to no
+// other task: staging more of the state is always correct).  Box words are
+// evolved with the tiles; cells whose
 // neighbours were not staged go wrong from the box edge inwards, one cell
 // per step, and never reach the super-tile within s steps.
 //
 // Tasks.  A task is one word column of at most 32 consecutive rows (a word
-// tile, or a piece of a box), taken by a half warp: lane i of the half keeps
-// rows 2i and 2i + 1.  The bit image is stored by columns (a column's rows
-// are consecutive words), so a lane's two words are one 8-byte access.  Each
-// step a lane reads rows 2i-1 .. 2i+2 of its column and of the columns left
-// and right, forms each row's three-cell horizontal sum (funnel shifts with
-// the left word's top cell and the right word's bottom cell, a full adder),
-// adds three of them for each of its two rows, applies the rule and masks
-// births outside the gasket.  Every staged word is the word of exactly one
-// task lane; every other word of the image is 0 and stays 0.
+// tile, or a piece of a box), taken by eight lanes: lane i of the eight keeps
+// rows 4i .. 4i + 3 of it in registers.  The bit image is stored by columns
+// (a column's rows are consecutive words, every four of them one 16-byte
+// group), so a lane's four words, and the four beside them in the columns
+// left and right, are one 16-byte access each, and the eight lanes of a task
+// read 128 consecutive bytes (no bank conflict).  Each step a lane forms the
+// three-cell horizontal sums of its four rows (funnel shifts with the left
+// word's top cell and the right word's bottom cell, a full adder), takes
+// the sums of the rows above and below from the neighbouring lanes by
+// shuffles (the first and last lane of a task form them from the image), and
+// applies the rule to its four rows.  Box pieces are staged from a row that
+// is a multiple of 8 with a multiple of 8 rows (the margin rounded up to
+// ME8, the right box to rows [-ME8, ME8 + 8)), so that a lane holds four
+// rows of its task or none; the words added belong to no other task.  Every
+// staged word is the word of exactly one task lane; every other word of the
+// image is 0 and stays 0.
 //
 // The rule modulo 4.  No member cell of the gasket has more than 5 member
 // neighbours (the neighbourhood of a cell inside one of the three copies of
@@ -61,13 +69,15 @@
 namespace fractal {
 namespace {
 
-constexpr int kCaSlots = 3;  // tasks per half warp, at most
-constexpr int kCaRow0 = 34;  // image row of super-tile row 0
+constexpr int kCaRows = 4;   // rows per lane
+constexpr int kCaLanes = 8;  // lanes per task (32 / kCaRows)
+constexpr int kCaRow0 = 36;  // image row of super-tile row 0 (a multiple of 4)
 
-// Image geometry: word columns [-2, T/32 + 1] of rows [-34, T + 34) whatever
-// the margin (the box pieces reach rows -ME .. T + ME - 1 and a lane reads one
-// row beyond its pair on each side), so that a column's stride is a
-// compile-time constant.  Word (c, y) is at (c + 2) * ca_col(T) + y + 34.
+// Image geometry: word columns [-2, T/32 + 1] of rows [-36, T + 36) whatever
+// the margin (the box pieces reach rows -32 .. T + 31 and a lane reads one
+// row beyond its four on each side), so that a column's stride is a
+// compile-time constant and every lane's eight rows are 16-byte aligned.
+// Word (c, y) is at (c + 2) * ca_col(T) + y + 36.
 __host__ __device__ constexpr int ca_cols(int T) { return (T >> 5) + 4; }
 __host__ __device__ constexpr int ca_col(int T) { return T + 2 * kCaRow0; }
 __host__ __device__ constexpr int ca_image_words(int T) { return ca_cols(T) * ca_col(T); }
@@ -75,9 +85,9 @@ __host__ __device__ constexpr int ca_image_words(int T) { return ca_cols(T) * ca
 // Tasks of a super-tile: word tiles first, then the seven box pieces.
 __host__ __device__ inline int ca_tasks(int wtiles) { return wtiles + 7; }
 
-// Task -> (word column c, first row y0, rows) in super-tile coordinates; ME:
-// the margin rounded up to even.  y0 and rows are even.
-__device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, int T, int ME, int& c, int& y0,
+// Task -> (word column c, first row y0, rows) in super-tile coordinates; ME8:
+// the margin rounded up to a multiple of 8.  y0 and rows are multiples of 8.
+__device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, int T, int ME8, int& c, int& y0,
                                         int& rows) {
   if (j < wtiles) {
     const uint32_t e = tab[j];
@@ -86,15 +96,15 @@ __device__ __forceinline__ void ca_task(int j, int wtiles, const uint32_t* tab, 
     rows = 32;
     return;
   }
-  const int right = 2 * ME + 2;  // rows of the right box, [-ME, ME + 1]
+  const int right = 2 * ME8 + 8;  // rows of the right box, [-ME8, ME8 + 8)
   switch (j - wtiles) {
-    case 0: c = -1; y0 = 0; rows = ME; return;                                   // left
-    case 1: c = 0; y0 = -ME; rows = ME; return;                                  // top
-    case 2: c = T >> 5; y0 = -ME; rows = min(right, 32); return;                 // right, in pieces of 32 rows
-    case 3: c = T >> 5; y0 = -ME + 32; rows = min(max(right - 32, 0), 32); return;
-    case 4: c = T >> 5; y0 = -ME + 64; rows = max(right - 64, 0); return;
-    case 5: c = -1; y0 = T; rows = ME; return;                                   // bottom, left word
-    default: c = 0; y0 = T; rows = ME; return;                                   // bottom, right word
+    case 0: c = -1; y0 = 0; rows = ME8; return;                                  // left
+    case 1: c = 0; y0 = -ME8; rows = ME8; return;                                // top
+    case 2: c = T >> 5; y0 = -ME8; rows = min(right, 32); return;                // right, in pieces of 32
+    case 3: c = T >> 5; y0 = -ME8 + 32; rows = min(max(right - 32, 0), 32); return;
+    case 4: c = T >> 5; y0 = -ME8 + 64; rows = max(right - 64, 0); return;
+    case 5: c = -1; y0 = T; rows = ME8; return;                                  // bottom, left word
+    default: c = 0; y0 = T; rows = ME8; return;                                  // bottom, right word
   }
 }
 
@@ -128,7 +138,7 @@ __device__ __forceinline__ uint32_t life_rule_mod4(uint32_t us, uint32_t uk, uin
 // TT: the super-tile side, a compile-time constant so that the column stride
 // and the neighbour offsets of a word are immediates.
 template <int MODE, int TT>
-__global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+__global__ void __launch_bounds__(704, 2) ca_fused_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                                        int nsteps, int M, Geo g,
                                                        unsigned long long* __restrict__ partials,
                                                        const uint32_t* __restrict__ pin, uint32_t* __restrict__ pout) {
@@ -148,7 +158,7 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
   for (int i = 0; i < (wlev + 1) / 2; ++i) wlw *= 3;
   constexpr int CW = ca_col(TT);                       // words per image column
   constexpr int img = ca_image_words(TT);
-  const int ME = M + (M & 1);
+  const int ME8 = (M + 7) & ~7;
   uint32_t* tab = reinterpret_cast<uint32_t*>(sm);
   uint32_t* A = tab + tab_words(wtiles);
   uint32_t* B = A + img;
@@ -187,74 +197,88 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
     reinterpret_cast<uint4*>(A)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 
-  // this lane's row pair of each of its half warp's tasks: image offset of
-  // the first row and the two rows' member bits
-  const int sub = threadIdx.x & 15, hw = threadIdx.x >> 4, nh = blockDim.x >> 4;
+  // this lane's four rows of its task: image offset of the first row, the
+  // rows' member bits and words (the lane is their only writer)
+  const int sub = threadIdx.x & (kCaLanes - 1), j = threadIdx.x / kCaLanes;
   const int ntasks = ca_tasks(wtiles);
-  int off[kCaSlots];
-  uint32_t mk0[kCaSlots], mk1[kCaSlots];
-  uint2 own[kCaSlots];  // the pair's words (the lane is their only writer)
+  int off = -1, c = 0, y = 0;
+  bool last = false;  // the task's last lane with rows: the row below comes from the image
+  uint32_t mk[kCaRows], w[kCaRows];
 #pragma unroll
-  for (int k = 0; k < kCaSlots; ++k) {
-    off[k] = -1;
-    mk0[k] = mk1[k] = 0u;
-    own[k] = make_uint2(0u, 0u);
-    const int j = hw + k * nh;
-    if (j >= ntasks) continue;
-    int c, y0, rows;
-    ca_task(j, wtiles, tab, T, ME, c, y0, rows);
-    if (2 * sub >= rows) continue;
-    const int y = y0 + 2 * sub;
-    const int gx0 = ox + 32 * c, gy = oy + y;
-    off[k] = (c + 2) * CW + y + kCaRow0;
-    if ((unsigned)gx0 < (unsigned)n) {
-      mk0[k] = chunk_members<32>(gx0, gy, n);
-      mk1[k] = chunk_members<32>(gx0, gy + 1, n);
-    }
-    uint32_t w0 = 0u, w1 = 0u;
-    if (pin) {  // a member word: its word tile is a member
-      if (mk0[k]) w0 = __ldg(pin + (j < wtiles ? srec + j : tile_record(gx0 >> 5, gy >> 5)) * 32 + (gy & 31));
-      if (mk1[k])
-        w1 = __ldg(pin + (j < wtiles ? srec + j : tile_record(gx0 >> 5, (gy + 1) >> 5)) * 32 + ((gy + 1) & 31));
-    } else {
-      uint4 r0[2], r1[2];
-      if (mk0[k]) {
-        const uint4* q = reinterpret_cast<const uint4*>(in + (size_t)gy * n + gx0);
-        r0[0] = __ldg(q);
-        r0[1] = __ldg(q + 1);
+  for (int r = 0; r < kCaRows; ++r) mk[r] = w[r] = 0u;
+  if (j < ntasks) {
+    int y0, rows;
+    ca_task(j, wtiles, tab, T, ME8, c, y0, rows);
+    if (kCaRows * sub < rows) {
+      y = y0 + kCaRows * sub;
+      last = kCaRows * (sub + 1) >= rows;
+      const int gx0 = ox + 32 * c, gy = oy + y;
+      off = (c + 2) * CW + y + kCaRow0;
+      if ((unsigned)gx0 < (unsigned)n) {
+#pragma unroll
+        for (int r = 0; r < kCaRows; ++r) mk[r] = chunk_members<32>(gx0, gy + r, n);
       }
-      if (mk1[k]) {
-        const uint4* q = reinterpret_cast<const uint4*>(in + (size_t)(gy + 1) * n + gx0);
-        r1[0] = __ldg(q);
-        r1[1] = __ldg(q + 1);
+      if (mk[0] | mk[1] | mk[2] | mk[3]) {
+        if (pin) {  // the four rows lie in one member word tile: 16 bytes of its record
+          const int64_t rec = j < wtiles ? srec + j : tile_record(gx0 >> 5, gy >> 5);
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(pin + rec * 32 + (gy & 31)));
+          w[0] = v.x;
+          w[1] = v.y;
+          w[2] = v.z;
+          w[3] = v.w;
+        } else {
+#pragma unroll
+          for (int r = 0; r < kCaRows; ++r) {
+            if (!mk[r]) continue;
+            const uint4* q = reinterpret_cast<const uint4*>(in + (size_t)(gy + r) * n + gx0);
+            w[r] = pack32(__ldg(q), __ldg(q + 1));
+          }
+        }
       }
-      if (mk0[k]) w0 = pack32(r0[0], r0[1]);
-      if (mk1[k]) w1 = pack32(r1[0], r1[1]);
+#pragma unroll
+      for (int r = 0; r < kCaRows; ++r) w[r] &= mk[r];
+      *reinterpret_cast<uint4*>(A + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    own[k] = make_uint2(w0 & mk0[k], w1 & mk1[k]);
-    *reinterpret_cast<uint2*>(A + off[k]) = own[k];
   }
   __syncthreads();
 
-  // unrolled: the image pointers of both parities are fixed
-#pragma unroll 4
+  // unrolled: the image pointers of both parities are fixed; every lane takes
+  // part in the shuffles (lanes without rows carry zeros)
+  const bool first = sub == 0;
+#pragma unroll 2
   for (int t = 0; t < nsteps; ++t) {
+    uint32_t s[kCaRows + 2], q[kCaRows + 2];  // horizontal sums of rows y-1 .. y+4
+    const uint32_t* p = A + (off >= 0 ? off : kCaRow0);
+    if (off >= 0) {
+      const uint4 l = *reinterpret_cast<const uint4*>(p - CW), r = *reinterpret_cast<const uint4*>(p + CW);
+      row_sum3(l.x, w[0], r.x, s[1], q[1]);
+      row_sum3(l.y, w[1], r.y, s[2], q[2]);
+      row_sum3(l.z, w[2], r.z, s[3], q[3]);
+      row_sum3(l.w, w[3], r.w, s[4], q[4]);
+    } else {
 #pragma unroll
-    for (int k = 0; k < kCaSlots; ++k) {
-      if (off[k] < 0) continue;
-      const uint32_t* p = A + off[k];
-      uint32_t s[4], q[4];  // horizontal sums of rows y-1 .. y+2
-      const uint2 cm = own[k];
-      const uint2 lm = *reinterpret_cast<const uint2*>(p - CW);
-      const uint2 rm = *reinterpret_cast<const uint2*>(p + CW);
-      row_sum3(p[-CW - 1], p[-1], p[CW - 1], s[0], q[0]);
-      row_sum3(lm.x, cm.x, rm.x, s[1], q[1]);
-      row_sum3(lm.y, cm.y, rm.y, s[2], q[2]);
-      row_sum3(p[-CW + 2], p[2], p[CW + 2], s[3], q[3]);
-      const uint32_t o0 = life_rule_mod4(s[0], q[0], s[1], q[1], s[2], q[2], cm.x, mk0[k]);
-      const uint32_t o1 = life_rule_mod4(s[1], q[1], s[2], q[2], s[3], q[3], cm.y, mk1[k]);
-      own[k] = make_uint2(o0, o1);
-      *reinterpret_cast<uint2*>(B + off[k]) = own[k];
+      for (int r = 1; r <= kCaRows; ++r) s[r] = q[r] = 0u;
+    }
+    // the row above is the previous lane's last, the row below the next lane's first
+    s[0] = __shfl_up_sync(0xffffffffu, s[kCaRows], 1, kCaLanes);
+    q[0] = __shfl_up_sync(0xffffffffu, q[kCaRows], 1, kCaLanes);
+    s[kCaRows + 1] = __shfl_down_sync(0xffffffffu, s[1], 1, kCaLanes);
+    q[kCaRows + 1] = __shfl_down_sync(0xffffffffu, q[1], 1, kCaLanes);
+    if (off >= 0) {
+      if (first) {  // row y - 1: the last word of the 16-byte groups above, in the three columns
+        const uint32_t lu = reinterpret_cast<const uint4*>(p - CW)[-1].w, cu = reinterpret_cast<const uint4*>(p)[-1].w,
+                       ru = reinterpret_cast<const uint4*>(p + CW)[-1].w;
+        row_sum3(lu, cu, ru, s[0], q[0]);
+      }
+      if (last) {  // row y + 4: the first word of the 16-byte groups below
+        const uint32_t ld = reinterpret_cast<const uint4*>(p - CW)[1].x, cd = reinterpret_cast<const uint4*>(p)[1].x,
+                       rd = reinterpret_cast<const uint4*>(p + CW)[1].x;
+        row_sum3(ld, cd, rd, s[kCaRows + 1], q[kCaRows + 1]);
+      }
+#pragma unroll
+      for (int r = 0; r < kCaRows; ++r)
+        w[r] = life_rule_mod4(s[r], q[r], s[r + 1], q[r + 1], s[r + 2], q[r + 2], w[r], mk[r]);
+      *reinterpret_cast<uint4*>(B + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __syncthreads();
     uint32_t* tmp = A;
@@ -264,32 +288,28 @@ __global__ void __launch_bounds__(512, 2) ca_fused_kernel(const uint8_t* __restr
 
   // write back the word tiles (whole 32-byte row segments); count the alive
   unsigned alive = 0;
+  if (off >= 0 && j < wtiles) {
 #pragma unroll
-  for (int k = 0; k < kCaSlots; ++k) {
-    const int j = hw + k * nh;
-    if (off[k] < 0 || j >= wtiles) continue;
-    const int c = off[k] / CW - 2, y = off[k] % CW - kCaRow0;
-    const uint2 w = own[k];
-    alive += __popc(w.x) + __popc(w.y);
-    if (pout) {  // record of word tile j, rows y, y + 1 mod 32
-      *reinterpret_cast<uint2*>(pout + (srec + j) * 32 + (y & 31)) = w;
-      continue;
-    }
+    for (int r = 0; r < kCaRows; ++r) alive += __popc(w[r]);
+    if (pout) {  // record of word tile j, rows y .. y + 3 mod 32
+      *reinterpret_cast<uint4*>(pout + (srec + j) * 32 + (y & 31)) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t v = h ? w.y : w.x;
-      uint4 v0, v1;
-      v0.x = spread4(v);
-      v0.y = spread4(v >> 4);
-      v0.z = spread4(v >> 8);
-      v0.w = spread4(v >> 12);
-      v1.x = spread4(v >> 16);
-      v1.y = spread4(v >> 20);
-      v1.z = spread4(v >> 24);
-      v1.w = spread4(v >> 28);
-      uint4* q = reinterpret_cast<uint4*>(out + (size_t)(oy + y + h) * n + ox + 32 * c);
-      q[0] = v0;
-      q[1] = v1;
+      for (int r = 0; r < kCaRows; ++r) {
+        const uint32_t v = w[r];
+        uint4 v0, v1;
+        v0.x = spread4(v);
+        v0.y = spread4(v >> 4);
+        v0.z = spread4(v >> 8);
+        v0.w = spread4(v >> 12);
+        v1.x = spread4(v >> 16);
+        v1.y = spread4(v >> 20);
+        v1.z = spread4(v >> 24);
+        v1.w = spread4(v >> 28);
+        uint4* q = reinterpret_cast<uint4*>(out + (size_t)(oy + y + r) * n + ox + 32 * c);
+        q[0] = v0;
+        q[1] = v1;
+      }
     }
   }
   if (partials) {  // alive members of the result, per CTA (uniform branch)
@@ -327,18 +347,13 @@ int ca_fused_smem_bytes(const Geo& g, int margin) {
   return tab_words(wtiles) * 4 + 2 * ca_image_words(g.T) * 4;
 }
 
-// Warps of a fused automaton launch: the fewest half warps that give every
-// half warp the least number of tasks; 0 if the super-tile does not fit the
-// kernel.
+// Threads of a fused automaton launch: four lanes per task, in whole warps;
+// 0 if the super-tile does not fit the kernel.
 int ca_fused_threads(const Geo& g, int margin) {
   if (g.T < 32 || g.T > 512 || margin < 1 || margin > 31 || 2 * margin > g.T) return 0;
   int wtiles = 1;
   for (int i = 0; i < ilog2c(g.T) - 5; ++i) wtiles *= 3;
-  const int tasks = ca_tasks(wtiles);
-  const int per = (tasks + 31) / 32;  // with 16 warps
-  if (per > kCaSlots) return 0;
-  const int halves = (tasks + per - 1) / per;
-  return 32 * ((halves + 1) / 2);
+  return (kCaLanes * ca_tasks(wtiles) + 31) / 32 * 32;
 }
 
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,

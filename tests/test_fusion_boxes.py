@@ -165,39 +165,40 @@ def test_mod4_rule_matches_b3s23_for_sums_up_to_six():
 def _automaton_tasks(T, M):
     """The fused automaton's staging layout (word column c, first row y0,
     rows) in super-tile coordinates: every member 32 x 32 word tile of the
-    super-tile, then the seven box pieces, with the margin rounded up to even
-    (ME) and the right box reaching rows [-ME, ME + 1]."""
+    super-tile, then the seven box pieces, with the margin rounded up to a
+    multiple of 8 (ME8) and the right box reaching rows [-ME8, ME8 + 8)."""
     ws = T // 32
     tasks = [(tx, 32 * ty, 32) for ty in range(ws) for tx in range(ws) if (tx & ty) == 0]
-    ME = M + (M & 1)
-    right = 2 * ME + 2
-    tasks += [(-1, 0, ME), (0, -ME, ME), (ws, -ME, min(right, 32)), (ws, -ME + 32, min(max(right - 32, 0), 32)),
-              (ws, -ME + 64, max(right - 64, 0)), (-1, T, ME), (0, T, ME)]
+    ME8 = (M + 7) // 8 * 8
+    right = 2 * ME8 + 8
+    tasks += [(-1, 0, ME8), (0, -ME8, ME8), (ws, -ME8, min(right, 32)), (ws, -ME8 + 32, min(max(right - 32, 0), 32)),
+              (ws, -ME8 + 64, max(right - 64, 0)), (-1, T, ME8), (0, T, ME8)]
     return tasks
 
 
 @pytest.mark.parametrize("T", [32, 64, 128, 256, 512])
 def test_automaton_staging_layout(T):
     """For every margin the fused automaton takes (1 <= M <= 31, 2 M <= T):
-    each task starts on an even row and has an even number of rows (a lane
-    keeps two adjacent rows as one 8-byte word pair); no word of the bit image
-    is staged twice (each has one writer); the staged words hold the
-    automaton's margin boxes; and the rows a lane reads (one beyond its pair
-    on each side, in its column and the two beside it) stay inside the image's
-    word columns [-2, T/32 + 1] and rows [-34, T + 34)."""
+    each task starts on a row that is a multiple of 8 and has a multiple of 8
+    rows (a lane keeps four rows as one 16-byte group, and lanes pair up
+    within 8-row blocks); no word of the bit
+    image is staged twice (each has one writer); the staged words hold the
+    automaton's margin boxes; and the rows a lane reads (the 16-byte groups
+    above and below its four, in its column and the two beside it) stay inside the image's
+    word columns [-2, T/32 + 1] and rows [-36, T + 36)."""
     ws = T // 32
     for M in range(1, 32):
         if 2 * M > T:
             break
         staged = set()
         for c, y0, rows in _automaton_tasks(T, M):
-            assert y0 % 2 == 0 and rows % 2 == 0 and 0 <= rows <= 32
+            assert y0 % 8 == 0 and rows % 8 == 0 and 0 <= rows <= 32
             for y in range(y0, y0 + rows):
                 assert (c, y) not in staged, (T, M, c, y)
                 staged.add((c, y))
             if rows:
                 assert -2 <= c - 1 and c + 1 <= ws + 1
-                assert -34 <= y0 - 1 and y0 + rows < T + 34
+                assert -36 <= y0 - 4 and y0 + rows + 4 <= T + 36
         for x0, x1, y0, y1 in _boxes(T, M, 8):
             for y in range(y0, y1):
                 for x in (x0, x1 - 1):
