@@ -555,8 +555,8 @@ def useful_threads(wl, info, spl, mode):
     member cells); slots = CTAs (super-tiles; BB: the whole 2^R x 2^R box)
     x block slots per CTA, so the idle slots, the margin-box blocks (redundant:
     evolved again by their own super-tile) and BB's discarded CTAs all count
-    as launched.  Fused automaton: a slot is one lane's two 32-cell words of
-    a task (three task slots per half warp), 64 cells."""
+    as launched.  Fused automaton: a slot is one lane, four 32-cell words of
+    a task (eight lanes per task), 128 cells."""
     k = info["k"]
     ctas, per_cta = info["ctas"][0 if wl == "ca" else 1], info["threads"][0 if wl == "ca" else 1]
     out = {"ctas": ctas, "mode": "lambda" if mode == 0 else "bb"}
@@ -574,9 +574,8 @@ def useful_threads(wl, info, spl, mode):
             out["box_blocks_per_own_block"] = box / own
     else:
         lanes = ctas * per_cta
-        slots = lanes * 3
-        out.update({"unit": "lane task slot (two 32-cell words)", "threads_per_cta": per_cta,
-                    "useful_fraction": 3 ** k / (slots * 64)})
+        out.update({"unit": "lane (four 32-cell words)", "threads_per_cta": per_cta,
+                    "useful_fraction": 3 ** k / (lanes * 128)})
     return out
 
 

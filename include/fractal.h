@@ -556,8 +556,9 @@ int fractal_batch_bind(fractal_batch_t batch, float* const* dev_a, float* const*
 
 /*
  * fractal_batch_configure -- super-tile side T (a power of two, 16 <= T <=
- * 2^k_min, T >= 2 * margin, at most 512 threads per CTA) and steps per launch
- * spl (1 .. 32; margin = spl rounded up to a multiple of 8).  T = 0 keeps
+ * 2^k_min, T >= 2 * margin, at most 288 block slots per super-tile, or 320
+ * for T = 256 at margins of 64 cells) and steps per launch spl (1 .. 56;
+ * margin = the smallest power of two >= max(spl, 8)).  T = 0 keeps
  * the current side.  Drops a captured graph.  Synchronous when bound (the
  * offset table is rewritten).  Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
  */

@@ -63,11 +63,14 @@ void drop_graph(fractal_batch_s* b) {
 }
 
 // Threads for side T, margin M and reach (0 if invalid for this batch).
+// Launches of 320 slots (side 256, margins of 64 cells at reach <= 56) run
+// four warps per item; the others one block per thread in at most 288.
 int batch_threads(const fractal_batch_s* b, int T, int margin, int reach) {
   if (T < 16 || (T & (T - 1)) != 0 || T > (1 << b->kmin)) return 0;
   Geo g{};
   g.T = T;
-  return fused_threads(g, 0, margin, reach);
+  const int t = fused_threads(g, 0, margin, reach);
+  return t <= 288 || t == fused_q3_slots() ? t : 0;
 }
 
 // Offsets, R and the persistent grid for the current T; table upload if bound.
@@ -93,6 +96,7 @@ int rebuild(fractal_batch_s* b) {
   if (per_sm < 1) per_sm = 1;
   const int64_t grid = (int64_t)per_sm * sms;
   b->ctas = (int)(grid < b->items ? grid : b->items);
+  if (b->threads == fused_q3_slots()) b->ctas = (int)b->items;  // one CTA per item
   if (b->bound &&
       cudaMemcpy(b->d_inst, b->h.data(), sizeof(BatchInst) * b->count, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
@@ -123,6 +127,8 @@ int rebuild(fractal_batch_s* b) {
       }
       b->desc_ok = true;
     }
+    // the four-warp launch reads its threads' setups from the descriptors
+    if (!b->desc_ok && b->threads == fused_q3_slots()) return FRACTAL_ENOMEM;
   }
   return FRACTAL_OK;
 }
@@ -245,7 +251,7 @@ int fractal_batch_bind(fractal_batch_t b, float* const* dev_a, float* const* dev
 }
 
 int fractal_batch_configure(fractal_batch_t b, int supertile, int spl) {
-  if (!b || spl < 1 || spl > 32 || supertile < 0) return FRACTAL_EINVAL;
+  if (!b || spl < 1 || spl > 56 || supertile < 0) return FRACTAL_EINVAL;
   const int T = supertile ? supertile : b->T;
   const int margin = fused_margin(spl);
   const int threads = batch_threads(b, T, margin, spl);
@@ -298,9 +304,9 @@ int fractal_batch_autotune(fractal_batch_t b, float a, int reps, float* best_us,
   float best = -1.f;
   int best_T = old_T, best_spl = old_spl;
   int status = FRACTAL_OK;
-  const int spls[3] = {8, 16, 32};
+  const int spls[4] = {8, 16, 32, 50};
   for (int T = 16; T <= 512 && status == FRACTAL_OK; T *= 2) {
-    for (int si = 0; si < 3 && status == FRACTAL_OK; ++si) {
+    for (int si = 0; si < 4 && status == FRACTAL_OK; ++si) {
       if (fractal_batch_configure(b, T, spls[si]) != FRACTAL_OK) continue;
       // launches of spl steps, dev_a -> dev_b only (which = 0)
       auto one = [&]() -> int {

@@ -979,8 +979,30 @@ __global__ void __launch_bounds__(288, 4) diffusion_batch_kernel(const BatchInst
   }
 }
 
+// Batches in the four-warp layout of fused_supertile3 (super-tile side 256,
+// 320 slots): one CTA per item (its instance by binary search, its
+// super-tile by lambda at the instance's level), three CTAs per SM.
+__global__ void __launch_bounds__(kQ3Threads, 3) diffusion_batch3_kernel(const BatchInst* __restrict__ inst,
+                                                                         int count, int which, float a, int nsteps,
+                                                                         int M, int reach, int T,
+                                                                         const float* __restrict__ pin,
+                                                                         float* __restrict__ pout,
+                                                                         const int4* __restrict__ desc) {
+  __shared__ __align__(16) float ports[6 * (kQ3Slots + 2)];
+  const int64_t w = blockIdx.x;
+  const BatchInst I = inst[batch_instance(inst, count, w)];
+  const int64_t om = w - I.first;
+  int sx, sy;
+  warp_lambda((uint32_t)(om % I.lwR), (uint32_t)(om / I.lwR), I.R, sx, sy);
+  FGeo f = make_fgeo(I.n, T, M, reach, 3, I.R);
+  f.rec0 = I.first * f.nb;  // item w's records start at w * nb
+  fused_supertile3<kLambda>(pin ? nullptr : (which ? I.b : I.a), pout ? nullptr : (which ? I.a : I.b), a, nsteps, f,
+                            sx << f.L, sy << f.L, ports, false, pin, pout, w * f.nb, desc + w * kQ3Slots,
+                            (int)(w & 1));
+}
+
 // The batch launch's per-thread setups, item by item (w * blockDim.x + t).
-__global__ void __launch_bounds__(288) batch_describe_kernel(const BatchInst* __restrict__ inst, int count,
+__global__ void __launch_bounds__(512) batch_describe_kernel(const BatchInst* __restrict__ inst, int count,
                                                              int64_t items, int M, int reach, int T,
                                                              int4* __restrict__ desc) {
   for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
@@ -1197,7 +1219,8 @@ cudaError_t launch_batch_describe(const BatchInst* inst, int count, int64_t item
                                   int ctas, int threads, int4* desc, cudaStream_t s) {
   Geo g{};
   g.T = T;
-  if (fused_threads(g, 0, margin, reach) != threads || threads > 288 || ctas < 1) return cudaErrorInvalidValue;
+  if (fused_threads(g, 0, margin, reach) != threads || (threads > 288 && threads != kQ3Slots) || ctas < 1)
+    return cudaErrorInvalidValue;
   batch_describe_kernel<<<ctas, threads, 0, s>>>(inst, count, items, margin, reach, T, desc);
   return cudaGetLastError();
 }
@@ -1209,6 +1232,13 @@ cudaError_t launch_diffusion_batch(const BatchInst* inst, int count, int64_t ite
   Geo g{};
   g.T = T;
   if (fused_threads(g, 0, margin, reach) != threads) return cudaErrorInvalidValue;
+  if (threads == kQ3Slots) {  // four warps, one CTA per item (needs the descriptors)
+    if (!desc || items < 1 || items > 0x7fffffff) return cudaErrorInvalidValue;
+    diffusion_batch3_kernel<<<(unsigned)items, kQ3Threads, 0, s>>>(inst, count, which, a, nsteps, margin, reach, T,
+                                                                    pin, pout, desc);
+    return cudaGetLastError();
+  }
+  if (threads > 288) return cudaErrorInvalidValue;
   diffusion_batch_kernel<<<ctas, threads, fused_batch_smem_bytes(threads), s>>>(inst, count, items, which, a, nsteps,
                                                                                margin, reach, T, pin, pout, desc);
   return cudaGetLastError();
@@ -1270,6 +1300,7 @@ cudaError_t launch_fused_describe(int mode, int log_rho, int margin, int reach, 
 }
 
 int fused_warp_slots() { return kWarpSlots; }
+int fused_q3_slots() { return kQ3Slots; }
 
 int64_t fused_records(int k) {
   int64_t r = 1;

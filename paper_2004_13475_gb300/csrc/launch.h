@@ -82,6 +82,9 @@ int fused_threads(const Geo& g, int rho, int margin, int reach);
 // Block slots of the one-warp fused launch (super-tiles of side 128, margins
 // up to 16 cells).
 int fused_warp_slots();
+// Block slots of the four-warp fused launch (super-tiles of side 256,
+// margins of 64 cells at a reach of at most 56 steps).
+int fused_q3_slots();
 // Most member blocks of the margin boxes (W blocks wide) of a level-L
 // super-tile within `reach` cells of it.
 int box_cap_reach(int L, int W, int reach);

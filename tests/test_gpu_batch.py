@@ -45,7 +45,8 @@ def reference(fr, k, u0, steps, spl):
     return fr.fractal_step_diffusion(plan, a, b, 0.2, steps).cpu().numpy().reshape(n, n)
 
 
-@pytest.mark.parametrize("ks_range,T,spl", [((4, 9), 16, 8), ((6, 10), 64, 32), ((7, 11), 128, 16), ((8, 10), 0, 3)])
+@pytest.mark.parametrize("ks_range,T,spl", [((4, 9), 16, 8), ((6, 10), 64, 32), ((7, 11), 128, 16), ((8, 10), 0, 3),
+                                             ((8, 11), 256, 50), ((8, 10), 256, 40)])
 def test_batch_equals_single_instances_and_oracle(fr, ks_range, T, spl):
     rng = np.random.default_rng(ks_range[0])
     ks = [int(k) for k in rng.integers(ks_range[0], ks_range[1] + 1, size=9)]
@@ -93,11 +94,14 @@ def _valid(n, x0, y0, w, h, steps):
     return slice(lo_y, hi_y), slice(lo_x, hi_x)
 
 
-def test_batch_as_benchmarked_against_oracle(fr):
-    """The configuration the benchmark times: super-tile side 256, 32 steps
-    per launch, levels drawn from 8..13, 100 steps through the captured graph.
-    One instance of every level is compared with the FP64 oracle (whole array
-    up to k = 11, windows across super-tile and replica seams above)."""
+@pytest.mark.parametrize("spl", [32, 50])
+def test_batch_as_benchmarked_against_oracle(fr, spl):
+    """The configurations the benchmark's autotuner chooses between: super-tile
+    side 256 with 32 steps per launch (one block per thread) or 50 (four
+    warps, 320 block slots), levels drawn from 8..13, 100 steps through the
+    captured graph.  One instance of every level is compared with the FP64
+    oracle (whole array up to k = 11, windows across super-tile and replica
+    seams above)."""
     rng = np.random.default_rng(13)
     ks = [8, 9, 10, 11, 12, 13] + [int(k) for k in rng.integers(8, 14, size=10)]
     seed0, steps = 900, 100
@@ -107,9 +111,9 @@ def test_batch_as_benchmarked_against_oracle(fr):
         synth.device_fill(a[i].data_ptr(), synth.SYNTH_UNIFORM_F32, 1 << k, seed0 + i)
     batch = fr.fractal_batch_create(ks)
     fr.fractal_batch_bind(batch, a, b)
-    fr.fractal_batch_configure(batch, 256, 32)
+    fr.fractal_batch_configure(batch, 256, spl)
     inf = batch.info()
-    assert inf["supertile"] == 256 and inf["steps_per_launch"] == 32
+    assert inf["supertile"] == 256 and inf["steps_per_launch"] == spl
     fr.fractal_batch_graph_capture(batch, 0.2, steps)
     fr.fractal_batch_graph_launch(batch)              # 100 steps: result in a (records between launches)
     torch.cuda.synchronize()
