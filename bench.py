@@ -664,6 +664,25 @@ KERNEL_SOURCES = {
                         "paper_2004_13475_gb300/csrc/dfloat.cuh", "paper_2004_13475_gb300/csrc/gasket.cuh"),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+STALLS_FILE = os.path.join(ROOT, "profiles", "stalls.txt")
+
+
+def measured_stalls(kernel):
+    """Top warp stalls (per issued instruction) of `kernel` from the committed
+    ncu summary (profiles/stalls.txt), or None if absent or the kernel's
+    sources changed since the capture."""
+    try:
+        with open(STALLS_FILE) as f:
+            for ln in f:
+                parts = ln.split()
+                if len(parts) >= 4 and parts[0] == kernel and not ln.startswith("#"):
+                    if parts[1] != sources_hash(kernel):
+                        return None
+                    return {"capture": parts[2],
+                            "per_issue": {kv.split("=")[0]: float(kv.split("=")[1]) for kv in parts[3:]}}
+    except OSError:
+        return None
+    return None
 
 
 def sources_hash(kernel):
@@ -773,6 +792,7 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps, every=N
     achieved = alg / launch_s / 1e9
     name = kernel_name(wl, info, spl)
     traffic = measured_traffic(name.split("<")[0], info["k"]) if spl > 1 else None
+    stalls = measured_stalls(name.split("<")[0]) if spl > 1 else None
     hbm_rf = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
               "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
               "alg_bytes_per_launch": alg, "launch_us": launch_s * 1e6, "steps_per_launch": spl,
@@ -784,7 +804,8 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps, every=N
                "peak_kind": "derived: 152 SMs x 64 integer ALU lanes x 2.07 GHz (probe: 63.8 ops/clk/SM)",
                "unit": "Tops/s", "frac": to / ALU_PEAK_TOPS, "traffic": traffic, "alg_ops_per_launch": ops,
                "ops_per_word_step": CA_OPS_PER_WORD_STEP, "launch_us": launch_s * 1e6,
-               "steps_per_launch": call_steps / len(kinds), "launch_kinds": ",".join(kinds)}
+               "steps_per_launch": call_steps / len(kinds), "launch_kinds": ",".join(kinds),
+               "warp_stalls": stalls}
     if wl == "diffusion" and spl > 1:
         flops = diffusion_flops_per_step(info["k"]) * call_steps / len(kinds)
         tf = flops / launch_s / 1e12
@@ -792,7 +813,7 @@ def launch_roofline(wl, info, spl, launch_s, hbm, peak_kind, call_steps, every=N
                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz", "unit": "TFLOP/s",
                "frac": tf / FP32_PEAK_TFLOPS, "traffic": traffic, "alg_flops_per_launch": flops,
                "launch_us": launch_s * 1e6, "steps_per_launch": call_steps / len(kinds),
-               "launch_kinds": ",".join(kinds)}
+               "launch_kinds": ",".join(kinds), "warp_stalls": stalls}
     return hbm_rf, alu
 
 

@@ -79,3 +79,19 @@ def test_automaton_ops_per_word_by_hand():
     # carry bit) and the rule modulo 4 (5 three-input logic operations)
     assert bench.CA_OPS_PER_WORD_STEP == 4 + 5
     assert abs(bench.ALU_PEAK_TOPS - 152 * 64 * 2.07e-3) < 1e-9
+
+
+def test_committed_profile_tables_parse():
+    """profiles/traffic.txt and profiles/stalls.txt name kernels whose sources
+    the bench can hash, with well-formed values (the bench reports them only
+    while the hashes match)."""
+    import os
+    for path, ncol in ((bench.TRAFFIC_FILE, 4), (bench.STALLS_FILE, 4)):
+        assert os.path.exists(path)
+        rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+        assert rows
+        for r in rows:
+            assert len(r) >= ncol and r[0] in bench.KERNEL_SOURCES
+            assert len(bench.sources_hash(r[0])) == 16
+    for r in (ln.split() for ln in open(bench.STALLS_FILE) if ln.strip() and not ln.startswith("#")):
+        assert all(float(kv.split("=")[1]) >= 0 for kv in r[3:])
