@@ -1137,11 +1137,12 @@ def adjoint(fr, torch, stream, seed):
     out = {"workload": (f"gasket k={ADJ_K} ({n}x{n}), kappa ~ U[0.5,1.5), {ADJ_STEPS} steps a={COEF}, "
                         f"loss sum((u_T - target)^2), gradients w.r.t. u0 and kappa, checkpoint every {ADJ_EVERY}")}
     members = 3 ** ADJ_K
-    for state in ("df", "f64", "f32"):
+    for name, state, fused in (("df", "df", True), ("df_single_step", "df", False), ("f64", "f64", True),
+                               ("f32", "f32", True)):
         def one():
             u = u0.clone().requires_grad_(True)
             k = kap.clone().requires_grad_(True)
-            loss = ((diffusion_kappa(u, k, ADJ_K, COEF, ADJ_STEPS, ADJ_EVERY, 0, state) - tg) ** 2).sum()
+            loss = ((diffusion_kappa(u, k, ADJ_K, COEF, ADJ_STEPS, ADJ_EVERY, 0, state, fused) - tg) ** 2).sum()
             loss.backward()
             return loss
         one()
@@ -1156,7 +1157,7 @@ def adjoint(fr, torch, stream, seed):
         torch.cuda.synchronize()
         t = t0.elapsed_time(t1) / 1e3 / reps
         elem = 4 if state == "f32" else 8
-        out[state] = {
+        out[name] = {
             "ms_forward_backward": t * 1e3,
             # forward, recomputation and reverse: three passes over the steps
             "cell_steps_per_s": 3 * members * ADJ_STEPS / t,
@@ -1164,6 +1165,21 @@ def adjoint(fr, torch, stream, seed):
             "state_memory_gib_without_checkpoints": (ADJ_STEPS + 1) * n * n * elem / 2 ** 30,
         }
     plan.close()
+    out["speedup_fused_over_single_step"] = out["df_single_step"]["ms_forward_backward"] / out["df"]["ms_forward_backward"]
+    # FP32 pipe operations of the double-float arithmetic (TwoSum 6, sum 11,
+    # product 7) per cell and step of the problem: forward, the recorded
+    # passes of u and p (one block-step each: 26 links x 40 + 27 sums x 11 +
+    # 4 port links x 29 = 1453 per 27 cells) and the kappa sums (26 x 51 +
+    # 4 x 29 = 1442 per 27 cells), with the u pass one step short per segment
+    passes = 2 * ADJ_STEPS + (ADJ_STEPS - ADJ_STEPS // ADJ_EVERY)
+    ops = members / 27 * (passes * 1453 + ADJ_STEPS * 1442)
+    t = out["df"]["ms_forward_backward"] / 1e3
+    out["roofline"] = {"kernel": "kappa_fused_df_kernel + kappa_grad_df_kernel (double-float)", "bound": "alu",
+                       "achieved": ops / t / 1e12, "peak": FP32_PEAK_TFLOPS / 2,
+                       "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (operations, not flops)",
+                       "unit": "Tops/s", "frac": ops / t / 1e12 / (FP32_PEAK_TFLOPS / 2),
+                       "alg_ops_per_forward_backward": ops,
+                       "note": "whole forward + backward through the autograd function, torch conversions included"}
     return out
 
 

@@ -488,13 +488,61 @@ int fractal_adjoint_diffusion_step_f64(fractal_plan_t plan, const double* dev_u,
  * TwoSum, Dekker's product with a fused multiply-add) runs on the FP32 pipes,
  * where this GPU has many times its FP64 rate; it keeps the gradients of a
  * 200-step run within 1e-4 of an FP64 reference like the double state does.
- * a is rounded to the nearest double-float.  Errors as above.
+ * a is rounded to the nearest double-float.  For k >= 4 the steps of
+ * fractal_step_diffusion_kappa_df run temporally fused (the launches below,
+ * up to max_steps each, a and b alternating with the parity of `steps`).
+ * Errors as above.
  */
 int fractal_step_diffusion_kappa_df(fractal_plan_t plan, float* dev_a, float* dev_b, const float* dev_kappa,
                                     double a, int steps, void* stream);
 int fractal_adjoint_diffusion_step_df(fractal_plan_t plan, const float* dev_u, const float* dev_p_in,
                                       float* dev_p_out, const float* dev_kappa, float* dev_gkappa, double a,
                                       void* stream);
+
+/*
+ * Fused gradient path (double-float, k >= 4).  The reverse step is the
+ * forward operator A applied to p (A is symmetric), so one kernel carries u
+ * forward and p back through a checkpoint segment, several steps per launch
+ * (super-tiles of side min(128, n) with the member blocks of their margin
+ * boxes, one 8 x 8 block per thread, ports in shared memory), recording the
+ * states it passes in compact form; dJ/dkappa of the segment is then summed
+ * from the two recorded trajectories in one pass.  Not in the paper.
+ *
+ * A trajectory holds states in record form: 3^(k-3) records of 56 floats
+ * (the 27 members of a member 8 x 8 block as (hi, lo) pairs and a pad),
+ * record_floats floats per state, state s at dev_traj + s * record_floats.
+ *
+ * fractal_kappa_fused_limits -- for level k and launch mode: the floats of
+ * one recorded state and the most steps one launch takes.  Host only.
+ * Errors: FRACTAL_EINVAL (k < 4 or > 16, bad mode, NULL).
+ *
+ * fractal_kappa_trajectory_df -- `steps` (1 .. max_steps) steps of the
+ * double-float conductivity diffusion from dev_in (2*n*n floats): the state
+ * before each step into the trajectory's states 0 .. steps - 1 (dev_traj,
+ * nullable) and the result into dev_out (2*n*n floats, every cell of every
+ * member 8 x 8 block written, 0 at non-members); with dev_out NULL the result
+ * goes to trajectory state `steps` instead.  Asynchronous.  Errors:
+ * FRACTAL_EINVAL (NULL dev_in or dev_kappa, both outputs NULL, aliasing,
+ * alignment, steps out of range, a not finite, k < 4), FRACTAL_ECUDA.
+ *
+ * fractal_kappa_gradient_df -- dev_gkappa (2*n*n floats, double-float) +=
+ * the dJ/dkappa contributions of `steps` steps t0 .. t0 + steps - 1 of a
+ * segment: dev_utraj state s = u_(t0+s), dev_ptraj state s = p_(t0+steps-s)
+ * (the trajectory the reverse launch records from p_(t0+steps)); per link and
+ * step (a / 2) (u_nb - u_c) (p_c - p_nb) at both ends.  Writes every cell of
+ * every member 8 x 8 block of dev_gkappa (0 at non-members).  Asynchronous.
+ * Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
+ */
+int fractal_kappa_fused_limits(int k, int mode, int64_t* record_floats, int* max_steps);
+
+/* Temporal fusion of fractal_step_diffusion_kappa_df on (on != 0, the
+ * default) or off (one launch of the single-step kernel per step, for
+ * comparison).  Errors: FRACTAL_EINVAL (NULL plan). */
+int fractal_plan_set_kappa_fusion(fractal_plan_t plan, int on);
+int fractal_kappa_trajectory_df(fractal_plan_t plan, const float* dev_in, float* dev_out, float* dev_traj,
+                                const float* dev_kappa, double a, int steps, void* stream);
+int fractal_kappa_gradient_df(fractal_plan_t plan, const float* dev_utraj, const float* dev_ptraj,
+                              float* dev_gkappa, double a, int steps, void* stream);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.

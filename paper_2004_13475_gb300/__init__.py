@@ -48,6 +48,8 @@ EXPORTS = (
     "fractal_pack", "fractal_unpack",
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
+    "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_gradient_df",
+    "fractal_plan_set_kappa_fusion",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -151,6 +153,10 @@ def _load() -> ctypes.CDLL:
         "fractal_step_diffusion_sums": (I, [P, VP, VP, F, I, I, VP, VP]),
         "fractal_adjoint_diffusion_step_f64": (I, [P, VP, VP, VP, VP, VP, D, VP]),
         "fractal_plan_selftest_wait": (I, [P, ctypes.c_uint, VP]),
+        "fractal_kappa_fused_limits": (I, [I, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I)]),
+        "fractal_kappa_trajectory_df": (I, [P, VP, VP, VP, VP, D, I, VP]),
+        "fractal_kappa_gradient_df": (I, [P, VP, VP, VP, D, I, VP]),
+        "fractal_plan_set_kappa_fusion": (I, [P, I]),
         "fractal_debug_fail_allocs": (I, [I]),
     }
     for name, (res, args) in sig.items():
@@ -265,6 +271,38 @@ def fractal_plan_selftest_wait(plan: Plan, spins: int = 1 << 16, stream=None) ->
 def fractal_debug_fail_allocs(after: int) -> None:
     """Fail the library's device allocation after `after` more successes (< 0: off)."""
     _check(_load().fractal_debug_fail_allocs(int(after)), "fractal_debug_fail_allocs")
+
+
+def fractal_plan_set_kappa_fusion(plan: Plan, on: bool) -> None:
+    """Temporal fusion of the double-float conductivity steps on (default) or off."""
+    _check(_load().fractal_plan_set_kappa_fusion(plan.handle, 1 if on else 0), "fractal_plan_set_kappa_fusion")
+
+
+def fractal_kappa_fused_limits(k: int, mode: int = FRACTAL_LAMBDA):
+    """(floats of one recorded state, most steps per fused launch) of the
+    double-float gradient path at level k; raises for k < 4."""
+    rf = ctypes.c_int64()
+    ms = ctypes.c_int()
+    _check(_load().fractal_kappa_fused_limits(int(k), int(mode), ctypes.byref(rf), ctypes.byref(ms)),
+           "fractal_kappa_fused_limits")
+    return rf.value, ms.value
+
+
+def fractal_kappa_trajectory_df(plan: Plan, dev_in, dev_out, dev_traj, dev_kappa, coef: float, steps: int,
+                                stream=None) -> None:
+    """`steps` fused double-float conductivity steps from dev_in, the states
+    before each step into dev_traj (record form; nullable) and the result into
+    dev_out (or, when dev_out is None, into trajectory state `steps`)."""
+    _check(_load().fractal_kappa_trajectory_df(plan.handle, _ptr(dev_in), _ptr(dev_out), _ptr(dev_traj),
+                                               _ptr(dev_kappa), float(coef), int(steps), _stream(stream)),
+           "fractal_kappa_trajectory_df")
+
+
+def fractal_kappa_gradient_df(plan: Plan, dev_utraj, dev_ptraj, dev_gkappa, coef: float, steps: int,
+                              stream=None) -> None:
+    """dJ/dkappa of a segment of `steps` steps from the recorded u and p trajectories (double-float)."""
+    _check(_load().fractal_kappa_gradient_df(plan.handle, _ptr(dev_utraj), _ptr(dev_ptraj), _ptr(dev_gkappa),
+                                             float(coef), int(steps), _stream(stream)), "fractal_kappa_gradient_df")
 
 
 def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:

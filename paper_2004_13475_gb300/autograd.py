@@ -13,7 +13,10 @@ roundings alone move the gradients by a few 1e-4 of their scale, beyond the
 1e-4 agreement with an FP64 adjoint, so the default state is wider:
 ``state="df"`` (default) keeps the trajectory, the adjoint state and dJ/dkappa
 in double-float, (hi, lo) float pairs with about 48 significant bits,
-computed on the FP32 pipes; ``state="f64"`` keeps them in float64 (the same
+computed on the FP32 pipes, and (k >= 4) runs temporally fused: the forward
+steps several per launch, and per segment one recorded pass of u from its
+checkpoint, one of p back (the reverse step is the same symmetric operator
+applied to p) and one pass summing dJ/dkappa from the two records; ``state="f64"`` keeps them in float64 (the same
 agreement, on this GPU's much slower FP64 units); ``state="f32"`` runs the
 float32 kernels.  Inputs and outputs keep the callers' dtypes.
 """
@@ -21,9 +24,11 @@ from __future__ import annotations
 
 import torch
 
-from . import (FRACTAL_F32, FRACTAL_LAMBDA, fractal_adjoint_diffusion_step, fractal_adjoint_diffusion_step_df,
-               fractal_adjoint_diffusion_step_f64, fractal_map, fractal_map_write, fractal_step_diffusion_kappa,
-               fractal_step_diffusion_kappa_df, fractal_step_diffusion_kappa_f64)
+from . import (FRACTAL_F32, FRACTAL_LAMBDA, FractalError, fractal_adjoint_diffusion_step,
+               fractal_adjoint_diffusion_step_df, fractal_adjoint_diffusion_step_f64, fractal_kappa_fused_limits,
+               fractal_kappa_gradient_df, fractal_kappa_trajectory_df, fractal_map, fractal_map_write,
+               fractal_plan_set_kappa_fusion,
+               fractal_step_diffusion_kappa, fractal_step_diffusion_kappa_df, fractal_step_diffusion_kappa_f64)
 
 # per state: (step, reverse step, storage dtype, elements per cell)
 _STATES = {
@@ -53,6 +58,30 @@ def _from_state(y, state, dtype):
     return y.to(dtype)
 
 
+def _fused_limits(k, mode):
+    """(floats per recorded state, steps per launch) of the fused double-float
+    gradient path, or None where it does not apply (k < 4)."""
+    try:
+        return fractal_kappa_fused_limits(k, mode)
+    except FractalError:
+        return None
+
+
+def _run_recorded(plan, src, dst, traj, rec_floats, kappa, a, steps, max_steps, temps):
+    """`steps` (>= 1) fused double-float steps from src: the state before each
+    step into traj states 0 .. steps - 1 (traj may be None) and the result
+    into dst (or, with dst None, into traj state `steps`), in launches of at
+    most max_steps steps
+    (temps: two spare state buffers for the chunks between launches)."""
+    cur, s0, i = src, 0, 0
+    while s0 < steps:
+        n = min(max_steps, steps - s0)
+        last = s0 + n == steps
+        out = dst if last else temps[i & 1]
+        fractal_kappa_trajectory_df(plan, cur, out, None if traj is None else traj[s0 * rec_floats:], kappa, a, n)
+        cur, s0, i = out, s0 + n, i + 1
+
+
 def _member_mask(plan, like):
     """1.0 at the members, 0 elsewhere (the library's single-write kernel on zeros)."""
     m = torch.zeros(like.shape, dtype=torch.float32, device=like.device)
@@ -61,7 +90,7 @@ def _member_mask(plan, like):
 
 
 class GasketDiffusion(torch.autograd.Function):
-    """u_T = GasketDiffusion.apply(u0, kappa, k, a, steps, every, mode, state).
+    """u_T = GasketDiffusion.apply(u0, kappa, k, a, steps, every, mode, state, fused).
 
     u0, kappa: flat float32 CUDA tensors of 4**k elements (the n x n arrays,
     row-major; non-member cells are ignored).  Returns u_T, 0 at every
@@ -71,29 +100,47 @@ class GasketDiffusion(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, u0, kappa, k: int, a: float, steps: int, every: int = 20, mode: int = FRACTAL_LAMBDA,
-                state: str = "df"):
+                state: str = "df", fused: bool = True):
         if every < 1:
             raise ValueError("every >= 1")
         if state not in _STATES:
             raise ValueError("state is 'df', 'f64' or 'f32'")
         step = _STATES[state][0]
         plan = fractal_map(k, 8 if k >= 3 else 1 << k, mode)
+        fractal_plan_set_kappa_fusion(plan, fused)
         mask = _member_mask(plan, u0)
         kappa = kappa.detach().to(torch.float32).contiguous()
-        # every buffer holds 0 at all non-member cells, so u_T does too
-        u = _to_state(u0.detach() * mask.to(u0.dtype), state)
-        v = torch.zeros_like(u)
+        lim = _fused_limits(k, mode) if state == "df" and fused else None
         ckpts = []
         t = 0
-        while t < steps:
-            ckpts.append(u.clone())
-            ns = min(every, steps - t)
-            out = step(plan, u, v, kappa, a, ns)
-            if out is v:
-                u, v = v, u
-            t += ns
+        if lim is not None:
+            # fused: each segment from its checkpoint into a new buffer (the
+            # kernels read member cells only and write every cell of every
+            # member block; the last buffer starts zeroed, so u_T is 0 at
+            # every non-member cell)
+            u = _to_state(u0.detach(), state)
+            temps = [torch.empty_like(u) for _ in range(2)] if min(every, steps) > lim[1] else [None, None]
+            while t < steps:
+                ns = min(every, steps - t)
+                v = torch.zeros_like(u) if t + ns >= steps else torch.empty_like(u)
+                _run_recorded(plan, u, v, None, 0, kappa, a, ns, lim[1], temps)
+                ckpts.append(u)
+                u = v
+                t += ns
+        else:
+            # every buffer holds 0 at all non-member cells, so u_T does too
+            u = _to_state(u0.detach() * mask.to(u0.dtype), state)
+            v = torch.zeros_like(u)
+            while t < steps:
+                ckpts.append(u.clone())
+                ns = min(every, steps - t)
+                out = step(plan, u, v, kappa, a, ns)
+                if out is v:
+                    u, v = v, u
+                t += ns
         ctx.save_for_backward(kappa, mask, *ckpts)
         ctx.plan, ctx.a, ctx.steps, ctx.every, ctx.state = plan, a, steps, every, state
+        ctx.fused = fused
         ctx.dtypes = (u0.dtype, kappa.dtype)
         return _from_state(u, state, u0.dtype)
 
@@ -111,6 +158,31 @@ class GasketDiffusion(torch.autograd.Function):
         # the recomputed states of a segment, one pool for all segments: a
         # step writes every member tile of its output and the kernels read
         # member cells only, so the pool is neither cleared nor reallocated
+        lim = _fused_limits(plan.info()["k"], plan.info()["mode"]) if state == "df" and ctx.fused else None
+        if lim is not None:
+            # fused: per segment, u recorded forward from its checkpoint and p
+            # carried back (the reverse step is A applied to p) in launches of
+            # several steps, then dJ/dkappa of the segment from both records
+            rf, ms = lim
+            seg_max = min(every, steps)
+            utraj = torch.empty(rf * (seg_max + 1), dtype=torch.float32, device=p.device)
+            ptraj = torch.empty(rf * seg_max, dtype=torch.float32, device=p.device)
+            temps = [torch.empty_like(p) for _ in range(2)] if seg_max > ms else [None, None]
+            for seg in range(len(ckpts) - 1, -1, -1):
+                t0 = seg * every
+                ns = min(every, steps - t0)
+                # u_(t0) .. u_(t0 + ns - 1) (at least one step, so that the
+                # segment's first state is recorded as well)
+                un = max(ns - 1, 1)
+                if un <= ms:
+                    fractal_kappa_trajectory_df(plan, ckpts[seg], None, utraj, kappa, a, un)
+                else:
+                    _run_recorded(plan, ckpts[seg], None, utraj, rf, kappa, a, un, ms, temps)
+                _run_recorded(plan, p, q, ptraj, rf, kappa, a, ns, ms, temps)
+                fractal_kappa_gradient_df(plan, utraj, ptraj, gk, a, ns)
+                p, q = q, p
+            du, dk = ctx.dtypes
+            return (_from_state(p, state, du), _from_state(gk, "df", dk), None, None, None, None, None, None, None)
         pool = [torch.empty_like(p) for _ in range(min(every, steps) - 1)]
         for seg in range(len(ckpts) - 1, -1, -1):
             t0 = seg * every
@@ -125,10 +197,11 @@ class GasketDiffusion(torch.autograd.Function):
                 p, q = q, p
         du, dk = ctx.dtypes
         gk = _from_state(gk, "df", dk) if state == "df" else gk.to(dk)
-        return _from_state(p, state, du), gk, None, None, None, None, None, None
+        return _from_state(p, state, du), gk, None, None, None, None, None, None, None
 
 
 def diffusion_kappa(u0, kappa, k: int, a: float, steps: int, every: int = 20, mode: int = FRACTAL_LAMBDA,
-                    state: str = "df"):
-    """Functional form of :class:`GasketDiffusion`."""
-    return GasketDiffusion.apply(u0, kappa, k, a, steps, every, mode, state)
+                    state: str = "df", fused: bool = True):
+    """Functional form of :class:`GasketDiffusion` (fused=False: one launch
+    per step, forward and backward, for comparison)."""
+    return GasketDiffusion.apply(u0, kappa, k, a, steps, every, mode, state, fused)

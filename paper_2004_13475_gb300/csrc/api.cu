@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <type_traits>
 #include <new>
 
 #include <cudaTypedefs.h>
@@ -106,6 +107,7 @@ struct fractal_plan_s {
   bool tma_ok[2] = {false, false};
   Launch aux[2];                // SW / reduce kernels (slot table only in shared memory)
   int spl[2] = {1, 1};          // steps per launch (temporal fusion), per dtype
+  bool kappa_fused = true;      // double-float conductivity steps temporally fused (k >= 4)
   bool user_levels[2] = {false, false};  // tile levels fixed by the caller
   Launch fused[2];              // fused kernel launch for the plan's steps per launch
   bool fused_ok[2] = {false, false};
@@ -594,6 +596,22 @@ int step_kappa(fractal_plan_t p, T* a, T* b, const float* kappa, T coef, int ste
   if (!kappa_geometry(p->k, p->mode, L, levels)) return FRACTAL_EINVAL;
   if (steps == 0) return FRACTAL_OK;
   T* buf[2] = {a, b};
+  if constexpr (std::is_same<T, dfloat>::value) {
+    // double-float: temporally fused launches of up to `margin` steps,
+    // ping-pong between a and b with the parity of `steps`
+    Launch F;
+    int margin = 0;
+    if (p->kappa_fused && kappa_fused_geometry(p->k, p->mode, F, margin)) {
+      const FusedSplit sp(steps, margin);
+      const dfloat ha(0.5f * coef.hi, 0.5f * coef.lo);  // halving is exact
+      for (int i = 0; i < sp.L; ++i) {
+        cudaError_t e = launch_kappa_fused_df(p->mode, p->k, buf[i & 1], buf[(i + 1) & 1], nullptr, kappa, ha,
+                                              sp.of(i), (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step_diffusion_kappa");
+      }
+      return FRACTAL_OK;
+    }
+  }
   for (int s = 0; s < steps; ++s) {
     cudaError_t e =
         launch_diffusion_kappa<T>(p->mode, L, levels, buf[s & 1], buf[(s + 1) & 1], kappa, coef, (cudaStream_t)stream);
@@ -935,6 +953,59 @@ int fractal_plan_selftest_wait(fractal_plan_t p, unsigned spins, void* stream) {
   cudaError_t e = launch_wait_selftest(p->d_err, spins, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "wait self-test");
+}
+
+int fractal_plan_set_kappa_fusion(fractal_plan_t p, int on) {
+  if (check_plan(p)) return FRACTAL_EINVAL;
+  p->kappa_fused = on != 0;
+  return FRACTAL_OK;
+}
+
+int fractal_kappa_fused_limits(int k, int mode, int64_t* record_floats, int* max_steps) {
+  if (!record_floats || !max_steps || (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB)) return FRACTAL_EINVAL;
+  Launch L;
+  int margin = 0;
+  if (!kappa_fused_geometry(k, mode, L, margin)) return FRACTAL_EINVAL;
+  *record_floats = kappa_record_float4s(k) * 4;
+  *max_steps = margin;
+  return FRACTAL_OK;
+}
+
+int fractal_kappa_trajectory_df(fractal_plan_t p, const float* dev_in, float* dev_out, float* dev_traj,
+                                const float* dev_kappa, double coef, int steps, void* stream) {
+  if (check_plan(p) || !dev_in || !dev_kappa || (!dev_out && !dev_traj) || !std::isfinite(coef)) return FRACTAL_EINVAL;
+  const void* all[4] = {dev_in, dev_out, dev_traj, dev_kappa};
+  for (int i = 0; i < 4; ++i) {
+    if (all[i] && !aligned16(all[i])) return FRACTAL_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (all[i] && all[i] == all[j]) return FRACTAL_EINVAL;
+  }
+  Launch L;
+  int margin = 0;
+  if (!kappa_fused_geometry(p->k, p->mode, L, margin) || steps < 1 || steps > margin) return FRACTAL_EINVAL;
+  cudaError_t e = launch_kappa_fused_df(p->mode, p->k, reinterpret_cast<const dfloat*>(dev_in),
+                                        reinterpret_cast<dfloat*>(dev_out), reinterpret_cast<float4*>(dev_traj),
+                                        dev_kappa, dfloat_from_double(0.5 * coef), steps, (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "kappa_trajectory_df");
+}
+
+int fractal_kappa_gradient_df(fractal_plan_t p, const float* dev_utraj, const float* dev_ptraj, float* dev_gkappa,
+                              double coef, int steps, void* stream) {
+  if (check_plan(p) || !dev_utraj || !dev_ptraj || !dev_gkappa || !std::isfinite(coef) || steps < 1)
+    return FRACTAL_EINVAL;
+  const void* all[3] = {dev_utraj, dev_ptraj, dev_gkappa};
+  for (int i = 0; i < 3; ++i) {
+    if (!aligned16(all[i])) return FRACTAL_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (all[i] == all[j]) return FRACTAL_EINVAL;
+  }
+  Launch L;
+  int margin = 0;
+  if (!kappa_fused_geometry(p->k, p->mode, L, margin)) return FRACTAL_EINVAL;
+  cudaError_t e = launch_kappa_grad_df(p->mode, p->k, reinterpret_cast<const float4*>(dev_utraj),
+                                       reinterpret_cast<const float4*>(dev_ptraj), reinterpret_cast<dfloat*>(dev_gkappa),
+                                       dfloat_from_double(0.5 * coef), steps, (cudaStream_t)stream);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "kappa_gradient_df");
 }
 
 int fractal_plan_device_status(fractal_plan_t p, int* code) {

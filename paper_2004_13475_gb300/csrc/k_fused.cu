@@ -946,6 +946,267 @@ __global__ void __launch_bounds__(32, MINB) diffusion_fused_warp_kernel(const fl
   }
 }
 
+// ------------------------------------- conductivity steps in double-float ---
+// The gradient path's state u (and the adjoint state p) in double-float,
+// advanced up to `margin` steps per launch like the float32 fused kernels:
+// one 8 x 8 block per thread, the super-tile (side 128 at most) and the
+// member blocks of its margin boxes within reach, ports exchanged through
+// shared memory once per step.  The step is u'_c = u_c + sum_nb c_{c,nb}
+// (u_nb - u_c) with c = (a / 2) (kappa_c + kappa_nb) (the edge conductance
+// of the gradient path), formed once per launch per link in double-float.
+// The flux of a link is computed once and given to both ends: the block's
+// 26 links form the tree of bparent, updated in place children first (a
+// child's flux with its parent enters the parent's sum before the parent is
+// overwritten), the four links to other blocks at the ports.  A launch may
+// record the state of its own blocks before every step (and after the last)
+// in compact records: 27 members x (hi, lo) and a pad, 14 float4s per block,
+// stored float4 by float4 per super-tile like the float32 records.  The
+// reverse step of the gradient is the same operator applied to p (it is
+// symmetric), so the same kernel carries p back through a segment; the
+// kappa gradient is then summed over the segment from the two recorded
+// trajectories (kappa_grad_df_kernel).
+constexpr int kKapThreads = 128;
+constexpr int kKRecF4 = 14;
+
+struct DfSum {
+  dfloat s = dfloat(0.f, 0.f);
+  bool any = false;
+  __device__ __forceinline__ void add(dfloat v) {
+    s = any ? s + v : v;
+    any = true;
+  }
+  __device__ __forceinline__ void sub(dfloat v) {
+    s = any ? s - v : -v;
+    any = true;
+  }
+};
+
+// One step of a block: c[q] is the coefficient of the link from member q to
+// its parent; cu, cl, cr, cd those of the port links (0 where the neighbour
+// block is not a member) and vu, vl, vr, vd the neighbour values there.
+__device__ __forceinline__ void kblock_step(dfloat (&u)[kB * kB], const dfloat (&c)[kB * kB], dfloat cu, dfloat cl,
+                                            dfloat cr, dfloat cd, dfloat vu, dfloat vl, dfloat vr, dfloat vd) {
+  DfSum acc[kB * kB];  // fluxes of the children's links, per cell
+#pragma unroll
+  for (int s = 2 * (kB - 1); s >= 0; --s) {
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const int i = s - j;
+      if (i < 0 || i >= kB || !amem(i, j)) continue;
+      const int q = j * kB + i;
+      DfSum f = acc[q];
+      if (q != 0) {
+        const int pq = bparent(i, j);
+        const dfloat fl = c[q] * (u[pq] - u[q]);
+        f.add(fl);
+        acc[pq].sub(fl);
+      } else {
+        f.add(cu * (vu - u[0]));
+        f.add(cl * (vl - u[0]));
+      }
+      if (q == kB - 1) f.add(cr * (vr - u[q]));
+      if (q == (kB - 1) * kB) f.add(cd * (vd - u[q]));
+      u[q] = u[q] + f.s;
+    }
+  }
+}
+
+// Float4 0 of the record of block `rec` (a record's float4s are nb apart).
+__device__ __forceinline__ int64_t krec_base(int64_t rec, int nb) {
+  const int64_t t = rec % nb;
+  return (rec - t) * kKRecF4 + t;
+}
+
+__device__ __forceinline__ void krec_write(float4* __restrict__ p, int nb, const dfloat (&u)[kB * kB]) {
+  float v[4 * kKRecF4];
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < kB * kB; ++q) {
+    if (!amem(q % kB, q / kB)) continue;
+    v[2 * m] = u[q].hi;
+    v[2 * m + 1] = u[q].lo;
+    ++m;
+  }
+  v[4 * kKRecF4 - 2] = v[4 * kKRecF4 - 1] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kKRecF4; ++i) p[(int64_t)i * nb] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
+__device__ __forceinline__ void krec_read(const float4* __restrict__ p, int nb, dfloat (&u)[kB * kB]) {
+  float v[4 * kKRecF4];
+#pragma unroll
+  for (int i = 0; i < kKRecF4; ++i) {
+    const float4 r = __ldg(p + (int64_t)i * nb);
+    v[4 * i] = r.x;
+    v[4 * i + 1] = r.y;
+    v[4 * i + 2] = r.z;
+    v[4 * i + 3] = r.w;
+  }
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < kB * kB; ++q) {
+    if (!amem(q % kB, q / kB)) {
+      u[q] = dfloat(0.f, 0.f);
+      continue;
+    }
+    u[q] = dfloat(v[2 * m], v[2 * m + 1]);
+    ++m;
+  }
+}
+
+// Member m of a record (its two floats lie in one float4: 2m is even).
+__device__ __forceinline__ dfloat krec_member(const float4* __restrict__ p, int nb, int m) {
+  const float4 r = __ldg(p + (int64_t)((2 * m) >> 2) * nb);
+  return ((2 * m) & 3) ? dfloat(r.z, r.w) : dfloat(r.x, r.y);
+}
+
+// A launch of nsteps <= reach <= M steps: `in` -> `out` (embedded double-
+// float arrays; out may be null), the state before each step into the
+// records traj + s * stride (s = 0 .. nsteps - 1) and, when out is null,
+// the final state into record nsteps (traj may be null).
+template <int MODE>
+__global__ void __launch_bounds__(kKapThreads, 3) kappa_fused_df_kernel(const dfloat* __restrict__ in,
+                                                                         dfloat* __restrict__ out,
+                                                                         float4* __restrict__ traj, int64_t stride,
+                                                                         const float* __restrict__ kappa, dfloat ha,
+                                                                         int nsteps, int M, int reach, Geo g) {
+  __shared__ __align__(16) float2 kports[6 * (kKapThreads + 1)];
+  __shared__ int tab[81];  // BB: member block slots of the super-tile (side <= 128)
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  const FGeo f = make_fgeo(g.n, g.T, M, reach, 3, g.R);
+  if (MODE == kBB) {
+    bb_table(tab, f);
+    __syncthreads();
+  }
+  const int OX = sx << f.L, OY = sy << f.L;
+  const FSetup su = fused_setup<MODE>(f, OX, OY, tab);
+  const int t = threadIdx.x, SL = blockDim.x + 1, zero = blockDim.x;
+  float2* P0 = kports;
+  float2* PR = kports + 2 * SL;
+  float2* PD = kports + 4 * SL;
+  const bool own = su.active && t < f.nb;
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
+  float4* rec = traj ? traj + krec_base(st * f.nb + t, f.nb) : nullptr;
+  dfloat u[kB * kB], c[kB * kB];
+  dfloat cu(0.f), cl(0.f), cr(0.f), cd(0.f);
+  size_t base = 0;
+#pragma unroll
+  for (int q = 0; q < kB * kB; ++q) c[q] = dfloat(0.f, 0.f);
+  if (su.active) {
+    base = (size_t)(OY + su.by) * kB * (size_t)f.n + (size_t)(OX + su.bx) * kB;
+    load_block(u, in + base, f.n);
+    float kk[kB * kB];
+    load_block(kk, kappa + base, f.n);
+#pragma unroll
+    for (int q = 1; q < kB * kB; ++q)
+      if (amem(q % kB, q / kB)) c[q] = ha * two_sum(kk[q], kk[bparent(q % kB, q / kB)]);
+    if (su.fu) cu = ha * two_sum(kk[0], __ldg(kappa + base - f.n));
+    if (su.fl) cl = ha * two_sum(kk[0], __ldg(kappa + base - 1));
+    if (su.fr) cr = ha * two_sum(kk[kB - 1], __ldg(kappa + base + kB));
+    if (su.fd) cd = ha * two_sum(kk[(kB - 1) * kB], __ldg(kappa + base + (size_t)kB * f.n));
+  } else {
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) u[q] = dfloat(0.f, 0.f);
+  }
+  P0[t] = make_float2(u[0].hi, u[0].lo);
+  PR[t] = make_float2(u[kB - 1].hi, u[kB - 1].lo);
+  PD[t] = make_float2(u[(kB - 1) * kB].hi, u[(kB - 1) * kB].lo);
+  if (t == 0) {
+    P0[zero] = P0[SL + zero] = make_float2(0.f, 0.f);
+    PR[zero] = PR[SL + zero] = make_float2(0.f, 0.f);
+    PD[zero] = PD[SL + zero] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int s = 0; s < nsteps; ++s) {
+    const int cur = (s & 1) * SL, nxt = SL - cur;
+    if (rec && own) krec_write(rec + (int64_t)s * stride, f.nb, u);
+    if (su.active) {
+      const float2 vu = PD[cur + su.up], vl = PR[cur + su.lf], vr = P0[cur + su.rt], vd = P0[cur + su.dn];
+      kblock_step(u, c, cu, cl, cr, cd, dfloat(vu.x, vu.y), dfloat(vl.x, vl.y), dfloat(vr.x, vr.y),
+                  dfloat(vd.x, vd.y));
+    }
+    P0[nxt + t] = make_float2(u[0].hi, u[0].lo);
+    PR[nxt + t] = make_float2(u[kB - 1].hi, u[kB - 1].lo);
+    PD[nxt + t] = make_float2(u[(kB - 1) * kB].hi, u[(kB - 1) * kB].lo);
+    __syncthreads();
+  }
+  if (!own) return;
+  if (rec && !out) krec_write(rec + (int64_t)nsteps * stride, f.nb, u);
+  if (out) store_block(out + base, f.n, u);
+}
+
+// dJ/dkappa over a segment of nsteps steps from the recorded trajectories:
+// utraj record s = u_(t0 + s), ptraj record s = p_(t0 + nsteps - s), so the
+// step t0 + s pairs utraj[s] with ptraj[nsteps - 1 - s].  Per link (c, nb)
+// and step, (u_nb - u_c) (p_c - p_nb) enters the sums of both ends (the same
+// value); at the end gkappa += (a / 2) * sum at every member (read-modify-
+// write of the embedded double-float array).  One thread per member block of
+// a super-tile (side as the fused launch).
+template <int MODE>
+__global__ void __launch_bounds__(96) kappa_grad_df_kernel(const float4* __restrict__ utraj,
+                                                           const float4* __restrict__ ptraj, int64_t stride,
+                                                           dfloat* __restrict__ gk, dfloat ha, int nsteps, Geo g) {
+  __shared__ int tab[81];
+  int sx, sy;
+  if (!cta_supertile<MODE>(g, sx, sy)) return;
+  const FGeo f = make_fgeo(g.n, g.T, kB, 1, 3, g.R);
+  if (MODE == kBB) {
+    bb_table(tab, f);
+    __syncthreads();
+  }
+  const int t = threadIdx.x;
+  if (t >= f.nb) return;
+  int bx, by;
+  member_block<MODE>(t, f, tab, bx, by);
+  const int GX = (sx << f.L) + bx, GY = (sy << f.L) + by, nblk = f.n / kB;
+  const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
+  const int64_t r0 = krec_base(st * f.nb + t, f.nb);
+  // the port neighbours' records and the member there: up (0,7) of the block
+  // above, left (7,0) of the block left, right and down (0,0)
+  const bool fu = block_member(GX, GY - 1, nblk), fl = block_member(GX - 1, GY, nblk),
+             fr = block_member(GX + 1, GY, nblk), fd = block_member(GX, GY + 1, nblk);
+  const int64_t ru = fu ? krec_base(block_record<MODE>(GX, GY - 1, f), f.nb) : 0;
+  const int64_t rl = fl ? krec_base(block_record<MODE>(GX - 1, GY, f), f.nb) : 0;
+  const int64_t rr = fr ? krec_base(block_record<MODE>(GX + 1, GY, f), f.nb) : 0;
+  const int64_t rd = fd ? krec_base(block_record<MODE>(GX, GY + 1, f), f.nb) : 0;
+  DfSum gs[kB * kB];
+  for (int s = 0; s < nsteps; ++s) {
+    const float4* U = utraj + (int64_t)s * stride;
+    const float4* P = ptraj + (int64_t)(nsteps - 1 - s) * stride;
+    dfloat u[kB * kB], p[kB * kB];
+    krec_read(U + r0, f.nb, u);
+    krec_read(P + r0, f.nb, p);
+#pragma unroll
+    for (int q = 1; q < kB * kB; ++q) {
+      if (!amem(q % kB, q / kB)) continue;
+      const int pq = bparent(q % kB, q / kB);
+      const dfloat w = (u[pq] - u[q]) * (p[q] - p[pq]);
+      gs[q].add(w);
+      gs[pq].add(w);
+    }
+    if (fu) gs[0].add((krec_member(U + ru, f.nb, 26) - u[0]) * (p[0] - krec_member(P + ru, f.nb, 26)));
+    if (fl) gs[0].add((krec_member(U + rl, f.nb, 7) - u[0]) * (p[0] - krec_member(P + rl, f.nb, 7)));
+    if (fr) gs[kB - 1].add((krec_member(U + rr, f.nb, 0) - u[kB - 1]) * (p[kB - 1] - krec_member(P + rr, f.nb, 0)));
+    if (fd) {
+      const int q = (kB - 1) * kB;
+      gs[q].add((krec_member(U + rd, f.nb, 0) - u[q]) * (p[q] - krec_member(P + rd, f.nb, 0)));
+    }
+  }
+  dfloat* row = gk + (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
+#pragma unroll
+  for (int j = 0; j < kB; ++j) {
+    dfloat v[kB];
+    ld4(row + (size_t)j * f.n, v);
+    ld4(row + (size_t)j * f.n + 4, v + 4);
+#pragma unroll
+    for (int i = 0; i < kB; ++i) v[i] = amem(i, j) && gs[j * kB + i].any ? v[i] + ha * gs[j * kB + i].s
+                                                                           : (amem(i, j) ? v[i] : dfloat(0.f, 0.f));
+    st4(row + (size_t)j * f.n, v);
+    st4(row + (size_t)j * f.n + 4, v + 4);
+  }
+}
+
 // ---------------------------------------------------------------- batches ---
 // Persistent launch over the member super-tiles of many instances: CTA c
 // takes items c, c + gridDim.x, ...; item w belongs to the last instance
@@ -1301,6 +1562,49 @@ cudaError_t launch_fused_describe(int mode, int log_rho, int margin, int reach, 
 
 int fused_warp_slots() { return kWarpSlots; }
 int fused_q3_slots() { return kQ3Slots; }
+
+// Geometry of the double-float conductivity launches: super-tiles of side
+// min(128, n) (k >= 4), margins min(32, side / 2); false if unsupported.
+bool kappa_fused_geometry(int k, int mode, Launch& L, int& margin) {
+  if (k < 4 || k > 16) return false;
+  const int T = k >= 7 ? 128 : 1 << k;
+  margin = T / 2 < 32 ? T / 2 : 32;
+  if (!supertile_grid(k, 3, mode, ilog2c(T) - 3, L)) return false;
+  L.threads = fused_threads(L.geo, 8, margin, margin);
+  L.smem = 0;
+  return L.threads > 0 && L.threads <= kKapThreads;
+}
+
+int64_t kappa_record_float4s(int k) { return fused_records(k) * kKRecF4; }
+
+cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out, float4* traj, const float* kappa,
+                                  dfloat ha, int nsteps, cudaStream_t s) {
+  Launch L;
+  int margin = 0;
+  if (!kappa_fused_geometry(k, mode, L, margin) || nsteps < 1 || nsteps > margin) return cudaErrorInvalidValue;
+  const int threads = fused_threads(L.geo, 8, margin, nsteps);
+  const int64_t stride = kappa_record_float4s(k);
+  if (mode == kLambda)
+    kappa_fused_df_kernel<kLambda><<<L.grid, threads, 0, s>>>(in, out, traj, stride, kappa, ha, nsteps, margin, nsteps,
+                                                              L.geo);
+  else
+    kappa_fused_df_kernel<kBB><<<L.grid, threads, 0, s>>>(in, out, traj, stride, kappa, ha, nsteps, margin, nsteps,
+                                                          L.geo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const float4* ptraj, dfloat* gk, dfloat ha,
+                                 int nsteps, cudaStream_t s) {
+  Launch L;
+  int margin = 0;
+  if (!kappa_fused_geometry(k, mode, L, margin) || nsteps < 1) return cudaErrorInvalidValue;
+  const int64_t stride = kappa_record_float4s(k);
+  if (mode == kLambda)
+    kappa_grad_df_kernel<kLambda><<<L.grid, 96, 0, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo);
+  else
+    kappa_grad_df_kernel<kBB><<<L.grid, 96, 0, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo);
+  return cudaGetLastError();
+}
 
 int64_t fused_records(int k) {
   int64_t r = 1;

@@ -82,6 +82,18 @@ int fused_threads(const Geo& g, int rho, int margin, int reach);
 // Block slots of the one-warp fused launch (super-tiles of side 128, margins
 // up to 16 cells).
 int fused_warp_slots();
+// Double-float conductivity launches for the gradient path (super-tiles of
+// side min(128, n), margins min(32, side / 2), k >= 4): `nsteps` <= margin
+// steps in -> out (out may be null) recording the state before each step
+// (and after the last when out is null) into traj (may be null); and the
+// kappa gradient of a segment from two recorded trajectories.
+bool kappa_fused_geometry(int k, int mode, Launch& L, int& margin);
+int64_t kappa_record_float4s(int k);
+cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out, float4* traj, const float* kappa,
+                                  dfloat ha, int nsteps, cudaStream_t s);
+cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const float4* ptraj, dfloat* gk, dfloat ha,
+                                 int nsteps, cudaStream_t s);
+
 // Block slots of the four-warp fused launch (super-tiles of side 256,
 // margins of 64 cells at a reach of at most 56 steps).
 int fused_q3_slots();

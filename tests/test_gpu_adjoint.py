@@ -194,3 +194,90 @@ def test_adjoint_validation(fr):
     with pytest.raises(fr.FractalError):
         fr.fractal_step_diffusion_kappa_df(plan, y[0], y[0], x[3], A, 1)              # a == b
     fr.fractal_adjoint_diffusion_step_df(plan, y[0], y[1], y[2], x[3], y[4], A)
+
+
+def _df(x):
+    """A float32 field as double-float (hi, lo = 0) pairs on the device."""
+    t = dev(x)
+    return torch.stack([t, torch.zeros_like(t)], dim=1).reshape(-1).contiguous()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k,steps", [(4, 8), (5, 13), (7, 32), (9, 20)])
+def test_fused_trajectory_launch_matches_oracle(fr, k, steps, mode):
+    """One fused double-float launch (the gradient path's forward and reverse
+    passes) against the FP64 oracle, every cell of every member block written;
+    the records it keeps are consistent: the same launch without an output
+    records the same states before each step, and its final record equals the
+    record of the output state."""
+    n = 1 << k
+    u0, kappa, _ = fields(k, 60 + k)
+    plan = fr.fractal_map(k, 8, mode)
+    rf, ms = fr.fractal_kappa_fused_limits(k, mode)
+    assert steps <= ms and rf == 3 ** (k - 3) * 56
+    kap = dev(kappa)
+    a_in = _df(u0)
+    out = torch.full_like(a_in, -5.0)
+    tr1 = torch.zeros(rf * (steps + 1), device="cuda")
+    tr2 = torch.zeros_like(tr1)
+    tr3 = torch.zeros(rf * 2, device="cuda")
+    fr.fractal_kappa_trajectory_df(plan, a_in, out, tr1, kap, A, steps)
+    fr.fractal_kappa_trajectory_df(plan, a_in, None, tr2, kap, A, steps)
+    fr.fractal_kappa_trajectory_df(plan, out, None, tr3, kap, A, 1)
+    hl = out.view(-1, 2).cpu().numpy()
+    got = (hl[:, 0].astype(np.float64) + hl[:, 1]).reshape(n, n)
+    dom = oracle.Domain.build(n)
+    want = oracle.diffusion_run(u0.astype(np.float64), steps, A, dom, kappa.astype(np.float64))
+    assert rel_err(got, want, dom.mask)[0] <= 1e-12
+    cover = block_cover(n)
+    assert np.all(got[cover & ~dom.mask] == 0) and np.all(got[~cover] == -10.0)
+    assert torch.equal(tr1[:rf * steps], tr2[:rf * steps])
+    assert torch.equal(tr2[rf * steps:], tr3[:rf])
+    assert not torch.equal(tr2[:rf], tr2[rf * steps:])
+
+
+def test_fused_gradient_path_validation(fr):
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_fused_limits(3)                                    # below the fused path's levels
+    plan = fr.fractal_map(8, 8)
+    rf, ms = fr.fractal_kappa_fused_limits(8)
+    x = torch.zeros(2 * 256 * 256, device="cuda")
+    y = torch.zeros_like(x)
+    kap = torch.zeros(256 * 256, device="cuda")
+    tr = torch.zeros(rf * (ms + 1), device="cuda")
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_trajectory_df(plan, x, y, tr, kap, A, ms + 1)      # more steps than one launch takes
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_trajectory_df(plan, x, x, tr, kap, A, 2)           # in == out
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_trajectory_df(plan, x, None, None, kap, A, 2)      # nowhere to write
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_gradient_df(plan, tr, tr, x, A, 2)                 # the two records alias
+    fr.fractal_kappa_trajectory_df(plan, x, y, tr, kap, A, ms)
+
+
+@pytest.mark.parametrize("k,steps,every", [(8, 45, 20), (7, 70, 40)])
+def test_fused_and_single_step_gradients_agree(fr, k, steps, every):
+    """The fused double-float path (several steps per launch, recorded
+    trajectories; every = 40 takes two launches per segment) and the
+    single-step path give the same gradients within the double-float
+    rounding, both within 1e-4 of the FP64 adjoint."""
+    n = 1 << k
+    u0, kappa, target = fields(k, 90 + k)
+    dom = oracle.Domain.build(n)
+    from paper_2004_13475_gb300.autograd import diffusion_kappa
+    res = []
+    for fused in (True, False):
+        u = dev(u0).requires_grad_(True)
+        kp = dev(kappa).requires_grad_(True)
+        loss = ((diffusion_kappa(u, kp, k, A, steps, every, 0, "df", fused) - dev(target)) ** 2).sum()
+        loss.backward()
+        res.append((u.grad.cpu().numpy().reshape(n, n), kp.grad.cpu().numpy().reshape(n, n)))
+    _, wu, wk = oracle.diffusion_loss_gradients(dom, dom.take(u0).astype(np.float64),
+                                                dom.take(kappa).astype(np.float64),
+                                                dom.take(target).astype(np.float64), steps, A)
+    for gu, gk in res:
+        assert rel_err(gu, dom.put(wu, np.float64), dom.mask)[0] <= 1e-4
+        assert rel_err(gk, dom.put(wk, np.float64), dom.mask)[0] <= 1e-4
+    assert rel_err(res[0][0], res[1][0].astype(np.float64), dom.mask)[0] <= 1e-6
+    assert rel_err(res[0][1], res[1][1].astype(np.float64), dom.mask)[0] <= 1e-6
