@@ -43,9 +43,10 @@ def _to_state(x, state):
     (lo = 0 for float32 input, the float64 remainder otherwise)."""
     x = x.detach()
     if state == "df":
+        if x.dtype == torch.float32:  # (x, 0) pairs in one pass: a complex with zero imaginary part
+            return torch.view_as_real(x.to(torch.complex64)).reshape(-1)
         hi = x.to(torch.float32)
-        lo = ((x.double() - hi.double()).to(torch.float32) if x.dtype == torch.float64
-              else torch.zeros_like(hi))
+        lo = (x.double() - hi.double()).to(torch.float32)
         return torch.stack([hi, lo], dim=1).reshape(-1).contiguous()
     return x.to(_STATES[state][2]).contiguous()
 
@@ -54,6 +55,8 @@ def _from_state(y, state, dtype):
     """The state's values as `dtype` (double-float: hi + lo in float64 first)."""
     if state == "df":
         hl = y.view(-1, 2)
+        if dtype == torch.float32:  # a float sum of the two parts rounds their exact sum correctly
+            return hl[:, 0] + hl[:, 1]
         return (hl[:, 0].double() + hl[:, 1].double()).to(dtype)
     return y.to(dtype)
 

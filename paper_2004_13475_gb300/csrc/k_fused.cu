@@ -33,6 +33,7 @@
 
 #include "blocks.cuh"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace fractal {
 namespace {
@@ -1054,6 +1055,29 @@ __device__ __forceinline__ void krec_read(const float4* __restrict__ p, int nb, 
   }
 }
 
+// A record in shared memory (float4s nb apart, as in the trajectory).
+__device__ __forceinline__ void krec_read_shared(const float4* p, int nb, dfloat (&u)[kB * kB]) {
+  float v[4 * kKRecF4];
+#pragma unroll
+  for (int i = 0; i < kKRecF4; ++i) {
+    const float4 r = p[i * nb];
+    v[4 * i] = r.x;
+    v[4 * i + 1] = r.y;
+    v[4 * i + 2] = r.z;
+    v[4 * i + 3] = r.w;
+  }
+  int m = 0;
+#pragma unroll
+  for (int q = 0; q < kB * kB; ++q) {
+    if (!amem(q % kB, q / kB)) {
+      u[q] = dfloat(0.f, 0.f);
+      continue;
+    }
+    u[q] = dfloat(v[2 * m], v[2 * m + 1]);
+    ++m;
+  }
+}
+
 // Member m of a record (its two floats lie in one float4: 2m is even).
 __device__ __forceinline__ dfloat krec_member(const float4* __restrict__ p, int nb, int m) {
   const float4 r = __ldg(p + (int64_t)((2 * m) >> 2) * nb);
@@ -1141,12 +1165,33 @@ __global__ void __launch_bounds__(kKapThreads, 3) kappa_fused_df_kernel(const df
 // step t0 + s pairs utraj[s] with ptraj[nsteps - 1 - s].  Per link (c, nb)
 // and step, (u_nb - u_c) (p_c - p_nb) enters the sums of both ends (the same
 // value); at the end gkappa += (a / 2) * sum at every member (read-modify-
-// write of the embedded double-float array).  One thread per member block of
-// a super-tile (side as the fused launch).
+// write of the embedded double-float array).  One CTA per super-tile (side
+// as the fused launch), one thread per member block; the super-tile's two
+// records of a step (contiguous) and the port neighbours' values are copied
+// into shared memory asynchronously one step ahead (cp.async, two stages),
+// so that the loads of step s + 1 overlap the sums of step s.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kGradThreads = 96;
+
+// Shared memory of one stage: the u and p records of the super-tile
+// (2 nb kKRecF4 float4) and eight port values per block (float2).
+__host__ __device__ inline int kgrad_stage_bytes(int nb) { return 2 * nb * kKRecF4 * 16 + nb * 8 * 8; }
+
 template <int MODE>
-__global__ void __launch_bounds__(96) kappa_grad_df_kernel(const float4* __restrict__ utraj,
-                                                           const float4* __restrict__ ptraj, int64_t stride,
-                                                           dfloat* __restrict__ gk, dfloat ha, int nsteps, Geo g) {
+__global__ void __launch_bounds__(kGradThreads, 2) kappa_grad_df_kernel(const float4* __restrict__ utraj,
+                                                                          const float4* __restrict__ ptraj,
+                                                                          int64_t stride, dfloat* __restrict__ gk,
+                                                                          dfloat ha, int nsteps, Geo g) {
+  extern __shared__ __align__(16) float4 gsm[];
   __shared__ int tab[81];
   int sx, sy;
   if (!cta_supertile<MODE>(g, sx, sy)) return;
@@ -1155,44 +1200,105 @@ __global__ void __launch_bounds__(96) kappa_grad_df_kernel(const float4* __restr
     bb_table(tab, f);
     __syncthreads();
   }
-  const int t = threadIdx.x;
-  if (t >= f.nb) return;
-  int bx, by;
-  member_block<MODE>(t, f, tab, bx, by);
-  const int GX = (sx << f.L) + bx, GY = (sy << f.L) + by, nblk = f.n / kB;
+  const int t = threadIdx.x, nb = f.nb;
+  const bool act = t < nb;
   const int64_t st = MODE == kLambda ? cta_id() : (int64_t)bb_rank(sx, sy, f.R);
-  const int64_t r0 = krec_base(st * f.nb + t, f.nb);
-  // the port neighbours' records and the member there: up (0,7) of the block
-  // above, left (7,0) of the block left, right and down (0,0)
-  const bool fu = block_member(GX, GY - 1, nblk), fl = block_member(GX - 1, GY, nblk),
-             fr = block_member(GX + 1, GY, nblk), fd = block_member(GX, GY + 1, nblk);
-  const int64_t ru = fu ? krec_base(block_record<MODE>(GX, GY - 1, f), f.nb) : 0;
-  const int64_t rl = fl ? krec_base(block_record<MODE>(GX - 1, GY, f), f.nb) : 0;
-  const int64_t rr = fr ? krec_base(block_record<MODE>(GX + 1, GY, f), f.nb) : 0;
-  const int64_t rd = fd ? krec_base(block_record<MODE>(GX, GY + 1, f), f.nb) : 0;
-  DfSum gs[kB * kB];
-  for (int s = 0; s < nsteps; ++s) {
-    const float4* U = utraj + (int64_t)s * stride;
-    const float4* P = ptraj + (int64_t)(nsteps - 1 - s) * stride;
-    dfloat u[kB * kB], p[kB * kB];
-    krec_read(U + r0, f.nb, u);
-    krec_read(P + r0, f.nb, p);
-#pragma unroll
-    for (int q = 1; q < kB * kB; ++q) {
-      if (!amem(q % kB, q / kB)) continue;
-      const int pq = bparent(q % kB, q / kB);
-      const dfloat w = (u[pq] - u[q]) * (p[q] - p[pq]);
-      gs[q].add(w);
-      gs[pq].add(w);
-    }
-    if (fu) gs[0].add((krec_member(U + ru, f.nb, 26) - u[0]) * (p[0] - krec_member(P + ru, f.nb, 26)));
-    if (fl) gs[0].add((krec_member(U + rl, f.nb, 7) - u[0]) * (p[0] - krec_member(P + rl, f.nb, 7)));
-    if (fr) gs[kB - 1].add((krec_member(U + rr, f.nb, 0) - u[kB - 1]) * (p[kB - 1] - krec_member(P + rr, f.nb, 0)));
-    if (fd) {
-      const int q = (kB - 1) * kB;
-      gs[q].add((krec_member(U + rd, f.nb, 0) - u[q]) * (p[q] - krec_member(P + rd, f.nb, 0)));
-    }
+  const int64_t tile0 = st * nb * kKRecF4;  // the super-tile's records: float4 [tile0, tile0 + nb * 14)
+  int GX = 0, GY = 0;
+  bool fu = false, fl = false, fr = false, fd = false;
+  int64_t nbr[4] = {0, 0, 0, 0};  // float4 holding the port neighbour's member (up, left, right, down)
+  if (act) {
+    int bx, by;
+    member_block<MODE>(t, f, tab, bx, by);
+    GX = (sx << f.L) + bx;
+    GY = (sy << f.L) + by;
+    const int nblk = f.n / kB;
+    fu = block_member(GX, GY - 1, nblk);
+    fl = block_member(GX - 1, GY, nblk);
+    fr = block_member(GX + 1, GY, nblk);
+    fd = block_member(GX, GY + 1, nblk);
+    // members 26 ((0,7)), 7 ((7,0)), 0, 0: float4 (2m) / 4 of the record
+    if (fu) nbr[0] = krec_base(block_record<MODE>(GX, GY - 1, f), nb) + (int64_t)13 * nb;
+    if (fl) nbr[1] = krec_base(block_record<MODE>(GX - 1, GY, f), nb) + (int64_t)3 * nb;
+    if (fr) nbr[2] = krec_base(block_record<MODE>(GX + 1, GY, f), nb);
+    if (fd) nbr[3] = krec_base(block_record<MODE>(GX, GY + 1, f), nb);
   }
+  const int sb = kgrad_stage_bytes(nb) / 16;  // float4 per stage
+  auto stage_u = [&](int b) { return gsm + b * sb; };
+  auto stage_p = [&](int b) { return gsm + b * sb + nb * kKRecF4; };
+  auto stage_n = [&](int b) { return reinterpret_cast<float2*>(gsm + b * sb + 2 * nb * kKRecF4); };
+  // copy step s's records and port values into stage b (one commit group)
+  auto load = [&](int b, int s) {
+    const float4* U = utraj + (int64_t)s * stride + tile0;
+    const float4* P = ptraj + (int64_t)(nsteps - 1 - s) * stride + tile0;
+    float4* du = stage_u(b);
+    float4* dp = stage_p(b);
+    for (int i = t; i < nb * kKRecF4; i += kGradThreads) {
+      cp_async16(du + i, U + i);
+      cp_async16(dp + i, P + i);
+    }
+    if (act) {
+      const float4* Ua = utraj + (int64_t)s * stride;
+      const float4* Pa = ptraj + (int64_t)(nsteps - 1 - s) * stride;
+      float2* dn = stage_n(b) + t * 8;
+      // the member's float2: member m is floats 2m, 2m + 1: (0,7) = member 26 -> .x.y of float4 13,
+      // (7,0) = member 7 -> .z.w of float4 3, (0,0) = member 0 -> .x.y of float4 0
+      const int off[4] = {0, 2, 0, 0};
+      const bool has[4] = {fu, fl, fr, fd};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!has[q]) continue;
+        cp_async8(dn + q, reinterpret_cast<const float*>(Ua + nbr[q]) + off[q]);
+        cp_async8(dn + 4 + q, reinterpret_cast<const float*>(Pa + nbr[q]) + off[q]);
+      }
+    }
+    cp_async_commit();
+  };
+  DfSum gs[kB * kB];
+  load(0, 0);
+  for (int s = 0; s < nsteps; ++s) {
+    const int b = s & 1;
+    if (s + 1 < nsteps) {
+      load(b ^ 1, s + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    if (act) {
+      dfloat u[kB * kB], p[kB * kB];
+      krec_read_shared(stage_u(b) + t, nb, u);
+      krec_read_shared(stage_p(b) + t, nb, p);
+#pragma unroll
+      for (int q = 1; q < kB * kB; ++q) {
+        if (!amem(q % kB, q / kB)) continue;
+        const int pq = bparent(q % kB, q / kB);
+        const dfloat w = (u[pq] - u[q]) * (p[q] - p[pq]);
+        gs[q].add(w);
+        gs[pq].add(w);
+      }
+      const float2* dn = stage_n(b) + t * 8;
+      if (fu) {
+        const float2 a = dn[0], c = dn[4];
+        gs[0].add((dfloat(a.x, a.y) - u[0]) * (p[0] - dfloat(c.x, c.y)));
+      }
+      if (fl) {
+        const float2 a = dn[1], c = dn[5];
+        gs[0].add((dfloat(a.x, a.y) - u[0]) * (p[0] - dfloat(c.x, c.y)));
+      }
+      if (fr) {
+        const float2 a = dn[2], c = dn[6];
+        gs[kB - 1].add((dfloat(a.x, a.y) - u[kB - 1]) * (p[kB - 1] - dfloat(c.x, c.y)));
+      }
+      if (fd) {
+        const float2 a = dn[3], c = dn[7];
+        const int q = (kB - 1) * kB;
+        gs[q].add((dfloat(a.x, a.y) - u[q]) * (p[q] - dfloat(c.x, c.y)));
+      }
+    }
+    __syncthreads();  // stage b is refilled by the next iteration's copies
+  }
+  if (!act) return;
   dfloat* row = gk + (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
 #pragma unroll
   for (int j = 0; j < kB; ++j) {
@@ -1599,11 +1705,14 @@ cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const flo
   int margin = 0;
   if (!kappa_fused_geometry(k, mode, L, margin) || nsteps < 1) return cudaErrorInvalidValue;
   const int64_t stride = kappa_record_float4s(k);
-  if (mode == kLambda)
-    kappa_grad_df_kernel<kLambda><<<L.grid, 96, 0, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo);
-  else
-    kappa_grad_df_kernel<kBB><<<L.grid, 96, 0, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo);
-  return cudaGetLastError();
+  const int smem = 2 * kgrad_stage_bytes(member_blocks(L.geo.T));
+  auto run = [&](auto* k) -> cudaError_t {
+    cudaError_t e = allow_smem((const void*)k, smem);
+    if (e != cudaSuccess) return e;
+    k<<<L.grid, kGradThreads, smem, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo);
+    return cudaGetLastError();
+  };
+  return mode == kLambda ? run(kappa_grad_df_kernel<kLambda>) : run(kappa_grad_df_kernel<kBB>);
 }
 
 int64_t fused_records(int k) {
