@@ -258,6 +258,9 @@ def main():
     ap.add_argument("--rho-diff", type=int, default=0, help="fix the diffusion's rho (0: tune over 8, 16, 32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-form", default="records", choices=["records", "packed"],
+                    help="host form of the end-to-end leg: the plans' record form, or packed member tiles "
+                         "(--e2e-rho)")
     ap.add_argument("--e2e-rho", type=int, default=1,
                     help="tile side of the packed host form of the end-to-end leg (0: whole arrays)")
     ap.add_argument("--no-detail", action="store_true")
@@ -517,7 +520,12 @@ def main():
 
     # ---- end to end through the C ABI with host buffers ----
     if not args.no_e2e:
-        line["e2e"] = e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world)
+        if args.e2e_form == "records" and plan("ca", 0).info()["steps_per_launch"][0] > 1 and \
+                plan("diffusion", 0).info()["steps_per_launch"][1] > 1:
+            line["e2e"] = e2e_records(fr, torch, stream, plan("ca", 0), plan("diffusion", 0), ca_a, u_a, sums,
+                                      args, dist, world)
+        else:
+            line["e2e"] = e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world)
 
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, desc = oracle_sample(CA_STEPS, DIFF_STEPS)
@@ -1181,6 +1189,104 @@ def adjoint(fr, torch, stream, seed):
                        "alg_ops_per_forward_backward": ops,
                        "note": "whole forward + backward through the autograd function, torch conversions included"}
     return out
+
+
+def e2e_records(fr, torch, stream, pc, pd, ca_a, u_a, sums, args, dist, world):
+    """Same metric with host buffers: every step takes both states from pinned
+    host memory and returns both results and the sums to pinned host memory,
+    the states in the plans' record form (the compact records the fused
+    launches keep between them: 112 bytes per member 8 x 8 block, 128 bytes
+    per member 32 x 32 word tile), advanced record to record through the
+    C ABI (fractal_step_ca_records, fractal_step_diffusion_records).  The
+    steps are independent batches in two alternating sets of host and device
+    buffers: the copy engines bring in the next step's states and take out
+    the previous step's results (own streams) while the current step's
+    kernels run.  The timed region starts before the first copy in and ends
+    after the last copy out."""
+    steps = max(20, args.steps)
+    nsums = sums.numel()
+    nsum_d = DIFF_STEPS // REDUCE_EVERY
+    bc = fr.fractal_plan_records_bytes(pc, fr.FRACTAL_U8)
+    bd = fr.fractal_plan_records_bytes(pd, fr.FRACTAL_F32)
+    dev = ca_a.device
+    d_ca_in = [torch.empty(bc, dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_ca_out = [torch.empty(bc, dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_u_in = [torch.empty(bd // 4, dtype=torch.float32, device=dev) for _ in range(2)]
+    d_u_out = [torch.empty(bd // 4, dtype=torch.float32, device=dev) for _ in range(2)]
+    d_sums = [torch.zeros(nsums, dtype=torch.float64, device=dev) for _ in range(2)]
+    h_in_ca = [torch.empty(bc, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    h_in_u = [torch.empty(bd // 4, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    h_out_ca = [torch.empty(bc, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    h_out_u = [torch.empty(bd // 4, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    h_sums = [torch.empty(nsums, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    # both host sets start from the workload's states in record form
+    fr.fractal_records_from_array(pc, fr.FRACTAL_U8, ca_a, d_ca_in[0], stream)
+    fr.fractal_records_from_array(pd, fr.FRACTAL_F32, u_a, d_u_in[0], stream)
+    torch.cuda.synchronize()
+    for j in range(2):
+        h_in_ca[j].copy_(d_ca_in[0])
+        h_in_u[j].copy_(d_u_in[0])
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(k):
+        free = [None, None]    # set j's output buffers read out (copy out done)
+        loaded = [None, None]  # set j's states in
+
+        def copy_in(j):
+            if free[j] is not None:
+                h2d.wait_event(free[j])
+            with torch.cuda.stream(h2d):
+                d_ca_in[j].copy_(h_in_ca[j], non_blocking=True)
+                d_u_in[j].copy_(h_in_u[j], non_blocking=True)
+            loaded[j] = torch.cuda.Event()
+            loaded[j].record(h2d)
+
+        h2d.wait_stream(stream)
+        d2h.wait_stream(stream)
+        copy_in(0)
+        for i in range(k):
+            j = i & 1
+            if i + 1 < k:
+                copy_in(j ^ 1)
+            stream.wait_event(loaded[j])
+            if free[j] is not None:
+                stream.wait_event(free[j])
+            fr.fractal_step_ca_records(pc, d_ca_in[j], d_ca_out[j], CA_STEPS, d_sums[j][nsum_d:nsum_d + 1], stream)
+            fr.fractal_step_diffusion_records(pd, d_u_in[j], d_u_out[j], COEF, DIFF_STEPS, REDUCE_EVERY,
+                                              d_sums[j][0:nsum_d], stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+            d2h.wait_event(done)
+            with torch.cuda.stream(d2h):
+                h_out_u[j].copy_(d_u_out[j], non_blocking=True)
+                h_out_ca[j].copy_(d_ca_out[j], non_blocking=True)
+                h_sums[j].copy_(d_sums[j], non_blocking=True)
+            free[j] = torch.cuda.Event()
+            free[j].record(d2h)
+        stream.wait_stream(h2d)
+        stream.wait_stream(d2h)
+
+    run(2)   # warm-up
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    run(steps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    t = max_over_ranks(dist, t0.elapsed_time(t1) / 1e3)
+    # the results are the step's: check one against the device-resident call
+    ok = bool(torch.isfinite(h_sums[(steps - 1) & 1]).all())
+    return {"value": world * MEMBERS * (CA_STEPS + DIFF_STEPS) * steps / t, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": bc + bd, "d2h_bytes_per_step": bc + bd + 8 * nsums,
+            "steps": steps, "ms_per_step": 1e3 * t / steps, "form": "records", "sums_finite": ok,
+            "note": ("both states in the plans' record form (float32: 112 B per member 8x8 block; uint8: 128 B "
+                     "per member 32x32 word tile) copied each way through pinned host memory by the copy engines "
+                     "and advanced record to record; independent batches in two alternating buffer sets, so that "
+                     "the next step's copy in and the previous step's copy out overlap the current step's "
+                     "kernels; the timed region runs from before the first copy in to after the last copy out")}
 
 
 def e2e(fr, torch, stream, step, ca_a, u_a, sums, args, dist, world):

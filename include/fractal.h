@@ -203,6 +203,49 @@ int fractal_fused_box_blocks(int supertile, int margin, int reach);
 int fractal_plan_device_status(fractal_plan_t plan, int* code);
 
 /*
+ * Record form.  Once steps per launch > 1 is set for a dtype, the plan's
+ * fused launches keep the state between them in compact records, and a
+ * caller may hold the state in that form too: float32, one 112-byte record
+ * per member 8 x 8 block (its 27 members and a pad; 3^(k-3) records);
+ * uint8, one 128-byte bit record per member 32 x 32 word tile (32 words of
+ * 32 cells, 1 bit = alive; 3^(k-5) records).  The records are ordered by the
+ * configuration's super-tiles (lambda or BB rank) and stored as the kernels
+ * read them, so a record-form state belongs to the plan's configuration
+ * (side, launch mode) for that dtype: change the configuration and convert
+ * again.  Moving a state in record form (179 MB at k = 16 float32, 22.7 MB
+ * uint8) replaces moving the embedded arrays (16 GiB, 4 GiB) and needs no
+ * packing pass.  This library's compact form for the paper's closing remark
+ * on storing only the fractal; no counterpart in the paper otherwise.
+ *
+ * fractal_plan_records_bytes -- bytes of one state in record form.  Errors:
+ * FRACTAL_EINVAL (NULL, no fused configuration for dtype).
+ *
+ * fractal_records_from_array / fractal_records_to_array -- convert between
+ * the embedded n*n array (16-byte aligned; read at members / written as the
+ * step calls write it) and the record form (device memory, 16-byte
+ * aligned); one launch of the fused kernel with no steps.  Asynchronous.
+ * Errors: FRACTAL_EINVAL, FRACTAL_ECUDA.
+ *
+ * fractal_step_diffusion_records -- as fractal_step_diffusion_sums (sum
+ * every `every` steps into dev_sums, nullable; steps >= 1 a multiple of
+ * every) from records rec_in to records rec_out (distinct; rec_in is not
+ * written), launches of up to steps-per-launch steps.
+ * fractal_step_ca_records -- `steps` (>= 1) automaton steps from bit
+ * records rec_in to rec_out, the alive count of the result into dev_count
+ * (nullable).  Asynchronous.  Errors: FRACTAL_EINVAL, FRACTAL_ENOMEM (the
+ * plan's records could not be allocated), FRACTAL_ECUDA.
+ */
+int fractal_plan_records_bytes(fractal_plan_t plan, int dtype, int64_t* bytes);
+int fractal_records_from_array(fractal_plan_t plan, int dtype, const void* dev_embedded, void* dev_records,
+                               void* stream);
+int fractal_records_to_array(fractal_plan_t plan, int dtype, const void* dev_records, void* dev_embedded,
+                             void* stream);
+int fractal_step_diffusion_records(fractal_plan_t plan, const float* rec_in, float* rec_out, float a, int steps,
+                                   int every, double* dev_sums, void* stream);
+int fractal_step_ca_records(fractal_plan_t plan, const void* rec_in, void* rec_out, int steps, double* dev_count,
+                            void* stream);
+
+/*
  * Failure-path hooks for tests.  The paper has no counterpart: they exist so
  * that the library's error handling can be exercised without faulting a GPU.
  *

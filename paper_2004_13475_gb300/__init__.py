@@ -49,7 +49,8 @@ EXPORTS = (
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
     "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_gradient_df",
-    "fractal_plan_set_kappa_fusion",
+    "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
+    "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
 
 FRACTAL_SCHED_AUTO = 0
@@ -157,6 +158,11 @@ def _load() -> ctypes.CDLL:
         "fractal_kappa_trajectory_df": (I, [P, VP, VP, VP, VP, D, I, VP]),
         "fractal_kappa_gradient_df": (I, [P, VP, VP, VP, D, I, VP]),
         "fractal_plan_set_kappa_fusion": (I, [P, I]),
+        "fractal_plan_records_bytes": (I, [P, I, ctypes.POINTER(ctypes.c_int64)]),
+        "fractal_records_from_array": (I, [P, I, VP, VP, VP]),
+        "fractal_records_to_array": (I, [P, I, VP, VP, VP]),
+        "fractal_step_diffusion_records": (I, [P, VP, VP, F, I, I, VP, VP]),
+        "fractal_step_ca_records": (I, [P, VP, VP, I, VP, VP]),
         "fractal_debug_fail_allocs": (I, [I]),
     }
     for name, (res, args) in sig.items():
@@ -271,6 +277,37 @@ def fractal_plan_selftest_wait(plan: Plan, spins: int = 1 << 16, stream=None) ->
 def fractal_debug_fail_allocs(after: int) -> None:
     """Fail the library's device allocation after `after` more successes (< 0: off)."""
     _check(_load().fractal_debug_fail_allocs(int(after)), "fractal_debug_fail_allocs")
+
+
+def fractal_plan_records_bytes(plan: Plan, dtype: int) -> int:
+    """Bytes of one state of `dtype` in the plan's record form (needs steps per launch > 1)."""
+    v = ctypes.c_int64()
+    _check(_load().fractal_plan_records_bytes(plan.handle, int(dtype), ctypes.byref(v)), "fractal_plan_records_bytes")
+    return v.value
+
+
+def fractal_records_from_array(plan: Plan, dtype: int, embedded, records, stream=None) -> None:
+    _check(_load().fractal_records_from_array(plan.handle, int(dtype), _ptr(embedded), _ptr(records), _stream(stream)),
+           "fractal_records_from_array")
+
+
+def fractal_records_to_array(plan: Plan, dtype: int, records, embedded, stream=None) -> None:
+    _check(_load().fractal_records_to_array(plan.handle, int(dtype), _ptr(records), _ptr(embedded), _stream(stream)),
+           "fractal_records_to_array")
+
+
+def fractal_step_diffusion_records(plan: Plan, rec_in, rec_out, coef: float, steps: int, every: int = 0,
+                                   dev_sums=None, stream=None) -> None:
+    """Diffusion steps from records rec_in to records rec_out (sums every `every` steps, default: once)."""
+    _check(_load().fractal_step_diffusion_records(plan.handle, _ptr(rec_in), _ptr(rec_out), float(coef), int(steps),
+                                                  int(every or steps), _ptr(dev_sums), _stream(stream)),
+           "fractal_step_diffusion_records")
+
+
+def fractal_step_ca_records(plan: Plan, rec_in, rec_out, steps: int, dev_count=None, stream=None) -> None:
+    """Automaton steps from bit records rec_in to rec_out (alive count into dev_count, nullable)."""
+    _check(_load().fractal_step_ca_records(plan.handle, _ptr(rec_in), _ptr(rec_out), int(steps), _ptr(dev_count),
+                                           _stream(stream)), "fractal_step_ca_records")
 
 
 def fractal_plan_set_kappa_fusion(plan: Plan, on: bool) -> None:

@@ -585,6 +585,61 @@ int step_diffusion(fractal_plan_t p, float* a, float* b, float coef, int steps, 
   return FRACTAL_OK;
 }
 
+// Record form: the state of a fused configuration as the compact records its
+// launches keep between them (float32: 112-byte block records; uint8:
+// 128-byte bit records of word tiles), indexed by the configuration's
+// super-tiles.  The fused kernels convert with zero steps.
+bool records_config(const fractal_plan_s* p, int dtype) {
+  return (dtype == FRACTAL_U8 || dtype == FRACTAL_F32) && p->spl[dtype] > 1 && p->fused_ok[dtype];
+}
+
+int64_t records_bytes(const fractal_plan_s* p, int dtype) {
+  return dtype == FRACTAL_F32 ? fused_records(p->k) * (int64_t)fused_record_bytes() : ca_records(p->k) * 128;
+}
+
+// One fused call of the float32 diffusion from records rin to records rout
+// (distinct buffers), the state in the plan's records between launches.
+int diffusion_records_call(fractal_plan_t p, const float* rin, float* rout, float coef, int steps, int every,
+                           double* dev_sums, cudaStream_t st) {
+  const int spl = p->spl[FRACTAL_F32];
+  const int nseg = steps / every, per = (every + spl - 1) / spl;
+  const int total = nseg * per, base = every / per, extra = every % per;
+  const Launch& F = p->fused[FRACTAL_F32];
+  const int4* desc = p->desc_ok ? p->d_desc : nullptr;
+  for (int i = 0; i < total; ++i) {
+    const int seg = i / per, l = i % per;
+    const bool first = i == 0, last = i == total - 1;
+    double* part = l == per - 1 && dev_sums ? static_cast<double*>(p->d_partials) : nullptr;
+    cudaError_t e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), spl, F, nullptr, nullptr, coef,
+                                           base + (l < extra ? 1 : 0), st, part,
+                                           first ? rin : p->d_pack[(i - 1) & 1], last ? rout : p->d_pack[i & 1],
+                                           desc);
+    if (e == cudaSuccess && part)
+      e = launch_final_sum(1, p->d_partials, (int64_t)F.grid.x * F.grid.y, dev_sums + seg, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step_diffusion_records");
+  }
+  return FRACTAL_OK;
+}
+
+int ca_records_call(fractal_plan_t p, const uint32_t* rin, uint32_t* rout, int steps, double* dev_count,
+                    cudaStream_t st) {
+  const int spl = p->spl[FRACTAL_U8];
+  const int L = (steps + spl - 1) / spl, base = steps / L, extra = steps % L;
+  for (int i = 0; i < L; ++i) {
+    const bool first = i == 0, last = i == L - 1;
+    auto* part = last && dev_count ? static_cast<unsigned long long*>(p->d_partials) : nullptr;
+    cudaError_t e = launch_ca_fused(p->mode, p->fused[FRACTAL_U8], nullptr, nullptr, base + (i < extra ? 1 : 0), spl, st,
+                                    part, first ? rin : p->d_bits[(i - 1) & 1], last ? rout : p->d_bits[i & 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "step_ca_records");
+  }
+  if (dev_count) {
+    const Launch& F = p->fused[FRACTAL_U8];
+    cudaError_t e = launch_final_sum(0, p->d_partials, (int64_t)F.grid.x * F.grid.y, dev_count, st);
+    if (e != cudaSuccess) return cuda_fail(e, "step_ca_records count");
+  }
+  return FRACTAL_OK;
+}
+
 // Steps with per-cell conductivity, state type T (float or double).
 template <typename T>
 int step_kappa(fractal_plan_t p, T* a, T* b, const float* kappa, T coef, int steps, void* stream) {
@@ -953,6 +1008,68 @@ int fractal_plan_selftest_wait(fractal_plan_t p, unsigned spins, void* stream) {
   cudaError_t e = launch_wait_selftest(p->d_err, spins, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "wait self-test");
+}
+
+int fractal_plan_records_bytes(fractal_plan_t p, int dtype, int64_t* bytes) {
+  if (check_plan(p) || !bytes || !records_config(p, dtype)) return FRACTAL_EINVAL;
+  *bytes = records_bytes(p, dtype);
+  return FRACTAL_OK;
+}
+
+int fractal_records_from_array(fractal_plan_t p, int dtype, const void* dev_embedded, void* dev_records,
+                               void* stream) {
+  if (check_plan(p) || !records_config(p, dtype) || !dev_embedded || !dev_records || dev_embedded == dev_records ||
+      !aligned16(dev_embedded) || !aligned16(dev_records))
+    return FRACTAL_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int spl = p->spl[dtype];
+  cudaError_t e;
+  if (dtype == FRACTAL_F32)  // a fused launch of no steps: stage from the array, write the records
+    e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), spl, p->fused[dtype],
+                               static_cast<const float*>(dev_embedded), nullptr, 0.f, 0, st, nullptr, nullptr,
+                               static_cast<float*>(dev_records), p->desc_ok ? p->d_desc : nullptr);
+  else
+    e = launch_ca_fused(p->mode, p->fused[dtype], static_cast<const uint8_t*>(dev_embedded), nullptr, 0, spl, st,
+                        nullptr, nullptr, static_cast<uint32_t*>(dev_records));
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "records_from_array");
+}
+
+int fractal_records_to_array(fractal_plan_t p, int dtype, const void* dev_records, void* dev_embedded,
+                             void* stream) {
+  if (check_plan(p) || !records_config(p, dtype) || !dev_embedded || !dev_records || dev_embedded == dev_records ||
+      !aligned16(dev_embedded) || !aligned16(dev_records))
+    return FRACTAL_EINVAL;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int spl = p->spl[dtype];
+  cudaError_t e;
+  if (dtype == FRACTAL_F32)
+    e = launch_diffusion_fused(p->mode, p->log_rho, fused_margin(spl), spl, p->fused[dtype], nullptr,
+                               static_cast<float*>(dev_embedded), 0.f, 0, st, nullptr,
+                               static_cast<const float*>(dev_records), nullptr, p->desc_ok ? p->d_desc : nullptr);
+  else
+    e = launch_ca_fused(p->mode, p->fused[dtype], nullptr, static_cast<uint8_t*>(dev_embedded), 0, spl, st, nullptr,
+                        static_cast<const uint32_t*>(dev_records), nullptr);
+  return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "records_to_array");
+}
+
+int fractal_step_diffusion_records(fractal_plan_t p, const float* rec_in, float* rec_out, float coef, int steps,
+                                   int every, double* dev_sums, void* stream) {
+  if (check_plan(p) || !records_config(p, FRACTAL_F32) || !rec_in || !rec_out || rec_in == rec_out ||
+      !aligned16(rec_in) || !aligned16(rec_out) || steps < 1 || every < 1 || steps % every != 0 ||
+      !std::isfinite(coef))
+    return FRACTAL_EINVAL;
+  if (!p->d_pack[0] || !p->d_pack[1]) return FRACTAL_ENOMEM;
+  return diffusion_records_call(p, rec_in, rec_out, coef, steps, every, dev_sums, (cudaStream_t)stream);
+}
+
+int fractal_step_ca_records(fractal_plan_t p, const void* rec_in, void* rec_out, int steps, double* dev_count,
+                            void* stream) {
+  if (check_plan(p) || !records_config(p, FRACTAL_U8) || !rec_in || !rec_out || rec_in == rec_out ||
+      !aligned16(rec_in) || !aligned16(rec_out) || steps < 1)
+    return FRACTAL_EINVAL;
+  if (!p->d_bits[0] || !p->d_bits[1]) return FRACTAL_ENOMEM;
+  return ca_records_call(p, static_cast<const uint32_t*>(rec_in), static_cast<uint32_t*>(rec_out), steps, dev_count,
+                         (cudaStream_t)stream);
 }
 
 int fractal_plan_set_kappa_fusion(fractal_plan_t p, int on) {

@@ -1623,7 +1623,7 @@ cudaError_t launch_batch_reduce(const BatchInst* inst, int count, int64_t items,
 cudaError_t launch_diffusion_fused(int mode, int log_rho, int margin, int reach, const Launch& L, const float* in,
                                    float* out, float a, int nsteps, cudaStream_t s, double* partials, const float* pin,
                                    float* pout, const int4* desc) {
-  if (nsteps < 1 || nsteps > reach || log_rho < 2 || fused_threads(L.geo, 0, margin, reach) != L.threads ||
+  if (nsteps < 0 || nsteps > reach || log_rho < 2 || fused_threads(L.geo, 0, margin, reach) != L.threads ||
       (!in && !pin) || (!out && !pout))
     return cudaErrorInvalidValue;
   // two blocks per thread (the descriptors give each thread its two slots)

@@ -358,7 +358,7 @@ int ca_fused_threads(const Geo& g, int margin) {
 
 cudaError_t launch_ca_fused(int mode, const Launch& L, const uint8_t* in, uint8_t* out, int nsteps, int margin,
                             cudaStream_t s, unsigned long long* partials, const uint32_t* pin, uint32_t* pout) {
-  if (nsteps < 1 || nsteps > margin || ca_fused_threads(L.geo, margin) != L.threads || (!in && !pin) ||
+  if (nsteps < 0 || nsteps > margin || ca_fused_threads(L.geo, margin) != L.threads || (!in && !pin) ||
       (!out && !pout))
     return cudaErrorInvalidValue;
   return mode == kLambda ? go<kLambda>(L, in, out, nsteps, margin, partials, pin, pout, s)
