@@ -273,7 +273,7 @@ def main():
     ap.add_argument("--no-bb", action="store_true", help="skip the bounding-box run of the step")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-gasket measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (adjoint) measurement")
-    ap.add_argument("--profile", choices=["ca", "diffusion", "reduce", "sw"],
+    ap.add_argument("--profile", choices=["ca", "diffusion", "reduce", "sw", "sw_u8"],
                     help="run only `--launches` launches of one kernel (for ncu captures)")
     ap.add_argument("--k", type=int, default=15, help="gasket level of a --profile run")
     ap.add_argument("--rho", type=int, default=8, help="tile side of a --profile run")
@@ -836,12 +836,12 @@ def profile_run(args):
         fr.fractal_set_l2_fetch_granularity(args.l2_fetch)
     n = 1 << args.k
     plan = fr.fractal_map(args.k, args.rho, args.mode)
-    dt = fr.FRACTAL_U8 if args.profile == "ca" else fr.FRACTAL_F32
+    dt = fr.FRACTAL_U8 if args.profile in ("ca", "sw_u8") else fr.FRACTAL_F32
     if args.levels >= 0:
         fr.fractal_plan_set_cta_levels(plan, dt, args.levels)
     if args.spl > 1:
         fr.fractal_plan_set_steps_per_launch(plan, dt, args.spl)
-    if args.profile == "ca":
+    if args.profile in ("ca", "sw_u8"):
         a = torch.empty(n * n, dtype=torch.uint8, device="cuda")
         synth.device_fill(a.data_ptr(), synth.SYNTH_BERNOULLI_U8, n, SEED)
     else:
@@ -859,7 +859,7 @@ def profile_run(args):
         elif args.profile == "reduce":
             fr.fractal_reduce_async(plan, a, fr.FRACTAL_F32, out)
         else:
-            fr.fractal_map_write(plan, b, fr.FRACTAL_F32, 1.0)
+            fr.fractal_map_write(plan, b, dt, 1.0)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "k": args.k, "rho": args.rho, "mode": args.mode,
                       "launches": args.launches, "plan": plan.info()}))
