@@ -1187,7 +1187,9 @@ def adjoint(fr, torch, stream, seed):
                        "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (operations, not flops)",
                        "unit": "Tops/s", "frac": ops / t / 1e12 / (FP32_PEAK_TFLOPS / 2),
                        "alg_ops_per_forward_backward": ops,
-                       "note": "whole forward + backward through the autograd function, torch conversions included"}
+                       "note": "whole forward + backward through the autograd function (float32 u0 and dJ/du_T read, u_T and "
+                               "dJ/du0 written as float32 by the first and last launches; dJ/dkappa converted "
+                               "from double-float by torch), timed end to end"}
     return out
 
 

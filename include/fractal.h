@@ -55,6 +55,7 @@ extern "C" {
 /* Element types. */
 #define FRACTAL_U8 0         /* uint8 automaton states (nonzero = alive) */
 #define FRACTAL_F32 1        /* float32 field */
+#define FRACTAL_DF 2         /* double-float field: (hi, lo) float pairs, 2 floats per cell (gradient path) */
 
 #define FRACTAL_MAX_LEVEL 16
 
@@ -584,6 +585,21 @@ int fractal_kappa_fused_limits(int k, int mode, int64_t* record_floats, int* max
 int fractal_plan_set_kappa_fusion(fractal_plan_t plan, int on);
 int fractal_kappa_trajectory_df(fractal_plan_t plan, const float* dev_in, float* dev_out, float* dev_traj,
                                 const float* dev_kappa, double a, int steps, void* stream);
+
+/*
+ * fractal_kappa_trajectory_df_io -- fractal_kappa_trajectory_df with the
+ * formats of its input and result chosen: in_format / out_format
+ * FRACTAL_DF (n*n double-float pairs, as fractal_kappa_trajectory_df) or
+ * FRACTAL_F32 (n*n floats: a float32 input x enters as the pair (x, 0); a
+ * float32 result is hi + lo rounded to float).  The steps run in double-float
+ * either way; this saves the caller the conversions before the first and
+ * after the last launch.  A float32 result has every cell of every member
+ * 8 x 8 block written (0 at non-members), no other cell.  Errors: as
+ * fractal_kappa_trajectory_df, and FRACTAL_EINVAL for another format.
+ */
+int fractal_kappa_trajectory_df_io(fractal_plan_t plan, const void* dev_in, int in_format, void* dev_out,
+                                   int out_format, float* dev_traj, const float* dev_kappa, double a, int steps,
+                                   void* stream);
 int fractal_kappa_gradient_df(fractal_plan_t plan, const float* dev_utraj, const float* dev_ptraj,
                               float* dev_gkappa, double a, int steps, void* stream);
 

@@ -27,6 +27,7 @@ FRACTAL_LAMBDA = 0
 FRACTAL_BB = 1
 FRACTAL_U8 = 0
 FRACTAL_F32 = 1
+FRACTAL_DF = 2  # double-float (hi, lo) pairs (gradient path)
 FRACTAL_MAX_LEVEL = 16
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfractal.so")
@@ -48,7 +49,8 @@ EXPORTS = (
     "fractal_pack", "fractal_unpack",
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
-    "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_gradient_df",
+    "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_trajectory_df_io",
+    "fractal_kappa_gradient_df",
     "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
     "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
@@ -156,6 +158,7 @@ def _load() -> ctypes.CDLL:
         "fractal_plan_selftest_wait": (I, [P, ctypes.c_uint, VP]),
         "fractal_kappa_fused_limits": (I, [I, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I)]),
         "fractal_kappa_trajectory_df": (I, [P, VP, VP, VP, VP, D, I, VP]),
+        "fractal_kappa_trajectory_df_io": (I, [P, VP, I, VP, I, VP, VP, D, I, VP]),
         "fractal_kappa_gradient_df": (I, [P, VP, VP, VP, D, I, VP]),
         "fractal_plan_set_kappa_fusion": (I, [P, I]),
         "fractal_plan_records_bytes": (I, [P, I, ctypes.POINTER(ctypes.c_int64)]),
@@ -333,6 +336,15 @@ def fractal_kappa_trajectory_df(plan: Plan, dev_in, dev_out, dev_traj, dev_kappa
     _check(_load().fractal_kappa_trajectory_df(plan.handle, _ptr(dev_in), _ptr(dev_out), _ptr(dev_traj),
                                                _ptr(dev_kappa), float(coef), int(steps), _stream(stream)),
            "fractal_kappa_trajectory_df")
+
+
+def fractal_kappa_trajectory_df_io(plan: Plan, dev_in, in_format: int, dev_out, out_format: int, dev_traj,
+                                   dev_kappa, coef: float, steps: int, stream=None) -> None:
+    """fractal_kappa_trajectory_df with the input and result formats chosen
+    (FRACTAL_DF pairs or FRACTAL_F32 floats)."""
+    _check(_load().fractal_kappa_trajectory_df_io(plan.handle, _ptr(dev_in), int(in_format), _ptr(dev_out),
+                                                  int(out_format), _ptr(dev_traj), _ptr(dev_kappa), float(coef),
+                                                  int(steps), _stream(stream)), "fractal_kappa_trajectory_df_io")
 
 
 def fractal_kappa_gradient_df(plan: Plan, dev_utraj, dev_ptraj, dev_gkappa, coef: float, steps: int,

@@ -24,9 +24,9 @@ from __future__ import annotations
 
 import torch
 
-from . import (FRACTAL_F32, FRACTAL_LAMBDA, FractalError, fractal_adjoint_diffusion_step,
+from . import (FRACTAL_DF, FRACTAL_F32, FRACTAL_LAMBDA, FractalError, fractal_adjoint_diffusion_step,
                fractal_adjoint_diffusion_step_df, fractal_adjoint_diffusion_step_f64, fractal_kappa_fused_limits,
-               fractal_kappa_gradient_df, fractal_kappa_trajectory_df, fractal_map, fractal_map_write,
+               fractal_kappa_gradient_df, fractal_kappa_trajectory_df_io, fractal_map, fractal_map_write,
                fractal_plan_set_kappa_fusion,
                fractal_step_diffusion_kappa, fractal_step_diffusion_kappa_df, fractal_step_diffusion_kappa_f64)
 
@@ -70,19 +70,23 @@ def _fused_limits(k, mode):
         return None
 
 
-def _run_recorded(plan, src, dst, traj, rec_floats, kappa, a, steps, max_steps, temps):
+def _run_recorded(plan, src, dst, traj, rec_floats, kappa, a, steps, max_steps, temps, src_fmt=None, dst_fmt=None):
     """`steps` (>= 1) fused double-float steps from src: the state before each
     step into traj states 0 .. steps - 1 (traj may be None) and the result
     into dst (or, with dst None, into traj state `steps`), in launches of at
     most max_steps steps
-    (temps: two spare state buffers for the chunks between launches)."""
-    cur, s0, i = src, 0, 0
+    (temps: two spare double-float buffers for the chunks between launches).
+    src_fmt / dst_fmt: FRACTAL_DF (default) or FRACTAL_F32 for src and dst."""
+    src_fmt = FRACTAL_DF if src_fmt is None else src_fmt
+    dst_fmt = FRACTAL_DF if dst_fmt is None else dst_fmt
+    cur, fmt, s0, i = src, src_fmt, 0, 0
     while s0 < steps:
         n = min(max_steps, steps - s0)
         last = s0 + n == steps
-        out = dst if last else temps[i & 1]
-        fractal_kappa_trajectory_df(plan, cur, out, None if traj is None else traj[s0 * rec_floats:], kappa, a, n)
-        cur, s0, i = out, s0 + n, i + 1
+        out, ofmt = (dst, dst_fmt) if last else (temps[i & 1], FRACTAL_DF)
+        fractal_kappa_trajectory_df_io(plan, cur, fmt, out, ofmt, None if traj is None else traj[s0 * rec_floats:],
+                                       kappa, a, n)
+        cur, fmt, s0, i = out, FRACTAL_DF, s0 + n, i + 1
 
 
 def _member_mask(plan, like):
@@ -111,26 +115,37 @@ class GasketDiffusion(torch.autograd.Function):
         step = _STATES[state][0]
         plan = fractal_map(k, 8 if k >= 3 else 1 << k, mode)
         fractal_plan_set_kappa_fusion(plan, fused)
-        mask = _member_mask(plan, u0)
         kappa = kappa.detach().to(torch.float32).contiguous()
         lim = _fused_limits(k, mode) if state == "df" and fused else None
         ckpts = []
         t = 0
+        ctx.f32_io = lim is not None and u0.dtype == torch.float32
         if lim is not None:
             # fused: each segment from its checkpoint into a new buffer (the
             # kernels read member cells only and write every cell of every
             # member block; the last buffer starts zeroed, so u_T is 0 at
-            # every non-member cell)
-            u = _to_state(u0.detach(), state)
-            temps = [torch.empty_like(u) for _ in range(2)] if min(every, steps) > lim[1] else [None, None]
+            # every non-member cell).  A float32 u0 is read as it is and u_T
+            # written as float32 by the kernels (no conversions around them).
+            mask = None
+            f32 = ctx.f32_io
+            u, ufmt = (u0.detach().contiguous(), FRACTAL_F32) if f32 else (_to_state(u0.detach(), state), FRACTAL_DF)
+            df_cells = 2 * u0.numel()
+            temps = ([torch.empty(df_cells, dtype=torch.float32, device=u0.device) for _ in range(2)]
+                     if min(every, steps) > lim[1] else [None, None])
             while t < steps:
                 ns = min(every, steps - t)
-                v = torch.zeros_like(u) if t + ns >= steps else torch.empty_like(u)
-                _run_recorded(plan, u, v, None, 0, kappa, a, ns, lim[1], temps)
+                final = t + ns >= steps
+                if final and f32:
+                    v, vfmt = torch.zeros(u0.numel(), dtype=torch.float32, device=u0.device), FRACTAL_F32
+                else:
+                    v = (torch.zeros if final else torch.empty)(df_cells, dtype=torch.float32, device=u0.device)
+                    vfmt = FRACTAL_DF
+                _run_recorded(plan, u, v, None, 0, kappa, a, ns, lim[1], temps, ufmt, vfmt)
                 ckpts.append(u)
-                u = v
+                u, ufmt = v, vfmt
                 t += ns
         else:
+            mask = _member_mask(plan, u0)
             # every buffer holds 0 at all non-member cells, so u_T does too
             u = _to_state(u0.detach() * mask.to(u0.dtype), state)
             v = torch.zeros_like(u)
@@ -141,51 +156,68 @@ class GasketDiffusion(torch.autograd.Function):
                 if out is v:
                     u, v = v, u
                 t += ns
-        ctx.save_for_backward(kappa, mask, *ckpts)
+        ctx.save_for_backward(kappa, *ckpts)
+        ctx.mask = mask
         ctx.plan, ctx.a, ctx.steps, ctx.every, ctx.state = plan, a, steps, every, state
         ctx.fused = fused
         ctx.dtypes = (u0.dtype, kappa.dtype)
-        return _from_state(u, state, u0.dtype)
+        return u if ctx.f32_io else _from_state(u, state, u0.dtype)
 
     @staticmethod
     def backward(ctx, grad_out):
-        kappa, mask, *ckpts = ctx.saved_tensors
+        kappa, *ckpts = ctx.saved_tensors
         plan, a, steps, every, state = ctx.plan, ctx.a, ctx.steps, ctx.every, ctx.state
         step, reverse = _STATES[state][0], _STATES[state][1]
-        # u_T is 0 at non-members whatever u0 is: only member cells carry gradient
-        p = _to_state(grad_out.detach() * mask.to(grad_out.dtype), state)
-        q = torch.zeros_like(p)
+        du, dk = ctx.dtypes
         # dJ/dkappa: double-float pairs for the "df" state, else float64
         gk = (torch.zeros(2 * kappa.numel(), dtype=torch.float32, device=kappa.device) if state == "df"
               else torch.zeros(kappa.shape, dtype=torch.float64, device=kappa.device))
-        # the recomputed states of a segment, one pool for all segments: a
-        # step writes every member tile of its output and the kernels read
-        # member cells only, so the pool is neither cleared nor reallocated
         lim = _fused_limits(plan.info()["k"], plan.info()["mode"]) if state == "df" and ctx.fused else None
         if lim is not None:
             # fused: per segment, u recorded forward from its checkpoint and p
             # carried back (the reverse step is A applied to p) in launches of
-            # several steps, then dJ/dkappa of the segment from both records
+            # several steps, then dJ/dkappa of the segment from both records.
+            # The kernels read member cells only, so a float32 dJ/du_T enters
+            # as it is; dJ/du0 leaves as float32 into a zeroed buffer (0 at
+            # non-members) when u0 was float32.
             rf, ms = lim
+            cells = kappa.numel()
+            dev = kappa.device
+            if grad_out.dtype == torch.float32:
+                p, pfmt = grad_out.detach().contiguous(), FRACTAL_F32
+            else:
+                p, pfmt = _to_state(grad_out.detach() * _member_mask(plan, grad_out).to(grad_out.dtype), state), \
+                    FRACTAL_DF
             seg_max = min(every, steps)
-            utraj = torch.empty(rf * (seg_max + 1), dtype=torch.float32, device=p.device)
-            ptraj = torch.empty(rf * seg_max, dtype=torch.float32, device=p.device)
-            temps = [torch.empty_like(p) for _ in range(2)] if seg_max > ms else [None, None]
-            for seg in range(len(ckpts) - 1, -1, -1):
+            utraj = torch.empty(rf * (seg_max + 1), dtype=torch.float32, device=dev)
+            ptraj = torch.empty(rf * seg_max, dtype=torch.float32, device=dev)
+            df = lambda: torch.empty(2 * cells, dtype=torch.float32, device=dev)  # noqa: E731
+            temps = [df(), df()] if seg_max > ms else [None, None]
+            carry = [df(), df()] if len(ckpts) > 1 else []
+            for i, seg in enumerate(range(len(ckpts) - 1, -1, -1)):
                 t0 = seg * every
                 ns = min(every, steps - t0)
+                cfmt = FRACTAL_F32 if seg == 0 and ctx.f32_io else FRACTAL_DF
                 # u_(t0) .. u_(t0 + ns - 1) (at least one step, so that the
                 # segment's first state is recorded as well)
-                un = max(ns - 1, 1)
-                if un <= ms:
-                    fractal_kappa_trajectory_df(plan, ckpts[seg], None, utraj, kappa, a, un)
+                _run_recorded(plan, ckpts[seg], None, utraj, rf, kappa, a, max(ns - 1, 1), ms, temps, cfmt)
+                if seg > 0:
+                    out, ofmt = carry[i & 1], FRACTAL_DF
+                elif du == torch.float32:
+                    out, ofmt = torch.zeros(cells, dtype=torch.float32, device=dev), FRACTAL_F32
                 else:
-                    _run_recorded(plan, ckpts[seg], None, utraj, rf, kappa, a, un, ms, temps)
-                _run_recorded(plan, p, q, ptraj, rf, kappa, a, ns, ms, temps)
+                    out, ofmt = torch.zeros(2 * cells, dtype=torch.float32, device=dev), FRACTAL_DF
+                _run_recorded(plan, p, out, ptraj, rf, kappa, a, ns, ms, temps, pfmt, ofmt)
                 fractal_kappa_gradient_df(plan, utraj, ptraj, gk, a, ns)
-                p, q = q, p
-            du, dk = ctx.dtypes
-            return (_from_state(p, state, du), _from_state(gk, "df", dk), None, None, None, None, None, None, None)
+                p, pfmt = out, ofmt
+            return (p if pfmt == FRACTAL_F32 else _from_state(p, state, du), _from_state(gk, "df", dk),
+                    None, None, None, None, None, None, None)
+        # u_T is 0 at non-members whatever u0 is: only member cells carry gradient
+        p = _to_state(grad_out.detach() * ctx.mask.to(grad_out.dtype), state)
+        q = torch.zeros_like(p)
+        # the recomputed states of a segment, one pool for all segments: a
+        # step writes every member tile of its output and the kernels read
+        # member cells only, so the pool is neither cleared nor reallocated
         pool = [torch.empty_like(p) for _ in range(min(every, steps) - 1)]
         for seg in range(len(ckpts) - 1, -1, -1):
             t0 = seg * every

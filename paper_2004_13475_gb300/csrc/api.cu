@@ -1088,9 +1088,12 @@ int fractal_kappa_fused_limits(int k, int mode, int64_t* record_floats, int* max
   return FRACTAL_OK;
 }
 
-int fractal_kappa_trajectory_df(fractal_plan_t p, const float* dev_in, float* dev_out, float* dev_traj,
-                                const float* dev_kappa, double coef, int steps, void* stream) {
+int fractal_kappa_trajectory_df_io(fractal_plan_t p, const void* dev_in, int in_format, void* dev_out,
+                                   int out_format, float* dev_traj, const float* dev_kappa, double coef, int steps,
+                                   void* stream) {
   if (check_plan(p) || !dev_in || !dev_kappa || (!dev_out && !dev_traj) || !std::isfinite(coef)) return FRACTAL_EINVAL;
+  if ((in_format != FRACTAL_F32 && in_format != FRACTAL_DF) || (out_format != FRACTAL_F32 && out_format != FRACTAL_DF))
+    return FRACTAL_EINVAL;
   const void* all[4] = {dev_in, dev_out, dev_traj, dev_kappa};
   for (int i = 0; i < 4; ++i) {
     if (all[i] && !aligned16(all[i])) return FRACTAL_EINVAL;
@@ -1100,10 +1103,19 @@ int fractal_kappa_trajectory_df(fractal_plan_t p, const float* dev_in, float* de
   Launch L;
   int margin = 0;
   if (!kappa_fused_geometry(p->k, p->mode, L, margin) || steps < 1 || steps > margin) return FRACTAL_EINVAL;
-  cudaError_t e = launch_kappa_fused_df(p->mode, p->k, reinterpret_cast<const dfloat*>(dev_in),
-                                        reinterpret_cast<dfloat*>(dev_out), reinterpret_cast<float4*>(dev_traj),
-                                        dev_kappa, dfloat_from_double(0.5 * coef), steps, (cudaStream_t)stream);
+  const bool fin = in_format == FRACTAL_F32, fout = out_format == FRACTAL_F32;
+  cudaError_t e = launch_kappa_fused_df(
+      p->mode, p->k, fin ? nullptr : static_cast<const dfloat*>(dev_in),
+      fout ? nullptr : static_cast<dfloat*>(dev_out), reinterpret_cast<float4*>(dev_traj), dev_kappa,
+      dfloat_from_double(0.5 * coef), steps, (cudaStream_t)stream, fin ? static_cast<const float*>(dev_in) : nullptr,
+      fout ? static_cast<float*>(dev_out) : nullptr);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "kappa_trajectory_df");
+}
+
+int fractal_kappa_trajectory_df(fractal_plan_t p, const float* dev_in, float* dev_out, float* dev_traj,
+                                const float* dev_kappa, double coef, int steps, void* stream) {
+  return fractal_kappa_trajectory_df_io(p, dev_in, FRACTAL_DF, dev_out, FRACTAL_DF, dev_traj, dev_kappa, coef, steps,
+                                        stream);
 }
 
 int fractal_kappa_gradient_df(fractal_plan_t p, const float* dev_utraj, const float* dev_ptraj, float* dev_gkappa,

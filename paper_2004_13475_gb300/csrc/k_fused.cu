@@ -1093,7 +1093,9 @@ __global__ void __launch_bounds__(kKapThreads, 3) kappa_fused_df_kernel(const df
                                                                          dfloat* __restrict__ out,
                                                                          float4* __restrict__ traj, int64_t stride,
                                                                          const float* __restrict__ kappa, dfloat ha,
-                                                                         int nsteps, int M, int reach, Geo g) {
+                                                                         int nsteps, int M, int reach, Geo g,
+                                                                         const float* __restrict__ in_f32,
+                                                                         float* __restrict__ out_f32) {
   __shared__ __align__(16) float2 kports[6 * (kKapThreads + 1)];
   __shared__ int tab[81];  // BB: member block slots of the super-tile (side <= 128)
   int sx, sy;
@@ -1119,7 +1121,14 @@ __global__ void __launch_bounds__(kKapThreads, 3) kappa_fused_df_kernel(const df
   for (int q = 0; q < kB * kB; ++q) c[q] = dfloat(0.f, 0.f);
   if (su.active) {
     base = (size_t)(OY + su.by) * kB * (size_t)f.n + (size_t)(OX + su.bx) * kB;
-    load_block(u, in + base, f.n);
+    if (in_f32) {  // a float32 state: each member x as the pair (x, 0)
+      float x[kB * kB];
+      load_block(x, in_f32 + base, f.n);
+#pragma unroll
+      for (int q = 0; q < kB * kB; ++q) u[q] = dfloat(x[q], 0.f);
+    } else {
+      load_block(u, in + base, f.n);
+    }
     float kk[kB * kB];
     load_block(kk, kappa + base, f.n);
 #pragma unroll
@@ -1156,8 +1165,15 @@ __global__ void __launch_bounds__(kKapThreads, 3) kappa_fused_df_kernel(const df
     __syncthreads();
   }
   if (!own) return;
-  if (rec && !out) krec_write(rec + (int64_t)nsteps * stride, f.nb, u);
-  if (out) store_block(out + base, f.n, u);
+  if (rec && !out && !out_f32) krec_write(rec + (int64_t)nsteps * stride, f.nb, u);
+  if (out_f32) {  // float32: hi + lo rounded once
+    float w[kB * kB];
+#pragma unroll
+    for (int q = 0; q < kB * kB; ++q) w[q] = u[q].hi + u[q].lo;
+    store_block(out_f32 + base, f.n, w);
+  } else if (out) {
+    store_block(out + base, f.n, u);
+  }
 }
 
 // dJ/dkappa over a segment of nsteps steps from the recorded trajectories:
@@ -1684,7 +1700,7 @@ bool kappa_fused_geometry(int k, int mode, Launch& L, int& margin) {
 int64_t kappa_record_float4s(int k) { return fused_records(k) * kKRecF4; }
 
 cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out, float4* traj, const float* kappa,
-                                  dfloat ha, int nsteps, cudaStream_t s) {
+                                  dfloat ha, int nsteps, cudaStream_t s, const float* in_f32, float* out_f32) {
   Launch L;
   int margin = 0;
   if (!kappa_fused_geometry(k, mode, L, margin) || nsteps < 1 || nsteps > margin) return cudaErrorInvalidValue;
@@ -1692,10 +1708,10 @@ cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out
   const int64_t stride = kappa_record_float4s(k);
   if (mode == kLambda)
     kappa_fused_df_kernel<kLambda><<<L.grid, threads, 0, s>>>(in, out, traj, stride, kappa, ha, nsteps, margin, nsteps,
-                                                              L.geo);
+                                                              L.geo, in_f32, out_f32);
   else
     kappa_fused_df_kernel<kBB><<<L.grid, threads, 0, s>>>(in, out, traj, stride, kappa, ha, nsteps, margin, nsteps,
-                                                          L.geo);
+                                                          L.geo, in_f32, out_f32);
   return cudaGetLastError();
 }
 

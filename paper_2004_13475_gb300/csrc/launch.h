@@ -86,11 +86,14 @@ int fused_warp_slots();
 // side min(128, n), margins min(32, side / 2), k >= 4): `nsteps` <= margin
 // steps in -> out (out may be null) recording the state before each step
 // (and after the last when out is null) into traj (may be null); and the
-// kappa gradient of a segment from two recorded trajectories.
+// kappa gradient of a segment from two recorded trajectories.  in_f32 (when
+// not null) replaces in: a float32 state read as (x, 0) pairs; out_f32 (when
+// not null) replaces out: hi + lo written as float32.
 bool kappa_fused_geometry(int k, int mode, Launch& L, int& margin);
 int64_t kappa_record_float4s(int k);
 cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out, float4* traj, const float* kappa,
-                                  dfloat ha, int nsteps, cudaStream_t s);
+                                  dfloat ha, int nsteps, cudaStream_t s, const float* in_f32 = nullptr,
+                                  float* out_f32 = nullptr);
 cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const float4* ptraj, dfloat* gk, dfloat ha,
                                  int nsteps, cudaStream_t s);
 

@@ -281,3 +281,63 @@ def test_fused_and_single_step_gradients_agree(fr, k, steps, every):
         assert rel_err(gk, dom.put(wk, np.float64), dom.mask)[0] <= 1e-4
     assert rel_err(res[0][0], res[1][0].astype(np.float64), dom.mask)[0] <= 1e-6
     assert rel_err(res[0][1], res[1][1].astype(np.float64), dom.mask)[0] <= 1e-6
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k,steps", [(5, 13), (9, 20)])
+def test_fused_trajectory_float32_formats(fr, k, steps, mode):
+    """A float32 input enters as the pairs (x, 0) and a float32 result is
+    hi + lo rounded to float: the float32 forms of the fused launch give, bit
+    for bit, the double-float launch on the converted input (records
+    included) and the float sum of its result; a float32 result writes every
+    cell of every member block and nothing else."""
+    n = 1 << k
+    u0, kappa, _ = fields(k, 70 + k)
+    plan = fr.fractal_map(k, 8, mode)
+    rf, _ = fr.fractal_kappa_fused_limits(k, mode)
+    kap = dev(kappa)
+    x32 = dev(u0)
+    out_df = torch.zeros(2 * n * n, device="cuda")
+    tr_df = torch.zeros(rf * (steps + 1), device="cuda")
+    fr.fractal_kappa_trajectory_df(plan, _df(u0), out_df, tr_df, kap, A, steps)
+    out_a = torch.zeros_like(out_df)
+    tr_a = torch.zeros_like(tr_df)
+    fr.fractal_kappa_trajectory_df_io(plan, x32, fr.FRACTAL_F32, out_a, fr.FRACTAL_DF, tr_a, kap, A, steps)
+    assert torch.equal(out_a, out_df) and torch.equal(tr_a, tr_df)
+    out_b = torch.full((n * n,), -7.0, device="cuda")
+    fr.fractal_kappa_trajectory_df_io(plan, x32, fr.FRACTAL_F32, out_b, fr.FRACTAL_F32, None, kap, A, steps)
+    hl = out_df.view(-1, 2)
+    cover = torch.from_numpy(block_cover(n).reshape(-1)).cuda()
+    assert torch.equal(out_b[cover], (hl[:, 0] + hl[:, 1])[cover])
+    assert bool((out_b[~cover] == -7.0).all())
+    out_c = torch.zeros(n * n, device="cuda")
+    fr.fractal_kappa_trajectory_df_io(plan, _df(u0), fr.FRACTAL_DF, out_c, fr.FRACTAL_F32, None, kap, A, steps)
+    assert torch.equal(out_c[cover], out_b[cover])
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_trajectory_df_io(plan, x32, 0, out_c, fr.FRACTAL_F32, None, kap, A, steps)  # uint8 format
+
+
+@pytest.mark.parametrize("k,steps,every", [(8, 45, 20), (7, 70, 40)])
+def test_fused_gradients_float32_and_float64_inputs_agree(fr, k, steps, every):
+    """The fused path with float32 u0 and dJ/du_T read and written by the
+    kernels as float32 gives the same u_T and gradients, bit for bit after
+    rounding to float32, as the same path with float64 inputs (converted to
+    double-float pairs around the kernels): the conversions moved into the
+    kernels change no value."""
+    n = 1 << k
+    u0, kappa, target = fields(k, 110 + k)
+    from paper_2004_13475_gb300.autograd import diffusion_kappa
+    res = []
+    g = None
+    for dt in (torch.float32, torch.float64):
+        u = dev(u0).to(dt).requires_grad_(True)
+        kp = dev(kappa).requires_grad_(True)
+        uT = diffusion_kappa(u, kp, k, A, steps, every)
+        if g is None:  # one float32 dJ/du_T for both runs
+            g = dev(target) - uT.detach()
+        uT.backward(g.to(dt))
+        res.append((uT.detach().float(), u.grad.float(), kp.grad.float()))
+    for x32, x64 in zip(res[0], res[1]):
+        assert torch.equal(x32, x64)
+    mask = torch.from_numpy(oracle.member_mask(n).reshape(-1)).cuda()
+    assert bool((res[0][0][~mask] == 0).all()) and bool((res[0][1][~mask] == 0).all())
