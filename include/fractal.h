@@ -603,6 +603,23 @@ int fractal_kappa_trajectory_df_io(fractal_plan_t plan, const void* dev_in, int 
 int fractal_kappa_gradient_df(fractal_plan_t plan, const float* dev_utraj, const float* dev_ptraj,
                               float* dev_gkappa, double a, int steps, void* stream);
 
+/*
+ * fractal_kappa_gradient_df_io -- fractal_kappa_gradient_df with the sum's
+ * start and destination chosen: accumulate != 0 adds to dev_gkappa (as
+ * fractal_kappa_gradient_df), accumulate == 0 starts from 0 (dev_gkappa is
+ * then not read, so it need not be cleared); the result goes to dev_gkappa
+ * (double-float), or, when dev_out_f32 is not NULL, to dev_out_f32 as float32
+ * (n*n floats, hi + lo rounded once; dev_gkappa is then not written and may
+ * be NULL without accumulate).  Either destination has every cell of every
+ * member 8 x 8 block written (0 at non-members), no other cell.  With these a
+ * segment loop needs no cleared accumulator and no final conversion.
+ * Errors: as fractal_kappa_gradient_df, and FRACTAL_EINVAL for dev_gkappa
+ * NULL where it is read or written, or aliasing buffers.
+ */
+int fractal_kappa_gradient_df_io(fractal_plan_t plan, const float* dev_utraj, const float* dev_ptraj,
+                                 float* dev_gkappa, int accumulate, float* dev_out_f32, double a, int steps,
+                                 void* stream);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.
  *

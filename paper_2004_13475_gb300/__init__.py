@@ -50,7 +50,7 @@ EXPORTS = (
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
     "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_trajectory_df_io",
-    "fractal_kappa_gradient_df",
+    "fractal_kappa_gradient_df", "fractal_kappa_gradient_df_io",
     "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
     "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
@@ -160,6 +160,7 @@ def _load() -> ctypes.CDLL:
         "fractal_kappa_trajectory_df": (I, [P, VP, VP, VP, VP, D, I, VP]),
         "fractal_kappa_trajectory_df_io": (I, [P, VP, I, VP, I, VP, VP, D, I, VP]),
         "fractal_kappa_gradient_df": (I, [P, VP, VP, VP, D, I, VP]),
+        "fractal_kappa_gradient_df_io": (I, [P, VP, VP, VP, I, VP, D, I, VP]),
         "fractal_plan_set_kappa_fusion": (I, [P, I]),
         "fractal_plan_records_bytes": (I, [P, I, ctypes.POINTER(ctypes.c_int64)]),
         "fractal_records_from_array": (I, [P, I, VP, VP, VP]),
@@ -352,6 +353,15 @@ def fractal_kappa_gradient_df(plan: Plan, dev_utraj, dev_ptraj, dev_gkappa, coef
     """dJ/dkappa of a segment of `steps` steps from the recorded u and p trajectories (double-float)."""
     _check(_load().fractal_kappa_gradient_df(plan.handle, _ptr(dev_utraj), _ptr(dev_ptraj), _ptr(dev_gkappa),
                                              float(coef), int(steps), _stream(stream)), "fractal_kappa_gradient_df")
+
+
+def fractal_kappa_gradient_df_io(plan: Plan, dev_utraj, dev_ptraj, dev_gkappa, accumulate: bool, dev_out_f32,
+                                 coef: float, steps: int, stream=None) -> None:
+    """dJ/dkappa of a segment added to dev_gkappa (accumulate) or from 0, into
+    dev_gkappa (double-float) or, when given, dev_out_f32 (float32)."""
+    _check(_load().fractal_kappa_gradient_df_io(plan.handle, _ptr(dev_utraj), _ptr(dev_ptraj), _ptr(dev_gkappa),
+                                                1 if accumulate else 0, _ptr(dev_out_f32), float(coef), int(steps),
+                                                _stream(stream)), "fractal_kappa_gradient_df_io")
 
 
 def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:

@@ -26,7 +26,7 @@ import torch
 
 from . import (FRACTAL_DF, FRACTAL_F32, FRACTAL_LAMBDA, FractalError, fractal_adjoint_diffusion_step,
                fractal_adjoint_diffusion_step_df, fractal_adjoint_diffusion_step_f64, fractal_kappa_fused_limits,
-               fractal_kappa_gradient_df, fractal_kappa_trajectory_df_io, fractal_map, fractal_map_write,
+               fractal_kappa_gradient_df_io, fractal_kappa_trajectory_df_io, fractal_map, fractal_map_write,
                fractal_plan_set_kappa_fusion,
                fractal_step_diffusion_kappa, fractal_step_diffusion_kappa_df, fractal_step_diffusion_kappa_f64)
 
@@ -169,9 +169,6 @@ class GasketDiffusion(torch.autograd.Function):
         plan, a, steps, every, state = ctx.plan, ctx.a, ctx.steps, ctx.every, ctx.state
         step, reverse = _STATES[state][0], _STATES[state][1]
         du, dk = ctx.dtypes
-        # dJ/dkappa: double-float pairs for the "df" state, else float64
-        gk = (torch.zeros(2 * kappa.numel(), dtype=torch.float32, device=kappa.device) if state == "df"
-              else torch.zeros(kappa.shape, dtype=torch.float64, device=kappa.device))
         lim = _fused_limits(plan.info()["k"], plan.info()["mode"]) if state == "df" and ctx.fused else None
         if lim is not None:
             # fused: per segment, u recorded forward from its checkpoint and p
@@ -194,6 +191,13 @@ class GasketDiffusion(torch.autograd.Function):
             df = lambda: torch.empty(2 * cells, dtype=torch.float32, device=dev)  # noqa: E731
             temps = [df(), df()] if seg_max > ms else [None, None]
             carry = [df(), df()] if len(ckpts) > 1 else []
+            # dJ/dkappa: the first gradient pass starts the double-float sum
+            # (no cleared buffer), the last writes it as float32 for a float32
+            # kappa; a float64 kappa takes the sum from a zeroed buffer
+            f32k = dk == torch.float32
+            gk = ((df() if len(ckpts) > 1 else None) if f32k
+                  else torch.zeros(2 * cells, dtype=torch.float32, device=dev))
+            gk_out = torch.zeros(cells, dtype=torch.float32, device=dev) if f32k else None
             for i, seg in enumerate(range(len(ckpts) - 1, -1, -1)):
                 t0 = seg * every
                 ns = min(every, steps - t0)
@@ -208,10 +212,13 @@ class GasketDiffusion(torch.autograd.Function):
                 else:
                     out, ofmt = torch.zeros(2 * cells, dtype=torch.float32, device=dev), FRACTAL_DF
                 _run_recorded(plan, p, out, ptraj, rf, kappa, a, ns, ms, temps, pfmt, ofmt)
-                fractal_kappa_gradient_df(plan, utraj, ptraj, gk, a, ns)
+                fractal_kappa_gradient_df_io(plan, utraj, ptraj, gk, i > 0, gk_out if seg == 0 else None, a, ns)
                 p, pfmt = out, ofmt
-            return (p if pfmt == FRACTAL_F32 else _from_state(p, state, du), _from_state(gk, "df", dk),
-                    None, None, None, None, None, None, None)
+            return (p if pfmt == FRACTAL_F32 else _from_state(p, state, du),
+                    gk_out if f32k else _from_state(gk, "df", dk), None, None, None, None, None, None, None)
+        # dJ/dkappa: double-float pairs for the "df" state, else float64
+        gk = (torch.zeros(2 * kappa.numel(), dtype=torch.float32, device=kappa.device) if state == "df"
+              else torch.zeros(kappa.shape, dtype=torch.float64, device=kappa.device))
         # u_T is 0 at non-members whatever u0 is: only member cells carry gradient
         p = _to_state(grad_out.detach() * ctx.mask.to(grad_out.dtype), state)
         q = torch.zeros_like(p)

@@ -1118,23 +1118,30 @@ int fractal_kappa_trajectory_df(fractal_plan_t p, const float* dev_in, float* de
                                         stream);
 }
 
-int fractal_kappa_gradient_df(fractal_plan_t p, const float* dev_utraj, const float* dev_ptraj, float* dev_gkappa,
-                              double coef, int steps, void* stream) {
-  if (check_plan(p) || !dev_utraj || !dev_ptraj || !dev_gkappa || !std::isfinite(coef) || steps < 1)
-    return FRACTAL_EINVAL;
-  const void* all[3] = {dev_utraj, dev_ptraj, dev_gkappa};
-  for (int i = 0; i < 3; ++i) {
-    if (!aligned16(all[i])) return FRACTAL_EINVAL;
+int fractal_kappa_gradient_df_io(fractal_plan_t p, const float* dev_utraj, const float* dev_ptraj, float* dev_gkappa,
+                                 int accumulate, float* dev_out_f32, double coef, int steps, void* stream) {
+  if (check_plan(p) || !dev_utraj || !dev_ptraj || !std::isfinite(coef) || steps < 1) return FRACTAL_EINVAL;
+  if (!dev_gkappa && (accumulate || !dev_out_f32)) return FRACTAL_EINVAL;
+  const void* all[4] = {dev_utraj, dev_ptraj, dev_gkappa, dev_out_f32};
+  for (int i = 0; i < 4; ++i) {
+    if (all[i] && !aligned16(all[i])) return FRACTAL_EINVAL;
     for (int j = 0; j < i; ++j)
-      if (all[i] == all[j]) return FRACTAL_EINVAL;
+      if (all[i] && all[i] == all[j]) return FRACTAL_EINVAL;
   }
   Launch L;
   int margin = 0;
   if (!kappa_fused_geometry(p->k, p->mode, L, margin)) return FRACTAL_EINVAL;
   cudaError_t e = launch_kappa_grad_df(p->mode, p->k, reinterpret_cast<const float4*>(dev_utraj),
                                        reinterpret_cast<const float4*>(dev_ptraj), reinterpret_cast<dfloat*>(dev_gkappa),
-                                       dfloat_from_double(0.5 * coef), steps, (cudaStream_t)stream);
+                                       dfloat_from_double(0.5 * coef), steps, (cudaStream_t)stream,
+                                       accumulate ? 1 : 0, dev_out_f32);
   return e == cudaSuccess ? FRACTAL_OK : cuda_fail(e, "kappa_gradient_df");
+}
+
+int fractal_kappa_gradient_df(fractal_plan_t p, const float* dev_utraj, const float* dev_ptraj, float* dev_gkappa,
+                              double coef, int steps, void* stream) {
+  if (!dev_gkappa) return FRACTAL_EINVAL;
+  return fractal_kappa_gradient_df_io(p, dev_utraj, dev_ptraj, dev_gkappa, 1, nullptr, coef, steps, stream);
 }
 
 int fractal_plan_device_status(fractal_plan_t p, int* code) {

@@ -1206,7 +1206,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kGradThreads, 2) kappa_grad_df_kernel(const float4* __restrict__ utraj,
                                                                           const float4* __restrict__ ptraj,
                                                                           int64_t stride, dfloat* __restrict__ gk,
-                                                                          dfloat ha, int nsteps, Geo g) {
+                                                                          dfloat ha, int nsteps, Geo g, int accumulate,
+                                                                          float* __restrict__ out_f32) {
   extern __shared__ __align__(16) float4 gsm[];
   __shared__ int tab[81];
   int sx, sy;
@@ -1315,17 +1316,32 @@ __global__ void __launch_bounds__(kGradThreads, 2) kappa_grad_df_kernel(const fl
     __syncthreads();  // stage b is refilled by the next iteration's copies
   }
   if (!act) return;
-  dfloat* row = gk + (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
+  // gk += (a / 2) sums (gk taken as 0 without `accumulate`), into gk, or
+  // into out_f32 as float32 (hi + lo rounded once) when that is not null
+  const size_t off = (size_t)GY * kB * (size_t)f.n + (size_t)GX * kB;
 #pragma unroll
   for (int j = 0; j < kB; ++j) {
     dfloat v[kB];
-    ld4(row + (size_t)j * f.n, v);
-    ld4(row + (size_t)j * f.n + 4, v + 4);
+    if (accumulate) {
+      ld4(gk + off + (size_t)j * f.n, v);
+      ld4(gk + off + (size_t)j * f.n + 4, v + 4);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kB; ++i) v[i] = dfloat(0.f, 0.f);
+    }
 #pragma unroll
     for (int i = 0; i < kB; ++i) v[i] = amem(i, j) && gs[j * kB + i].any ? v[i] + ha * gs[j * kB + i].s
                                                                            : (amem(i, j) ? v[i] : dfloat(0.f, 0.f));
-    st4(row + (size_t)j * f.n, v);
-    st4(row + (size_t)j * f.n + 4, v + 4);
+    if (out_f32) {
+      float o[kB];
+#pragma unroll
+      for (int i = 0; i < kB; ++i) o[i] = v[i].hi + v[i].lo;
+      st4(out_f32 + off + (size_t)j * f.n, o);
+      st4(out_f32 + off + (size_t)j * f.n + 4, o + 4);
+    } else {
+      st4(gk + off + (size_t)j * f.n, v);
+      st4(gk + off + (size_t)j * f.n + 4, v + 4);
+    }
   }
 }
 
@@ -1716,7 +1732,7 @@ cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out
 }
 
 cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const float4* ptraj, dfloat* gk, dfloat ha,
-                                 int nsteps, cudaStream_t s) {
+                                 int nsteps, cudaStream_t s, int accumulate, float* out_f32) {
   Launch L;
   int margin = 0;
   if (!kappa_fused_geometry(k, mode, L, margin) || nsteps < 1) return cudaErrorInvalidValue;
@@ -1725,7 +1741,7 @@ cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const flo
   auto run = [&](auto* k) -> cudaError_t {
     cudaError_t e = allow_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
-    k<<<L.grid, kGradThreads, smem, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo);
+    k<<<L.grid, kGradThreads, smem, s>>>(utraj, ptraj, stride, gk, ha, nsteps, L.geo, accumulate, out_f32);
     return cudaGetLastError();
   };
   return mode == kLambda ? run(kappa_grad_df_kernel<kLambda>) : run(kappa_grad_df_kernel<kBB>);

@@ -94,8 +94,10 @@ int64_t kappa_record_float4s(int k);
 cudaError_t launch_kappa_fused_df(int mode, int k, const dfloat* in, dfloat* out, float4* traj, const float* kappa,
                                   dfloat ha, int nsteps, cudaStream_t s, const float* in_f32 = nullptr,
                                   float* out_f32 = nullptr);
+// The gradient pass adds to gk (accumulate != 0) or starts from 0, and
+// writes gk, or out_f32 as float32 when that is not null.
 cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const float4* ptraj, dfloat* gk, dfloat ha,
-                                 int nsteps, cudaStream_t s);
+                                 int nsteps, cudaStream_t s, int accumulate = 1, float* out_f32 = nullptr);
 
 // Block slots of the four-warp fused launch (super-tiles of side 256,
 // margins of 64 cells at a reach of at most 56 steps).

@@ -341,3 +341,39 @@ def test_fused_gradients_float32_and_float64_inputs_agree(fr, k, steps, every):
         assert torch.equal(x32, x64)
     mask = torch.from_numpy(oracle.member_mask(n).reshape(-1)).cuda()
     assert bool((res[0][0][~mask] == 0).all()) and bool((res[0][1][~mask] == 0).all())
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_pass_start_and_float32_result(fr, mode):
+    """The dJ/dkappa pass started from 0 (its buffer not read) equals the pass
+    added to a cleared buffer, and its float32 result is the float sum hi + lo
+    of the double-float one, bit for bit, with every cell of every member
+    block written and no other cell."""
+    k, steps = 8, 12
+    n = 1 << k
+    u0, kappa, target = fields(k, 130)
+    plan = fr.fractal_map(k, 8, mode)
+    rf, _ = fr.fractal_kappa_fused_limits(k, mode)
+    kap = dev(kappa)
+    ut = torch.zeros(rf * (steps + 1), device="cuda")
+    pt = torch.zeros(rf * steps, device="cuda")
+    fr.fractal_kappa_trajectory_df(plan, _df(u0), None, ut, kap, A, steps - 1)
+    fr.fractal_kappa_trajectory_df(plan, _df(target), None, pt, kap, A, steps - 1)
+    g_acc = torch.zeros(2 * n * n, device="cuda")
+    fr.fractal_kappa_gradient_df(plan, ut, pt, g_acc, A, steps)
+    g_new = torch.full_like(g_acc, float("nan"))
+    fr.fractal_kappa_gradient_df_io(plan, ut, pt, g_new, False, None, A, steps)
+    cover = torch.from_numpy(block_cover(n).reshape(-1)).cuda()
+    cover2 = cover.repeat_interleave(2)
+    assert torch.equal(g_new[cover2], g_acc[cover2])
+    g32 = torch.full((n * n,), -3.0, device="cuda")
+    fr.fractal_kappa_gradient_df_io(plan, ut, pt, None, False, g32, A, steps)
+    hl = g_acc.view(-1, 2)
+    assert torch.equal(g32[cover], (hl[:, 0] + hl[:, 1])[cover]) and bool((g32[~cover] == -3.0).all())
+    g_twice = g_acc.clone()
+    fr.fractal_kappa_gradient_df_io(plan, ut, pt, g_twice, True, g32, A, steps)     # 2x the sum, into g32
+    assert torch.equal(g_twice, g_acc)                                               # gkappa not written
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_gradient_df_io(plan, ut, pt, None, True, g32, A, steps)    # nothing to add to
+    with pytest.raises(fr.FractalError):
+        fr.fractal_kappa_gradient_df_io(plan, ut, pt, None, False, None, A, steps)  # nowhere to write
