@@ -31,3 +31,4 @@ from .gasket import (  # noqa: F401
     reduce_sum,
     sw_write,
 )
+from . import nbb  # noqa: F401,E402  (other fractals of the NBB family)

@@ -1,0 +1,81 @@
+"""CPU pins of the NBB-family oracle (oracle/nbb.py): membership against the
+bottom-up construction of Sec. 3.1 and the counts of Sec. 3.2, the packed
+grid of Lemma 2, lambda of Theorem 1 as a bijection onto the member blocks,
+and the gasket special case against the gasket oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import nbb
+
+NAMES = nbb.names()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("r", [0, 1, 2, 3, 4])
+def test_membership_digits_match_bottom_up_construction(name, r):
+    assert np.array_equal(nbb.member_mask(name, r), nbb.member_mask_recursive(name, r))
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_member_counts_are_k_to_the_r(name):
+    s, k, cells = nbb.FRACTALS[name]
+    assert len(set(cells)) == k and all(0 <= x < s and 0 <= y < s for x, y in cells)
+    for r in range(5):
+        assert int(nbb.member_mask(name, r).sum()) == k ** r          # V = k^r (Sec. 3.1, Lemma 1)
+
+
+def test_textbook_shapes():
+    """Hand-checked features: the carpet's centre hole of side s**(r-1); the
+    Vicsek plus holds the whole middle row and column; the X holds both
+    diagonals; the H holds its left and right columns and its middle row."""
+    r = 3
+    c = nbb.member_mask("carpet", r)
+    assert not c[9:18, 9:18].any() and c[0, :].all() and c[:, 0].all()
+    v = nbb.member_mask("vicsek", r)
+    assert v[13, :].all() and v[:, 13].all() and not v[0, 0]
+    x = nbb.member_mask("xfractal", r)
+    assert all(x[i, i] and x[i, 26 - i] for i in range(27)) and not x[0, 13]
+    h = nbb.member_mask("hfractal", r)
+    assert h[:, 0].all() and h[:, 26].all() and h[13, :].all() and not h[0, 13]
+
+
+def test_gasket_case_is_the_gasket():
+    for r in range(6):
+        n = 1 << r
+        assert np.array_equal(nbb.member_mask("gasket", r), oracle.member_mask(n))
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("r", [0, 1, 2, 3, 4, 5])
+def test_lambda_is_a_bijection_onto_member_blocks(name, r):
+    """Theorem 1: lambda maps the packed grid (Lemma 2: W * H = k^r) one to
+    one onto the member blocks (brute force)."""
+    s, k, _ = nbb.FRACTALS[name]
+    if k ** r > 40000:
+        pytest.skip("large case")
+    W, H = nbb.grid_dims(k, r)
+    assert W * H == k ** r and (W == H or W == k * H)
+    tab = nbb.block_table(name, r).reshape(-1, 2)
+    pts = {(int(x), int(y)) for x, y in tab}
+    assert len(pts) == k ** r
+    mask = nbb.member_mask(name, r)
+    assert all(mask[y, x] for x, y in pts)
+
+
+def test_generic_lambda_reproduces_the_gasket_map():
+    """With the gasket's step cells in this library's numbering, the generic
+    map is the gasket map of the gasket oracle, block for block."""
+    for r in range(1, 8):
+        W, H = oracle.grid_dims(r)
+        for wy in range(H):
+            for wx in range(W):
+                assert nbb.lam("gasket", r, wx, wy) == oracle.lambda_canonical(wx, wy, r)
+
+
+def test_single_write_field():
+    f = nbb.sw_write("vicsek", 2, 1, 2.5)
+    mask = nbb.member_mask("vicsek", 3)
+    assert np.all(f[mask] == 2.5)
+    assert np.isnan(f).sum() == 27 * 27 - 25 * 9               # outside the 25 member tiles of side 3
+    assert np.count_nonzero(f == 0) == 25 * 9 - 125             # non-members of member tiles
