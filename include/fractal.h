@@ -621,6 +621,44 @@ int fractal_kappa_gradient_df_io(fractal_plan_t plan, const float* dev_utraj, co
                                  void* stream);
 
 /* ------------------------------------------------------------------------
+ * Other fractals of the NBB family (Sec. 3.1, Table 1).
+ *
+ * An NBB fractal is given by its step: k cells (x, y) of an s x s grid
+ * (s = 2..4, k = 1..s*s, distinct cells), listed in a host array cells_xy of
+ * 2k int32 in the order that numbers the replicas (the hash H of Theorem 1;
+ * the numbering is free).  A cell of the level-r fractal (side s^r) is a
+ * member iff each of its r base-s digit pairs is a step cell.  For the
+ * gasket of fractal_map, s = 2 and the cells (0,1), (0,0), (1,0) in this
+ * order give the same map.  Not covered by plans: these entries allocate
+ * nothing and keep no state.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * fractal_nbb_map_blocks -- lambda(omega) of Theorem 1 for every block of
+ * the packed k^ceil(r/2) x k^floor(r/2) grid (Lemma 2) of the level-r
+ * fractal: dev_xy[2 i], dev_xy[2 i + 1] = (x, y) of the member block that
+ * omega = (i mod W, i div W) maps to (2 k^r int32, 8-byte aligned).
+ * Asynchronous on `stream`.  Errors: FRACTAL_EINVAL (step, r < 0, k^r or s^r
+ * above 2^31 - 1, NULL or misaligned dev_xy), FRACTAL_ECUDA.
+ */
+int fractal_nbb_map_blocks(int s, int k, const int32_t* cells_xy, int r, void* dev_xy, void* stream);
+
+/*
+ * fractal_nbb_write -- the single write of Sec. 6.2 on the level-(r_b + j)
+ * fractal (side n = s^(r_b + j), dev_buf n*n floats, row-major) in tiles of
+ * side t = s^j, one CTA of t x t threads per tile, one thread per cell (the
+ * paper's setting): `value` at every member cell, 0 at the other cells of
+ * member tiles; no other cell is written.  mode FRACTAL_LAMBDA launches the
+ * k^r_b member tiles through lambda (Theorem 1); FRACTAL_BB launches all
+ * s^(2 r_b) tiles and lets the non-member ones return.  Asynchronous.
+ * Errors: FRACTAL_EINVAL (step, r_b or j < 0, t > 32, n > 2^20, a grid
+ * beyond the launch limits, NULL or misaligned dev_buf, mode),
+ * FRACTAL_ECUDA.
+ */
+int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, float value, float* dev_buf,
+                      void* stream);
+
+/* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.
  *
  * The diffusion step of fractal_step_diffusion applied to `count` separate

@@ -50,7 +50,7 @@ EXPORTS = (
     "fractal_step_diffusion_kappa_df", "fractal_adjoint_diffusion_step_df", "fractal_step_diffusion_sums",
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
     "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_trajectory_df_io",
-    "fractal_kappa_gradient_df", "fractal_kappa_gradient_df_io",
+    "fractal_kappa_gradient_df", "fractal_kappa_gradient_df_io", "fractal_nbb_map_blocks", "fractal_nbb_write",
     "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
     "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
@@ -120,6 +120,8 @@ def _load() -> ctypes.CDLL:
         "fractal_plan_get_info": (I, [P, ctypes.POINTER(PlanInfo)]),
         "fractal_plan_set_cta_levels": (I, [P, I, I]),
         "fractal_map_blocks": (I, [P, VP, VP]),
+        "fractal_nbb_map_blocks": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, VP, VP]),
+        "fractal_nbb_write": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, F, VP, VP]),
         "fractal_map_write": (I, [P, VP, I, D, VP]),
         "fractal_step_ca": (I, [P, VP, VP, I, VP]),
         "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
@@ -366,6 +368,24 @@ def fractal_kappa_gradient_df_io(plan: Plan, dev_utraj, dev_ptraj, dev_gkappa, a
 
 def fractal_map_blocks(plan: Plan, dev_xy, stream=None) -> None:
     _check(_load().fractal_map_blocks(plan.handle, _ptr(dev_xy), _stream(stream)), "fractal_map_blocks")
+
+
+def _nbb_cells(cells):
+    flat = [int(v) for xy in cells for v in xy]
+    return (ctypes.c_int32 * max(1, len(flat)))(*flat)
+
+
+def fractal_nbb_map_blocks(s: int, cells, r: int, dev_xy, stream=None) -> None:
+    """lambda(omega) of an NBB fractal (step: s and its k cells (x, y) in
+    numbering order) for every block of the packed grid at level r: 2 k^r int32."""
+    _check(_load().fractal_nbb_map_blocks(int(s), len(cells), _nbb_cells(cells), int(r), _ptr(dev_xy),
+                                          _stream(stream)), "fractal_nbb_map_blocks")
+
+
+def fractal_nbb_write(s: int, cells, r_b: int, j: int, mode: int, value: float, dev_buf, stream=None) -> None:
+    """The single write on the level-(r_b + j) NBB fractal, tiles of side s^j, one CTA per tile."""
+    _check(_load().fractal_nbb_write(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
+                                     float(value), _ptr(dev_buf), _stream(stream)), "fractal_nbb_write")
 
 
 FRACTAL_MAP_BALLOT = 0

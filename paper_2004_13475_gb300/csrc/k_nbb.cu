@@ -1,0 +1,185 @@
+// The block-space map lambda(omega) for any fractal of the NBB family
+// (Sec. 3.1, Theorem 1, Lemma 2), and the single write of Sec. 6.2 on such a
+// fractal with one CTA per tile (the paper's block-per-tile setting), by the
+// lambda launch or the bounding-box (BB) launch.
+//
+// An NBB fractal is given by its step: k cells (dx, dy) of an s x s grid, in
+// the order that numbers the replicas (the hash H of Theorem 1).  A cell of
+// the level-r fractal is a member iff each of its r base-s digit pairs is a
+// step cell; lambda takes block omega = (wx, wy) of the packed
+// k^ceil(r/2) x k^floor(r/2) grid to sum_mu H[beta_mu] s^(mu - 1), where
+// beta_mu is the next base-k digit of wx (odd mu) or wy (even mu).
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "fractal.h"
+
+namespace {
+
+// The step in the kernels' parameter space: the cells in numbering order,
+// four bits each (x | y << 2, s <= 4: at most 16 cells), and the s x s
+// membership bits (bit dy * s + dx).
+struct NbbStep {
+  int s, k;
+  uint32_t mask;
+  uint64_t cells;
+};
+
+// lambda(omega) at level r (Theorem 1): the replica offsets of each level
+// from the base-k digits of wx and wy, alternately, scaled by s^(mu - 1).
+template <int S>
+__device__ __forceinline__ void nbb_lambda(uint32_t wx, uint32_t wy, int r, const NbbStep& st, uint32_t& bx,
+                                           uint32_t& by) {
+  const uint32_t k = (uint32_t)st.k;
+  uint32_t px = 1, x = 0, y = 0;
+  for (int mu = 1; mu <= r; ++mu) {
+    uint32_t d;
+    if (mu & 1) {
+      d = wx % k;
+      wx /= k;
+    } else {
+      d = wy % k;
+      wy /= k;
+    }
+    const uint32_t c = (uint32_t)(st.cells >> (4 * d)) & 15u;
+    x += (c & 3u) * px;
+    y += (c >> 2) * px;
+    px *= S;
+  }
+  bx = x;
+  by = y;
+}
+
+// (x, y) is a member of the level-levels fractal iff every base-S digit pair
+// is a step cell.
+template <int S>
+__device__ __forceinline__ bool nbb_member(uint32_t x, uint32_t y, int levels, uint32_t mask) {
+  bool ok = true;
+  for (int i = 0; i < levels; ++i) {
+    ok &= ((mask >> ((y % S) * S + (x % S))) & 1u) != 0;
+    x /= S;
+    y /= S;
+  }
+  return ok;
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) nbb_map_kernel(NbbStep st, int r, uint32_t W, int64_t total,
+                                                      int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t bx, by;
+    nbb_lambda<S>((uint32_t)(i % W), (uint32_t)(i / W), r, st, bx, by);
+    reinterpret_cast<int2*>(out)[i] = make_int2((int)bx, (int)by);
+  }
+}
+
+// One CTA of t x t threads per tile (t = S^j), one thread per cell: value at
+// the tile's members, 0 at its other cells.  MODE 0: the CTA's tile by
+// lambda over the packed grid; MODE 1: the CTA's tile is (blockIdx.x,
+// blockIdx.y) of the whole n_b x n_b grid, and CTAs on non-member tiles
+// return at once (the BB launch).
+template <int S, int MODE>
+__global__ void nbb_write_kernel(NbbStep st, int rb, int j, int64_t n, float value, float* __restrict__ buf) {
+  uint32_t bx, by;
+  if (MODE == 0) {
+    nbb_lambda<S>(blockIdx.x, blockIdx.y, rb, st, bx, by);
+  } else {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+    if (!nbb_member<S>(bx, by, rb, st.mask)) return;
+  }
+  const int64_t x = (int64_t)bx * blockDim.x + threadIdx.x, y = (int64_t)by * blockDim.y + threadIdx.y;
+  buf[y * n + x] = nbb_member<S>(threadIdx.x, threadIdx.y, j, st.mask) ? value : 0.f;
+}
+
+int64_t ipow64(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+// Validates the step and fills `st`; FRACTAL_EINVAL if s is not 2..4, k not
+// 1..s*s, a cell outside the s x s grid or listed twice.
+int make_step(int s, int k, const int32_t* cells, NbbStep& st) {
+  if (s < 2 || s > 4 || k < 1 || k > s * s || !cells) return FRACTAL_EINVAL;
+  st = NbbStep{};
+  st.s = s;
+  st.k = k;
+  for (int i = 0; i < k; ++i) {
+    const int x = cells[2 * i], y = cells[2 * i + 1];
+    if (x < 0 || y < 0 || x >= s || y >= s) return FRACTAL_EINVAL;
+    const uint32_t bit = 1u << (y * s + x);
+    if (st.mask & bit) return FRACTAL_EINVAL;
+    st.mask |= bit;
+    st.cells |= (uint64_t)(x | y << 2) << (4 * i);
+  }
+  return FRACTAL_OK;
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? FRACTAL_OK : FRACTAL_ECUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int fractal_nbb_map_blocks(int s, int k, const int32_t* cells_xy, int r, void* dev_xy_, void* stream) {
+  int32_t* dev_xy = static_cast<int32_t*>(dev_xy_);
+  NbbStep st;
+  if (make_step(s, k, cells_xy, st) != FRACTAL_OK || r < 0 || !dev_xy ||
+      (reinterpret_cast<uintptr_t>(dev_xy) & 7u) != 0)
+    return FRACTAL_EINVAL;
+  if (r > 0 && (ipow64(k, r) > (int64_t)0x7fffffff || ipow64(s, r) > (int64_t)0x7fffffff)) return FRACTAL_EINVAL;
+  const int64_t total = ipow64(k, r);
+  const uint32_t W = (uint32_t)ipow64(k, (r + 1) / 2);
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  cudaStream_t cs = (cudaStream_t)stream;
+  switch (s) {
+    case 2: nbb_map_kernel<2><<<(unsigned)blocks, 256, 0, cs>>>(st, r, W, total, dev_xy); break;
+    case 3: nbb_map_kernel<3><<<(unsigned)blocks, 256, 0, cs>>>(st, r, W, total, dev_xy); break;
+    default: nbb_map_kernel<4><<<(unsigned)blocks, 256, 0, cs>>>(st, r, W, total, dev_xy); break;
+  }
+  return status_of(cudaGetLastError());
+}
+
+int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, float value, float* dev_buf,
+                      void* stream) {
+  NbbStep st;
+  if (make_step(s, k, cells_xy, st) != FRACTAL_OK || r_b < 0 || j < 0 || !dev_buf ||
+      (reinterpret_cast<uintptr_t>(dev_buf) & 3u) != 0 || (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB))
+    return FRACTAL_EINVAL;
+  const int64_t t = ipow64(s, j);
+  if (t > 32) return FRACTAL_EINVAL;  // a CTA holds the tile's t * t cells
+  const int64_t nb = ipow64(s, r_b), n = nb * t;
+  if (n > (int64_t)1 << 20) return FRACTAL_EINVAL;
+  const int64_t W = ipow64(k, (r_b + 1) / 2), H = ipow64(k, r_b / 2);
+  dim3 grid;
+  if (mode == FRACTAL_LAMBDA) {
+    if (W > 0x7fffffff || H > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)W, (unsigned)H);
+  } else {
+    if (nb > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)nb, (unsigned)nb);
+  }
+  const dim3 block((unsigned)t, (unsigned)t);
+  cudaStream_t cs = (cudaStream_t)stream;
+  const bool lam = mode == FRACTAL_LAMBDA;
+  switch (s) {
+    case 2:
+      if (lam) nbb_write_kernel<2, 0><<<grid, block, 0, cs>>>(st, r_b, j, n, value, dev_buf);
+      else nbb_write_kernel<2, 1><<<grid, block, 0, cs>>>(st, r_b, j, n, value, dev_buf);
+      break;
+    case 3:
+      if (lam) nbb_write_kernel<3, 0><<<grid, block, 0, cs>>>(st, r_b, j, n, value, dev_buf);
+      else nbb_write_kernel<3, 1><<<grid, block, 0, cs>>>(st, r_b, j, n, value, dev_buf);
+      break;
+    default:
+      if (lam) nbb_write_kernel<4, 0><<<grid, block, 0, cs>>>(st, r_b, j, n, value, dev_buf);
+      else nbb_write_kernel<4, 1><<<grid, block, 0, cs>>>(st, r_b, j, n, value, dev_buf);
+      break;
+  }
+  return status_of(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+"""Other fractals of the NBB family on the GPU (fractal_nbb_map_blocks,
+fractal_nbb_write) against the oracle (oracle/nbb.py): Theorem 1's lambda
+block for block, and the single write of Sec. 6.2 by the lambda and the BB
+launch cell for cell."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import nbb
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NAMES = nbb.names()
+SENTINEL = -5.0
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_2004_13475_gb300 import build as fbuild
+    fbuild.build()
+    import paper_2004_13475_gb300 as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def step(name):
+    s, k, cells = nbb.FRACTALS[name]
+    return s, list(cells)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_map_blocks_match_oracle(fr, name):
+    s, cells = step(name)
+    k = len(cells)
+    for r in range(0, 8):
+        if k ** r > 40000:
+            break
+        out = torch.zeros(2 * k ** r, dtype=torch.int32, device="cuda")
+        fr.fractal_nbb_map_blocks(s, cells, r, out)
+        want = nbb.block_table(name, r).reshape(-1)
+        assert np.array_equal(out.cpu().numpy(), want), (name, r)
+
+
+def test_generic_map_is_the_gasket_map_at_level_12(fr):
+    """The generic kernel with the gasket's step equals this library's
+    gasket map (ballot form) over all 3^12 blocks of a level-12 block grid."""
+    s, cells = step("gasket")
+    out = torch.zeros(2 * 3 ** 12, dtype=torch.int32, device="cuda")
+    fr.fractal_nbb_map_blocks(s, cells, 12, out)
+    plan = fr.fractal_map(15, 8)                     # r_b = 12
+    ref = torch.zeros_like(out)
+    fr.fractal_map_blocks(plan, ref)
+    assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_map_blocks_bijection_large(fr, name):
+    """At a larger level: every block is a member block and none repeats."""
+    s, cells = step(name)
+    k = len(cells)
+    r = max(rr for rr in range(1, 20) if k ** rr <= 5_000_000 and s ** rr <= 1 << 15)
+    out = torch.zeros(2 * k ** r, dtype=torch.int32, device="cuda")
+    fr.fractal_nbb_map_blocks(s, cells, r, out)
+    xy = out.view(-1, 2).long()
+    n = s ** r
+    key = xy[:, 1] * n + xy[:, 0]
+    assert torch.unique(key).numel() == k ** r
+    # membership by digits, on the device with torch integer ops (independent of the kernel)
+    x, y = xy[:, 0].clone(), xy[:, 1].clone()
+    mask = torch.from_numpy(nbb.step_mask(s, cells).reshape(-1)).cuda()
+    ok = torch.ones_like(x, dtype=torch.bool)
+    for _ in range(r):
+        ok &= mask[(y % s) * s + (x % s)]
+        x //= s
+        y //= s
+    assert bool(ok.all())
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("rb,j", [(0, 1), (2, 1), (3, 1), (2, 2), (4, 0)])
+def test_single_write_matches_oracle(fr, name, rb, j, mode):
+    s, cells = step(name)
+    if s ** j > 32 or (s ** (rb + j)) ** 2 > 1 << 22:
+        pytest.skip("size")
+    n = s ** (rb + j)
+    buf = torch.full((n * n,), SENTINEL, device="cuda")
+    fr.fractal_nbb_write(s, cells, rb, j, mode, 1.5, buf)
+    got = buf.cpu().numpy().reshape(n, n)
+    want = nbb.sw_write(name, rb, j, 1.5)
+    untouched = np.isnan(want)
+    assert np.all(got[untouched] == SENTINEL)
+    assert np.array_equal(got[~untouched], want[~untouched].astype(np.float32))
+
+
+@pytest.mark.parametrize("name", ["carpet", "vicsek", "hfractal"])
+def test_single_write_lambda_and_bb_agree_large(fr, name):
+    """Level 8 with tiles of side 9 (n = 6561): both launches write the same
+    field; the member count is k^8 cells."""
+    s, cells = step(name)
+    rb, j = 6, 2
+    n = s ** (rb + j)
+    a = torch.full((n * n,), SENTINEL, device="cuda")
+    b = torch.full_like(a, SENTINEL)
+    fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, a)
+    fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b)
+    assert torch.equal(a, b)
+    assert int((a == 1.0).sum()) == len(cells) ** (rb + j)
+    assert int((a != SENTINEL).sum()) == len(cells) ** rb * (s ** j) ** 2
+
+
+def test_nbb_validation(fr):
+    buf = torch.zeros(16, device="cuda")
+    xy = torch.zeros(32, dtype=torch.int32, device="cuda")
+    bad_steps = [(1, [(0, 0)]), (5, [(0, 0)]), (2, [(0, 0), (0, 0)]), (2, [(2, 0)]), (2, [(0, 0)] * 5)]
+    for s, cells in bad_steps:
+        with pytest.raises(fr.FractalError):
+            fr.fractal_nbb_map_blocks(s, cells, 1, xy)
+        with pytest.raises(fr.FractalError):
+            fr.fractal_nbb_write(s, cells, 1, 1, 0, 1.0, buf)
+    s, cells = step("carpet")
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_write(s, cells, 1, 4, 0, 1.0, buf)          # tile side 81 > 32
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_write(s, cells, 1, 1, 2, 1.0, buf)          # mode
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_map_blocks(s, cells, 11, xy)                 # 8^11 blocks > 2^31 - 1
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_map_blocks(s, cells, -1, xy)
