@@ -512,6 +512,8 @@ def main():
     if rank == 0 and not args.no_detail:
         line["lambda_forms"] = lambda_forms(fr, torch, stream)
     if rank == 0 and not args.no_detail:
+        line["nbb"] = nbb_forms(fr, torch, stream, hbm)
+    if rank == 0 and not args.no_detail:
         line["smaller_configs"] = small_configs(fr, torch, stream)
     if rank == 0 and not args.no_batch:
         line["batched"] = batched(fr, torch, stream, SEED + 17)
@@ -886,6 +888,63 @@ def lambda_forms(fr, torch, stream):
         out[name] = {"us": t * 1e6, "omegas_per_s": m / t}
     out["mma_kept"] = out["mma"]["us"] < min(out["ballot"]["us"], out["per_thread"]["us"])
     plan.close()
+    return out
+
+
+# Other NBB fractals (Sec. 3.1, Table 1): the step cells in numbering order.
+NBB_STEPS = {
+    "carpet": (3, [(x, y) for y in range(3) for x in range(3) if (x, y) != (1, 1)]),
+    "vicsek": (3, [(1, 0), (0, 1), (1, 1), (2, 1), (1, 2)]),
+    "xfractal": (3, [(0, 0), (2, 0), (1, 1), (0, 2), (2, 2)]),
+    "hfractal": (3, [(0, 0), (2, 0), (0, 1), (1, 1), (2, 1), (0, 2), (2, 2)]),
+}
+
+
+def nbb_forms(fr, torch, stream, hbm):
+    """Other NBB fractals: the single write of Sec. 6.2 with one CTA of 9 x 9
+    threads per 9 x 9 tile, lambda launch against BB launch (Theorem 2's
+    speedup), on the carpet at level 9 (19683^2 floats), the Vicsek and
+    X-fractal at level 10 (59049^2) and the H-fractal at level 9; and the
+    generic lambda map's block rate (fractal_nbb_map_blocks) at about 10^7
+    blocks.  Times are CUDA-event means of repeated calls."""
+    cases = {"carpet": 7, "vicsek": 8, "xfractal": 8, "hfractal": 7}   # r_b; tiles of side 3^2
+    j = 2
+    nmax = max(3 ** (rb + j) for rb in cases.values())
+    buf = torch.empty(nmax * nmax, dtype=torch.float32, device="cuda")
+    out = {"tile": "9 x 9 cells, one CTA of 81 threads per tile (the paper's setting)"}
+
+    def clock(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / 1e3 / reps
+
+    for name, rb in cases.items():
+        s, cells = NBB_STEPS[name]
+        k = len(cells)
+        n = s ** (rb + j)
+        b = buf[:n * n]
+        tl = clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, b, stream))
+        tb = clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b, stream))
+        alg = k ** rb * 81 * 4
+        rm = max(r for r in range(1, 30) if k ** r <= 20_000_000)
+        xy = torch.empty(2 * k ** rm, dtype=torch.int32, device="cuda")
+        tm = clock(lambda: fr.fractal_nbb_map_blocks(s, cells, rm, xy, stream))
+        out[name] = {"s": s, "k": k, "level": rb + j, "n": n, "member_tiles": k ** rb,
+                     "lambda_us": tl * 1e6, "bb_us": tb * 1e6, "speedup_lambda_over_bb": tb / tl,
+                     "lambda_alg_gbs": alg / tl / 1e9, "lambda_frac_hbm": alg / tl / 1e9 / hbm,
+                     "bb_ctas": (s ** rb) ** 2, "lambda_ctas": k ** rb,
+                     "map_blocks": {"level": rm, "blocks": k ** rm, "us": tm * 1e6, "blocks_per_s": k ** rm / tm}}
+        del xy
+    del buf
+    torch.cuda.empty_cache()
     return out
 
 

@@ -95,3 +95,11 @@ def test_committed_profile_tables_parse():
             assert len(bench.sources_hash(r[0])) == 16
     for r in (ln.split() for ln in open(bench.STALLS_FILE) if ln.strip() and not ln.startswith("#")):
         assert all(float(kv.split("=")[1]) >= 0 for kv in r[3:])
+
+
+def test_bench_nbb_steps_match_the_oracle():
+    """The NBB steps bench.py measures are the oracle's (same cells, same order)."""
+    from oracle import nbb
+    for name, (s, cells) in bench.NBB_STEPS.items():
+        s2, k2, cells2 = nbb.FRACTALS[name]
+        assert s == s2 and len(cells) == k2 and [tuple(c) for c in cells] == list(cells2)
