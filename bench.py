@@ -903,7 +903,8 @@ NBB_STEPS = {
 def nbb_forms(fr, torch, stream, hbm):
     """Other NBB fractals: the single write of Sec. 6.2 with one CTA of 9 x 9
     threads per 9 x 9 tile, lambda launch against BB launch (Theorem 2's
-    speedup), on the carpet at level 9 (19683^2 floats), the Vicsek and
+    speedup), and with one CTA of 256 threads per super-tile of 9 x 9 or
+    27 x 27 tiles (`supertiles`), on the carpet at level 9 (19683^2 floats), the Vicsek and
     X-fractal at level 10 (59049^2) and the H-fractal at level 9; and the
     generic lambda map's block rate (fractal_nbb_map_blocks) at about 10^7
     blocks.  Times are CUDA-event means of repeated calls."""
@@ -933,6 +934,11 @@ def nbb_forms(fr, torch, stream, hbm):
         b = buf[:n * n]
         tl = clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, b, stream))
         tb = clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b, stream))
+        # super-tiles of 3^m x 3^m tiles per CTA of 256 threads (the library's CTA shape)
+        st = {}
+        for m in (2, 3):
+            st[m] = (clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, b, stream, cta_levels=m)),
+                     clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b, stream, cta_levels=m)))
         alg = k ** rb * 81 * 4
         rm = max(r for r in range(1, 30) if k ** r <= 20_000_000)
         xy = torch.empty(2 * k ** rm, dtype=torch.int32, device="cuda")
@@ -941,6 +947,9 @@ def nbb_forms(fr, torch, stream, hbm):
                      "lambda_us": tl * 1e6, "bb_us": tb * 1e6, "speedup_lambda_over_bb": tb / tl,
                      "lambda_alg_gbs": alg / tl / 1e9, "lambda_frac_hbm": alg / tl / 1e9 / hbm,
                      "bb_ctas": (s ** rb) ** 2, "lambda_ctas": k ** rb,
+                     "supertiles": {str(m): {"lambda_us": a * 1e6, "bb_us": c * 1e6, "speedup_lambda_over_bb": c / a,
+                                             "lambda_alg_gbs": alg / a / 1e9, "lambda_frac_hbm": alg / a / 1e9 / hbm}
+                                    for m, (a, c) in st.items()},
                      "map_blocks": {"level": rm, "blocks": k ** rm, "us": tm * 1e6, "blocks_per_s": k ** rm / tm}}
         del xy
     del buf

@@ -646,17 +646,21 @@ int fractal_nbb_map_blocks(int s, int k, const int32_t* cells_xy, int r, void* d
 /*
  * fractal_nbb_write -- the single write of Sec. 6.2 on the level-(r_b + j)
  * fractal (side n = s^(r_b + j), dev_buf n*n floats, row-major) in tiles of
- * side t = s^j, one CTA of t x t threads per tile, one thread per cell (the
- * paper's setting): `value` at every member cell, 0 at the other cells of
- * member tiles; no other cell is written.  mode FRACTAL_LAMBDA launches the
- * k^r_b member tiles through lambda (Theorem 1); FRACTAL_BB launches all
- * s^(2 r_b) tiles and lets the non-member ones return.  Asynchronous.
- * Errors: FRACTAL_EINVAL (step, r_b or j < 0, t > 32, n > 2^20, a grid
- * beyond the launch limits, NULL or misaligned dev_buf, mode),
- * FRACTAL_ECUDA.
+ * side t = s^j: `value` at every member cell, 0 at the other cells of member
+ * tiles; no other cell is written.  cta_levels == 0: one CTA of t x t
+ * threads per tile, one thread per cell (the paper's setting); mode
+ * FRACTAL_LAMBDA launches the k^r_b member tiles through lambda (Theorem 1),
+ * FRACTAL_BB all s^(2 r_b) tiles, the non-member ones returning at once.
+ * cta_levels == m > 0: one CTA of 256 threads per super-tile of s^m x s^m
+ * tiles (Sec. 5.1's further unrolling): lambda at level r_b - m for the
+ * super-tiles and at level m for their k^m member tiles, or, BB, all
+ * super-tiles and all their tiles with the non-members skipped (at most 4096
+ * tiles per super-tile).  Asynchronous.  Errors: FRACTAL_EINVAL (step, r_b or
+ * j < 0, cta_levels outside 0..r_b, t > 32, n > 2^20, a grid or super-tile
+ * beyond the launch limits, NULL or misaligned dev_buf, mode), FRACTAL_ECUDA.
  */
-int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, float value, float* dev_buf,
-                      void* stream);
+int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int cta_levels, int mode, float value,
+                      float* dev_buf, void* stream);
 
 /* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.

@@ -121,7 +121,7 @@ def _load() -> ctypes.CDLL:
         "fractal_plan_set_cta_levels": (I, [P, I, I]),
         "fractal_map_blocks": (I, [P, VP, VP]),
         "fractal_nbb_map_blocks": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, VP, VP]),
-        "fractal_nbb_write": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, F, VP, VP]),
+        "fractal_nbb_write": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, I, F, VP, VP]),
         "fractal_map_write": (I, [P, VP, I, D, VP]),
         "fractal_step_ca": (I, [P, VP, VP, I, VP]),
         "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
@@ -382,10 +382,12 @@ def fractal_nbb_map_blocks(s: int, cells, r: int, dev_xy, stream=None) -> None:
                                           _stream(stream)), "fractal_nbb_map_blocks")
 
 
-def fractal_nbb_write(s: int, cells, r_b: int, j: int, mode: int, value: float, dev_buf, stream=None) -> None:
-    """The single write on the level-(r_b + j) NBB fractal, tiles of side s^j, one CTA per tile."""
-    _check(_load().fractal_nbb_write(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
-                                     float(value), _ptr(dev_buf), _stream(stream)), "fractal_nbb_write")
+def fractal_nbb_write(s: int, cells, r_b: int, j: int, mode: int, value: float, dev_buf, stream=None,
+                      cta_levels: int = 0) -> None:
+    """The single write on the level-(r_b + j) NBB fractal in tiles of side
+    s^j: one CTA per tile (cta_levels = 0) or per super-tile of s^m x s^m tiles."""
+    _check(_load().fractal_nbb_write(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(cta_levels),
+                                     int(mode), float(value), _ptr(dev_buf), _stream(stream)), "fractal_nbb_write")
 
 
 FRACTAL_MAP_BALLOT = 0

@@ -93,6 +93,57 @@ __global__ void nbb_write_kernel(NbbStep st, int rb, int j, int64_t n, float val
   buf[y * n + x] = nbb_member<S>(threadIdx.x, threadIdx.y, j, st.mask) ? value : 0.f;
 }
 
+// One CTA per super-tile of k^m member tiles (this library's CTA shape, the
+// further unrolling of Sec. 5.1): MODE 0: the super-tile by lambda over the
+// packed grid of level rb - m and its tiles by lambda again at level m;
+// MODE 1: the super-tile (blockIdx.x, blockIdx.y) of the whole grid, left at
+// once when it is not a member, and its s^m x s^m tiles, the non-member ones
+// skipped.  The CTA's threads stride over tile cells in tile order, so a
+// warp's stores run along the rows of one or two tiles.
+template <int S, int MODE>
+__global__ void __launch_bounds__(256) nbb_write_tiles_kernel(NbbStep st, int rb, int j, int m, int t, int64_t n,
+                                                               float value, float* __restrict__ buf) {
+  extern __shared__ uint32_t toff[];  // tile offsets inside the super-tile: x | y << 16
+  uint32_t sx, sy;
+  int ntiles;
+  if (MODE == 0) {
+    nbb_lambda<S>(blockIdx.x, blockIdx.y, rb - m, st, sx, sy);
+    ntiles = 1;
+    for (int i = 0; i < m; ++i) ntiles *= st.k;
+    uint32_t W = 1;
+    for (int i = 0; i < (m + 1) / 2; ++i) W *= (uint32_t)st.k;
+    for (int q = threadIdx.x; q < ntiles; q += blockDim.x) {
+      uint32_t ox, oy;
+      nbb_lambda<S>((uint32_t)q % W, (uint32_t)q / W, m, st, ox, oy);
+      toff[q] = ox | oy << 16;
+    }
+  } else {
+    sx = blockIdx.x;
+    sy = blockIdx.y;
+    if (!nbb_member<S>(sx, sy, rb - m, st.mask)) return;
+    int side = 1;
+    for (int i = 0; i < m; ++i) side *= S;
+    ntiles = side * side;
+    for (int q = threadIdx.x; q < ntiles; q += blockDim.x) {
+      const uint32_t ox = (uint32_t)(q % side), oy = (uint32_t)(q / side);
+      toff[q] = nbb_member<S>(ox, oy, m, st.mask) ? (ox | oy << 16) : 0xffffffffu;
+    }
+  }
+  __syncthreads();
+  int sm = 1;
+  for (int i = 0; i < m; ++i) sm *= S;
+  const int64_t X0 = (int64_t)sx * sm * t, Y0 = (int64_t)sy * sm * t;
+  const int cells = t * t;
+  for (int i = threadIdx.x; i < ntiles * cells; i += blockDim.x) {
+    const int q = i / cells, c = i - q * cells;
+    const uint32_t e = toff[q];
+    if (MODE == 1 && e == 0xffffffffu) continue;
+    const int cx = c % t, cy = c / t;
+    const int64_t x = X0 + (int64_t)(e & 0xffffu) * t + cx, y = Y0 + (int64_t)(e >> 16) * t + cy;
+    buf[y * n + x] = nbb_member<S>((uint32_t)cx, (uint32_t)cy, j, st.mask) ? value : 0.f;
+  }
+}
+
 int64_t ipow64(int64_t b, int e) {
   int64_t r = 1;
   while (e-- > 0) r *= b;
@@ -143,16 +194,50 @@ int fractal_nbb_map_blocks(int s, int k, const int32_t* cells_xy, int r, void* d
   return status_of(cudaGetLastError());
 }
 
-int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, float value, float* dev_buf,
-                      void* stream) {
+int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int cta_levels, int mode, float value,
+                      float* dev_buf, void* stream) {
   NbbStep st;
   if (make_step(s, k, cells_xy, st) != FRACTAL_OK || r_b < 0 || j < 0 || !dev_buf ||
-      (reinterpret_cast<uintptr_t>(dev_buf) & 3u) != 0 || (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB))
+      (reinterpret_cast<uintptr_t>(dev_buf) & 3u) != 0 || (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB) ||
+      cta_levels < 0 || cta_levels > r_b)
     return FRACTAL_EINVAL;
   const int64_t t = ipow64(s, j);
   if (t > 32) return FRACTAL_EINVAL;  // a CTA holds the tile's t * t cells
   const int64_t nb = ipow64(s, r_b), n = nb * t;
   if (n > (int64_t)1 << 20) return FRACTAL_EINVAL;
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (cta_levels > 0) {  // one CTA of 256 threads per super-tile of k^m member tiles
+    const int m = cta_levels;
+    const int64_t tiles = mode == FRACTAL_LAMBDA ? ipow64(k, m) : ipow64(s, 2 * m);
+    if (tiles > 4096 || (uint32_t)(ipow64(s, m)) > 0xffffu) return FRACTAL_EINVAL;
+    const int64_t W = ipow64(k, (r_b - m + 1) / 2), H = ipow64(k, (r_b - m) / 2), G = ipow64(s, r_b - m);
+    dim3 grid;
+    if (mode == FRACTAL_LAMBDA) {
+      if (W > 0x7fffffff || H > 65535) return FRACTAL_EINVAL;
+      grid = dim3((unsigned)W, (unsigned)H);
+    } else {
+      if (G > 65535) return FRACTAL_EINVAL;
+      grid = dim3((unsigned)G, (unsigned)G);
+    }
+    const size_t smem = (size_t)tiles * 4;
+    const bool lam = mode == FRACTAL_LAMBDA;
+    const int ti = (int)t;
+    switch (s) {
+      case 2:
+        if (lam) nbb_write_tiles_kernel<2, 0><<<grid, 256, smem, cs>>>(st, r_b, j, m, ti, n, value, dev_buf);
+        else nbb_write_tiles_kernel<2, 1><<<grid, 256, smem, cs>>>(st, r_b, j, m, ti, n, value, dev_buf);
+        break;
+      case 3:
+        if (lam) nbb_write_tiles_kernel<3, 0><<<grid, 256, smem, cs>>>(st, r_b, j, m, ti, n, value, dev_buf);
+        else nbb_write_tiles_kernel<3, 1><<<grid, 256, smem, cs>>>(st, r_b, j, m, ti, n, value, dev_buf);
+        break;
+      default:
+        if (lam) nbb_write_tiles_kernel<4, 0><<<grid, 256, smem, cs>>>(st, r_b, j, m, ti, n, value, dev_buf);
+        else nbb_write_tiles_kernel<4, 1><<<grid, 256, smem, cs>>>(st, r_b, j, m, ti, n, value, dev_buf);
+        break;
+    }
+    return status_of(cudaGetLastError());
+  }
   const int64_t W = ipow64(k, (r_b + 1) / 2), H = ipow64(k, r_b / 2);
   dim3 grid;
   if (mode == FRACTAL_LAMBDA) {
@@ -163,7 +248,6 @@ int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int
     grid = dim3((unsigned)nb, (unsigned)nb);
   }
   const dim3 block((unsigned)t, (unsigned)t);
-  cudaStream_t cs = (cudaStream_t)stream;
   const bool lam = mode == FRACTAL_LAMBDA;
   switch (s) {
     case 2:

@@ -78,16 +78,19 @@ def test_map_blocks_bijection_large(fr, name):
     assert bool(ok.all())
 
 
+@pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("rb,j", [(0, 1), (2, 1), (3, 1), (2, 2), (4, 0)])
-def test_single_write_matches_oracle(fr, name, rb, j, mode):
+def test_single_write_matches_oracle(fr, name, rb, j, mode, levels):
+    """Both launches and both CTA shapes (one CTA per tile, or per super-tile
+    of s^m x s^m tiles) against the oracle, cells outside member tiles untouched."""
     s, cells = step(name)
-    if s ** j > 32 or (s ** (rb + j)) ** 2 > 1 << 22:
+    if s ** j > 32 or (s ** (rb + j)) ** 2 > 1 << 22 or levels > rb:
         pytest.skip("size")
     n = s ** (rb + j)
     buf = torch.full((n * n,), SENTINEL, device="cuda")
-    fr.fractal_nbb_write(s, cells, rb, j, mode, 1.5, buf)
+    fr.fractal_nbb_write(s, cells, rb, j, mode, 1.5, buf, cta_levels=levels)
     got = buf.cpu().numpy().reshape(n, n)
     want = nbb.sw_write(name, rb, j, 1.5)
     untouched = np.isnan(want)
@@ -107,6 +110,10 @@ def test_single_write_lambda_and_bb_agree_large(fr, name):
     fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, a)
     fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b)
     assert torch.equal(a, b)
+    for mode in (0, 1):                                   # super-tiles of 9 x 9 tiles
+        c = torch.full_like(a, SENTINEL)
+        fr.fractal_nbb_write(s, cells, rb, j, mode, 1.0, c, cta_levels=2)
+        assert torch.equal(a, c)
     assert int((a == 1.0).sum()) == len(cells) ** (rb + j)
     assert int((a != SENTINEL).sum()) == len(cells) ** rb * (s ** j) ** 2
 
@@ -125,6 +132,10 @@ def test_nbb_validation(fr):
         fr.fractal_nbb_write(s, cells, 1, 4, 0, 1.0, buf)          # tile side 81 > 32
     with pytest.raises(fr.FractalError):
         fr.fractal_nbb_write(s, cells, 1, 1, 2, 1.0, buf)          # mode
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_write(s, cells, 1, 1, 0, 1.0, buf, cta_levels=2)   # more CTA levels than block levels
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_write(s, cells, 6, 1, 1, 1.0, buf, cta_levels=5)   # 3^10 BB tiles per super-tile
     with pytest.raises(fr.FractalError):
         fr.fractal_nbb_map_blocks(s, cells, 11, xy)                 # 8^11 blocks > 2^31 - 1
     with pytest.raises(fr.FractalError):
