@@ -139,3 +139,63 @@ def sw_write(name: str, r_b: int, j: int, value: float) -> np.ndarray:
 
 def names() -> List[str]:
     return list(FRACTALS)
+
+
+def ca_step(name: str, r: int, alive: np.ndarray) -> np.ndarray:
+    """One synchronous B3/S23 step on the level-r fractal (Sec. 6.2's CA test,
+    the rule read as for the gasket): a cell's count is its alive member
+    neighbours in the Moore neighbourhood (cells outside the array count 0);
+    a member is alive next if it has 3, or if it is alive and has 2;
+    non-members stay 0.  alive: (n, n) array, nonzero = alive, read at members only."""
+    mask = member_mask(name, r)
+    a = (alive != 0) & mask
+    n = a.shape[0]
+    p = np.zeros((n + 2, n + 2), dtype=np.int32)
+    p[1:-1, 1:-1] = a
+    cnt = sum(p[1 + dy:n + 1 + dy, 1 + dx:n + 1 + dx] for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+              if (dx, dy) != (0, 0))
+    nxt = (cnt == 3) | (a & (cnt == 2))
+    return (nxt & mask).astype(np.uint8)
+
+
+def ca_step_loops(name: str, r: int, alive: np.ndarray) -> np.ndarray:
+    """The same step cell by cell with plain loops over the neighbours, for
+    small levels: an independent formulation to pin ca_step against."""
+    s, _, cells = FRACTALS[name]
+    n = s ** r
+    allowed = set(cells)
+
+    def member(x, y):
+        if not (0 <= x < n and 0 <= y < n):
+            return False
+        for _ in range(r):
+            if (x % s, y % s) not in allowed:
+                return False
+            x //= s
+            y //= s
+        return True
+
+    out = np.zeros((n, n), dtype=np.uint8)
+    for y in range(n):
+        for x in range(n):
+            if not member(x, y):
+                continue
+            c = 0
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if (dx or dy) and member(x + dx, y + dy) and alive[y + dy, x + dx]:
+                        c += 1
+            me = bool(alive[y, x])
+            out[y, x] = 1 if (c == 3 or (me and c == 2)) else 0
+    return out
+
+
+def ca_write(name: str, r_b: int, j: int, alive: np.ndarray) -> np.ndarray:
+    """The next state as a tile launch writes it: the step's values in member
+    tiles (side s**j), NaN elsewhere (cells the launch must not touch)."""
+    s, _, _ = FRACTALS[name]
+    t = s ** j
+    nxt = ca_step(name, r_b + j, alive).astype(np.float64)
+    in_tile = np.kron(member_mask(name, r_b), np.ones((t, t), dtype=bool))
+    nxt[~in_tile] = np.nan
+    return nxt

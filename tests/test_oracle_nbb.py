@@ -79,3 +79,41 @@ def test_single_write_field():
     assert np.all(f[mask] == 2.5)
     assert np.isnan(f).sum() == 27 * 27 - 25 * 9               # outside the 25 member tiles of side 3
     assert np.count_nonzero(f == 0) == 25 * 9 - 125             # non-members of member tiles
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_ca_step_matches_cell_by_cell_loops(name, r):
+    s, _, _ = nbb.FRACTALS[name]
+    n = s ** r
+    rng = np.random.default_rng(7 + r)
+    alive = (rng.random((n, n)) < 0.5).astype(np.uint8)
+    assert np.array_equal(nbb.ca_step(name, r, alive), nbb.ca_step_loops(name, r, alive))
+
+
+def test_ca_gasket_case_is_the_gasket_automaton():
+    r = 6
+    n = 1 << r
+    rng = np.random.default_rng(3)
+    alive = (rng.random((n, n)) < 0.5).astype(np.uint8)
+    a = alive.copy()
+    b = alive.copy()
+    for _ in range(5):
+        a = nbb.ca_step("gasket", r, a)
+    b = oracle.ca_run(b, 5)
+    assert np.array_equal(a, b.astype(np.uint8))
+
+
+def test_ca_still_life_and_dead_field():
+    """A 2 x 2 block of member cells is a still life (each of its cells has 3
+    alive neighbours, no dead cell has 3); an all-dead field stays dead."""
+    r = 3
+    n = 27
+    alive = np.zeros((n, n), dtype=np.uint8)
+    alive[0:2, 2:4] = 1                                  # carpet cells (2,0), (3,0), (2,1), (3,1)
+    assert nbb.member_mask("carpet", r)[0:2, 2:4].all()
+    nxt = alive
+    for _ in range(4):
+        nxt = nbb.ca_step("carpet", r, nxt)
+    assert np.array_equal(nxt, alive)
+    assert not nbb.ca_step("vicsek", r, np.zeros((n, n), dtype=np.uint8)).any()
