@@ -904,7 +904,8 @@ def nbb_forms(fr, torch, stream, hbm):
     """Other NBB fractals: the single write of Sec. 6.2 with one CTA of 9 x 9
     threads per 9 x 9 tile, lambda launch against BB launch (Theorem 2's
     speedup), and with one CTA of 256 threads per super-tile of 9 x 9 or
-    27 x 27 tiles (`supertiles`), on the carpet at level 9 (19683^2 floats), the Vicsek and
+    27 x 27 tiles (`supertiles`), and the CA test of Sec. 6.2 (`ca`, uint8,
+    one CTA per 9 x 9 tile with its halo in shared memory), on the carpet at level 9 (19683^2 floats), the Vicsek and
     X-fractal at level 10 (59049^2) and the H-fractal at level 9; and the
     generic lambda map's block rate (fractal_nbb_map_blocks) at about 10^7
     blocks.  Times are CUDA-event means of repeated calls."""
@@ -940,6 +941,12 @@ def nbb_forms(fr, torch, stream, hbm):
             st[m] = (clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, b, stream, cta_levels=m)),
                      clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b, stream, cta_levels=m)))
         alg = k ** rb * 81 * 4
+        # the CA test (Sec. 6.2) on the same fractal, uint8, 10 steps, one CTA per 9 x 9 tile
+        ca_a = torch.zeros(n * n, dtype=torch.uint8, device="cuda")
+        ca_b = torch.zeros_like(ca_a)
+        ca_t = [clock(lambda: fr.fractal_nbb_step_ca(s, cells, rb, j, md, ca_a, ca_b, 10, stream), reps=3) / 10
+                for md in (0, 1)]
+        del ca_a, ca_b
         rm = max(r for r in range(1, 30) if k ** r <= 20_000_000)
         xy = torch.empty(2 * k ** rm, dtype=torch.int32, device="cuda")
         tm = clock(lambda: fr.fractal_nbb_map_blocks(s, cells, rm, xy, stream))
@@ -947,6 +954,9 @@ def nbb_forms(fr, torch, stream, hbm):
                      "lambda_us": tl * 1e6, "bb_us": tb * 1e6, "speedup_lambda_over_bb": tb / tl,
                      "lambda_alg_gbs": alg / tl / 1e9, "lambda_frac_hbm": alg / tl / 1e9 / hbm,
                      "bb_ctas": (s ** rb) ** 2, "lambda_ctas": k ** rb,
+                     "ca": {"lambda_us_per_step": ca_t[0] * 1e6, "bb_us_per_step": ca_t[1] * 1e6,
+                            "speedup_lambda_over_bb": ca_t[1] / ca_t[0],
+                            "cell_updates_per_s_lambda": k ** (rb + j) / ca_t[0]},
                      "supertiles": {str(m): {"lambda_us": a * 1e6, "bb_us": c * 1e6, "speedup_lambda_over_bb": c / a,
                                              "lambda_alg_gbs": alg / a / 1e9, "lambda_frac_hbm": alg / a / 1e9 / hbm}
                                     for m, (a, c) in st.items()},

@@ -662,6 +662,24 @@ int fractal_nbb_map_blocks(int s, int k, const int32_t* cells_xy, int r, void* d
 int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int cta_levels, int mode, float value,
                       float* dev_buf, void* stream);
 
+/*
+ * fractal_nbb_step_ca -- `steps` steps of the CA test of Sec. 6.2 (B3/S23 on
+ * the Moore neighbourhood, only member neighbours counted, non-members never
+ * born, cells outside the array dead) on the level-(r_b + j) fractal (side
+ * n = s^(r_b + j); dev_a, dev_b: n*n bytes, nonzero = alive, distinct),
+ * alternating dev_a -> dev_b -> dev_a ...: the state ends in dev_a for an even
+ * `steps`, in dev_b for an odd one.  One CTA of t x t threads per tile of
+ * side t = s^j (the paper's setting), the tile and its halo staged in shared
+ * memory; mode FRACTAL_LAMBDA launches the member tiles through lambda
+ * (Theorem 1), FRACTAL_BB all tiles.  Only member cells are read; member
+ * tiles are written (0 at their non-member cells), no other cell.
+ * Asynchronous.  Errors: FRACTAL_EINVAL (step, r_b or j < 0, t > 32,
+ * n > 2^20, grid limits, NULL or equal buffers, steps < 0, mode),
+ * FRACTAL_ECUDA.
+ */
+int fractal_nbb_step_ca(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, uint8_t* dev_a,
+                        uint8_t* dev_b, int steps, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.
  *

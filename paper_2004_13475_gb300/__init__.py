@@ -51,6 +51,7 @@ EXPORTS = (
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
     "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_trajectory_df_io",
     "fractal_kappa_gradient_df", "fractal_kappa_gradient_df_io", "fractal_nbb_map_blocks", "fractal_nbb_write",
+    "fractal_nbb_step_ca",
     "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
     "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
@@ -122,6 +123,7 @@ def _load() -> ctypes.CDLL:
         "fractal_map_blocks": (I, [P, VP, VP]),
         "fractal_nbb_map_blocks": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, VP, VP]),
         "fractal_nbb_write": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, I, F, VP, VP]),
+        "fractal_nbb_step_ca": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, VP, VP, I, VP]),
         "fractal_map_write": (I, [P, VP, I, D, VP]),
         "fractal_step_ca": (I, [P, VP, VP, I, VP]),
         "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
@@ -388,6 +390,14 @@ def fractal_nbb_write(s: int, cells, r_b: int, j: int, mode: int, value: float, 
     s^j: one CTA per tile (cta_levels = 0) or per super-tile of s^m x s^m tiles."""
     _check(_load().fractal_nbb_write(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(cta_levels),
                                      int(mode), float(value), _ptr(dev_buf), _stream(stream)), "fractal_nbb_write")
+
+
+def fractal_nbb_step_ca(s: int, cells, r_b: int, j: int, mode: int, dev_a, dev_b, steps: int, stream=None):
+    """`steps` B3/S23 steps on the level-(r_b + j) NBB fractal, one CTA per
+    tile of side s^j; returns the buffer holding the result (dev_a for even steps)."""
+    _check(_load().fractal_nbb_step_ca(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
+                                       _ptr(dev_a), _ptr(dev_b), int(steps), _stream(stream)), "fractal_nbb_step_ca")
+    return dev_a if steps % 2 == 0 else dev_b
 
 
 FRACTAL_MAP_BALLOT = 0

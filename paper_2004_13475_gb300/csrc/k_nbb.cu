@@ -144,6 +144,48 @@ __global__ void __launch_bounds__(256) nbb_write_tiles_kernel(NbbStep st, int rb
   }
 }
 
+// One B3/S23 step of the CA test (Sec. 6.2) on a tile of t x t cells per
+// CTA of t x t threads (the paper's setting), tile by lambda (MODE 0) or by
+// identity over the whole grid with non-member tiles returning (MODE 1):
+// the tile and its one-cell halo are staged in shared memory as
+// "alive and member" (cells outside the array count as dead), then each
+// thread counts its eight neighbours.  Member cells get the rule, the tile's
+// other cells 0.
+template <int S, int MODE>
+__global__ void nbb_ca_kernel(NbbStep st, int rb, int j, int64_t n, const uint8_t* __restrict__ in,
+                              uint8_t* __restrict__ out) {
+  extern __shared__ uint8_t halo[];
+  uint32_t bx, by;
+  if (MODE == 0) {
+    nbb_lambda<S>(blockIdx.x, blockIdx.y, rb, st, bx, by);
+  } else {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+    if (!nbb_member<S>(bx, by, rb, st.mask)) return;
+  }
+  const int t = blockDim.x, h = t + 2, levels = rb + j;
+  const int tid = threadIdx.y * t + threadIdx.x;
+  const int64_t x0 = (int64_t)bx * t - 1, y0 = (int64_t)by * t - 1;
+  for (int i = tid; i < h * h; i += t * t) {
+    const int64_t gx = x0 + i % h, gy = y0 + i / h;
+    uint8_t v = 0;
+    if (gx >= 0 && gy >= 0 && gx < n && gy < n && nbb_member<S>((uint32_t)gx, (uint32_t)gy, levels, st.mask))
+      v = in[gy * n + gx] != 0;
+    halo[i] = v;
+  }
+  __syncthreads();
+  const int cx = threadIdx.x + 1, cy = threadIdx.y + 1;
+  int c = 0;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx)
+      if (dx || dy) c += halo[(cy + dy) * h + cx + dx];
+  const bool me = halo[cy * h + cx] != 0;
+  const bool alive = nbb_member<S>(threadIdx.x, threadIdx.y, j, st.mask) && (c == 3 || (me && c == 2));
+  out[(y0 + cy) * n + x0 + cx] = alive ? 1 : 0;
+}
+
 int64_t ipow64(int64_t b, int e) {
   int64_t r = 1;
   while (e-- > 0) r *= b;
@@ -264,6 +306,52 @@ int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int
       break;
   }
   return status_of(cudaGetLastError());
+}
+
+int fractal_nbb_step_ca(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, uint8_t* dev_a,
+                        uint8_t* dev_b, int steps, void* stream) {
+  NbbStep st;
+  if (make_step(s, k, cells_xy, st) != FRACTAL_OK || r_b < 0 || j < 0 || !dev_a || !dev_b || dev_a == dev_b ||
+      steps < 0 || (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB))
+    return FRACTAL_EINVAL;
+  const int64_t t = ipow64(s, j);
+  if (t > 32) return FRACTAL_EINVAL;
+  const int64_t nb = ipow64(s, r_b), n = nb * t;
+  if (n > (int64_t)1 << 20) return FRACTAL_EINVAL;
+  const int64_t W = ipow64(k, (r_b + 1) / 2), H = ipow64(k, r_b / 2);
+  dim3 grid;
+  if (mode == FRACTAL_LAMBDA) {
+    if (W > 0x7fffffff || H > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)W, (unsigned)H);
+  } else {
+    if (nb > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)nb, (unsigned)nb);
+  }
+  const dim3 block((unsigned)t, (unsigned)t);
+  const size_t smem = (size_t)(t + 2) * (t + 2);
+  cudaStream_t cs = (cudaStream_t)stream;
+  const bool lam = mode == FRACTAL_LAMBDA;
+  for (int i = 0; i < steps; ++i) {
+    const uint8_t* in = (i & 1) ? dev_b : dev_a;
+    uint8_t* out = (i & 1) ? dev_a : dev_b;
+    switch (s) {
+      case 2:
+        if (lam) nbb_ca_kernel<2, 0><<<grid, block, smem, cs>>>(st, r_b, j, n, in, out);
+        else nbb_ca_kernel<2, 1><<<grid, block, smem, cs>>>(st, r_b, j, n, in, out);
+        break;
+      case 3:
+        if (lam) nbb_ca_kernel<3, 0><<<grid, block, smem, cs>>>(st, r_b, j, n, in, out);
+        else nbb_ca_kernel<3, 1><<<grid, block, smem, cs>>>(st, r_b, j, n, in, out);
+        break;
+      default:
+        if (lam) nbb_ca_kernel<4, 0><<<grid, block, smem, cs>>>(st, r_b, j, n, in, out);
+        else nbb_ca_kernel<4, 1><<<grid, block, smem, cs>>>(st, r_b, j, n, in, out);
+        break;
+    }
+    const int e = status_of(cudaGetLastError());
+    if (e != FRACTAL_OK) return e;
+  }
+  return FRACTAL_OK;
 }
 
 }  // extern "C"

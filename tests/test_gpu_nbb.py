@@ -140,3 +140,57 @@ def test_nbb_validation(fr):
         fr.fractal_nbb_map_blocks(s, cells, 11, xy)                 # 8^11 blocks > 2^31 - 1
     with pytest.raises(fr.FractalError):
         fr.fractal_nbb_map_blocks(s, cells, -1, xy)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("rb,j,steps", [(2, 1, 1), (3, 1, 4), (1, 2, 3), (4, 0, 2), (2, 2, 5)])
+def test_ca_matches_oracle(fr, name, rb, j, steps, mode):
+    """The CA test on other NBB fractals, bit for bit against the oracle, both
+    launches; non-member cells hold noise that must be ignored, cells outside
+    member tiles of the output stay as they were."""
+    s, cells = step(name)
+    if s ** j > 32 or (s ** (rb + j)) ** 2 > 1 << 22:
+        pytest.skip("size")
+    n = s ** (rb + j)
+    rng = np.random.default_rng(11 + rb + j)
+    a0 = (rng.random((n, n)) < 0.5).astype(np.uint8)
+    a0[~nbb.member_mask(name, rb + j)] = 9                  # noise off the fractal
+    a = torch.from_numpy(a0.reshape(-1)).cuda()
+    b = torch.full_like(a, 7)
+    res = fr.fractal_nbb_step_ca(s, cells, rb, j, mode, a, b, steps)
+    got = res.cpu().numpy().reshape(n, n)
+    want = a0.copy()
+    for _ in range(steps):
+        want = nbb.ca_step(name, rb + j, want)
+    in_tile = np.kron(nbb.member_mask(name, rb), np.ones((s ** j, s ** j), dtype=bool))
+    assert np.array_equal(got[in_tile], want[in_tile])
+    outside = a0 if steps % 2 == 0 else np.full((n, n), 7, dtype=np.uint8)
+    assert np.array_equal(got[~in_tile], outside[~in_tile])
+
+
+@pytest.mark.parametrize("name", ["carpet", "vicsek"])
+def test_ca_lambda_and_bb_agree_large(fr, name):
+    s, cells = step(name)
+    rb, j = 6, 2
+    n = s ** (rb + j)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    a0 = (torch.rand(n * n, device="cuda", generator=g) < 0.5).to(torch.uint8)
+    outs = []
+    for mode in (0, 1):
+        a = a0.clone()
+        b = torch.zeros_like(a)
+        outs.append(fr.fractal_nbb_step_ca(s, cells, rb, j, mode, a, b, 10).clone())
+    assert torch.equal(outs[0], outs[1])
+    assert int(outs[0].sum()) > 0
+
+
+def test_ca_validation(fr):
+    s, cells = step("carpet")
+    a = torch.zeros(81 * 81, dtype=torch.uint8, device="cuda")
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_step_ca(s, cells, 2, 2, 0, a, a, 1)         # same buffer
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_step_ca(s, cells, 2, 4, 0, a, torch.zeros_like(a), 1)   # tile side 81
+    with pytest.raises(fr.FractalError):
+        fr.fractal_nbb_step_ca(s, cells, 2, 2, 0, a, torch.zeros_like(a), -1)
