@@ -904,8 +904,9 @@ def nbb_forms(fr, torch, stream, hbm):
     """Other NBB fractals: the single write of Sec. 6.2 with one CTA of 9 x 9
     threads per 9 x 9 tile, lambda launch against BB launch (Theorem 2's
     speedup), and with one CTA of 256 threads per super-tile of 9 x 9 or
-    27 x 27 tiles (`supertiles`), and the CA test of Sec. 6.2 (`ca`, uint8,
-    one CTA per 9 x 9 tile with its halo in shared memory), on the carpet at level 9 (19683^2 floats), the Vicsek and
+    27 x 27 tiles (`supertiles`), the reduce test over the written field
+    (`reduce`, FP64 partial per tile) and the CA test of Sec. 6.2 (`ca`,
+    uint8, one CTA per 9 x 9 tile with its halo in shared memory), on the carpet at level 9 (19683^2 floats), the Vicsek and
     X-fractal at level 10 (59049^2) and the H-fractal at level 9; and the
     generic lambda map's block rate (fractal_nbb_map_blocks) at about 10^7
     blocks.  Times are CUDA-event means of repeated calls."""
@@ -941,6 +942,12 @@ def nbb_forms(fr, torch, stream, hbm):
             st[m] = (clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 0, 1.0, b, stream, cta_levels=m)),
                      clock(lambda: fr.fractal_nbb_write(s, cells, rb, j, 1, 1.0, b, stream, cta_levels=m)))
         alg = k ** rb * 81 * 4
+        # the reduce test (Sec. 6.2 RD) over the field just written, FP64 partials per tile
+        parts = torch.empty(max(k ** rb, (s ** rb) ** 2), dtype=torch.float64, device="cuda")
+        rd_out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        rd_t = [clock(lambda: fr.fractal_nbb_reduce(s, cells, rb, j, md, b, parts, rd_out, stream)) for md in (0, 1)]
+        rd_ok = rd_out.item() == float(k ** (rb + j))          # the field holds 1.0 at every member
+        del parts
         # the CA test (Sec. 6.2) on the same fractal, uint8, 10 steps, one CTA per 9 x 9 tile
         ca_a = torch.zeros(n * n, dtype=torch.uint8, device="cuda")
         ca_b = torch.zeros_like(ca_a)
@@ -954,6 +961,9 @@ def nbb_forms(fr, torch, stream, hbm):
                      "lambda_us": tl * 1e6, "bb_us": tb * 1e6, "speedup_lambda_over_bb": tb / tl,
                      "lambda_alg_gbs": alg / tl / 1e9, "lambda_frac_hbm": alg / tl / 1e9 / hbm,
                      "bb_ctas": (s ** rb) ** 2, "lambda_ctas": k ** rb,
+                     "reduce": {"lambda_us": rd_t[0] * 1e6, "bb_us": rd_t[1] * 1e6,
+                                "speedup_lambda_over_bb": rd_t[1] / rd_t[0],
+                                "lambda_alg_gbs": alg / rd_t[0] / 1e9, "sum_equals_members": rd_ok},
                      "ca": {"lambda_us_per_step": ca_t[0] * 1e6, "bb_us_per_step": ca_t[1] * 1e6,
                             "speedup_lambda_over_bb": ca_t[1] / ca_t[0],
                             "cell_updates_per_s_lambda": k ** (rb + j) / ca_t[0]},

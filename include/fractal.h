@@ -680,6 +680,22 @@ int fractal_nbb_write(int s, int k, const int32_t* cells_xy, int r_b, int j, int
 int fractal_nbb_step_ca(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, uint8_t* dev_a,
                         uint8_t* dev_b, int steps, void* stream);
 
+/*
+ * fractal_nbb_reduce -- the reduce test of Sec. 6.2 (RD): *dev_out = the sum
+ * of dev_buf over the member cells of the level-(r_b + j) fractal (n*n
+ * floats; non-member cells are not read), in FP64.  One CTA per tile of side
+ * t = s^j (t * t threads rounded up to whole warps), each writing its FP64
+ * partial into dev_partials (caller-owned: k^r_b doubles for
+ * FRACTAL_LAMBDA, s^(2 r_b) for FRACTAL_BB, whose CTAs on non-member tiles
+ * write 0); one CTA then adds the partials in a fixed order, so the result
+ * does not vary from call to call.  Asynchronous; calls sharing dev_partials
+ * must not overlap.  Errors: FRACTAL_EINVAL (step, sizes as
+ * fractal_nbb_step_ca, NULL pointers, partials_len below the launch's CTA
+ * count, mode), FRACTAL_ECUDA.
+ */
+int fractal_nbb_reduce(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, const float* dev_buf,
+                       double* dev_partials, int64_t partials_len, double* dev_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent gaskets of uneven levels in one launch.
  *

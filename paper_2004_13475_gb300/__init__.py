@@ -51,7 +51,7 @@ EXPORTS = (
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
     "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_trajectory_df_io",
     "fractal_kappa_gradient_df", "fractal_kappa_gradient_df_io", "fractal_nbb_map_blocks", "fractal_nbb_write",
-    "fractal_nbb_step_ca",
+    "fractal_nbb_step_ca", "fractal_nbb_reduce",
     "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
     "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
@@ -124,6 +124,8 @@ def _load() -> ctypes.CDLL:
         "fractal_nbb_map_blocks": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, VP, VP]),
         "fractal_nbb_write": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, I, F, VP, VP]),
         "fractal_nbb_step_ca": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, VP, VP, I, VP]),
+        "fractal_nbb_reduce": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, VP, VP, ctypes.c_int64, VP,
+                                   VP]),
         "fractal_map_write": (I, [P, VP, I, D, VP]),
         "fractal_step_ca": (I, [P, VP, VP, I, VP]),
         "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
@@ -398,6 +400,15 @@ def fractal_nbb_step_ca(s: int, cells, r_b: int, j: int, mode: int, dev_a, dev_b
     _check(_load().fractal_nbb_step_ca(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
                                        _ptr(dev_a), _ptr(dev_b), int(steps), _stream(stream)), "fractal_nbb_step_ca")
     return dev_a if steps % 2 == 0 else dev_b
+
+
+def fractal_nbb_reduce(s: int, cells, r_b: int, j: int, mode: int, dev_buf, dev_partials, dev_out,
+                       stream=None) -> None:
+    """Sum over the members of the level-(r_b + j) NBB fractal into dev_out
+    (FP64), one CTA per tile of side s^j; dev_partials: one double per CTA."""
+    _check(_load().fractal_nbb_reduce(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
+                                      _ptr(dev_buf), _ptr(dev_partials), int(dev_partials.numel()), _ptr(dev_out),
+                                      _stream(stream)), "fractal_nbb_reduce")
 
 
 FRACTAL_MAP_BALLOT = 0

@@ -186,6 +186,62 @@ __global__ void nbb_ca_kernel(NbbStep st, int rb, int j, int64_t n, const uint8_
   out[(y0 + cy) * n + x0 + cx] = alive ? 1 : 0;
 }
 
+// Block-wide FP64 sum in a fixed order (warp trees over the linear thread
+// index, then the first warp over the warps); the result in thread 0.
+__device__ __forceinline__ double nbb_block_sum(double v) {
+  __shared__ double red[32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (tid < 32) {
+    t = tid < (nthreads + 31) / 32 ? red[tid] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+// The reduce test (Sec. 6.2 RD) on a tile per CTA: thread i < t * t takes
+// cell (i mod t, i div t) if it is a member, and the CTA's FP64 sum goes to
+// its partial (0 for a BB CTA on a non-member tile).  The CTA is one
+// dimension of t * t threads rounded up to whole warps (the warp trees use
+// full masks), the threads beyond t * t idle.
+template <int S, int MODE>
+__global__ void nbb_reduce_kernel(NbbStep st, int rb, int j, int t, int64_t n, const float* __restrict__ in,
+                                  double* __restrict__ partials) {
+  uint32_t bx, by;
+  const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  const int tid = threadIdx.x;
+  bool tile = true;
+  if (MODE == 0) {
+    nbb_lambda<S>(blockIdx.x, blockIdx.y, rb, st, bx, by);
+  } else {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+    tile = nbb_member<S>(bx, by, rb, st.mask);
+  }
+  double v = 0.0;
+  if (tile && tid < t * t) {
+    const int cx = tid % t, cy = tid / t;
+    if (nbb_member<S>((uint32_t)cx, (uint32_t)cy, j, st.mask))
+      v = (double)in[((int64_t)by * t + cy) * n + (int64_t)bx * t + cx];
+  }
+  const double sum = nbb_block_sum(v);
+  if (tid == 0) partials[cta] = sum;
+}
+
+// Sum of `count` partials in a fixed order, one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) nbb_final_sum_kernel(const double* __restrict__ partials, int64_t count,
+                                                             double* __restrict__ out) {
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) acc += partials[i];
+  const double s = nbb_block_sum(acc);
+  if (threadIdx.x == 0) *out = s;
+}
+
 int64_t ipow64(int64_t b, int e) {
   int64_t r = 1;
   while (e-- > 0) r *= b;
@@ -352,6 +408,54 @@ int fractal_nbb_step_ca(int s, int k, const int32_t* cells_xy, int r_b, int j, i
     if (e != FRACTAL_OK) return e;
   }
   return FRACTAL_OK;
+}
+
+int fractal_nbb_reduce(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, const float* dev_buf,
+                       double* dev_partials, int64_t partials_len, double* dev_out, void* stream) {
+  NbbStep st;
+  if (make_step(s, k, cells_xy, st) != FRACTAL_OK || r_b < 0 || j < 0 || !dev_buf || !dev_partials || !dev_out ||
+      (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB))
+    return FRACTAL_EINVAL;
+  const int64_t t = ipow64(s, j);
+  if (t > 32) return FRACTAL_EINVAL;
+  const int64_t nb = ipow64(s, r_b), n = nb * t;
+  if (n > (int64_t)1 << 20) return FRACTAL_EINVAL;
+  const int64_t W = ipow64(k, (r_b + 1) / 2), H = ipow64(k, r_b / 2);
+  dim3 grid;
+  int64_t ctas;
+  if (mode == FRACTAL_LAMBDA) {
+    if (W > 0x7fffffff || H > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)W, (unsigned)H);
+    ctas = W * H;
+  } else {
+    if (nb > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)nb, (unsigned)nb);
+    ctas = nb * nb;
+  }
+  if (partials_len < ctas) return FRACTAL_EINVAL;
+  // t * t threads rounded up to whole warps
+  const dim3 block((unsigned)((t * t + 31) / 32 * 32));
+  cudaStream_t cs = (cudaStream_t)stream;
+  const bool lam = mode == FRACTAL_LAMBDA;
+  const int ti = (int)t;
+  switch (s) {
+    case 2:
+      if (lam) nbb_reduce_kernel<2, 0><<<grid, block, 0, cs>>>(st, r_b, j, ti, n, dev_buf, dev_partials);
+      else nbb_reduce_kernel<2, 1><<<grid, block, 0, cs>>>(st, r_b, j, ti, n, dev_buf, dev_partials);
+      break;
+    case 3:
+      if (lam) nbb_reduce_kernel<3, 0><<<grid, block, 0, cs>>>(st, r_b, j, ti, n, dev_buf, dev_partials);
+      else nbb_reduce_kernel<3, 1><<<grid, block, 0, cs>>>(st, r_b, j, ti, n, dev_buf, dev_partials);
+      break;
+    default:
+      if (lam) nbb_reduce_kernel<4, 0><<<grid, block, 0, cs>>>(st, r_b, j, ti, n, dev_buf, dev_partials);
+      else nbb_reduce_kernel<4, 1><<<grid, block, 0, cs>>>(st, r_b, j, ti, n, dev_buf, dev_partials);
+      break;
+  }
+  int e = status_of(cudaGetLastError());
+  if (e != FRACTAL_OK) return e;
+  nbb_final_sum_kernel<<<1, 1024, 0, cs>>>(dev_partials, ctas, dev_out);
+  return status_of(cudaGetLastError());
 }
 
 }  // extern "C"

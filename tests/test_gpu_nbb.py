@@ -194,3 +194,34 @@ def test_ca_validation(fr):
         fr.fractal_nbb_step_ca(s, cells, 2, 4, 0, a, torch.zeros_like(a), 1)   # tile side 81
     with pytest.raises(fr.FractalError):
         fr.fractal_nbb_step_ca(s, cells, 2, 2, 0, a, torch.zeros_like(a), -1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("rb,j", [(2, 1), (3, 2), (4, 0), (5, 1)])
+def test_reduce_matches_oracle(fr, name, rb, j, mode):
+    """The sum over the members (FP64) against the oracle's FP64 sum, with NaN
+    off the fractal that must not be read; the same result on a second call;
+    a partials array too short for the launch is refused."""
+    s, cells = step(name)
+    if s ** j > 32 or (s ** (rb + j)) ** 2 > 1 << 22:
+        pytest.skip("size")
+    k = len(cells)
+    n = s ** (rb + j)
+    rng = np.random.default_rng(21 + rb)
+    x = rng.random((n, n)).astype(np.float32)
+    mask = nbb.member_mask(name, rb + j)
+    x[~mask] = np.nan
+    buf = torch.from_numpy(x.reshape(-1)).cuda()
+    parts = torch.zeros(k ** rb if mode == 0 else s ** (2 * rb), dtype=torch.float64, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fr.fractal_nbb_reduce(s, cells, rb, j, mode, buf, parts, out)
+    got = out.item()
+    want = oracle.reduce_sum(x[mask].astype(np.float64))
+    assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+    fr.fractal_nbb_reduce(s, cells, rb, j, mode, buf, parts, out)
+    assert out.item() == got
+    short = torch.zeros(parts.numel() - 1, dtype=torch.float64, device="cuda")
+    if short.numel() > 0:
+        with pytest.raises(fr.FractalError):
+            fr.fractal_nbb_reduce(s, cells, rb, j, mode, buf, short, out)
