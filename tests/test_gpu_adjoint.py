@@ -377,3 +377,21 @@ def test_gradient_pass_start_and_float32_result(fr, mode):
         fr.fractal_kappa_gradient_df_io(plan, ut, pt, None, True, g32, A, steps)    # nothing to add to
     with pytest.raises(fr.FractalError):
         fr.fractal_kappa_gradient_df_io(plan, ut, pt, None, False, None, A, steps)  # nowhere to write
+
+
+def test_fused_gradients_float64_kappa(fr):
+    """A float64 kappa takes the double-float dJ/dkappa sum through a cleared
+    buffer and the torch conversion; rounded to float32 it equals the float32
+    kappa's result, which the last gradient pass writes as float32 itself."""
+    k, steps, every = 8, 45, 20
+    u0, kappa, target = fields(k, 150)
+    from paper_2004_13475_gb300.autograd import diffusion_kappa
+    res = []
+    for dt in (torch.float32, torch.float64):
+        u = dev(u0).requires_grad_(True)
+        kp = dev(kappa).to(dt).requires_grad_(True)
+        loss = ((diffusion_kappa(u, kp, k, A, steps, every) - dev(target)) ** 2).sum()
+        loss.backward()
+        assert kp.grad.dtype == dt
+        res.append((u.grad.clone(), kp.grad.float()))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
