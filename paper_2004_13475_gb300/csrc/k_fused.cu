@@ -1184,8 +1184,10 @@ __global__ void __launch_bounds__(kKapThreads, 3) kappa_fused_df_kernel(const df
 // write of the embedded double-float array).  One CTA per super-tile (side
 // as the fused launch), one thread per member block; the super-tile's two
 // records of a step (contiguous) and the port neighbours' values are copied
-// into shared memory asynchronously one step ahead (cp.async, two stages),
-// so that the loads of step s + 1 overlap the sums of step s.
+// into shared memory (cp.async) before the step's sums.  One stage of 41 KB
+// lets four CTAs share an SM, whose copies and sums overlap one another's
+// (205 against 221 us per 20-step segment at k = 13 for two stages and two
+// CTAs per SM).
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -1203,7 +1205,7 @@ constexpr int kGradThreads = 96;
 __host__ __device__ inline int kgrad_stage_bytes(int nb) { return 2 * nb * kKRecF4 * 16 + nb * 8 * 8; }
 
 template <int MODE>
-__global__ void __launch_bounds__(kGradThreads, 2) kappa_grad_df_kernel(const float4* __restrict__ utraj,
+__global__ void __launch_bounds__(kGradThreads, 4) kappa_grad_df_kernel(const float4* __restrict__ utraj,
                                                                           const float4* __restrict__ ptraj,
                                                                           int64_t stride, dfloat* __restrict__ gk,
                                                                           dfloat ha, int nsteps, Geo g, int accumulate,
@@ -1272,15 +1274,10 @@ __global__ void __launch_bounds__(kGradThreads, 2) kappa_grad_df_kernel(const fl
     cp_async_commit();
   };
   DfSum gs[kB * kB];
-  load(0, 0);
   for (int s = 0; s < nsteps; ++s) {
-    const int b = s & 1;
-    if (s + 1 < nsteps) {
-      load(b ^ 1, s + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    const int b = 0;  // one stage
+    load(b, s);
+    cp_async_wait<0>();
     __syncthreads();
     if (act) {
       dfloat u[kB * kB], p[kB * kB];
@@ -1313,7 +1310,7 @@ __global__ void __launch_bounds__(kGradThreads, 2) kappa_grad_df_kernel(const fl
         gs[q].add((dfloat(a.x, a.y) - u[q]) * (p[q] - dfloat(c.x, c.y)));
       }
     }
-    __syncthreads();  // stage b is refilled by the next iteration's copies
+    __syncthreads();  // the stage is refilled by the next step's copies
   }
   if (!act) return;
   // gk += (a / 2) sums (gk taken as 0 without `accumulate`), into gk, or
@@ -1737,7 +1734,7 @@ cudaError_t launch_kappa_grad_df(int mode, int k, const float4* utraj, const flo
   int margin = 0;
   if (!kappa_fused_geometry(k, mode, L, margin) || nsteps < 1) return cudaErrorInvalidValue;
   const int64_t stride = kappa_record_float4s(k);
-  const int smem = 2 * kgrad_stage_bytes(member_blocks(L.geo.T));
+  const int smem = kgrad_stage_bytes(member_blocks(L.geo.T));
   auto run = [&](auto* k) -> cudaError_t {
     cudaError_t e = allow_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
