@@ -199,3 +199,23 @@ def ca_write(name: str, r_b: int, j: int, alive: np.ndarray) -> np.ndarray:
     in_tile = np.kron(member_mask(name, r_b), np.ones((t, t), dtype=bool))
     nxt[~in_tile] = np.nan
     return nxt
+
+
+def diffusion_step(name: str, r: int, u: np.ndarray, a: float) -> np.ndarray:
+    """One explicit heat-diffusion step on the level-r fractal, FP64 (the
+    gasket's step, read the same way for the family): at a member c,
+    u'_c = u_c + a * sum over its member 4-neighbours nb of (u_nb - u_c);
+    non-members (and cells outside the array) carry no flux, so the sum over
+    the members is conserved; non-members are returned as 0."""
+    mask = member_mask(name, r)
+    n = mask.shape[0]
+    v = np.where(mask, np.asarray(u, dtype=np.float64), 0.0)
+    pv = np.zeros((n + 2, n + 2))
+    pm = np.zeros((n + 2, n + 2), dtype=bool)
+    pv[1:-1, 1:-1] = v
+    pm[1:-1, 1:-1] = mask
+    flux = np.zeros((n, n))
+    for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+        nb = pm[1 + dy:n + 1 + dy, 1 + dx:n + 1 + dx]
+        flux += np.where(nb, pv[1 + dy:n + 1 + dy, 1 + dx:n + 1 + dx] - v, 0.0)
+    return np.where(mask, v + a * flux, 0.0)

@@ -117,3 +117,48 @@ def test_ca_still_life_and_dead_field():
         nxt = nbb.ca_step("carpet", r, nxt)
     assert np.array_equal(nxt, alive)
     assert not nbb.ca_step("vicsek", r, np.zeros((n, n), dtype=np.uint8)).any()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_diffusion_conserves_heat_and_keeps_constants(name):
+    """Zero-flux walls: the sum over the members is conserved; a constant
+    field on the members is a fixed point."""
+    s, _, _ = nbb.FRACTALS[name]
+    r = 3
+    n = s ** r
+    mask = nbb.member_mask(name, r)
+    rng = np.random.default_rng(5)
+    u = rng.random((n, n))
+    total = u[mask].sum()
+    v = u
+    for _ in range(20):
+        v = nbb.diffusion_step(name, r, v, 0.2)
+    assert abs(v[mask].sum() - total) <= 1e-12 * total
+    c = nbb.diffusion_step(name, r, np.full((n, n), 2.5), 0.2)
+    assert np.all(c[mask] == 2.5) and np.all(c[~mask] == 0)
+
+
+def test_diffusion_gasket_case_is_the_gasket_step():
+    r = 6
+    n = 1 << r
+    rng = np.random.default_rng(9)
+    u = rng.random((n, n))
+    dom = oracle.Domain.build(n)
+    a = u
+    for _ in range(5):
+        a = nbb.diffusion_step("gasket", r, a, 0.2)
+    b = oracle.diffusion_run(u, 5, 0.2, dom)
+    mask = dom.mask
+    assert np.allclose(a[mask], b[mask], rtol=0, atol=1e-14)
+
+
+def test_diffusion_hand_example_vicsek_level_1():
+    """Level 1 of the Vicsek plus: the centre (1,1) has four member neighbours,
+    each arm cell one (the centre)."""
+    u = np.zeros((3, 3))
+    u[1, 1] = 1.0
+    v = nbb.diffusion_step("vicsek", 1, u, 0.2)
+    assert v[1, 1] == pytest.approx(1.0 - 4 * 0.2)
+    for y, x in ((0, 1), (1, 0), (1, 2), (2, 1)):
+        assert v[y, x] == pytest.approx(0.2)
+    assert v[0, 0] == 0 and v[2, 2] == 0
