@@ -905,8 +905,9 @@ def nbb_forms(fr, torch, stream, hbm):
     threads per 9 x 9 tile, lambda launch against BB launch (Theorem 2's
     speedup), and with one CTA of 256 threads per super-tile of 9 x 9 or
     27 x 27 tiles (`supertiles`), the reduce test over the written field
-    (`reduce`, FP64 partial per tile) and the CA test of Sec. 6.2 (`ca`,
-    uint8, one CTA per 9 x 9 tile with its halo in shared memory), on the carpet at level 9 (19683^2 floats), the Vicsek and
+    (`reduce`, FP64 partial per tile), the CA test of Sec. 6.2 (`ca`, uint8)
+    and the FP32 diffusion (`diffusion`), one CTA per 9 x 9 tile with its halo
+    in shared memory, on the carpet at level 9 (19683^2 floats), the Vicsek and
     X-fractal at level 10 (59049^2) and the H-fractal at level 9; and the
     generic lambda map's block rate (fractal_nbb_map_blocks) at about 10^7
     blocks.  Times are CUDA-event means of repeated calls."""
@@ -954,6 +955,12 @@ def nbb_forms(fr, torch, stream, hbm):
         ca_t = [clock(lambda: fr.fractal_nbb_step_ca(s, cells, rb, j, md, ca_a, ca_b, 10, stream), reps=3) / 10
                 for md in (0, 1)]
         del ca_a, ca_b
+        # FP32 diffusion on the same fractal, 10 steps, one CTA per 9 x 9 tile
+        d_a = torch.zeros(n * n, dtype=torch.float32, device="cuda")
+        d_b = torch.zeros_like(d_a)
+        df_t = [clock(lambda: fr.fractal_nbb_step_diffusion(s, cells, rb, j, md, d_a, d_b, 0.2, 10, stream), reps=3) / 10
+                for md in (0, 1)]
+        del d_a, d_b
         rm = max(r for r in range(1, 30) if k ** r <= 20_000_000)
         xy = torch.empty(2 * k ** rm, dtype=torch.int32, device="cuda")
         tm = clock(lambda: fr.fractal_nbb_map_blocks(s, cells, rm, xy, stream))
@@ -964,6 +971,9 @@ def nbb_forms(fr, torch, stream, hbm):
                      "reduce": {"lambda_us": rd_t[0] * 1e6, "bb_us": rd_t[1] * 1e6,
                                 "speedup_lambda_over_bb": rd_t[1] / rd_t[0],
                                 "lambda_alg_gbs": alg / rd_t[0] / 1e9, "sum_equals_members": rd_ok},
+                     "diffusion": {"lambda_us_per_step": df_t[0] * 1e6, "bb_us_per_step": df_t[1] * 1e6,
+                                   "speedup_lambda_over_bb": df_t[1] / df_t[0],
+                                   "cell_updates_per_s_lambda": k ** (rb + j) / df_t[0]},
                      "ca": {"lambda_us_per_step": ca_t[0] * 1e6, "bb_us_per_step": ca_t[1] * 1e6,
                             "speedup_lambda_over_bb": ca_t[1] / ca_t[0],
                             "cell_updates_per_s_lambda": k ** (rb + j) / ca_t[0]},

@@ -681,6 +681,21 @@ int fractal_nbb_step_ca(int s, int k, const int32_t* cells_xy, int r_b, int j, i
                         uint8_t* dev_b, int steps, void* stream);
 
 /*
+ * fractal_nbb_step_diffusion -- `steps` explicit heat-diffusion steps (float32,
+ * u' = u + a * (sum over member 4-neighbours of u_nb - degree * u), zero flux
+ * at non-members and at the array's edge, the FDM step of Sec. 1 read as for
+ * the gasket) on the level-(r_b + j) fractal (dev_a, dev_b: n*n floats,
+ * distinct, 4-byte aligned), alternating dev_a -> dev_b -> dev_a ... as
+ * fractal_nbb_step_ca; one CTA of t x t threads per tile of side t = s^j,
+ * the tile and its halo staged in shared memory, by the lambda or the BB
+ * launch.  Only member cells are read; member tiles are written (0 at their
+ * non-member cells), no other cell.  Asynchronous.  Errors: FRACTAL_EINVAL
+ * (as fractal_nbb_step_ca, and a NaN), FRACTAL_ECUDA.
+ */
+int fractal_nbb_step_diffusion(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, float* dev_a,
+                               float* dev_b, float a, int steps, void* stream);
+
+/*
  * fractal_nbb_reduce -- the reduce test of Sec. 6.2 (RD): *dev_out = the sum
  * of dev_buf over the member cells of the level-(r_b + j) fractal (n*n
  * floats; non-member cells are not read), in FP64.  One CTA per tile of side

@@ -51,7 +51,7 @@ EXPORTS = (
     "fractal_fused_box_blocks", "fractal_plan_selftest_wait", "fractal_debug_fail_allocs",
     "fractal_kappa_fused_limits", "fractal_kappa_trajectory_df", "fractal_kappa_trajectory_df_io",
     "fractal_kappa_gradient_df", "fractal_kappa_gradient_df_io", "fractal_nbb_map_blocks", "fractal_nbb_write",
-    "fractal_nbb_step_ca", "fractal_nbb_reduce",
+    "fractal_nbb_step_ca", "fractal_nbb_reduce", "fractal_nbb_step_diffusion",
     "fractal_plan_set_kappa_fusion", "fractal_plan_records_bytes", "fractal_records_from_array",
     "fractal_records_to_array", "fractal_step_diffusion_records", "fractal_step_ca_records",
 )
@@ -126,6 +126,7 @@ def _load() -> ctypes.CDLL:
         "fractal_nbb_step_ca": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, VP, VP, I, VP]),
         "fractal_nbb_reduce": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, VP, VP, ctypes.c_int64, VP,
                                    VP]),
+        "fractal_nbb_step_diffusion": (I, [I, I, ctypes.POINTER(ctypes.c_int32), I, I, I, VP, VP, F, I, VP]),
         "fractal_map_write": (I, [P, VP, I, D, VP]),
         "fractal_step_ca": (I, [P, VP, VP, I, VP]),
         "fractal_step_diffusion": (I, [P, VP, VP, F, I, VP]),
@@ -409,6 +410,16 @@ def fractal_nbb_reduce(s: int, cells, r_b: int, j: int, mode: int, dev_buf, dev_
     _check(_load().fractal_nbb_reduce(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
                                       _ptr(dev_buf), _ptr(dev_partials), int(dev_partials.numel()), _ptr(dev_out),
                                       _stream(stream)), "fractal_nbb_reduce")
+
+
+def fractal_nbb_step_diffusion(s: int, cells, r_b: int, j: int, mode: int, dev_a, dev_b, coef: float, steps: int,
+                               stream=None):
+    """`steps` float32 diffusion steps on the level-(r_b + j) NBB fractal, one
+    CTA per tile of side s^j; returns the buffer holding the result."""
+    _check(_load().fractal_nbb_step_diffusion(int(s), len(cells), _nbb_cells(cells), int(r_b), int(j), int(mode),
+                                              _ptr(dev_a), _ptr(dev_b), float(coef), int(steps), _stream(stream)),
+           "fractal_nbb_step_diffusion")
+    return dev_a if steps % 2 == 0 else dev_b
 
 
 FRACTAL_MAP_BALLOT = 0

@@ -242,6 +242,53 @@ __global__ void __launch_bounds__(1024) nbb_final_sum_kernel(const double* __res
   if (threadIdx.x == 0) *out = s;
 }
 
+// One explicit diffusion step (FP32) on a tile of t x t cells per CTA of
+// t x t threads, tile by lambda (MODE 0) or by identity with non-member
+// tiles returning (MODE 1): the tile and its one-cell halo are staged in
+// shared memory with a membership flag, non-members (and cells outside the
+// array) as 0 whatever they hold; each member then takes
+// fmaf(a, fmaf(-degree, u, sum), u), the sum and degree over its member
+// 4-neighbours in the order up, left, right, down; the tile's other cells
+// get 0.
+template <int S, int MODE>
+__global__ void nbb_diffusion_kernel(NbbStep st, int rb, int j, int64_t n, float a, const float* __restrict__ in,
+                                     float* __restrict__ out) {
+  extern __shared__ float hv[];  // (t + 2)^2 values, then (t + 2)^2 membership flags as floats (1 / 0)
+  uint32_t bx, by;
+  if (MODE == 0) {
+    nbb_lambda<S>(blockIdx.x, blockIdx.y, rb, st, bx, by);
+  } else {
+    bx = blockIdx.x;
+    by = blockIdx.y;
+    if (!nbb_member<S>(bx, by, rb, st.mask)) return;
+  }
+  const int t = blockDim.x, h = t + 2, levels = rb + j;
+  float* hm = hv + h * h;
+  const int tid = threadIdx.y * t + threadIdx.x;
+  const int64_t x0 = (int64_t)bx * t - 1, y0 = (int64_t)by * t - 1;
+  for (int i = tid; i < h * h; i += t * t) {
+    const int64_t gx = x0 + i % h, gy = y0 + i / h;
+    const bool m = gx >= 0 && gy >= 0 && gx < n && gy < n && nbb_member<S>((uint32_t)gx, (uint32_t)gy, levels, st.mask);
+    hv[i] = m ? in[gy * n + gx] : 0.f;
+    hm[i] = m ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int c = (threadIdx.y + 1) * h + threadIdx.x + 1;
+  float r = 0.f;
+  if (hm[c] != 0.f) {
+    const float u = hv[c];
+    const int nbs[4] = {c - h, c - 1, c + 1, c + h};
+    float sum = 0.f, deg = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sum += hv[nbs[q]];  // 0 at non-members
+      deg += hm[nbs[q]];
+    }
+    r = fmaf(a, fmaf(-deg, u, sum), u);
+  }
+  out[(y0 + threadIdx.y + 1) * n + x0 + threadIdx.x + 1] = r;
+}
+
 int64_t ipow64(int64_t b, int e) {
   int64_t r = 1;
   while (e-- > 0) r *= b;
@@ -456,6 +503,53 @@ int fractal_nbb_reduce(int s, int k, const int32_t* cells_xy, int r_b, int j, in
   if (e != FRACTAL_OK) return e;
   nbb_final_sum_kernel<<<1, 1024, 0, cs>>>(dev_partials, ctas, dev_out);
   return status_of(cudaGetLastError());
+}
+
+int fractal_nbb_step_diffusion(int s, int k, const int32_t* cells_xy, int r_b, int j, int mode, float* dev_a,
+                               float* dev_b, float a, int steps, void* stream) {
+  NbbStep st;
+  if (make_step(s, k, cells_xy, st) != FRACTAL_OK || r_b < 0 || j < 0 || !dev_a || !dev_b || dev_a == dev_b ||
+      steps < 0 || !(a == a) || (mode != FRACTAL_LAMBDA && mode != FRACTAL_BB) ||
+      (reinterpret_cast<uintptr_t>(dev_a) & 3u) != 0 || (reinterpret_cast<uintptr_t>(dev_b) & 3u) != 0)
+    return FRACTAL_EINVAL;
+  const int64_t t = ipow64(s, j);
+  if (t > 32) return FRACTAL_EINVAL;
+  const int64_t nb = ipow64(s, r_b), n = nb * t;
+  if (n > (int64_t)1 << 20) return FRACTAL_EINVAL;
+  const int64_t W = ipow64(k, (r_b + 1) / 2), H = ipow64(k, r_b / 2);
+  dim3 grid;
+  if (mode == FRACTAL_LAMBDA) {
+    if (W > 0x7fffffff || H > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)W, (unsigned)H);
+  } else {
+    if (nb > 65535) return FRACTAL_EINVAL;
+    grid = dim3((unsigned)nb, (unsigned)nb);
+  }
+  const dim3 block((unsigned)t, (unsigned)t);
+  const size_t smem = (size_t)2 * (t + 2) * (t + 2) * sizeof(float);
+  cudaStream_t cs = (cudaStream_t)stream;
+  const bool lam = mode == FRACTAL_LAMBDA;
+  for (int i = 0; i < steps; ++i) {
+    const float* in = (i & 1) ? dev_b : dev_a;
+    float* out = (i & 1) ? dev_a : dev_b;
+    switch (s) {
+      case 2:
+        if (lam) nbb_diffusion_kernel<2, 0><<<grid, block, smem, cs>>>(st, r_b, j, n, a, in, out);
+        else nbb_diffusion_kernel<2, 1><<<grid, block, smem, cs>>>(st, r_b, j, n, a, in, out);
+        break;
+      case 3:
+        if (lam) nbb_diffusion_kernel<3, 0><<<grid, block, smem, cs>>>(st, r_b, j, n, a, in, out);
+        else nbb_diffusion_kernel<3, 1><<<grid, block, smem, cs>>>(st, r_b, j, n, a, in, out);
+        break;
+      default:
+        if (lam) nbb_diffusion_kernel<4, 0><<<grid, block, smem, cs>>>(st, r_b, j, n, a, in, out);
+        else nbb_diffusion_kernel<4, 1><<<grid, block, smem, cs>>>(st, r_b, j, n, a, in, out);
+        break;
+    }
+    const int e = status_of(cudaGetLastError());
+    if (e != FRACTAL_OK) return e;
+  }
+  return FRACTAL_OK;
 }
 
 }  // extern "C"

@@ -225,3 +225,48 @@ def test_reduce_matches_oracle(fr, name, rb, j, mode):
     if short.numel() > 0:
         with pytest.raises(fr.FractalError):
             fr.fractal_nbb_reduce(s, cells, rb, j, mode, buf, short, out)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("rb,j,steps", [(2, 1, 1), (3, 1, 6), (1, 2, 3), (4, 0, 2), (2, 2, 25)])
+def test_diffusion_matches_oracle(fr, name, rb, j, steps, mode):
+    """FP32 diffusion on other NBB fractals against the FP64 oracle (relative
+    to the field's scale, 2e-6 + 1e-7 per step), NaN off the fractal ignored,
+    cells outside member tiles of the output untouched, heat conserved."""
+    s, cells = step(name)
+    if s ** j > 32 or (s ** (rb + j)) ** 2 > 1 << 22:
+        pytest.skip("size")
+    n = s ** (rb + j)
+    mask = nbb.member_mask(name, rb + j)
+    rng = np.random.default_rng(31 + rb + j)
+    u0 = rng.random((n, n)).astype(np.float32)
+    u0[~mask] = np.nan
+    a = torch.from_numpy(u0.reshape(-1)).cuda()
+    b = torch.full_like(a, SENTINEL)
+    res = fr.fractal_nbb_step_diffusion(s, cells, rb, j, mode, a, b, 0.2, steps)
+    got = res.cpu().numpy().reshape(n, n)
+    want = u0.astype(np.float64)
+    for _ in range(steps):
+        want = nbb.diffusion_step(name, rb + j, want, 0.2)
+    in_tile = np.kron(nbb.member_mask(name, rb), np.ones((s ** j, s ** j), dtype=bool))
+    assert np.all(got[in_tile & ~mask] == 0)
+    err = np.abs(got[mask].astype(np.float64) - want[mask]).max()
+    assert err <= (2e-6 + 1e-7 * steps) * max(1.0, np.abs(want[mask]).max())
+    outside = u0 if steps % 2 == 0 else np.full((n, n), SENTINEL, dtype=np.float32)
+    assert np.array_equal(got[~in_tile], outside[~in_tile], equal_nan=True)
+    assert abs(got[mask].astype(np.float64).sum() - u0[mask].astype(np.float64).sum()) <= 1e-5 * mask.sum()
+
+
+def test_diffusion_lambda_and_bb_agree_bit_for_bit(fr):
+    s, cells = step("vicsek")
+    rb, j = 6, 2
+    n = s ** (rb + j)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    u0 = torch.rand(n * n, device="cuda", generator=g)
+    outs = []
+    for mode in (0, 1):
+        a = u0.clone()
+        b = torch.zeros_like(a)
+        outs.append(fr.fractal_nbb_step_diffusion(s, cells, rb, j, mode, a, b, 0.2, 10).clone())
+    assert torch.equal(outs[0], outs[1])
