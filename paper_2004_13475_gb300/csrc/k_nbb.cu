@@ -18,11 +18,15 @@
 namespace {
 
 // The step in the kernels' parameter space: the cells in numbering order,
-// four bits each (x | y << 2, s <= 4: at most 16 cells), and the s x s
-// membership bits (bit dy * s + dx).
+// four bits each (x | y << 2, s <= 4: at most 16 cells), the s x s
+// membership bits (bit dy * s + dx), and kmagic = ceil(2^32 / k) (0 for
+// k = 1), with which floor(w / k) = umulhi(w, kmagic) for every w < 2^32 / k
+// (the error w * (kmagic - 2^32 / k) / 2^32 stays below 1 / k), so for every
+// block coordinate here (below 2^28: the grids are at most 2^20 wide).
 struct NbbStep {
   int s, k;
   uint32_t mask;
+  uint32_t kmagic;
   uint64_t cells;
 };
 
@@ -36,11 +40,13 @@ __device__ __forceinline__ void nbb_lambda(uint32_t wx, uint32_t wy, int r, cons
   for (int mu = 1; mu <= r; ++mu) {
     uint32_t d;
     if (mu & 1) {
-      d = wx % k;
-      wx /= k;
+      const uint32_t q = __umulhi(wx, st.kmagic);
+      d = wx - q * k;
+      wx = q;
     } else {
-      d = wy % k;
-      wy /= k;
+      const uint32_t q = __umulhi(wy, st.kmagic);
+      d = wy - q * k;
+      wy = q;
     }
     const uint32_t c = (uint32_t)(st.cells >> (4 * d)) & 15u;
     x += (c & 3u) * px;
@@ -302,6 +308,7 @@ int make_step(int s, int k, const int32_t* cells, NbbStep& st) {
   st = NbbStep{};
   st.s = s;
   st.k = k;
+  st.kmagic = k > 1 ? (uint32_t)(((uint64_t)1 << 32) / (uint64_t)k + ((((uint64_t)1 << 32) % (uint64_t)k) ? 1 : 0)) : 0u;
   for (int i = 0; i < k; ++i) {
     const int x = cells[2 * i], y = cells[2 * i + 1];
     if (x < 0 || y < 0 || x >= s || y >= s) return FRACTAL_EINVAL;
